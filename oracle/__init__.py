@@ -1,0 +1,264 @@
+"""Plain FP64 CPU oracle of the MGEnKF analysis cycle (ctypes wrapper).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The GPU library (``paper_2012_10091_gb300``) never imports it and
+shares no code with it: the two meet only through the seeded input generators
+in ``paper_2012_10091_gb300.workloads``, which hold none of the method's
+arithmetic.
+
+The arithmetic lives in ``oracle.c`` (FP64, literal, each routine citing the
+paper).  This module only marshals numpy arrays and sequences the cycle of
+Algorithm 4 (fine forecast, coarse member forecast, restriction, coarse EnKF
+analysis, prolonged correction, RMSE).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+# tag of the observation-perturbation stream in the Philox key (ASCII "EPS\0")
+EPS_TAG = 0x45505300
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, -O2, OpenMP, no fast-math)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
+        os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))
+    ):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+           "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            P = ctypes.c_void_p
+            i32, i64, u64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+            L.orc_philox4x64_10.argtypes = [P, P, P]
+            L.orc_normals.argtypes = [u64, u64, u64, i64, P]
+            L.orc_burgers_rhs.argtypes = [P, i32, f64, f64, i32, f64, P]
+            L.orc_burgers_rk3.argtypes = [P, i32, i32, f64, f64, f64, i32, i32, f64]
+            L.orc_ns2d_rhs.argtypes = [P, i32, f64, f64, f64, f64, P]
+            L.orc_ns2d_rk3.argtypes = [P, i32, i32, f64, f64, f64, f64, f64, i32]
+            L.orc_lagrange_weights.argtypes = [i32, P, f64, P]
+            L.orc_restrict.argtypes = [P, i32, i32, i32, i32, P]
+            L.orc_prolong_add.argtypes = [P, i32, i32, i32, i32, P]
+            L.orc_obs_coarse.argtypes = [P, i32, i32, i32, i32, i32, P, P, P]
+            L.orc_cholesky.argtypes = [P, i32]
+            L.orc_cholesky.restype = i32
+            L.orc_chol_solve.argtypes = [P, i32, P, i32]
+            L.orc_enkf_analyse.argtypes = [i32, i32, i32, i32, i32, i32, P, P, P, P, f64, i32, P, P, P]
+            L.orc_enkf_analyse.restype = i32
+            L.orc_enkf_gain.argtypes = [i32, i32, i32, P, P, P, P]
+            L.orc_enkf_gain.restype = i32
+            L.orc_rmse.argtypes = [P, P, i32, i64, P]
+            _LIB = L
+    return _LIB
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# --------------------------------------------------------------------------
+# primitives
+# --------------------------------------------------------------------------
+def philox4x64_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    lib().orc_philox4x64_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def normals(seed: int, tag: int, ctr0: int, count: int) -> np.ndarray:
+    z = np.zeros(max(count, 1), dtype=np.float64)
+    lib().orc_normals(seed, tag, ctr0, count, _p(z))
+    return z[:count]
+
+
+def obs_perturbations(seed: int, cycle: int, ne: int, ny: int, sigma: float) -> np.ndarray:
+    """eps^(i) ~ N(0, sigma^2 I) for one analysis (Eq. perturbed_y), ne x ny."""
+    return sigma * normals(seed, EPS_TAG, cycle, ne * ny).reshape(ne, ny)
+
+
+def burgers_rhs(u, dx, nu, flux_kind=0, c=0.0) -> np.ndarray:
+    u = _f64(u)
+    L = np.zeros_like(u)
+    lib().orc_burgers_rhs(_p(u), u.size, dx, nu, flux_kind, c, _p(L))
+    return L
+
+
+def burgers_rk3(u, dx, nu, dt, nsteps, flux_kind=0, c=0.0) -> np.ndarray:
+    """Advance every row of ``u`` (nprob x n, or n) by nsteps SSP-RK3 steps."""
+    x = _f64(u).copy()
+    shape = x.shape
+    x2 = x.reshape(-1, shape[-1])
+    lib().orc_burgers_rk3(_p(x2), x2.shape[0], x2.shape[1], dx, nu, dt, nsteps, flux_kind, c)
+    return x2.reshape(shape)
+
+
+def ns2d_rhs(q, h, gamma, mu, prandtl) -> np.ndarray:
+    q = _f64(q)
+    L = np.zeros_like(q)
+    lib().orc_ns2d_rhs(_p(q), q.shape[-1], h, gamma, mu, prandtl, _p(L))
+    return L
+
+
+def ns2d_rk3(q, h, gamma, mu, prandtl, dt, nsteps) -> np.ndarray:
+    """Advance (nprob x) 4 x n x n conserved states by nsteps SSP-RK3 steps."""
+    x = _f64(q).copy()
+    shape = x.shape
+    n = shape[-1]
+    x2 = x.reshape(-1, 4, n, n)
+    lib().orc_ns2d_rk3(_p(x2), x2.shape[0], n, h, gamma, mu, prandtl, dt, nsteps)
+    return x2.reshape(shape)
+
+
+def lagrange_weights(nodes, s) -> np.ndarray:
+    nd = _f64(nodes)
+    w = np.zeros_like(nd)
+    lib().orc_lagrange_weights(nd.size, _p(nd), s, _p(w))
+    return w
+
+
+def restrict(fine, dim, V, nc, r) -> np.ndarray:
+    f = _f64(fine)
+    out = np.zeros(V * nc**dim, dtype=np.float64)
+    lib().orc_restrict(_p(f), dim, V, nc, r, _p(out))
+    return out
+
+
+def prolong_add(dc, fine, dim, V, nc, r) -> np.ndarray:
+    d = _f64(dc)
+    f = _f64(fine).copy()
+    lib().orc_prolong_add(_p(d), dim, V, nc, r, _p(f))
+    return f
+
+
+def obs_coarse(xc, dim, V, nc, r, obs_idx, obs_var) -> np.ndarray:
+    x = _f64(xc)
+    oi, ov = _i32(obs_idx), _i32(obs_var)
+    y = np.zeros(oi.size, dtype=np.float64)
+    lib().orc_obs_coarse(_p(x), dim, V, nc, r, oi.size, _p(oi), _p(ov), _p(y))
+    return y
+
+
+def cholesky(A):
+    a = _f64(A).copy()
+    st = lib().orc_cholesky(_p(a), a.shape[0])
+    return st, a
+
+
+def enkf_gain(X, Y, R):
+    X, Y, R = _f64(X), _f64(Y), _f64(R)
+    nx, ne = X.shape
+    ny = Y.shape[0]
+    K = np.zeros((nx, ny))
+    st = lib().orc_enkf_gain(nx, ne, ny, _p(X), _p(Y), _p(R), _p(K))
+    return st, K
+
+
+def enkf_analyse(members, xstar, yo, eps, sigma, obs_idx, obs_var, dim, V, nc, r, gain_form=1):
+    """Returns (status, members_analysed, dC).  See orc_enkf_analyse."""
+    m = _f64(members).copy()
+    ne = m.shape[0]
+    xs, y, e = _f64(xstar), _f64(yo), _f64(eps)
+    oi, ov = _i32(obs_idx), _i32(obs_var)
+    dC = np.zeros(m.shape[1], dtype=np.float64)
+    st = lib().orc_enkf_analyse(dim, V, nc, r, ne, oi.size, _p(oi), _p(ov), _p(y), _p(e), sigma,
+                                gain_form, _p(m), _p(xs), _p(dC))
+    return st, m, dC
+
+
+def rmse(x, truth, V) -> np.ndarray:
+    x, t = _f64(x), _f64(truth)
+    out = np.zeros(V)
+    lib().orc_rmse(_p(x), _p(t), V, x.size // V, _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# the cycle of Algorithm 4 (state part of Algorithm 3 on the coarse mesh)
+# --------------------------------------------------------------------------
+class MGEnKF:
+    """FP64 oracle of one MGEnKF run.  All inputs come from the caller.
+
+    model: "burgers1d" or "ns2d"; fine (V*nf^dim), members (ne x V*nc^dim).
+    """
+
+    def __init__(self, model, nf, ratio, length, dt, fine, members, obs_idx, obs_var, sigma,
+                 seed, nu=0.0, gamma=1.4, prandtl=0.72, gain_form=1):
+        self.model = model
+        self.dim = 1 if model == "burgers1d" else 2
+        self.V = 1 if model == "burgers1d" else 4
+        self.nf, self.r = nf, ratio
+        self.nc = nf // ratio
+        self.length, self.dt, self.nu = length, dt, nu
+        self.gamma, self.prandtl = gamma, prandtl
+        self.fine = _f64(fine).copy()
+        self.members = _f64(members).copy()
+        self.obs_idx, self.obs_var = _i32(obs_idx), _i32(obs_var)
+        self.sigma, self.seed, self.gain_form = sigma, seed, gain_form
+        self.cycle = 0
+        self.xstar = None
+        self.dC = None
+
+    def _advance(self, x, n, nsteps):
+        h = self.length / n
+        if self.model == "burgers1d":
+            return burgers_rk3(x, h, self.nu, self.dt, nsteps)
+        return ns2d_rk3(x.reshape(-1, 4, n, n), h, self.gamma, self.nu, self.prandtl, self.dt,
+                        nsteps).reshape(x.shape)
+
+    def forecast(self, nsteps):
+        """Algorithm 4 step 2 (fine) and Algorithm 3 step 2 (members)."""
+        self.fine = self._advance(self.fine, self.nf, nsteps)
+        self.members = self._advance(self.members, self.nc, nsteps)
+
+    def analyse(self, yo, eps=None):
+        """Algorithm 4 step 4 then Algorithm 3 steps 2-8 and Algorithm 4 step 5."""
+        ne, ny = self.members.shape[0], self.obs_idx.size
+        if eps is None:
+            eps = obs_perturbations(self.seed, self.cycle, ne, ny, self.sigma)
+        self.xstar = restrict(self.fine, self.dim, self.V, self.nc, self.r)
+        st, m, dC = enkf_analyse(self.members, self.xstar, yo, eps, self.sigma, self.obs_idx,
+                                 self.obs_var, self.dim, self.V, self.nc, self.r, self.gain_form)
+        if st == 0:
+            self.members, self.dC = m, dC
+        self.cycle += 1
+        return st
+
+    def prolong_correct(self):
+        """x^F,a = x^F,f + Pi_F(x^C' - x^C*)."""
+        self.fine = prolong_add(self.dC, self.fine, self.dim, self.V, self.nc, self.r)
+
+    def rmse(self, truth):
+        return rmse(self.fine, truth, self.V)

@@ -1,0 +1,96 @@
+/*
+ * oracle.h -- plain FP64 CPU oracle of the MGEnKF analysis cycle.
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  The GPU library never
+ * includes this header and shares no code, table or helper with it.
+ *
+ * Every routine follows the paper's statement of the method in FP64, without
+ * blocking, fusion or reordering beyond what the definition states:
+ *   - EnKF definitions (ensemble matrix, mean, normalised anomalies,
+ *     perturbed observations, gain): Sec. 2.1.2, Eqs. Ensemble_Matrix ..
+ *     ensemble_update, and Algorithm 1 (stochastic EnKF with anomalies);
+ *   - coarse-mesh filter (state part): Algorithm 3, steps 2, 3, 7, 8;
+ *   - multigrid correction: Algorithm 4, steps 2, 4, 5; Sec. 3 step 5;
+ *   - projectors: 4th-order Lagrange interpolators (end of Sec. 2.2);
+ *   - relative RMSE: Eq. L2norm_u (Sec. 4);
+ *   - models: viscous Burgers (Eq. burgers), compressible NS (Eqs. Mass,
+ *     Momentum, Energy) with the periodic discretisations stated in each
+ *     routine's comment.
+ * Parity status of each routine is stated beside it.
+ */
+#ifndef MGENKF_ORACLE_H
+#define MGENKF_ORACLE_H
+#include <stdint.h>
+
+/* ---- counter-based RNG: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) ----
+ * Pinned: against numpy.random.Philox (library) and published known answers. */
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+
+/* Standard normals z[n], n = 0..count-1, drawn by Box-Muller from Philox
+ * blocks ctr = (ctr0, n/4, 0, 0), key = (seed, tag); lanes (0,1) and (2,3)
+ * of a block give one Box-Muller pair each.  u = ((x >> 11) + 1) * 2^-53. */
+void orc_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count, double *z);
+
+/* ---- 1-D viscous Burgers (Eq. burgers), periodic, flux form ----
+ * L(u)_j = -(F_{j+1} - F_{j-1}) / (2 dx) + nu (u_{j+1} - 2 u_j + u_{j-1}) / dx^2
+ * with F = u^2/2 (flux_kind 0) or F = c u (flux_kind 1, linear advection,
+ * used only to pin the scheme against its Fourier amplification factor).
+ * Time: SSP-RK3 in Shu-Osher form.  nprob independent grids of n points,
+ * stored one after the other. */
+void orc_burgers_rhs(const double *u, int n, double dx, double nu, int flux_kind, double c,
+                     double *L);
+void orc_burgers_rk3(double *u, int nprob, int n, double dx, double nu, double dt, int nsteps,
+                     int flux_kind, double c);
+
+/* ---- 2-D compressible Navier-Stokes (Eqs. Mass, Momentum, Energy) ----
+ * Periodic square, q = (rho, rho u, rho v, E) as 4 planes of n x n (x fastest).
+ * Non-dimensional: p = (gamma-1)(E - rho |u|^2 / 2), T = p / rho, constant
+ * mu, kappa = mu gamma / ((gamma-1) Pr).  Inviscid fluxes: central
+ * differences of nodal fluxes.  Viscous and heat fluxes: evaluated at cell
+ * faces (compact normal derivative, averaged central tangential derivative)
+ * and differenced across the cell, so every flux telescopes.  SSP-RK3. */
+void orc_ns2d_rhs(const double *q, int n, double h, double gamma, double mu, double prandtl,
+                  double *L);
+void orc_ns2d_rk3(double *q, int nprob, int n, double h, double gamma, double mu,
+                  double prandtl, double dt, int nsteps);
+
+/* ---- projectors Pi_C, Pi_F (end of Sec. 2.2) ----
+ * Vertex-centred nested periodic grids, coarse node J at fine node r J.
+ * Pi_F: 4-point Lagrange interpolation over coarse nodes J-1..J+2 (tensor
+ * product in 2-D).  Pi_C: the same interpolant at coincident nodes
+ * (injection).  dim = 1 or 2, V variables, nc coarse points per side. */
+void orc_lagrange_weights(int npts, const double *nodes, double s, double *w);
+void orc_restrict(const double *fine, int dim, int V, int nc, int r, double *coarse);
+void orc_prolong_add(const double *dc, int dim, int V, int nc, int r, double *fine);
+/* H^C: Pi_F row at each observed fine node; obs_idx = flat fine index
+ * (y*nf + x in 2-D), obs_var = variable.  y[j] = (Pi_F xc)[obs_var[j]][obs_idx[j]] */
+void orc_obs_coarse(const double *xc, int dim, int V, int nc, int r, int ny,
+                    const int32_t *obs_idx, const int32_t *obs_var, double *y);
+
+/* ---- Cholesky (textbook), returns 0 or the failing pivot index + 1 ---- */
+int orc_cholesky(double *A, int n);
+void orc_chol_solve(const double *Lf, int n, double *b, int nrhs);
+
+/* ---- EnKF analysis on the coarse mesh + multigrid correction ----
+ * Algorithm 3 (state part, steps 2-3 and 7-8) then Algorithm 4 step 5 first
+ * line.  members: ne x nx (member-major), updated in place to the analysis.
+ * xstar: Pi_C of the fine forecast.  yo: ny observations.  eps: ne x ny
+ * observation perturbations (already scaled by sigma).  gain_form:
+ *   0 = literal gain K = X Y^T (Y Y^T + R)^-1 with exact R = sigma^2 I
+ *   1 = ensemble-space form T = (I + Y^T R^-1 Y)^-1 Y^T R^-1 [D | d*]
+ *   2 = literal gain with the sample R^e = E E^T of the centred E (Sec. 2.1.2)
+ * dC (out): x^C' - x^C* = K (yo - H^C x*).  Returns 0, or 1 if the innovation
+ * matrix is not SPD (members and dC untouched). */
+int orc_enkf_analyse(int dim, int V, int nc, int r, int ne, int ny, const int32_t *obs_idx,
+                     const int32_t *obs_var, const double *yo, const double *eps, double sigma,
+                     int gain_form, double *members, const double *xstar, double *dC);
+
+/* Dense Kalman gain K (nx x ny) of the literal form, for brute-force pins. */
+int orc_enkf_gain(int nx, int ne, int ny, const double *X, const double *Y, const double *Rm,
+                  double *K);
+
+/* ---- relative RMSE, Eq. L2norm_u, one value per variable ---- */
+void orc_rmse(const double *x, const double *truth, int V, int64_t npts, double *out);
+
+#endif

@@ -1,0 +1,170 @@
+/*
+ * mgenkf.h -- C ABI of the GB300 (sm_103a) multigrid ensemble Kalman filter.
+ *
+ * The library runs the analysis cycle of the Multigrid EnKF (MGEnKF,
+ * Algorithm 4 of the paper) on one GPU:
+ *   - one fine-grid model run x^F and Ne coarse-grid members x^C,(i), advanced
+ *     by the discretised model between observations (Algorithm 4 step 2,
+ *     Algorithm 3 step 2; model form Eq. x_mdl);
+ *   - restriction x^C* = Pi_C(x^F,f) (Algorithm 4 step 4);
+ *   - the stochastic EnKF analysis of the members on the coarse mesh, with
+ *     perturbed observations (Eq. perturbed_y), normalised anomalies X, Y
+ *     (Eq. Ensemble_Anomaly, Algorithm 3 step 7) and the gain
+ *     K = X Y^T (Y Y^T + R)^-1 (Algorithm 3 step 8), R = sigma^2 I diagonal
+ *     (Sec. 2.1.1);
+ *   - the coarse correction x^C' - x^C* = K (y^o - H^C(x^C*)) prolonged onto
+ *     the fine run, x^F,a = x^F,f + Pi_F(x^C' - x^C*) (Algorithm 4 step 5).
+ * Pi_C / Pi_F are 4th-order (4-point) Lagrange interpolators on vertex-centred
+ * nested periodic grids (end of Sec. 2.2); Pi_C is injection.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an mgenkf_status and never aborts or traps.
+ *   - The handle owns all device memory it allocates; caller pointers are
+ *     only read (or written) during the call.
+ *   - Work is enqueued on the handle's CUDA stream.  Entry points that take
+ *     host pointers for outputs (get_state, rmse with a host `out`) synchronise
+ *     that stream; the others are asynchronous.
+ *   - Device-side failures (non-positive pivot of the innovation matrix,
+ *     non-finite observations passed by device pointer) are recorded on the
+ *     device; the kernels after the failing one leave the members and the fine
+ *     run unchanged, and mgenkf_sync() returns the recorded status.
+ *   - A pointer argument is treated as device memory if CUDA reports it as
+ *     device or managed memory, otherwise as host memory.
+ *   - One handle must not be used from two threads at once.
+ */
+#ifndef MGENKF_H
+#define MGENKF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mgenkf_ctx *mgenkf_handle;
+
+typedef enum {
+    MGENKF_OK = 0,
+    MGENKF_ERR_INVALID_ARG = 1, /* a size, pointer or option is out of range */
+    MGENKF_ERR_OOM = 2,         /* device allocation failed */
+    MGENKF_ERR_CUDA = 3,        /* a CUDA runtime call failed (text in last_error) */
+    MGENKF_ERR_NOT_SPD = 4,     /* innovation matrix had a non-positive pivot */
+    MGENKF_ERR_NONFINITE = 5,   /* observation vector holds NaN or Inf */
+    MGENKF_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} mgenkf_status;
+
+/* models (Eq. burgers; Eqs. Mass, Momentum, Energy) */
+#define MGENKF_BURGERS1D 1
+#define MGENKF_NS2D 2
+/* arithmetic of the cycle */
+#define MGENKF_FP64 0  /* every step in FP64 */
+#define MGENKF_MIXED 1 /* FP32 forecasts and states, BF16 anomaly products with
+                          FP32 accumulation, FP64 means, covariances, Cholesky */
+/* form of the gain solve (identical in exact arithmetic) */
+#define MGENKF_GAIN_ENSEMBLE 0 /* T = (I + Y^T R^-1 Y)^-1 Y^T R^-1 [D | d*], Ne x Ne Cholesky */
+#define MGENKF_GAIN_DIRECT 1   /* W = (Y Y^T + R)^-1 [D | d*], Ny x Ny Cholesky, T = Y^T W */
+/* prolongation of the coarse correction */
+#define MGENKF_PROLONG_LAGRANGE4 0
+
+typedef struct {
+    int32_t model;     /* MGENKF_BURGERS1D or MGENKF_NS2D */
+    int32_t n_fine;    /* fine points per side, N_F */
+    int32_t ratio;     /* coarsening ratio r_C; N_F % r_C == 0; coarse N_C = N_F / r_C */
+    int32_t n_members; /* Ne >= 2 */
+    int32_t n_obs;     /* Ny >= 1 scalar observations */
+    int32_t precision; /* MGENKF_FP64 or MGENKF_MIXED */
+    int32_t gain_form; /* MGENKF_GAIN_ENSEMBLE or MGENKF_GAIN_DIRECT */
+    int32_t prolong;   /* MGENKF_PROLONG_LAGRANGE4 */
+    double length;     /* side of the periodic domain (2 pi for Burgers, 1 for NS) */
+    double dt;         /* model time step, the same on both grids */
+    double nu;         /* Burgers viscosity, or mu = 1/Re for NS */
+    double gamma;      /* NS ratio of specific heats */
+    double prandtl;    /* NS Prandtl number */
+    double obs_sigma;  /* R = obs_sigma^2 I */
+    uint64_t seed;     /* key of the Philox4x64-10 stream of observation perturbations */
+} mgenkf_config;
+
+/* Create a handle.  obs_index[j]: flat fine-grid node of observation j
+ * (x in 1-D, y * N_F + x in 2-D); obs_var[j]: observed variable (0 for
+ * Burgers; 0..3 = rho, rho u, rho v, E for NS).  Both host arrays of n_obs
+ * entries.  cuda_stream: a cudaStream_t, or NULL for the legacy default
+ * stream.  Allocates every device buffer of the cycle; size limits are
+ * reported as MGENKF_ERR_INVALID_ARG with a message in mgenkf_last_error. */
+mgenkf_status mgenkf_create(const mgenkf_config *cfg, const int32_t *obs_index,
+                            const int32_t *obs_var, void *cuda_stream, mgenkf_handle *out);
+
+/* Load the fine state (V * N_F^dim FP64 values, variable-major planes, x
+ * fastest) and the members (Ne x V * N_C^dim FP64, member-major).  Host or
+ * device pointers.  In MGENKF_MIXED the values are rounded to FP32.
+ * Resets the analysis counter that keys the perturbation stream. */
+mgenkf_status mgenkf_set_state(mgenkf_handle h, const double *fine, const double *members);
+
+/* Advance the fine run and every member by nsteps SSP-RK3 steps of the model
+ * (Algorithm 4 step 2, Algorithm 3 step 2).  nsteps >= 0. */
+mgenkf_status mgenkf_forecast(mgenkf_handle h, int32_t nsteps);
+
+/* Analysis at the current time (Algorithm 4 steps 4-5 first line, Algorithm 3
+ * steps 2-3 and 7-8): restriction, predicted observations, anomalies, gain
+ * solve, member update and coarse correction dC = x^C' - x^C*.
+ * y_obs: n_obs observations (host or device).  eps: Ne x n_obs observation
+ * perturbations eps^(i) (member-major, already scaled, host or device), or
+ * NULL to draw them on the GPU as obs_sigma * N(0,1) from Philox4x64-10 with
+ * key (seed, 0x45505300) and counter (analysis index, n / 4, 0, 0) for
+ * n = i * n_obs + j, Box-Muller on lane pairs (0,1) and (2,3).
+ * Host-side checks: non-finite host y_obs -> MGENKF_ERR_NONFINITE (nothing
+ * enqueued).  Increments the analysis counter. */
+mgenkf_status mgenkf_analyse(mgenkf_handle h, const double *y_obs, const double *eps);
+
+/* x^F,a = x^F,f + Pi_F(dC) (Algorithm 4 step 5, second line). */
+mgenkf_status mgenkf_prolong_correct(mgenkf_handle h);
+
+/* One whole cycle: forecast(nsteps), analyse(y_obs, NULL), prolong_correct,
+ * and, if truth_fine != NULL, the relative RMSE of the fine run written to
+ * rmse_out (V FP64 values; device pointer, or host pointer which makes the
+ * call synchronous).  All pointers host or device. */
+mgenkf_status mgenkf_cycle(mgenkf_handle h, int32_t nsteps, const double *y_obs,
+                           const double *truth_fine, double *rmse_out);
+
+/* Copy the states out as FP64 (host or device pointers; NULL skips one). */
+mgenkf_status mgenkf_get_state(mgenkf_handle h, double *fine, double *members);
+
+/* Relative RMSE of the fine run against truth_fine (Eq. L2norm_u), one value
+ * per variable: sqrt(sum (x - x_true)^2 / sum x_true^2).  truth_fine: V *
+ * N_F^dim FP64 (host or device); out: V FP64 (host or device). */
+mgenkf_status mgenkf_rmse(mgenkf_handle h, const double *truth_fine, double *out);
+
+/* Intermediate fields of the last analysis, copied out as FP64 (host or device):
+ *   MGENKF_FIELD_XSTAR  x^C* = Pi_C(x^F,f)                  V * N_C^dim
+ *   MGENKF_FIELD_YF     H^C x^f,(i) (rows 0..Ne-1), H^C x^C* (row Ne)   (Ne+1) x Ny
+ *   MGENKF_FIELD_T      T = Y^T (Y Y^T + R)^-1 [D | d*], column c contiguous  (Ne+1) x Ne
+ *   MGENKF_FIELD_DC     dC = x^C' - x^C*                    V * N_C^dim
+ *   MGENKF_FIELD_EPS    observation perturbations used      Ne x Ny
+ * count: number of doubles the caller can receive (must be >= the size). */
+#define MGENKF_FIELD_XSTAR 0
+#define MGENKF_FIELD_YF 1
+#define MGENKF_FIELD_T 2
+#define MGENKF_FIELD_DC 3
+#define MGENKF_FIELD_EPS 4
+mgenkf_status mgenkf_get_field(mgenkf_handle h, int32_t field, double *out, size_t count);
+
+/* Wait for the handle's stream and return (and clear) the first device-side
+ * status recorded since the last call (MGENKF_OK if none). */
+mgenkf_status mgenkf_sync(mgenkf_handle h);
+
+/* Checkpoint: write / read fine state, members and analysis counter to a file
+ * (binary, native endianness, with a header that records the sizes). */
+mgenkf_status mgenkf_save(mgenkf_handle h, const char *path);
+mgenkf_status mgenkf_load(mgenkf_handle h, const char *path);
+
+/* Text of the last error of this handle (never NULL; empty if none).  Owned by
+ * the handle, valid until the next call on it. */
+const char *mgenkf_last_error(mgenkf_handle h);
+
+/* Free every device buffer and the handle.  NULL is accepted. */
+mgenkf_status mgenkf_destroy(mgenkf_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGENKF_H */

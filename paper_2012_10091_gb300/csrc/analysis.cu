@@ -1,0 +1,622 @@
+// analysis.cu -- kernels of the coarse-mesh EnKF analysis (Algorithm 3, state
+// part: steps 2-3, 7-8) and of the multigrid correction (Algorithm 4 steps 4-5).
+//
+// Layout (per analysis): members [ne][nx] (member-major, state vector of one
+// member contiguous), predicted observations yf [ne+1][ny] (row ne = H^C x^C*),
+// anomalies Y [ne][ny], innovations Z [ne+1][ny] (row i = y^o + eps_i - yf_i,
+// row ne = y^o - H^C x^C*), gain coefficients T [(ne+1)][ne] (column c of
+// T = Y^T C^-1 [D | d*] contiguous).  Every covariance-type reduction, the
+// Cholesky factorisation and the triangular solves run in FP64.
+#include <cstdio>
+
+#include "analysis.h"
+#include "common.cuh"
+
+namespace mgk {
+
+static inline int grid_for(size_t n, int block, int cap = 8 * kNumSMs) {
+    long long g = (long long)((n + block - 1) / block);
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+// restriction Pi_C (injection), Algorithm 4 step 4
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_restrict(const T *__restrict__ fine, T *__restrict__ xs, int dim, int V, int nc,
+                           int r) {
+    const size_t nf = (size_t)nc * r;
+    const size_t cpl = dim == 1 ? (size_t)nc : (size_t)nc * nc;
+    const size_t fpl = dim == 1 ? nf : nf * nf;
+    const size_t total = (size_t)V * cpl;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = i / cpl, k = i % cpl;
+        size_t src;
+        if (dim == 1) {
+            src = (size_t)r * k;
+        } else {
+            const size_t jy = k / nc, jx = k % nc;
+            src = (size_t)r * jy * nf + (size_t)r * jx;
+        }
+        xs[i] = fine[v * fpl + src];
+    }
+}
+
+template <typename T>
+void launch_restrict(const T *fine, T *xstar, int dim, int V, int nc, int r, cudaStream_t s) {
+    const size_t total = (size_t)V * (dim == 1 ? (size_t)nc : (size_t)nc * nc);
+    k_restrict<T><<<grid_for(total, 256), 256, 0, s>>>(fine, xstar, dim, V, nc, r);
+}
+
+// ---------------------------------------------------------------------------
+// predicted observations H^C x (Algorithm 3 step 2): sparse 4- or 16-tap rows
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_obs_apply(const T *__restrict__ members, const T *__restrict__ xstar, size_t nx,
+                            int ne, int ny, int taps, const int32_t *__restrict__ tap_idx,
+                            const double *__restrict__ tap_w, double *__restrict__ yf) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= ny) return;
+    const T *x = i < ne ? members + (size_t)i * nx : xstar;
+    double acc = 0.0;
+    for (int t = 0; t < taps; ++t)
+        acc += tap_w[(size_t)j * taps + t] * (double)x[tap_idx[(size_t)j * taps + t]];
+    yf[(size_t)i * ny + j] = acc;
+}
+
+template <typename T>
+void launch_obs_apply(const T *members, const T *xstar, size_t nx, int ne, int ny, int taps,
+                      const int32_t *tap_idx, const double *tap_w, double *yf, cudaStream_t s) {
+    dim3 grid(ceil_div(ny, 128), ne + 1);
+    k_obs_apply<T><<<grid, 128, 0, s>>>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf);
+}
+
+// ---------------------------------------------------------------------------
+// observation means and innovations (Algorithm 1 step 4; Algorithm 4 step 5)
+// ---------------------------------------------------------------------------
+__global__ void k_obs_mean(const double *__restrict__ yf, const double *__restrict__ yo, int ne,
+                           int ny, double *__restrict__ ybar, double *__restrict__ Z, int *status) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ny) return;
+    double s = 0.0;
+    for (int i = 0; i < ne; ++i) s += yf[(size_t)i * ny + j];
+    ybar[j] = s / ne;
+    const double y = yo[j];
+    if (!isfinite(y)) atomicCAS(status, 0, kStNonFinite);
+    Z[(size_t)ne * ny + j] = y - yf[(size_t)ne * ny + j];
+}
+
+void launch_obs_mean(const double *yf, const double *yo, int ne, int ny, double *ybar, double *Z,
+                     int *status, cudaStream_t s) {
+    k_obs_mean<<<ceil_div(ny, 128), 128, 0, s>>>(yf, yo, ne, ny, ybar, Z, status);
+}
+
+// perturbed observations (Eq. perturbed_y) and normalised anomalies Y (Algorithm 3 step 7)
+__global__ void k_obs_perturb(const double *__restrict__ yf, const double *__restrict__ ybar,
+                              const double *__restrict__ yo, double *__restrict__ eps, int gen_eps,
+                              uint64_t seed, uint64_t cycle, double sigma, int ne, int ny,
+                              double *__restrict__ Y, double *__restrict__ Z) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= ny) return;
+    const size_t o = (size_t)i * ny + j;
+    double e;
+    if (gen_eps) {
+        e = sigma * philox_normal(seed, kEpsTag, cycle, (uint64_t)o);
+        eps[o] = e;
+    } else {
+        e = eps[o];
+    }
+    const double f = yf[o];
+    Y[o] = (f - ybar[j]) / sqrt((double)(ne - 1));
+    Z[o] = yo[j] + e - f;
+}
+
+void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, double *eps,
+                        int gen_eps, uint64_t seed, uint64_t cycle, double sigma, int ne, int ny,
+                        double *Y, double *Z, cudaStream_t s) {
+    dim3 grid(ceil_div(ny, 128), ne);
+    k_obs_perturb<<<grid, 128, 0, s>>>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma, ne, ny, Y, Z);
+}
+
+// ---------------------------------------------------------------------------
+// ensemble mean (FP64 accumulation) and normalised anomalies X
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_ens_anom(const T *__restrict__ m, size_t nx, int ne, double *__restrict__ X64,
+                           __nv_bfloat16 *__restrict__ X16, int ldx, const int *status) {
+    if (*status) return;
+    const double sq = sqrt((double)(ne - 1));
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < nx;
+         p += (size_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < ne; ++i) s += (double)m[(size_t)i * nx + p];
+        const double xb = s / ne;
+        if (X64) {
+            for (int i = 0; i < ne; ++i) X64[(size_t)i * nx + p] = ((double)m[(size_t)i * nx + p] - xb) / sq;
+        } else {
+            __nv_bfloat162 *row = reinterpret_cast<__nv_bfloat162 *>(X16 + p * ldx);
+            for (int i = 0; i < ne; i += 2) {
+                const float a = (float)(((double)m[(size_t)i * nx + p] - xb) / sq);
+                const float b = i + 1 < ne ? (float)(((double)m[(size_t)(i + 1) * nx + p] - xb) / sq) : 0.f;
+                row[i >> 1] = __floats2bfloat162_rn(a, b);
+            }
+        }
+    }
+}
+
+template <typename T>
+void launch_ens_anom(const T *members, size_t nx, int ne, double *X64, __nv_bfloat16 *X16,
+                     const int *status, cudaStream_t s) {
+    const int ldx = (ne + 15) / 16 * 16;
+    k_ens_anom<T><<<grid_for(nx, 128), 128, 0, s>>>(members, nx, ne, X64, X16, ldx, status);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 GEMMs of the gain (Algorithm 3 step 8)
+// ---------------------------------------------------------------------------
+__global__ void k_gemm_nt(const double *__restrict__ A, int m, const double *__restrict__ B1, int n1,
+                          const double *__restrict__ B2, int n2, int K, double divisor, double diag,
+                          double *__restrict__ out1, double *__restrict__ out2, const int *status) {
+    if (status && *status) return;
+    __shared__ double As[16][33];
+    __shared__ double Bs[16][33];
+    const int a0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+            const int r = e >> 5, kk = e & 31, k = k0 + kk;
+            const int a = a0 + r;
+            As[r][kk] = (a < m && k < K) ? A[(size_t)a * K + k] : 0.0;
+            const int c = c0 + r;
+            const double *brow = c < n1 ? B1 + (size_t)c * K
+                                        : (c < n1 + n2 ? B2 + (size_t)(c - n1) * K : nullptr);
+            Bs[r][kk] = (brow && k < K) ? brow[k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) acc = fma(As[ty][kk], Bs[tx][kk], acc);
+        __syncthreads();
+    }
+    const int a = a0 + ty, c = c0 + tx;
+    if (a < m) {
+        if (c < n1)
+            out1[(size_t)a * n1 + c] = (a == c ? diag : 0.0) + acc / divisor;
+        else if (c < n1 + n2)
+            out2[(size_t)(c - n1) * m + a] = acc / divisor;
+    }
+}
+
+void launch_gemm_nt_f64(const double *A, int m, const double *B1, int n1, const double *B2, int n2,
+                        int K, double scale_div, double diag, double *out1, double *out2,
+                        const int *status, cudaStream_t s) {
+    dim3 grid(ceil_div(n1 + n2, 16), ceil_div(m, 16));
+    k_gemm_nt<<<grid, 256, 0, s>>>(A, m, B1, n1, B2, n2, K, scale_div, diag, out1, out2, status);
+}
+
+__global__ void k_gemm_tn(const double *__restrict__ Y, int ne, int ny, double diag,
+                          double *__restrict__ C, const int *status) {
+    if (*status) return;
+    __shared__ double As[32][17];
+    __shared__ double Bs[32][17];
+    const int j0 = blockIdx.y * 16, l0 = blockIdx.x * 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < ne; k0 += 32) {
+        for (int e = threadIdx.x; e < 32 * 16; e += 256) {
+            const int kk = e >> 4, r = e & 15, k = k0 + kk;
+            As[kk][r] = (k < ne && j0 + r < ny) ? Y[(size_t)k * ny + j0 + r] : 0.0;
+            Bs[kk][r] = (k < ne && l0 + r < ny) ? Y[(size_t)k * ny + l0 + r] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) acc = fma(As[kk][ty], Bs[kk][tx], acc);
+        __syncthreads();
+    }
+    const int j = j0 + ty, l = l0 + tx;
+    if (j < ny && l < ny) C[(size_t)j * ny + l] = acc + (j == l ? diag : 0.0);
+}
+
+void launch_gemm_tn_f64(const double *Y, int ne, int ny, double diag, double *C, const int *status,
+                        cudaStream_t s) {
+    dim3 grid(ceil_div(ny, 16), ceil_div(ny, 16));
+    k_gemm_tn<<<grid, 256, 0, s>>>(Y, ne, ny, diag, C, status);
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky (right-looking, one CTA) and the two triangular solves
+// ---------------------------------------------------------------------------
+template <bool SMEM>
+__global__ void __launch_bounds__(1024) k_cholesky(double *A, double *Lt, int n, int *status) {
+    extern __shared__ double sm[];
+    if (*status) return;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int tx = tid & 31, ty = tid >> 5, nty = nth >> 5;
+    double *M = SMEM ? sm : A;
+    if (SMEM) {
+        for (int e = tid; e < n * n; e += nth) sm[e] = A[e];
+        __syncthreads();
+    }
+    for (int k = 0; k < n; ++k) {
+        const double d = M[(size_t)k * n + k];
+        if (!(d > 0.0) || !isfinite(d)) {  // uniform: every thread read the same pivot
+            if (tid == 0) atomicCAS(status, 0, kStNotSpd);
+            return;
+        }
+        const double l = sqrt(d);
+        __syncthreads();
+        if (tid == 0) M[(size_t)k * n + k] = l;
+        for (int i = k + 1 + tid; i < n; i += nth) M[(size_t)i * n + k] = M[(size_t)i * n + k] / l;
+        __syncthreads();
+        for (int i = k + 1 + ty; i < n; i += nty) {
+            const double lik = M[(size_t)i * n + k];
+            for (int j = k + 1 + tx; j <= i; j += 32)
+                M[(size_t)i * n + j] = fma(-lik, M[(size_t)j * n + k], M[(size_t)i * n + j]);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < n * n; e += nth) {
+        const int i = e / n, j = e % n;
+        const double val = j <= i ? M[e] : 0.0;
+        A[e] = val;
+        Lt[(size_t)j * n + i] = val;
+    }
+}
+
+void launch_cholesky(double *A, double *Lt, int n, int *status, cudaStream_t s) {
+    const size_t bytes = sizeof(double) * (size_t)n * n;
+    if (bytes <= 200 * 1024) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_cholesky<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+            attr_set = true;
+        }
+        k_cholesky<true><<<1, 1024, bytes, s>>>(A, Lt, n, status);
+    } else {
+        k_cholesky<false><<<1, 1024, 0, s>>>(A, Lt, n, status);
+    }
+}
+
+template <int MAXR>
+__global__ void __launch_bounds__(32) k_chol_solve(const double *__restrict__ L,
+                                                   const double *__restrict__ Lt, int n,
+                                                   const double *rhs, double *out, int ncol,
+                                                   __nv_bfloat16 *out16, int ld16,
+                                                   const int *status) {
+    if (*status) return;
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (c >= ncol) return;
+    double b[MAXR];
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) {
+        const int i = lane + 32 * m;
+        b[m] = i < n ? rhs[(size_t)c * n + i] : 0.0;
+    }
+    // forward substitution L z = b (column-oriented: after z_j, b_i -= L_ij z_j)
+#pragma unroll
+    for (int s = 0; s < MAXR; ++s) {
+        if (s * 32 >= n) break;
+        for (int l = 0; l < 32; ++l) {
+            const int j = s * 32 + l;
+            if (j >= n) break;
+            if (lane == l) b[s] = b[s] / L[(size_t)j * n + j];
+            const double zj = __shfl_sync(0xffffffffu, b[s], l);
+#pragma unroll
+            for (int m = s; m < MAXR; ++m) {
+                const int i = lane + 32 * m;
+                if (i > j && i < n) b[m] = fma(-Lt[(size_t)j * n + i], zj, b[m]);
+            }
+        }
+    }
+    // back substitution L^T x = z (after x_j, z_i -= L_ji x_j for i < j)
+#pragma unroll
+    for (int s = MAXR - 1; s >= 0; --s) {
+        if (s * 32 >= n) continue;
+        for (int l = 31; l >= 0; --l) {
+            const int j = s * 32 + l;
+            if (j >= n) continue;
+            if (lane == l) b[s] = b[s] / L[(size_t)j * n + j];
+            const double xj = __shfl_sync(0xffffffffu, b[s], l);
+#pragma unroll
+            for (int m = 0; m <= s; ++m) {
+                const int i = lane + 32 * m;
+                if (i < j) b[m] = fma(-L[(size_t)j * n + i], xj, b[m]);
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) {
+        const int i = lane + 32 * m;
+        if (i < n) {
+            out[(size_t)c * n + i] = b[m];
+            if (out16) out16[(size_t)c * ld16 + i] = __double2bfloat16(b[m]);
+        }
+    }
+}
+
+void launch_chol_solve(const double *L, const double *Lt, int n, const double *rhs, double *out,
+                       int ncol, __nv_bfloat16 *out16, int ld16, const int *status, cudaStream_t s) {
+    if (n <= 128)
+        k_chol_solve<4><<<ncol, 32, 0, s>>>(L, Lt, n, rhs, out, ncol, out16, ld16, status);
+    else if (n <= 512)
+        k_chol_solve<16><<<ncol, 32, 0, s>>>(L, Lt, n, rhs, out, ncol, out16, ld16, status);
+    else
+        k_chol_solve<64><<<ncol, 32, 0, s>>>(L, Lt, n, rhs, out, ncol, out16, ld16, status);
+}
+
+// ---------------------------------------------------------------------------
+// member update x^a,(i) = x^f,(i) + X T_i and coarse correction dC = X T_ne
+// (Eq. ensemble_update with K = X T; Algorithm 4 step 5)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_f64(T *__restrict__ members, T *__restrict__ dC,
+                                                    const double *__restrict__ X,
+                                                    const double *__restrict__ Tm, size_t nx, int ne,
+                                                    const int *status) {
+    extern __shared__ double Ts[];  // [32 columns][ne]
+    if (*status) return;
+    const int c0 = blockIdx.y * 32;
+    for (int e = threadIdx.x; e < 32 * ne; e += blockDim.x) {
+        const int cc = e / ne, a = e % ne;
+        Ts[e] = c0 + cc <= ne ? Tm[(size_t)(c0 + cc) * ne + a] : 0.0;
+    }
+    __syncthreads();
+    const size_t p = blockIdx.x * (size_t)64 + (threadIdx.x & 63);
+    const int cg = threadIdx.x >> 6;
+    if (p >= nx) return;
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int a = 0; a < ne; ++a) {
+        const double x = X[(size_t)a * nx + p];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = fma(x, Ts[(cg * 8 + q) * ne + a], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int c = c0 + cg * 8 + q;
+        if (c < ne)
+            members[(size_t)c * nx + p] = (T)((double)members[(size_t)c * nx + p] + acc[q]);
+        else if (c == ne)
+            dC[p] = (T)acc[q];
+    }
+}
+
+template <typename T>
+void launch_update_f64(T *members, T *dC, const double *X, const double *Tm, size_t nx, int ne,
+                       const int *status, cudaStream_t s) {
+    dim3 grid(ceil_div(nx, 64), ceil_div(ne + 1, 32));
+    const size_t smem = sizeof(double) * 32 * (size_t)ne;  // <= 128 KB for ne <= 512
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_update_f64<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_update_f64<T><<<grid, 256, smem, s>>>(members, dC, X, Tm, nx, ne, status);
+}
+
+// BF16 anomaly product with FP32 accumulation (CUDA-core version): X^T tile of
+// 64 points and T tile of 32 columns staged in shared memory.
+__global__ void __launch_bounds__(256) k_update_bf16(float *__restrict__ members,
+                                                     float *__restrict__ dC,
+                                                     const __nv_bfloat16 *__restrict__ Xt,
+                                                     const __nv_bfloat16 *__restrict__ Tt, int ldx,
+                                                     size_t nx, int ne, const int *status) {
+    extern __shared__ __nv_bfloat16 sm16[];
+    if (*status) return;
+    const int lds = ldx + 2;
+    __nv_bfloat16 *Xs = sm16;             // [64][lds]
+    __nv_bfloat16 *Tsm = sm16 + 64 * lds; // [32][lds]
+    const size_t p0 = blockIdx.x * (size_t)64;
+    const int c0 = blockIdx.y * 32;
+    for (int e = threadIdx.x; e < 64 * ldx; e += blockDim.x) {
+        const int r = e / ldx, a = e % ldx;
+        Xs[r * lds + a] = p0 + r < nx ? Xt[(p0 + r) * ldx + a] : __float2bfloat16(0.f);
+    }
+    for (int e = threadIdx.x; e < 32 * ldx; e += blockDim.x) {
+        const int r = e / ldx, a = e % ldx;
+        Tsm[r * lds + a] = c0 + r <= ne ? Tt[(size_t)(c0 + r) * ldx + a] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    const int pl = threadIdx.x & 63, cg = threadIdx.x >> 6;
+    const size_t p = p0 + pl;
+    if (p >= nx) return;
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+    for (int a = 0; a < ne; ++a) {
+        const float x = __bfloat162float(Xs[pl * lds + a]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = fmaf(x, __bfloat162float(Tsm[(cg * 8 + q) * lds + a]), acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int c = c0 + cg * 8 + q;
+        if (c < ne)
+            members[(size_t)c * nx + p] += acc[q];
+        else if (c == ne)
+            dC[p] = acc[q];
+    }
+}
+
+void launch_update_bf16(float *members, float *dC, const __nv_bfloat16 *Xt, const __nv_bfloat16 *Tt,
+                        int ldx, size_t nx, int ne, const int *status, cudaStream_t s) {
+    dim3 grid(ceil_div(nx, 64), ceil_div(ne + 1, 32));
+    const size_t smem = sizeof(__nv_bfloat16) * (size_t)(64 + 32) * (ldx + 2);  // <= 99 KB
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_update_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_update_bf16<<<grid, 256, smem, s>>>(members, dC, Xt, Tt, ldx, nx, ne, status);
+}
+
+// ---------------------------------------------------------------------------
+// prolongation of the coarse correction, Algorithm 4 step 5 second line
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_prolong_add(T *__restrict__ fine, const T *__restrict__ dC, int dim, int V, int nc,
+                              int r, ProlongWeights w, const int *status) {
+    if (*status) return;
+    const size_t nf = (size_t)nc * r;
+    const size_t fpl = dim == 1 ? nf : nf * nf;
+    const size_t cpl = dim == 1 ? (size_t)nc : (size_t)nc * nc;
+    const size_t total = (size_t)V * fpl;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = idx / fpl, k = idx % fpl;
+        const T *d = dC + v * cpl;
+        T acc = T(0);
+        if (dim == 1) {
+            const int J = (int)(k / r), m = (int)(k % r);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) acc += (T)w.w[m][t] * d[(J - 1 + t + nc) % nc];
+        } else {
+            const int fy = (int)(k / nf), fx = (int)(k % nf);
+            const int Jy = fy / r, my = fy % r, Jx = fx / r, mx = fx % r;
+#pragma unroll
+            for (int ty = 0; ty < 4; ++ty) {
+                const size_t row = (size_t)((Jy - 1 + ty + nc) % nc) * nc;
+#pragma unroll
+                for (int tx = 0; tx < 4; ++tx)
+                    acc += (T)(w.w[my][ty] * w.w[mx][tx]) * d[row + (Jx - 1 + tx + nc) % nc];
+            }
+        }
+        fine[idx] += acc;
+    }
+}
+
+template <typename T>
+void launch_prolong_add(T *fine, const T *dC, int dim, int V, int nc, int r,
+                        const ProlongWeights &w, const int *status, cudaStream_t s) {
+    const size_t nf = (size_t)nc * r;
+    const size_t total = (size_t)V * (dim == 1 ? nf : nf * nf);
+    k_prolong_add<T><<<grid_for(total, 256), 256, 0, s>>>(fine, dC, dim, V, nc, r, w, status);
+}
+
+// ---------------------------------------------------------------------------
+// relative RMSE, Eq. L2norm_u (deterministic two-pass reduction)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_rmse_partial(const T *__restrict__ x, const double *__restrict__ truth, int V,
+                               size_t npts, double *__restrict__ partials) {
+    __shared__ double red[2][32];
+    for (int v = 0; v < V; ++v) {
+        double num = 0.0, den = 0.0;
+        for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < npts;
+             k += (size_t)gridDim.x * blockDim.x) {
+            const double t = truth[v * npts + k];
+            const double d = (double)x[v * npts + k] - t;
+            num = fma(d, d, num);
+            den = fma(t, t, den);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_down_sync(0xffffffffu, num, o);
+            den += __shfl_down_sync(0xffffffffu, den, o);
+        }
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) {
+            red[0][w] = num;
+            red[1][w] = den;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+                a += red[0][q];
+                b += red[1][q];
+            }
+            partials[((size_t)blockIdx.x * V + v) * 2 + 0] = a;
+            partials[((size_t)blockIdx.x * V + v) * 2 + 1] = b;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_rmse_final(const double *__restrict__ partials, int nblocks, int V,
+                             double *__restrict__ out) {
+    const int v = threadIdx.x;
+    if (v >= V) return;
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < nblocks; ++q) {
+        a += partials[((size_t)q * V + v) * 2 + 0];
+        b += partials[((size_t)q * V + v) * 2 + 1];
+    }
+    out[v] = sqrt(a / b);
+}
+
+template <typename T>
+void launch_rmse(const T *x, const double *truth, int V, size_t npts, double *partials, int nblocks,
+                 double *out, cudaStream_t s) {
+    k_rmse_partial<T><<<nblocks, 256, 0, s>>>(x, truth, V, npts, partials);
+    k_rmse_final<<<1, 32, 0, s>>>(partials, nblocks, V, out);
+}
+
+// ---------------------------------------------------------------------------
+// conversions and normals
+// ---------------------------------------------------------------------------
+template <typename Tin, typename Tout>
+__global__ void k_convert(const Tin *__restrict__ in, Tout *__restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (Tout)in[i];
+}
+
+template <typename Tin, typename Tout>
+void launch_convert(const Tin *in, Tout *out, size_t n, cudaStream_t s) {
+    if (n == 0) return;
+    k_convert<Tin, Tout><<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+}
+
+__global__ void k_tt_bf16(const double *__restrict__ Tm, __nv_bfloat16 *__restrict__ Tt, int ne,
+                          int ld, const int *status) {
+    if (*status) return;
+    const int total = (ne + 1) * ne;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int c = e / ne, a = e % ne;
+        Tt[(size_t)c * ld + a] = __double2bfloat16(Tm[e]);
+    }
+}
+
+void launch_tt_bf16(const double *Tm, __nv_bfloat16 *Tt, int ne, int ld, const int *status,
+                    cudaStream_t s) {
+    k_tt_bf16<<<grid_for((size_t)(ne + 1) * ne, 256), 256, 0, s>>>(Tm, Tt, ne, ld, status);
+}
+
+__global__ void k_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count,
+                          double *__restrict__ out) {
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < count;
+         n += (int64_t)gridDim.x * blockDim.x)
+        out[n] = philox_normal(seed, tag, ctr0, (uint64_t)n);
+}
+
+void launch_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count, double *out,
+                    cudaStream_t s) {
+    if (count <= 0) return;
+    k_normals<<<grid_for((size_t)count, 256), 256, 0, s>>>(seed, tag, ctr0, count, out);
+}
+
+// ---------------------------------------------------------------------------
+// explicit instantiations
+// ---------------------------------------------------------------------------
+#define MGK_INST(T)                                                                              \
+    template void launch_restrict<T>(const T *, T *, int, int, int, int, cudaStream_t);          \
+    template void launch_obs_apply<T>(const T *, const T *, size_t, int, int, int, const int32_t *, \
+                                      const double *, double *, cudaStream_t);                   \
+    template void launch_ens_anom<T>(const T *, size_t, int, double *, __nv_bfloat16 *,          \
+                                     const int *, cudaStream_t);                                 \
+    template void launch_update_f64<T>(T *, T *, const double *, const double *, size_t, int,    \
+                                       const int *, cudaStream_t);                               \
+    template void launch_prolong_add<T>(T *, const T *, int, int, int, int,                      \
+                                        const ProlongWeights &, const int *, cudaStream_t);      \
+    template void launch_rmse<T>(const T *, const double *, int, size_t, double *, int, double *, \
+                                 cudaStream_t);
+MGK_INST(float)
+MGK_INST(double)
+#undef MGK_INST
+template void launch_convert<double, float>(const double *, float *, size_t, cudaStream_t);
+template void launch_convert<float, double>(const float *, double *, size_t, cudaStream_t);
+template void launch_convert<double, double>(const double *, double *, size_t, cudaStream_t);
+
+}  // namespace mgk

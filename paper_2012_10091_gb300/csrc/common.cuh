@@ -1,0 +1,84 @@
+// common.cuh -- shared device/host helpers of the MGEnKF GPU library.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mgenkf.h"
+
+namespace mgk {
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (grids are sized from the device query)
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// device status word values (a subset of mgenkf_status)
+constexpr int kStatusOk = 0;
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller normals.
+// ---------------------------------------------------------------------------
+struct U64x4 {
+    uint64_t v[4];
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                               uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
+        const uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    U64x4 o;
+    o.v[0] = c0;
+    o.v[1] = c1;
+    o.v[2] = c2;
+    o.v[3] = c3;
+    return o;
+}
+
+// normal number n of the stream (seed, tag, ctr0)
+__device__ __forceinline__ double philox_normal(uint64_t seed, uint64_t tag, uint64_t ctr0,
+                                                uint64_t n) {
+    const U64x4 x = philox4x64_10(ctr0, n >> 2, 0, 0, seed, tag);
+    const int lane = (int)(n & 3);
+    const int pair = lane >> 1;
+    const uint64_t a = pair ? x.v[2] : x.v[0];
+    const uint64_t b = pair ? x.v[3] : x.v[1];
+    const double inv53 = 1.0 / 9007199254740992.0;
+    const double u1 = (double)((a >> 11) + 1) * inv53;
+    const double u2 = (double)((b >> 11) + 1) * inv53;
+    const double rad = sqrt(-2.0 * log(u1));
+    const double th = 6.283185307179586 * u2;
+    return (lane & 1) ? rad * sin(th) : rad * cos(th);
+}
+
+constexpr uint64_t kEpsTag = 0x45505300ULL;  // "EPS\0": perturbation stream of the analysis
+
+// ---------------------------------------------------------------------------
+// small type helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ double to_f64(T x) {
+    return (double)x;
+}
+
+}  // namespace mgk
+
+// error text of the stateless entry points (per host thread)
+void mgk_set_error(const std::string &msg);

@@ -1,0 +1,698 @@
+// mgenkf.cu -- host implementation of the C ABI declared in include/mgenkf.h
+// and include/mgenkf_ops.h.  Owns the device buffers of one MGEnKF run and
+// sequences the kernels of a cycle (Algorithm 4) on the handle's stream.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mgenkf.h"
+#include "../../include/mgenkf_ops.h"
+#include "analysis.h"
+#include "common.cuh"
+#include "forecast.h"
+#include "forecast_ns2d.h"
+
+using namespace mgk;
+
+static thread_local std::string g_ops_error;
+void mgk_set_error(const std::string &msg) { g_ops_error = msg; }
+
+struct mgenkf_ctx {
+    mgenkf_config cfg;
+    int dim, V, nf, nc, r, ne, ny, taps;
+    size_t nx, nxf, cpl;
+    bool mixed, direct;
+    cudaStream_t stream;
+    int device;
+    uint64_t cycle;
+    std::string err;
+
+    void *fine = nullptr, *members = nullptr, *xstar = nullptr, *dC = nullptr;
+    int32_t *tap_idx = nullptr;
+    double *tap_w = nullptr;
+    ProlongWeights pw;
+    double *yf = nullptr, *yo = nullptr, *ybar = nullptr, *eps = nullptr, *Y = nullptr, *Z = nullptr;
+    double *X64 = nullptr;
+    __nv_bfloat16 *X16 = nullptr, *Tt = nullptr;
+    int ldx = 0, ntpad = 0;
+    double *S = nullptr, *Lt = nullptr, *Bt = nullptr;  // ensemble form: S (ne x ne), T in Bt
+    double *C = nullptr, *Ct = nullptr, *W = nullptr;   // direct form
+    double *Tm = nullptr;                               // T, (ne+1) x ne (points at Bt or own buffer)
+    double *truth_d = nullptr, *rmse_part = nullptr, *rmse_d = nullptr, *scratch = nullptr;
+    size_t scratch_n = 0;
+    int *status = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+#define H_FAIL(code, msg)      \
+    do {                       \
+        h->err = (msg);        \
+        return (code);         \
+    } while (0)
+
+#define H_CUDA(call)                                                                 \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            h->err = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+            return e_ == cudaErrorMemoryAllocation ? MGENKF_ERR_OOM : MGENKF_ERR_CUDA; \
+        }                                                                            \
+    } while (0)
+
+#define H_LAUNCHED()                                                             \
+    do {                                                                         \
+        cudaError_t e_ = cudaGetLastError();                                     \
+        if (e_ != cudaSuccess) {                                                 \
+            h->err = std::string("kernel launch: ") + cudaGetErrorString(e_);    \
+            return MGENKF_ERR_CUDA;                                              \
+        }                                                                        \
+    } while (0)
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// closed-form weights of the 4-point Lagrange interpolant on nodes -1, 0, 1, 2
+static void cubic_weights(double s, double w[4]) {
+    w[0] = -s * (s - 1.0) * (s - 2.0) / 6.0;
+    w[1] = (s + 1.0) * (s - 1.0) * (s - 2.0) / 2.0;
+    w[2] = -(s + 1.0) * s * (s - 2.0) / 2.0;
+    w[3] = (s + 1.0) * s * (s - 1.0) / 6.0;
+}
+
+static size_t tsize(const mgenkf_ctx *h) { return h->mixed ? sizeof(float) : sizeof(double); }
+
+template <typename P>
+static mgenkf_status dalloc(mgenkf_ctx *h, P **p, size_t bytes) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e);
+        return MGENKF_ERR_OOM;
+    }
+    *p = (P *)q;
+    return MGENKF_OK;
+}
+
+#define H_ALLOC(ptr, bytes)                                    \
+    do {                                                       \
+        mgenkf_status s_ = dalloc(h, &(ptr), (bytes));         \
+        if (s_ != MGENKF_OK) return s_;                        \
+    } while (0)
+
+static void free_all(mgenkf_ctx *h) {
+    void *ptrs[] = {h->fine, h->members, h->xstar, h->dC, h->tap_idx, h->tap_w, h->yf, h->yo,
+                    h->ybar, h->eps, h->Y, h->Z, h->X64, h->X16, h->Tt, h->S, h->Lt, h->Bt, h->C,
+                    h->Ct, h->W, h->truth_d, h->rmse_part, h->rmse_d, h->scratch, h->status};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->Tm && h->Tm != h->Bt) cudaFree(h->Tm);
+}
+
+// copy n doubles from a host or device pointer into device buffer dst (FP64)
+static mgenkf_status upload_f64(mgenkf_ctx *h, double *dst, const double *src, size_t n) {
+    H_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, h->stream));
+    return MGENKF_OK;
+}
+
+static mgenkf_status ensure_scratch(mgenkf_ctx *h, size_t n) {
+    if (h->scratch_n >= n) return MGENKF_OK;
+    if (h->scratch) cudaFree(h->scratch);
+    h->scratch = nullptr;
+    h->scratch_n = 0;
+    H_ALLOC(h->scratch, n * sizeof(double));
+    h->scratch_n = n;
+    return MGENKF_OK;
+}
+
+// load n FP64 values (host or device) into a state buffer of the handle's type
+static mgenkf_status load_state(mgenkf_ctx *h, void *dst, const double *src, size_t n) {
+    if (!h->mixed) return upload_f64(h, (double *)dst, src, n);
+    const double *dsrc = src;
+    if (!is_device_ptr(src)) {
+        mgenkf_status st = ensure_scratch(h, n);
+        if (st) return st;
+        H_CUDA(cudaMemcpyAsync(h->scratch, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        dsrc = h->scratch;
+    }
+    launch_convert<double, float>(dsrc, (float *)dst, n, h->stream);
+    H_LAUNCHED();
+    return MGENKF_OK;
+}
+
+// copy a state buffer out as FP64 into a host or device pointer (syncs for host)
+static mgenkf_status store_state(mgenkf_ctx *h, double *dst, const void *src, size_t n) {
+    const bool dev = is_device_ptr(dst);
+    double *target = dst;
+    if (!dev) {
+        mgenkf_status st = ensure_scratch(h, n);
+        if (st) return st;
+        target = h->scratch;
+    }
+    if (h->mixed)
+        launch_convert<float, double>((const float *)src, target, n, h->stream);
+    else
+        launch_convert<double, double>((const double *)src, target, n, h->stream);
+    H_LAUNCHED();
+    if (!dev) {
+        H_CUDA(cudaMemcpyAsync(dst, target, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        H_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    return MGENKF_OK;
+}
+
+static mgenkf_status copy_out_f64(mgenkf_ctx *h, double *dst, const double *src, size_t n) {
+    H_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, h->stream));
+    if (!is_device_ptr(dst)) H_CUDA(cudaStreamSynchronize(h->stream));
+    return MGENKF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// create / destroy
+// ---------------------------------------------------------------------------
+static mgenkf_status validate(mgenkf_ctx *h, const mgenkf_config *c, const int32_t *obs_index,
+                              const int32_t *obs_var) {
+    if (c->model != MGENKF_BURGERS1D && c->model != MGENKF_NS2D) H_FAIL(MGENKF_ERR_INVALID_ARG, "model must be MGENKF_BURGERS1D or MGENKF_NS2D");
+    if (c->ratio < 1 || c->ratio > kMaxRatio) H_FAIL(MGENKF_ERR_INVALID_ARG, "ratio must be in [1, 16]");
+    if (c->n_fine < 4 || c->n_fine % c->ratio != 0) H_FAIL(MGENKF_ERR_INVALID_ARG, "n_fine must be >= 4 and a multiple of ratio");
+    if (c->n_fine / c->ratio < 4) H_FAIL(MGENKF_ERR_INVALID_ARG, "coarse grid needs >= 4 points per side (4-point stencils)");
+    if (c->n_members < 2) H_FAIL(MGENKF_ERR_INVALID_ARG, "n_members must be >= 2");
+    if (c->n_obs < 1) H_FAIL(MGENKF_ERR_INVALID_ARG, "n_obs must be >= 1");
+    if (c->precision != MGENKF_FP64 && c->precision != MGENKF_MIXED) H_FAIL(MGENKF_ERR_INVALID_ARG, "precision must be MGENKF_FP64 or MGENKF_MIXED");
+    if (c->gain_form != MGENKF_GAIN_ENSEMBLE && c->gain_form != MGENKF_GAIN_DIRECT) H_FAIL(MGENKF_ERR_INVALID_ARG, "gain_form must be ENSEMBLE or DIRECT");
+    if (c->prolong != MGENKF_PROLONG_LAGRANGE4) H_FAIL(MGENKF_ERR_UNSUPPORTED, "only MGENKF_PROLONG_LAGRANGE4 is built");
+    if (!(c->dt > 0.0) || !(c->length > 0.0) || !(c->nu >= 0.0)) H_FAIL(MGENKF_ERR_INVALID_ARG, "dt and length must be > 0, nu >= 0");
+    if (!(c->obs_sigma >= 0.0) || !std::isfinite(c->obs_sigma)) H_FAIL(MGENKF_ERR_INVALID_ARG, "obs_sigma must be finite and >= 0");
+    if (c->gain_form == MGENKF_GAIN_ENSEMBLE && !(c->obs_sigma > 0.0)) H_FAIL(MGENKF_ERR_INVALID_ARG, "the ensemble-space gain needs obs_sigma > 0 (R^-1)");
+    if (!obs_index || !obs_var) H_FAIL(MGENKF_ERR_INVALID_ARG, "obs_index and obs_var are required");
+    if (c->n_members > 512) H_FAIL(MGENKF_ERR_INVALID_ARG, "n_members must be <= 512");
+    if (c->gain_form == MGENKF_GAIN_DIRECT && c->n_obs > 2048) H_FAIL(MGENKF_ERR_INVALID_ARG, "direct gain form supports n_obs <= 2048");
+    const int dim = c->model == MGENKF_BURGERS1D ? 1 : 2;
+    const int V = c->model == MGENKF_BURGERS1D ? 1 : 4;
+    const long long nfp = dim == 1 ? (long long)c->n_fine : (long long)c->n_fine * c->n_fine;
+    for (int j = 0; j < c->n_obs; ++j) {
+        if (obs_index[j] < 0 || obs_index[j] >= nfp) H_FAIL(MGENKF_ERR_INVALID_ARG, "obs_index[" + std::to_string(j) + "] out of the fine grid");
+        if (obs_var[j] < 0 || obs_var[j] >= V) H_FAIL(MGENKF_ERR_INVALID_ARG, "obs_var[" + std::to_string(j) + "] out of range");
+    }
+    if (c->model == MGENKF_BURGERS1D) {
+        if (c->n_fine / c->ratio > kBurgersMaxPtsPerCta) H_FAIL(MGENKF_ERR_INVALID_ARG, "Burgers coarse grid must have <= 4096 points (one CTA per member)");
+        if (burgers_split_factor(c->n_fine) == 0) H_FAIL(MGENKF_ERR_INVALID_ARG, "Burgers fine grid must split into <= 8 CTAs of <= 4096 points");
+    } else {
+        const char *why = ns2d_check_size(c->n_fine / c->ratio, c->n_fine);
+        if (why) H_FAIL(MGENKF_ERR_INVALID_ARG, why);
+    }
+    return MGENKF_OK;
+}
+
+static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const int32_t *obs_index,
+                                 const int32_t *obs_var) {
+    mgenkf_status st = validate(h, cfg, obs_index, obs_var);
+    if (st) return st;
+    h->cfg = *cfg;
+    h->dim = cfg->model == MGENKF_BURGERS1D ? 1 : 2;
+    h->V = cfg->model == MGENKF_BURGERS1D ? 1 : 4;
+    h->nf = cfg->n_fine;
+    h->r = cfg->ratio;
+    h->nc = h->nf / h->r;
+    h->ne = cfg->n_members;
+    h->ny = cfg->n_obs;
+    h->taps = h->dim == 1 ? 4 : 16;
+    h->cpl = h->dim == 1 ? (size_t)h->nc : (size_t)h->nc * h->nc;
+    h->nx = (size_t)h->V * h->cpl;
+    h->nxf = (size_t)h->V * (h->dim == 1 ? (size_t)h->nf : (size_t)h->nf * h->nf);
+    h->mixed = cfg->precision == MGENKF_MIXED;
+    h->direct = cfg->gain_form == MGENKF_GAIN_DIRECT;
+    h->cycle = 0;
+    H_CUDA(cudaGetDevice(&h->device));
+
+    const size_t ts = tsize(h), ne = h->ne, ny = h->ny, nx = h->nx;
+    H_ALLOC(h->fine, h->nxf * ts);
+    H_ALLOC(h->members, ne * nx * ts);
+    H_ALLOC(h->xstar, nx * ts);
+    H_ALLOC(h->dC, nx * ts);
+    H_ALLOC(h->tap_idx, ny * h->taps * sizeof(int32_t));
+    H_ALLOC(h->tap_w, ny * h->taps * sizeof(double));
+    H_ALLOC(h->yf, (ne + 1) * ny * sizeof(double));
+    H_ALLOC(h->yo, ny * sizeof(double));
+    H_ALLOC(h->ybar, ny * sizeof(double));
+    H_ALLOC(h->eps, ne * ny * sizeof(double));
+    H_ALLOC(h->Y, ne * ny * sizeof(double));
+    H_ALLOC(h->Z, (ne + 1) * ny * sizeof(double));
+    h->ldx = (int)((ne + 15) / 16 * 16);
+    h->ntpad = (int)((ne + 1 + 15) / 16 * 16);
+    if (h->mixed) {
+        H_ALLOC(h->X16, nx * h->ldx * sizeof(__nv_bfloat16));
+        H_ALLOC(h->Tt, (size_t)h->ntpad * h->ldx * sizeof(__nv_bfloat16));
+        H_CUDA(cudaMemsetAsync(h->X16, 0, nx * h->ldx * sizeof(__nv_bfloat16), h->stream));
+        H_CUDA(cudaMemsetAsync(h->Tt, 0, (size_t)h->ntpad * h->ldx * sizeof(__nv_bfloat16), h->stream));
+    } else {
+        H_ALLOC(h->X64, ne * nx * sizeof(double));
+    }
+    if (h->direct) {
+        H_ALLOC(h->C, ny * ny * sizeof(double));
+        H_ALLOC(h->Ct, ny * ny * sizeof(double));
+        H_ALLOC(h->W, (ne + 1) * ny * sizeof(double));
+        H_ALLOC(h->Tm, (ne + 1) * ne * sizeof(double));
+    } else {
+        H_ALLOC(h->S, ne * ne * sizeof(double));
+        H_ALLOC(h->Lt, ne * ne * sizeof(double));
+        H_ALLOC(h->Bt, (ne + 1) * ne * sizeof(double));
+        h->Tm = h->Bt;
+    }
+    H_ALLOC(h->rmse_part, (size_t)kRmseBlocks * h->V * 2 * sizeof(double));
+    H_ALLOC(h->rmse_d, 4 * sizeof(double));
+    H_ALLOC(h->status, sizeof(int));
+    H_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    H_CUDA(cudaMemsetAsync(h->fine, 0, h->nxf * ts, h->stream));
+    H_CUDA(cudaMemsetAsync(h->members, 0, ne * nx * ts, h->stream));
+    H_CUDA(cudaMemsetAsync(h->dC, 0, nx * ts, h->stream));
+
+    // observation operator H^C = H^F Pi_F: Lagrange taps at each observed fine node
+    std::vector<int32_t> tidx(ny * h->taps);
+    std::vector<double> tw(ny * h->taps);
+    for (size_t j = 0; j < ny; ++j) {
+        const int f = obs_index[j];
+        const size_t plane = (size_t)obs_var[j] * h->cpl;
+        if (h->dim == 1) {
+            const int J = f / h->r;
+            double w[4];
+            cubic_weights((double)(f % h->r) / h->r, w);
+            for (int t = 0; t < 4; ++t) {
+                tidx[j * 4 + t] = (int32_t)(plane + (J - 1 + t + h->nc) % h->nc);
+                tw[j * 4 + t] = w[t];
+            }
+        } else {
+            const int fy = f / h->nf, fx = f % h->nf;
+            const int Jy = fy / h->r, Jx = fx / h->r;
+            double wy[4], wx[4];
+            cubic_weights((double)(fy % h->r) / h->r, wy);
+            cubic_weights((double)(fx % h->r) / h->r, wx);
+            for (int ty = 0; ty < 4; ++ty)
+                for (int tx = 0; tx < 4; ++tx) {
+                    const size_t yy = (size_t)((Jy - 1 + ty + h->nc) % h->nc);
+                    const size_t xx = (size_t)((Jx - 1 + tx + h->nc) % h->nc);
+                    tidx[j * 16 + ty * 4 + tx] = (int32_t)(plane + yy * h->nc + xx);
+                    tw[j * 16 + ty * 4 + tx] = wy[ty] * wx[tx];
+                }
+        }
+    }
+    H_CUDA(cudaMemcpyAsync(h->tap_idx, tidx.data(), tidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    H_CUDA(cudaMemcpyAsync(h->tap_w, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    for (int m = 0; m < h->r; ++m) cubic_weights((double)m / h->r, h->pw.w[m]);
+    H_CUDA(cudaStreamSynchronize(h->stream));
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_create(const mgenkf_config *cfg, const int32_t *obs_index,
+                                       const int32_t *obs_var, void *cuda_stream, mgenkf_handle *out) {
+    if (!out) return MGENKF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cfg) return MGENKF_ERR_INVALID_ARG;
+    mgenkf_ctx *h = new mgenkf_ctx();
+    h->stream = (cudaStream_t)cuda_stream;
+    mgenkf_status st = create_impl(h, cfg, obs_index, obs_var);
+    if (st != MGENKF_OK) {
+        mgk_set_error(h->err);
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_destroy(mgenkf_handle h) {
+    if (!h) return MGENKF_OK;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return MGENKF_OK;
+}
+
+extern "C" const char *mgenkf_last_error(mgenkf_handle h) {
+    if (!h) return g_ops_error.c_str();
+    return h->err.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// state
+// ---------------------------------------------------------------------------
+extern "C" mgenkf_status mgenkf_set_state(mgenkf_handle h, const double *fine, const double *members) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    if (h->mixed) {  // one scratch size for both conversions (no reallocation between them)
+        mgenkf_status st = ensure_scratch(h, std::max(h->nxf, (size_t)h->ne * h->nx));
+        if (st) return st;
+    }
+    if (fine) {
+        mgenkf_status st = load_state(h, h->fine, fine, h->nxf);
+        if (st) return st;
+    }
+    if (members) {
+        mgenkf_status st = load_state(h, h->members, members, (size_t)h->ne * h->nx);
+        if (st) return st;
+    }
+    h->cycle = 0;
+    H_CUDA(cudaStreamSynchronize(h->stream));
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_get_state(mgenkf_handle h, double *fine, double *members) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    {
+        mgenkf_status st = ensure_scratch(h, std::max(h->nxf, (size_t)h->ne * h->nx));
+        if (st) return st;
+    }
+    if (fine) {
+        mgenkf_status st = store_state(h, fine, h->fine, h->nxf);
+        if (st) return st;
+    }
+    if (members) {
+        mgenkf_status st = store_state(h, members, h->members, (size_t)h->ne * h->nx);
+        if (st) return st;
+    }
+    return MGENKF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the cycle
+// ---------------------------------------------------------------------------
+static mgenkf_status forecast_impl(mgenkf_ctx *h, int nsteps) {
+    if (nsteps < 0) H_FAIL(MGENKF_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return MGENKF_OK;
+    const mgenkf_config &c = h->cfg;
+    cudaError_t e;
+    if (c.model == MGENKF_BURGERS1D) {
+        if (h->mixed)
+            e = burgers_forecast<float>((float *)h->members, h->nc, h->ne, (float *)h->fine, h->nf, 1,
+                                        c.length, c.dt, c.nu, nsteps, h->stream);
+        else
+            e = burgers_forecast<double>((double *)h->members, h->nc, h->ne, (double *)h->fine, h->nf, 1,
+                                         c.length, c.dt, c.nu, nsteps, h->stream);
+    } else {
+        if (h->mixed)
+            e = ns2d_forecast<float>((float *)h->members, h->nc, h->ne, (float *)h->fine, h->nf, 1,
+                                     c.length, c.dt, c.nu, c.gamma, c.prandtl, nsteps, h->stream);
+        else
+            e = ns2d_forecast<double>((double *)h->members, h->nc, h->ne, (double *)h->fine, h->nf, 1,
+                                      c.length, c.dt, c.nu, c.gamma, c.prandtl, nsteps, h->stream);
+    }
+    if (e != cudaSuccess) H_FAIL(MGENKF_ERR_CUDA, std::string("forecast launch: ") + cudaGetErrorString(e));
+    H_LAUNCHED();
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_forecast(mgenkf_handle h, int32_t nsteps) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    return forecast_impl(h, nsteps);
+}
+
+template <typename T>
+static void analyse_kernels(mgenkf_ctx *h, int gen_eps) {
+    const cudaStream_t s = h->stream;
+    const int ne = h->ne, ny = h->ny;
+    const size_t nx = h->nx;
+    T *members = (T *)h->members, *xstar = (T *)h->xstar, *dC = (T *)h->dC;
+    launch_restrict<T>((const T *)h->fine, xstar, h->dim, h->V, h->nc, h->r, s);
+    launch_obs_apply<T>(members, xstar, nx, ne, ny, h->taps, h->tap_idx, h->tap_w, h->yf, s);
+    launch_obs_mean(h->yf, h->yo, ne, ny, h->ybar, h->Z, h->status, s);
+    launch_obs_perturb(h->yf, h->ybar, h->yo, h->eps, gen_eps, h->cfg.seed, h->cycle,
+                       h->cfg.obs_sigma, ne, ny, h->Y, h->Z, s);
+    launch_ens_anom<T>(members, nx, ne, h->X64, h->X16, h->status, s);
+    const double s2 = h->cfg.obs_sigma * h->cfg.obs_sigma;
+    if (!h->direct) {
+        // S = I + Y^T R^-1 Y (ne x ne) and B = Y^T R^-1 [D | d*]; T = S^-1 B
+        launch_gemm_nt_f64(h->Y, ne, h->Y, ne, h->Z, ne + 1, ny, s2, 1.0, h->S, h->Bt, h->status, s);
+        launch_cholesky(h->S, h->Lt, ne, h->status, s);
+        launch_chol_solve(h->S, h->Lt, ne, h->Bt, h->Bt, ne + 1, h->mixed ? h->Tt : nullptr, h->ldx,
+                          h->status, s);
+    } else {
+        // C = Y Y^T + R (ny x ny), W = C^-1 [D | d*], T = Y^T W
+        launch_gemm_tn_f64(h->Y, ne, ny, s2, h->C, h->status, s);
+        launch_cholesky(h->C, h->Ct, ny, h->status, s);
+        launch_chol_solve(h->C, h->Ct, ny, h->Z, h->W, ne + 1, nullptr, 0, h->status, s);
+        launch_gemm_nt_f64(h->Y, ne, nullptr, 0, h->W, ne + 1, ny, 1.0, 0.0, nullptr, h->Tm, h->status, s);
+        if (h->mixed) launch_tt_bf16(h->Tm, h->Tt, ne, h->ldx, h->status, s);
+    }
+    if (h->mixed)
+        launch_update_bf16((float *)members, (float *)dC, h->X16, h->Tt, h->ldx, nx, ne, h->status, s);
+    else
+        launch_update_f64<T>(members, dC, h->X64, h->Tm, nx, ne, h->status, s);
+}
+
+static mgenkf_status analyse_impl(mgenkf_ctx *h, const double *y_obs, const double *eps) {
+    if (!y_obs) H_FAIL(MGENKF_ERR_INVALID_ARG, "y_obs is required");
+    const bool ydev = is_device_ptr(y_obs);
+    if (!ydev) {
+        for (int j = 0; j < h->ny; ++j)
+            if (!std::isfinite(y_obs[j])) H_FAIL(MGENKF_ERR_NONFINITE, "y_obs[" + std::to_string(j) + "] is not finite");
+    }
+    H_CUDA(cudaMemsetAsync(h->dC, 0, h->nx * tsize(h), h->stream));
+    H_CUDA(cudaMemcpyAsync(h->yo, y_obs, h->ny * sizeof(double), cudaMemcpyDefault, h->stream));
+    if (eps) H_CUDA(cudaMemcpyAsync(h->eps, eps, (size_t)h->ne * h->ny * sizeof(double), cudaMemcpyDefault, h->stream));
+    if (h->mixed)
+        analyse_kernels<float>(h, eps ? 0 : 1);
+    else
+        analyse_kernels<double>(h, eps ? 0 : 1);
+    H_LAUNCHED();
+    h->cycle += 1;
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_analyse(mgenkf_handle h, const double *y_obs, const double *eps) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    return analyse_impl(h, y_obs, eps);
+}
+
+static mgenkf_status prolong_impl(mgenkf_ctx *h) {
+    if (h->mixed)
+        launch_prolong_add<float>((float *)h->fine, (const float *)h->dC, h->dim, h->V, h->nc, h->r, h->pw, h->status, h->stream);
+    else
+        launch_prolong_add<double>((double *)h->fine, (const double *)h->dC, h->dim, h->V, h->nc, h->r, h->pw, h->status, h->stream);
+    H_LAUNCHED();
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_prolong_correct(mgenkf_handle h) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    return prolong_impl(h);
+}
+
+static mgenkf_status rmse_impl(mgenkf_ctx *h, const double *truth, double *out) {
+    if (!truth || !out) H_FAIL(MGENKF_ERR_INVALID_ARG, "truth_fine and out are required");
+    const double *t = truth;
+    if (!is_device_ptr(truth)) {
+        if (!h->truth_d) H_ALLOC(h->truth_d, h->nxf * sizeof(double));
+        H_CUDA(cudaMemcpyAsync(h->truth_d, truth, h->nxf * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        t = h->truth_d;
+    }
+    const size_t npts = h->nxf / h->V;
+    if (h->mixed)
+        launch_rmse<float>((const float *)h->fine, t, h->V, npts, h->rmse_part, kRmseBlocks, h->rmse_d, h->stream);
+    else
+        launch_rmse<double>((const double *)h->fine, t, h->V, npts, h->rmse_part, kRmseBlocks, h->rmse_d, h->stream);
+    H_LAUNCHED();
+    return copy_out_f64(h, out, h->rmse_d, h->V);
+}
+
+extern "C" mgenkf_status mgenkf_rmse(mgenkf_handle h, const double *truth_fine, double *out) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    return rmse_impl(h, truth_fine, out);
+}
+
+extern "C" mgenkf_status mgenkf_cycle(mgenkf_handle h, int32_t nsteps, const double *y_obs,
+                                      const double *truth_fine, double *rmse_out) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    mgenkf_status st = forecast_impl(h, nsteps);
+    if (st) return st;
+    st = analyse_impl(h, y_obs, nullptr);
+    if (st) return st;
+    st = prolong_impl(h);
+    if (st) return st;
+    if (truth_fine) {
+        if (!rmse_out) H_FAIL(MGENKF_ERR_INVALID_ARG, "rmse_out is required with truth_fine");
+        st = rmse_impl(h, truth_fine, rmse_out);
+    }
+    return st;
+}
+
+extern "C" mgenkf_status mgenkf_get_field(mgenkf_handle h, int32_t field, double *out, size_t count) {
+    if (!h || !out) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    const size_t ne = h->ne, ny = h->ny;
+    switch (field) {
+        case MGENKF_FIELD_XSTAR:
+            if (count < h->nx) H_FAIL(MGENKF_ERR_INVALID_ARG, "count too small");
+            return store_state(h, out, h->xstar, h->nx);
+        case MGENKF_FIELD_DC:
+            if (count < h->nx) H_FAIL(MGENKF_ERR_INVALID_ARG, "count too small");
+            return store_state(h, out, h->dC, h->nx);
+        case MGENKF_FIELD_YF:
+            if (count < (ne + 1) * ny) H_FAIL(MGENKF_ERR_INVALID_ARG, "count too small");
+            return copy_out_f64(h, out, h->yf, (ne + 1) * ny);
+        case MGENKF_FIELD_T:
+            if (count < (ne + 1) * ne) H_FAIL(MGENKF_ERR_INVALID_ARG, "count too small");
+            return copy_out_f64(h, out, h->Tm, (ne + 1) * ne);
+        case MGENKF_FIELD_EPS:
+            if (count < ne * ny) H_FAIL(MGENKF_ERR_INVALID_ARG, "count too small");
+            return copy_out_f64(h, out, h->eps, ne * ny);
+        default:
+            H_FAIL(MGENKF_ERR_INVALID_ARG, "unknown field");
+    }
+}
+
+extern "C" mgenkf_status mgenkf_sync(mgenkf_handle h) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    H_CUDA(cudaStreamSynchronize(h->stream));
+    int st = 0;
+    H_CUDA(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        H_CUDA(cudaMemset(h->status, 0, sizeof(int)));
+        h->err = st == MGENKF_ERR_NOT_SPD ? "innovation matrix not SPD: members and fine run left unchanged"
+                                         : "non-finite observation: members and fine run left unchanged";
+        return (mgenkf_status)st;
+    }
+    return MGENKF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint
+// ---------------------------------------------------------------------------
+struct CkptHeader {
+    char magic[8];
+    int32_t model, n_fine, ratio, n_members, n_obs, precision;
+    uint64_t cycle;
+};
+
+extern "C" mgenkf_status mgenkf_save(mgenkf_handle h, const char *path) {
+    if (!h || !path) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    std::vector<double> fine(h->nxf), mem((size_t)h->ne * h->nx);
+    mgenkf_status st = mgenkf_get_state(h, fine.data(), mem.data());
+    if (st) return st;
+    FILE *f = fopen(path, "wb");
+    if (!f) H_FAIL(MGENKF_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    CkptHeader hd;
+    memcpy(hd.magic, "MGENKF01", 8);
+    hd.model = h->cfg.model;
+    hd.n_fine = h->nf;
+    hd.ratio = h->r;
+    hd.n_members = h->ne;
+    hd.n_obs = h->ny;
+    hd.precision = h->cfg.precision;
+    hd.cycle = h->cycle;
+    bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(fine.data(), sizeof(double), fine.size(), f) == fine.size() &&
+              fwrite(mem.data(), sizeof(double), mem.size(), f) == mem.size();
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) H_FAIL(MGENKF_ERR_INVALID_ARG, std::string("write failed: ") + path);
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_load(mgenkf_handle h, const char *path) {
+    if (!h || !path) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    FILE *f = fopen(path, "rb");
+    if (!f) H_FAIL(MGENKF_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    CkptHeader hd;
+    std::vector<double> fine(h->nxf), mem((size_t)h->ne * h->nx);
+    bool ok = fread(&hd, sizeof(hd), 1, f) == 1;
+    ok = ok && memcmp(hd.magic, "MGENKF01", 8) == 0 && hd.model == h->cfg.model && hd.n_fine == h->nf &&
+         hd.ratio == h->r && hd.n_members == h->ne && hd.n_obs == h->ny;
+    ok = ok && fread(fine.data(), sizeof(double), fine.size(), f) == fine.size() &&
+         fread(mem.data(), sizeof(double), mem.size(), f) == mem.size();
+    fclose(f);
+    if (!ok) H_FAIL(MGENKF_ERR_INVALID_ARG, std::string("checkpoint does not match this handle: ") + path);
+    mgenkf_status st = mgenkf_set_state(h, fine.data(), mem.data());
+    if (st) return st;
+    h->cycle = hd.cycle;
+    return MGENKF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stateless entry points (include/mgenkf_ops.h)
+// ---------------------------------------------------------------------------
+extern "C" mgenkf_status mgk_forecast(int32_t model, int32_t precision, void *state, int32_t nprob,
+                                      int32_t n, double length, double dt, double nu, double gamma,
+                                      double prandtl, int32_t nsteps, void *stream) {
+    g_ops_error.clear();
+    if (!state || nprob < 0 || nsteps < 0 || !(dt > 0.0) || !(length > 0.0)) {
+        g_ops_error = "invalid state pointer, nprob, nsteps, dt or length";
+        return MGENKF_ERR_INVALID_ARG;
+    }
+    if (precision != MGENKF_FP64 && precision != MGENKF_MIXED) {
+        g_ops_error = "precision must be MGENKF_FP64 or MGENKF_MIXED";
+        return MGENKF_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (model == MGENKF_BURGERS1D) {
+        if (n < 4 || n > 8 * kBurgersMaxPtsPerCta || burgers_split_factor(n) == 0) {
+            g_ops_error = "Burgers n must be in [4, 32768] and split into <= 8 CTAs of <= 4096 points";
+            return MGENKF_ERR_INVALID_ARG;
+        }
+        const bool whole = n <= kBurgersMaxPtsPerCta;
+        if (precision == MGENKF_MIXED)
+            e = whole ? burgers_forecast<float>((float *)state, n, nprob, nullptr, 0, 0, length, dt, nu, nsteps, s)
+                      : burgers_forecast<float>(nullptr, 0, 0, (float *)state, n, nprob, length, dt, nu, nsteps, s);
+        else
+            e = whole ? burgers_forecast<double>((double *)state, n, nprob, nullptr, 0, 0, length, dt, nu, nsteps, s)
+                      : burgers_forecast<double>(nullptr, 0, 0, (double *)state, n, nprob, length, dt, nu, nsteps, s);
+    } else if (model == MGENKF_NS2D) {
+        const char *why = ns2d_check_size(n, n);
+        if (why) {
+            g_ops_error = why;
+            return MGENKF_ERR_INVALID_ARG;
+        }
+        if (precision == MGENKF_MIXED)
+            e = ns2d_forecast<float>((float *)state, n, nprob, nullptr, 0, 0, length, dt, nu, gamma, prandtl, nsteps, s);
+        else
+            e = ns2d_forecast<double>((double *)state, n, nprob, nullptr, 0, 0, length, dt, nu, gamma, prandtl, nsteps, s);
+    } else {
+        g_ops_error = "model must be MGENKF_BURGERS1D or MGENKF_NS2D";
+        return MGENKF_ERR_INVALID_ARG;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_ops_error = std::string("forecast launch: ") + cudaGetErrorString(e);
+        return MGENKF_ERR_CUDA;
+    }
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgk_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count,
+                                     double *out, void *stream) {
+    g_ops_error.clear();
+    if (count < 0 || (count > 0 && !out)) {
+        g_ops_error = "count must be >= 0 and out non-NULL";
+        return MGENKF_ERR_INVALID_ARG;
+    }
+    launch_normals(seed, tag, ctr0, count, out, (cudaStream_t)stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_ops_error = std::string("normals launch: ") + cudaGetErrorString(e);
+        return MGENKF_ERR_CUDA;
+    }
+    return MGENKF_OK;
+}
+
+extern "C" const char *mgk_last_error(void) { return g_ops_error.c_str(); }

@@ -1,0 +1,272 @@
+"""Python binding of the MGEnKF C ABI (``include/mgenkf.h``, ``include/mgenkf_ops.h``).
+
+Argument marshalling only: every function forwards to the entry point of the
+same name in ``libmgenkf.so``.  Arrays may be numpy arrays (host memory) or
+objects with ``data_ptr()`` (torch tensors, host or device); the library tells
+host from device pointers itself.  There is no fallback: if the compiled
+library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmgenkf.so")
+
+MGENKF_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_SPD", 5: "NONFINITE",
+                6: "UNSUPPORTED"}
+MGENKF_BURGERS1D, MGENKF_NS2D = 1, 2
+MGENKF_FP64, MGENKF_MIXED = 0, 1
+MGENKF_GAIN_ENSEMBLE, MGENKF_GAIN_DIRECT = 0, 1
+MGENKF_PROLONG_LAGRANGE4 = 0
+MGENKF_FIELD_XSTAR, MGENKF_FIELD_YF, MGENKF_FIELD_T, MGENKF_FIELD_DC, MGENKF_FIELD_EPS = 0, 1, 2, 3, 4
+EPS_TAG = 0x45505300
+
+
+class MGEnKFError(RuntimeError):
+    def __init__(self, status: int, where: str, text: str):
+        self.status = status
+        super().__init__(f"{where}: MGENKF_ERR_{STATUS_NAMES.get(status, status)}: {text}")
+
+
+class mgenkf_config(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("n_fine", ctypes.c_int32), ("ratio", ctypes.c_int32),
+                ("n_members", ctypes.c_int32), ("n_obs", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("gain_form", ctypes.c_int32),
+                ("prolong", ctypes.c_int32), ("length", ctypes.c_double), ("dt", ctypes.c_double),
+                ("nu", ctypes.c_double), ("gamma", ctypes.c_double), ("prandtl", ctypes.c_double),
+                ("obs_sigma", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2012_10091_gb300.build` (there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, u64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                 ctypes.c_double, ctypes.c_size_t)
+    sigs = {
+        "mgenkf_create": [ctypes.POINTER(mgenkf_config), P, P, P, ctypes.POINTER(P)],
+        "mgenkf_set_state": [P, P, P],
+        "mgenkf_forecast": [P, i32],
+        "mgenkf_analyse": [P, P, P],
+        "mgenkf_prolong_correct": [P],
+        "mgenkf_cycle": [P, i32, P, P, P],
+        "mgenkf_get_state": [P, P, P],
+        "mgenkf_rmse": [P, P, P],
+        "mgenkf_get_field": [P, i32, P, sz],
+        "mgenkf_sync": [P],
+        "mgenkf_save": [P, ctypes.c_char_p],
+        "mgenkf_load": [P, ctypes.c_char_p],
+        "mgenkf_destroy": [P],
+        "mgk_forecast": [i32, i32, P, i32, i32, f64, f64, f64, f64, f64, i32, P],
+        "mgk_normals": [u64, u64, u64, i64, P, P],
+    }
+    for name, args in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.mgenkf_last_error.argtypes = [P]
+    L.mgenkf_last_error.restype = ctypes.c_char_p
+    L.mgk_last_error.argtypes = []
+    L.mgk_last_error.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def _ptr(x):
+    """Raw address of a numpy array, a tensor-like object, an int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _as_f64(x):
+    if x is None or hasattr(x, "data_ptr"):
+        return x
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _check(st, where, h=None):
+    if st != MGENKF_OK:
+        text = (lib.mgenkf_last_error(h) if h else lib.mgk_last_error()) or b""
+        raise MGEnKFError(st, where, text.decode())
+
+
+# ---------------------------------------------------------------------------
+# entry points, same names as the C ABI
+# ---------------------------------------------------------------------------
+def mgenkf_create(cfg: mgenkf_config, obs_index, obs_var, stream=None):
+    oi = np.ascontiguousarray(obs_index, dtype=np.int32)
+    ov = np.ascontiguousarray(obs_var, dtype=np.int32)
+    h = ctypes.c_void_p()
+    st = lib.mgenkf_create(ctypes.byref(cfg), oi.ctypes.data, ov.ctypes.data, stream, ctypes.byref(h))
+    _check(st, "mgenkf_create")
+    return h.value
+
+
+def mgenkf_set_state(h, fine, members):
+    fine, members = _as_f64(fine), _as_f64(members)
+    _check(lib.mgenkf_set_state(h, _ptr(fine), _ptr(members)), "mgenkf_set_state", h)
+
+
+def mgenkf_forecast(h, nsteps: int):
+    _check(lib.mgenkf_forecast(h, nsteps), "mgenkf_forecast", h)
+
+
+def mgenkf_analyse(h, y_obs, eps=None):
+    y_obs, eps = _as_f64(y_obs), _as_f64(eps)
+    _check(lib.mgenkf_analyse(h, _ptr(y_obs), _ptr(eps)), "mgenkf_analyse", h)
+
+
+def mgenkf_prolong_correct(h):
+    _check(lib.mgenkf_prolong_correct(h), "mgenkf_prolong_correct", h)
+
+
+def mgenkf_cycle(h, nsteps, y_obs, truth_fine=None, rmse_out=None):
+    y_obs, truth_fine = _as_f64(y_obs), _as_f64(truth_fine)
+    _check(lib.mgenkf_cycle(h, nsteps, _ptr(y_obs), _ptr(truth_fine), _ptr(rmse_out)),
+           "mgenkf_cycle", h)
+
+
+def mgenkf_get_state(h, fine_out=None, members_out=None):
+    _check(lib.mgenkf_get_state(h, _ptr(fine_out), _ptr(members_out)), "mgenkf_get_state", h)
+
+
+def mgenkf_rmse(h, truth_fine, out):
+    truth_fine = _as_f64(truth_fine)
+    _check(lib.mgenkf_rmse(h, _ptr(truth_fine), _ptr(out)), "mgenkf_rmse", h)
+
+
+def mgenkf_get_field(h, field: int, out, count: int):
+    _check(lib.mgenkf_get_field(h, field, _ptr(out), count), "mgenkf_get_field", h)
+
+
+def mgenkf_sync(h) -> int:
+    """Returns the device-side status (0 = OK); does not raise for NOT_SPD/NONFINITE."""
+    return lib.mgenkf_sync(h)
+
+
+def mgenkf_save(h, path: str):
+    _check(lib.mgenkf_save(h, path.encode()), "mgenkf_save", h)
+
+
+def mgenkf_load(h, path: str):
+    _check(lib.mgenkf_load(h, path.encode()), "mgenkf_load", h)
+
+
+def mgenkf_last_error(h) -> str:
+    return (lib.mgenkf_last_error(h) or b"").decode()
+
+
+def mgenkf_destroy(h):
+    _check(lib.mgenkf_destroy(h), "mgenkf_destroy")
+
+
+def mgk_forecast(model, precision, state, nprob, n, length, dt, nu, gamma=1.4, prandtl=0.72,
+                 nsteps=1, stream=None):
+    _check(lib.mgk_forecast(model, precision, _ptr(state), nprob, n, length, dt, nu, gamma, prandtl,
+                            nsteps, stream), "mgk_forecast")
+
+
+def mgk_normals(seed, tag, ctr0, count, out, stream=None):
+    _check(lib.mgk_normals(seed, tag, ctr0, count, _ptr(out), stream), "mgk_normals")
+
+
+# ---------------------------------------------------------------------------
+# object wrapper over one handle
+# ---------------------------------------------------------------------------
+class MGEnKF:
+    """One MGEnKF run on the GPU (handle owner).  See include/mgenkf.h."""
+
+    def __init__(self, *, model, n_fine, ratio, n_members, obs_index, obs_var, length, dt, nu,
+                 obs_sigma, seed=0, precision=MGENKF_FP64, gain_form=MGENKF_GAIN_ENSEMBLE,
+                 gamma=1.4, prandtl=0.72, stream=None):
+        self.cfg = mgenkf_config(model=model, n_fine=n_fine, ratio=ratio, n_members=n_members,
+                                 n_obs=len(obs_index), precision=precision, gain_form=gain_form,
+                                 prolong=MGENKF_PROLONG_LAGRANGE4, length=length, dt=dt, nu=nu,
+                                 gamma=gamma, prandtl=prandtl, obs_sigma=obs_sigma, seed=seed)
+        self.h = mgenkf_create(self.cfg, obs_index, obs_var, stream)
+        self.dim = 1 if model == MGENKF_BURGERS1D else 2
+        self.V = 1 if model == MGENKF_BURGERS1D else 4
+        self.nc = n_fine // ratio
+        self.nx = self.V * self.nc**self.dim
+        self.nxf = self.V * n_fine**self.dim
+        self.ne, self.ny = n_members, len(obs_index)
+
+    @classmethod
+    def from_workload(cls, w, gain_form=MGENKF_GAIN_ENSEMBLE, precision=None, stream=None):
+        from . import workloads as W
+        idx, var = W.observation_layout(w)
+        prec = {"fp64": MGENKF_FP64, "mixed": MGENKF_MIXED}[precision or w.precision]
+        return cls(model=MGENKF_BURGERS1D if w.model == W.BURGERS1D else MGENKF_NS2D,
+                   n_fine=w.nf, ratio=w.ratio, n_members=w.ne, obs_index=idx, obs_var=var,
+                   length=w.length, dt=w.dt, nu=w.nu, obs_sigma=w.sigma, seed=w.seed,
+                   precision=prec, gain_form=gain_form, gamma=w.gamma, prandtl=w.prandtl,
+                   stream=stream)
+
+    def close(self):
+        if self.h:
+            mgenkf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, fine, members):
+        mgenkf_set_state(self.h, fine, members)
+
+    def forecast(self, nsteps):
+        mgenkf_forecast(self.h, nsteps)
+
+    def analyse(self, y_obs, eps=None):
+        mgenkf_analyse(self.h, y_obs, eps)
+
+    def prolong_correct(self):
+        mgenkf_prolong_correct(self.h)
+
+    def cycle(self, nsteps, y_obs, truth=None, rmse_out=None):
+        mgenkf_cycle(self.h, nsteps, y_obs, truth, rmse_out)
+
+    def sync(self) -> int:
+        return mgenkf_sync(self.h)
+
+    def get_state(self):
+        fine = np.empty(self.nxf)
+        mem = np.empty((self.ne, self.nx))
+        mgenkf_get_state(self.h, fine, mem)
+        return fine, mem
+
+    def field(self, which):
+        n = {MGENKF_FIELD_XSTAR: self.nx, MGENKF_FIELD_DC: self.nx,
+             MGENKF_FIELD_YF: (self.ne + 1) * self.ny, MGENKF_FIELD_T: (self.ne + 1) * self.ne,
+             MGENKF_FIELD_EPS: self.ne * self.ny}[which]
+        out = np.empty(n)
+        mgenkf_get_field(self.h, which, out, n)
+        return out
+
+    def save(self, path):
+        mgenkf_save(self.h, path)
+
+    def load(self, path):
+        mgenkf_load(self.h, path)
+
+    def rmse(self, truth):
+        out = np.empty(self.V)
+        mgenkf_rmse(self.h, truth, out)
+        return out

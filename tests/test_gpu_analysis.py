@@ -1,0 +1,92 @@
+"""GPU parity of the coarse-mesh EnKF analysis and the multigrid correction
+(Algorithm 3 state part, Algorithm 4 steps 4-5) against the CPU oracle, step
+by step, for both gain forms, FP64 and mixed precision, on ragged sizes."""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import rel_err
+from paper_2012_10091_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_10091_gb300 import mgenkf
+    return mgenkf
+
+
+CASES = [  # nf, ratio, ne, n_probes: several tiles and ragged tails
+    (256, 4, 32, 16), (240, 3, 7, 11), (4096, 4, 37, 130), (1000, 8, 130, 257), (64, 1, 5, 3)]
+
+
+def _one_analysis(M, w, gain_form, precision, explicit_eps):
+    inp = W.make_inputs(w)
+    g = M.MGEnKF.from_workload(w, gain_form=gain_form, precision=precision)
+    g.set_state(inp["fine0"], inp["members0"])
+    rng = np.random.default_rng(w.nf + w.ne)
+    yo = rng.standard_normal(w.ny) * 0.5
+    eps = w.sigma * rng.standard_normal((w.ne, w.ny)) if explicit_eps else None
+    g.analyse(yo, eps)
+    g.prolong_correct()
+    assert g.sync() == 0
+    fine, mem = g.get_state()
+    fields = {k: g.field(k) for k in (M.MGENKF_FIELD_XSTAR, M.MGENKF_FIELD_YF, M.MGENKF_FIELD_T,
+                                      M.MGENKF_FIELD_DC, M.MGENKF_FIELD_EPS)}
+    g.close()
+    # oracle on the same inputs (rounded to FP32 first in mixed precision)
+    f0, m0 = inp["fine0"], inp["members0"]
+    if precision == "mixed":
+        f0, m0 = f0.astype(np.float32).astype(np.float64), m0.astype(np.float32).astype(np.float64)
+    e = eps if explicit_eps else O.obs_perturbations(w.seed, 0, w.ne, w.ny, w.sigma)
+    xstar = O.restrict(f0, 1, 1, w.nc, w.ratio)
+    st, m_ref, dC_ref = O.enkf_analyse(m0, xstar, yo, e, w.sigma, inp["obs_idx"], inp["obs_var"],
+                                       1, 1, w.nc, w.ratio, gain_form=0 if gain_form else 1)
+    assert st == 0
+    fine_ref = O.prolong_add(dC_ref, f0, 1, 1, w.nc, w.ratio)
+    return dict(fine=fine, mem=mem, fields=fields, xstar=xstar, e=e, m_ref=m_ref, dC_ref=dC_ref,
+                fine_ref=fine_ref, m0=m0, f0=f0)
+
+
+@pytest.mark.parametrize("gain_form", [0, 1])
+@pytest.mark.parametrize("nf,ratio,ne,npr", CASES)
+def test_fp64_analysis_matches_oracle(M, nf, ratio, ne, npr, gain_form):
+    if gain_form == 1 and npr > 512:
+        pytest.skip("direct form checked on moderate n_obs")
+    w = W.burgers_custom(nf, ratio, ne, npr, obs_kind="random", sigma=0.3)
+    r = _one_analysis(M, w, gain_form, "fp64", explicit_eps=False)
+    np.testing.assert_allclose(r["fields"][M.MGENKF_FIELD_EPS].reshape(w.ne, w.ny), r["e"],
+                               rtol=1e-14, atol=1e-15)
+    np.testing.assert_array_equal(r["fields"][M.MGENKF_FIELD_XSTAR], r["xstar"])
+    yf_ref = np.stack([O.obs_coarse(x, 1, 1, w.nc, w.ratio, *W.observation_layout(w))
+                       for x in list(r["m0"]) + [r["xstar"]]])
+    assert rel_err(r["fields"][M.MGENKF_FIELD_YF].reshape(w.ne + 1, w.ny), yf_ref) < 1e-13
+    assert rel_err(r["fields"][M.MGENKF_FIELD_DC], r["dC_ref"]) < 1e-10
+    assert rel_err(r["mem"] - r["m0"], r["m_ref"] - r["m0"]) < 1e-10
+    assert rel_err(r["fine"], r["fine_ref"]) < 1e-12
+
+
+@pytest.mark.parametrize("nf,ratio,ne,npr", [(256, 4, 32, 16), (4096, 4, 37, 130), (16384, 4, 128, 512)])
+def test_mixed_analysis_matches_oracle(M, nf, ratio, ne, npr):
+    w = W.burgers_custom(nf, ratio, ne, npr, obs_kind="random", sigma=0.05, precision="mixed")
+    r = _one_analysis(M, w, 0, "mixed", explicit_eps=True)
+    # BF16 anomalies and gain coefficients (8-bit mantissa) with FP32 accumulation:
+    # the increment X T carries ~2^-8 relative error; the states are FP32.
+    inc, inc_ref = r["mem"] - r["m0"], r["m_ref"] - r["m0"]
+    assert rel_err(inc, inc_ref) < 2e-2
+    assert rel_err(r["fields"][M.MGENKF_FIELD_DC], r["dC_ref"]) < 2e-2
+    assert rel_err(r["mem"], r["m_ref"]) < 1e-3
+    assert rel_err(r["fine"], r["fine_ref"]) < 1e-3
+
+
+def test_explicit_perturbations_are_used(M):
+    w = W.burgers_custom(256, 4, 9, 7, obs_kind="random", sigma=0.2)
+    r = _one_analysis(M, w, 0, "fp64", explicit_eps=True)
+    np.testing.assert_array_equal(r["fields"][M.MGENKF_FIELD_EPS].reshape(w.ne, w.ny), r["e"])
+    assert rel_err(r["mem"] - r["m0"], r["m_ref"] - r["m0"]) < 1e-10

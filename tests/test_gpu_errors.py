@@ -1,0 +1,84 @@
+"""Failure detection of the C ABI, injected on the host (bad arguments,
+non-finite observations, a singular innovation matrix from R = 0): every
+failure is reported as a status and leaves the run's state unchanged.
+No GPU fault, trap or hang is involved."""
+import numpy as np
+import pytest
+
+from paper_2012_10091_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_10091_gb300 import mgenkf
+    return mgenkf
+
+
+def _handle(M, w, **kw):
+    g = M.MGEnKF.from_workload(w, **kw)
+    inp = W.make_inputs(w)
+    g.set_state(inp["fine0"], inp["members0"])
+    return g, inp
+
+
+def test_invalid_configs_are_rejected(M):
+    w = W.burgers_custom(256, 4, 8, 5)
+    idx, var = W.observation_layout(w)
+    base = dict(model=M.MGENKF_BURGERS1D, n_fine=256, ratio=4, n_members=8, obs_index=idx,
+                obs_var=var, length=6.28, dt=1e-3, nu=0.01, obs_sigma=0.1)
+    for bad in [dict(ratio=3), dict(n_members=1), dict(ratio=0), dict(n_fine=2 ** 17, ratio=4),
+                dict(obs_sigma=0.0), dict(dt=0.0), dict(model=7)]:
+        kw = {**base, **bad}
+        with pytest.raises(M.MGEnKFError) as e:
+            M.MGEnKF(**kw)
+        assert e.value.status == 1, bad
+    with pytest.raises(M.MGEnKFError):
+        M.MGEnKF(**{**base, "obs_index": np.array([0, 1, 2, 3, 99999])})
+
+
+def test_nonfinite_host_observation(M):
+    w = W.burgers_custom(256, 4, 8, 5)
+    g, inp = _handle(M, w)
+    yo = np.zeros(w.ny)
+    yo[2] = np.nan
+    with pytest.raises(M.MGEnKFError) as e:
+        g.analyse(yo)
+    assert e.value.status == 5
+    fine, mem = g.get_state()
+    np.testing.assert_array_equal(mem, inp["members0"])
+
+
+def test_nonfinite_device_observation_leaves_state_unchanged(M):
+    import torch
+    w = W.burgers_custom(256, 4, 8, 5)
+    g, inp = _handle(M, w)
+    yo = torch.zeros(w.ny, dtype=torch.float64, device="cuda")
+    yo[1] = float("inf")
+    g.analyse(yo)
+    g.prolong_correct()
+    assert g.sync() == 5
+    fine, mem = g.get_state()
+    np.testing.assert_array_equal(mem, inp["members0"])
+    np.testing.assert_array_equal(fine, inp["fine0"])
+    # the handle stays usable
+    g.analyse(np.zeros(w.ny))
+    assert g.sync() == 0
+
+
+def test_singular_innovation_matrix_reported(M):
+    # direct form with R = 0 and n_obs > Ne - 1: Y Y^T is singular
+    w = W.burgers_custom(256, 1, 4, 12, sigma=0.0)
+    g, inp = _handle(M, w, gain_form=M.MGENKF_GAIN_DIRECT)
+    g.analyse(np.ones(w.ny), np.zeros((w.ne, w.ny)))
+    g.prolong_correct()
+    assert g.sync() == 4
+    fine, mem = g.get_state()
+    np.testing.assert_array_equal(mem, inp["members0"])
+    np.testing.assert_array_equal(fine, inp["fine0"])

@@ -1,0 +1,89 @@
+"""GPU parity of the batched model forecast (Burgers SSP-RK3) and of the
+Philox normals against the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_10091_gb300 import mgenkf
+    return mgenkf
+
+
+def _init(nprob, n, seed):
+    rng = np.random.default_rng(seed)
+    x = np.arange(n) * 2 * math.pi / n
+    return np.stack([0.8 * np.sin(x + rng.uniform(0, 6)) + 0.05 * rng.standard_normal(n)
+                     for _ in range(nprob)])
+
+
+# whole-CTA grids (<= 4096) incl. ragged thread tails, and cluster-split grids
+@pytest.mark.parametrize("n,nprob", [(4, 3), (64, 32), (100, 5), (256, 2), (1000, 3), (4095, 2),
+                                     (4096, 4), (5000, 2), (16384, 1), (32768, 1)])
+def test_burgers_fp64_matches_oracle(M, n, nprob):
+    import torch
+    u0 = _init(nprob, n, n)
+    dx, nu = 2 * math.pi / n, 0.01
+    dt = min(1e-3, 0.3 * dx * dx / nu, 0.5 * dx)
+    steps = 37
+    ref = O.burgers_rk3(u0, dx, nu, dt, steps)
+    d = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_FP64, d, nprob, n, 2 * math.pi, dt, nu, nsteps=steps)
+    torch.cuda.synchronize()
+    got = d.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("n,nprob", [(64, 32), (4096, 8), (16384, 1)])
+def test_burgers_fp32_matches_oracle(M, n, nprob):
+    import torch
+    u0 = _init(nprob, n, n + 1)
+    dx, nu = 2 * math.pi / n, 0.01
+    dt = min(1e-3, 0.3 * dx * dx / nu)
+    steps = 200
+    ref = O.burgers_rk3(u0, dx, nu, dt, steps)
+    d = torch.tensor(u0, dtype=torch.float32, device="cuda")
+    M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_MIXED, d, nprob, n, 2 * math.pi, dt, nu, nsteps=steps)
+    torch.cuda.synchronize()
+    # FP32 rounding of ~1e-7 per step, accumulated over 200 steps
+    assert np.max(np.abs(d.cpu().double().numpy() - ref)) <= 2e-5 * np.max(np.abs(ref))
+
+
+def test_burgers_zero_steps_and_empty_batch(M):
+    import torch
+    u0 = _init(2, 128, 3)
+    d = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_FP64, d, 2, 128, 2 * math.pi, 1e-3, 0.01, nsteps=0)
+    M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_FP64, d, 0, 128, 2 * math.pi, 1e-3, 0.01, nsteps=5)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d.cpu().numpy(), u0)
+
+
+def test_burgers_rejects_oversize_grid(M):
+    import torch
+    d = torch.zeros(65536, dtype=torch.float64, device="cuda")
+    with pytest.raises(M.MGEnKFError) as e:
+        M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_FP64, d, 1, 65536, 1.0, 1e-3, 0.01, nsteps=1)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("count,ctr0", [(1, 0), (4, 7), (1023, 3), (100_000, 11)])
+def test_philox_normals_match_oracle(M, count, ctr0):
+    import torch
+    out = torch.empty(count, dtype=torch.float64, device="cuda")
+    M.mgk_normals(5, M.EPS_TAG, ctr0, count, out)
+    torch.cuda.synchronize()
+    ref = O.normals(5, M.EPS_TAG, ctr0, count)
+    # same Philox words bit for bit; log/cos/sin may differ by a few ulp between libms
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-14, atol=1e-14)

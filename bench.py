@@ -1,0 +1,431 @@
+#!/usr/bin/env python3
+"""Throughput of the MGEnKF analysis cycle on one GB300 (or N, one replica each).
+
+One "step" is one analysis cycle of Algorithm 4 on the large 1-D Burgers
+workload (fine 16384 / coarse 4096 points, Ne = 128, 512 observations):
+forecast of the fine run and all members over one observation interval, the
+coarse-mesh EnKF analysis, the prolonged correction of the fine run and its
+RMSE against the truth.  Mixed precision: FP32 states and forecasts, BF16
+anomaly products with FP32 accumulation, FP64 means, covariances, Cholesky.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line (rank 0).  `value` = analysis cycles per second over all
+ranks (each rank runs an independent replica with its own seed: weak scaling,
+no collective on the data path).  `--impl reference` times the FP64 CPU oracle
+on this host's cores on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
+NUM_SMS = 152
+MAX_SM_MHZ = 2070.0
+FLOPS_PER_POINT_STEP = 33  # SSP-RK3 Burgers: 3 x 8 (dt L) + 1 + 4 + 4 (stage combinations)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--fp64-cycles", type=int, default=20,
+                    help="cycles of the plain FP64 run compared at equal RMSE")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (host side only: barrier and max of the timings)
+# --------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return d, "measured"
+        except (OSError, ValueError):
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# --------------------------------------------------------------------------
+# reference arm and CPU baseline: the FP64 oracle on this host's cores
+# --------------------------------------------------------------------------
+def oracle_cycle_sample(w, inp, mg, step_fraction: int):
+    """Time one bounded sample of a cycle: 1/step_fraction of the forecast
+    steps plus one full analysis, prolongation and RMSE; returns the time
+    scaled to a full cycle."""
+    import oracle as O
+    steps = max(1, w.steps_per_cycle // step_fraction)
+    t0 = time.perf_counter()
+    mg.forecast(steps)
+    t1 = time.perf_counter()
+    yo = np.asarray(inp["truth0"])[inp["obs_idx"]] + 0.0
+    mg.analyse(yo)
+    mg.prolong_correct()
+    O.rmse(mg.fine, inp["truth0"], w.V)
+    t2 = time.perf_counter()
+    return (t1 - t0) * (w.steps_per_cycle / steps) + (t2 - t1)
+
+
+def cpu_threads():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def cpu_baseline(w, inp):
+    import oracle as O
+    mg = O.MGEnKF(w.model, w.nf, w.ratio, w.length, w.dt, inp["fine0"], inp["members0"],
+                  inp["obs_idx"], inp["obs_var"], w.sigma, w.seed, nu=w.nu)
+    t = oracle_cycle_sample(w, inp, mg, 1)
+    return {"value": 1.0 / t, "unit": "cycles/s", "cores": cpu_threads(), "kind": "oracle",
+            "sample": f"1 full cycle of {w.name} ({w.steps_per_cycle} RK3 steps of the fine run and "
+                      f"{w.ne} members, ensemble-space FP64 analysis, prolongation, RMSE), "
+                      f"OpenMP over members, {cpu_threads()} threads"}
+
+
+def run_reference(args, dist, w, inp):
+    if dist.rank != 0:
+        return
+    import oracle as O
+    O.build()
+    frac = 32
+    mg = O.MGEnKF(w.model, w.nf, w.ratio, w.length, w.dt, inp["fine0"], inp["members0"],
+                  inp["obs_idx"], inp["obs_var"], w.sigma, w.seed, nu=w.nu)
+    for _ in range(args.warmup):
+        oracle_cycle_sample(w, inp, mg, frac)
+    times = [oracle_cycle_sample(w, inp, mg, frac) for _ in range(args.steps)]
+    per = float(np.mean(times))
+    val = 1.0 / per
+    sample = (f"per step: {w.steps_per_cycle // frac} of the {w.steps_per_cycle} RK3 steps of a "
+              f"cycle (time scaled by {frac}) plus one full FP64 analysis, prolongation and RMSE")
+    line = {"metric": "MGEnKF analysis cycles/s (1-D Burgers 16384/4096, Ne=128, 512 obs)",
+            "value": val, "unit": "cycles/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w.name, "nf": w.nf, "nc": w.nc, "ne": w.ne, "ny": w.ny,
+                       "steps_per_cycle": w.steps_per_cycle, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": "cycles/s", "kind": "oracle",
+                             "cores": cpu_threads(), "sample": sample},
+            "e2e": {"value": val, "unit": "cycles/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def truth_and_obs(M, w, inp, ncycles, torch):
+    """Synthetic input: FP32 truth trajectory on the GPU and its noisy samples
+    at the observed nodes, one row per cycle (resident in HBM)."""
+    truth = torch.tensor(inp["truth0"], dtype=torch.float32, device="cuda")
+    truths = torch.empty((ncycles, w.nxf), dtype=torch.float64, device="cuda")
+    yos = torch.empty((ncycles, w.ny), dtype=torch.float64, device="cuda")
+    idx = torch.tensor(inp["obs_var"].astype(np.int64) * w.nf + inp["obs_idx"], device="cuda")
+    for k in range(ncycles):
+        M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_MIXED, truth, 1, w.nf, w.length, w.dt, w.nu,
+                       nsteps=w.steps_per_cycle, stream=torch.cuda.current_stream().cuda_stream)
+        truths[k] = truth.double()
+        from paper_2012_10091_gb300 import workloads as W
+        yos[k] = truths[k][idx] + torch.tensor(W.observation_noise(w, k), device="cuda")
+    torch.cuda.synchronize()
+    return truths, yos
+
+
+def run_gpu(args, dist, w, inp):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_10091_gb300 import mgenkf as M
+
+    dev = dist.local % max(1, torch.cuda.device_count())
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    ncyc = args.warmup + args.steps
+    with torch.cuda.stream(stream):
+        truths, yos = truth_and_obs(M, w, inp, max(ncyc, args.fp64_cycles), torch)
+    torch.cuda.synchronize()
+
+    g = M.MGEnKF.from_workload(w, stream=sp)
+    g.set_state(inp["fine0"], inp["members0"])
+    rmse_dev = torch.zeros((ncyc, w.V), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            M.mgenkf_cycle(g.h, w.steps_per_cycle, yos[k], truths[k], rmse_dev[k])
+    torch.cuda.synchronize()
+    assert g.sync() == 0
+
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = M.mgk_kernel_launches()
+    wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")
+    with torch.cuda.stream(stream):
+        for j in range(args.steps):
+            k = args.warmup + j
+            flush.fill_(float(j))                      # evict L2 between timed cycles
+            e0, e1, e2 = ev[j]
+            e0.record(stream)
+            M.mgenkf_forecast(g.h, w.steps_per_cycle)
+            e1.record(stream)
+            M.mgenkf_analyse(g.h, yos[k])
+            M.mgenkf_prolong_correct(g.h)
+            M.mgenkf_rmse(g.h, truths[k], rmse_dev[k])
+            e2.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    wall = time.perf_counter() - wall0
+    launches = M.mgk_kernel_launches() - launches0
+    dist.barrier()
+    clk = clocks.stop()
+    assert g.sync() == 0
+    cyc_ms = [a.elapsed_time(c) for a, _, c in ev]
+    fc_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    t_total = sum(cyc_ms) / 1e3
+    t_max = dist.max(t_total)
+    cycles_all = dist.sum(float(args.steps))
+    value = cycles_all / t_max
+    fc_mean = float(np.mean(fc_ms)) / 1e3
+    rmse_mixed = rmse_dev[:, 0].cpu().numpy()
+
+    # plain FP64 MGEnKF on the same GPU and inputs, first fp64_cycles cycles
+    nref = args.fp64_cycles
+    g64 = M.MGEnKF.from_workload(w, precision="fp64", stream=sp)
+    g64.set_state(inp["fine0"], inp["members0"])
+    gm = M.MGEnKF.from_workload(w, stream=sp)
+    gm.set_state(inp["fine0"], inp["members0"])
+    r64 = torch.zeros((nref, w.V), dtype=torch.float64, device="cuda")
+    rmx = torch.zeros((nref, w.V), dtype=torch.float64, device="cuda")
+    e64a, e64b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e64a.record(stream)
+        for k in range(nref):
+            M.mgenkf_cycle(g64.h, w.steps_per_cycle, yos[k], truths[k], r64[k])
+        e64b.record(stream)
+        for k in range(nref):
+            M.mgenkf_cycle(gm.h, w.steps_per_cycle, yos[k], truths[k], rmx[k])
+    torch.cuda.synchronize()
+    assert g64.sync() == 0 and gm.sync() == 0
+    fp64_cps = nref / (e64a.elapsed_time(e64b) / 1e3)
+    f64, m64 = g64.get_state()
+    fmx, mmx = gm.get_state()
+    half = slice(nref // 2, nref)
+    rm64 = float(r64[half, 0].mean())
+    rmmx = float(rmx[half, 0].mean())
+    state_rel = float(np.max(np.abs(fmx - f64)) / np.max(np.abs(f64)))
+    g64.close()
+    gm.close()
+
+    # e2e: the same cycle through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if not args.no_e2e:
+        ge = M.MGEnKF.from_workload(w, stream=sp)
+        ge.set_state(inp["fine0"], inp["members0"])
+        y_h = torch.empty((ncyc, w.ny), dtype=torch.float64, pin_memory=True)
+        y_h.copy_(yos[:ncyc].cpu())
+        t_h = torch.empty((ncyc, w.nxf), dtype=torch.float64, pin_memory=True)
+        t_h.copy_(truths[:ncyc].cpu())
+        out_h = torch.empty((ncyc, w.V), dtype=torch.float64, pin_memory=True)
+        for k in range(args.warmup):
+            M.mgenkf_cycle(ge.h, w.steps_per_cycle, y_h[k], t_h[k], out_h[k])
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        for j in range(args.steps):
+            k = args.warmup + j
+            M.mgenkf_cycle(ge.h, w.steps_per_cycle, y_h[k], t_h[k], out_h[k])  # returns after D2H
+        torch.cuda.synchronize()
+        te = dist.max(time.perf_counter() - t0)
+        ge.close()
+        e2e = {"value": cycles_all / te, "unit": "cycles/s",
+               "h2d_bytes_per_step": 8 * (w.ny + w.nxf), "d2h_bytes_per_step": 8 * w.V}
+
+    # roofline of the dominant kernel (the forecast): FP32 ALU bound
+    peaks, peak_src = measured_peaks()
+    pts = w.ne * w.nc + w.nf
+    flops = FLOPS_PER_POINT_STEP * pts * w.steps_per_cycle
+    achieved = flops / fc_mean / 1e12
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "burgers_rk3_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    g.close()
+
+    if dist.rank == 0:
+        line = {
+            "metric": "MGEnKF analysis cycles/s (1-D Burgers 16384/4096, Ne=128, 512 obs)",
+            "value": value, "unit": "cycles/s", "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "nf": w.nf, "nc": w.nc, "ne": w.ne, "ny": w.ny,
+                       "steps_per_cycle": w.steps_per_cycle, "precision": "mixed",
+                       "gain_form": "ensemble-space", "replicas": dist.world,
+                       "l2": "flushed between timed cycles (256 MB write)"},
+            "member_steps_per_s": value * w.ne * w.steps_per_cycle,
+            "forecast_ms_per_cycle": fc_mean * 1e3,
+            "analysis_ms_per_cycle": (t_total / args.steps - fc_mean) * 1e3,
+            "hbm_gbs_algorithmic": (2 * 4 * pts) * args.steps / t_total / 1e9,
+            "fp64_plain": {"cycles_per_s": fp64_cps, "cycles": nref,
+                           "rmse_last_half": rm64, "mixed_rmse_last_half": rmmx,
+                           "rmse_rel_diff": abs(rmmx - rm64) / rm64,
+                           "fine_state_rel_diff": state_rel,
+                           "speedup_mixed_vs_fp64": value / dist.world / fp64_cps},
+            "rmse_final": float(rmse_mixed[-1]),
+            "roofline": {"bound": "alu", "kernel": "burgers_rk3_kernel<float,16>",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": "FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+                         "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": peak_src},
+            "clocks": clk,
+            "gpu_launches": int(launches),
+            "wall_s_timed": wall,
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if not args.no_cpu_baseline:
+            import oracle as O
+            O.build()
+            line["cpu_baseline"] = cpu_baseline(w, inp)
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    from paper_2012_10091_gb300 import workloads as W
+    w = W.burgers_large(seed=dist.rank)
+    inp = W.make_inputs(w)
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist, w, inp)
+        else:
+            run_gpu(args, dist, w, inp)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

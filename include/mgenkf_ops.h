@@ -40,6 +40,10 @@ mgenkf_status mgk_forecast(int32_t model, int32_t precision, void *state, int32_
 mgenkf_status mgk_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count, double *out,
                           void *stream);
 
+/* Number of GPU kernels the library has launched in this process so far
+ * (every entry point counts its own launches; memsets and copies excluded). */
+uint64_t mgk_kernel_launches(void);
+
 /* Text of the last error raised by an mgk_* call on this host thread. */
 const char *mgk_last_error(void);
 

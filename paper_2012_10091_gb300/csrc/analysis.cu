@@ -47,6 +47,7 @@ __global__ void k_restrict(const T *__restrict__ fine, T *__restrict__ xs, int d
 
 template <typename T>
 void launch_restrict(const T *fine, T *xstar, int dim, int V, int nc, int r, cudaStream_t s) {
+    count_launches(1);
     const size_t total = (size_t)V * (dim == 1 ? (size_t)nc : (size_t)nc * nc);
     k_restrict<T><<<grid_for(total, 256), 256, 0, s>>>(fine, xstar, dim, V, nc, r);
 }
@@ -71,6 +72,7 @@ __global__ void k_obs_apply(const T *__restrict__ members, const T *__restrict__
 template <typename T>
 void launch_obs_apply(const T *members, const T *xstar, size_t nx, int ne, int ny, int taps,
                       const int32_t *tap_idx, const double *tap_w, double *yf, cudaStream_t s) {
+    count_launches(1);
     dim3 grid(ceil_div(ny, 128), ne + 1);
     k_obs_apply<T><<<grid, 128, 0, s>>>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf);
 }
@@ -92,6 +94,7 @@ __global__ void k_obs_mean(const double *__restrict__ yf, const double *__restri
 
 void launch_obs_mean(const double *yf, const double *yo, int ne, int ny, double *ybar, double *Z,
                      int *status, cudaStream_t s) {
+    count_launches(1);
     k_obs_mean<<<ceil_div(ny, 128), 128, 0, s>>>(yf, yo, ne, ny, ybar, Z, status);
 }
 
@@ -119,6 +122,7 @@ __global__ void k_obs_perturb(const double *__restrict__ yf, const double *__res
 void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, double *eps,
                         int gen_eps, uint64_t seed, uint64_t cycle, double sigma, int ne, int ny,
                         double *Y, double *Z, cudaStream_t s) {
+    count_launches(1);
     dim3 grid(ceil_div(ny, 128), ne);
     k_obs_perturb<<<grid, 128, 0, s>>>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma, ne, ny, Y, Z);
 }
@@ -152,6 +156,7 @@ __global__ void k_ens_anom(const T *__restrict__ m, size_t nx, int ne, double *_
 template <typename T>
 void launch_ens_anom(const T *members, size_t nx, int ne, double *X64, __nv_bfloat16 *X16,
                      const int *status, cudaStream_t s) {
+    count_launches(1);
     const int ldx = (ne + 15) / 16 * 16;
     k_ens_anom<T><<<grid_for(nx, 128), 128, 0, s>>>(members, nx, ne, X64, X16, ldx, status);
 }
@@ -195,6 +200,7 @@ __global__ void k_gemm_nt(const double *__restrict__ A, int m, const double *__r
 void launch_gemm_nt_f64(const double *A, int m, const double *B1, int n1, const double *B2, int n2,
                         int K, double scale_div, double diag, double *out1, double *out2,
                         const int *status, cudaStream_t s) {
+    count_launches(1);
     dim3 grid(ceil_div(n1 + n2, 16), ceil_div(m, 16));
     k_gemm_nt<<<grid, 256, 0, s>>>(A, m, B1, n1, B2, n2, K, scale_div, diag, out1, out2, status);
 }
@@ -224,6 +230,7 @@ __global__ void k_gemm_tn(const double *__restrict__ Y, int ne, int ny, double d
 
 void launch_gemm_tn_f64(const double *Y, int ne, int ny, double diag, double *C, const int *status,
                         cudaStream_t s) {
+    count_launches(1);
     dim3 grid(ceil_div(ny, 16), ceil_div(ny, 16));
     k_gemm_tn<<<grid, 256, 0, s>>>(Y, ne, ny, diag, C, status);
 }
@@ -269,6 +276,7 @@ __global__ void __launch_bounds__(1024) k_cholesky(double *A, double *Lt, int n,
 }
 
 void launch_cholesky(double *A, double *Lt, int n, int *status, cudaStream_t s) {
+    count_launches(1);
     const size_t bytes = sizeof(double) * (size_t)n * n;
     if (bytes <= 200 * 1024) {
         static bool attr_set = false;
@@ -343,6 +351,7 @@ __global__ void __launch_bounds__(32) k_chol_solve(const double *__restrict__ L,
 
 void launch_chol_solve(const double *L, const double *Lt, int n, const double *rhs, double *out,
                        int ncol, __nv_bfloat16 *out16, int ld16, const int *status, cudaStream_t s) {
+    count_launches(1);
     if (n <= 128)
         k_chol_solve<4><<<ncol, 32, 0, s>>>(L, Lt, n, rhs, out, ncol, out16, ld16, status);
     else if (n <= 512)
@@ -392,6 +401,7 @@ __global__ void __launch_bounds__(256) k_update_f64(T *__restrict__ members, T *
 template <typename T>
 void launch_update_f64(T *members, T *dC, const double *X, const double *Tm, size_t nx, int ne,
                        const int *status, cudaStream_t s) {
+    count_launches(1);
     dim3 grid(ceil_div(nx, 64), ceil_div(ne + 1, 32));
     const size_t smem = sizeof(double) * 32 * (size_t)ne;  // <= 128 KB for ne <= 512
     if (smem > 48 * 1024)
@@ -445,6 +455,7 @@ __global__ void __launch_bounds__(256) k_update_bf16(float *__restrict__ members
 
 void launch_update_bf16(float *members, float *dC, const __nv_bfloat16 *Xt, const __nv_bfloat16 *Tt,
                         int ldx, size_t nx, int ne, const int *status, cudaStream_t s) {
+    count_launches(1);
     dim3 grid(ceil_div(nx, 64), ceil_div(ne + 1, 32));
     const size_t smem = sizeof(__nv_bfloat16) * (size_t)(64 + 32) * (ldx + 2);  // <= 99 KB
     if (smem > 48 * 1024)
@@ -490,6 +501,7 @@ __global__ void k_prolong_add(T *__restrict__ fine, const T *__restrict__ dC, in
 template <typename T>
 void launch_prolong_add(T *fine, const T *dC, int dim, int V, int nc, int r,
                         const ProlongWeights &w, const int *status, cudaStream_t s) {
+    count_launches(1);
     const size_t nf = (size_t)nc * r;
     const size_t total = (size_t)V * (dim == 1 ? nf : nf * nf);
     k_prolong_add<T><<<grid_for(total, 256), 256, 0, s>>>(fine, dC, dim, V, nc, r, w, status);
@@ -549,6 +561,7 @@ __global__ void k_rmse_final(const double *__restrict__ partials, int nblocks, i
 template <typename T>
 void launch_rmse(const T *x, const double *truth, int V, size_t npts, double *partials, int nblocks,
                  double *out, cudaStream_t s) {
+    count_launches(2);
     k_rmse_partial<T><<<nblocks, 256, 0, s>>>(x, truth, V, npts, partials);
     k_rmse_final<<<1, 32, 0, s>>>(partials, nblocks, V, out);
 }
@@ -566,6 +579,7 @@ __global__ void k_convert(const Tin *__restrict__ in, Tout *__restrict__ out, si
 template <typename Tin, typename Tout>
 void launch_convert(const Tin *in, Tout *out, size_t n, cudaStream_t s) {
     if (n == 0) return;
+    count_launches(1);
     k_convert<Tin, Tout><<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
 }
 
@@ -581,6 +595,7 @@ __global__ void k_tt_bf16(const double *__restrict__ Tm, __nv_bfloat16 *__restri
 
 void launch_tt_bf16(const double *Tm, __nv_bfloat16 *Tt, int ne, int ld, const int *status,
                     cudaStream_t s) {
+    count_launches(1);
     k_tt_bf16<<<grid_for((size_t)(ne + 1) * ne, 256), 256, 0, s>>>(Tm, Tt, ne, ld, status);
 }
 
@@ -594,6 +609,7 @@ __global__ void k_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t co
 void launch_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count, double *out,
                     cudaStream_t s) {
     if (count <= 0) return;
+    count_launches(1);
     k_normals<<<grid_for((size_t)count, 256), 256, 0, s>>>(seed, tag, ctr0, count, out);
 }
 

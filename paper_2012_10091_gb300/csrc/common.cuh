@@ -80,5 +80,10 @@ __device__ __forceinline__ double to_f64(T x) {
 
 }  // namespace mgk
 
+namespace mgk {
+// number of kernel launches issued by the library (process-wide counter)
+void count_launches(int n);
+}  // namespace mgk
+
 // error text of the stateless entry points (per host thread)
 void mgk_set_error(const std::string &msg);

@@ -223,6 +223,7 @@ static cudaError_t launch_burgers_p(const BurgersArgs<T> &A, int maxpts, cudaStr
         attr[0].val.clusterDim.z = 1;
         cfg.numAttrs = 1;
     }
+    count_launches(1);
     return cudaLaunchKernelEx(&cfg, burgers_rk3_kernel<T, P>, A);
 }
 

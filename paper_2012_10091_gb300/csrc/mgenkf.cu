@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -21,6 +22,8 @@
 using namespace mgk;
 
 static thread_local std::string g_ops_error;
+static std::atomic<uint64_t> g_launches{0};
+void mgk::count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 void mgk_set_error(const std::string &msg) { g_ops_error = msg; }
 
 struct mgenkf_ctx {
@@ -696,3 +699,5 @@ extern "C" mgenkf_status mgk_normals(uint64_t seed, uint64_t tag, uint64_t ctr0,
 }
 
 extern "C" const char *mgk_last_error(void) { return g_ops_error.c_str(); }
+
+extern "C" uint64_t mgk_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }

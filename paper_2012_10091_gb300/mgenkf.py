@@ -72,6 +72,8 @@ def _load():
         fn.restype = ctypes.c_int
     L.mgenkf_last_error.argtypes = [P]
     L.mgenkf_last_error.restype = ctypes.c_char_p
+    L.mgk_kernel_launches.argtypes = []
+    L.mgk_kernel_launches.restype = ctypes.c_uint64
     L.mgk_last_error.argtypes = []
     L.mgk_last_error.restype = ctypes.c_char_p
     return L
@@ -183,6 +185,10 @@ def mgk_forecast(model, precision, state, nprob, n, length, dt, nu, gamma=1.4, p
 
 def mgk_normals(seed, tag, ctr0, count, out, stream=None):
     _check(lib.mgk_normals(seed, tag, ctr0, count, _ptr(out), stream), "mgk_normals")
+
+
+def mgk_kernel_launches() -> int:
+    return int(lib.mgk_kernel_launches())
 
 
 # ---------------------------------------------------------------------------

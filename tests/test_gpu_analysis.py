@@ -76,13 +76,20 @@ def test_fp64_analysis_matches_oracle(M, nf, ratio, ne, npr, gain_form):
 def test_mixed_analysis_matches_oracle(M, nf, ratio, ne, npr):
     w = W.burgers_custom(nf, ratio, ne, npr, obs_kind="random", sigma=0.05, precision="mixed")
     r = _one_analysis(M, w, 0, "mixed", explicit_eps=True)
-    # BF16 anomalies and gain coefficients (8-bit mantissa) with FP32 accumulation:
-    # the increment X T carries ~2^-8 relative error; the states are FP32.
+    # BF16 anomalies X and gain coefficients T (8-bit significands, rounding
+    # 2^-9 each) with FP32 accumulation: the increment X T carries a relative
+    # error of a few 2^-8; tolerance 5 * 2^-8 = 2e-2 of the largest increment.
+    # The states themselves are FP32 (2^-24), so their error is that increment
+    # error plus FP32 rounding of the state.
+    tol = 2e-2
     inc, inc_ref = r["mem"] - r["m0"], r["m_ref"] - r["m0"]
-    assert rel_err(inc, inc_ref) < 2e-2
-    assert rel_err(r["fields"][M.MGENKF_FIELD_DC], r["dC_ref"]) < 2e-2
-    assert rel_err(r["mem"], r["m_ref"]) < 1e-3
-    assert rel_err(r["fine"], r["fine_ref"]) < 1e-3
+    assert rel_err(inc, inc_ref) < tol
+    assert rel_err(r["fields"][M.MGENKF_FIELD_DC], r["dC_ref"]) < tol
+    bound = tol * np.max(np.abs(inc_ref)) + 1e-6 * np.max(np.abs(r["m_ref"]))
+    assert np.max(np.abs(r["mem"] - r["m_ref"])) < bound
+    dfine = r["fine_ref"] - r["f0"]
+    bound_f = tol * np.max(np.abs(dfine)) + 1e-6 * np.max(np.abs(r["fine_ref"]))
+    assert np.max(np.abs(r["fine"] - r["fine_ref"])) < bound_f
 
 
 def test_explicit_perturbations_are_used(M):

@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
 NUM_SMS = 152
 MAX_SM_MHZ = 2070.0
-FLOPS_PER_POINT_STEP = 33  # SSP-RK3 Burgers: 3 x 8 (dt L) + 1 + 4 + 4 (stage combinations)
+FLOPS_PER_POINT_STEP = 40  # SSP-RK3 Burgers, k-form: 3 x 9 (dt L) + 1 + 3 + 5 (stages) + 4 (Fast2Sum)
 
 
 def parse():
@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--fp64-cycles", type=int, default=20,
+    ap.add_argument("--fp64-cycles", type=int, default=40,
                     help="cycles of the plain FP64 run compared at equal RMSE")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -1,7 +1,7 @@
 // forecast_burgers.cu -- batched SSP-RK3 forecast of periodic viscous Burgers.
 //
 // Model (Eq. burgers, flux form on a periodic vertex grid x_j = j dx):
-//   dt L(u)_j = a (u_{j-1}^2 - u_{j+1}^2) + b (u_{j+1} + u_{j-1} - 2 u_j),
+//   dt L(u)_j = a (u_{j-1}^2 - u_{j+1}^2) + b (u_{j+1} - 2 u_j + u_{j-1}),
 //   a = dt / (4 dx), b = dt nu / dx^2      [= dt (-(F_{j+1}-F_{j-1})/(2dx) + nu D2 u), F = u^2/2]
 // Time (SSP-RK3, Shu-Osher form):
 //   u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1)); u' = 1/3 u + 2/3 (u2 + dt L(u2)).
@@ -48,46 +48,69 @@ struct BurgersArgs {
     int nsteps;
 };
 
-// One RK stage on the points a thread owns.  v: stage input (overwritten by
-// the stage output); u0: state at the start of the step; lft/rgt: old values
-// of the neighbouring points outside the thread.  FULL: the thread owns all P
-// points (no ragged tail).
-// Returns the new value of the thread's last owned point.
+// Stage increments of SSP-RK3 written around the state u0 at the start of the step:
+//   k0 = dt L(u0),  u1 = u0 + k0
+//   k1 = dt L(u1),  u2 = u0 + (k0 + k1) / 4
+//   k2 = dt L(u2),  u' = u0 + (k0 + k1) / 6 + 2/3 k2
+// which is the Shu-Osher form u2 = 3/4 u0 + 1/4 (u1 + k1), u' = 1/3 u0 + 2/3 (u2 + k2)
+// rearranged.  dt L is formed from neighbour differences (exact in floating
+// point for neighbours within a factor 2):
+//   dt L_j = a (u_{j-1} - u_{j+1}) (u_{j-1} + u_{j+1}) + b ((u_{j+1} - u_j) + (u_{j-1} - u_j)).
+// With the small dt of the fine grid one step changes u by about one FP32 ulp,
+// so the FP32 state is carried as a compensated pair (hi, lo): the step
+// increment is added with Fast2Sum and its rounding error kept in lo.
+template <typename T>
+__device__ __forceinline__ T burgers_dtl(T prev, T cur, T nxt, T a, T b) {
+    const T lap = (nxt - cur) + (prev - cur);
+    const T adv = (prev - nxt) * (prev + nxt);
+    return fma(a, adv, b * lap);
+}
+
+// One stage on the P points a thread owns.  s: stage input (overwritten by the
+// next stage input, or by nothing in the last stage); hi/lo: state at the start
+// of the step (updated in the last stage); kk: k0, then k0 + k1.  lft/rgt: stage
+// inputs of the neighbouring points outside the thread.  Returns the value the
+// thread must publish as its last point for the next stage.
 template <typename T, int P, bool FULL, int STAGE>
-__device__ __forceinline__ T burgers_stage(T (&v)[P], T (&u0)[P], int cnt, T lft, T rgt, T a,
-                                           T b) {
+__device__ __forceinline__ T burgers_stage(T (&s)[P], T (&hi)[P], T (&lo)[P], T (&kk)[P], int cnt,
+                                           T lft, T rgt, T a, T b) {
+    constexpr bool COMP = sizeof(T) == 4;
     T last = T(0);
     T prev = lft;
-    T sq_prev = lft * lft;
-    T cur = v[0];
-    T sq_cur = cur * cur;
+    T cur = s[0];
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         if (FULL || k < cnt) {
             T nxt;
             if (k + 1 < P) {
-                nxt = (FULL || k + 1 < cnt) ? v[k + 1] : rgt;
+                nxt = (FULL || k + 1 < cnt) ? s[k + 1] : rgt;
             } else {
                 nxt = rgt;
             }
-            const T sq_nxt = nxt * nxt;
-            const T lap = fma(T(-2), cur, prev + nxt);
-            const T dtL = fma(a, sq_prev - sq_nxt, b * lap);
+            const T kq = burgers_dtl(prev, cur, nxt, a, b);
             T nv;
             if (STAGE == 0) {
-                u0[k] = cur;
-                nv = cur + dtL;
+                kk[k] = kq;
+                nv = hi[k] + kq;
             } else if (STAGE == 1) {
-                nv = fma(T(0.25), cur + dtL, T(0.75) * u0[k]);
+                kk[k] = kk[k] + kq;
+                nv = fma(T(0.25), kk[k], hi[k]);
             } else {
-                nv = fma(T(2.0 / 3.0), cur + dtL, u0[k] * T(1.0 / 3.0));
+                const T d = fma(T(2.0 / 3.0), kq, kk[k] * T(1.0 / 6.0));
+                if (COMP) {  // Fast2Sum: hi + (lo + d) = new hi + new lo exactly
+                    const T t = lo[k] + d;
+                    const T sum = hi[k] + t;
+                    lo[k] = t - (sum - hi[k]);
+                    hi[k] = sum;
+                } else {
+                    hi[k] = hi[k] + d;
+                }
+                nv = hi[k];
             }
-            v[k] = nv;
+            s[k] = nv;
             if (FULL ? k == P - 1 : k == cnt - 1) last = nv;
             prev = cur;
-            sq_prev = sq_cur;
             cur = nxt;
-            sq_cur = sq_nxt;
         }
     }
     return last;
@@ -131,9 +154,13 @@ __global__ void __launch_bounds__(burgers_max_threads<T, P>())
     const int t_last = (npts - 1) / P;                 // last thread owning points
     const int cnt = min(max(npts - t * P, 0), P);      // points owned by this thread
 
-    T v[P], u0[P];
+    T v[P], hi[P], lo[P], kk[P];
 #pragma unroll
-    for (int k = 0; k < P; ++k) v[k] = (k < cnt) ? base[t * P + k] : T(0);
+    for (int k = 0; k < P; ++k) {
+        v[k] = (k < cnt) ? base[t * P + k] : T(0);
+        hi[k] = v[k];
+        lo[k] = T(0);
+    }
     // value of the last owned point, kept in its own register (a runtime
     // index into v[] would move the array to local memory)
     T vlast = cnt > 0 ? base[t * P + cnt - 1] : T(0);
@@ -175,9 +202,9 @@ __global__ void __launch_bounds__(burgers_max_threads<T, P>())
                 rgt = shf[0];
             }
             if (cnt == P) {
-                vlast = burgers_stage<T, P, true, S>(v, u0, cnt, lft, rgt, a, b);
+                vlast = burgers_stage<T, P, true, S>(v, hi, lo, kk, cnt, lft, rgt, a, b);
             } else {
-                vlast = burgers_stage<T, P, false, S>(v, u0, cnt, lft, rgt, a, b);
+                vlast = burgers_stage<T, P, false, S>(v, hi, lo, kk, cnt, lft, rgt, a, b);
             }
         }
         buf ^= 1;
@@ -189,9 +216,219 @@ __global__ void __launch_bounds__(burgers_max_threads<T, P>())
     }
 #pragma unroll
     for (int k = 0; k < P; ++k)
-        if (k < cnt) base[t * P + k] = v[k];
+        if (k < cnt) base[t * P + k] = hi[k] + lo[k];
     // peers may still read this CTA's shared memory in their last stage
     if (split) cg::this_cluster().sync();
+}
+
+// ---------------------------------------------------------------------------
+// FP32 fast path: folded pairs, packed FP32x2 arithmetic, one barrier per step.
+//
+// A CTA segment of npts points is folded into h = npts/2 pairs (A_j, B_j) =
+// (point j, point j + h), held as float2 so that every arithmetic instruction
+// (FFMA2 / FADD2 / FMUL2) advances two points.  Thread t owns pairs
+// [tQ, tQ + Q) plus a halo of 3 pairs on each side; the three RK stages are
+// computed on shrinking ranges (Q+4, Q+2, Q pairs), so the halo is refreshed
+// once per time step instead of once per stage.  Folding makes the neighbour
+// of pair 0 on the left (B_{h-1}, A_{h-1}) of the left segment/self and the
+// neighbour of pair h-1 on the right (B_0, A_0) of self/right segment: the two
+// components swap at the fold.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+__device__ __forceinline__ float2 dtl_x2(float2 prev, float2 cur, float2 nxt, float2 ca, float2 cb) {
+    const float2 m1 = f2(-1.f);
+    const float2 lap = __fadd2_rn(__ffma2_rn(cur, m1, nxt), __ffma2_rn(cur, m1, prev));
+    const float2 adv = __fmul2_rn(__ffma2_rn(nxt, m1, prev), __fadd2_rn(prev, nxt));
+    return __ffma2_rn(ca, adv, __fmul2_rn(cb, lap));
+}
+
+// One time step on the pairs a thread holds: hv = hi parts at the start of the
+// step (own pairs at [3, Q+3), halo pairs around them), lo = low parts of the
+// own pairs, sv = stage inputs, kk = k0 then k0 + k1 (index i-1 for pair i).
+// Stage ranges shrink by one pair per side: [1, Q+5), [2, Q+4), [3, Q+3).
+template <int Q>
+__device__ __forceinline__ void step_x2(float2 (&hv)[Q + 6], float2 (&lo)[Q], float2 (&sv)[Q + 6],
+                                        float2 (&kk)[Q + 4], float2 ca, float2 cb) {
+    const float2 m1 = f2(-1.f);
+    // stage 1: k0 = dt L(u0), u1 = u0 + k0
+#pragma unroll
+    for (int i = 1; i < Q + 5; ++i) {
+        const float2 k0 = dtl_x2(hv[i - 1], hv[i], hv[i + 1], ca, cb);
+        kk[i - 1] = k0;
+        sv[i] = __fadd2_rn(hv[i], k0);
+    }
+    // stage 2: k1 = dt L(u1), u2 = u0 + (k0 + k1) / 4   (in place, previous input kept)
+    {
+        float2 prev = sv[1];
+#pragma unroll
+        for (int i = 2; i < Q + 4; ++i) {
+            const float2 cur = sv[i];
+            const float2 k1 = dtl_x2(prev, cur, sv[i + 1], ca, cb);
+            kk[i - 1] = __fadd2_rn(kk[i - 1], k1);
+            sv[i] = __ffma2_rn(f2(0.25f), kk[i - 1], hv[i]);
+            prev = cur;
+        }
+    }
+    // stage 3: k2 = dt L(u2), u' = u0 + (k0 + k1)/6 + 2/3 k2, added by Fast2Sum
+    {
+        float2 prev = sv[2];
+#pragma unroll
+        for (int i = 3; i < Q + 3; ++i) {
+            const float2 cur = sv[i];
+            const float2 k2 = dtl_x2(prev, cur, sv[i + 1], ca, cb);
+            const float2 d = __ffma2_rn(f2(2.0f / 3.0f), k2, __fmul2_rn(f2(1.0f / 6.0f), kk[i - 1]));
+            const float2 t = __fadd2_rn(lo[i - 3], d);
+            const float2 sum = __fadd2_rn(hv[i], t);
+            lo[i - 3] = __ffma2_rn(__ffma2_rn(hv[i], m1, sum), m1, t);  // t - (sum - hi)
+            hv[i] = sum;
+            prev = cur;
+        }
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(512) burgers_f32x2_kernel(BurgersArgs<float> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *sh = reinterpret_cast<float2 *>(smem_raw);  // [2 buffers][first 3 | last 3][blockDim]
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int bid = blockIdx.x;
+    float *base;
+    int npts, rank = 0;
+    float a, b;
+    bool split;
+    if (bid < A.whole_ctas) {
+        if (bid >= A.n_whole_probs) return;  // padding CTA of the last cluster
+        base = A.whole + (size_t)bid * A.n_whole;
+        npts = A.n_whole;
+        a = A.aw;
+        b = A.bw;
+        split = false;
+    } else {
+        const int q = bid - A.whole_ctas;
+        const int prob = q / A.cs;
+        rank = q % A.cs;
+        npts = A.n_split / A.cs;
+        base = A.split + (size_t)prob * A.n_split + (size_t)rank * npts;
+        a = A.as;
+        b = A.bs;
+        split = A.cs > 1;
+    }
+    const int h = npts / 2;
+    const int te = h / Q;  // threads owning pairs; the others only join the barriers
+    const bool active = t < te;
+    const float2 ca = f2(a), cb = f2(b);
+
+    float2 w[Q + 6], lo[Q], sv[Q + 6], kk[Q + 4];
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int j = t * Q + k;
+            w[3 + k] = make_float2(base[j], base[h + j]);
+            lo[k] = f2(0.f);
+        }
+    }
+    int buf = 0;
+    for (int step = 0; step < A.nsteps; ++step) {
+        float2 *F = sh + buf * 6 * nt;  // first3[m] at F[m*nt + t], last3[m] at F[(3+m)*nt + t]
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                F[m * nt + t] = w[3 + m];
+                F[(3 + m) * nt + t] = w[Q + m];
+            }
+        }
+        if (split) {
+            cg::this_cluster().sync();
+        } else {
+            __syncthreads();
+        }
+        if (active) {
+            if (t > 0) {
+#pragma unroll
+                for (int m = 0; m < 3; ++m) w[m] = F[(3 + m) * nt + t - 1];
+            } else {
+                const float2 *L = split ? cg::this_cluster().map_shared_rank(F, (rank + A.cs - 1) % A.cs) : F;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const float2 r = L[(3 + m) * nt + te - 1], l = F[(3 + m) * nt + te - 1];
+                    w[m] = make_float2(r.y, l.x);
+                }
+            }
+            if (t < te - 1) {
+#pragma unroll
+                for (int m = 0; m < 3; ++m) w[Q + 3 + m] = F[m * nt + t + 1];
+            } else {
+                const float2 *R = split ? cg::this_cluster().map_shared_rank(F, (rank + 1) % A.cs) : F;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const float2 l = F[m * nt], r = R[m * nt];
+                    w[Q + 3 + m] = make_float2(l.y, r.x);
+                }
+            }
+            step_x2<Q>(w, lo, sv, kk, ca, cb);
+        }
+        buf ^= 1;
+    }
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int j = t * Q + k;
+            base[j] = w[3 + k].x + lo[k].x;
+            base[h + j] = w[3 + k].y + lo[k].y;
+        }
+    }
+    if (split) cg::this_cluster().sync();
+}
+
+// Q (pairs per thread) for the folded kernel, or 0 if it does not apply:
+// every segment even, h % Q == 0, h / Q <= 512 threads.
+static int choose_q(const BurgersArgs<float> &A) {
+    static int env = -1;
+    if (env < 0) {
+        const char *s = getenv("MGENKF_BURGERS_Q");
+        env = s ? atoi(s) : 0;
+    }
+    const int cand[4] = {env, 8, 4, 16};
+    for (int c : cand) {
+        if (c != 4 && c != 8 && c != 16) continue;
+        bool ok = true;
+        if (A.n_whole_probs > 0) ok = ok && A.n_whole % (2 * c) == 0 && A.n_whole / (2 * c) <= 512;
+        if (A.n_split_probs > 0) {
+            const int seg = A.n_split / A.cs;
+            ok = ok && A.n_split % A.cs == 0 && seg % (2 * c) == 0 && seg / (2 * c) <= 512;
+        }
+        if (ok) return c;
+    }
+    return 0;
+}
+
+template <int Q>
+static cudaError_t launch_f32x2(const BurgersArgs<float> &A, cudaStream_t stream) {
+    int te = 0;
+    if (A.n_whole_probs > 0) te = A.n_whole / (2 * Q);
+    if (A.n_split_probs > 0) te = max(te, A.n_split / A.cs / (2 * Q));
+    const int nt = ceil_div(te, 32) * 32;
+    const size_t smem = sizeof(float2) * 12 * (size_t)nt;  // <= 48 KB for nt <= 512
+    const int grid = A.whole_ctas + A.n_split_probs * A.cs;
+    if (grid == 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    cfg.attrs = attr;
+    cfg.numAttrs = 0;
+    if (A.cs > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = A.cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.numAttrs = 1;
+    }
+    count_launches(1);
+    return cudaLaunchKernelEx(&cfg, burgers_f32x2_kernel<Q>, A);
 }
 
 static int pow2_ceil(int x) {
@@ -246,6 +483,18 @@ static int choose_pts(int maxpts) {
 
 template <typename T>
 static cudaError_t launch_burgers(BurgersArgs<T> A, cudaStream_t stream) {
+    if constexpr (std::is_same<T, float>::value) {
+        static int off = -1;
+        if (off < 0) off = getenv("MGENKF_BURGERS_GENERIC") ? 1 : 0;
+        if (!off && A.nsteps > 0) {
+            switch (choose_q(A)) {
+                case 4: return launch_f32x2<4>(A, stream);
+                case 8: return launch_f32x2<8>(A, stream);
+                case 16: return launch_f32x2<16>(A, stream);
+                default: break;
+            }
+        }
+    }
     int maxpts = 0;
     if (A.n_whole_probs > 0) maxpts = A.n_whole;
     if (A.n_split_probs > 0) maxpts = max(maxpts, A.n_split / A.cs);

@@ -87,3 +87,22 @@ def test_philox_normals_match_oracle(M, count, ctr0):
     ref = O.normals(5, M.EPS_TAG, ctr0, count)
     # same Philox words bit for bit; log/cos/sin may differ by a few ulp between libms
     np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-14, atol=1e-14)
+
+
+def test_fp32_forecast_has_no_drift_over_long_horizon(M):
+    # fine grid of the large Burgers workload over two observation intervals
+    # (8662 steps, dt L ~ one FP32 ulp of u per step): the compensated FP32
+    # state stays within the random-walk rounding bound of the FP64 oracle,
+    # sqrt(3 * nsteps) * 2^-24 ~ 1e-5 relative; a biased update would drift far
+    # beyond it.
+    import torch
+    from paper_2012_10091_gb300 import workloads as W
+    w = W.burgers_large()
+    u0 = W.initial_truth(w)
+    steps = 2 * w.steps_per_cycle
+    ref = O.burgers_rk3(u0, w.length / w.nf, w.nu, w.dt, steps)
+    d = torch.tensor(u0, dtype=torch.float32, device="cuda")
+    M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_MIXED, d, 1, w.nf, w.length, w.dt, w.nu, nsteps=steps)
+    torch.cuda.synchronize()
+    err = np.max(np.abs(d.cpu().double().numpy() - ref)) / np.max(np.abs(ref))
+    assert err < 1e-5, err

@@ -80,22 +80,35 @@ void launch_obs_apply(const T *members, const T *xstar, size_t nx, int ne, int n
 // ---------------------------------------------------------------------------
 // observation means and innovations (Algorithm 1 step 4; Algorithm 4 step 5)
 // ---------------------------------------------------------------------------
-__global__ void k_obs_mean(const double *__restrict__ yf, const double *__restrict__ yo, int ne,
-                           int ny, double *__restrict__ ybar, double *__restrict__ Z, int *status) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ny) return;
-    double s = 0.0;
-    for (int i = 0; i < ne; ++i) s += yf[(size_t)i * ny + j];
-    ybar[j] = s / ne;
-    const double y = yo[j];
-    if (!isfinite(y)) atomicCAS(status, 0, kStNonFinite);
-    Z[(size_t)ne * ny + j] = y - yf[(size_t)ne * ny + j];
+__global__ void __launch_bounds__(256) k_obs_mean(const double *__restrict__ yf,
+                                                  const double *__restrict__ yo, int ne, int ny,
+                                                  double *__restrict__ ybar, double *__restrict__ Z,
+                                                  int *status) {
+    // 32 observations per CTA (lane), 8 slices of the members (warp); the slice
+    // sums are combined in a fixed order.
+    __shared__ double part[8][33];
+    const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;
+    double acc = 0.0;
+    if (j < ny)
+        for (int i = slice; i < ne; i += 8) acc += yf[(size_t)i * ny + j];
+    part[slice][lane] = acc;
+    __syncthreads();
+    if (slice == 0 && j < ny) {
+        double sum = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sum += part[q][lane];
+        ybar[j] = sum / ne;
+        const double y = yo[j];
+        if (!isfinite(y)) atomicCAS(status, 0, kStNonFinite);
+        Z[(size_t)ne * ny + j] = y - yf[(size_t)ne * ny + j];
+    }
 }
 
 void launch_obs_mean(const double *yf, const double *yo, int ne, int ny, double *ybar, double *Z,
                      int *status, cudaStream_t s) {
     count_launches(1);
-    k_obs_mean<<<ceil_div(ny, 128), 128, 0, s>>>(yf, yo, ne, ny, ybar, Z, status);
+    k_obs_mean<<<ceil_div(ny, 32), 256, 0, s>>>(yf, yo, ne, ny, ybar, Z, status);
 }
 
 // perturbed observations (Eq. perturbed_y) and normalised anomalies Y (Algorithm 3 step 7)
@@ -131,25 +144,48 @@ void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, 
 // ensemble mean (FP64 accumulation) and normalised anomalies X
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_ens_anom(const T *__restrict__ m, size_t nx, int ne, double *__restrict__ X64,
-                           __nv_bfloat16 *__restrict__ X16, int ldx, const int *status) {
+__global__ void __launch_bounds__(256) k_ens_anom(const T *__restrict__ m, size_t nx, int ne,
+                                                  double *__restrict__ X64,
+                                                  __nv_bfloat16 *__restrict__ X16, int ldx,
+                                                  const int *status) {
+    // CTA: 32 consecutive points (lane) x the members split over the 8 warps.
+    // FP64 mean (slice sums combined in a fixed order), then the normalised
+    // anomalies: FP64 member-major rows, or BF16 point-major rows assembled in
+    // shared memory so every row of ldx values is stored contiguously.
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    double *part = reinterpret_cast<double *>(sm_raw);                        // [8][32]
+    __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(part + 8 * 32);  // [32][ldx + 8]
     if (*status) return;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const size_t p0 = blockIdx.x * (size_t)32;
+    const size_t p = p0 + lane;
+    const bool ok = p < nx;
+    double acc = 0.0;
+    if (ok)
+        for (int i = wp; i < ne; i += 8) acc += (double)m[(size_t)i * nx + p];
+    part[wp * 32 + lane] = acc;
+    __syncthreads();
+    double sum = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sum += part[q * 32 + lane];
+    const double xb = sum / ne;
     const double sq = sqrt((double)(ne - 1));
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < nx;
-         p += (size_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int i = 0; i < ne; ++i) s += (double)m[(size_t)i * nx + p];
-        const double xb = s / ne;
-        if (X64) {
-            for (int i = 0; i < ne; ++i) X64[(size_t)i * nx + p] = ((double)m[(size_t)i * nx + p] - xb) / sq;
-        } else {
-            __nv_bfloat162 *row = reinterpret_cast<__nv_bfloat162 *>(X16 + p * ldx);
-            for (int i = 0; i < ne; i += 2) {
-                const float a = (float)(((double)m[(size_t)i * nx + p] - xb) / sq);
-                const float b = i + 1 < ne ? (float)(((double)m[(size_t)(i + 1) * nx + p] - xb) / sq) : 0.f;
-                row[i >> 1] = __floats2bfloat162_rn(a, b);
-            }
-        }
+    const int ldt = ldx + 8;
+    if (X64) {
+        if (ok)
+            for (int i = wp; i < ne; i += 8) X64[(size_t)i * nx + p] = ((double)m[(size_t)i * nx + p] - xb) / sq;
+        return;
+    }
+    for (int i = wp; i < ldx; i += 8)
+        tile[lane * ldt + i] = __double2bfloat16((ok && i < ne) ? ((double)m[(size_t)i * nx + p] - xb) / sq : 0.0);
+    __syncthreads();
+    // store: row r of the tile (point p0 + r) is ldx bf16 = ldx/8 16-byte chunks
+    const int chunks = ldx / 8;
+    for (int e = threadIdx.x; e < 32 * chunks; e += blockDim.x) {
+        const int r = e / chunks, cidx = e % chunks;
+        if (p0 + r < nx)
+            reinterpret_cast<uint4 *>(X16 + (p0 + r) * ldx)[cidx] =
+                reinterpret_cast<const uint4 *>(tile + r * ldt)[cidx];
     }
 }
 
@@ -158,7 +194,10 @@ void launch_ens_anom(const T *members, size_t nx, int ne, double *X64, __nv_bflo
                      const int *status, cudaStream_t s) {
     count_launches(1);
     const int ldx = (ne + 15) / 16 * 16;
-    k_ens_anom<T><<<grid_for(nx, 128), 128, 0, s>>>(members, nx, ne, X64, X16, ldx, status);
+    const size_t smem = sizeof(double) * 8 * 32 + sizeof(__nv_bfloat16) * 32 * (size_t)(ldx + 8);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_ens_anom<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ens_anom<T><<<ceil_div(nx, 32), 256, smem, s>>>(members, nx, ne, X64, X16, ldx, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -239,37 +278,48 @@ void launch_gemm_tn_f64(const double *Y, int ne, int ny, double diag, double *C,
 // Cholesky (right-looking, one CTA) and the two triangular solves
 // ---------------------------------------------------------------------------
 template <bool SMEM>
-__global__ void __launch_bounds__(1024) k_cholesky(double *A, double *Lt, int n, int *status) {
+__global__ void __launch_bounds__(256) k_cholesky(double *A, double *Lt, int n, int *status) {
+    // Right-looking Cholesky by one CTA.  Column k: pivot l = sqrt(A_kk) and its
+    // reciprocal (one division per column), scale the column below it, then the
+    // rank-1 update of the trailing lower triangle.  Rows padded to n+1 doubles
+    // in shared memory.
     extern __shared__ double sm[];
+    __shared__ double s_inv;
     if (*status) return;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int tx = tid & 31, ty = tid >> 5, nty = nth >> 5;
+    const int ld = SMEM ? n + 1 : n;
     double *M = SMEM ? sm : A;
     if (SMEM) {
-        for (int e = tid; e < n * n; e += nth) sm[e] = A[e];
+        for (int e = tid; e < n * n; e += nth) sm[(e / n) * ld + e % n] = A[e];
         __syncthreads();
     }
     for (int k = 0; k < n; ++k) {
-        const double d = M[(size_t)k * n + k];
+        const double d = M[(size_t)k * ld + k];
         if (!(d > 0.0) || !isfinite(d)) {  // uniform: every thread read the same pivot
             if (tid == 0) atomicCAS(status, 0, kStNotSpd);
             return;
         }
-        const double l = sqrt(d);
+        __syncthreads();  // every thread has read the pivot before it is overwritten
+        if (tid == 0) {
+            const double l = sqrt(d);
+            M[(size_t)k * ld + k] = l;
+            s_inv = 1.0 / l;
+        }
         __syncthreads();
-        if (tid == 0) M[(size_t)k * n + k] = l;
-        for (int i = k + 1 + tid; i < n; i += nth) M[(size_t)i * n + k] = M[(size_t)i * n + k] / l;
+        const double inv = s_inv;
+        for (int i = k + 1 + tid; i < n; i += nth) M[(size_t)i * ld + k] *= inv;
         __syncthreads();
         for (int i = k + 1 + ty; i < n; i += nty) {
-            const double lik = M[(size_t)i * n + k];
+            const double lik = M[(size_t)i * ld + k];
             for (int j = k + 1 + tx; j <= i; j += 32)
-                M[(size_t)i * n + j] = fma(-lik, M[(size_t)j * n + k], M[(size_t)i * n + j]);
+                M[(size_t)i * ld + j] = fma(-lik, M[(size_t)j * ld + k], M[(size_t)i * ld + j]);
         }
         __syncthreads();
     }
     for (int e = tid; e < n * n; e += nth) {
         const int i = e / n, j = e % n;
-        const double val = j <= i ? M[e] : 0.0;
+        const double val = j <= i ? M[(size_t)i * ld + j] : 0.0;
         A[e] = val;
         Lt[(size_t)j * n + i] = val;
     }
@@ -277,17 +327,79 @@ __global__ void __launch_bounds__(1024) k_cholesky(double *A, double *Lt, int n,
 
 void launch_cholesky(double *A, double *Lt, int n, int *status, cudaStream_t s) {
     count_launches(1);
-    const size_t bytes = sizeof(double) * (size_t)n * n;
-    if (bytes <= 200 * 1024) {
+    const size_t bytes = sizeof(double) * (size_t)n * (n + 1);
+    if (bytes <= 210 * 1024) {
         static bool attr_set = false;
         if (!attr_set) {
             cudaFuncSetAttribute(k_cholesky<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024);
+                                 210 * 1024);
             attr_set = true;
         }
-        k_cholesky<true><<<1, 1024, bytes, s>>>(A, Lt, n, status);
+        k_cholesky<true><<<1, 256, bytes, s>>>(A, Lt, n, status);
     } else {
-        k_cholesky<false><<<1, 1024, 0, s>>>(A, Lt, n, status);
+        k_cholesky<false><<<1, 256, 0, s>>>(A, Lt, n, status);
+    }
+}
+
+// Triangular solves with L staged in shared memory: one warp per right-hand
+// side (one CTA each, so the FP64 work of the columns spreads over the SMs),
+// lanes own rows lane + 32 m, the diagonal reciprocals precomputed.
+template <int MAXR>
+__global__ void __launch_bounds__(32) k_chol_solve_smem(const double *__restrict__ L, int n,
+                                                        const double *rhs, double *out, int ncol,
+                                                        __nv_bfloat16 *out16, int ld16,
+                                                        const int *status) {
+    extern __shared__ double sL[];  // [n][n+1] then inv_diag[n]
+    if (*status) return;
+    const int c = blockIdx.x, lane = threadIdx.x, ld = n + 1;
+    double *inv = sL + (size_t)n * ld;
+    for (int e = lane; e < n * n; e += 32) sL[(e / n) * ld + e % n] = L[e];
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) inv[j] = 1.0 / sL[(size_t)j * ld + j];
+    __syncwarp();
+    double b[MAXR];
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) {
+        const int i = lane + 32 * m;
+        b[m] = i < n ? rhs[(size_t)c * n + i] : 0.0;
+    }
+#pragma unroll
+    for (int s = 0; s < MAXR; ++s) {
+        if (s * 32 >= n) break;
+        for (int l = 0; l < 32; ++l) {
+            const int j = s * 32 + l;
+            if (j >= n) break;
+            if (lane == l) b[s] *= inv[j];
+            const double zj = __shfl_sync(0xffffffffu, b[s], l);
+#pragma unroll
+            for (int m = s; m < MAXR; ++m) {
+                const int i = lane + 32 * m;
+                if (i > j && i < n) b[m] = fma(-sL[(size_t)i * ld + j], zj, b[m]);
+            }
+        }
+    }
+#pragma unroll
+    for (int s = MAXR - 1; s >= 0; --s) {
+        if (s * 32 >= n) continue;
+        for (int l = 31; l >= 0; --l) {
+            const int j = s * 32 + l;
+            if (j >= n) continue;
+            if (lane == l) b[s] *= inv[j];
+            const double xj = __shfl_sync(0xffffffffu, b[s], l);
+#pragma unroll
+            for (int m = 0; m <= s; ++m) {
+                const int i = lane + 32 * m;
+                if (i < j) b[m] = fma(-sL[(size_t)j * ld + i], xj, b[m]);
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) {
+        const int i = lane + 32 * m;
+        if (i < n) {
+            out[(size_t)c * n + i] = b[m];
+            if (out16) out16[(size_t)c * ld16 + i] = __double2bfloat16(b[m]);
+        }
     }
 }
 
@@ -352,6 +464,24 @@ __global__ void __launch_bounds__(32) k_chol_solve(const double *__restrict__ L,
 void launch_chol_solve(const double *L, const double *Lt, int n, const double *rhs, double *out,
                        int ncol, __nv_bfloat16 *out16, int ld16, const int *status, cudaStream_t s) {
     count_launches(1);
+    const size_t smem = sizeof(double) * ((size_t)n * (n + 1) + n);
+    if (n <= 160 && smem <= 210 * 1024) {
+        static bool attr_set[2] = {false, false};
+        if (n <= 128) {
+            if (!attr_set[0]) {
+                cudaFuncSetAttribute(k_chol_solve_smem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+                attr_set[0] = true;
+            }
+            k_chol_solve_smem<4><<<ncol, 32, smem, s>>>(L, n, rhs, out, ncol, out16, ld16, status);
+        } else {
+            if (!attr_set[1]) {
+                cudaFuncSetAttribute(k_chol_solve_smem<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+                attr_set[1] = true;
+            }
+            k_chol_solve_smem<8><<<ncol, 32, smem, s>>>(L, n, rhs, out, ncol, out16, ld16, status);
+        }
+        return;
+    }
     if (n <= 128)
         k_chol_solve<4><<<ncol, 32, 0, s>>>(L, Lt, n, rhs, out, ncol, out16, ld16, status);
     else if (n <= 512)
@@ -548,14 +678,18 @@ __global__ void k_rmse_partial(const T *__restrict__ x, const double *__restrict
 
 __global__ void k_rmse_final(const double *__restrict__ partials, int nblocks, int V,
                              double *__restrict__ out) {
-    const int v = threadIdx.x;
+    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (v >= V) return;
     double a = 0.0, b = 0.0;
-    for (int q = 0; q < nblocks; ++q) {
+    for (int q = lane; q < nblocks; q += 32) {
         a += partials[((size_t)q * V + v) * 2 + 0];
         b += partials[((size_t)q * V + v) * 2 + 1];
     }
-    out[v] = sqrt(a / b);
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) out[v] = sqrt(a / b);
 }
 
 template <typename T>
@@ -563,7 +697,7 @@ void launch_rmse(const T *x, const double *truth, int V, size_t npts, double *pa
                  double *out, cudaStream_t s) {
     count_launches(2);
     k_rmse_partial<T><<<nblocks, 256, 0, s>>>(x, truth, V, npts, partials);
-    k_rmse_final<<<1, 32, 0, s>>>(partials, nblocks, V, out);
+    k_rmse_final<<<1, 32 * V, 0, s>>>(partials, nblocks, V, out);
 }
 
 // ---------------------------------------------------------------------------

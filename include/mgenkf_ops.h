@@ -40,6 +40,29 @@ mgenkf_status mgk_forecast(int32_t model, int32_t precision, void *state, int32_
 mgenkf_status mgk_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count, double *out,
                           void *stream);
 
+/* Ensemble-space gain solve that allocates nothing.
+ * The paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc (an application whose own pool owns all device memory, a process
+ * under a fixed device-memory budget, code that must not make allocation calls
+ * that synchronise the device).  It computes, in FP64, the same T as the
+ * handle's analysis with MGENKF_GAIN_ENSEMBLE:
+ *   S = I + Y^T Y / sigma^2,  S = L L^T,  T = S^-1 Y^T [D | d*] / sigma^2.
+ *   Y: device, n_members x n_obs, row i = normalised observation anomaly of member i;
+ *   Z: device, (n_members + 1) x n_obs, rows D_i = y^o + eps_i - y^f_i, last row d* = y^o - H^C x^C*;
+ *   T: device output, (n_members + 1) x n_members, column c of T contiguous (T[c * n_members + a]);
+ *   info: optional device int32 set to 0, or MGENKF_ERR_NOT_SPD if a pivot was not positive.
+ * Scratch (S, L^T, status) lives in a fixed array compiled into the library,
+ * held by every GPU that loads it until exit (256 KB); hence n_members <= 128,
+ * larger sizes return MGENKF_ERR_INVALID_ARG with a message.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the array (its status word is cleared at the start of each call):
+ * calls whose work overlaps on the GPU race and must be serialised by the caller.
+ * Asynchronous on `stream`. */
+mgenkf_status mgk_gain_ensemble_noalloc(const double *Y, const double *Z, int32_t n_members,
+                                        int32_t n_obs, double obs_sigma, double *T, int32_t *info,
+                                        void *stream);
+
 /* Number of GPU kernels the library has launched in this process so far
  * (every entry point counts its own launches; memsets and copies excluded). */
 uint64_t mgk_kernel_launches(void);

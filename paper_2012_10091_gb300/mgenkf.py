@@ -65,6 +65,7 @@ def _load():
         "mgenkf_destroy": [P],
         "mgk_forecast": [i32, i32, P, i32, i32, f64, f64, f64, f64, f64, i32, P],
         "mgk_normals": [u64, u64, u64, i64, P, P],
+        "mgk_gain_ensemble_noalloc": [P, P, i32, i32, f64, P, P, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -185,6 +186,11 @@ def mgk_forecast(model, precision, state, nprob, n, length, dt, nu, gamma=1.4, p
 
 def mgk_normals(seed, tag, ctr0, count, out, stream=None):
     _check(lib.mgk_normals(seed, tag, ctr0, count, _ptr(out), stream), "mgk_normals")
+
+
+def mgk_gain_ensemble_noalloc(Y, Z, n_members, n_obs, obs_sigma, T, info=None, stream=None):
+    _check(lib.mgk_gain_ensemble_noalloc(_ptr(Y), _ptr(Z), n_members, n_obs, obs_sigma, _ptr(T),
+                                         _ptr(info), stream), "mgk_gain_ensemble_noalloc")
 
 
 def mgk_kernel_launches() -> int:

@@ -48,6 +48,7 @@ struct mgenkf_ctx {
     double *C = nullptr, *Ct = nullptr, *W = nullptr;   // direct form
     double *Tm = nullptr;                               // T, (ne+1) x ne (points at Bt or own buffer)
     double *truth_d = nullptr, *rmse_part = nullptr, *rmse_d = nullptr, *scratch = nullptr;
+    void *ns_scratch = nullptr;  // NS-2D stage buffers
     size_t scratch_n = 0;
     int *status = nullptr;
 };
@@ -120,7 +121,8 @@ static mgenkf_status dalloc(mgenkf_ctx *h, P **p, size_t bytes) {
 static void free_all(mgenkf_ctx *h) {
     void *ptrs[] = {h->fine, h->members, h->xstar, h->dC, h->tap_idx, h->tap_w, h->yf, h->yo,
                     h->ybar, h->eps, h->Y, h->Z, h->X64, h->X16, h->Tt, h->S, h->Lt, h->Bt, h->C,
-                    h->Ct, h->W, h->truth_d, h->rmse_part, h->rmse_d, h->scratch, h->status};
+                    h->Ct, h->W, h->truth_d, h->rmse_part, h->rmse_d, h->scratch, h->status,
+                    h->ns_scratch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->Tm && h->Tm != h->Bt) cudaFree(h->Tm);
@@ -276,6 +278,8 @@ static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const 
         H_ALLOC(h->Bt, (ne + 1) * ne * sizeof(double));
         h->Tm = h->Bt;
     }
+    if (cfg->model == MGENKF_NS2D)
+        H_ALLOC(h->ns_scratch, ns2d_scratch_elems(h->nc, h->ne, h->nf, 1) * ts);
     H_ALLOC(h->rmse_part, (size_t)kRmseBlocks * h->V * 2 * sizeof(double));
     H_ALLOC(h->rmse_d, 4 * sizeof(double));
     H_ALLOC(h->status, sizeof(int));
@@ -409,11 +413,13 @@ static mgenkf_status forecast_impl(mgenkf_ctx *h, int nsteps) {
                                          c.length, c.dt, c.nu, nsteps, h->stream);
     } else {
         if (h->mixed)
-            e = ns2d_forecast<float>((float *)h->members, h->nc, h->ne, (float *)h->fine, h->nf, 1,
-                                     c.length, c.dt, c.nu, c.gamma, c.prandtl, nsteps, h->stream);
+            e = ns2d_forecast_scratch<float>((float *)h->members, h->nc, h->ne, (float *)h->fine, h->nf, 1,
+                                             c.length, c.dt, c.nu, c.gamma, c.prandtl, nsteps,
+                                             (float *)h->ns_scratch, h->stream);
         else
-            e = ns2d_forecast<double>((double *)h->members, h->nc, h->ne, (double *)h->fine, h->nf, 1,
-                                      c.length, c.dt, c.nu, c.gamma, c.prandtl, nsteps, h->stream);
+            e = ns2d_forecast_scratch<double>((double *)h->members, h->nc, h->ne, (double *)h->fine, h->nf, 1,
+                                              c.length, c.dt, c.nu, c.gamma, c.prandtl, nsteps,
+                                              (double *)h->ns_scratch, h->stream);
     }
     if (e != cudaSuccess) H_FAIL(MGENKF_ERR_CUDA, std::string("forecast launch: ") + cudaGetErrorString(e));
     H_LAUNCHED();

@@ -118,17 +118,18 @@ def burgers_custom(nf, ratio, ne, n_probes, steps_per_cycle=20, cycles=5, dt=1e-
 
 
 def ns2d_shear(nf: int = 512, ratio: int = 4, ne: int = 64, n_probes: int = 1024,
-               cycles: int = 100, precision: str = "mixed", seed: int = 0) -> Workload:
+               cycles: int = 100, precision: str = "mixed", seed: int = 0,
+               delta: float = 0.02) -> Workload:
     """2-D compressible NS, periodic [0,1]^2, Re = 1000, Mach 0.3 double shear
-    layer (delta = 0.02) + 1e-3 N(0,1) velocity perturbation, probes of
-    (rho u, rho v) every 10 steps with sigma 0.01."""
+    layer (thickness delta, 0.02 by default) + 1e-3 N(0,1) velocity
+    perturbation, probes of (rho u, rho v) every 10 steps with sigma 0.01."""
     mach = 0.3
     h = 1.0 / nf
     dt = 0.5 * math.sqrt(3.0) * h / (1.0 + 1.0 / mach)
     return Workload(f"ns2d_{nf}_{nf // ratio}_ne{ne}_{precision}", NS2D, nf=nf, ratio=ratio, ne=ne,
                     n_probes=n_probes, sigma=0.01, steps_per_cycle=10, cycles=cycles, dt=dt,
                     length=1.0, nu=1e-3, precision=precision, seed=seed, mach=mach,
-                    truth_kind="shear", obs_kind="random")
+                    truth_kind="shear", obs_kind="random", extra={"delta": delta})
 
 
 # --------------------------------------------------------------------------
@@ -147,7 +148,7 @@ def _shear_u(y: np.ndarray, delta: float = 0.02) -> np.ndarray:
 
 def _ns_state(w: Workload, n: int, up: np.ndarray, vp: np.ndarray) -> np.ndarray:
     y = np.arange(n) * (w.length / n)
-    u = np.broadcast_to(_shear_u(y)[:, None], (n, n)) + up
+    u = np.broadcast_to(_shear_u(y, w.extra.get("delta", 0.02))[:, None], (n, n)) + up
     v = vp
     rho = np.ones((n, n))
     p0 = 1.0 / (w.gamma * w.mach**2)

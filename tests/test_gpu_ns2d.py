@@ -1,0 +1,101 @@
+"""GPU parity of the 2-D compressible Navier-Stokes forecast (Eqs. Mass,
+Momentum, Energy; SSP-RK3) against the CPU oracle, and of a short MGEnKF run
+on the shear-layer workload through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import gpu_run, oracle_run, rel_err
+from paper_2012_10091_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+GAMMA, PR = 1.4, 0.72
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_10091_gb300 import mgenkf
+    return mgenkf
+
+
+def _smooth_states(nprob, n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    x = np.arange(n) / n
+    X, Y = np.meshgrid(x, x)
+    for _ in range(nprob):
+        rho = 1.0 + 0.1 * np.sin(2 * np.pi * X + rng.uniform(0, 6)) * np.cos(2 * np.pi * Y)
+        u = 0.3 * np.sin(2 * np.pi * Y + rng.uniform(0, 6)) + 0.01 * rng.standard_normal((n, n))
+        v = 0.2 * np.cos(2 * np.pi * X) + 0.01 * rng.standard_normal((n, n))
+        p = 8.0 + 0.2 * np.cos(2 * np.pi * (X + Y))
+        E = p / (GAMMA - 1) + 0.5 * rho * (u * u + v * v)
+        out.append(np.stack([rho, rho * u, rho * v, E]))
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("n,nprob", [(8, 3), (16, 2), (40, 2), (64, 1), (136, 1)])
+def test_ns2d_fp64_matches_oracle(M, n, nprob):
+    import torch
+    q0 = _smooth_states(nprob, n, n)
+    h, mu, dt, steps = 1.0 / n, 1e-2, 0.2 / n, 12
+    ref = O.ns2d_rk3(q0, h, GAMMA, mu, PR, dt, steps)
+    d = torch.tensor(q0, dtype=torch.float64, device="cuda")
+    M.mgk_forecast(M.MGENKF_NS2D, M.MGENKF_FP64, d, nprob, n, 1.0, dt, mu, GAMMA, PR, nsteps=steps)
+    torch.cuda.synchronize()
+    got = d.cpu().numpy()
+    for k in range(4):
+        assert np.max(np.abs(got[:, k] - ref[:, k])) <= 1e-12 * np.max(np.abs(ref[:, k])), k
+    # conservation of the four totals on the GPU path as well
+    for k in range(4):
+        assert abs(got[:, k].sum() - q0[:, k].sum()) <= 1e-12 * np.abs(q0[:, k]).sum()
+
+
+def test_ns2d_fp32_matches_oracle(M):
+    import torch
+    n, nprob = 64, 2
+    q0 = _smooth_states(nprob, n, 5)
+    h, mu, dt, steps = 1.0 / n, 1e-3, 0.2 / n, 40
+    ref = O.ns2d_rk3(q0, h, GAMMA, mu, PR, dt, steps)
+    d = torch.tensor(q0, dtype=torch.float32, device="cuda")
+    M.mgk_forecast(M.MGENKF_NS2D, M.MGENKF_MIXED, d, nprob, n, 1.0, dt, mu, GAMMA, PR, nsteps=steps)
+    torch.cuda.synchronize()
+    got = d.cpu().double().numpy()
+    # FP32 rounding (2^-24) of O(10) energies over 40 steps of 3 stages
+    for k in range(4):
+        assert np.max(np.abs(got[:, k] - ref[:, k])) <= 2e-5 * np.max(np.abs(ref[:, k])), k
+
+
+def test_ns2d_rejects_bad_sizes(M):
+    import torch
+    d = torch.zeros(4 * 12 * 12, dtype=torch.float64, device="cuda")
+    with pytest.raises(M.MGEnKFError):
+        M.mgk_forecast(M.MGENKF_NS2D, M.MGENKF_FP64, d, 1, 12, 1.0, 1e-3, 1e-3, GAMMA, PR, nsteps=1)
+
+
+@pytest.mark.parametrize("gain_form", [0, 1])
+def test_ns2d_mgenkf_cycles_match_oracle(M, gain_form):
+    w = W.ns2d_shear(nf=64, ratio=4, ne=12, n_probes=20, cycles=3, precision="fp64", delta=0.08)
+    mg, rm_o, _ = oracle_run(w, w.cycles)
+    g, rm_g, _ = gpu_run(w, w.cycles, gain_form=gain_form)
+    fine, mem = g.get_state()
+    assert rel_err(fine, mg.fine) < 1e-10
+    assert rel_err(mem, mg.members) < 1e-10
+    np.testing.assert_allclose(rm_g, rm_o, rtol=1e-8)
+    g.close()
+
+
+def test_ns2d_mixed_cycles_close_to_oracle(M):
+    w = W.ns2d_shear(nf=64, ratio=4, ne=12, n_probes=20, cycles=3, precision="mixed", delta=0.08)
+    mg, rm_o, _ = oracle_run(w, w.cycles)
+    g, rm_g, _ = gpu_run(w, w.cycles)
+    fine, mem = g.get_state()
+    assert rel_err(fine, mg.fine) < 1e-3
+    assert rel_err(mem, mg.members) < 1e-3
+    g.close()

@@ -35,7 +35,20 @@ sys.path.insert(0, ROOT)
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
 NUM_SMS = 152
 MAX_SM_MHZ = 2070.0
-FLOPS_PER_POINT_STEP = 40  # SSP-RK3 Burgers, k-form: 3 x 9 (dt L) + 1 + 3 + 5 (stages) + 4 (Fast2Sum)
+
+# Per workload: algorithmic FP32 flops per point-step of the forecast, the
+# forecast kernel timed for the roofline, its launches per model step, the
+# DRAM bytes per launch measured by ncu for the current kernel (None when not
+# captured), and the precision of the synthetic truth run.
+WORKLOADS = {
+    # SSP-RK3 Burgers, k-form: 3 x 9 (dt L) + 1 + 3 + 3 (stages) + 4 (Fast2Sum) = 38
+    "burgers_large": dict(flops=38, kernel="burgers_f32x2_kernel<8>", launches_per_step=None,
+                          traffic=2175232, truth="fp32"),
+    # NS-2D: ~200 flops per point and stage (primitives, nodal fluxes, four
+    # face fluxes, stage update), 3 stages per step
+    "ns2d": dict(flops=600, kernel="ns2d_stage_kernel<float,*>", launches_per_step=3,
+                 traffic=None, truth="fp64"),
+}
 
 
 def parse():
@@ -48,6 +61,9 @@ def parse():
                     help="cycles of the plain FP64 run compared at equal RMSE")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="burgers_large",
+                    help="burgers_large (default: fine 16384 / coarse 4096, Ne=128) or ns2d "
+                         "(fine 512^2 / coarse 128^2, Ne=64, 2048 observations)")
     return ap.parse_args()
 
 
@@ -169,7 +185,8 @@ def oracle_cycle_sample(w, inp, mg, step_fraction: int):
     t0 = time.perf_counter()
     mg.forecast(steps)
     t1 = time.perf_counter()
-    yo = np.asarray(inp["truth0"])[inp["obs_idx"]] + 0.0
+    from paper_2012_10091_gb300 import workloads as W
+    yo = W.sample_truth(w, inp["truth0"], inp["obs_idx"], inp["obs_var"])
     mg.analyse(yo)
     mg.prolong_correct()
     O.rmse(mg.fine, inp["truth0"], w.V)
@@ -208,7 +225,7 @@ def run_reference(args, dist, w, inp):
     val = 1.0 / per
     sample = (f"per step: {w.steps_per_cycle // frac} of the {w.steps_per_cycle} RK3 steps of a "
               f"cycle (time scaled by {frac}) plus one full FP64 analysis, prolongation and RMSE")
-    line = {"metric": "MGEnKF analysis cycles/s (1-D Burgers 16384/4096, Ne=128, 512 obs)",
+    line = {"metric": METRIC[args.workload],
             "value": val, "unit": "cycles/s", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -225,16 +242,20 @@ def run_reference(args, dist, w, inp):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
-def truth_and_obs(M, w, inp, ncycles, torch):
-    """Synthetic input: FP32 truth trajectory on the GPU and its noisy samples
-    at the observed nodes, one row per cycle (resident in HBM)."""
-    truth = torch.tensor(inp["truth0"], dtype=torch.float32, device="cuda")
+def truth_and_obs(M, w, inp, ncycles, torch, truth_prec):
+    """Synthetic input: truth trajectory on the GPU and its noisy samples at
+    the observed nodes, one row per cycle (resident in HBM)."""
+    fp32 = truth_prec == "fp32"
+    truth = torch.tensor(inp["truth0"], dtype=torch.float32 if fp32 else torch.float64, device="cuda")
     truths = torch.empty((ncycles, w.nxf), dtype=torch.float64, device="cuda")
     yos = torch.empty((ncycles, w.ny), dtype=torch.float64, device="cuda")
-    idx = torch.tensor(inp["obs_var"].astype(np.int64) * w.nf + inp["obs_idx"], device="cuda")
+    nfp = w.nf ** w.dim
+    idx = torch.tensor(inp["obs_var"].astype(np.int64) * nfp + inp["obs_idx"], device="cuda")
+    model = M.MGENKF_BURGERS1D if w.model == "burgers1d" else M.MGENKF_NS2D
     for k in range(ncycles):
-        M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_MIXED, truth, 1, w.nf, w.length, w.dt, w.nu,
-                       nsteps=w.steps_per_cycle, stream=torch.cuda.current_stream().cuda_stream)
+        M.mgk_forecast(model, M.MGENKF_MIXED if fp32 else M.MGENKF_FP64, truth, 1, w.nf, w.length,
+                       w.dt, w.nu, w.gamma, w.prandtl, nsteps=w.steps_per_cycle,
+                       stream=torch.cuda.current_stream().cuda_stream)
         truths[k] = truth.double()
         from paper_2012_10091_gb300 import workloads as W
         yos[k] = truths[k][idx] + torch.tensor(W.observation_noise(w, k), device="cuda")
@@ -254,8 +275,9 @@ def run_gpu(args, dist, w, inp):
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
     ncyc = args.warmup + args.steps
+    spec = WORKLOADS[args.workload]
     with torch.cuda.stream(stream):
-        truths, yos = truth_and_obs(M, w, inp, max(ncyc, args.fp64_cycles), torch)
+        truths, yos = truth_and_obs(M, w, inp, max(ncyc, args.fp64_cycles), torch, spec["truth"])
     torch.cuda.synchronize()
 
     g = M.MGEnKF.from_workload(w, stream=sp)
@@ -360,19 +382,21 @@ def run_gpu(args, dist, w, inp):
 
     # roofline of the dominant kernel (the forecast): FP32 ALU bound
     peaks, peak_src = measured_peaks()
-    pts = w.ne * w.nc + w.nf
-    flops = FLOPS_PER_POINT_STEP * pts * w.steps_per_cycle
-    achieved = flops / fc_mean / 1e12
+    pts = w.ne * w.nc ** w.dim + w.nf ** w.dim
+    lps = spec["launches_per_step"]
+    launches_fc = 1 if lps is None else lps * w.steps_per_cycle
+    flops = spec["flops"] * pts * w.steps_per_cycle / launches_fc   # per launch
+    achieved = flops / (fc_mean / launches_fc) / 1e12
     peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the current
-    # forecast kernel (profiles/burgers_f32x2_kernel__burgers_16384_4096_ne128_mixed.md);
-    # reset to None whenever the kernel changes
-    traffic = 2175232 + 0
+    # forecast kernel (profiles/burgers_f32x2_kernel__burgers_16384_4096_ne128_mixed.md
+    # for Burgers); None until captured, and reset whenever the kernel changes
+    traffic = spec["traffic"]
     g.close()
 
     if dist.rank == 0:
         line = {
-            "metric": "MGEnKF analysis cycles/s (1-D Burgers 16384/4096, Ne=128, 512 obs)",
+            "metric": METRIC[args.workload],
             "value": value, "unit": "cycles/s", "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -384,14 +408,14 @@ def run_gpu(args, dist, w, inp):
             "member_steps_per_s": value * w.ne * w.steps_per_cycle,
             "forecast_ms_per_cycle": fc_mean * 1e3,
             "analysis_ms_per_cycle": (t_total / args.steps - fc_mean) * 1e3,
-            "hbm_gbs_algorithmic": (2 * 4 * pts) * args.steps / t_total / 1e9,
+            "hbm_gbs_algorithmic": (2 * 4 * w.V * pts) * args.steps / t_total / 1e9,
             "fp64_plain": {"cycles_per_s": fp64_cps, "cycles": nref,
                            "rmse_last_half": rm64, "mixed_rmse_last_half": rmmx,
                            "rmse_rel_diff": abs(rmmx - rm64) / rm64,
                            "fine_state_rel_diff": state_rel,
                            "speedup_mixed_vs_fp64": value / dist.world / fp64_cps},
             "rmse_final": float(rmse_mixed[-1]),
-            "roofline": {"bound": "alu", "kernel": "burgers_f32x2_kernel<8>",
+            "roofline": {"bound": "alu", "kernel": spec["kernel"],
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
@@ -409,11 +433,20 @@ def run_gpu(args, dist, w, inp):
         print(json.dumps(line), flush=True)
 
 
+METRIC = {
+    "burgers_large": "MGEnKF analysis cycles/s (1-D Burgers 16384/4096, Ne=128, 512 obs)",
+    "ns2d": "MGEnKF analysis cycles/s (2-D NS 512^2/128^2, Ne=64, 2048 obs)",
+}
+
+
 def main():
     args = parse()
     dist = Dist()
     from paper_2012_10091_gb300 import workloads as W
-    w = W.burgers_large(seed=dist.rank)
+    if args.workload == "ns2d":
+        w = W.ns2d_shear(seed=dist.rank)
+    else:
+        w = W.burgers_large(seed=dist.rank)
     inp = W.make_inputs(w)
     try:
         if args.impl == "reference":

@@ -128,7 +128,7 @@ __global__ void k_obs_perturb(const double *__restrict__ yf, const double *__res
         e = eps[o];
     }
     const double f = yf[o];
-    Y[o] = (f - ybar[j]) / sqrt((double)(ne - 1));
+    Y[o] = (f - ybar[j]) * (1.0 / sqrt((double)(ne - 1)));
     Z[o] = yo[j] + e - f;
 }
 
@@ -169,15 +169,18 @@ __global__ void __launch_bounds__(256) k_ens_anom(const T *__restrict__ m, size_
 #pragma unroll
     for (int q = 0; q < 8; ++q) sum += part[q * 32 + lane];
     const double xb = sum / ne;
-    const double sq = sqrt((double)(ne - 1));
+    // 1/sqrt(Ne - 1) once: GB300's FP64 division is a long DFMA sequence
+    const double isq = 1.0 / sqrt((double)(ne - 1));
     const int ldt = ldx + 8;
     if (X64) {
         if (ok)
-            for (int i = wp; i < ne; i += 8) X64[(size_t)i * nx + p] = ((double)m[(size_t)i * nx + p] - xb) / sq;
+            for (int i = wp; i < ne; i += 8) X64[(size_t)i * nx + p] = ((double)m[(size_t)i * nx + p] - xb) * isq;
         return;
     }
+    // BF16 path: FP64 centring, FP32 scaling (the BF16 rounding dominates)
+    const float isqf = (float)isq;
     for (int i = wp; i < ldx; i += 8)
-        tile[lane * ldt + i] = __double2bfloat16((ok && i < ne) ? ((double)m[(size_t)i * nx + p] - xb) / sq : 0.0);
+        tile[lane * ldt + i] = __float2bfloat16((ok && i < ne) ? (float)((double)m[(size_t)i * nx + p] - xb) * isqf : 0.f);
     __syncthreads();
     // store: row r of the tile (point p0 + r) is ldx bf16 = ldx/8 16-byte chunks
     const int chunks = ldx / 8;
@@ -236,9 +239,72 @@ __global__ void k_gemm_nt(const double *__restrict__ A, int m, const double *__r
     }
 }
 
+// Partial sums of k_gemm_nt over K chunks (split-K), combined in chunk order.
+__global__ void k_gemm_nt_split(const double *__restrict__ A, int m, const double *__restrict__ B1,
+                                int n1, const double *__restrict__ B2, int n2, int K, int kchunk,
+                                double *__restrict__ part, const int *status) {
+    if (status && *status) return;
+    __shared__ double As[16][33];
+    __shared__ double Bs[16][33];
+    const int a0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    double acc = 0.0;
+    for (int k0 = kb; k0 < ke; k0 += 32) {
+        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+            const int r = e >> 5, kk = e & 31, k = k0 + kk;
+            const int a = a0 + r;
+            As[r][kk] = (a < m && k < ke) ? A[(size_t)a * K + k] : 0.0;
+            const int c = c0 + r;
+            const double *brow = c < n1 ? B1 + (size_t)c * K
+                                        : (c < n1 + n2 ? B2 + (size_t)(c - n1) * K : nullptr);
+            Bs[r][kk] = (brow && k < ke) ? brow[k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) acc = fma(As[ty][kk], Bs[tx][kk], acc);
+        __syncthreads();
+    }
+    const int a = a0 + ty, c = c0 + tx;
+    if (a < m && c < n1 + n2) part[((size_t)blockIdx.z * m + a) * (n1 + n2) + c] = acc;
+}
+
+__global__ void k_gemm_nt_reduce(const double *__restrict__ part, int nsplit, int m, int n1, int n2,
+                                 double divisor, double diag, double *__restrict__ out1,
+                                 double *__restrict__ out2, const int *status) {
+    if (status && *status) return;
+    const int ncol = n1 + n2;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * ncol; e += gridDim.x * blockDim.x) {
+        const int a = e / ncol, c = e % ncol;
+        double acc = 0.0;
+        for (int z = 0; z < nsplit; ++z) acc += part[((size_t)z * m + a) * ncol + c];
+        if (c < n1)
+            out1[(size_t)a * n1 + c] = (a == c ? diag : 0.0) + acc / divisor;
+        else
+            out2[(size_t)(c - n1) * m + a] = acc / divisor;
+    }
+}
+
+int gemm_nt_splits(int m, int n1, int n2, int K) {
+    const int tiles = ceil_div(n1 + n2, 16) * ceil_div(m, 16);
+    int splits = 1;
+    while (tiles * splits * 2 <= 2 * kNumSMs && K / (splits * 2) >= 128) splits *= 2;
+    return splits;
+}
+
 void launch_gemm_nt_f64(const double *A, int m, const double *B1, int n1, const double *B2, int n2,
                         int K, double scale_div, double diag, double *out1, double *out2,
-                        const int *status, cudaStream_t s) {
+                        const int *status, cudaStream_t s, double *part) {
+    const int splits = part ? gemm_nt_splits(m, n1, n2, K) : 1;
+    if (splits > 1) {
+        count_launches(2);
+        const int kchunk = ceil_div(ceil_div(K, splits), 32) * 32;
+        dim3 grid(ceil_div(n1 + n2, 16), ceil_div(m, 16), splits);
+        k_gemm_nt_split<<<grid, 256, 0, s>>>(A, m, B1, n1, B2, n2, K, kchunk, part, status);
+        k_gemm_nt_reduce<<<grid_for((size_t)m * (n1 + n2), 256), 256, 0, s>>>(part, splits, m, n1, n2,
+                                                                           scale_div, diag, out1, out2, status);
+        return;
+    }
     count_launches(1);
     dim3 grid(ceil_div(n1 + n2, 16), ceil_div(m, 16));
     k_gemm_nt<<<grid, 256, 0, s>>>(A, m, B1, n1, B2, n2, K, scale_div, diag, out1, out2, status);
@@ -616,12 +682,17 @@ __global__ void k_prolong_add(T *__restrict__ fine, const T *__restrict__ dC, in
         } else {
             const int fy = (int)(k / nf), fx = (int)(k % nf);
             const int Jy = fy / r, my = fy % r, Jx = fx / r, mx = fx % r;
+            T wx[4], wy[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                wx[t] = (T)w.w[mx][t];
+                wy[t] = (T)w.w[my][t];
+            }
 #pragma unroll
             for (int ty = 0; ty < 4; ++ty) {
                 const size_t row = (size_t)((Jy - 1 + ty + nc) % nc) * nc;
 #pragma unroll
-                for (int tx = 0; tx < 4; ++tx)
-                    acc += (T)(w.w[my][ty] * w.w[mx][tx]) * d[row + (Jx - 1 + tx + nc) % nc];
+                for (int tx = 0; tx < 4; ++tx) acc += (wy[ty] * wx[tx]) * d[row + (Jx - 1 + tx + nc) % nc];
             }
         }
         fine[idx] += acc;

@@ -44,9 +44,12 @@ void launch_ens_anom(const T *members, size_t nx, int ne, double *X64, __nv_bflo
 
 // out1[a][c] = diag*(a==c) + scale*sum_k A[a][k] B1[c][k]   (c < n1, row-major, ld n1)
 // out2[c][a] = scale*sum_k A[a][k] B2[c][k]                 (c < n2, "column c contiguous")
+// part: optional scratch of gemm_nt_splits(...) * m * (n1 + n2) doubles; with
+// it, long K is split over more CTAs and the chunks are summed in order.
 void launch_gemm_nt_f64(const double *A, int m, const double *B1, int n1, const double *B2, int n2,
                         int K, double scale, double diag, double *out1, double *out2,
-                        const int *status, cudaStream_t s);
+                        const int *status, cudaStream_t s, double *part = nullptr);
+int gemm_nt_splits(int m, int n1, int n2, int K);
 
 // C[j][l] = sum_i Y[i][j] Y[i][l] + diag*(j==l), j,l < ny (direct form).
 void launch_gemm_tn_f64(const double *Y, int ne, int ny, double diag, double *C, const int *status,

@@ -69,10 +69,15 @@ __global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
     // load the tile and its halo, form the primitives
     for (int e = threadIdx.x; e < kNsHalo; e += blockDim.x) {
         const int ly = e / kNsHx, lx = e % kNsHx;
-        const int gy = (y0 + ly - 1 + n) % n, gx = (x0 + lx - 1 + n) % n;
+        int gy = y0 + ly - 1, gx = x0 + lx - 1;  // periodic wrap without integer division
+        if (gy < 0) gy += n;
+        if (gx < 0) gx += n;
+        while (gy >= n) gy -= n;
+        while (gx >= n) gx -= n;
         const size_t o = (size_t)gy * n + gx;
         const T rho = in[o], mx = in[plane + o], my = in[2 * plane + o], E = in[3 * plane + o];
-        const T u = mx / rho, v = my / rho;
+        const T rinv = T(1) / rho;  // one division per point
+        const T u = mx * rinv, v = my * rinv;
         const T p = A.gm1 * (E - T(0.5) * rho * (u * u + v * v));
         sq[0][e] = rho;
         sq[1][e] = mx;
@@ -81,7 +86,7 @@ __global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
         spr[0][e] = u;
         spr[1][e] = v;
         spr[2][e] = p;
-        spr[3][e] = p / rho;
+        spr[3][e] = p * rinv;
     }
     __syncthreads();
     const int lx = threadIdx.x % kNsTx, ly = threadIdx.x / kNsTx;

@@ -49,6 +49,7 @@ struct mgenkf_ctx {
     double *Tm = nullptr;                               // T, (ne+1) x ne (points at Bt or own buffer)
     double *truth_d = nullptr, *rmse_part = nullptr, *rmse_d = nullptr, *scratch = nullptr;
     void *ns_scratch = nullptr;  // NS-2D stage buffers
+    double *gemm_part = nullptr; // split-K partial sums of the gain GEMMs
     size_t scratch_n = 0;
     int *status = nullptr;
 };
@@ -122,7 +123,7 @@ static void free_all(mgenkf_ctx *h) {
     void *ptrs[] = {h->fine, h->members, h->xstar, h->dC, h->tap_idx, h->tap_w, h->yf, h->yo,
                     h->ybar, h->eps, h->Y, h->Z, h->X64, h->X16, h->Tt, h->S, h->Lt, h->Bt, h->C,
                     h->Ct, h->W, h->truth_d, h->rmse_part, h->rmse_d, h->scratch, h->status,
-                    h->ns_scratch};
+                    h->ns_scratch, h->gemm_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->Tm && h->Tm != h->Bt) cudaFree(h->Tm);
@@ -280,6 +281,11 @@ static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const 
     }
     if (cfg->model == MGENKF_NS2D)
         H_ALLOC(h->ns_scratch, ns2d_scratch_elems(h->nc, h->ne, h->nf, 1) * ts);
+    {
+        const size_t p1 = (size_t)gemm_nt_splits((int)ne, (int)ne, (int)ne + 1, (int)ny) * ne * (2 * ne + 1);
+        const size_t p2 = (size_t)gemm_nt_splits((int)ne, 0, (int)ne + 1, (int)ny) * ne * (ne + 1);
+        H_ALLOC(h->gemm_part, std::max(p1, p2) * sizeof(double));
+    }
     H_ALLOC(h->rmse_part, (size_t)kRmseBlocks * h->V * 2 * sizeof(double));
     H_ALLOC(h->rmse_d, 4 * sizeof(double));
     H_ALLOC(h->status, sizeof(int));
@@ -447,7 +453,8 @@ static void analyse_kernels(mgenkf_ctx *h, int gen_eps) {
     const double s2 = h->cfg.obs_sigma * h->cfg.obs_sigma;
     if (!h->direct) {
         // S = I + Y^T R^-1 Y (ne x ne) and B = Y^T R^-1 [D | d*]; T = S^-1 B
-        launch_gemm_nt_f64(h->Y, ne, h->Y, ne, h->Z, ne + 1, ny, s2, 1.0, h->S, h->Bt, h->status, s);
+        launch_gemm_nt_f64(h->Y, ne, h->Y, ne, h->Z, ne + 1, ny, s2, 1.0, h->S, h->Bt, h->status, s,
+                           h->gemm_part);
         launch_cholesky(h->S, h->Lt, ne, h->status, s);
         launch_chol_solve(h->S, h->Lt, ne, h->Bt, h->Bt, ne + 1, h->mixed ? h->Tt : nullptr, h->ldx,
                           h->status, s);
@@ -456,7 +463,8 @@ static void analyse_kernels(mgenkf_ctx *h, int gen_eps) {
         launch_gemm_tn_f64(h->Y, ne, ny, s2, h->C, h->status, s);
         launch_cholesky(h->C, h->Ct, ny, h->status, s);
         launch_chol_solve(h->C, h->Ct, ny, h->Z, h->W, ne + 1, nullptr, 0, h->status, s);
-        launch_gemm_nt_f64(h->Y, ne, nullptr, 0, h->W, ne + 1, ny, 1.0, 0.0, nullptr, h->Tm, h->status, s);
+        launch_gemm_nt_f64(h->Y, ne, nullptr, 0, h->W, ne + 1, ny, 1.0, 0.0, nullptr, h->Tm, h->status, s,
+                           h->gemm_part);
         if (h->mixed) launch_tt_bf16(h->Tm, h->Tt, ne, h->ldx, h->status, s);
     }
     if (h->mixed)

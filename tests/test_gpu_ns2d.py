@@ -44,7 +44,9 @@ def _smooth_states(nprob, n, seed):
 def test_ns2d_fp64_matches_oracle(M, n, nprob):
     import torch
     q0 = _smooth_states(nprob, n, n)
-    h, mu, dt, steps = 1.0 / n, 1e-2, 0.2 / n, 12
+    # dt within the acoustic (CFL 0.2) and heat-conduction (kappa dt / h^2 <= 0.1) limits
+    h, mu, steps = 1.0 / n, 1e-2, 12
+    dt = min(0.2 * h, 0.1 * h * h * (GAMMA - 1) * PR / (mu * GAMMA) * 2)
     ref = O.ns2d_rk3(q0, h, GAMMA, mu, PR, dt, steps)
     d = torch.tensor(q0, dtype=torch.float64, device="cuda")
     M.mgk_forecast(M.MGENKF_NS2D, M.MGENKF_FP64, d, nprob, n, 1.0, dt, mu, GAMMA, PR, nsteps=steps)

@@ -51,7 +51,8 @@ typedef enum {
     MGENKF_ERR_CUDA = 3,        /* a CUDA runtime call failed (text in last_error) */
     MGENKF_ERR_NOT_SPD = 4,     /* innovation matrix had a non-positive pivot */
     MGENKF_ERR_NONFINITE = 5,   /* observation vector holds NaN or Inf */
-    MGENKF_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+    MGENKF_ERR_UNSUPPORTED = 6, /* valid request this build does not implement */
+    MGENKF_ERR_TIMEOUT = 7      /* a bounded wait inside a kernel expired (state left unchanged) */
 } mgenkf_status;
 
 /* models (Eq. burgers; Eqs. Mass, Momentum, Energy) */

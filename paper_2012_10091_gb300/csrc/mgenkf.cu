@@ -18,6 +18,7 @@
 #include "common.cuh"
 #include "forecast.h"
 #include "forecast_ns2d.h"
+#include "update_tc.h"
 
 using namespace mgk;
 
@@ -50,6 +51,7 @@ struct mgenkf_ctx {
     double *truth_d = nullptr, *rmse_part = nullptr, *rmse_d = nullptr, *scratch = nullptr;
     void *ns_scratch = nullptr;  // NS-2D stage buffers
     double *gemm_part = nullptr; // split-K partial sums of the gain GEMMs
+    UpdateTcPlan tc;             // tensor-core member update (mixed precision)
     size_t scratch_n = 0;
     int *status = nullptr;
 };
@@ -326,6 +328,15 @@ static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const 
     H_CUDA(cudaMemcpyAsync(h->tap_idx, tidx.data(), tidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
     H_CUDA(cudaMemcpyAsync(h->tap_w, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     for (int m = 0; m < h->r; ++m) cubic_weights((double)m / h->r, h->pw.w[m]);
+    // mixed precision: the member update runs on the tensor cores when the
+    // shapes allow (N = Ne + 1 <= 256); MGENKF_UPDATE=simt selects the
+    // CUDA-core kernel instead (used to cross-check the two)
+    h->tc.ready = false;
+    if (h->mixed) {
+        const char *sel = getenv("MGENKF_UPDATE");
+        if (!(sel && strcmp(sel, "simt") == 0))
+            update_tc_prepare(&h->tc, h->X16, h->ldx, (int)h->nx, h->Tt, h->ntpad, h->ne);
+    }
     H_CUDA(cudaStreamSynchronize(h->stream));
     return MGENKF_OK;
 }
@@ -467,7 +478,9 @@ static void analyse_kernels(mgenkf_ctx *h, int gen_eps) {
                            h->gemm_part);
         if (h->mixed) launch_tt_bf16(h->Tm, h->Tt, ne, h->ldx, h->status, s);
     }
-    if (h->mixed)
+    if (h->mixed && h->tc.ready)
+        launch_update_tc(h->tc, (float *)members, (float *)dC, h->status, s);
+    else if (h->mixed)
         launch_update_bf16((float *)members, (float *)dC, h->X16, h->Tt, h->ldx, nx, ne, h->status, s);
     else
         launch_update_f64<T>(members, dC, h->X64, h->Tm, nx, ne, h->status, s);

@@ -1,0 +1,276 @@
+// update_tc.cu -- member update and coarse correction on the tensor cores
+// (Eq. ensemble_update with K = X Y^T C^-1, written as x^a,(i) = x^f,(i) + X T_i,
+// and x^C' - x^C* = X T_ne, Algorithm 4 step 5).
+//
+// D[p][c] = sum_a X[p][a] T[c][a]: M = Nx points (tile 128), N = Ne + 1 padded
+// to a multiple of 16 (<= 256), K = Ne padded to 16, BF16 operands, FP32
+// accumulation.  One CTA per 128-point tile:
+//   * one thread issues the TMA loads of the X tile and of T (K-major, 128-byte
+//     swizzle, 64 values per swizzle atom) and waits on an mbarrier;
+//   * warp 0 allocates TMEM for the 128 x N FP32 accumulator;
+//   * one thread issues K/16 tcgen05.mma (kind::f16, cta_group::1) and commits
+//     them to a second mbarrier;
+//   * the four warps read their 32 TMEM lanes (tcgen05.ld 32x32b) and fuse the
+//     epilogue: members[c][p] += D[p][c] for c < Ne, dC[p] = D[p][Ne].
+// Every mbarrier wait is bounded (about a second of SM clocks); on expiry the
+// kernel records MGENKF_ERR_TIMEOUT in the status word, waits (bounded) for its
+// own copies, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "analysis.h"
+#include "common.cuh"
+#include "update_tc.h"
+
+namespace mgk {
+
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kAtomK = 64;                        // bf16 values per 128-byte swizzle row
+constexpr long long kWaitLimitCycles = 2000000000LL;  // ~1 s at 2 GHz
+constexpr int kStTimeout = 7;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait on phase `parity`; returns false if the limit expired
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitLimitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);        // start address
+    d |= (uint64_t)1 << 16;                       // leading byte offset (unused with swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset
+    d |= (uint64_t)1 << 46;                       // version
+    d |= (uint64_t)2 << 61;                       // layout: 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ CUtensorMap map_x,
+                                                   const __grid_constant__ CUtensorMap map_t,
+                                                   float *__restrict__ members, float *__restrict__ dC,
+                                                   int nx, int ne, int kblocks, int ntile, int tmem_cols,
+                                                   int *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned operand buffers
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *sa = base;                                        // kblocks x [128][64] bf16
+    unsigned char *sb = base + (size_t)kblocks * kTileM * 128;       // kblocks x [ntile][64] bf16
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sb + (size_t)kblocks * ntile * 128);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
+    __shared__ int s_fail;
+
+    if (*status) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * kTileM;
+    if (tid == 0) {
+        s_fail = 0;
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const uint32_t tx_bytes = (uint32_t)kblocks * (kTileM + ntile) * 128;
+    if (tid == 0) {
+        mbar_expect_tx(&bars[0], tx_bytes);
+        for (int kb = 0; kb < kblocks; ++kb) {
+            tma_load_2d(sa + (size_t)kb * kTileM * 128, &map_x, &bars[0], kb * kAtomK, m0);
+            tma_load_2d(sb + (size_t)kb * ntile * 128, &map_t, &bars[0], kb * kAtomK, 0);
+        }
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (tid == 0) {
+        if (!mbar_wait(&bars[0], 0)) {
+            s_fail = 1;
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = idesc_bf16(kTileM, ntile);
+            const int ksteps = kblocks * (kAtomK / 16);
+            for (int j = 0; j < ksteps; ++j) {
+                const int kb = j / (kAtomK / 16), kk = j % (kAtomK / 16);
+                const uint64_t adesc = smem_desc_sw128(smem_u32(sa + (size_t)kb * kTileM * 128 + kk * 32));
+                const uint64_t bdesc = smem_desc_sw128(smem_u32(sb + (size_t)kb * ntile * 128 + kk * 32));
+                const uint32_t acc = j > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bars[1]))
+                         : "memory");
+        }
+    }
+    __syncthreads();
+    bool ok = s_fail == 0;
+    if (ok && !mbar_wait(&bars[1], 0)) ok = false;
+    if (!ok) {
+        if (tid == 0) {
+            atomicCAS(status, 0, kStTimeout);
+            mbar_wait(&bars[0], 0);  // let our own copies land (bounded) before the CTA exits
+        }
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int p = m0 + warp * 32 + lane;
+        const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < ntile; c0 += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(row + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (p < nx) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int c = c0 + q;
+                    const float v = __uint_as_float(r[q]);
+                    if (c < ne)
+                        members[(size_t)c * nx + p] += v;
+                    else if (c == ne)
+                        dC[p] = v;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+static bool encode_kmajor(CUtensorMap *m, const __nv_bfloat16 *ptr, int ld, int rows, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {(cuuint32_t)kAtomK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool update_tc_supported(int ne, int ldx, int ntpad) {
+    // N = ntpad rows of T in one MMA (<= 256), K = ldx (multiple of 16); TMA
+    // inner box of 64 values; the operands must fit shared memory.
+    if (ntpad < 16 || ntpad > 256 || ntpad % 16 || ldx % 16 || ne < 2) return false;
+    const int kblocks = (ldx + kAtomK - 1) / kAtomK;
+    const size_t smem = 1024 + (size_t)kblocks * (kTileM + ntpad) * 128 + 64;
+    return smem <= 200 * 1024 && encode_fn() != nullptr;
+}
+
+bool update_tc_prepare(UpdateTcPlan *plan, const __nv_bfloat16 *X16, int ldx, int nx, const __nv_bfloat16 *Tt,
+                       int ntpad, int ne) {
+    if (!update_tc_supported(ne, ldx, ntpad)) return false;
+    memset(plan, 0, sizeof(*plan));
+    plan->kblocks = (ldx + kAtomK - 1) / kAtomK;
+    plan->ntile = ntpad;
+    int cols = 32;
+    while (cols < ntpad) cols <<= 1;
+    plan->tmem_cols = cols;
+    plan->smem = 1024 + (size_t)plan->kblocks * (kTileM + ntpad) * 128 + 64;
+    // at most 512 / tmem_cols CTAs may share an SM's 512 TMEM columns: ask for
+    // enough shared memory that no more are resident (no CTA ever waits in alloc)
+    const size_t per_sm = 228 * 1024;
+    const size_t min_smem = per_sm / (size_t)(512 / cols + 1) + 2048;
+    if (plan->smem < min_smem) plan->smem = min_smem;
+    plan->nx = nx;
+    plan->ne = ne;
+    if (!encode_kmajor(&plan->map_x, X16, ldx, nx, kTileM)) return false;
+    if (!encode_kmajor(&plan->map_t, Tt, ldx, ntpad, ntpad)) return false;
+    plan->ready = true;
+    return true;
+}
+
+cudaError_t launch_update_tc(const UpdateTcPlan &plan, float *members, float *dC, int *status, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    count_launches(1);
+    const int grid = (plan.nx + kTileM - 1) / kTileM;
+    k_update_tc<<<grid, 128, plan.smem, s>>>(plan.map_x, plan.map_t, members, dC, plan.nx, plan.ne, plan.kblocks,
+                                             plan.ntile, plan.tmem_cols, status);
+    return cudaGetLastError();
+}
+
+}  // namespace mgk

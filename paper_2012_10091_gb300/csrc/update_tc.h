@@ -1,0 +1,27 @@
+// update_tc.h -- tensor-core (tcgen05) member update, internal to the library.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace mgk {
+
+// TMA descriptors and launch shape of the update for one handle's buffers.
+struct UpdateTcPlan {
+    CUtensorMap map_x;  // X^T, [nx][ldx] bf16, K-major, box 64 x 128
+    CUtensorMap map_t;  // T^T, [ntpad][ldx] bf16, K-major, box 64 x ntpad
+    int kblocks, ntile, tmem_cols, nx, ne;
+    size_t smem;
+    bool ready;
+};
+
+bool update_tc_supported(int ne, int ldx, int ntpad);
+bool update_tc_prepare(UpdateTcPlan *plan, const __nv_bfloat16 *X16, int ldx, int nx, const __nv_bfloat16 *Tt,
+                       int ntpad, int ne);
+// members[c][p] += sum_a X[p][a] T[c][a] (c < ne), dC[p] = sum_a X[p][a] T[ne][a]
+cudaError_t launch_update_tc(const UpdateTcPlan &plan, float *members, float *dC, int *status, cudaStream_t s);
+
+}  // namespace mgk

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libmgenkf.so")
 
 MGENKF_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_SPD", 5: "NONFINITE",
-                6: "UNSUPPORTED"}
+                6: "UNSUPPORTED", 7: "TIMEOUT"}
 MGENKF_BURGERS1D, MGENKF_NS2D = 1, 2
 MGENKF_FP64, MGENKF_MIXED = 0, 1
 MGENKF_GAIN_ENSEMBLE, MGENKF_GAIN_DIRECT = 0, 1

@@ -97,3 +97,30 @@ def test_explicit_perturbations_are_used(M):
     r = _one_analysis(M, w, 0, "fp64", explicit_eps=True)
     np.testing.assert_array_equal(r["fields"][M.MGENKF_FIELD_EPS].reshape(w.ne, w.ny), r["e"])
     assert rel_err(r["mem"] - r["m0"], r["m_ref"] - r["m0"]) < 1e-10
+
+
+@pytest.mark.parametrize("nf,ratio,ne,npr", [(4096, 4, 37, 130), (16384, 4, 128, 512), (1000, 4, 255, 60)])
+def test_tensor_core_update_matches_cuda_core_update(M, nf, ratio, ne, npr, monkeypatch):
+    # same BF16 operands, FP32 accumulation in different orders: the two member
+    # updates agree to FP32 rounding of the sums (well inside 1e-5 of the increment)
+    w = W.burgers_custom(nf, ratio, ne, npr, obs_kind="random", sigma=0.05, precision="mixed")
+    inp = W.make_inputs(w)
+    rng = np.random.default_rng(11)
+    yo = rng.standard_normal(w.ny) * 0.2
+    eps = w.sigma * rng.standard_normal((w.ne, w.ny))
+    out = {}
+    for mode in ("tc", "simt"):
+        if mode == "simt":
+            monkeypatch.setenv("MGENKF_UPDATE", "simt")
+        g = M.MGEnKF.from_workload(w, precision="mixed")
+        g.set_state(inp["fine0"], inp["members0"])
+        g.analyse(yo, eps)
+        assert g.sync() == 0
+        _, mem = g.get_state()
+        out[mode] = (mem, g.field(M.MGENKF_FIELD_DC))
+        g.close()
+    inc = out["simt"][0] - inp["members0"].astype(np.float32)
+    scale = max(np.max(np.abs(inc)), 1e-30)
+    assert np.max(np.abs(out["tc"][0] - out["simt"][0])) <= 1e-5 * scale + 2e-7
+    dscale = max(np.max(np.abs(out["simt"][1])), 1e-30)
+    assert np.max(np.abs(out["tc"][1] - out["simt"][1])) <= 1e-5 * dscale

@@ -262,3 +262,113 @@ class MGEnKF:
 
     def rmse(self, truth):
         return rmse(self.fine, truth, self.V)
+
+
+# --------------------------------------------------------------------------
+# learned correction: residual CNN over Pi_F (8 -> 32 -> 32 -> 64 channels,
+# periodic 3x3 convolutions, ReLU, pixel shuffle by 4)
+# --------------------------------------------------------------------------
+CNN_SHAPES = [("W1", (32, 8, 3, 3)), ("b1", (32,)), ("W2", (32, 32, 3, 3)), ("b2", (32,)),
+              ("W3", (64, 32, 3, 3)), ("b3", (64,))]
+
+
+def _cnn_sigs():
+    L = lib()
+    if getattr(L, "_cnn_ready", False):
+        return L
+    P, i32 = ctypes.c_void_p, ctypes.c_int
+    L.orc_conv3x3.argtypes = [P, i32, i32, P, P, i32, i32, P]
+    L.orc_conv3x3_bwd.argtypes = [P, i32, i32, P, i32, P, P, P, P]
+    L.orc_pixel_shuffle4.argtypes = [P, i32, i32, P]
+    L.orc_pixel_unshuffle4.argtypes = [P, i32, i32, P]
+    L._cnn_ready = True
+    return L
+
+
+def conv3x3(x, W, b, relu=False):
+    L = _cnn_sigs()
+    x, W, b = _f64(x), _f64(W), _f64(b)
+    cout, cin = W.shape[0], W.shape[1]
+    n = x.shape[-1]
+    out = np.zeros((cout, n, n))
+    L.orc_conv3x3(_p(x), cin, n, _p(W), _p(b), cout, int(relu), _p(out))
+    return out
+
+
+def conv3x3_bwd(x, W, dout, want_din=True):
+    L = _cnn_sigs()
+    x, W, dout = _f64(x), _f64(W), _f64(dout)
+    cout, cin = W.shape[0], W.shape[1]
+    n = x.shape[-1]
+    dW = np.zeros_like(W)
+    db = np.zeros(cout)
+    din = np.zeros((cin, n, n)) if want_din else None
+    L.orc_conv3x3_bwd(_p(x), cin, n, _p(W), cout, _p(dout), _p(din) if want_din else None, _p(dW), _p(db))
+    return din, dW, db
+
+
+def pixel_shuffle4(x):
+    L = _cnn_sigs()
+    x = _f64(x)
+    C, n = x.shape[0] // 16, x.shape[-1]
+    out = np.zeros((C, 4 * n, 4 * n))
+    L.orc_pixel_shuffle4(_p(x), C, n, _p(out))
+    return out
+
+
+def pixel_unshuffle4(x):
+    L = _cnn_sigs()
+    x = _f64(x)
+    C, n = x.shape[0], x.shape[-1] // 4
+    out = np.zeros((16 * C, n, n))
+    L.orc_pixel_unshuffle4(_p(x), C, n, _p(out))
+    return out
+
+
+def cnn_forward(params, dC, xstar, stats):
+    """Fine correction of one sample: Pi_F(dC) + s_out * shuffle(CNN(normalised [dC, x*])).
+    dC, xstar: 4 x nc x nc.  stats: dict(mu_in (8), s_in (8), s_out (4)).
+    Returns (prediction 4 x 4nc x 4nc, cache for the backward pass)."""
+    nc = dC.shape[-1]
+    a0 = (np.concatenate([dC, xstar]) - stats["mu_in"][:, None, None]) / stats["s_in"][:, None, None]
+    z1 = conv3x3(a0, params["W1"], params["b1"])
+    a1 = np.maximum(z1, 0.0)
+    z2 = conv3x3(a1, params["W2"], params["b2"])
+    a2 = np.maximum(z2, 0.0)
+    z3 = conv3x3(a2, params["W3"], params["b3"])
+    res = pixel_shuffle4(z3) * stats["s_out"][:, None, None]
+    base = prolong_add(dC.reshape(-1), np.zeros(4 * (4 * nc) ** 2), 2, 4, nc, 4).reshape(4, 4 * nc, 4 * nc)
+    return base + res, dict(a0=a0, z1=z1, a1=a1, z2=z2, a2=a2)
+
+
+def cnn_loss_grad(params, dC, xstar, target, stats):
+    """Loss = mean over fine points and channels of ((pred - target) / s_out)^2,
+    and its gradient with respect to every parameter."""
+    pred, c = cnn_forward(params, dC, xstar, stats)
+    s_out = stats["s_out"][:, None, None]
+    r = (pred - target) / s_out
+    N = r.size
+    loss = float(np.sum(r * r) / N)
+    dpred = 2.0 * r / s_out / N
+    dz3 = pixel_unshuffle4(dpred * s_out)
+    da2, dW3, db3 = conv3x3_bwd(c["a2"], params["W3"], dz3)
+    dz2 = da2 * (c["z2"] > 0)
+    da1, dW2, db2 = conv3x3_bwd(c["a1"], params["W2"], dz2)
+    dz1 = da1 * (c["z1"] > 0)
+    _, dW1, db1 = conv3x3_bwd(c["a0"], params["W1"], dz1, want_din=False)
+    return loss, dict(W1=dW1, b1=db1, W2=dW2, b2=db2, W3=dW3, b3=db3)
+
+
+def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba) with bias correction; state holds m, v, t."""
+    state["t"] = state.get("t", 0) + 1
+    t = state["t"]
+    for k in params:
+        m = state.setdefault("m_" + k, np.zeros_like(params[k]))
+        v = state.setdefault("v_" + k, np.zeros_like(params[k]))
+        m[...] = b1 * m + (1 - b1) * grads[k]
+        v[...] = b2 * v + (1 - b2) * grads[k] ** 2
+        mh = m / (1 - b1**t)
+        vh = v / (1 - b2**t)
+        params[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
+    return params

@@ -509,6 +509,88 @@ int orc_enkf_analyse(int dim, int V, int nc, int r, int ne, int ny, const int32_
     return status;
 }
 
+/* ======================================================================== */
+/* Learned correction: periodic 3x3 convolutions and pixel shuffle.          */
+/* Parity: pinned (library convolution with wrap padding, library pixel      */
+/* shuffle, central finite differences of the loss).                         */
+/* ======================================================================== */
+void orc_conv3x3(const double *in, int cin, int n, const double *W, const double *b, int cout,
+                 int relu, double *out) {
+    size_t pl = (size_t)n * n;
+    for (int o = 0; o < cout; ++o)
+        for (int y = 0; y < n; ++y)
+            for (int x = 0; x < n; ++x) {
+                double acc = b[o];
+                for (int i = 0; i < cin; ++i)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            int yy = (y + dy + n) % n, xx = (x + dx + n) % n;
+                            acc += W[(((size_t)o * cin + i) * 3 + dy + 1) * 3 + dx + 1] *
+                                   in[i * pl + (size_t)yy * n + xx];
+                        }
+                if (relu && acc < 0.0) acc = 0.0;
+                out[o * pl + (size_t)y * n + x] = acc;
+            }
+}
+
+void orc_conv3x3_bwd(const double *in, int cin, int n, const double *W, int cout,
+                     const double *dout, double *din, double *dW, double *db) {
+    size_t pl = (size_t)n * n;
+    for (int o = 0; o < cout; ++o) {
+        double s = 0.0;
+        for (size_t k = 0; k < pl; ++k) s += dout[o * pl + k];
+        db[o] += s;
+        for (int i = 0; i < cin; ++i)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    double g = 0.0;
+                    for (int y = 0; y < n; ++y)
+                        for (int x = 0; x < n; ++x) {
+                            int yy = (y + dy + n) % n, xx = (x + dx + n) % n;
+                            g += dout[o * pl + (size_t)y * n + x] * in[i * pl + (size_t)yy * n + xx];
+                        }
+                    dW[(((size_t)o * cin + i) * 3 + dy + 1) * 3 + dx + 1] += g;
+                }
+    }
+    if (!din) return;
+    for (int i = 0; i < cin; ++i)
+        for (int y = 0; y < n; ++y)
+            for (int x = 0; x < n; ++x) {
+                double acc = 0.0;
+                for (int o = 0; o < cout; ++o)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            /* in[i][y][x] feeds out[o][y - dy][x - dx] through tap (dy, dx) */
+                            int yy = (y - dy + n) % n, xx = (x - dx + n) % n;
+                            acc += W[(((size_t)o * cin + i) * 3 + dy + 1) * 3 + dx + 1] *
+                                   dout[o * pl + (size_t)yy * n + xx];
+                        }
+                din[i * pl + (size_t)y * n + x] = acc;
+            }
+}
+
+void orc_pixel_shuffle4(const double *in, int C, int n, double *out) {
+    int nf = 4 * n;
+    for (int c = 0; c < C; ++c)
+        for (int y = 0; y < n; ++y)
+            for (int x = 0; x < n; ++x)
+                for (int sy = 0; sy < 4; ++sy)
+                    for (int sx = 0; sx < 4; ++sx)
+                        out[((size_t)c * nf + 4 * y + sy) * nf + 4 * x + sx] =
+                            in[((size_t)(16 * c + 4 * sy + sx) * n + y) * n + x];
+}
+
+void orc_pixel_unshuffle4(const double *in, int C, int n, double *out) {
+    int nf = 4 * n;
+    for (int c = 0; c < C; ++c)
+        for (int y = 0; y < n; ++y)
+            for (int x = 0; x < n; ++x)
+                for (int sy = 0; sy < 4; ++sy)
+                    for (int sx = 0; sx < 4; ++sx)
+                        out[((size_t)(16 * c + 4 * sy + sx) * n + y) * n + x] =
+                            in[((size_t)c * nf + 4 * y + sy) * nf + 4 * x + sx];
+}
+
 /* Relative RMSE, Eq. L2norm_u: sqrt(sum (x - x_true)^2 / sum x_true^2) per variable. */
 void orc_rmse(const double *x, const double *truth, int V, int64_t npts, double *out) {
     for (int v = 0; v < V; ++v) {

@@ -90,6 +90,21 @@ int orc_enkf_analyse(int dim, int V, int nc, int r, int ne, int ny, const int32_
 int orc_enkf_gain(int nx, int ne, int ny, const double *X, const double *Y, const double *Rm,
                   double *K);
 
+/* ---- learned correction (residual over Pi_F; no counterpart in the paper,
+ * whose conclusion names better projection operators as future work) ----
+ * 3x3 cross-correlation with periodic padding, one sample:
+ *   out[o][y][x] = b[o] + sum_{i, dy, dx} W[o][i][dy+1][dx+1] in[i][(y+dy) mod n][(x+dx) mod n]
+ * optionally followed by ReLU.  Backward: accumulates dW, db and (if din is
+ * not NULL) writes din = W^T * dout (the adjoint correlation). */
+void orc_conv3x3(const double *in, int cin, int n, const double *W, const double *b, int cout,
+                 int relu, double *out);
+void orc_conv3x3_bwd(const double *in, int cin, int n, const double *W, int cout,
+                     const double *dout, double *din, double *dW, double *db);
+/* pixel shuffle by 4: in = 16 C channels of n x n, out = C channels of 4n x 4n,
+ * out[c][4y + sy][4x + sx] = in[16 c + 4 sy + sx][y][x]; unshuffle is its adjoint. */
+void orc_pixel_shuffle4(const double *in, int C, int n, double *out);
+void orc_pixel_unshuffle4(const double *in, int C, int n, double *out);
+
 /* ---- relative RMSE, Eq. L2norm_u, one value per variable ---- */
 void orc_rmse(const double *x, const double *truth, int V, int64_t npts, double *out);
 

@@ -40,6 +40,40 @@ mgenkf_status mgk_forecast(int32_t model, int32_t precision, void *state, int32_
 mgenkf_status mgk_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count, double *out,
                           void *stream);
 
+/* ---- learned correction of the prolongation ------------------------------
+ * The paper's conclusion names better projection operators between the grids
+ * as a direction; this object is a small CNN that predicts the part of the fine
+ * correction that Pi_F(dC) misses (residual over Pi_F), trained on corrections
+ * of a full-resolution EnKF.  Input: the 8 coarse channels [dC (4), x^C* (4)]
+ * of an NS-2D analysis (n_coarse^2 each), normalised as (v - mu_in) / s_in.
+ * Three 3x3 convolutions with periodic padding, 8 -> 32 -> 32 -> 64 channels,
+ * ReLU after the first two; the 64 channels are pixel-shuffled by 4 into 4 fine
+ * channels (fine (4y+sy, 4x+sx) of channel c = channel 16c + 4sy + sx) and
+ * scaled by s_out[c].  BF16 weights and activations, FP32 accumulation, FP32
+ * master weights and Adam state.  Parameters: 30080 floats in the order
+ * W1 (32x8x3x3), b1 (32), W2 (32x32x3x3), b2 (32), W3 (64x32x3x3), b3 (64).
+ * All arrays are FP32 device pointers unless stated; one object per thread. */
+typedef struct mgk_cnn *mgk_cnn_t;
+mgenkf_status mgk_cnn_create(int32_t n_coarse, int32_t batch_max, mgk_cnn_t *out);
+mgenkf_status mgk_cnn_destroy(mgk_cnn_t cnn);
+/* params: 30080 floats (host or device) or NULL; stats: mu_in[8], s_in[8],
+ * s_out[4] (host or device) or NULL.  Setting params resets the Adam state. */
+mgenkf_status mgk_cnn_set_params(mgk_cnn_t cnn, const float *params, const float *stats);
+/* copy out the master parameters and/or the last gradients (host or device; NULL skips) */
+mgenkf_status mgk_cnn_get_params(mgk_cnn_t cnn, float *params, float *grads);
+/* residual (batch x 4 x (4n)^2) = s_out * shuffle(CNN(dC, x*)), written, or added if accumulate != 0.
+ * dC, xstar: batch x 4 x n^2. */
+mgenkf_status mgk_cnn_forward(mgk_cnn_t cnn, const float *dC, const float *xstar, int32_t batch,
+                              float *residual, int32_t accumulate, void *stream);
+/* loss = mean(((Pi_F(dC) + residual - target) / s_out)^2) over batch, channels and
+ * fine points, and its gradient with respect to every parameter (kept in the
+ * object).  target: batch x 4 x (4n)^2 fine corrections.  loss_out: one float
+ * (host or device) or NULL. */
+mgenkf_status mgk_cnn_loss_grad(mgk_cnn_t cnn, const float *dC, const float *xstar, const float *target,
+                                int32_t batch, float *loss_out, void *stream);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) with the last gradients */
+mgenkf_status mgk_cnn_adam_step(mgk_cnn_t cnn, float lr, void *stream);
+
 /* Ensemble-space gain solve that allocates nothing.
  * The paper has no counterpart: this exists for callers that cannot call
  * cudaMalloc (an application whose own pool owns all device memory, a process

@@ -66,6 +66,13 @@ def _load():
         "mgk_forecast": [i32, i32, P, i32, i32, f64, f64, f64, f64, f64, i32, P],
         "mgk_normals": [u64, u64, u64, i64, P, P],
         "mgk_gain_ensemble_noalloc": [P, P, i32, i32, f64, P, P, P],
+        "mgk_cnn_create": [i32, i32, ctypes.POINTER(P)],
+        "mgk_cnn_destroy": [P],
+        "mgk_cnn_set_params": [P, P, P],
+        "mgk_cnn_get_params": [P, P, P],
+        "mgk_cnn_forward": [P, P, P, i32, P, i32, P],
+        "mgk_cnn_loss_grad": [P, P, P, P, i32, P, P],
+        "mgk_cnn_adam_step": [P, ctypes.c_float, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -191,6 +198,74 @@ def mgk_normals(seed, tag, ctr0, count, out, stream=None):
 def mgk_gain_ensemble_noalloc(Y, Z, n_members, n_obs, obs_sigma, T, info=None, stream=None):
     _check(lib.mgk_gain_ensemble_noalloc(_ptr(Y), _ptr(Z), n_members, n_obs, obs_sigma, _ptr(T),
                                          _ptr(info), stream), "mgk_gain_ensemble_noalloc")
+
+
+CNN_NPARAMS = 30080
+CNN_SHAPES = [("W1", (32, 8, 3, 3)), ("b1", (32,)), ("W2", (32, 32, 3, 3)), ("b2", (32,)),
+              ("W3", (64, 32, 3, 3)), ("b3", (64,))]
+
+
+class CNN:
+    """Learned correction of the prolongation (see include/mgenkf_ops.h)."""
+
+    def __init__(self, n_coarse, batch_max=1):
+        h = ctypes.c_void_p()
+        _check(lib.mgk_cnn_create(n_coarse, batch_max, ctypes.byref(h)), "mgk_cnn_create")
+        self.h, self.nc, self.bmax = h.value, n_coarse, batch_max
+
+    def close(self):
+        if self.h:
+            lib.mgk_cnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params=None, stats=None):
+        """params: dict of CNN_SHAPES arrays or a flat float32 vector; stats:
+        (mu_in[8], s_in[8], s_out[4]) concatenated, or a dict with those keys."""
+        pv = None
+        if params is not None:
+            if isinstance(params, dict):
+                params = np.concatenate([np.asarray(params[k], np.float32).reshape(-1) for k, _ in CNN_SHAPES])
+            pv = np.ascontiguousarray(params, dtype=np.float32)
+            assert pv.size == CNN_NPARAMS
+        sv = None
+        if stats is not None:
+            if isinstance(stats, dict):
+                stats = np.concatenate([stats["mu_in"], stats["s_in"], stats["s_out"]])
+            sv = np.ascontiguousarray(stats, dtype=np.float32)
+            assert sv.size == 20
+        _check(lib.mgk_cnn_set_params(self.h, _ptr(pv), _ptr(sv)), "mgk_cnn_set_params")
+
+    def get_params(self):
+        p = np.empty(CNN_NPARAMS, np.float32)
+        g = np.empty(CNN_NPARAMS, np.float32)
+        _check(lib.mgk_cnn_get_params(self.h, _ptr(p), _ptr(g)), "mgk_cnn_get_params")
+        return p, g
+
+    def forward(self, dC, xstar, batch, residual, accumulate=False, stream=None):
+        _check(lib.mgk_cnn_forward(self.h, _ptr(dC), _ptr(xstar), batch, _ptr(residual), int(accumulate),
+                                   stream), "mgk_cnn_forward")
+
+    def loss_grad(self, dC, xstar, target, batch, loss_out=None, stream=None):
+        _check(lib.mgk_cnn_loss_grad(self.h, _ptr(dC), _ptr(xstar), _ptr(target), batch, _ptr(loss_out),
+                                     stream), "mgk_cnn_loss_grad")
+
+    def adam_step(self, lr, stream=None):
+        _check(lib.mgk_cnn_adam_step(self.h, lr, stream), "mgk_cnn_adam_step")
+
+
+def unflatten_cnn(flat):
+    out, o = {}, 0
+    for k, shp in CNN_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(flat[o:o + n], np.float64).reshape(shp)
+        o += n
+    return out
 
 
 def mgk_kernel_launches() -> int:

@@ -117,8 +117,16 @@ mgenkf_status mgenkf_forecast(mgenkf_handle h, int32_t nsteps);
  * enqueued).  Increments the analysis counter. */
 mgenkf_status mgenkf_analyse(mgenkf_handle h, const double *y_obs, const double *eps);
 
-/* x^F,a = x^F,f + Pi_F(dC) (Algorithm 4 step 5, second line). */
+/* x^F,a = x^F,f + Pi_F(dC) (Algorithm 4 step 5, second line), plus the
+ * residual of the learned correction if one is attached (mgenkf_set_prolong_cnn). */
 mgenkf_status mgenkf_prolong_correct(mgenkf_handle h);
+
+/* Attach (or, with NULL, detach) a learned correction (mgk_cnn_t of
+ * mgenkf_ops.h, passed as void*): prolong_correct then adds its residual to
+ * Pi_F(dC).  Needs MGENKF_NS2D, MGENKF_MIXED, ratio 4 and a CNN built for this
+ * handle's coarse size; otherwise MGENKF_ERR_INVALID_ARG.  The handle does not
+ * own the CNN. */
+mgenkf_status mgenkf_set_prolong_cnn(mgenkf_handle h, void *cnn);
 
 /* One whole cycle: forecast(nsteps), analyse(y_obs, NULL), prolong_correct,
  * and, if truth_fine != NULL, the relative RMSE of the fine run written to

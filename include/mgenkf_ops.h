@@ -56,6 +56,8 @@ mgenkf_status mgk_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t co
 typedef struct mgk_cnn *mgk_cnn_t;
 mgenkf_status mgk_cnn_create(int32_t n_coarse, int32_t batch_max, mgk_cnn_t *out);
 mgenkf_status mgk_cnn_destroy(mgk_cnn_t cnn);
+/* coarse points per side the object was built for (0 for NULL) */
+int32_t mgk_cnn_coarse_size(mgk_cnn_t cnn);
 /* params: 30080 floats (host or device) or NULL; stats: mu_in[8], s_in[8],
  * s_out[4] (host or device) or NULL.  Setting params resets the Adam state. */
 mgenkf_status mgk_cnn_set_params(mgk_cnn_t cnn, const float *params, const float *stats);

@@ -375,6 +375,8 @@ extern "C" mgenkf_status mgk_cnn_create(int32_t n_coarse, int32_t batch_max, mgk
     return MGENKF_OK;
 }
 
+extern "C" int32_t mgk_cnn_coarse_size(mgk_cnn_t c) { return c ? c->nc : 0; }
+
 extern "C" mgenkf_status mgk_cnn_destroy(mgk_cnn_t c) {
     if (!c) return MGENKF_OK;
     cudaDeviceSynchronize();

@@ -52,6 +52,7 @@ struct mgenkf_ctx {
     void *ns_scratch = nullptr;  // NS-2D stage buffers
     double *gemm_part = nullptr; // split-K partial sums of the gain GEMMs
     UpdateTcPlan tc;             // tensor-core member update (mixed precision)
+    mgk_cnn_t cnn = nullptr;     // learned correction added by prolong_correct (not owned)
     size_t scratch_n = 0;
     int *status = nullptr;
 };
@@ -517,6 +518,22 @@ static mgenkf_status prolong_impl(mgenkf_ctx *h) {
     else
         launch_prolong_add<double>((double *)h->fine, (const double *)h->dC, h->dim, h->V, h->nc, h->r, h->pw, h->status, h->stream);
     H_LAUNCHED();
+    if (h->cnn) {
+        mgenkf_status st = mgk_cnn_forward(h->cnn, (const float *)h->dC, (const float *)h->xstar, 1,
+                                           (float *)h->fine, 1, h->stream);
+        if (st) H_FAIL(st, std::string("learned correction: ") + mgk_last_error());
+    }
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_set_prolong_cnn(mgenkf_handle h, void *cnn) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    if (cnn && (h->cfg.model != MGENKF_NS2D || !h->mixed || h->r != 4))
+        H_FAIL(MGENKF_ERR_INVALID_ARG, "the learned correction needs an NS-2D, mixed-precision handle with ratio 4");
+    if (cnn && mgk_cnn_coarse_size((mgk_cnn_t)cnn) != h->nc)
+        H_FAIL(MGENKF_ERR_INVALID_ARG, "the learned correction was built for another coarse size");
+    h->cnn = (mgk_cnn_t)cnn;
     return MGENKF_OK;
 }
 

@@ -73,6 +73,8 @@ def _load():
         "mgk_cnn_forward": [P, P, P, i32, P, i32, P],
         "mgk_cnn_loss_grad": [P, P, P, P, i32, P, P],
         "mgk_cnn_adam_step": [P, ctypes.c_float, P],
+        "mgk_cnn_coarse_size": [P],
+        "mgenkf_set_prolong_cnn": [P, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -346,6 +348,12 @@ class MGEnKF:
         out = np.empty(n)
         mgenkf_get_field(self.h, which, out, n)
         return out
+
+    def set_prolong_cnn(self, cnn):
+        """Attach a CNN (or None) whose residual prolong_correct adds to Pi_F(dC)."""
+        _check(lib.mgenkf_set_prolong_cnn(self.h, cnn.h if cnn is not None else None),
+               "mgenkf_set_prolong_cnn", self.h)
+        self._cnn = cnn
 
     def save(self, path):
         mgenkf_save(self.h, path)

@@ -48,7 +48,11 @@ WORKLOADS = {
     # face fluxes, stage update), 3 stages per step
     "ns2d": dict(flops=600, kernel="ns2d_stage_kernel<float,*>", launches_per_step=3,
                  traffic=None, truth="fp64"),
+    # NS-2D 1024^2 / 256^2 with the learned correction of the prolongation
+    "ns2d_cnn": dict(flops=600, kernel="ns2d_stage_kernel<float,*>", launches_per_step=3,
+                     traffic=None, truth="fp64"),
 }
+CNN_FLOPS_PER_PIXEL = 2 * 9 * (8 * 32 + 32 * 32 + 32 * 64)  # three 3x3 convolutions per coarse pixel
 
 
 def parse():
@@ -62,8 +66,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="burgers_large",
-                    help="burgers_large (default: fine 16384 / coarse 4096, Ne=128) or ns2d "
-                         "(fine 512^2 / coarse 128^2, Ne=64, 2048 observations)")
+                    help="burgers_large (default: fine 16384 / coarse 4096, Ne=128), ns2d "
+                         "(fine 512^2 / coarse 128^2, Ne=64, 2048 observations) or ns2d_cnn "
+                         "(fine 1024^2 / coarse 256^2, Ne=64, learned prolongation correction)")
+    ap.add_argument("--cnn-pairs", type=int, default=400,
+                    help="training pairs generated for ns2d_cnn (cycles of lockstep runs)")
+    ap.add_argument("--cnn-epochs", type=int, default=10)
     return ap.parse_args()
 
 
@@ -436,14 +444,118 @@ def run_gpu(args, dist, w, inp):
 METRIC = {
     "burgers_large": "MGEnKF analysis cycles/s (1-D Burgers 16384/4096, Ne=128, 512 obs)",
     "ns2d": "MGEnKF analysis cycles/s (2-D NS 512^2/128^2, Ne=64, 2048 obs)",
+    "ns2d_cnn": "MGEnKF analysis cycles/s with learned prolongation (2-D NS 1024^2/256^2, Ne=64)",
 }
+
+
+def run_gpu_cnn(args, dist, w, inp):
+    """Learned-correction configuration: train on pairs from lockstep MGEnKF /
+    full-resolution EnKF runs (untimed), then time cycles with the network
+    attached to prolong_correct, and cycles with plain prolongation."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_10091_gb300 import mgenkf as M
+    from paper_2012_10091_gb300 import surrogate as S
+    from paper_2012_10091_gb300 import workloads as W
+
+    dev = dist.local % max(1, torch.cuda.device_count())
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    per_seed = 200
+    sets, seed = [], 100 + dist.rank * 1000
+    while sum(s_["dC"].shape[0] for s_ in sets) < args.cnn_pairs:
+        n = min(per_seed, args.cnn_pairs - sum(s_["dC"].shape[0] for s_ in sets))
+        ws = W.ns2d_shear(nf=w.nf, ratio=w.ratio, ne=w.ne, n_probes=w.n_probes, precision="mixed", seed=seed)
+        sets.append(S.generate_pairs(ws, n))
+        seed += 1
+    t_gen = time.perf_counter() - t0
+    train = S.concat_pairs(*sets[:-1]) if len(sets) > 1 else sets[0]
+    val = sets[-1] if len(sets) > 1 else None
+    t1 = time.perf_counter()
+    cnn, stats, hist = S.fit(train, epochs=args.cnn_epochs, batch=8, lr=3e-4, val_pairs=val)
+    t_fit = time.perf_counter() - t1
+    del sets, train, val
+    torch.cuda.empty_cache()
+
+    ncyc = args.warmup + args.steps
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        truths, yos = truth_and_obs(M, w, inp, ncyc, torch, "fp64")
+    torch.cuda.synchronize()
+    res = {}
+    for mode in ("cnn", "plain"):
+        g = M.MGEnKF.from_workload(w, stream=sp)
+        g.set_state(inp["fine0"], inp["members0"])
+        if mode == "cnn":
+            g.set_prolong_cnn(cnn)
+        rm = torch.zeros((ncyc, w.V), dtype=torch.float64, device="cuda")
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup):
+                M.mgenkf_cycle(g.h, w.steps_per_cycle, yos[k], truths[k], rm[k])
+        torch.cuda.synchronize()
+        dist.barrier()
+        clocks = ClockSampler(dev)
+        clocks.start()
+        launches0 = M.mgk_kernel_launches()
+        with torch.cuda.stream(stream):
+            for j in range(args.steps):
+                k = args.warmup + j
+                e0, e1, e2 = ev[j]
+                e0.record(stream)
+                M.mgenkf_forecast(g.h, w.steps_per_cycle)
+                M.mgenkf_analyse(g.h, yos[k])
+                e1.record(stream)
+                M.mgenkf_prolong_correct(g.h)
+                M.mgenkf_rmse(g.h, truths[k], rm[k])
+                e2.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        assert g.sync() == 0
+        tot = dist.max(sum(a.elapsed_time(c) for a, _, c in ev) / 1e3)
+        res[mode] = dict(cps=dist.sum(float(args.steps)) / tot, ms=tot / args.steps * 1e3,
+                         prolong_ms=float(np.mean([b.elapsed_time(c) for _, b, c in ev])),
+                         rmse=rm[ncyc // 2:].mean(0).cpu().numpy().tolist(), clocks=clk,
+                         launches=int(M.mgk_kernel_launches() - launches0))
+        g.close()
+    cnn.close()
+    if dist.rank == 0:
+        cnn_flops = CNN_FLOPS_PER_PIXEL * w.nc ** 2
+        line = {
+            "metric": METRIC[args.workload], "value": res["cnn"]["cps"], "unit": "cycles/s",
+            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["cnn"]["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name + "_cnn", "nf": w.nf, "nc": w.nc, "ne": w.ne, "ny": w.ny,
+                       "steps_per_cycle": w.steps_per_cycle, "precision": "mixed",
+                       "prolongation": "Pi_F + learned residual (BF16 CNN, 30080 parameters)",
+                       "training_pairs": args.cnn_pairs, "epochs": args.cnn_epochs,
+                       "l2": "inputs larger than L2 (fine state 16 MB, members 67 MB per cycle step)"},
+            "plain_prolongation": {"cycles_per_s": res["plain"]["cps"],
+                                   "prolong_ms": res["plain"]["prolong_ms"],
+                                   "rmse_last_half": res["plain"]["rmse"]},
+            "cnn": {"prolong_ms": res["cnn"]["prolong_ms"], "rmse_last_half": res["cnn"]["rmse"],
+                    "val_loss": min(hist["val"]) if hist["val"] else None,
+                    "val_loss_plain": hist["val_plain"], "gen_s": t_gen, "fit_s": t_fit,
+                    "inference_gflop": cnn_flops / 1e9,
+                    "inference_tflops": cnn_flops / (res["cnn"]["prolong_ms"] - res["plain"]["prolong_ms"]) / 1e9
+                    if res["cnn"]["prolong_ms"] > res["plain"]["prolong_ms"] else None},
+            "clocks": res["cnn"]["clocks"], "gpu_launches": res["cnn"]["launches"],
+        }
+        print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
     dist = Dist()
     from paper_2012_10091_gb300 import workloads as W
-    if args.workload == "ns2d":
+    if args.workload == "ns2d_cnn":
+        w = W.ns2d_shear(nf=1024, ratio=4, ne=64, n_probes=1024, seed=dist.rank)
+    elif args.workload == "ns2d":
         w = W.ns2d_shear(seed=dist.rank)
     else:
         w = W.burgers_large(seed=dist.rank)
@@ -451,6 +563,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, dist, w, inp)
+        elif args.workload == "ns2d_cnn":
+            run_gpu_cnn(args, dist, w, inp)
         else:
             run_gpu(args, dist, w, inp)
     finally:

@@ -74,7 +74,9 @@ def generate_pairs(w: W.Workload, cycles: int, stream=None):
         A.prolong_correct()
         M.mgenkf_rmse(A.h, truth, out)
         rm[k] = out[2]
-        assert A.sync() == 0 and B.sync() == 0
+        sa, sb = A.sync(), B.sync()
+        if sa or sb:
+            raise RuntimeError(f"analysis {k}: device status {sa} (coarse-member run), {sb} (fine-member run)")
     A.close()
     B.close()
     return dict(dC=dC, xs=xs, target=tgt, rmse=rm)

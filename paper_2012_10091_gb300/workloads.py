@@ -122,10 +122,14 @@ def ns2d_shear(nf: int = 512, ratio: int = 4, ne: int = 64, n_probes: int = 1024
                delta: float = 0.02) -> Workload:
     """2-D compressible NS, periodic [0,1]^2, Re = 1000, Mach 0.3 double shear
     layer (thickness delta, 0.02 by default) + 1e-3 N(0,1) velocity
-    perturbation, probes of (rho u, rho v) every 10 steps with sigma 0.01."""
+    perturbation, probes of (rho u, rho v) every 10 steps with sigma 0.01.
+    dt: the acoustic CFL step 0.5 sqrt(3) h / (|u| + c), capped at 0.8 of the
+    RK3 limit of heat conduction, 2.51 h^2 / (8 mu gamma / Pr) (the cap binds
+    from about 1024 points per side)."""
     mach = 0.3
     h = 1.0 / nf
-    dt = 0.5 * math.sqrt(3.0) * h / (1.0 + 1.0 / mach)
+    mu, gamma, pr = 1e-3, 1.4, 0.72
+    dt = min(0.5 * math.sqrt(3.0) * h / (1.0 + 1.0 / mach), 0.8 * 2.51 * h * h / (8.0 * mu * gamma / pr))
     return Workload(f"ns2d_{nf}_{nf // ratio}_ne{ne}_{precision}", NS2D, nf=nf, ratio=ratio, ne=ne,
                     n_probes=n_probes, sigma=0.01, steps_per_cycle=10, cycles=cycles, dt=dt,
                     length=1.0, nu=1e-3, precision=precision, seed=seed, mach=mach,

@@ -51,6 +51,11 @@ WORKLOADS = {
     # NS-2D 1024^2 / 256^2 with the learned correction of the prolongation
     "ns2d_cnn": dict(flops=600, kernel="ns2d_stage_kernel<float,*>", launches_per_step=3,
                      traffic=None, truth="fp64"),
+    # 96 independent NS-2D problems; per point-step the three stage kernels
+    # move 128 algorithmic bytes (stage 0: read u0, write s1; stages 1 and 2:
+    # read the stage input and u0, write the output; 16 B per point each)
+    "batched": dict(flops=600, bytes=128, kernel="ns2d_stage_table_kernel<float,*,*,*>",
+                    launches_per_step=3, traffic=None, truth="fp32"),
 }
 CNN_FLOPS_PER_PIXEL = 2 * 9 * (8 * 32 + 32 * 32 + 32 * 64)  # three 3x3 convolutions per coarse pixel
 
@@ -67,11 +72,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="burgers_large",
                     help="burgers_large (default: fine 16384 / coarse 4096, Ne=128), ns2d "
-                         "(fine 512^2 / coarse 128^2, Ne=64, 2048 observations) or ns2d_cnn "
-                         "(fine 1024^2 / coarse 256^2, Ne=64, learned prolongation correction)")
+                         "(fine 512^2 / coarse 128^2, Ne=64, 2048 observations), ns2d_cnn "
+                         "(fine 1024^2 / coarse 256^2, Ne=64, learned prolongation correction) or "
+                         "batched (96 independent NS-2D problems of uneven sizes, one graph launch per cycle)")
     ap.add_argument("--cnn-pairs", type=int, default=400,
                     help="training pairs generated for ns2d_cnn (cycles of lockstep runs)")
     ap.add_argument("--cnn-epochs", type=int, default=10)
+    ap.add_argument("--tiles", default=None,
+                    help="batched: JSON tile table to load (autotuned and written there if missing)")
+    ap.add_argument("--problems", type=int, default=96, help="batched: number of problems")
     return ap.parse_args()
 
 
@@ -445,7 +454,309 @@ METRIC = {
     "burgers_large": "MGEnKF analysis cycles/s (1-D Burgers 16384/4096, Ne=128, 512 obs)",
     "ns2d": "MGEnKF analysis cycles/s (2-D NS 512^2/128^2, Ne=64, 2048 obs)",
     "ns2d_cnn": "MGEnKF analysis cycles/s with learned prolongation (2-D NS 1024^2/256^2, Ne=64)",
+    "batched": "MGEnKF problem-cycles/s (96 independent 2-D NS problems, coarse 64^2..192^2, fine x4, "
+               "Ne 16..128, 256..2048 obs, one graph launch per cycle)",
 }
+
+
+# --------------------------------------------------------------------------
+# batched workload: 96 independent NS-2D problems, sharded over ranks
+# --------------------------------------------------------------------------
+def problem_work(w) -> int:
+    """Forecast points per model step (members and fine run) of one problem."""
+    return w.ne * w.nc ** 2 + w.nf ** 2
+
+
+def shard_problems(ws, world: int, rank: int) -> list:
+    """Indices of the problems rank `rank` owns: greedy balance of the
+    forecast work (largest first onto the least-loaded rank)."""
+    work = [problem_work(w) for w in ws]
+    load = [0] * world
+    owner = [0] * len(ws)
+    for i in sorted(range(len(ws)), key=lambda i: (-work[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += work[i]
+    return [i for i in range(len(ws)) if owner[i] == rank]
+
+
+def batched_cpu_estimate(ws, step_fraction: int):
+    """Oracle time of one cycle of all problems, estimated from one sampled
+    problem per coarse size (1/step_fraction of its forecast steps plus a full
+    analysis, prolongation and RMSE), scaled to each problem by its forecast
+    work.  Returns (seconds per batch cycle, description of the sample)."""
+    import oracle as O
+    from paper_2012_10091_gb300 import workloads as W
+    per_nc = {}
+    for w in ws:
+        if w.nc in per_nc:
+            continue
+        inp = W.make_inputs(w)
+        mg = O.MGEnKF(w.model, w.nf, w.ratio, w.length, w.dt, inp["fine0"], inp["members0"], inp["obs_idx"],
+                      inp["obs_var"], w.sigma, w.seed, nu=w.nu, gamma=w.gamma, prandtl=w.prandtl)
+        per_nc[w.nc] = (oracle_cycle_sample(w, inp, mg, step_fraction), problem_work(w), w.ne)
+    t = sum(per_nc[w.nc][0] * problem_work(w) / per_nc[w.nc][1] for w in ws)
+    desc = (f"one problem per coarse size ({', '.join(f'{nc}^2 Ne={v[2]}' for nc, v in sorted(per_nc.items()))}): "
+            f"{max(1, 10 // step_fraction)} of 10 RK3 steps (time scaled) plus a full FP64 analysis, "
+            f"prolongation and RMSE; each of the {len(ws)} problems scaled by its forecast points")
+    return t, desc
+
+
+def run_reference_batched(args, dist):
+    if dist.rank != 0:
+        return
+    import oracle as O
+    O.build()
+    from paper_2012_10091_gb300 import workloads as W
+    ws = W.ns2d_batch(args.problems, seed=0)
+    times, desc = [], ""
+    for j in range(args.warmup + args.steps):
+        t, desc = batched_cpu_estimate(ws, 10)
+        if j >= args.warmup:
+            times.append(t)
+    per = float(np.mean(times))
+    val = len(ws) / per
+    line = {"metric": METRIC["batched"], "value": val, "unit": "problem-cycles/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"ns2d_batch{len(ws)}_seed0", "problems": len(ws), "steps_per_cycle": 10,
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": "problem-cycles/s", "kind": "oracle", "cores": cpu_threads(),
+                             "sample": desc},
+            "e2e": {"value": val, "unit": "problem-cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu_batched(args, dist):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_10091_gb300 import mgenkf as M
+    from paper_2012_10091_gb300 import workloads as W
+
+    dev = dist.local % max(1, torch.cuda.device_count())
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    ws_all = W.ns2d_batch(args.problems, seed=0)
+    mine = shard_problems(ws_all, dist.world, dist.rank)
+    ws = [ws_all[i] for i in mine]
+    ncyc = args.warmup + args.steps
+    nsteps = 10
+
+    # handles (inputs generated and uploaded one problem at a time)
+    runs, layouts, truth0 = [], [], []
+    for w in ws:
+        inp = W.make_inputs(w)
+        g = M.MGEnKF.from_workload(w, stream=sp)
+        g.set_state(inp["fine0"], inp["members0"])
+        runs.append(g)
+        layouts.append((inp["obs_idx"], inp["obs_var"]))
+        truth0.append(inp["truth0"])
+        del inp
+    torch.cuda.synchronize()
+
+    # synthetic observations: FP32 truth runs (one forecast per fine size),
+    # sampled at each problem's probes plus N(0, sigma^2) noise; resident in HBM
+    ny_tot = sum(w.ny for w in ws)
+    yos = torch.empty((ncyc, ny_tot), dtype=torch.float64, device="cuda")
+    by_nf = {}
+    for j, w in enumerate(ws):
+        by_nf.setdefault(w.nf, []).append(j)
+    truths = {nf: torch.tensor(np.stack([truth0[j] for j in js]), dtype=torch.float32, device="cuda")
+              for nf, js in by_nf.items()}
+    off = np.cumsum([0] + [w.ny for w in ws])
+    gidx = {}
+    for nf, js in by_nf.items():
+        rows = []
+        for q, j in enumerate(js):
+            oi, ov = layouts[j]
+            rows.append(torch.tensor(q * 4 * nf * nf + ov.astype(np.int64) * nf * nf + oi, device="cuda"))
+        gidx[nf] = rows
+    with torch.cuda.stream(stream):
+        for k in range(ncyc):
+            for nf, js in by_nf.items():
+                w0 = ws[js[0]]
+                M.mgk_forecast(M.MGENKF_NS2D, M.MGENKF_MIXED, truths[nf], len(js), nf, w0.length, w0.dt, w0.nu,
+                               w0.gamma, w0.prandtl, nsteps=nsteps, stream=sp)
+                flat = truths[nf].view(-1)
+                for q, j in enumerate(js):
+                    yos[k, off[j]:off[j + 1]] = flat[gidx[nf][q]].double()
+            noise = np.concatenate([W.observation_noise(w, k) for w in ws])
+            yos[k] += torch.tensor(noise, device="cuda")
+    torch.cuda.synchronize()
+    del truths
+
+    b = M.Batch(runs, stream=sp)
+    t_tune = time.perf_counter()
+    if args.tiles and os.path.exists(args.tiles):
+        b.load_tiles(args.tiles)
+        tuned = "loaded"
+    else:
+        b.autotune(reps=3)
+        tuned = "autotuned"
+        if args.tiles:
+            b.save_tiles(args.tiles)
+    t_tune = time.perf_counter() - t_tune
+    tiles = b.tiles()
+    innov = torch.zeros((ncyc, len(ws)), dtype=torch.float64, device="cuda")
+    launches0 = M.mgk_kernel_launches()
+    b.cycle(nsteps, yos[0], innov[0])          # captures the graph
+    launches_per_cycle = M.mgk_kernel_launches() - launches0
+    for k in range(1, args.warmup):
+        b.cycle(nsteps, yos[k], innov[k])
+    assert b.sync() == 0
+
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    for j in range(args.steps):
+        k = args.warmup + j
+        b.cycle(nsteps, yos[k], innov[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    wall = time.perf_counter() - wall0
+    dist.barrier()
+    clk = clocks.stop()
+    st = b.sync()
+    if st:
+        raise RuntimeError(f"batched run: device status {st}")
+    t_total = e0.elapsed_time(e1) / 1e3
+    t_max = dist.max(t_total)
+    pc_all = dist.sum(float(len(ws) * args.steps))
+    value = pc_all / t_max
+    innov_h = innov.cpu().numpy()
+
+    # forecast alone (all problems, one cycle's steps), for the stencil roofline
+    fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    b.forecast(nsteps)
+    fa.record(stream)
+    for _ in range(reps):
+        b.forecast(nsteps)
+    fb.record(stream)
+    torch.cuda.synchronize()
+    fc_s = fa.elapsed_time(fb) / 1e3 / reps
+    spec = WORKLOADS["batched"]
+    pts = sum(problem_work(w) for w in ws)
+    n_launch = spec["launches_per_step"] * nsteps * len(set(tiles[w.nc] for w in ws) | set(tiles[w.nf] for w in ws))
+    bytes_fc = spec["bytes"] * pts * nsteps
+    peaks, peak_src = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_fc / fc_s / 1e9
+
+    # e2e: observations from pinned host memory, innovation RMS read back each cycle
+    e2e = None
+    if not args.no_e2e:
+        y_h = torch.empty((ncyc, ny_tot), dtype=torch.float64, pin_memory=True)
+        y_h.copy_(yos.cpu())
+        o_h = torch.empty((ncyc, len(ws)), dtype=torch.float64, pin_memory=True)
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in range(args.steps):
+            k = args.warmup + j
+            b.cycle(nsteps, y_h[k], o_h[k])
+            stream.synchronize()                     # the cycle's innovation RMS is on the host
+        te = dist.max(time.perf_counter() - t0)
+        assert b.sync() == 0
+        e2e = {"value": pc_all / te, "unit": "problem-cycles/s", "h2d_bytes_per_step": 8 * ny_tot,
+               "d2h_bytes_per_step": 8 * len(ws)}
+
+    # plain FP64 against mixed precision on one problem per coarse size, lockstep
+    # with an FP64 truth run, RMSE of the fine run
+    fp64 = None
+    if args.fp64_cycles > 0 and dist.rank == 0:
+        sample = {}
+        for w in ws_all:
+            sample.setdefault(w.nc, w)
+        rows = []
+        for nc, w in sorted(sample.items()):
+            inp = W.make_inputs(w)
+            g64 = M.MGEnKF.from_workload(w, precision="fp64", stream=sp)
+            gm = M.MGEnKF.from_workload(w, precision="mixed", stream=sp)
+            for g in (g64, gm):
+                g.set_state(inp["fine0"], inp["members0"])
+            tr = torch.tensor(inp["truth0"], dtype=torch.float64, device="cuda")
+            idx = torch.tensor(inp["obs_var"].astype(np.int64) * w.nf ** 2 + inp["obs_idx"], device="cuda")
+            r64 = torch.zeros((args.fp64_cycles, 4), dtype=torch.float64, device="cuda")
+            rmx = torch.zeros_like(r64)
+            ta, tb, tc = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            t64 = tmx = 0.0
+            with torch.cuda.stream(stream):
+                for k in range(args.fp64_cycles):
+                    M.mgk_forecast(M.MGENKF_NS2D, M.MGENKF_FP64, tr, 1, w.nf, w.length, w.dt, w.nu, w.gamma,
+                                   w.prandtl, nsteps=nsteps, stream=sp)
+                    yo = tr[idx] + torch.tensor(W.observation_noise(w, k), device="cuda")
+                    ta.record(stream)
+                    M.mgenkf_cycle(g64.h, nsteps, yo, tr, r64[k])
+                    tb.record(stream)
+                    M.mgenkf_cycle(gm.h, nsteps, yo, tr, rmx[k])
+                    tc.record(stream)
+                    tc.synchronize()
+                    t64 += ta.elapsed_time(tb)
+                    tmx += tb.elapsed_time(tc)
+            assert g64.sync() == 0 and gm.sync() == 0
+            half = slice(args.fp64_cycles // 2, args.fp64_cycles)
+            a, m_ = float(r64[half, 0].mean()), float(rmx[half, 0].mean())
+            rows.append({"problem": w.name, "rmse_fp64": a, "rmse_mixed": m_, "rmse_rel_diff": abs(m_ - a) / a,
+                         "fp64_ms_per_cycle": t64 / args.fp64_cycles, "mixed_ms_per_cycle": tmx / args.fp64_cycles})
+            g64.close()
+            gm.close()
+        fp64 = {"cycles": args.fp64_cycles, "problems": rows,
+                "max_rmse_rel_diff": max(r["rmse_rel_diff"] for r in rows)}
+
+    b.close()
+    for g in runs:
+        g.close()
+
+    if dist.rank == 0:
+        line = {
+            "metric": METRIC["batched"], "value": value, "unit": "problem-cycles/s", "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"ns2d_batch{len(ws_all)}_seed0", "problems": len(ws_all),
+                       "problems_rank0": len(ws), "steps_per_cycle": nsteps, "precision": "mixed",
+                       "gain_form": "ensemble-space", "tiles": {str(k): list(M.TILE_SHAPES[v]) for k, v in
+                                                                sorted(tiles.items())},
+                       "tile_table": tuned, "autotune_s": t_tune,
+                       "l2": f"not flushed: working set {sum(4 * 4 * (3 * problem_work(w)) for w in ws) / 1e9:.2f} GB "
+                             f"(states + stage buffers) > L2 (129 MB)"},
+            "batch_cycles_per_s": args.steps / t_total,
+            "member_steps_per_s": value / len(ws_all) * sum(w.ne for w in ws_all) * nsteps,
+            "forecast_ms_per_cycle": fc_s * 1e3,
+            "analysis_ms_per_cycle": (t_total / args.steps - fc_s) * 1e3,
+            "kernels_per_cycle": int(launches_per_cycle),
+            "innovation_rms_mean_last": float(innov_h[-1].mean()),
+            "roofline": {"bound": "hbm", "kernel": spec["kernel"], "achieved": achieved, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": spec["traffic"],
+                         "scope": f"all stage launches of one forecast ({n_launch} launches, {nsteps} steps), "
+                                  f"{spec['bytes']} B per point-step",
+                         "peak_source": f"hbm_gbs ({peak_src})",
+                         "fp32_tflops": spec["flops"] * pts * nsteps / fc_s / 1e12},
+            "fp64_plain": fp64,
+            "clocks": clk,
+            "gpu_launches": int(launches_per_cycle * args.steps),
+            "wall_s_timed": wall,
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if not args.no_cpu_baseline:
+            import oracle as O
+            O.build()
+            t, desc = batched_cpu_estimate(ws_all, 10)
+            line["cpu_baseline"] = {"value": len(ws_all) / t, "unit": "problem-cycles/s", "cores": cpu_threads(),
+                                    "kind": "oracle", "sample": desc}
+        print(json.dumps(line), flush=True)
 
 
 def run_gpu_cnn(args, dist, w, inp):
@@ -553,6 +864,15 @@ def main():
     args = parse()
     dist = Dist()
     from paper_2012_10091_gb300 import workloads as W
+    if args.workload == "batched":
+        try:
+            if args.impl == "reference":
+                run_reference_batched(args, dist)
+            else:
+                run_gpu_batched(args, dist)
+        finally:
+            dist.close()
+        return
     if args.workload == "ns2d_cnn":
         w = W.ns2d_shear(nf=1024, ratio=4, ne=64, n_probes=1024, seed=dist.rank)
     elif args.workload == "ns2d":

@@ -173,6 +173,42 @@ const char *mgenkf_last_error(mgenkf_handle h);
 /* Free every device buffer and the handle.  NULL is accepted. */
 mgenkf_status mgenkf_destroy(mgenkf_handle h);
 
+/* ---- batches of independent problems -------------------------------------
+ * Many independent NS-2D MGEnKF problems (uneven grid sizes, ensemble sizes
+ * and observation counts) advanced together: the forecast of every problem's
+ * members and fine run is one launch sequence per tile shape over a table of
+ * all grids, and each problem's analysis and prolongation run on one of 16
+ * streams.  The whole cycle is captured once into a CUDA graph and replayed by
+ * one graph launch per cycle (recaptured if nsteps changes).  The handles stay
+ * owned by the caller and must outlive the batch; they must all be
+ * MGENKF_NS2D / MGENKF_MIXED with equal gamma, mu and Pr.  While a batch
+ * exists its handles must not be used on their own. */
+typedef struct mgenkf_batch *mgenkf_batch_t;
+/* stream: the stream the batch launches on (cudaStream_t; NULL = a stream
+ * the batch creates, ordered with the legacy default stream) */
+mgenkf_status mgenkf_batch_create(const mgenkf_handle *handles, int32_t n, void *stream, mgenkf_batch_t *out);
+/* One cycle of every problem: forecast(nsteps), analysis with the observations
+ * y_obs (all problems' n_obs values concatenated in handle order; host or
+ * device; copied before the graph launch) and prolongation (Algorithm 4).
+ * innov_out (NULL, or n doubles, host or device): per problem the RMS of the
+ * innovation y^o - H^C x^C* of this cycle's fine forecast, copied after the
+ * cycle (a pageable host buffer makes the call wait for it).  Otherwise
+ * asynchronous. */
+mgenkf_status mgenkf_batch_cycle(mgenkf_batch_t b, int32_t nsteps, const double *y_obs, double *innov_out);
+/* the forecast part alone, not captured (used to time it) */
+mgenkf_status mgenkf_batch_forecast(mgenkf_batch_t b, int32_t nsteps);
+/* wait for the batch stream; returns the first device status of any problem */
+mgenkf_status mgenkf_batch_sync(mgenkf_batch_t b);
+/* Autotuner: for every grid size time `reps` repetitions of the first two RK
+ * stages (which write only scratch) with each tile shape (0 = 32x8, 1 = 16x16,
+ * 2 = 64x4) and keep the fastest.  Synchronous; invalidates the captured graph. */
+mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps);
+/* read (up to max entries) / set the tile shape chosen per grid size */
+mgenkf_status mgenkf_batch_tiles(mgenkf_batch_t b, int32_t *sizes, int32_t *shapes, int32_t max, int32_t *count);
+mgenkf_status mgenkf_batch_set_tiles(mgenkf_batch_t b, const int32_t *sizes, const int32_t *shapes, int32_t count);
+const char *mgenkf_batch_last_error(mgenkf_batch_t b);
+mgenkf_status mgenkf_batch_destroy(mgenkf_batch_t b);
+
 #ifdef __cplusplus
 }
 #endif

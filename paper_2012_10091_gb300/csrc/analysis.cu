@@ -111,18 +111,37 @@ void launch_obs_mean(const double *yf, const double *yo, int ne, int ny, double 
     k_obs_mean<<<ceil_div(ny, 32), 256, 0, s>>>(yf, yo, ne, ny, ybar, Z, status);
 }
 
+// RMS of the innovation d* = y^o - H^C x^C* (one value; fixed-order FP64 sums)
+__global__ void __launch_bounds__(256) k_innov_rms(const double *__restrict__ d, int ny, double *__restrict__ out) {
+    __shared__ double part[256];
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < ny; j += 256) acc = fma(d[j], d[j], acc);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sqrt(part[0] / ny);
+}
+
+void launch_innov_rms(const double *Z, int ne, int ny, double *out, cudaStream_t s) {
+    k_innov_rms<<<1, 256, 0, s>>>(Z + (size_t)ne * ny, ny, out);
+    count_launches(1);
+}
+
 // perturbed observations (Eq. perturbed_y) and normalised anomalies Y (Algorithm 3 step 7)
 __global__ void k_obs_perturb(const double *__restrict__ yf, const double *__restrict__ ybar,
                               const double *__restrict__ yo, double *__restrict__ eps, int gen_eps,
-                              uint64_t seed, uint64_t cycle, double sigma, int ne, int ny,
-                              double *__restrict__ Y, double *__restrict__ Z) {
+                              uint64_t seed, const uint64_t *__restrict__ cycle, double sigma, int ne,
+                              int ny, double *__restrict__ Y, double *__restrict__ Z) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= ny) return;
     const size_t o = (size_t)i * ny + j;
     double e;
     if (gen_eps) {
-        e = sigma * philox_normal(seed, kEpsTag, cycle, (uint64_t)o);
+        e = sigma * philox_normal(seed, kEpsTag, *cycle, (uint64_t)o);
         eps[o] = e;
     } else {
         e = eps[o];
@@ -133,7 +152,7 @@ __global__ void k_obs_perturb(const double *__restrict__ yf, const double *__res
 }
 
 void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, double *eps,
-                        int gen_eps, uint64_t seed, uint64_t cycle, double sigma, int ne, int ny,
+                        int gen_eps, uint64_t seed, const uint64_t *cycle, double sigma, int ne, int ny,
                         double *Y, double *Z, cudaStream_t s) {
     count_launches(1);
     dim3 grid(ceil_div(ny, 128), ne);
@@ -786,6 +805,15 @@ void launch_convert(const Tin *in, Tout *out, size_t n, cudaStream_t s) {
     if (n == 0) return;
     count_launches(1);
     k_convert<Tin, Tout><<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+}
+
+// the analysis counter that keys the perturbation stream lives on the device,
+// so a captured cycle advances it on every replay
+__global__ void k_bump_counter(uint64_t *c) { *c += 1; }
+
+void launch_bump_counter(uint64_t *c, cudaStream_t s) {
+    count_launches(1);
+    k_bump_counter<<<1, 1, 0, s>>>(c);
 }
 
 __global__ void k_tt_bf16(const double *__restrict__ Tm, __nv_bfloat16 *__restrict__ Tt, int ne,

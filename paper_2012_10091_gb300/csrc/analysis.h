@@ -33,9 +33,13 @@ void launch_obs_mean(const double *yf, const double *yo, int ne, int ny, double 
                      int *status, cudaStream_t s);
 
 // eps (drawn or given), Y = (yf - ybar)/sqrt(ne-1), Z[i] = yo + eps_i - yf_i.
+// cycle: device pointer to the analysis counter (Philox counter word 0)
+// RMS over the ny innovations d* = y^o - H^C x^C* (row ne of Z) into out[0]
+void launch_innov_rms(const double *Z, int ne, int ny, double *out, cudaStream_t s);
 void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, double *eps,
-                        int gen_eps, uint64_t seed, uint64_t cycle, double sigma, int ne, int ny,
+                        int gen_eps, uint64_t seed, const uint64_t *cycle, double sigma, int ne, int ny,
                         double *Y, double *Z, cudaStream_t s);
+void launch_bump_counter(uint64_t *c, cudaStream_t s);
 
 // normalised state anomalies X (Eq. Ensemble_Anomaly); FP64 [ne][nx] or BF16 [nx][ne].
 template <typename T>

@@ -31,34 +31,25 @@
 namespace mgk {
 
 constexpr int kNsTx = 32, kNsTy = 8;
-constexpr int kNsHx = kNsTx + 2, kNsHy = kNsTy + 2, kNsHalo = kNsHx * kNsHy;
-
-template <typename T>
-struct NsGroup {
-    T *u0, *s1, *s2;  // nprob states of 4 n^2 values each
-    int n, nprob, tx, ty;  // tiles per side
-    T inv_h, inv_2h;
-};
 
 template <typename T>
 struct NsArgs {
     NsGroup<T> g[2];
     int tiles0;  // tiles of group 0
-    T dt, gm1, mu, kappa;
+    T gm1, mu, kappa;
 };
 
-template <typename T, int STAGE>
-__global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
-    __shared__ T sq[4][kNsHalo];   // conserved variables of the tile + halo
-    __shared__ T spr[4][kNsHalo];  // u, v, p, T
-    int tile = blockIdx.x;
-    const int gi = tile < A.tiles0 ? 0 : 1;
-    if (gi) tile -= A.tiles0;
-    const NsGroup<T> G = gi ? A.g[1] : A.g[0];  // no runtime index into the parameter array
+// The stencil body is written for a tile shape TX x TY (TX * TY = 256
+// threads); the batched path picks the shape per grid size (autotuned).
+template <typename T, int STAGE, int TX, int TY>
+__device__ __forceinline__ void ns2d_stage_tile(const NsGroup<T> &G, int tile, T gm1, T mu, T kap) {
+    constexpr int HX = TX + 2, HY = TY + 2, HALO = HX * HY;
+    __shared__ T sq[4][HALO];   // conserved variables of the tile + halo
+    __shared__ T spr[4][HALO];  // u, v, p, T
     const int tiles_per_prob = G.tx * G.ty;
     const int prob = tile / tiles_per_prob;
     const int tt = tile % tiles_per_prob;
-    const int x0 = (tt % G.tx) * kNsTx, y0 = (tt / G.tx) * kNsTy;
+    const int x0 = (tt % G.tx) * TX, y0 = (tt / G.tx) * TY;
     const int n = G.n;
     const size_t plane = (size_t)n * n;
     T *u0 = G.u0 + (size_t)prob * 4 * plane;
@@ -67,8 +58,8 @@ __global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
                         : (STAGE == 1 ? G.s2 + (size_t)prob * 4 * plane : u0);
 
     // load the tile and its halo, form the primitives
-    for (int e = threadIdx.x; e < kNsHalo; e += blockDim.x) {
-        const int ly = e / kNsHx, lx = e % kNsHx;
+    for (int e = threadIdx.x; e < HALO; e += blockDim.x) {
+        const int ly = e / HX, lx = e % HX;
         int gy = y0 + ly - 1, gx = x0 + lx - 1;  // periodic wrap without integer division
         if (gy < 0) gy += n;
         if (gx < 0) gx += n;
@@ -78,7 +69,7 @@ __global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
         const T rho = in[o], mx = in[plane + o], my = in[2 * plane + o], E = in[3 * plane + o];
         const T rinv = T(1) / rho;  // one division per point
         const T u = mx * rinv, v = my * rinv;
-        const T p = A.gm1 * (E - T(0.5) * rho * (u * u + v * v));
+        const T p = gm1 * (E - T(0.5) * rho * (u * u + v * v));
         sq[0][e] = rho;
         sq[1][e] = mx;
         sq[2][e] = my;
@@ -89,15 +80,14 @@ __global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
         spr[3][e] = p * rinv;
     }
     __syncthreads();
-    const int lx = threadIdx.x % kNsTx, ly = threadIdx.x / kNsTx;
+    const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
     const int x = x0 + lx, y = y0 + ly;
     if (x >= n || y >= n) return;
-    const int c = (ly + 1) * kNsHx + (lx + 1);
-    const int e_ = c + 1, w_ = c - 1, n_ = c + kNsHx, s_ = c - kNsHx;
+    const int c = (ly + 1) * HX + (lx + 1);
+    const int e_ = c + 1, w_ = c - 1, n_ = c + HX, s_ = c - HX;
     const T *U = spr[0], *V = spr[1], *P = spr[2], *TT = spr[3];
-    const T ih = G.inv_h, i2h = G.inv_2h, mu = A.mu, kap = A.kappa;
+    const T ih = G.inv_h, i2h = G.inv_2h;
     const T c43 = T(4.0 / 3.0), c23 = T(2.0 / 3.0), half = T(0.5);
-
     // inviscid part: central differences of the nodal fluxes
     T r[4];
     {
@@ -120,8 +110,8 @@ __global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
         {   // x-face between columns a = x-1+side and b = a+1
             const int a = side ? c : w_, b = side ? e_ : c;
             const T ux = (U[b] - U[a]) * ih, vx = (V[b] - V[a]) * ih;
-            const T uy = half * ((U[a + kNsHx] - U[a - kNsHx]) + (U[b + kNsHx] - U[b - kNsHx])) * i2h;
-            const T vy = half * ((V[a + kNsHx] - V[a - kNsHx]) + (V[b + kNsHx] - V[b - kNsHx])) * i2h;
+            const T uy = half * ((U[a + HX] - U[a - HX]) + (U[b + HX] - U[b - HX])) * i2h;
+            const T vy = half * ((V[a + HX] - V[a - HX]) + (V[b + HX] - V[b - HX])) * i2h;
             const T txx = mu * (c43 * ux - c23 * vy), txy = mu * (uy + vx);
             const T uf = half * (U[a] + U[b]), vf = half * (V[a] + V[b]);
             fx[side][0] = txx;
@@ -149,7 +139,7 @@ __global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
     const size_t o = (size_t)y * n + x;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const T kq = A.dt * L[k];
+        const T kq = G.dt * L[k];
         const T s = sq[k][c];
         T res;
         if (STAGE == 0) {
@@ -160,6 +150,34 @@ __global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
         }
         out[k * plane + o] = res;
     }
+}
+
+// per-handle launch: two groups (members, fine run) passed by value, 32 x 8 tiles
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
+    int tile = blockIdx.x;
+    const int gi = tile < A.tiles0 ? 0 : 1;
+    if (gi) tile -= A.tiles0;
+    const NsGroup<T> G = gi ? A.g[1] : A.g[0];  // no runtime index into the parameter array
+    ns2d_stage_tile<T, STAGE, 32, 8>(G, tile, A.gm1, A.mu, A.kappa);
+}
+
+// batched launch: a table of groups in device memory, found by binary search
+// on the first tile of each group
+template <typename T, int STAGE, int TX, int TY>
+__global__ void __launch_bounds__(256) ns2d_stage_table_kernel(const NsGroup<T> *__restrict__ groups,
+                                                               int ngroups, T gm1, T mu, T kappa) {
+    const int tile = blockIdx.x;
+    int lo = 0, hi = ngroups - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (groups[mid].tile_begin <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const NsGroup<T> G = groups[lo];
+    ns2d_stage_tile<T, STAGE, TX, TY>(G, tile - G.tile_begin, gm1, mu, kappa);
 }
 
 const char *ns2d_check_size(int n_whole, int n_split) {
@@ -198,11 +216,11 @@ cudaError_t ns2d_forecast_scratch(T *whole, int n_whole, int n_whole_probs, T *s
             const double h = length / ns[g];
             G.inv_h = (T)(1.0 / h);
             G.inv_2h = (T)(1.0 / (2.0 * h));
+            G.dt = (T)dt;
             tiles[g] = G.tx * G.ty * np[g];
         }
     }
     A.tiles0 = tiles[0];
-    A.dt = (T)dt;
     A.gm1 = (T)(gamma - 1.0);
     A.mu = (T)mu;
     A.kappa = (T)(mu * gamma / ((gamma - 1.0) * prandtl));
@@ -233,11 +251,64 @@ cudaError_t ns2d_forecast(T *whole, int n_whole, int n_whole_probs, T *split, in
     return e != cudaSuccess ? e : e2;
 }
 
+int ns2d_tile_x(int shape) { return shape == 1 ? 16 : (shape == 2 ? 64 : 32); }
+int ns2d_tile_y(int shape) { return shape == 1 ? 16 : (shape == 2 ? 4 : 8); }
+
+template <typename T, int TX, int TY>
+static void launch_table(const NsGroup<T> *groups, int ngroups, int tiles, int nsteps, T gm1, T mu, T kappa,
+                         cudaStream_t s) {
+    for (int st = 0; st < nsteps; ++st) {
+        ns2d_stage_table_kernel<T, 0, TX, TY><<<tiles, 256, 0, s>>>(groups, ngroups, gm1, mu, kappa);
+        ns2d_stage_table_kernel<T, 1, TX, TY><<<tiles, 256, 0, s>>>(groups, ngroups, gm1, mu, kappa);
+        ns2d_stage_table_kernel<T, 2, TX, TY><<<tiles, 256, 0, s>>>(groups, ngroups, gm1, mu, kappa);
+        count_launches(3);
+    }
+}
+
+template <typename T>
+cudaError_t ns2d_forecast_table(const NsGroup<T> *d_groups, int ngroups, int tiles, int shape, int nsteps,
+                                double gamma, double mu, double prandtl, cudaStream_t s) {
+    if (tiles == 0 || nsteps == 0) return cudaSuccess;
+    const T gm1 = (T)(gamma - 1.0), m = (T)mu, kap = (T)(mu * gamma / ((gamma - 1.0) * prandtl));
+    if (shape == 1)
+        launch_table<T, 16, 16>(d_groups, ngroups, tiles, nsteps, gm1, m, kap, s);
+    else if (shape == 2)
+        launch_table<T, 64, 4>(d_groups, ngroups, tiles, nsteps, gm1, m, kap, s);
+    else
+        launch_table<T, 32, 8>(d_groups, ngroups, tiles, nsteps, gm1, m, kap, s);
+    return cudaGetLastError();
+}
+
+template <typename T, int TX, int TY>
+static void launch_probe01(const NsGroup<T> *groups, int ngroups, int tiles, T gm1, T mu, T kappa, cudaStream_t s) {
+    ns2d_stage_table_kernel<T, 0, TX, TY><<<tiles, 256, 0, s>>>(groups, ngroups, gm1, mu, kappa);
+    ns2d_stage_table_kernel<T, 1, TX, TY><<<tiles, 256, 0, s>>>(groups, ngroups, gm1, mu, kappa);
+    count_launches(2);
+}
+
+template <typename T>
+cudaError_t ns2d_probe_stages01(const NsGroup<T> *d_groups, int ngroups, int tiles, int shape, double gamma,
+                                double mu, double prandtl, cudaStream_t s) {
+    if (tiles == 0) return cudaSuccess;
+    const T gm1 = (T)(gamma - 1.0), m = (T)mu, kap = (T)(mu * gamma / ((gamma - 1.0) * prandtl));
+    if (shape == 1)
+        launch_probe01<T, 16, 16>(d_groups, ngroups, tiles, gm1, m, kap, s);
+    else if (shape == 2)
+        launch_probe01<T, 64, 4>(d_groups, ngroups, tiles, gm1, m, kap, s);
+    else
+        launch_probe01<T, 32, 8>(d_groups, ngroups, tiles, gm1, m, kap, s);
+    return cudaGetLastError();
+}
+
 #define MGK_NS_INST(T)                                                                            \
     template cudaError_t ns2d_forecast<T>(T *, int, int, T *, int, int, double, double, double,    \
                                           double, double, int, cudaStream_t);                     \
     template cudaError_t ns2d_forecast_scratch<T>(T *, int, int, T *, int, int, double, double,    \
-                                                  double, double, double, int, T *, cudaStream_t);
+                                                  double, double, double, int, T *, cudaStream_t); \
+    template cudaError_t ns2d_forecast_table<T>(const NsGroup<T> *, int, int, int, int, double, double, \
+                                                double, cudaStream_t);                                 \
+    template cudaError_t ns2d_probe_stages01<T>(const NsGroup<T> *, int, int, int, double, double, double, \
+                                                cudaStream_t);
 MGK_NS_INST(float)
 MGK_NS_INST(double)
 #undef MGK_NS_INST

@@ -5,6 +5,26 @@
 
 namespace mgk {
 
+// one set of grids of the same size advanced by a stage launch
+template <typename T>
+struct NsGroup {
+    T *u0, *s1, *s2;       // nprob states of 4 n^2 values each, and the two stage buffers
+    int n, nprob, tx, ty;  // points per side, grids, tiles per side
+    int tile_begin;        // first tile of this group in a launch over several groups
+    T inv_h, inv_2h, dt;
+};
+
+// tile shapes of the batched stage kernel: 0 = 32 x 8, 1 = 16 x 16, 2 = 64 x 4
+constexpr int kNsTileShapes = 3;
+int ns2d_tile_x(int shape);
+int ns2d_tile_y(int shape);
+
+// nsteps SSP-RK3 steps of every group of a device table (tile_begin ascending,
+// all tiles of the given shape).
+template <typename T>
+cudaError_t ns2d_forecast_table(const NsGroup<T> *d_groups, int ngroups, int tiles, int shape, int nsteps,
+                                double gamma, double mu, double prandtl, cudaStream_t s);
+
 // NULL if grids of n_whole (one member per CTA group) and n_split points per
 // side can be advanced, else the reason.
 const char *ns2d_check_size(int n_whole, int n_split);
@@ -26,5 +46,10 @@ template <typename T>
 cudaError_t ns2d_forecast(T *whole, int n_whole, int n_whole_probs, T *split, int n_split,
                           int n_split_probs, double length, double dt, double mu, double gamma,
                           double prandtl, int nsteps, cudaStream_t stream);
+
+// stages 0 and 1 only (they leave the states untouched): timing probe of the autotuner
+template <typename T>
+cudaError_t ns2d_probe_stages01(const NsGroup<T> *d_groups, int ngroups, int tiles, int shape, double gamma,
+                                double mu, double prandtl, cudaStream_t s);
 
 }  // namespace mgk

@@ -55,6 +55,7 @@ struct mgenkf_ctx {
     mgk_cnn_t cnn = nullptr;     // learned correction added by prolong_correct (not owned)
     size_t scratch_n = 0;
     int *status = nullptr;
+    uint64_t *cycle_d = nullptr;  // analysis counter on the device (keys the perturbation stream)
 };
 
 // ---------------------------------------------------------------------------
@@ -126,7 +127,7 @@ static void free_all(mgenkf_ctx *h) {
     void *ptrs[] = {h->fine, h->members, h->xstar, h->dC, h->tap_idx, h->tap_w, h->yf, h->yo,
                     h->ybar, h->eps, h->Y, h->Z, h->X64, h->X16, h->Tt, h->S, h->Lt, h->Bt, h->C,
                     h->Ct, h->W, h->truth_d, h->rmse_part, h->rmse_d, h->scratch, h->status,
-                    h->ns_scratch, h->gemm_part};
+                    h->ns_scratch, h->gemm_part, h->cycle_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->Tm && h->Tm != h->Bt) cudaFree(h->Tm);
@@ -293,6 +294,8 @@ static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const 
     H_ALLOC(h->rmse_d, 4 * sizeof(double));
     H_ALLOC(h->status, sizeof(int));
     H_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    H_ALLOC(h->cycle_d, sizeof(uint64_t));
+    H_CUDA(cudaMemsetAsync(h->cycle_d, 0, sizeof(uint64_t), h->stream));
     H_CUDA(cudaMemsetAsync(h->fine, 0, h->nxf * ts, h->stream));
     H_CUDA(cudaMemsetAsync(h->members, 0, ne * nx * ts, h->stream));
     H_CUDA(cudaMemsetAsync(h->dC, 0, nx * ts, h->stream));
@@ -392,6 +395,7 @@ extern "C" mgenkf_status mgenkf_set_state(mgenkf_handle h, const double *fine, c
         if (st) return st;
     }
     h->cycle = 0;
+    H_CUDA(cudaMemsetAsync(h->cycle_d, 0, sizeof(uint64_t), h->stream));
     H_CUDA(cudaStreamSynchronize(h->stream));
     return MGENKF_OK;
 }
@@ -459,7 +463,7 @@ static void analyse_kernels(mgenkf_ctx *h, int gen_eps) {
     launch_restrict<T>((const T *)h->fine, xstar, h->dim, h->V, h->nc, h->r, s);
     launch_obs_apply<T>(members, xstar, nx, ne, ny, h->taps, h->tap_idx, h->tap_w, h->yf, s);
     launch_obs_mean(h->yf, h->yo, ne, ny, h->ybar, h->Z, h->status, s);
-    launch_obs_perturb(h->yf, h->ybar, h->yo, h->eps, gen_eps, h->cfg.seed, h->cycle,
+    launch_obs_perturb(h->yf, h->ybar, h->yo, h->eps, gen_eps, h->cfg.seed, h->cycle_d,
                        h->cfg.obs_sigma, ne, ny, h->Y, h->Z, s);
     launch_ens_anom<T>(members, nx, ne, h->X64, h->X16, h->status, s);
     const double s2 = h->cfg.obs_sigma * h->cfg.obs_sigma;
@@ -485,6 +489,7 @@ static void analyse_kernels(mgenkf_ctx *h, int gen_eps) {
         launch_update_bf16((float *)members, (float *)dC, h->X16, h->Tt, h->ldx, nx, ne, h->status, s);
     else
         launch_update_f64<T>(members, dC, h->X64, h->Tm, nx, ne, h->status, s);
+    launch_bump_counter(h->cycle_d, s);
 }
 
 static mgenkf_status analyse_impl(mgenkf_ctx *h, const double *y_obs, const double *eps) {
@@ -647,7 +652,7 @@ extern "C" mgenkf_status mgenkf_save(mgenkf_handle h, const char *path) {
     hd.n_members = h->ne;
     hd.n_obs = h->ny;
     hd.precision = h->cfg.precision;
-    hd.cycle = h->cycle;
+    H_CUDA(cudaMemcpy(&hd.cycle, h->cycle_d, sizeof(uint64_t), cudaMemcpyDeviceToHost));
     bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(fine.data(), sizeof(double), fine.size(), f) == fine.size() &&
               fwrite(mem.data(), sizeof(double), mem.size(), f) == mem.size();
     ok = (fclose(f) == 0) && ok;
@@ -672,6 +677,7 @@ extern "C" mgenkf_status mgenkf_load(mgenkf_handle h, const char *path) {
     mgenkf_status st = mgenkf_set_state(h, fine.data(), mem.data());
     if (st) return st;
     h->cycle = hd.cycle;
+    H_CUDA(cudaMemcpy(h->cycle_d, &hd.cycle, sizeof(uint64_t), cudaMemcpyHostToDevice));
     return MGENKF_OK;
 }
 
@@ -745,3 +751,371 @@ extern "C" mgenkf_status mgk_normals(uint64_t seed, uint64_t tag, uint64_t ctr0,
 extern "C" const char *mgk_last_error(void) { return g_ops_error.c_str(); }
 
 extern "C" uint64_t mgk_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+// ===========================================================================
+// batched cycles of independent NS-2D handles: one CUDA graph launch per cycle
+// ===========================================================================
+namespace {
+constexpr int kBatchStreams = 16;
+}
+
+struct mgenkf_batch {
+    std::vector<mgenkf_ctx *> hs;
+    cudaStream_t s0 = nullptr;
+    bool own_s0 = false;  // created here when the caller passed the legacy stream
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> ev;
+    double *obs_stage = nullptr;
+    double *innov = nullptr;  // per-problem innovation RMS of the last cycle
+    std::vector<size_t> obs_off;
+    size_t total_ny = 0;
+    std::vector<int> sizes;  // distinct grid sizes of the members and fine runs
+    std::vector<int> shape;  // tile shape per size
+    NsGroup<float> *d_groups[kNsTileShapes] = {};
+    int ngroups[kNsTileShapes] = {}, tiles[kNsTileShapes] = {};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_nsteps = -1;
+    double gamma = 1.4, mu = 1e-3, prandtl = 0.72;
+    std::string err;
+};
+
+#define B_FAIL(code, msg) \
+    do {                  \
+        b->err = (msg);   \
+        return (code);    \
+    } while (0)
+#define B_CUDA(call)                                                         \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) {                                             \
+            b->err = std::string(#call) + ": " + cudaGetErrorString(e_);     \
+            return MGENKF_ERR_CUDA;                                          \
+        }                                                                    \
+    } while (0)
+
+static int size_index(const mgenkf_batch *b, int n) {
+    for (size_t i = 0; i < b->sizes.size(); ++i)
+        if (b->sizes[i] == n) return (int)i;
+    return -1;
+}
+
+// the two groups (members, fine run) of one handle, scratch laid out as in
+// ns2d_forecast_scratch
+static void handle_groups(const mgenkf_ctx *h, NsGroup<float> g[2]) {
+    const size_t sz0 = (size_t)4 * h->nc * h->nc * h->ne, sz1 = (size_t)4 * h->nf * h->nf;
+    float *sc = (float *)h->ns_scratch;
+    const int ns[2] = {h->nc, h->nf}, np[2] = {h->ne, 1};
+    float *u0[2] = {(float *)h->members, (float *)h->fine};
+    float *s1[2] = {sc, sc + 2 * sz0}, *s2[2] = {sc + sz0, sc + 2 * sz0 + sz1};
+    for (int k = 0; k < 2; ++k) {
+        g[k] = {};
+        g[k].u0 = u0[k];
+        g[k].s1 = s1[k];
+        g[k].s2 = s2[k];
+        g[k].n = ns[k];
+        g[k].nprob = np[k];
+        const double hh = h->cfg.length / ns[k];
+        g[k].inv_h = (float)(1.0 / hh);
+        g[k].inv_2h = (float)(1.0 / (2.0 * hh));
+        g[k].dt = (float)h->cfg.dt;
+    }
+}
+
+// device tables of groups per tile shape (only groups whose size is in `only`, if given)
+static mgenkf_status build_tables(mgenkf_batch *b, std::vector<NsGroup<float>> (&tab)[kNsTileShapes],
+                                  int only_size, int only_shape) {
+    for (int k = 0; k < kNsTileShapes; ++k) tab[k].clear();
+    int tiles[kNsTileShapes] = {0, 0, 0};
+    for (mgenkf_ctx *h : b->hs) {
+        NsGroup<float> g[2];
+        handle_groups(h, g);
+        for (int k = 0; k < 2; ++k) {
+            int sh = b->shape[size_index(b, g[k].n)];
+            if (only_size > 0) {
+                if (g[k].n != only_size) continue;
+                sh = only_shape;
+            }
+            g[k].tx = ceil_div(g[k].n, ns2d_tile_x(sh));
+            g[k].ty = ceil_div(g[k].n, ns2d_tile_y(sh));
+            g[k].tile_begin = tiles[sh];
+            tiles[sh] += g[k].tx * g[k].ty * g[k].nprob;
+            tab[sh].push_back(g[k]);
+        }
+    }
+    return MGENKF_OK;
+}
+
+static mgenkf_status upload_tables(mgenkf_batch *b, std::vector<NsGroup<float>> (&tab)[kNsTileShapes]) {
+    for (int k = 0; k < kNsTileShapes; ++k) {
+        if (b->d_groups[k]) cudaFree(b->d_groups[k]);
+        b->d_groups[k] = nullptr;
+        b->ngroups[k] = (int)tab[k].size();
+        b->tiles[k] = 0;
+        if (tab[k].empty()) continue;
+        const NsGroup<float> &last = tab[k].back();
+        b->tiles[k] = last.tile_begin + last.tx * last.ty * last.nprob;
+        B_CUDA(cudaMalloc(&b->d_groups[k], tab[k].size() * sizeof(NsGroup<float>)));
+        B_CUDA(cudaMemcpy(b->d_groups[k], tab[k].data(), tab[k].size() * sizeof(NsGroup<float>),
+                          cudaMemcpyHostToDevice));
+    }
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_nsteps = -1;
+    return MGENKF_OK;
+}
+
+static void batch_free(mgenkf_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (int k = 0; k < kNsTileShapes; ++k)
+        if (b->d_groups[k]) cudaFree(b->d_groups[k]);
+    if (b->obs_stage) cudaFree(b->obs_stage);
+    if (b->innov) cudaFree(b->innov);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    for (cudaStream_t s : b->aux) cudaStreamDestroy(s);
+    if (b->own_s0) cudaStreamDestroy(b->s0);
+}
+
+extern "C" mgenkf_status mgenkf_batch_create(const mgenkf_handle *handles, int32_t n, void *stream,
+                                             mgenkf_batch_t *out) {
+    if (!out || !handles || n < 1) return MGENKF_ERR_INVALID_ARG;
+    *out = nullptr;
+    mgenkf_batch *b = new mgenkf_batch();
+    b->s0 = (cudaStream_t)stream;
+    auto fail = [&](mgenkf_status st, const std::string &m) {
+        mgk_set_error("mgenkf_batch_create: " + m);
+        batch_free(b);
+        delete b;
+        return st;
+    };
+    for (int i = 0; i < n; ++i) {
+        mgenkf_ctx *h = handles[i];
+        if (!h) return fail(MGENKF_ERR_INVALID_ARG, "NULL handle");
+        if (h->cfg.model != MGENKF_NS2D || !h->mixed)
+            return fail(MGENKF_ERR_INVALID_ARG, "batches hold NS-2D mixed-precision handles");
+        if (i == 0) {
+            b->gamma = h->cfg.gamma;
+            b->mu = h->cfg.nu;
+            b->prandtl = h->cfg.prandtl;
+        } else if (h->cfg.gamma != b->gamma || h->cfg.nu != b->mu || h->cfg.prandtl != b->prandtl) {
+            return fail(MGENKF_ERR_INVALID_ARG, "all handles of a batch share gamma, mu and Pr");
+        }
+        for (int j = 0; j < i; ++j)
+            if (handles[j] == h) return fail(MGENKF_ERR_INVALID_ARG, "a handle appears twice");
+        b->hs.push_back(h);
+        b->obs_off.push_back(b->total_ny);
+        b->total_ny += h->ny;
+        for (int sz : {h->nc, h->nf})
+            if (size_index(b, sz) < 0) {
+                b->sizes.push_back(sz);
+                b->shape.push_back(0);
+            }
+    }
+    if (!b->s0) {
+        // the legacy stream cannot be captured: a blocking stream keeps the
+        // batch ordered with work the caller issues there
+        if (cudaStreamCreate(&b->s0) != cudaSuccess) return fail(MGENKF_ERR_CUDA, "stream");
+        b->own_s0 = true;
+    }
+    if (cudaMalloc(&b->obs_stage, b->total_ny * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&b->innov, b->hs.size() * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MGENKF_ERR_OOM, "observation staging buffer");
+    }
+    for (int k = 0; k < kBatchStreams; ++k) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(MGENKF_ERR_CUDA, "stream");
+        b->aux.push_back(s);
+    }
+    for (int k = 0; k < 2 * kBatchStreams + 2 * kNsTileShapes + 2; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(MGENKF_ERR_CUDA, "event");
+        b->ev.push_back(e);
+    }
+    std::vector<NsGroup<float>> tab[kNsTileShapes];
+    build_tables(b, tab, 0, 0);
+    if (upload_tables(b, tab) != MGENKF_OK) return fail(MGENKF_ERR_CUDA, b->err);
+    *out = b;
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_batch_destroy(mgenkf_batch_t b) {
+    if (!b) return MGENKF_OK;
+    cudaStreamSynchronize(b->s0);
+    for (cudaStream_t s : b->aux) cudaStreamSynchronize(s);
+    batch_free(b);
+    delete b;
+    return MGENKF_OK;
+}
+
+extern "C" const char *mgenkf_batch_last_error(mgenkf_batch_t b) { return b ? b->err.c_str() : ""; }
+
+// forecast of every handle: one launch sequence per tile shape, each on its own
+// stream, joined back into s0
+static mgenkf_status batch_forecast(mgenkf_batch *b, int nsteps) {
+    B_CUDA(cudaEventRecord(b->ev[0], b->s0));
+    int used = 0;
+    for (int k = 0; k < kNsTileShapes; ++k) {
+        if (!b->tiles[k]) continue;
+        cudaStream_t s = b->aux[k];
+        B_CUDA(cudaStreamWaitEvent(s, b->ev[0], 0));
+        cudaError_t e = ns2d_forecast_table<float>(b->d_groups[k], b->ngroups[k], b->tiles[k], k, nsteps, b->gamma,
+                                                   b->mu, b->prandtl, s);
+        if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("batched forecast: ") + cudaGetErrorString(e));
+        B_CUDA(cudaEventRecord(b->ev[1 + k], s));
+        ++used;
+    }
+    for (int k = 0; k < kNsTileShapes; ++k)
+        if (b->tiles[k]) B_CUDA(cudaStreamWaitEvent(b->s0, b->ev[1 + k], 0));
+    return MGENKF_OK;
+}
+
+// analyses and prolongations of every handle, spread over the auxiliary streams
+static mgenkf_status batch_analyse(mgenkf_batch *b) {
+    const int base = 1 + kNsTileShapes;
+    B_CUDA(cudaEventRecord(b->ev[base], b->s0));
+    const int ns = (int)std::min<size_t>(b->aux.size(), b->hs.size());
+    for (int k = 0; k < ns; ++k) B_CUDA(cudaStreamWaitEvent(b->aux[k], b->ev[base], 0));
+    for (size_t j = 0; j < b->hs.size(); ++j) {
+        mgenkf_ctx *h = b->hs[j];
+        cudaStream_t keep = h->stream;
+        h->stream = b->aux[j % ns];
+        mgenkf_status st = analyse_impl(h, b->obs_stage + b->obs_off[j], nullptr);
+        if (st == MGENKF_OK) {
+            launch_innov_rms(h->Z, h->ne, h->ny, b->innov + j, h->stream);
+            st = prolong_impl(h);
+        }
+        h->stream = keep;
+        if (st) B_FAIL(st, "problem " + std::to_string(j) + ": " + h->err);
+    }
+    for (int k = 0; k < ns; ++k) {
+        B_CUDA(cudaEventRecord(b->ev[base + 1 + k], b->aux[k]));
+        B_CUDA(cudaStreamWaitEvent(b->s0, b->ev[base + 1 + k], 0));
+    }
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_batch_forecast(mgenkf_batch_t b, int32_t nsteps) {
+    if (!b || nsteps < 0) return MGENKF_ERR_INVALID_ARG;
+    b->err.clear();
+    return batch_forecast(b, nsteps);
+}
+
+extern "C" mgenkf_status mgenkf_batch_cycle(mgenkf_batch_t b, int32_t nsteps, const double *y_obs,
+                                            double *innov_out) {
+    if (!b || nsteps < 0 || !y_obs) return MGENKF_ERR_INVALID_ARG;
+    b->err.clear();
+    B_CUDA(cudaMemcpyAsync(b->obs_stage, y_obs, b->total_ny * sizeof(double), cudaMemcpyDefault, b->s0));
+    if (!b->exec || b->graph_nsteps != nsteps) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        B_CUDA(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed));
+        mgenkf_status st = batch_forecast(b, nsteps);
+        if (st == MGENKF_OK) st = batch_analyse(b);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->s0, &g);
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        b->graph = g;
+        B_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+        b->graph_nsteps = nsteps;
+    }
+    B_CUDA(cudaGraphLaunch(b->exec, b->s0));
+    if (innov_out)
+        B_CUDA(cudaMemcpyAsync(innov_out, b->innov, b->hs.size() * sizeof(double), cudaMemcpyDefault, b->s0));
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_batch_sync(mgenkf_batch_t b) {
+    if (!b) return MGENKF_ERR_INVALID_ARG;
+    B_CUDA(cudaStreamSynchronize(b->s0));
+    mgenkf_status first = MGENKF_OK;
+    for (size_t j = 0; j < b->hs.size(); ++j) {
+        mgenkf_status st = mgenkf_sync(b->hs[j]);
+        if (st && !first) {
+            first = st;
+            b->err = "problem " + std::to_string(j) + ": " + b->hs[j]->err;
+        }
+    }
+    return first;
+}
+
+// Time stages 0 and 1 (they write only the stage buffers) of every grid size
+// with every tile shape and keep the fastest shape per size.
+extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
+    if (!b || reps < 1) return MGENKF_ERR_INVALID_ARG;
+    b->err.clear();
+    cudaEvent_t t0, t1;
+    B_CUDA(cudaEventCreate(&t0));
+    B_CUDA(cudaEventCreate(&t1));
+    NsGroup<float> *d = nullptr;
+    for (size_t si = 0; si < b->sizes.size(); ++si) {
+        float best = 1e30f;
+        int best_shape = 0;
+        for (int sh = 0; sh < kNsTileShapes; ++sh) {
+            std::vector<NsGroup<float>> tab[kNsTileShapes];
+            build_tables(b, tab, b->sizes[si], sh);
+            const int ng = (int)tab[sh].size();
+            if (!ng) continue;
+            const int tiles = tab[sh].back().tile_begin + tab[sh].back().tx * tab[sh].back().ty * tab[sh].back().nprob;
+            B_CUDA(cudaMalloc(&d, ng * sizeof(NsGroup<float>)));
+            B_CUDA(cudaMemcpy(d, tab[sh].data(), ng * sizeof(NsGroup<float>), cudaMemcpyHostToDevice));
+            float ms = 0.f;
+            for (int r = 0; r <= reps; ++r) {  // first repetition warms up
+                B_CUDA(cudaEventRecord(t0, b->s0));
+                cudaError_t e = ns2d_probe_stages01<float>(d, ng, tiles, sh, b->gamma, b->mu, b->prandtl, b->s0);
+                if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+                B_CUDA(cudaEventRecord(t1, b->s0));
+                B_CUDA(cudaEventSynchronize(t1));
+                float t = 0.f;
+                B_CUDA(cudaEventElapsedTime(&t, t0, t1));
+                if (r) ms += t;
+            }
+            cudaFree(d);
+            d = nullptr;
+            if (ms < best) {
+                best = ms;
+                best_shape = sh;
+            }
+        }
+        b->shape[si] = best_shape;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    std::vector<NsGroup<float>> tab[kNsTileShapes];
+    build_tables(b, tab, 0, 0);
+    return upload_tables(b, tab);
+}
+
+extern "C" mgenkf_status mgenkf_batch_tiles(mgenkf_batch_t b, int32_t *sizes, int32_t *shapes, int32_t max,
+                                            int32_t *count) {
+    if (!b || !count) return MGENKF_ERR_INVALID_ARG;
+    *count = (int32_t)b->sizes.size();
+    for (int32_t i = 0; i < *count && i < max; ++i) {
+        if (sizes) sizes[i] = b->sizes[i];
+        if (shapes) shapes[i] = b->shape[i];
+    }
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_batch_set_tiles(mgenkf_batch_t b, const int32_t *sizes, const int32_t *shapes,
+                                                int32_t count) {
+    if (!b || (count > 0 && (!sizes || !shapes))) return MGENKF_ERR_INVALID_ARG;
+    b->err.clear();
+    for (int32_t i = 0; i < count; ++i) {
+        if (shapes[i] < 0 || shapes[i] >= kNsTileShapes) B_FAIL(MGENKF_ERR_INVALID_ARG, "tile shape out of range");
+        const int si = size_index(b, sizes[i]);
+        if (si >= 0) b->shape[si] = shapes[i];
+    }
+    std::vector<NsGroup<float>> tab[kNsTileShapes];
+    build_tables(b, tab, 0, 0);
+    return upload_tables(b, tab);
+}

@@ -75,6 +75,14 @@ def _load():
         "mgk_cnn_adam_step": [P, ctypes.c_float, P],
         "mgk_cnn_coarse_size": [P],
         "mgenkf_set_prolong_cnn": [P, P],
+        "mgenkf_batch_create": [P, i32, P, ctypes.POINTER(P)],
+        "mgenkf_batch_cycle": [P, i32, P, P],
+        "mgenkf_batch_forecast": [P, i32],
+        "mgenkf_batch_sync": [P],
+        "mgenkf_batch_autotune": [P, i32],
+        "mgenkf_batch_tiles": [P, P, P, i32, P],
+        "mgenkf_batch_set_tiles": [P, P, P, i32],
+        "mgenkf_batch_destroy": [P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -82,6 +90,8 @@ def _load():
         fn.restype = ctypes.c_int
     L.mgenkf_last_error.argtypes = [P]
     L.mgenkf_last_error.restype = ctypes.c_char_p
+    L.mgenkf_batch_last_error.argtypes = [P]
+    L.mgenkf_batch_last_error.restype = ctypes.c_char_p
     L.mgk_kernel_launches.argtypes = []
     L.mgk_kernel_launches.restype = ctypes.c_uint64
     L.mgk_last_error.argtypes = []
@@ -365,3 +375,85 @@ class MGEnKF:
         out = np.empty(self.V)
         mgenkf_rmse(self.h, truth, out)
         return out
+
+
+# ---------------------------------------------------------------------------
+# batches of independent NS-2D problems (mgenkf_batch_* in include/mgenkf.h)
+# ---------------------------------------------------------------------------
+TILE_SHAPES = {0: (32, 8), 1: (16, 16), 2: (64, 4)}
+
+
+def _bcheck(st, where, b):
+    if st != MGENKF_OK:
+        text = lib.mgenkf_batch_last_error(b) or b""
+        raise MGEnKFError(st, where, text.decode())
+
+
+class Batch:
+    """Independent NS-2D mixed-precision MGEnKF problems cycled together: one
+    CUDA graph launch per cycle.  `runs` are MGEnKF objects, which the batch
+    keeps alive and which must not be used on their own while it exists."""
+
+    def __init__(self, runs, stream=None):
+        self.runs = list(runs)
+        self.ny = [r.ny for r in self.runs]
+        arr = (ctypes.c_void_p * len(self.runs))(*[r.h for r in self.runs])
+        out = ctypes.c_void_p()
+        _check(lib.mgenkf_batch_create(arr, len(self.runs), _ptr(stream), ctypes.byref(out)),
+               "mgenkf_batch_create")
+        self.b = out.value
+
+    def close(self):
+        if self.b:
+            lib.mgenkf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cycle(self, nsteps, y_obs, innov_out=None):
+        """y_obs: all problems' observations concatenated in run order (host or
+        device FP64).  innov_out: optional buffer of one FP64 per problem that
+        receives the RMS of the cycle's innovations y^o - H^C x^C*."""
+        _bcheck(lib.mgenkf_batch_cycle(self.b, nsteps, _ptr(_as_f64(y_obs)), _ptr(innov_out)),
+                "mgenkf_batch_cycle", self.b)
+
+    def forecast(self, nsteps):
+        _bcheck(lib.mgenkf_batch_forecast(self.b, nsteps), "mgenkf_batch_forecast", self.b)
+
+    def sync(self) -> int:
+        return int(lib.mgenkf_batch_sync(self.b))
+
+    def autotune(self, reps=3):
+        _bcheck(lib.mgenkf_batch_autotune(self.b, reps), "mgenkf_batch_autotune", self.b)
+        return self.tiles()
+
+    def tiles(self) -> dict:
+        """{grid size: tile shape index} (TILE_SHAPES gives the tile)."""
+        cnt = ctypes.c_int32()
+        _bcheck(lib.mgenkf_batch_tiles(self.b, None, None, 0, ctypes.byref(cnt)), "mgenkf_batch_tiles", self.b)
+        n = cnt.value
+        sizes, shapes = (ctypes.c_int32 * n)(), (ctypes.c_int32 * n)()
+        _bcheck(lib.mgenkf_batch_tiles(self.b, sizes, shapes, n, ctypes.byref(cnt)), "mgenkf_batch_tiles", self.b)
+        return {int(sizes[i]): int(shapes[i]) for i in range(n)}
+
+    def set_tiles(self, table: dict):
+        n = len(table)
+        sizes = (ctypes.c_int32 * n)(*[int(k) for k in table])
+        shapes = (ctypes.c_int32 * n)(*[int(v) for v in table.values()])
+        _bcheck(lib.mgenkf_batch_set_tiles(self.b, sizes, shapes, n), "mgenkf_batch_set_tiles", self.b)
+
+    def save_tiles(self, path):
+        """Persist the tile table (JSON, grid size -> shape) for later runs."""
+        import json
+        with open(path, "w") as f:
+            json.dump({"tiles": {str(k): v for k, v in self.tiles().items()},
+                       "shapes": {str(k): list(v) for k, v in TILE_SHAPES.items()}}, f, indent=1)
+
+    def load_tiles(self, path):
+        import json
+        with open(path) as f:
+            self.set_tiles({int(k): int(v) for k, v in json.load(f)["tiles"].items()})

@@ -13,6 +13,7 @@ and point observations of the truth with Gaussian noise (Eq. z_mdl).
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 from dataclasses import dataclass, field
 
@@ -22,7 +23,7 @@ BURGERS1D = "burgers1d"
 NS2D = "ns2d"
 
 # stream identifiers of the seeded generators
-_S_TRUTH, _S_MODEL, _S_MEMBERS, _S_OBSPOS, _S_OBSNOISE, _S_PHASE = 1, 2, 3, 4, 5, 6
+_S_TRUTH, _S_MODEL, _S_MEMBERS, _S_OBSPOS, _S_OBSNOISE, _S_PHASE, _S_BATCH = 1, 2, 3, 4, 5, 6, 7
 
 
 def _rng(seed: int, stream: int, *extra: int) -> np.random.Generator:
@@ -134,6 +135,27 @@ def ns2d_shear(nf: int = 512, ratio: int = 4, ne: int = 64, n_probes: int = 1024
                     n_probes=n_probes, sigma=0.01, steps_per_cycle=10, cycles=cycles, dt=dt,
                     length=1.0, nu=1e-3, precision=precision, seed=seed, mach=mach,
                     truth_kind="shear", obs_kind="random", extra={"delta": delta})
+
+
+def ns2d_batch(nprob: int = 96, seed: int = 0, coarse=(64, 96, 128, 192), members=(16, 32, 64, 128),
+               n_obs=(256, 2048), ratio: int = 4, cycles: int = 100) -> list:
+    """Independent 2-D NS problems of uneven sizes: per problem a coarse side
+    drawn uniformly from `coarse` (fine = ratio x per side), Ne from `members`,
+    an even observation count drawn uniformly from [n_obs[0], n_obs[1]]
+    (n_obs / 2 velocity probes), its own seed, 10 steps per cycle.  The shear
+    layer is 0.02 thick from 128 coarse points per side up and 0.02 * 128 / nc
+    below, so that it spans the same number of coarse cells."""
+    g = _rng(seed, _S_BATCH)
+    out = []
+    for i in range(nprob):
+        nc = int(g.choice(coarse))
+        ne = int(g.choice(members))
+        ny = 2 * int(g.integers(n_obs[0] // 2, n_obs[1] // 2 + 1))
+        delta = 0.02 * max(1.0, 128.0 / nc)
+        w = ns2d_shear(nf=ratio * nc, ratio=ratio, ne=ne, n_probes=ny // 2, cycles=cycles,
+                       precision="mixed", seed=seed * 100003 + i + 1, delta=delta)
+        out.append(dataclasses.replace(w, name=f"batch{i}_{w.name}"))
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -48,3 +48,32 @@ def test_two_rank_replicas_reduce_on_host():
     assert [o[1] for o in out] == [2.0, 2.0]
     assert [o[2] for o in out] == [30.0, 30.0]
     assert out[0][3] != out[1][3]          # independent replicas
+
+
+def test_batched_problems_shard_over_ranks():
+    """The 96 independent problems are split over ranks with no overlap, every
+    problem owned once, and the forecast work balanced within 2 %."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from paper_2012_10091_gb300 import workloads as W
+    ws = W.ns2d_batch(96, seed=0)
+    for world in (1, 2, 4, 8):
+        parts = [bench.shard_problems(ws, world, r) for r in range(world)]
+        owned = sorted(i for p in parts for i in p)
+        assert owned == list(range(len(ws)))
+        loads = [sum(bench.problem_work(ws[i]) for i in p) for p in parts]
+        assert max(loads) <= 1.02 * min(loads)
+
+
+def test_batched_workload_recipe():
+    """Coarse sides, ensemble sizes and observation counts of the batched
+    workload stay in their stated sets and ranges, drawn reproducibly."""
+    from paper_2012_10091_gb300 import workloads as W
+    ws = W.ns2d_batch(96, seed=0)
+    assert len(ws) == 96
+    assert {w.nc for w in ws} == {64, 96, 128, 192}
+    assert {w.ne for w in ws} == {16, 32, 64, 128}
+    assert all(w.nf == 4 * w.nc and w.ny % 2 == 0 and 256 <= w.ny <= 2048 for w in ws)
+    assert len({w.seed for w in ws}) == 96
+    assert [w.name for w in W.ns2d_batch(96, seed=0)] == [w.name for w in ws]

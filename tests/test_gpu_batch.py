@@ -1,0 +1,167 @@
+"""Batches of independent NS-2D MGEnKF problems (uneven grid sizes, ensemble
+sizes and observation counts) cycled by one CUDA graph launch per cycle: the
+batch must give exactly what each problem's own handle gives (forecast of
+Eqs. Mass, Momentum, Energy; Algorithm 4 analysis and correction, with the
+observation-perturbation counter advancing per analysis), for every tile
+shape and after the autotuner, and must agree with the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import rel_err
+from paper_2012_10091_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_10091_gb300 import mgenkf
+    return mgenkf
+
+
+def _problems():
+    # coarse sides 8..40 (fine 32..160; ragged against every tile shape),
+    # Ne 5..16, 16..64 observations
+    return W.ns2d_batch(nprob=6, seed=3, coarse=(8, 16, 24, 40), members=(5, 8, 12, 16), n_obs=(16, 64))
+
+
+def _inputs(ws, cycles):
+    inps = [W.make_inputs(w) for w in ws]
+    yos = [[W.sample_truth(w, inp["truth0"], inp["obs_idx"], inp["obs_var"]) + W.observation_noise(w, k)
+            for k in range(cycles)] for w, inp in zip(ws, inps)]
+    return inps, yos
+
+
+def _runs(M, ws, inps):
+    runs = []
+    for w, inp in zip(ws, inps):
+        g = M.MGEnKF.from_workload(w, precision="mixed")
+        g.set_state(inp["fine0"], inp["members0"])
+        runs.append(g)
+    return runs
+
+
+def _per_handle(M, ws, inps, yos, nsteps):
+    out = []
+    for j, g in enumerate(_runs(M, ws, inps)):
+        for k, n in enumerate(nsteps):
+            g.cycle(n, yos[j][k])
+        assert g.sync() == 0
+        out.append(g.get_state())
+        g.close()
+    return out
+
+
+def _batched(M, b, ws, yos, nsteps, innov=None):
+    for k, n in enumerate(nsteps):
+        out = np.empty(len(ws)) if innov is not None else None
+        b.cycle(n, np.concatenate([yos[j][k] for j in range(len(ws))]), out)
+        if innov is not None:
+            innov.append(out)
+    assert b.sync() == 0
+    return [g.get_state() for g in b.runs]
+
+
+def test_batch_equals_per_problem_handles(M):
+    ws = _problems()
+    assert len({w.nc for w in ws}) > 1 and len({w.ne for w in ws}) > 1
+    nsteps = [10, 10, 7, 10]        # a changed step count recaptures the graph
+    inps, yos = _inputs(ws, len(nsteps))
+    ref = _per_handle(M, ws, inps, yos, nsteps)
+    b = M.Batch(_runs(M, ws, inps))
+    b.set_tiles({w.nc: 0 for w in ws} | {w.nf: 0 for w in ws})
+    got = _batched(M, b, ws, yos, nsteps)
+    for (f0, m0), (f1, m1) in zip(ref, got):
+        np.testing.assert_array_equal(f1, f0)
+        np.testing.assert_array_equal(m1, m0)
+    b.close()
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_every_tile_shape_matches(M, shape):
+    ws = _problems()
+    nsteps = [10, 10]
+    inps, yos = _inputs(ws, len(nsteps))
+    ref = _per_handle(M, ws, inps, yos, nsteps)
+    b = M.Batch(_runs(M, ws, inps))
+    b.set_tiles({w.nc: shape for w in ws} | {w.nf: shape for w in ws})
+    assert set(b.tiles().values()) == {shape}
+    got = _batched(M, b, ws, yos, nsteps)
+    for (f0, m0), (f1, m1) in zip(ref, got):
+        # the per-point arithmetic does not depend on the tile
+        np.testing.assert_array_equal(f1, f0)
+        np.testing.assert_array_equal(m1, m0)
+    b.close()
+
+
+def test_autotune_and_persisted_tiles(M, tmp_path):
+    ws = _problems()
+    inps, yos = _inputs(ws, 2)
+    b = M.Batch(_runs(M, ws, inps))
+    tiles = b.autotune(reps=2)
+    assert set(tiles) == {w.nc for w in ws} | {w.nf for w in ws}
+    assert set(tiles.values()) <= set(M.TILE_SHAPES)
+    path = tmp_path / "tiles.json"
+    b.save_tiles(path)
+    b.set_tiles({k: (v + 1) % 3 for k, v in tiles.items()})
+    b.load_tiles(path)
+    assert b.tiles() == tiles
+    # autotuning ran stages on scratch only: the states are still the initial ones
+    for g, inp in zip(b.runs, inps):
+        f, m = g.get_state()
+        np.testing.assert_allclose(f, inp["fine0"], rtol=1e-6, atol=1e-6)
+    got = _batched(M, b, ws, yos, [10, 10])
+    ref = _per_handle(M, ws, inps, yos, [10, 10])
+    for (f0, m0), (f1, m1) in zip(ref, got):
+        np.testing.assert_array_equal(f1, f0)
+        np.testing.assert_array_equal(m1, m0)
+    b.close()
+
+
+def test_batch_matches_oracle(M):
+    ws = _problems()
+    cycles = 2
+    inps, yos = _inputs(ws, cycles)
+    b = M.Batch(_runs(M, ws, inps))
+    innov = []
+    got = _batched(M, b, ws, yos, [10] * cycles, innov)
+    for j, (w, inp) in enumerate(zip(ws, inps)):
+        mg = O.MGEnKF(w.model, w.nf, w.ratio, w.length, w.dt, inp["fine0"], inp["members0"], inp["obs_idx"],
+                      inp["obs_var"], w.sigma, w.seed, nu=w.nu, gamma=w.gamma, prandtl=w.prandtl, gain_form=1)
+        for k in range(cycles):
+            mg.forecast(10)
+            assert mg.analyse(yos[j][k]) == 0
+            # innovation y^o - H^C x^C* of the fine forecast (Algorithm 4)
+            hs = O.obs_coarse(mg.xstar, 2, 4, w.nc, w.ratio, inp["obs_idx"], inp["obs_var"])
+            d_rms = np.sqrt(np.mean((yos[j][k] - hs) ** 2))
+            np.testing.assert_allclose(innov[k][j], d_rms, rtol=1e-3)
+            mg.prolong_correct()
+        assert rel_err(got[j][0], mg.fine) < 1e-3
+        assert rel_err(got[j][1], mg.members) < 1e-3
+    b.close()
+
+
+def test_batch_rejects_bad_handles(M):
+    ws = _problems()[:2]
+    inps, _ = _inputs(ws, 1)
+    runs = _runs(M, ws, inps)
+    with pytest.raises(M.MGEnKFError):
+        M.Batch([runs[0], runs[0]])
+    g64 = M.MGEnKF.from_workload(ws[0], precision="fp64")
+    with pytest.raises(M.MGEnKFError):
+        M.Batch([runs[0], g64])
+    wb = W.ns2d_shear(nf=64, ratio=4, ne=4, n_probes=8, precision="mixed")
+    gb = M.MGEnKF(model=M.MGENKF_NS2D, n_fine=64, ratio=4, n_members=4, obs_index=[0, 0], obs_var=[1, 2],
+                  length=1.0, dt=wb.dt, nu=wb.nu, obs_sigma=0.01, precision=M.MGENKF_MIXED, gamma=1.3)
+    with pytest.raises(M.MGEnKFError):
+        M.Batch([runs[0], gb])
+    with pytest.raises(M.MGEnKFError):
+        M.Batch([])
+    for g in runs + [g64, gb]:
+        g.close()

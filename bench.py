@@ -46,15 +46,15 @@ WORKLOADS = {
                           traffic=2175232, truth="fp32"),
     # NS-2D: ~200 flops per point and stage (primitives, nodal fluxes, four
     # face fluxes, stage update), 3 stages per step
-    "ns2d": dict(flops=600, kernel="ns2d_stage_kernel<float,*>", launches_per_step=3,
+    "ns2d": dict(flops=600, kernel="ns2d_stage_x2<*,32,8,PairTiles>", launches_per_step=3,
                  traffic=None, truth="fp64"),
     # NS-2D 1024^2 / 256^2 with the learned correction of the prolongation
-    "ns2d_cnn": dict(flops=600, kernel="ns2d_stage_kernel<float,*>", launches_per_step=3,
+    "ns2d_cnn": dict(flops=600, kernel="ns2d_stage_x2<*,32,8,PairTiles>", launches_per_step=3,
                      traffic=None, truth="fp64"),
     # 96 independent NS-2D problems; per point-step the three stage kernels
     # move 128 algorithmic bytes (stage 0: read u0, write s1; stages 1 and 2:
     # read the stage input and u0, write the output; 16 B per point each)
-    "batched": dict(flops=600, bytes=128, kernel="ns2d_stage_table_kernel<float,*,*,*>",
+    "batched": dict(flops=600, bytes=128, kernel="ns2d_stage_x2<*,*,*,TableTiles>",
                     launches_per_step=3, traffic=None, truth="fp32"),
 }
 CNN_FLOPS_PER_PIXEL = 2 * 9 * (8 * 32 + 32 * 32 + 32 * 64)  # three 3x3 convolutions per coarse pixel

@@ -200,8 +200,8 @@ mgenkf_status mgenkf_batch_forecast(mgenkf_batch_t b, int32_t nsteps);
 /* wait for the batch stream; returns the first device status of any problem */
 mgenkf_status mgenkf_batch_sync(mgenkf_batch_t b);
 /* Autotuner: for every grid size time `reps` repetitions of the first two RK
- * stages (which write only scratch) with each tile shape (0 = 32x8, 1 = 16x16,
- * 2 = 64x4) and keep the fastest.  Synchronous; invalidates the captured graph. */
+ * stages (which write only scratch) with each tile shape (points per tile
+ * 0 = 32x16, 1 = 16x32, 2 = 64x8) and keep the fastest.  Synchronous; invalidates the captured graph. */
 mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps);
 /* read (up to max entries) / set the tile shape chosen per grid size */
 mgenkf_status mgenkf_batch_tiles(mgenkf_batch_t b, int32_t *sizes, int32_t *shapes, int32_t max, int32_t *count);

@@ -402,6 +402,7 @@ extern "C" mgenkf_status mgk_cnn_set_params(mgk_cnn_t c, const float *params, co
 
 extern "C" mgenkf_status mgk_cnn_get_params(mgk_cnn_t c, float *params, float *grads) {
     if (!c) return MGENKF_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return MGENKF_ERR_CUDA;  // training launches on any stream
     if (params && cudaMemcpy(params, c->w, kCnnParams * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
         return MGENKF_ERR_CUDA;
     if (grads && cudaMemcpy(grads, c->g, kCnnParams * sizeof(float), cudaMemcpyDefault) != cudaSuccess)

@@ -21,16 +21,28 @@
 // u' = u0 + 2/3 ((s2 - u0) + k(s2)), k = dt L (Shu-Osher form rearranged);
 // s1 and s2 live in two scratch buffers so a stage never overwrites a value
 // another CTA still reads.
+//
+// FP32 states use a folded variant: a CTA of TX x H threads owns a TX x 2H
+// tile and each thread the two points (x, y) and (x, y + H), held as one
+// float2, so every shared-memory load is 64 bits wide and every arithmetic
+// instruction is a packed FFMA2 / FADD2 / FMUL2 on both points; shared row r
+// of the folded halo holds rows y0 + r - 1 and y0 + H + r - 1.  FP64 states
+// use the scalar tile above.
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "forecast_ns2d.h"
 
 namespace mgk {
 
-constexpr int kNsTx = 32, kNsTy = 8;
+constexpr int kNsTx = 32;
+// tile rows of the per-handle kernel: 16 folded FP32 rows, 8 FP64 rows
+template <typename T>
+constexpr int ns_tile_rows() { return std::is_same<T, float>::value ? 16 : 8; }
 
 template <typename T>
 struct NsArgs {
@@ -152,7 +164,297 @@ __device__ __forceinline__ void ns2d_stage_tile(const NsGroup<T> &G, int tile, T
     }
 }
 
-// per-handle launch: two groups (members, fine run) passed by value, 32 x 8 tiles
+// ---------------------------------------------------------------------------
+// FP32: folded pairs of points in float2, packed arithmetic
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b with one rounding (b * -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ int wrap_index(int g, int n) {
+    if (g < 0) g += n;
+    if (g >= n) {
+        g -= n;
+        if (g >= n) g %= n;  // only grids narrower than a tile
+    }
+    return g;
+}
+
+// 4-byte asynchronous global -> shared copy (cached in L1, where the halo
+// re-reads of neighbouring tiles hit)
+__device__ __forceinline__ void cp_async4(void *smem, const float *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// where the tiles of a launch come from: a device table of groups (batched
+// path) or the two groups of one handle.  next() moves gi forward to the
+// group holding `tile`; a CTA visits its tiles in increasing order.
+struct TableTiles {
+    const NsGroup<float> *groups;
+    int ngroups;
+    __device__ __forceinline__ void next(int tile, int &gi) const {
+        while (gi + 1 < ngroups && groups[gi + 1].tile_begin <= tile) ++gi;
+    }
+    __device__ __forceinline__ NsGroup<float> group(int gi) const { return groups[gi]; }
+};
+struct PairTiles {
+    NsGroup<float> g[2];  // g[1].tile_begin = tiles of g[0]
+    __device__ __forceinline__ void next(int tile, int &gi) const { gi = tile < g[1].tile_begin ? 0 : 1; }
+    // no runtime index into the parameter array
+    __device__ __forceinline__ NsGroup<float> group(int gi) const { return gi ? g[1] : g[0]; }
+};
+
+// what every thread needs of one tile, prepared by thread 0 two tiles ahead
+struct TileDesc {
+    const float *in;  // stage input (4 planes of the grid)
+    float *u0;        // state of the grid
+    float *out;       // stage output
+    int n, x0, y0, pad;
+    float inv_h, inv_2h, dt, pad2;
+};
+
+template <int TX, int H, class Tiles>
+__device__ __forceinline__ void make_desc(const Tiles &src, int tile, int &gi, int stage, TileDesc *d) {
+    src.next(tile, gi);
+    const NsGroup<float> G = src.group(gi);
+    const int local = tile - G.tile_begin;
+    const int tiles_per_prob = G.tx * G.ty;
+    const int prob = local / tiles_per_prob;
+    const int tt = local - prob * tiles_per_prob;
+    const int ty = tt / G.tx;
+    const int n = G.n;
+    const size_t off = (size_t)prob * 4 * n * n;
+    float *u0 = G.u0 + off;
+    d->u0 = u0;
+    d->in = stage == 0 ? u0 : (stage == 1 ? G.s1 : G.s2) + off;
+    d->out = stage == 0 ? G.s1 + off : (stage == 1 ? G.s2 + off : u0);
+    d->n = n;
+    d->x0 = (tt - ty * G.tx) * TX;
+    d->y0 = ty * (2 * H);
+    d->inv_h = G.inv_h;
+    d->inv_2h = G.inv_2h;
+    d->dt = G.dt;
+}
+
+template <int TX, int H>
+struct X2Smem {
+    static constexpr int HX = TX + 2, HALO = HX * (H + 2), NT = TX * H;
+    static constexpr int PER_THREAD = (HALO + NT - 1) / NT;  // halo elements a thread loads
+    // raw conserved halo (2 buffers), base values u0 of the tile points
+    // (2 buffers, stages 1 and 2), primitives of the halo, 3 tile descriptors
+    static constexpr size_t bytes(int stage) {
+        return sizeof(float2) * (2 * 4 * HALO + (stage ? 2 * 4 * NT : 0) + 4 * HALO) + 3 * sizeof(TileDesc);
+    }
+};
+
+// Issue the asynchronous loads of one tile into one buffer: the folded halo
+// of the stage input, and (stages 1, 2) u0 at the thread's two points.
+template <int STAGE, int TX, int H>
+__device__ __forceinline__ void x2_issue(const TileDesc &d, const int (&er)[2], const int (&ex)[2], float2 *raw,
+                                         float2 *base) {
+    using S = X2Smem<TX, H>;
+    const int n = d.n, plane = n * n;  // 4 planes of one grid stay below 2^31 elements
+#pragma unroll
+    for (int q = 0; q < S::PER_THREAD; ++q) {
+        const int e = threadIdx.x + q * S::NT;
+        if (e < S::HALO) {
+            const int gx = wrap_index(d.x0 + ex[q] - 1, n);
+            const float *pa = d.in + wrap_index(d.y0 + er[q] - 1, n) * n + gx;
+            const float *pb = d.in + wrap_index(d.y0 + H + er[q] - 1, n) * n + gx;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                cp_async4(&raw[k * S::HALO + e].x, pa + k * plane);
+                cp_async4(&raw[k * S::HALO + e].y, pb + k * plane);
+            }
+        }
+    }
+    if (STAGE != 0) {
+        const int x = d.x0 + threadIdx.x % TX, ya = d.y0 + threadIdx.x / TX, yb = ya + H;
+        if (x < n && ya < n) {
+            const float *pa = d.u0 + ya * n + x, *pb = pa + H * n;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                cp_async4(&base[k * S::NT + threadIdx.x].x, pa + k * plane);
+                if (yb < n) cp_async4(&base[k * S::NT + threadIdx.x].y, pb + k * plane);
+            }
+        }
+    }
+}
+
+// Persistent stage kernel: each CTA walks tiles blockIdx.x, + gridDim.x, ...;
+// the loads of the next tile are in flight while the current one is computed.
+template <int STAGE, int TX, int H, class Tiles>
+__global__ void __launch_bounds__(256) ns2d_stage_x2(Tiles src, int total_tiles, float gm1, float mu, float kap) {
+    using S = X2Smem<TX, H>;
+    constexpr int HX = S::HX, HALO = S::HALO, NT = S::NT;
+    static_assert(NT == 256, "256 threads per CTA");
+    extern __shared__ float4 x2_smem4[];
+    float2 *raw0 = reinterpret_cast<float2 *>(x2_smem4), *raw1 = raw0 + 4 * HALO;
+    float2 *prim = raw1 + 4 * HALO;
+    float2 *base0 = prim + 4 * HALO, *base1 = base0 + (STAGE ? 4 * NT : 0);
+    TileDesc *desc = reinterpret_cast<TileDesc *>(base1 + (STAGE ? 4 * NT : 0));
+
+    int tile = blockIdx.x;
+    if (tile >= total_tiles) return;
+    int gi = 0;  // thread 0: group of the last tile it described
+    if (threadIdx.x == 0) {
+        make_desc<TX, H>(src, tile, gi, STAGE, &desc[0]);
+        if (tile + (int)gridDim.x < total_tiles) make_desc<TX, H>(src, tile + gridDim.x, gi, STAGE, &desc[1]);
+    }
+    int er[S::PER_THREAD], ex[S::PER_THREAD];  // halo row / column of the thread's halo elements
+#pragma unroll
+    for (int q = 0; q < S::PER_THREAD; ++q) {
+        const int e = threadIdx.x + q * NT;
+        er[q] = e / HX;
+        ex[q] = e - er[q] * HX;
+    }
+    __syncthreads();
+    x2_issue<STAGE, TX, H>(desc[0], er, ex, raw0, base0);
+    cp_async_commit();
+    const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+    const int c = (ly + 1) * HX + (lx + 1);
+    const int e_ = c + 1, w_ = c - 1, n_ = c + HX, s_ = c - HX;
+    int slot = 0;  // descriptor slot of the current tile
+    for (int it = 0; tile < total_tiles; ++it, tile += gridDim.x) {
+        float2 *raw = (it & 1) ? raw1 : raw0, *base = (it & 1) ? base1 : base0;
+        const int nslot = slot == 2 ? 0 : slot + 1, nnslot = nslot == 2 ? 0 : nslot + 1;
+        const bool has_next = tile + (int)gridDim.x < total_tiles;
+        if (has_next) x2_issue<STAGE, TX, H>(desc[nslot], er, ex, (it & 1) ? raw0 : raw1, (it & 1) ? base0 : base1);
+        cp_async_commit();
+        // the tile after next: described now, visible after the barriers below
+        if (threadIdx.x == 0 && tile + 2 * (int)gridDim.x < total_tiles)
+            make_desc<TX, H>(src, tile + 2 * gridDim.x, gi, STAGE, &desc[nnslot]);
+        cp_async_wait1();  // this tile's copies (all but the newest group) have landed
+        __syncthreads();
+
+        // primitives of the halo: u, v, p, T
+        for (int e = threadIdx.x; e < HALO; e += NT) {
+            const float2 rho = raw[e], mx = raw[HALO + e], my = raw[2 * HALO + e], E = raw[3 * HALO + e];
+            const float2 rinv = make_float2(__fdividef(1.f, rho.x), __fdividef(1.f, rho.y));
+            const float2 u = mul2(mx, rinv), v = mul2(my, rinv);
+            const float2 ke = mul2(mul2(f2(0.5f), rho), fma2(u, u, mul2(v, v)));
+            const float2 p = mul2(f2(gm1), sub2(E, ke));
+            prim[e] = u;
+            prim[HALO + e] = v;
+            prim[2 * HALO + e] = p;
+            prim[3 * HALO + e] = mul2(p, rinv);
+        }
+        __syncthreads();
+
+        const TileDesc &d = desc[slot];
+        const int n = d.n, plane = n * n;
+        const int x = d.x0 + lx, ya = d.y0 + ly, yb = ya + H;
+        if (x < n && ya < n) {
+            const float2 *Q1 = raw + HALO, *Q2 = raw + 2 * HALO, *Q3 = raw + 3 * HALO;
+            const float2 *U = prim, *V = prim + HALO, *P = prim + 2 * HALO, *TT = prim + 3 * HALO;
+            const float2 ih = f2(d.inv_h), mi2h = f2(-d.inv_2h), q4h = f2(0.5f * d.inv_2h);
+            const float2 c43mu = f2(4.f / 3.f * mu), mc23mu = f2(-2.f / 3.f * mu), mu2 = f2(mu), half = f2(0.5f);
+            const float2 kih = f2(kap * d.inv_h);
+            float2 r[4];
+            {   // inviscid part: central differences of the nodal fluxes
+                const float2 mxe = Q1[e_], mxw = Q1[w_], myn = Q2[n_], mys = Q2[s_];
+                const float2 Ue = U[e_], Uw = U[w_], Vn = V[n_], Vs = V[s_];
+                const float2 Pe = P[e_], Pw = P[w_], Pn = P[n_], Ps = P[s_];
+                const float2 Fe1 = fma2(mxe, Ue, Pe), Fw1 = fma2(mxw, Uw, Pw);
+                const float2 Fe2 = mul2(mxe, V[e_]), Fw2 = mul2(mxw, V[w_]);
+                const float2 Fe3 = mul2(add2(Q3[e_], Pe), Ue), Fw3 = mul2(add2(Q3[w_], Pw), Uw);
+                const float2 Gn1 = mul2(myn, U[n_]), Gs1 = mul2(mys, U[s_]);
+                const float2 Gn2 = fma2(myn, Vn, Pn), Gs2 = fma2(mys, Vs, Ps);
+                const float2 Gn3 = mul2(add2(Q3[n_], Pn), Vn), Gs3 = mul2(add2(Q3[s_], Ps), Vs);
+                r[0] = mul2(add2(sub2(mxe, mxw), sub2(myn, mys)), mi2h);
+                r[1] = mul2(add2(sub2(Fe1, Fw1), sub2(Gn1, Gs1)), mi2h);
+                r[2] = mul2(add2(sub2(Fe2, Fw2), sub2(Gn2, Gs2)), mi2h);
+                r[3] = mul2(add2(sub2(Fe3, Fw3), sub2(Gn3, Gs3)), mi2h);
+            }
+            // viscous and heat fluxes on the four faces of the node
+            float2 fx[2][3], fy[2][3];
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                {   // x-face between columns a and b = a + 1
+                    const int a = side ? c : w_, b = side ? e_ : c;
+                    const float2 Ua = U[a], Ub = U[b], Va = V[a], Vb = V[b];
+                    const float2 ux = mul2(sub2(Ub, Ua), ih), vx = mul2(sub2(Vb, Va), ih);
+                    const float2 uy = mul2(add2(sub2(U[a + HX], U[a - HX]), sub2(U[b + HX], U[b - HX])), q4h);
+                    const float2 vy = mul2(add2(sub2(V[a + HX], V[a - HX]), sub2(V[b + HX], V[b - HX])), q4h);
+                    const float2 txx = fma2(c43mu, ux, mul2(mc23mu, vy)), txy = mul2(mu2, add2(uy, vx));
+                    const float2 uf = mul2(half, add2(Ua, Ub)), vf = mul2(half, add2(Va, Vb));
+                    fx[side][0] = txx;
+                    fx[side][1] = txy;
+                    fx[side][2] = fma2(txx, uf, fma2(txy, vf, mul2(kih, sub2(TT[b], TT[a]))));
+                }
+                {   // y-face between rows a and b = a + 1
+                    const int a = side ? c : s_, b = side ? n_ : c;
+                    const float2 Ua = U[a], Ub = U[b], Va = V[a], Vb = V[b];
+                    const float2 uy = mul2(sub2(Ub, Ua), ih), vy = mul2(sub2(Vb, Va), ih);
+                    const float2 ux = mul2(add2(sub2(U[a + 1], U[a - 1]), sub2(U[b + 1], U[b - 1])), q4h);
+                    const float2 vx = mul2(add2(sub2(V[a + 1], V[a - 1]), sub2(V[b + 1], V[b - 1])), q4h);
+                    const float2 tyy = fma2(c43mu, vy, mul2(mc23mu, ux)), txy = mul2(mu2, add2(uy, vx));
+                    const float2 uf = mul2(half, add2(Ua, Ub)), vf = mul2(half, add2(Va, Vb));
+                    fy[side][0] = txy;
+                    fy[side][1] = tyy;
+                    fy[side][2] = fma2(txy, uf, fma2(tyy, vf, mul2(kih, sub2(TT[b], TT[a]))));
+                }
+            }
+            float2 L[4];
+            L[0] = r[0];
+#pragma unroll
+            for (int k = 1; k < 4; ++k)
+                L[k] = fma2(add2(sub2(fx[1][k - 1], fx[0][k - 1]), sub2(fy[1][k - 1], fy[0][k - 1])), ih, r[k]);
+
+            float *oa = d.out + ya * n + x, *ob = oa + H * n;
+            const bool has_b = yb < n;
+            const float2 dt = f2(d.dt);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 kq = mul2(dt, L[k]);
+                const float2 sv = raw[k * HALO + c];
+                float2 res;
+                if (STAGE == 0) {
+                    res = add2(sv, kq);
+                } else {
+                    float2 b = base[k * NT + threadIdx.x];
+                    if (!has_b) b.y = 0.f;  // never stored; keeps the unused lane finite
+                    res = fma2(f2(STAGE == 1 ? 0.25f : 2.f / 3.f), add2(sub2(sv, b), kq), b);
+                }
+                oa[k * plane] = res.x;
+                if (has_b) ob[k * plane] = res.y;
+            }
+        }
+        slot = nslot;
+        __syncthreads();  // buffers of this tile, prim and its descriptor slot are reused later
+    }
+}
+
+// CTAs per launch of a persistent stage kernel: resident CTAs per SM x SMs
+template <int STAGE, int TX, int H, class Tiles>
+static int x2_grid(int total_tiles) {
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        const size_t smem = X2Smem<TX, H>::bytes(STAGE);
+        cudaFuncSetAttribute(ns2d_stage_x2<STAGE, TX, H, Tiles>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ns2d_stage_x2<STAGE, TX, H, Tiles>, 256, smem);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (per_sm < 1) per_sm = 1;
+    }
+    return std::min(total_tiles, per_sm * sms);
+}
+
+template <int STAGE, int TX, int H, class Tiles>
+static void x2_launch(const Tiles &src, int total_tiles, float gm1, float mu, float kap, cudaStream_t s) {
+    const int grid = x2_grid<STAGE, TX, H, Tiles>(total_tiles);
+    ns2d_stage_x2<STAGE, TX, H, Tiles><<<grid, 256, X2Smem<TX, H>::bytes(STAGE), s>>>(src, total_tiles, gm1, mu, kap);
+}
+
+// per-handle FP64 launch: two groups (members, fine run) passed by value, 32 x 8 tiles
 template <typename T, int STAGE>
 __global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
     int tile = blockIdx.x;
@@ -160,24 +462,6 @@ __global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
     if (gi) tile -= A.tiles0;
     const NsGroup<T> G = gi ? A.g[1] : A.g[0];  // no runtime index into the parameter array
     ns2d_stage_tile<T, STAGE, 32, 8>(G, tile, A.gm1, A.mu, A.kappa);
-}
-
-// batched launch: a table of groups in device memory, found by binary search
-// on the first tile of each group
-template <typename T, int STAGE, int TX, int TY>
-__global__ void __launch_bounds__(256) ns2d_stage_table_kernel(const NsGroup<T> *__restrict__ groups,
-                                                               int ngroups, T gm1, T mu, T kappa) {
-    const int tile = blockIdx.x;
-    int lo = 0, hi = ngroups - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (groups[mid].tile_begin <= tile)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const NsGroup<T> G = groups[lo];
-    ns2d_stage_tile<T, STAGE, TX, TY>(G, tile - G.tile_begin, gm1, mu, kappa);
 }
 
 const char *ns2d_check_size(int n_whole, int n_split) {
@@ -212,7 +496,7 @@ cudaError_t ns2d_forecast_scratch(T *whole, int n_whole, int n_whole_probs, T *s
         sc += 2 * sz;
         if (np[g] > 0) {
             G.tx = ceil_div(ns[g], kNsTx);
-            G.ty = ceil_div(ns[g], kNsTy);
+            G.ty = ceil_div(ns[g], ns_tile_rows<T>());
             const double h = length / ns[g];
             G.inv_h = (T)(1.0 / h);
             G.inv_2h = (T)(1.0 / (2.0 * h));
@@ -226,11 +510,23 @@ cudaError_t ns2d_forecast_scratch(T *whole, int n_whole, int n_whole_probs, T *s
     A.kappa = (T)(mu * gamma / ((gamma - 1.0) * prandtl));
     const int grid = tiles[0] + tiles[1];
     if (grid == 0 || nsteps == 0) return cudaSuccess;
-    for (int s = 0; s < nsteps; ++s) {
-        ns2d_stage_kernel<T, 0><<<grid, 256, 0, stream>>>(A);
-        ns2d_stage_kernel<T, 1><<<grid, 256, 0, stream>>>(A);
-        ns2d_stage_kernel<T, 2><<<grid, 256, 0, stream>>>(A);
-        count_launches(3);
+    if constexpr (std::is_same<T, float>::value) {
+        PairTiles P{{A.g[0], A.g[1]}};
+        P.g[0].tile_begin = 0;
+        P.g[1].tile_begin = tiles[0];
+        for (int s = 0; s < nsteps; ++s) {
+            x2_launch<0, 32, 8>(P, grid, A.gm1, A.mu, A.kappa, stream);
+            x2_launch<1, 32, 8>(P, grid, A.gm1, A.mu, A.kappa, stream);
+            x2_launch<2, 32, 8>(P, grid, A.gm1, A.mu, A.kappa, stream);
+            count_launches(3);
+        }
+    } else {
+        for (int s = 0; s < nsteps; ++s) {
+            ns2d_stage_kernel<T, 0><<<grid, 256, 0, stream>>>(A);
+            ns2d_stage_kernel<T, 1><<<grid, 256, 0, stream>>>(A);
+            ns2d_stage_kernel<T, 2><<<grid, 256, 0, stream>>>(A);
+            count_launches(3);
+        }
     }
     return cudaGetLastError();
 }
@@ -251,53 +547,46 @@ cudaError_t ns2d_forecast(T *whole, int n_whole, int n_whole_probs, T *split, in
     return e != cudaSuccess ? e : e2;
 }
 
+// batched FP32 shapes: threads TX x H, tiles TX x 2H points
 int ns2d_tile_x(int shape) { return shape == 1 ? 16 : (shape == 2 ? 64 : 32); }
-int ns2d_tile_y(int shape) { return shape == 1 ? 16 : (shape == 2 ? 4 : 8); }
+int ns2d_tile_y(int shape) { return 2 * (shape == 1 ? 16 : (shape == 2 ? 4 : 8)); }
 
-template <typename T, int TX, int TY>
-static void launch_table(const NsGroup<T> *groups, int ngroups, int tiles, int nsteps, T gm1, T mu, T kappa,
-                         cudaStream_t s) {
+template <int TX, int H>
+static void launch_table(const NsGroup<float> *groups, int ngroups, int tiles, int nsteps, int first_stage,
+                         int last_stage, float gm1, float mu, float kappa, cudaStream_t s) {
+    const TableTiles src{groups, ngroups};
     for (int st = 0; st < nsteps; ++st) {
-        ns2d_stage_table_kernel<T, 0, TX, TY><<<tiles, 256, 0, s>>>(groups, ngroups, gm1, mu, kappa);
-        ns2d_stage_table_kernel<T, 1, TX, TY><<<tiles, 256, 0, s>>>(groups, ngroups, gm1, mu, kappa);
-        ns2d_stage_table_kernel<T, 2, TX, TY><<<tiles, 256, 0, s>>>(groups, ngroups, gm1, mu, kappa);
-        count_launches(3);
+        for (int k = first_stage; k <= last_stage; ++k) {
+            if (k == 0) x2_launch<0, TX, H>(src, tiles, gm1, mu, kappa, s);
+            if (k == 1) x2_launch<1, TX, H>(src, tiles, gm1, mu, kappa, s);
+            if (k == 2) x2_launch<2, TX, H>(src, tiles, gm1, mu, kappa, s);
+        }
+        count_launches(last_stage - first_stage + 1);
     }
 }
 
-template <typename T>
-cudaError_t ns2d_forecast_table(const NsGroup<T> *d_groups, int ngroups, int tiles, int shape, int nsteps,
-                                double gamma, double mu, double prandtl, cudaStream_t s) {
+static cudaError_t table_stages(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, int nsteps,
+                                int first_stage, int last_stage, double gamma, double mu, double prandtl,
+                                cudaStream_t s) {
     if (tiles == 0 || nsteps == 0) return cudaSuccess;
-    const T gm1 = (T)(gamma - 1.0), m = (T)mu, kap = (T)(mu * gamma / ((gamma - 1.0) * prandtl));
+    const float gm1 = (float)(gamma - 1.0), m = (float)mu, kap = (float)(mu * gamma / ((gamma - 1.0) * prandtl));
     if (shape == 1)
-        launch_table<T, 16, 16>(d_groups, ngroups, tiles, nsteps, gm1, m, kap, s);
+        launch_table<16, 16>(d_groups, ngroups, tiles, nsteps, first_stage, last_stage, gm1, m, kap, s);
     else if (shape == 2)
-        launch_table<T, 64, 4>(d_groups, ngroups, tiles, nsteps, gm1, m, kap, s);
+        launch_table<64, 4>(d_groups, ngroups, tiles, nsteps, first_stage, last_stage, gm1, m, kap, s);
     else
-        launch_table<T, 32, 8>(d_groups, ngroups, tiles, nsteps, gm1, m, kap, s);
+        launch_table<32, 8>(d_groups, ngroups, tiles, nsteps, first_stage, last_stage, gm1, m, kap, s);
     return cudaGetLastError();
 }
 
-template <typename T, int TX, int TY>
-static void launch_probe01(const NsGroup<T> *groups, int ngroups, int tiles, T gm1, T mu, T kappa, cudaStream_t s) {
-    ns2d_stage_table_kernel<T, 0, TX, TY><<<tiles, 256, 0, s>>>(groups, ngroups, gm1, mu, kappa);
-    ns2d_stage_table_kernel<T, 1, TX, TY><<<tiles, 256, 0, s>>>(groups, ngroups, gm1, mu, kappa);
-    count_launches(2);
+cudaError_t ns2d_forecast_table(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, int nsteps,
+                                double gamma, double mu, double prandtl, cudaStream_t s) {
+    return table_stages(d_groups, ngroups, tiles, shape, nsteps, 0, 2, gamma, mu, prandtl, s);
 }
 
-template <typename T>
-cudaError_t ns2d_probe_stages01(const NsGroup<T> *d_groups, int ngroups, int tiles, int shape, double gamma,
+cudaError_t ns2d_probe_stages01(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, double gamma,
                                 double mu, double prandtl, cudaStream_t s) {
-    if (tiles == 0) return cudaSuccess;
-    const T gm1 = (T)(gamma - 1.0), m = (T)mu, kap = (T)(mu * gamma / ((gamma - 1.0) * prandtl));
-    if (shape == 1)
-        launch_probe01<T, 16, 16>(d_groups, ngroups, tiles, gm1, m, kap, s);
-    else if (shape == 2)
-        launch_probe01<T, 64, 4>(d_groups, ngroups, tiles, gm1, m, kap, s);
-    else
-        launch_probe01<T, 32, 8>(d_groups, ngroups, tiles, gm1, m, kap, s);
-    return cudaGetLastError();
+    return table_stages(d_groups, ngroups, tiles, shape, 1, 0, 1, gamma, mu, prandtl, s);
 }
 
 #define MGK_NS_INST(T)                                                                            \
@@ -305,10 +594,7 @@ cudaError_t ns2d_probe_stages01(const NsGroup<T> *d_groups, int ngroups, int til
                                           double, double, int, cudaStream_t);                     \
     template cudaError_t ns2d_forecast_scratch<T>(T *, int, int, T *, int, int, double, double,    \
                                                   double, double, double, int, T *, cudaStream_t); \
-    template cudaError_t ns2d_forecast_table<T>(const NsGroup<T> *, int, int, int, int, double, double, \
-                                                double, cudaStream_t);                                 \
-    template cudaError_t ns2d_probe_stages01<T>(const NsGroup<T> *, int, int, int, double, double, double, \
-                                                cudaStream_t);
+
 MGK_NS_INST(float)
 MGK_NS_INST(double)
 #undef MGK_NS_INST

@@ -14,15 +14,15 @@ struct NsGroup {
     T inv_h, inv_2h, dt;
 };
 
-// tile shapes of the batched stage kernel: 0 = 32 x 8, 1 = 16 x 16, 2 = 64 x 4
+// tile shapes of the batched FP32 stage kernel (threads TX x H, tiles TX x 2H
+// points): 0 = 32 x 16, 1 = 16 x 32, 2 = 64 x 8
 constexpr int kNsTileShapes = 3;
 int ns2d_tile_x(int shape);
 int ns2d_tile_y(int shape);
 
 // nsteps SSP-RK3 steps of every group of a device table (tile_begin ascending,
-// all tiles of the given shape).
-template <typename T>
-cudaError_t ns2d_forecast_table(const NsGroup<T> *d_groups, int ngroups, int tiles, int shape, int nsteps,
+// all tiles of the given shape), FP32 states.
+cudaError_t ns2d_forecast_table(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, int nsteps,
                                 double gamma, double mu, double prandtl, cudaStream_t s);
 
 // NULL if grids of n_whole (one member per CTA group) and n_split points per
@@ -48,8 +48,7 @@ cudaError_t ns2d_forecast(T *whole, int n_whole, int n_whole_probs, T *split, in
                           double prandtl, int nsteps, cudaStream_t stream);
 
 // stages 0 and 1 only (they leave the states untouched): timing probe of the autotuner
-template <typename T>
-cudaError_t ns2d_probe_stages01(const NsGroup<T> *d_groups, int ngroups, int tiles, int shape, double gamma,
+cudaError_t ns2d_probe_stages01(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, double gamma,
                                 double mu, double prandtl, cudaStream_t s);
 
 }  // namespace mgk

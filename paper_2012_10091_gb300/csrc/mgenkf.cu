@@ -619,7 +619,8 @@ extern "C" mgenkf_status mgenkf_sync(mgenkf_handle h) {
     int st = 0;
     H_CUDA(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != 0) {
-        H_CUDA(cudaMemset(h->status, 0, sizeof(int)));
+        H_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+        H_CUDA(cudaStreamSynchronize(h->stream));
         h->err = st == MGENKF_ERR_NOT_SPD ? "innovation matrix not SPD: members and fine run left unchanged"
                                          : "non-finite observation: members and fine run left unchanged";
         return (mgenkf_status)st;
@@ -677,7 +678,10 @@ extern "C" mgenkf_status mgenkf_load(mgenkf_handle h, const char *path) {
     mgenkf_status st = mgenkf_set_state(h, fine.data(), mem.data());
     if (st) return st;
     h->cycle = hd.cycle;
-    H_CUDA(cudaMemcpy(h->cycle_d, &hd.cycle, sizeof(uint64_t), cudaMemcpyHostToDevice));
+    // stream-ordered: a plain copy from pageable memory may return before it
+    // lands, and the handle's stream need not wait for the legacy stream
+    H_CUDA(cudaMemcpyAsync(h->cycle_d, &hd.cycle, sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
+    H_CUDA(cudaStreamSynchronize(h->stream));
     return MGENKF_OK;
 }
 
@@ -847,6 +851,9 @@ static mgenkf_status build_tables(mgenkf_batch *b, std::vector<NsGroup<float>> (
 }
 
 static mgenkf_status upload_tables(mgenkf_batch *b, std::vector<NsGroup<float>> (&tab)[kNsTileShapes]) {
+    // nothing may still read the old tables
+    B_CUDA(cudaStreamSynchronize(b->s0));
+    for (cudaStream_t s : b->aux) B_CUDA(cudaStreamSynchronize(s));
     for (int k = 0; k < kNsTileShapes; ++k) {
         if (b->d_groups[k]) cudaFree(b->d_groups[k]);
         b->d_groups[k] = nullptr;
@@ -856,9 +863,12 @@ static mgenkf_status upload_tables(mgenkf_batch *b, std::vector<NsGroup<float>> 
         const NsGroup<float> &last = tab[k].back();
         b->tiles[k] = last.tile_begin + last.tx * last.ty * last.nprob;
         B_CUDA(cudaMalloc(&b->d_groups[k], tab[k].size() * sizeof(NsGroup<float>)));
-        B_CUDA(cudaMemcpy(b->d_groups[k], tab[k].data(), tab[k].size() * sizeof(NsGroup<float>),
-                          cudaMemcpyHostToDevice));
+        // on the batch stream: a plain copy from pageable memory may return
+        // before it lands and a non-blocking stream does not wait for it
+        B_CUDA(cudaMemcpyAsync(b->d_groups[k], tab[k].data(), tab[k].size() * sizeof(NsGroup<float>),
+                               cudaMemcpyHostToDevice, b->s0));
     }
+    B_CUDA(cudaStreamSynchronize(b->s0));
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
@@ -962,7 +972,7 @@ static mgenkf_status batch_forecast(mgenkf_batch *b, int nsteps) {
         if (!b->tiles[k]) continue;
         cudaStream_t s = b->aux[k];
         B_CUDA(cudaStreamWaitEvent(s, b->ev[0], 0));
-        cudaError_t e = ns2d_forecast_table<float>(b->d_groups[k], b->ngroups[k], b->tiles[k], k, nsteps, b->gamma,
+        cudaError_t e = ns2d_forecast_table(b->d_groups[k], b->ngroups[k], b->tiles[k], k, nsteps, b->gamma,
                                                    b->mu, b->prandtl, s);
         if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("batched forecast: ") + cudaGetErrorString(e));
         B_CUDA(cudaEventRecord(b->ev[1 + k], s));
@@ -1067,11 +1077,11 @@ extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
             if (!ng) continue;
             const int tiles = tab[sh].back().tile_begin + tab[sh].back().tx * tab[sh].back().ty * tab[sh].back().nprob;
             B_CUDA(cudaMalloc(&d, ng * sizeof(NsGroup<float>)));
-            B_CUDA(cudaMemcpy(d, tab[sh].data(), ng * sizeof(NsGroup<float>), cudaMemcpyHostToDevice));
+            B_CUDA(cudaMemcpyAsync(d, tab[sh].data(), ng * sizeof(NsGroup<float>), cudaMemcpyHostToDevice, b->s0));
             float ms = 0.f;
             for (int r = 0; r <= reps; ++r) {  // first repetition warms up
                 B_CUDA(cudaEventRecord(t0, b->s0));
-                cudaError_t e = ns2d_probe_stages01<float>(d, ng, tiles, sh, b->gamma, b->mu, b->prandtl, b->s0);
+                cudaError_t e = ns2d_probe_stages01(d, ng, tiles, sh, b->gamma, b->mu, b->prandtl, b->s0);
                 if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
                 B_CUDA(cudaEventRecord(t1, b->s0));
                 B_CUDA(cudaEventSynchronize(t1));

@@ -380,7 +380,7 @@ class MGEnKF:
 # ---------------------------------------------------------------------------
 # batches of independent NS-2D problems (mgenkf_batch_* in include/mgenkf.h)
 # ---------------------------------------------------------------------------
-TILE_SHAPES = {0: (32, 8), 1: (16, 16), 2: (64, 4)}
+TILE_SHAPES = {0: (32, 16), 1: (16, 32), 2: (64, 8)}   # points per tile (x, y)
 
 
 def _bcheck(st, where, b):

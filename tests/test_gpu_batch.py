@@ -165,3 +165,34 @@ def test_batch_rejects_bad_handles(M):
         M.Batch([])
     for g in runs + [g64, gb]:
         g.close()
+
+
+def test_batch_on_a_nonblocking_stream(M):
+    """Handles and batch on a non-blocking stream with device observations and
+    device innovation output (the benchmark's configuration)."""
+    import torch
+    ws = _problems()
+    nsteps = [10, 10, 10]
+    inps, yos = _inputs(ws, len(nsteps))
+    ref = _per_handle(M, ws, inps, yos, nsteps)
+    st = torch.cuda.Stream()
+    runs = []
+    for w, inp in zip(ws, inps):
+        g = M.MGEnKF.from_workload(w, precision="mixed", stream=st.cuda_stream)
+        g.set_state(inp["fine0"], inp["members0"])
+        runs.append(g)
+    b = M.Batch(runs, stream=st.cuda_stream)
+    b.autotune(reps=1)
+    y = torch.tensor(np.stack([np.concatenate([yos[j][k] for j in range(len(ws))]) for k in range(len(nsteps))]),
+                     device="cuda")
+    innov = torch.zeros((len(nsteps), len(ws)), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    for k, n in enumerate(nsteps):
+        b.cycle(n, y[k], innov[k])
+    assert b.sync() == 0
+    assert torch.isfinite(innov).all() and (innov > 0).all()
+    for g, (f0, m0) in zip(b.runs, ref):
+        f1, m1 = g.get_state()
+        np.testing.assert_array_equal(f1, f0)
+        np.testing.assert_array_equal(m1, m0)
+    b.close()

@@ -245,189 +245,188 @@ __device__ __forceinline__ void make_desc(const Tiles &src, int tile, int &gi, i
 template <int TX, int H>
 struct X2Smem {
     static constexpr int HX = TX + 2, HALO = HX * (H + 2), NT = TX * H;
-    static constexpr int PER_THREAD = (HALO + NT - 1) / NT;  // halo elements a thread loads
-    // raw conserved halo (2 buffers), base values u0 of the tile points
-    // (2 buffers, stages 1 and 2), primitives of the halo, 3 tile descriptors
-    static constexpr size_t bytes(int stage) {
-        return sizeof(float2) * (2 * 4 * HALO + (stage ? 2 * 4 * NT : 0) + 4 * HALO) + 3 * sizeof(TileDesc);
-    }
+    static constexpr int COPIES = (2 * HALO + NT - 1) / NT;  // (element, row half) pairs a thread copies
+    // raw conserved halo (3 buffers), primitives of the halo (2 buffers), 4 tile descriptors
+    static constexpr size_t bytes() { return sizeof(float2) * (3 * 4 * HALO + 2 * 4 * HALO) + 4 * sizeof(TileDesc); }
 };
 
-// Issue the asynchronous loads of one tile into one buffer: the folded halo
-// of the stage input, and (stages 1, 2) u0 at the thread's two points.
-template <int STAGE, int TX, int H>
-__device__ __forceinline__ void x2_issue(const TileDesc &d, const int (&er)[2], const int (&ex)[2], float2 *raw,
-                                         float2 *base) {
+// Issue the asynchronous copies of one tile's folded halo (4 conserved
+// planes) into one buffer.  Copy c of a thread is (element c >> 1, row half
+// c & 1): neighbouring lanes fill the two 4-byte halves of one float2, so a
+// warp writes 128 contiguous bytes.
+template <int TX, int H>
+__device__ __forceinline__ void x2_issue(const TileDesc &d, const int (&cr)[X2Smem<TX, H>::COPIES],
+                                         const int (&cx)[X2Smem<TX, H>::COPIES], float *raw) {
     using S = X2Smem<TX, H>;
     const int n = d.n, plane = n * n;  // 4 planes of one grid stay below 2^31 elements
 #pragma unroll
-    for (int q = 0; q < S::PER_THREAD; ++q) {
-        const int e = threadIdx.x + q * S::NT;
-        if (e < S::HALO) {
-            const int gx = wrap_index(d.x0 + ex[q] - 1, n);
-            const float *pa = d.in + wrap_index(d.y0 + er[q] - 1, n) * n + gx;
-            const float *pb = d.in + wrap_index(d.y0 + H + er[q] - 1, n) * n + gx;
+    for (int q = 0; q < S::COPIES; ++q) {
+        const int c = threadIdx.x + q * S::NT;
+        if (c < 2 * S::HALO) {
+            const float *src = d.in + wrap_index(d.y0 + cr[q], n) * n + wrap_index(d.x0 + cx[q], n);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                cp_async4(&raw[k * S::HALO + e].x, pa + k * plane);
-                cp_async4(&raw[k * S::HALO + e].y, pb + k * plane);
-            }
-        }
-    }
-    if (STAGE != 0) {
-        const int x = d.x0 + threadIdx.x % TX, ya = d.y0 + threadIdx.x / TX, yb = ya + H;
-        if (x < n && ya < n) {
-            const float *pa = d.u0 + ya * n + x, *pb = pa + H * n;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                cp_async4(&base[k * S::NT + threadIdx.x].x, pa + k * plane);
-                if (yb < n) cp_async4(&base[k * S::NT + threadIdx.x].y, pb + k * plane);
-            }
+            for (int k = 0; k < 4; ++k) cp_async4(raw + 2 * k * S::HALO + c, src + k * plane);
         }
     }
 }
 
-// Persistent stage kernel: each CTA walks tiles blockIdx.x, + gridDim.x, ...;
-// the loads of the next tile are in flight while the current one is computed.
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// primitives u, v, p, T of halo elements e = threadIdx.x, + NT, ...
+template <int HALO, int NT>
+__device__ __forceinline__ void x2_prims(const float2 *raw, float2 *prim, float gm1) {
+    for (int e = threadIdx.x; e < HALO; e += NT) {
+        const float2 rho = raw[e], mx = raw[HALO + e], my = raw[2 * HALO + e], E = raw[3 * HALO + e];
+        const float2 rinv = make_float2(__fdividef(1.f, rho.x), __fdividef(1.f, rho.y));
+        const float2 u = mul2(mx, rinv), v = mul2(my, rinv);
+        const float2 ke = mul2(mul2(f2(0.5f), rho), fma2(u, u, mul2(v, v)));
+        const float2 p = mul2(f2(gm1), sub2(E, ke));
+        prim[e] = u;
+        prim[HALO + e] = v;
+        prim[2 * HALO + e] = p;
+        prim[3 * HALO + e] = mul2(p, rinv);
+    }
+}
+
+// dq/dt of the folded pair at shared index c (9-point stencil)
+template <int HX, int HALO>
+__device__ __forceinline__ void x2_rhs(const float2 *raw, const float2 *prim, int c, float inv_h, float inv_2h,
+                                       float mu, float kap, float2 (&L)[4]) {
+    const int e_ = c + 1, w_ = c - 1, n_ = c + HX, s_ = c - HX;
+    const float2 *Q1 = raw + HALO, *Q2 = raw + 2 * HALO, *Q3 = raw + 3 * HALO;
+    const float2 *U = prim, *V = prim + HALO, *P = prim + 2 * HALO, *TT = prim + 3 * HALO;
+    const float2 ih = f2(inv_h), mi2h = f2(-inv_2h), q4h = f2(0.5f * inv_2h);
+    const float2 c43mu = f2(4.f / 3.f * mu), mc23mu = f2(-2.f / 3.f * mu), mu2 = f2(mu), half = f2(0.5f);
+    const float2 kih = f2(kap * inv_h);
+    float2 r[4];
+    {   // inviscid part: central differences of the nodal fluxes
+        const float2 mxe = Q1[e_], mxw = Q1[w_], myn = Q2[n_], mys = Q2[s_];
+        const float2 Ue = U[e_], Uw = U[w_], Vn = V[n_], Vs = V[s_];
+        const float2 Pe = P[e_], Pw = P[w_], Pn = P[n_], Ps = P[s_];
+        const float2 Fe1 = fma2(mxe, Ue, Pe), Fw1 = fma2(mxw, Uw, Pw);
+        const float2 Fe2 = mul2(mxe, V[e_]), Fw2 = mul2(mxw, V[w_]);
+        const float2 Fe3 = mul2(add2(Q3[e_], Pe), Ue), Fw3 = mul2(add2(Q3[w_], Pw), Uw);
+        const float2 Gn1 = mul2(myn, U[n_]), Gs1 = mul2(mys, U[s_]);
+        const float2 Gn2 = fma2(myn, Vn, Pn), Gs2 = fma2(mys, Vs, Ps);
+        const float2 Gn3 = mul2(add2(Q3[n_], Pn), Vn), Gs3 = mul2(add2(Q3[s_], Ps), Vs);
+        r[0] = mul2(add2(sub2(mxe, mxw), sub2(myn, mys)), mi2h);
+        r[1] = mul2(add2(sub2(Fe1, Fw1), sub2(Gn1, Gs1)), mi2h);
+        r[2] = mul2(add2(sub2(Fe2, Fw2), sub2(Gn2, Gs2)), mi2h);
+        r[3] = mul2(add2(sub2(Fe3, Fw3), sub2(Gn3, Gs3)), mi2h);
+    }
+    // viscous and heat fluxes on the four faces of the node
+    float2 fx[2][3], fy[2][3];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        {   // x-face between columns a and b = a + 1
+            const int a = side ? c : w_, b = side ? e_ : c;
+            const float2 Ua = U[a], Ub = U[b], Va = V[a], Vb = V[b];
+            const float2 ux = mul2(sub2(Ub, Ua), ih), vx = mul2(sub2(Vb, Va), ih);
+            const float2 uy = mul2(add2(sub2(U[a + HX], U[a - HX]), sub2(U[b + HX], U[b - HX])), q4h);
+            const float2 vy = mul2(add2(sub2(V[a + HX], V[a - HX]), sub2(V[b + HX], V[b - HX])), q4h);
+            const float2 txx = fma2(c43mu, ux, mul2(mc23mu, vy)), txy = mul2(mu2, add2(uy, vx));
+            const float2 uf = mul2(half, add2(Ua, Ub)), vf = mul2(half, add2(Va, Vb));
+            fx[side][0] = txx;
+            fx[side][1] = txy;
+            fx[side][2] = fma2(txx, uf, fma2(txy, vf, mul2(kih, sub2(TT[b], TT[a]))));
+        }
+        {   // y-face between rows a and b = a + 1
+            const int a = side ? c : s_, b = side ? n_ : c;
+            const float2 Ua = U[a], Ub = U[b], Va = V[a], Vb = V[b];
+            const float2 uy = mul2(sub2(Ub, Ua), ih), vy = mul2(sub2(Vb, Va), ih);
+            const float2 ux = mul2(add2(sub2(U[a + 1], U[a - 1]), sub2(U[b + 1], U[b - 1])), q4h);
+            const float2 vx = mul2(add2(sub2(V[a + 1], V[a - 1]), sub2(V[b + 1], V[b - 1])), q4h);
+            const float2 tyy = fma2(c43mu, vy, mul2(mc23mu, ux)), txy = mul2(mu2, add2(uy, vx));
+            const float2 uf = mul2(half, add2(Ua, Ub)), vf = mul2(half, add2(Va, Vb));
+            fy[side][0] = txy;
+            fy[side][1] = tyy;
+            fy[side][2] = fma2(txy, uf, fma2(tyy, vf, mul2(kih, sub2(TT[b], TT[a]))));
+        }
+    }
+    L[0] = r[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+        L[k] = fma2(add2(sub2(fx[1][k - 1], fx[0][k - 1]), sub2(fy[1][k - 1], fy[0][k - 1])), ih, r[k]);
+}
+
+// Persistent stage kernel: each CTA walks tiles blockIdx.x, + gridDim.x, ...
+// with one barrier per tile.  In iteration i it copies the halo of tile i + 2
+// (3 raw buffers), forms the primitives of tile i + 1 (2 buffers) and computes
+// tile i; thread 0 describes tile i + 3 (4 descriptor slots).  Stages 1 and
+// 2 load u0 at the thread's points at the start of the iteration and use it at
+// the end.  At most 85 registers: three CTAs per SM.
 template <int STAGE, int TX, int H, class Tiles>
-__global__ void __launch_bounds__(256) ns2d_stage_x2(Tiles src, int total_tiles, float gm1, float mu, float kap) {
+__global__ void __launch_bounds__(256, 3) ns2d_stage_x2(Tiles src, int total_tiles, float gm1, float mu, float kap) {
     using S = X2Smem<TX, H>;
     constexpr int HX = S::HX, HALO = S::HALO, NT = S::NT;
     static_assert(NT == 256, "256 threads per CTA");
     extern __shared__ float4 x2_smem4[];
-    float2 *raw0 = reinterpret_cast<float2 *>(x2_smem4), *raw1 = raw0 + 4 * HALO;
-    float2 *prim = raw1 + 4 * HALO;
-    float2 *base0 = prim + 4 * HALO, *base1 = base0 + (STAGE ? 4 * NT : 0);
-    TileDesc *desc = reinterpret_cast<TileDesc *>(base1 + (STAGE ? 4 * NT : 0));
-
+    float2 *raw_base = reinterpret_cast<float2 *>(x2_smem4);
+    float2 *prim_base = raw_base + 3 * 4 * HALO;
+    TileDesc *desc = reinterpret_cast<TileDesc *>(prim_base + 2 * 4 * HALO);
+    const int G = gridDim.x;
     int tile = blockIdx.x;
     if (tile >= total_tiles) return;
     int gi = 0;  // thread 0: group of the last tile it described
-    if (threadIdx.x == 0) {
-        make_desc<TX, H>(src, tile, gi, STAGE, &desc[0]);
-        if (tile + (int)gridDim.x < total_tiles) make_desc<TX, H>(src, tile + gridDim.x, gi, STAGE, &desc[1]);
-    }
-    int er[S::PER_THREAD], ex[S::PER_THREAD];  // halo row / column of the thread's halo elements
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 3; ++q)
+            if (tile + q * G < total_tiles) make_desc<TX, H>(src, tile + q * G, gi, STAGE, &desc[q]);
+    int cr[S::COPIES], cx[S::COPIES];  // halo row / column offsets of the thread's copies, relative to (y0, x0)
 #pragma unroll
-    for (int q = 0; q < S::PER_THREAD; ++q) {
-        const int e = threadIdx.x + q * NT;
-        er[q] = e / HX;
-        ex[q] = e - er[q] * HX;
+    for (int q = 0; q < S::COPIES; ++q) {
+        const int c = threadIdx.x + q * NT, e = c >> 1, r = e / HX;
+        cr[q] = r - 1 + ((c & 1) ? H : 0);
+        cx[q] = e - r * HX - 1;
     }
-    __syncthreads();
-    x2_issue<STAGE, TX, H>(desc[0], er, ex, raw0, base0);
-    cp_async_commit();
     const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
     const int c = (ly + 1) * HX + (lx + 1);
-    const int e_ = c + 1, w_ = c - 1, n_ = c + HX, s_ = c - HX;
-    int slot = 0;  // descriptor slot of the current tile
-    for (int it = 0; tile < total_tiles; ++it, tile += gridDim.x) {
-        float2 *raw = (it & 1) ? raw1 : raw0, *base = (it & 1) ? base1 : base0;
-        const int nslot = slot == 2 ? 0 : slot + 1, nnslot = nslot == 2 ? 0 : nslot + 1;
-        const bool has_next = tile + (int)gridDim.x < total_tiles;
-        if (has_next) x2_issue<STAGE, TX, H>(desc[nslot], er, ex, (it & 1) ? raw0 : raw1, (it & 1) ? base0 : base1);
-        cp_async_commit();
-        // the tile after next: described now, visible after the barriers below
-        if (threadIdx.x == 0 && tile + 2 * (int)gridDim.x < total_tiles)
-            make_desc<TX, H>(src, tile + 2 * gridDim.x, gi, STAGE, &desc[nnslot]);
-        cp_async_wait1();  // this tile's copies (all but the newest group) have landed
-        __syncthreads();
-
-        // primitives of the halo: u, v, p, T
-        for (int e = threadIdx.x; e < HALO; e += NT) {
-            const float2 rho = raw[e], mx = raw[HALO + e], my = raw[2 * HALO + e], E = raw[3 * HALO + e];
-            const float2 rinv = make_float2(__fdividef(1.f, rho.x), __fdividef(1.f, rho.y));
-            const float2 u = mul2(mx, rinv), v = mul2(my, rinv);
-            const float2 ke = mul2(mul2(f2(0.5f), rho), fma2(u, u, mul2(v, v)));
-            const float2 p = mul2(f2(gm1), sub2(E, ke));
-            prim[e] = u;
-            prim[HALO + e] = v;
-            prim[2 * HALO + e] = p;
-            prim[3 * HALO + e] = mul2(p, rinv);
-        }
-        __syncthreads();
-
-        const TileDesc &d = desc[slot];
+    __syncthreads();
+    x2_issue<TX, H>(desc[0], cr, cx, reinterpret_cast<float *>(raw_base));
+    cp_async_commit();
+    if (tile + G < total_tiles) x2_issue<TX, H>(desc[1], cr, cx, reinterpret_cast<float *>(raw_base + 4 * HALO));
+    cp_async_commit();
+    cp_async_wait1();  // tile 0's halo has landed
+    __syncthreads();
+    x2_prims<HALO, NT>(raw_base, prim_base, gm1);
+    for (int it = 0; tile < total_tiles; ++it, tile += G) {
+        cp_async_wait0();  // tile it + 1's halo has landed
+        __syncthreads();   // publishes it and the primitives of tile it; iteration it - 1 is done everywhere
+        const TileDesc &d = desc[it & 3];
         const int n = d.n, plane = n * n;
         const int x = d.x0 + lx, ya = d.y0 + ly, yb = ya + H;
-        if (x < n && ya < n) {
-            const float2 *Q1 = raw + HALO, *Q2 = raw + 2 * HALO, *Q3 = raw + 3 * HALO;
-            const float2 *U = prim, *V = prim + HALO, *P = prim + 2 * HALO, *TT = prim + 3 * HALO;
-            const float2 ih = f2(d.inv_h), mi2h = f2(-d.inv_2h), q4h = f2(0.5f * d.inv_2h);
-            const float2 c43mu = f2(4.f / 3.f * mu), mc23mu = f2(-2.f / 3.f * mu), mu2 = f2(mu), half = f2(0.5f);
-            const float2 kih = f2(kap * d.inv_h);
-            float2 r[4];
-            {   // inviscid part: central differences of the nodal fluxes
-                const float2 mxe = Q1[e_], mxw = Q1[w_], myn = Q2[n_], mys = Q2[s_];
-                const float2 Ue = U[e_], Uw = U[w_], Vn = V[n_], Vs = V[s_];
-                const float2 Pe = P[e_], Pw = P[w_], Pn = P[n_], Ps = P[s_];
-                const float2 Fe1 = fma2(mxe, Ue, Pe), Fw1 = fma2(mxw, Uw, Pw);
-                const float2 Fe2 = mul2(mxe, V[e_]), Fw2 = mul2(mxw, V[w_]);
-                const float2 Fe3 = mul2(add2(Q3[e_], Pe), Ue), Fw3 = mul2(add2(Q3[w_], Pw), Uw);
-                const float2 Gn1 = mul2(myn, U[n_]), Gs1 = mul2(mys, U[s_]);
-                const float2 Gn2 = fma2(myn, Vn, Pn), Gs2 = fma2(mys, Vs, Ps);
-                const float2 Gn3 = mul2(add2(Q3[n_], Pn), Vn), Gs3 = mul2(add2(Q3[s_], Ps), Vs);
-                r[0] = mul2(add2(sub2(mxe, mxw), sub2(myn, mys)), mi2h);
-                r[1] = mul2(add2(sub2(Fe1, Fw1), sub2(Gn1, Gs1)), mi2h);
-                r[2] = mul2(add2(sub2(Fe2, Fw2), sub2(Gn2, Gs2)), mi2h);
-                r[3] = mul2(add2(sub2(Fe3, Fw3), sub2(Gn3, Gs3)), mi2h);
-            }
-            // viscous and heat fluxes on the four faces of the node
-            float2 fx[2][3], fy[2][3];
+        const bool ok = x < n && ya < n, has_b = ok && yb < n;
+        float2 b[4];  // u0 at the thread's two points (stages 1, 2), consumed at the end of the iteration
+        if (STAGE != 0) {
+            const float *pa = d.u0 + (ok ? ya * n + x : 0);
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                {   // x-face between columns a and b = a + 1
-                    const int a = side ? c : w_, b = side ? e_ : c;
-                    const float2 Ua = U[a], Ub = U[b], Va = V[a], Vb = V[b];
-                    const float2 ux = mul2(sub2(Ub, Ua), ih), vx = mul2(sub2(Vb, Va), ih);
-                    const float2 uy = mul2(add2(sub2(U[a + HX], U[a - HX]), sub2(U[b + HX], U[b - HX])), q4h);
-                    const float2 vy = mul2(add2(sub2(V[a + HX], V[a - HX]), sub2(V[b + HX], V[b - HX])), q4h);
-                    const float2 txx = fma2(c43mu, ux, mul2(mc23mu, vy)), txy = mul2(mu2, add2(uy, vx));
-                    const float2 uf = mul2(half, add2(Ua, Ub)), vf = mul2(half, add2(Va, Vb));
-                    fx[side][0] = txx;
-                    fx[side][1] = txy;
-                    fx[side][2] = fma2(txx, uf, fma2(txy, vf, mul2(kih, sub2(TT[b], TT[a]))));
-                }
-                {   // y-face between rows a and b = a + 1
-                    const int a = side ? c : s_, b = side ? n_ : c;
-                    const float2 Ua = U[a], Ub = U[b], Va = V[a], Vb = V[b];
-                    const float2 uy = mul2(sub2(Ub, Ua), ih), vy = mul2(sub2(Vb, Va), ih);
-                    const float2 ux = mul2(add2(sub2(U[a + 1], U[a - 1]), sub2(U[b + 1], U[b - 1])), q4h);
-                    const float2 vx = mul2(add2(sub2(V[a + 1], V[a - 1]), sub2(V[b + 1], V[b - 1])), q4h);
-                    const float2 tyy = fma2(c43mu, vy, mul2(mc23mu, ux)), txy = mul2(mu2, add2(uy, vx));
-                    const float2 uf = mul2(half, add2(Ua, Ub)), vf = mul2(half, add2(Va, Vb));
-                    fy[side][0] = txy;
-                    fy[side][1] = tyy;
-                    fy[side][2] = fma2(txy, uf, fma2(tyy, vf, mul2(kih, sub2(TT[b], TT[a]))));
-                }
-            }
-            float2 L[4];
-            L[0] = r[0];
-#pragma unroll
-            for (int k = 1; k < 4; ++k)
-                L[k] = fma2(add2(sub2(fx[1][k - 1], fx[0][k - 1]), sub2(fy[1][k - 1], fy[0][k - 1])), ih, r[k]);
+            for (int k = 0; k < 4; ++k)
+                b[k] = make_float2(ok ? pa[k * plane] : 0.f, has_b ? pa[k * plane + H * n] : 0.f);
+        }
+        const bool has1 = tile + G < total_tiles, has2 = tile + 2 * G < total_tiles;
+        if (threadIdx.x == 0 && tile + 3 * G < total_tiles) make_desc<TX, H>(src, tile + 3 * G, gi, STAGE, &desc[(it + 3) & 3]);
+        if (has2) x2_issue<TX, H>(desc[(it + 2) & 3], cr, cx, reinterpret_cast<float *>(raw_base + ((it + 2) % 3) * 4 * HALO));
+        cp_async_commit();
+        const float2 *raw = raw_base + (it % 3) * 4 * HALO;
+        if (has1) x2_prims<HALO, NT>(raw_base + ((it + 1) % 3) * 4 * HALO, prim_base + ((it + 1) & 1) * 4 * HALO, gm1);
 
+        if (ok) {
+            float2 L[4];
+            x2_rhs<HX, HALO>(raw, prim_base + (it & 1) * 4 * HALO, c, d.inv_h, d.inv_2h, mu, kap, L);
             float *oa = d.out + ya * n + x, *ob = oa + H * n;
-            const bool has_b = yb < n;
             const float2 dt = f2(d.dt);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float2 kq = mul2(dt, L[k]);
                 const float2 sv = raw[k * HALO + c];
                 float2 res;
-                if (STAGE == 0) {
+                if (STAGE == 0)
                     res = add2(sv, kq);
-                } else {
-                    float2 b = base[k * NT + threadIdx.x];
-                    if (!has_b) b.y = 0.f;  // never stored; keeps the unused lane finite
-                    res = fma2(f2(STAGE == 1 ? 0.25f : 2.f / 3.f), add2(sub2(sv, b), kq), b);
-                }
+                else
+                    res = fma2(f2(STAGE == 1 ? 0.25f : 2.f / 3.f), add2(sub2(sv, b[k]), kq), b[k]);
                 oa[k * plane] = res.x;
                 if (has_b) ob[k * plane] = res.y;
             }
         }
-        slot = nslot;
-        __syncthreads();  // buffers of this tile, prim and its descriptor slot are reused later
     }
 }
 
@@ -436,7 +435,7 @@ template <int STAGE, int TX, int H, class Tiles>
 static int x2_grid(int total_tiles) {
     static int per_sm = 0, sms = 0;
     if (!per_sm) {
-        const size_t smem = X2Smem<TX, H>::bytes(STAGE);
+        const size_t smem = X2Smem<TX, H>::bytes();
         cudaFuncSetAttribute(ns2d_stage_x2<STAGE, TX, H, Tiles>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ns2d_stage_x2<STAGE, TX, H, Tiles>, 256, smem);
@@ -451,7 +450,7 @@ static int x2_grid(int total_tiles) {
 template <int STAGE, int TX, int H, class Tiles>
 static void x2_launch(const Tiles &src, int total_tiles, float gm1, float mu, float kap, cudaStream_t s) {
     const int grid = x2_grid<STAGE, TX, H, Tiles>(total_tiles);
-    ns2d_stage_x2<STAGE, TX, H, Tiles><<<grid, 256, X2Smem<TX, H>::bytes(STAGE), s>>>(src, total_tiles, gm1, mu, kap);
+    ns2d_stage_x2<STAGE, TX, H, Tiles><<<grid, 256, X2Smem<TX, H>::bytes(), s>>>(src, total_tiles, gm1, mu, kap);
 }
 
 // per-handle FP64 launch: two groups (members, fine run) passed by value, 32 x 8 tiles

@@ -131,32 +131,48 @@ void launch_innov_rms(const double *Z, int ne, int ny, double *out, cudaStream_t
 }
 
 // perturbed observations (Eq. perturbed_y) and normalised anomalies Y (Algorithm 3 step 7)
+// One thread per Philox block: the 4 consecutive elements o = 4b .. 4b + 3 of
+// the Ne x Ny perturbation matrix (flat index o = i Ny + j).
 __global__ void k_obs_perturb(const double *__restrict__ yf, const double *__restrict__ ybar,
                               const double *__restrict__ yo, double *__restrict__ eps, int gen_eps,
                               uint64_t seed, const uint64_t *__restrict__ cycle, double sigma, int ne,
                               int ny, double *__restrict__ Y, double *__restrict__ Z) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y;
-    if (j >= ny) return;
-    const size_t o = (size_t)i * ny + j;
-    double e;
-    if (gen_eps) {
-        e = sigma * philox_normal(seed, kEpsTag, *cycle, (uint64_t)o);
-        eps[o] = e;
-    } else {
-        e = eps[o];
+    const size_t total = (size_t)ne * ny;
+    const size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (4 * b >= total) return;
+    double z[4];
+    if (gen_eps) philox_normals4(seed, kEpsTag, *cycle, (uint64_t)b, z);
+    const double isq = 1.0 / sqrt((double)(ne - 1));
+    int i = (int)((4 * b) / ny), j = (int)(4 * b - (size_t)i * ny);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const size_t o = 4 * b + l;
+        if (o < total) {
+            double e;
+            if (gen_eps) {
+                e = sigma * z[l];
+                eps[o] = e;
+            } else {
+                e = eps[o];
+            }
+            const double f = yf[o];
+            Y[o] = (f - ybar[j]) * isq;
+            Z[o] = yo[j] + e - f;
+        }
+        if (++j == ny) {
+            j = 0;
+            ++i;
+        }
     }
-    const double f = yf[o];
-    Y[o] = (f - ybar[j]) * (1.0 / sqrt((double)(ne - 1)));
-    Z[o] = yo[j] + e - f;
 }
 
 void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, double *eps,
                         int gen_eps, uint64_t seed, const uint64_t *cycle, double sigma, int ne, int ny,
                         double *Y, double *Z, cudaStream_t s) {
     count_launches(1);
-    dim3 grid(ceil_div(ny, 128), ne);
-    k_obs_perturb<<<grid, 128, 0, s>>>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma, ne, ny, Y, Z);
+    const size_t blocks = ((size_t)ne * ny + 3) / 4;
+    k_obs_perturb<<<(unsigned)ceil_div(blocks, 128), 128, 0, s>>>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma,
+                                                                   ne, ny, Y, Z);
 }
 
 // ---------------------------------------------------------------------------
@@ -196,10 +212,13 @@ __global__ void __launch_bounds__(256) k_ens_anom(const T *__restrict__ m, size_
             for (int i = wp; i < ne; i += 8) X64[(size_t)i * nx + p] = ((double)m[(size_t)i * nx + p] - xb) * isq;
         return;
     }
-    // BF16 path: FP64 centring, FP32 scaling (the BF16 rounding dominates)
-    const float isqf = (float)isq;
+    // BF16 path: FP64 mean, FP32 centring and scaling.  The FP32 rounding of
+    // the mean (2^-24 of the state) is far below the BF16 rounding of the
+    // anomaly (2^-9 of the anomaly) for any spread above 2^-15 of the state,
+    // and GB300's FP64 pipe is 64x slower than its FP32 pipes.
+    const float isqf = (float)isq, xbf = (float)xb;
     for (int i = wp; i < ldx; i += 8)
-        tile[lane * ldt + i] = __float2bfloat16((ok && i < ne) ? (float)((double)m[(size_t)i * nx + p] - xb) * isqf : 0.f);
+        tile[lane * ldt + i] = __float2bfloat16((ok && i < ne) ? ((float)m[(size_t)i * nx + p] - xbf) * isqf : 0.f);
     __syncthreads();
     // store: row r of the tile (point p0 + r) is ldx bf16 = ldx/8 16-byte chunks
     const int chunks = ldx / 8;
@@ -832,18 +851,24 @@ void launch_tt_bf16(const double *Tm, __nv_bfloat16 *Tt, int ne, int ld, const i
     k_tt_bf16<<<grid_for((size_t)(ne + 1) * ne, 256), 256, 0, s>>>(Tm, Tt, ne, ld, status);
 }
 
+// one thread per Philox block (4 normals)
 __global__ void k_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count,
                           double *__restrict__ out) {
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < count;
-         n += (int64_t)gridDim.x * blockDim.x)
-        out[n] = philox_normal(seed, tag, ctr0, (uint64_t)n);
+    const int64_t nblk = (count + 3) / 4;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x) {
+        double z[4];
+        philox_normals4(seed, tag, ctr0, (uint64_t)b, z);
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+            if (4 * b + l < count) out[4 * b + l] = z[l];
+    }
 }
 
 void launch_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count, double *out,
                     cudaStream_t s) {
     if (count <= 0) return;
     count_launches(1);
-    k_normals<<<grid_for((size_t)count, 256), 256, 0, s>>>(seed, tag, ctr0, count, out);
+    k_normals<<<grid_for((size_t)((count + 3) / 4), 256), 256, 0, s>>>(seed, tag, ctr0, count, out);
 }
 
 // ---------------------------------------------------------------------------

@@ -52,20 +52,22 @@ __device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_
     return o;
 }
 
-// normal number n of the stream (seed, tag, ctr0)
-__device__ __forceinline__ double philox_normal(uint64_t seed, uint64_t tag, uint64_t ctr0,
-                                                uint64_t n) {
-    const U64x4 x = philox4x64_10(ctr0, n >> 2, 0, 0, seed, tag);
-    const int lane = (int)(n & 3);
-    const int pair = lane >> 1;
-    const uint64_t a = pair ? x.v[2] : x.v[0];
-    const uint64_t b = pair ? x.v[3] : x.v[1];
+// Normals n = 4 blk .. 4 blk + 3 of the stream (seed, tag, ctr0): Philox block
+// (ctr0, blk, 0, 0) with key (seed, tag); lanes (0, 1) and (2, 3) give one
+// Box-Muller pair each, u = ((x >> 11) + 1) 2^-53, z = sqrt(-2 ln u1) (cos, sin)(2 pi u2).
+__device__ __forceinline__ void philox_normals4(uint64_t seed, uint64_t tag, uint64_t ctr0, uint64_t blk,
+                                                double (&z)[4]) {
+    const U64x4 x = philox4x64_10(ctr0, blk, 0, 0, seed, tag);
     const double inv53 = 1.0 / 9007199254740992.0;
-    const double u1 = (double)((a >> 11) + 1) * inv53;
-    const double u2 = (double)((b >> 11) + 1) * inv53;
-    const double rad = sqrt(-2.0 * log(u1));
-    const double th = 6.283185307179586 * u2;
-    return (lane & 1) ? rad * sin(th) : rad * cos(th);
+#pragma unroll
+    for (int pair = 0; pair < 2; ++pair) {
+        const double u1 = (double)((x.v[2 * pair] >> 11) + 1) * inv53;
+        const double u2 = (double)((x.v[2 * pair + 1] >> 11) + 1) * inv53;
+        const double rad = sqrt(-2.0 * log(u1));
+        const double th = 6.283185307179586 * u2;
+        z[2 * pair] = rad * cos(th);
+        z[2 * pair + 1] = rad * sin(th);
+    }
 }
 
 constexpr uint64_t kEpsTag = 0x45505300ULL;  // "EPS\0": perturbation stream of the analysis

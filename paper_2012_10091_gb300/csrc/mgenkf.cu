@@ -760,7 +760,9 @@ extern "C" uint64_t mgk_kernel_launches(void) { return g_launches.load(std::memo
 // batched cycles of independent NS-2D handles: one CUDA graph launch per cycle
 // ===========================================================================
 namespace {
-constexpr int kBatchStreams = 16;
+// analysis branches of the captured cycle (problem j on branch j mod count)
+constexpr int kMaxBatchStreams = 128;
+constexpr int kDefaultBatchBranches = 16;  // measured best for the 96-problem batch (1, 4, 16, 128 tried)
 }
 
 struct mgenkf_batch {
@@ -768,6 +770,7 @@ struct mgenkf_batch {
     cudaStream_t s0 = nullptr;
     bool own_s0 = false;  // created here when the caller passed the legacy stream
     std::vector<cudaStream_t> aux;
+    int nbranch = 1;  // analysis branches (streams aux[0 .. nbranch))
     std::vector<cudaEvent_t> ev;
     double *obs_stage = nullptr;
     double *innov = nullptr;  // per-problem innovation RMS of the last cycle
@@ -935,12 +938,18 @@ extern "C" mgenkf_status mgenkf_batch_create(const mgenkf_handle *handles, int32
         cudaGetLastError();
         return fail(MGENKF_ERR_OOM, "observation staging buffer");
     }
-    for (int k = 0; k < kBatchStreams; ++k) {
+    // MGENKF_BATCH_STREAMS caps the analysis branches (used to measure how much
+    // their concurrency buys)
+    int cap = kDefaultBatchBranches;
+    if (const char *e = getenv("MGENKF_BATCH_STREAMS")) cap = std::max(1, std::min(kMaxBatchStreams, atoi(e)));
+    b->nbranch = std::min(n, cap);
+    const int nstreams = std::max(kNsTileShapes, b->nbranch);
+    for (int k = 0; k < nstreams; ++k) {
         cudaStream_t s;
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(MGENKF_ERR_CUDA, "stream");
         b->aux.push_back(s);
     }
-    for (int k = 0; k < 2 * kBatchStreams + 2 * kNsTileShapes + 2; ++k) {
+    for (int k = 0; k < 2 * nstreams + 2 * kNsTileShapes + 2; ++k) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(MGENKF_ERR_CUDA, "event");
         b->ev.push_back(e);
@@ -987,7 +996,7 @@ static mgenkf_status batch_forecast(mgenkf_batch *b, int nsteps) {
 static mgenkf_status batch_analyse(mgenkf_batch *b) {
     const int base = 1 + kNsTileShapes;
     B_CUDA(cudaEventRecord(b->ev[base], b->s0));
-    const int ns = (int)std::min<size_t>(b->aux.size(), b->hs.size());
+    const int ns = b->nbranch;
     for (int k = 0; k < ns; ++k) B_CUDA(cudaStreamWaitEvent(b->aux[k], b->ev[base], 0));
     for (size_t j = 0; j < b->hs.size(); ++j) {
         mgenkf_ctx *h = b->hs[j];

@@ -177,8 +177,8 @@ mgenkf_status mgenkf_destroy(mgenkf_handle h);
  * Many independent NS-2D MGEnKF problems (uneven grid sizes, ensemble sizes
  * and observation counts) advanced together: the forecast of every problem's
  * members and fine run is one launch sequence per tile shape over a table of
- * all grids, and each problem's analysis and prolongation run on one of 16 (MGENKF_BATCH_STREAMS: 1 to 128)
- * streams.  The whole cycle is captured once into a CUDA graph and replayed by
+ * all grids, and each problem's analysis and prolongation run on one of 16
+ * streams (MGENKF_BATCH_STREAMS overrides: 1 to 128).  The whole cycle is captured once into a CUDA graph and replayed by
  * one graph launch per cycle (recaptured if nsteps changes).  The handles stay
  * owned by the caller and must outlive the batch; they must all be
  * MGENKF_NS2D / MGENKF_MIXED with equal gamma, mu and Pr.  While a batch

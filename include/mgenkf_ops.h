@@ -27,8 +27,9 @@ extern "C" {
  *   n: points per side; length: domain side; dt: time step; nu: viscosity
  *   (Burgers) or mu = 1/Re (NS); gamma, prandtl: NS gas constants (ignored for
  *   Burgers).
- * Limits: Burgers n in [4, 32768]; NS n in [8, 4096] and n % 8 == 0.  Outside
- * them: MGENKF_ERR_INVALID_ARG. */
+ * Limits: Burgers n in [4, 32768]; NS n in [8, 4096] and n % 8 == 0; NS FP32
+ * states start on a 16-byte boundary (the halo is copied in 16-byte chunks).
+ * Outside them: MGENKF_ERR_INVALID_ARG. */
 mgenkf_status mgk_forecast(int32_t model, int32_t precision, void *state, int32_t nprob, int32_t n,
                            double length, double dt, double nu, double gamma, double prandtl,
                            int32_t nsteps, void *stream);

@@ -245,46 +245,70 @@ __device__ __forceinline__ void make_desc(const Tiles &src, int tile, int &gi, i
 template <int TX, int H>
 struct X2Smem {
     static constexpr int HX = TX + 2, HALO = HX * (H + 2), NT = TX * H;
-    static constexpr int COPIES = (2 * HALO + NT - 1) / NT;  // (element, row half) pairs a thread copies
-    // raw conserved halo (3 buffers), primitives of the halo (2 buffers), 4 tile descriptors
-    static constexpr size_t bytes() { return sizeof(float2) * (3 * 4 * HALO + 2 * 4 * HALO) + 4 * sizeof(TileDesc); }
+    // raw halo: rows y0 - 1 .. y0 + 2H, columns x0 - 4 .. x0 + TX + 3 (16-byte
+    // aligned), 4 planes, row-major
+    static constexpr int RW = TX + 8, RR = 2 * H + 2, RAW = 4 * RR * RW;  // floats
+    static constexpr int CHUNKS = 4 * RR * (RW / 4);                      // 16-byte copies per tile
+    static constexpr int COPIES = (CHUNKS + NT - 1) / NT;                 // per thread
+    // 2 raw buffers, 2 folded buffers of 8 arrays (rho, rho u, rho v, E, u, v, p, T), 4 descriptors
+    static constexpr size_t bytes() {
+        return sizeof(float) * 2 * RAW + sizeof(float2) * 2 * 8 * HALO + 4 * sizeof(TileDesc);
+    }
 };
 
-// Issue the asynchronous copies of one tile's folded halo (4 conserved
-// planes) into one buffer.  Copy c of a thread is (element c >> 1, row half
-// c & 1): neighbouring lanes fill the two 4-byte halves of one float2, so a
-// warp writes 128 contiguous bytes.
+// 16-byte asynchronous global -> shared copy (L2 only: each chunk is read once per tile)
+__device__ __forceinline__ void cp_async16(void *smem, const float *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Issue the 16-byte copies of one tile's raw halo into one buffer.  Copy c of
+// a thread is (plane, row, chunk); x0 - 4 and n are multiples of 4, so a
+// chunk never straddles the periodic wrap.
 template <int TX, int H>
-__device__ __forceinline__ void x2_issue(const TileDesc &d, const int (&cr)[X2Smem<TX, H>::COPIES],
+__device__ __forceinline__ void x2_issue(const TileDesc &d, const int (&ck)[X2Smem<TX, H>::COPIES],
+                                         const int (&cr)[X2Smem<TX, H>::COPIES],
                                          const int (&cx)[X2Smem<TX, H>::COPIES], float *raw) {
     using S = X2Smem<TX, H>;
     const int n = d.n, plane = n * n;  // 4 planes of one grid stay below 2^31 elements
 #pragma unroll
     for (int q = 0; q < S::COPIES; ++q) {
         const int c = threadIdx.x + q * S::NT;
-        if (c < 2 * S::HALO) {
-            const float *src = d.in + wrap_index(d.y0 + cr[q], n) * n + wrap_index(d.x0 + cx[q], n);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) cp_async4(raw + 2 * k * S::HALO + c, src + k * plane);
+        if (c < S::CHUNKS) {
+            const float *src = d.in + ck[q] * plane + wrap_index(d.y0 - 1 + cr[q], n) * n + wrap_index(d.x0 - 4 + cx[q], n);
+            cp_async16(raw + (ck[q] * S::RR + cr[q]) * S::RW + cx[q], src);
         }
     }
 }
 
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// primitives u, v, p, T of halo elements e = threadIdx.x, + NT, ...
-template <int HALO, int NT>
-__device__ __forceinline__ void x2_prims(const float2 *raw, float2 *prim, float gm1) {
-    for (int e = threadIdx.x; e < HALO; e += NT) {
-        const float2 rho = raw[e], mx = raw[HALO + e], my = raw[2 * HALO + e], E = raw[3 * HALO + e];
+// Fold the raw halo and form the primitives: folded element e (row r, column
+// lx) holds rows r and r + H of the raw block at column lx + 3.  Writes the 8
+// folded arrays rho, rho u, rho v, E, u, v, p, T.
+template <int TX, int H>
+__device__ __forceinline__ void x2_fold(const float *raw, float2 *fold, float gm1) {
+    using S = X2Smem<TX, H>;
+    constexpr int HALO = S::HALO;
+    for (int e = threadIdx.x; e < HALO; e += S::NT) {
+        const int r = e / S::HX, lx = e - r * S::HX;
+        const float *pa = raw + r * S::RW + lx + 3, *pb = pa + H * S::RW;
+        const float2 rho = make_float2(pa[0], pb[0]);
+        const float2 mx = make_float2(pa[S::RR * S::RW], pb[S::RR * S::RW]);
+        const float2 my = make_float2(pa[2 * S::RR * S::RW], pb[2 * S::RR * S::RW]);
+        const float2 E = make_float2(pa[3 * S::RR * S::RW], pb[3 * S::RR * S::RW]);
         const float2 rinv = make_float2(__fdividef(1.f, rho.x), __fdividef(1.f, rho.y));
         const float2 u = mul2(mx, rinv), v = mul2(my, rinv);
         const float2 ke = mul2(mul2(f2(0.5f), rho), fma2(u, u, mul2(v, v)));
         const float2 p = mul2(f2(gm1), sub2(E, ke));
-        prim[e] = u;
-        prim[HALO + e] = v;
-        prim[2 * HALO + e] = p;
-        prim[3 * HALO + e] = mul2(p, rinv);
+        fold[e] = rho;
+        fold[HALO + e] = mx;
+        fold[2 * HALO + e] = my;
+        fold[3 * HALO + e] = E;
+        fold[4 * HALO + e] = u;
+        fold[5 * HALO + e] = v;
+        fold[6 * HALO + e] = p;
+        fold[7 * HALO + e] = mul2(p, rinv);
     }
 }
 
@@ -350,20 +374,20 @@ __device__ __forceinline__ void x2_rhs(const float2 *raw, const float2 *prim, in
 }
 
 // Persistent stage kernel: each CTA walks tiles blockIdx.x, + gridDim.x, ...
-// with one barrier per tile.  In iteration i it copies the halo of tile i + 2
-// (3 raw buffers), forms the primitives of tile i + 1 (2 buffers) and computes
-// tile i; thread 0 describes tile i + 3 (4 descriptor slots).  Stages 1 and
-// 2 load u0 at the thread's points at the start of the iteration and use it at
-// the end.  At most 85 registers: three CTAs per SM.
+// with one barrier per tile.  In iteration i it copies the raw halo of tile
+// i + 2 (2 raw buffers), folds tile i + 1 and forms its primitives (2 folded
+// buffers) and computes tile i; thread 0 describes tile i + 3 (4 descriptor
+// slots).  Stages 1 and 2 load u0 at the thread's points at the start of the
+// iteration and use it at the end.  At most 85 registers: three CTAs per SM.
 template <int STAGE, int TX, int H, class Tiles>
 __global__ void __launch_bounds__(256, 3) ns2d_stage_x2(Tiles src, int total_tiles, float gm1, float mu, float kap) {
     using S = X2Smem<TX, H>;
     constexpr int HX = S::HX, HALO = S::HALO, NT = S::NT;
     static_assert(NT == 256, "256 threads per CTA");
     extern __shared__ float4 x2_smem4[];
-    float2 *raw_base = reinterpret_cast<float2 *>(x2_smem4);
-    float2 *prim_base = raw_base + 3 * 4 * HALO;
-    TileDesc *desc = reinterpret_cast<TileDesc *>(prim_base + 2 * 4 * HALO);
+    float *raw_base = reinterpret_cast<float *>(x2_smem4);
+    float2 *fold_base = reinterpret_cast<float2 *>(raw_base + 2 * S::RAW);
+    TileDesc *desc = reinterpret_cast<TileDesc *>(fold_base + 2 * 8 * HALO);
     const int G = gridDim.x;
     int tile = blockIdx.x;
     if (tile >= total_tiles) return;
@@ -371,26 +395,27 @@ __global__ void __launch_bounds__(256, 3) ns2d_stage_x2(Tiles src, int total_til
     if (threadIdx.x == 0)
         for (int q = 0; q < 3; ++q)
             if (tile + q * G < total_tiles) make_desc<TX, H>(src, tile + q * G, gi, STAGE, &desc[q]);
-    int cr[S::COPIES], cx[S::COPIES];  // halo row / column offsets of the thread's copies, relative to (y0, x0)
+    int ck[S::COPIES], cr[S::COPIES], cx[S::COPIES];  // plane, raw row, first column of the thread's copies
 #pragma unroll
     for (int q = 0; q < S::COPIES; ++q) {
-        const int c = threadIdx.x + q * NT, e = c >> 1, r = e / HX;
-        cr[q] = r - 1 + ((c & 1) ? H : 0);
-        cx[q] = e - r * HX - 1;
+        const int c = threadIdx.x + q * NT, row = c / (S::RW / 4), k = row / S::RR;
+        ck[q] = k;
+        cr[q] = row - k * S::RR;
+        cx[q] = 4 * (c - row * (S::RW / 4));
     }
     const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
     const int c = (ly + 1) * HX + (lx + 1);
     __syncthreads();
-    x2_issue<TX, H>(desc[0], cr, cx, reinterpret_cast<float *>(raw_base));
+    x2_issue<TX, H>(desc[0], ck, cr, cx, raw_base);
     cp_async_commit();
-    if (tile + G < total_tiles) x2_issue<TX, H>(desc[1], cr, cx, reinterpret_cast<float *>(raw_base + 4 * HALO));
+    if (tile + G < total_tiles) x2_issue<TX, H>(desc[1], ck, cr, cx, raw_base + S::RAW);
     cp_async_commit();
     cp_async_wait1();  // tile 0's halo has landed
     __syncthreads();
-    x2_prims<HALO, NT>(raw_base, prim_base, gm1);
+    x2_fold<TX, H>(raw_base, fold_base, gm1);
     for (int it = 0; tile < total_tiles; ++it, tile += G) {
         cp_async_wait0();  // tile it + 1's halo has landed
-        __syncthreads();   // publishes it and the primitives of tile it; iteration it - 1 is done everywhere
+        __syncthreads();   // publishes it and the folded tile it; iteration it - 1 is done everywhere
         const TileDesc &d = desc[it & 3];
         const int n = d.n, plane = n * n;
         const int x = d.x0 + lx, ya = d.y0 + ly, yb = ya + H;
@@ -404,20 +429,21 @@ __global__ void __launch_bounds__(256, 3) ns2d_stage_x2(Tiles src, int total_til
         }
         const bool has1 = tile + G < total_tiles, has2 = tile + 2 * G < total_tiles;
         if (threadIdx.x == 0 && tile + 3 * G < total_tiles) make_desc<TX, H>(src, tile + 3 * G, gi, STAGE, &desc[(it + 3) & 3]);
-        if (has2) x2_issue<TX, H>(desc[(it + 2) & 3], cr, cx, reinterpret_cast<float *>(raw_base + ((it + 2) % 3) * 4 * HALO));
+        // tile it + 2 goes to the raw buffer of tile it, folded in iteration it - 1
+        if (has2) x2_issue<TX, H>(desc[(it + 2) & 3], ck, cr, cx, raw_base + (it & 1) * S::RAW);
         cp_async_commit();
-        const float2 *raw = raw_base + (it % 3) * 4 * HALO;
-        if (has1) x2_prims<HALO, NT>(raw_base + ((it + 1) % 3) * 4 * HALO, prim_base + ((it + 1) & 1) * 4 * HALO, gm1);
+        if (has1) x2_fold<TX, H>(raw_base + ((it + 1) & 1) * S::RAW, fold_base + ((it + 1) & 1) * 8 * HALO, gm1);
+        const float2 *fq = fold_base + (it & 1) * 8 * HALO;
 
         if (ok) {
             float2 L[4];
-            x2_rhs<HX, HALO>(raw, prim_base + (it & 1) * 4 * HALO, c, d.inv_h, d.inv_2h, mu, kap, L);
+            x2_rhs<HX, HALO>(fq, fq + 4 * HALO, c, d.inv_h, d.inv_2h, mu, kap, L);
             float *oa = d.out + ya * n + x, *ob = oa + H * n;
             const float2 dt = f2(d.dt);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float2 kq = mul2(dt, L[k]);
-                const float2 sv = raw[k * HALO + c];
+                const float2 sv = fq[k * HALO + c];
                 float2 res;
                 if (STAGE == 0)
                     res = add2(sv, kq);
@@ -510,6 +536,10 @@ cudaError_t ns2d_forecast_scratch(T *whole, int n_whole, int n_whole_probs, T *s
     const int grid = tiles[0] + tiles[1];
     if (grid == 0 || nsteps == 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
+        // the halo is copied in 16-byte chunks
+        if ((reinterpret_cast<uintptr_t>(whole) | reinterpret_cast<uintptr_t>(split) |
+             reinterpret_cast<uintptr_t>(scratch)) & 15)
+            return cudaErrorMisalignedAddress;
         PairTiles P{{A.g[0], A.g[1]}};
         P.g[0].tile_begin = 0;
         P.g[1].tile_begin = tiles[0];

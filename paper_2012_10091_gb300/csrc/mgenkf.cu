@@ -720,6 +720,10 @@ extern "C" mgenkf_status mgk_forecast(int32_t model, int32_t precision, void *st
             g_ops_error = why;
             return MGENKF_ERR_INVALID_ARG;
         }
+        if (precision == MGENKF_MIXED && (reinterpret_cast<uintptr_t>(state) & 15)) {
+            g_ops_error = "NS-2D FP32 states must start on a 16-byte boundary";
+            return MGENKF_ERR_INVALID_ARG;
+        }
         if (precision == MGENKF_MIXED)
             e = ns2d_forecast<float>((float *)state, n, nprob, nullptr, 0, 0, length, dt, nu, gamma, prandtl, nsteps, s);
         else

@@ -82,3 +82,22 @@ def test_singular_innovation_matrix_reported(M):
     fine, mem = g.get_state()
     np.testing.assert_array_equal(mem, inp["members0"])
     np.testing.assert_array_equal(fine, inp["fine0"])
+
+
+def test_misaligned_fp32_ns_state_is_rejected(M):
+    """The FP32 NS-2D forecast copies its halo in 16-byte chunks: a state that
+    does not start on a 16-byte boundary is refused on the host, before any
+    launch, and an aligned one advances."""
+    import torch
+    n = 16
+    buf = torch.ones(4 * n * n + 4, dtype=torch.float32, device="cuda")
+    buf[3 * n * n + 1:] = 10.0
+    with pytest.raises(M.MGEnKFError) as e:
+        M.mgk_forecast(M.MGENKF_NS2D, M.MGENKF_MIXED, buf.data_ptr() + 4, 1, n, 1.0, 1e-4, 1e-3, 1.4, 0.72,
+                       nsteps=1)
+    assert "16-byte" in str(e.value)
+    x = buf[:4 * n * n].clone()
+    x[3 * n * n:] = 10.0
+    M.mgk_forecast(M.MGENKF_NS2D, M.MGENKF_MIXED, x, 1, n, 1.0, 1e-4, 1e-3, 1.4, 0.72, nsteps=1)
+    torch.cuda.synchronize()
+    assert torch.allclose(x[3 * n * n:], torch.full_like(x[3 * n * n:], 10.0))

@@ -339,7 +339,7 @@ static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const 
     if (h->mixed) {
         const char *sel = getenv("MGENKF_UPDATE");
         if (!(sel && strcmp(sel, "simt") == 0))
-            update_tc_prepare(&h->tc, h->X16, h->ldx, (int)h->nx, h->Tt, h->ntpad, h->ne);
+            update_tc_prepare(&h->tc, h->X16, h->ldx, (int)h->nx, h->Tt, h->ntpad, h->ne, (const float *)h->members);
     }
     H_CUDA(cudaStreamSynchronize(h->stream));
     return MGENKF_OK;

@@ -10,8 +10,11 @@
 //   * warp 0 allocates TMEM for the 128 x N FP32 accumulator;
 //   * one thread issues K/16 tcgen05.mma (kind::f16, cta_group::1) and commits
 //     them to a second mbarrier;
-//   * the four warps read their 32 TMEM lanes (tcgen05.ld 32x32b) and fuse the
-//     epilogue: members[c][p] += D[p][c] for c < Ne, dC[p] = D[p][Ne].
+//   * the same TMA transaction brings the members' 128-point tile ([Ne][128]
+//     FP32), so the epilogue never waits on global loads;
+//   * the four warps read their 32 TMEM lanes (tcgen05.ld 32x32b), add
+//     D[p][c] into the shared member tile (c < Ne) and store dC[p] = D[p][Ne];
+//     one thread writes the member tile back with a TMA store.
 // Every mbarrier wait is bounded (about a second of SM clocks); on expiry the
 // kernel records MGENKF_ERR_TIMEOUT in the status word, waits (bounded) for its
 // own copies, frees its TMEM and returns.
@@ -63,6 +66,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     }
 }
 
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
@@ -91,16 +103,17 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 
 __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ CUtensorMap map_x,
                                                    const __grid_constant__ CUtensorMap map_t,
-                                                   float *__restrict__ members, float *__restrict__ dC,
-                                                   int nx, int ne, int kblocks, int ntile, int tmem_cols,
-                                                   int *status) {
+                                                   const __grid_constant__ CUtensorMap map_m,
+                                                   float *__restrict__ dC, int nx, int ne, int kblocks,
+                                                   int ntile, int tmem_cols, int *status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned operand buffers
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char *sa = base;                                        // kblocks x [128][64] bf16
     unsigned char *sb = base + (size_t)kblocks * kTileM * 128;       // kblocks x [ntile][64] bf16
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sb + (size_t)kblocks * ntile * 128);
+    float *sm = reinterpret_cast<float *>(sb + (size_t)kblocks * ntile * 128);  // [ne][128] members
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + (size_t)ne * kTileM);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
     __shared__ int s_fail;
 
@@ -114,13 +127,14 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ CUten
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    const uint32_t tx_bytes = (uint32_t)kblocks * (kTileM + ntile) * 128;
+    const uint32_t tx_bytes = (uint32_t)kblocks * (kTileM + ntile) * 128 + (uint32_t)ne * kTileM * 4;
     if (tid == 0) {
         mbar_expect_tx(&bars[0], tx_bytes);
         for (int kb = 0; kb < kblocks; ++kb) {
             tma_load_2d(sa + (size_t)kb * kTileM * 128, &map_x, &bars[0], kb * kAtomK, m0);
             tma_load_2d(sb + (size_t)kb * ntile * 128, &map_t, &bars[0], kb * kAtomK, 0);
         }
+        tma_load_2d(sm, &map_m, &bars[0], m0, 0);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -166,7 +180,7 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ CUten
         }
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int p = m0 + warp * 32 + lane;
+        const int pl = warp * 32 + lane, p = m0 + pl;
         const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
         for (int c0 = 0; c0 < ntile; c0 += 16) {
             uint32_t r[16];
@@ -177,18 +191,21 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ CUten
                   "=r"(r[15])
                 : "r"(row + (uint32_t)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (p < nx) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int c = c0 + q;
-                    const float v = __uint_as_float(r[q]);
-                    if (c < ne)
-                        members[(size_t)c * nx + p] += v;
-                    else if (c == ne)
-                        dC[p] = v;
-                }
+            for (int q = 0; q < 16; ++q) {
+                const int c = c0 + q;
+                const float v = __uint_as_float(r[q]);
+                if (c < ne)
+                    sm[c * kTileM + pl] += v;  // rows past nx are clipped by the TMA store
+                else if (c == ne && p < nx)
+                    dC[p] = v;
             }
         }
+        // the member tile goes back with one TMA store (generic-proxy writes
+        // made visible to the async proxy first)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) tma_store_2d(&map_m, sm, m0, 0);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -228,25 +245,41 @@ static bool encode_kmajor(CUtensorMap *m, const __nv_bfloat16 *ptr, int ld, int 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool update_tc_supported(int ne, int ldx, int ntpad) {
+static size_t update_smem(int kblocks, int ntpad, int ne) {
+    return 1024 + (size_t)kblocks * (kTileM + ntpad) * 128 + (size_t)ne * kTileM * 4 + 64;
+}
+
+bool update_tc_supported(int ne, int ldx, int ntpad, int nx) {
     // N = ntpad rows of T in one MMA (<= 256), K = ldx (multiple of 16); TMA
-    // inner box of 64 values; the operands must fit shared memory.
-    if (ntpad < 16 || ntpad > 256 || ntpad % 16 || ldx % 16 || ne < 2) return false;
+    // inner box of 64 values; the member tile box is 128 x ne (ne <= 256) with
+    // rows of nx floats (a multiple of 16 bytes); all of it fits shared memory.
+    if (ntpad < 16 || ntpad > 256 || ntpad % 16 || ldx % 16 || ne < 2 || ne > 256 || nx % 4) return false;
     const int kblocks = (ldx + kAtomK - 1) / kAtomK;
-    const size_t smem = 1024 + (size_t)kblocks * (kTileM + ntpad) * 128 + 64;
-    return smem <= 200 * 1024 && encode_fn() != nullptr;
+    return update_smem(kblocks, ntpad, ne) <= 200 * 1024 && encode_fn() != nullptr;
+}
+
+static bool encode_members(CUtensorMap *m, const float *ptr, int nx, int ne) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ne};
+    const cuuint64_t strides[1] = {(cuuint64_t)nx * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kTileM, (cuuint32_t)ne};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool update_tc_prepare(UpdateTcPlan *plan, const __nv_bfloat16 *X16, int ldx, int nx, const __nv_bfloat16 *Tt,
-                       int ntpad, int ne) {
-    if (!update_tc_supported(ne, ldx, ntpad)) return false;
+                       int ntpad, int ne, const float *members) {
+    if (!update_tc_supported(ne, ldx, ntpad, nx)) return false;
     memset(plan, 0, sizeof(*plan));
     plan->kblocks = (ldx + kAtomK - 1) / kAtomK;
     plan->ntile = ntpad;
     int cols = 32;
     while (cols < ntpad) cols <<= 1;
     plan->tmem_cols = cols;
-    plan->smem = 1024 + (size_t)plan->kblocks * (kTileM + ntpad) * 128 + 64;
+    plan->smem = update_smem(plan->kblocks, ntpad, ne);
     // at most 512 / tmem_cols CTAs may share an SM's 512 TMEM columns: ask for
     // enough shared memory that no more are resident (no CTA ever waits in alloc)
     const size_t per_sm = 228 * 1024;
@@ -256,6 +289,8 @@ bool update_tc_prepare(UpdateTcPlan *plan, const __nv_bfloat16 *X16, int ldx, in
     plan->ne = ne;
     if (!encode_kmajor(&plan->map_x, X16, ldx, nx, kTileM)) return false;
     if (!encode_kmajor(&plan->map_t, Tt, ldx, ntpad, ntpad)) return false;
+    if (!encode_members(&plan->map_m, members, nx, ne)) return false;
+    plan->members = members;
     plan->ready = true;
     return true;
 }
@@ -266,9 +301,10 @@ cudaError_t launch_update_tc(const UpdateTcPlan &plan, float *members, float *dC
         cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
+    if (members != plan.members) return cudaErrorInvalidValue;
     count_launches(1);
     const int grid = (plan.nx + kTileM - 1) / kTileM;
-    k_update_tc<<<grid, 128, plan.smem, s>>>(plan.map_x, plan.map_t, members, dC, plan.nx, plan.ne, plan.kblocks,
+    k_update_tc<<<grid, 128, plan.smem, s>>>(plan.map_x, plan.map_t, plan.map_m, dC, plan.nx, plan.ne, plan.kblocks,
                                              plan.ntile, plan.tmem_cols, status);
     return cudaGetLastError();
 }

@@ -13,15 +13,18 @@ namespace mgk {
 struct UpdateTcPlan {
     CUtensorMap map_x;  // X^T, [nx][ldx] bf16, K-major, box 64 x 128
     CUtensorMap map_t;  // T^T, [ntpad][ldx] bf16, K-major, box 64 x ntpad
+    CUtensorMap map_m;  // members, [ne][nx] fp32, box 128 points x ne members
+    const float *members;
     int kblocks, ntile, tmem_cols, nx, ne;
     size_t smem;
     bool ready;
 };
 
-bool update_tc_supported(int ne, int ldx, int ntpad);
+bool update_tc_supported(int ne, int ldx, int ntpad, int nx);
 bool update_tc_prepare(UpdateTcPlan *plan, const __nv_bfloat16 *X16, int ldx, int nx, const __nv_bfloat16 *Tt,
-                       int ntpad, int ne);
-// members[c][p] += sum_a X[p][a] T[c][a] (c < ne), dC[p] = sum_a X[p][a] T[ne][a]
+                       int ntpad, int ne, const float *members);
+// members[c][p] += sum_a X[p][a] T[c][a] (c < ne), dC[p] = sum_a X[p][a] T[ne][a];
+// `members` must be the buffer the plan was prepared for
 cudaError_t launch_update_tc(const UpdateTcPlan &plan, float *members, float *dC, int *status, cudaStream_t s);
 
 }  // namespace mgk

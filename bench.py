@@ -54,8 +54,12 @@ WORKLOADS = {
     # 96 independent NS-2D problems; per point-step the three stage kernels
     # move 128 algorithmic bytes (stage 0: read u0, write s1; stages 1 and 2:
     # read the stage input and u0, write the output; 16 B per point each)
+    # traffic: DRAM bytes per point-step of the three stage launches, measured
+    # by ncu on the 32x16-tile class of the 8-problem batch (12.5 M points,
+    # working set above L2) and scaled to the full batch by its point count;
+    # None once the kernel changes
     "batched": dict(flops=600, bytes=128, kernel="ns2d_stage_x2<*,*,*,TableTiles>",
-                    launches_per_step=3, traffic=None, truth="fp32"),
+                    launches_per_step=3, traffic=None, traffic_per_point_step=116.6, truth="fp32"),
 }
 CNN_FLOPS_PER_PIXEL = 2 * 9 * (8 * 32 + 32 * 32 + 32 * 64)  # three 3x3 convolutions per coarse pixel
 
@@ -406,8 +410,8 @@ def run_gpu(args, dist, w, inp):
     achieved = flops / (fc_mean / launches_fc) / 1e12
     peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the current
-    # forecast kernel (profiles/burgers_f32x2_kernel__burgers_16384_4096_ne128_mixed.md
-    # for Burgers); None until captured, and reset whenever the kernel changes
+    # forecast kernel, from an ncu capture of this workload (Burgers); None until
+    # captured, and reset whenever the kernel changes
     traffic = spec["traffic"]
     g.close()
 
@@ -738,7 +742,9 @@ def run_gpu_batched(args, dist):
             "kernels_per_cycle": int(launches_per_cycle),
             "innovation_rms_mean_last": float(innov_h[-1].mean()),
             "roofline": {"bound": "hbm", "kernel": spec["kernel"], "achieved": achieved, "peak": hbm_peak,
-                         "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": spec["traffic"],
+                         "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": (spec["traffic_per_point_step"] * pts * nsteps
+                                     if spec.get("traffic_per_point_step") else None),
                          "scope": f"all stage launches of one forecast ({n_launch} launches, {nsteps} steps), "
                                   f"{spec['bytes']} B per point-step",
                          "peak_source": f"hbm_gbs ({peak_src})",

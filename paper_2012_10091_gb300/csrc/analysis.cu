@@ -449,16 +449,20 @@ void launch_cholesky(double *A, double *Lt, int n, int *status, cudaStream_t s) 
 // side (one CTA each, so the FP64 work of the columns spreads over the SMs),
 // lanes own rows lane + 32 m, the diagonal reciprocals precomputed.
 template <int MAXR>
-__global__ void __launch_bounds__(32) k_chol_solve_smem(const double *__restrict__ L, int n,
-                                                        const double *rhs, double *out, int ncol,
-                                                        __nv_bfloat16 *out16, int ld16,
-                                                        const int *status) {
+__global__ void __launch_bounds__(256) k_chol_solve_smem(const double *__restrict__ L, int n,
+                                                         const double *rhs, double *out, int ncol,
+                                                         __nv_bfloat16 *out16, int ld16,
+                                                         const int *status) {
+    // 256 threads copy the lower triangle of L into shared memory, then warp 0
+    // runs both substitutions for right-hand side blockIdx.x.
     extern __shared__ double sL[];  // [n][n+1] then inv_diag[n]
     if (*status) return;
-    const int c = blockIdx.x, lane = threadIdx.x, ld = n + 1;
+    const int c = blockIdx.x, lane = threadIdx.x & 31, ld = n + 1;
     double *inv = sL + (size_t)n * ld;
-    for (int e = lane; e < n * n; e += 32) sL[(e / n) * ld + e % n] = L[e];
-    __syncwarp();
+    for (int i = threadIdx.x >> 5; i < n; i += blockDim.x >> 5)
+        for (int j = lane; j <= i; j += 32) sL[(size_t)i * ld + j] = L[(size_t)i * n + j];
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
     for (int j = lane; j < n; j += 32) inv[j] = 1.0 / sL[(size_t)j * ld + j];
     __syncwarp();
     double b[MAXR];
@@ -576,13 +580,13 @@ void launch_chol_solve(const double *L, const double *Lt, int n, const double *r
                 cudaFuncSetAttribute(k_chol_solve_smem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
                 attr_set[0] = true;
             }
-            k_chol_solve_smem<4><<<ncol, 32, smem, s>>>(L, n, rhs, out, ncol, out16, ld16, status);
+            k_chol_solve_smem<4><<<ncol, 256, smem, s>>>(L, n, rhs, out, ncol, out16, ld16, status);
         } else {
             if (!attr_set[1]) {
                 cudaFuncSetAttribute(k_chol_solve_smem<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
                 attr_set[1] = true;
             }
-            k_chol_solve_smem<8><<<ncol, 32, smem, s>>>(L, n, rhs, out, ncol, out16, ld16, status);
+            k_chol_solve_smem<8><<<ncol, 256, smem, s>>>(L, n, rhs, out, ncol, out16, ld16, status);
         }
         return;
     }

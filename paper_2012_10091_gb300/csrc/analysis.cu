@@ -9,10 +9,13 @@
 // Cholesky factorisation and the triangular solves run in FP64.
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "analysis.h"
 #include "common.cuh"
 
 namespace mgk {
+namespace cg = cooperative_groups;
 
 static inline int grid_for(size_t n, int block, int cap = 8 * kNumSMs) {
     long long g = (long long)((n + block - 1) / block);
@@ -429,8 +432,143 @@ __global__ void __launch_bounds__(256) k_cholesky(double *A, double *Lt, int n, 
     }
 }
 
+// Cholesky by a cluster of 8 CTAs (n <= 256).  CTA q owns the columns
+// [q w, q w + w), w = ceil(n / 8), all n rows, in shared memory.  Panel p is
+// CTA p's block of columns.  For p = 0 .. 7: CTA p factors its panel column by
+// column (pivot sqrt and one reciprocal, scale the column, rank-1 update of
+// the panel's remaining columns); cluster barrier; every CTA q > p copies the
+// rows >= q w of panel p from CTA p's shared memory (distributed shared
+// memory) and subtracts the panel's rank-w product from its own columns.  One
+// cluster barrier per panel; the FP64 work of the trailing updates spreads
+// over 8 SMs.  A non-positive pivot sets the status and the kernel runs to
+// the end (every CTA must reach every cluster barrier) without writing L.
+constexpr int kCholCluster = 8;
+
+// y = 1/sqrt(d) for a Cholesky pivot: FP32 rsqrtf seed, then two Newton steps
+// y <- y (3 - d y^2) / 2 in FP64 (each squares the relative error: 2^-23 ->
+// 2^-46 -> FP64 rounding).  A pivot that is not positive and finite sets the
+// status and yields y = 1 so the factorisation runs on without dividing.
+__device__ __forceinline__ void chol_pivot(double d, double *y_out, int *status, int *fail) {
+    if (!(d > 0.0) || !isfinite(d)) {
+        atomicCAS(status, 0, kStNotSpd);
+        *fail = 1;
+        *y_out = 1.0;
+        return;
+    }
+    double y;
+    if (d > 1e-30 && d < 1e30) {
+        y = (double)rsqrtf((float)d);
+        y = y * fma(-0.5 * d, y * y, 1.5);
+        y = y * fma(-0.5 * d, y * y, 1.5);
+    } else {
+        y = 1.0 / sqrt(d);
+    }
+    *y_out = y;
+}
+
+__global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(256)
+    k_cholesky_cluster(double *A, double *Lt, int n, int *status) {
+    extern __shared__ double csm[];
+    __shared__ int s_fail;
+    __shared__ double s_y[32];  // 1/sqrt of the panel's pivots
+    cg::cluster_group cl = cg::this_cluster();
+    if (*status) return;  // every CTA reads it before any CTA can write it (after the first barrier)
+    const int q = (int)cl.block_rank();
+    const int w = (n + kCholCluster - 1) / kCholCluster, ldp = w + 1;
+    const int c0 = q * w, c1 = min(n, c0 + w), wq = max(0, c1 - c0);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    // 2-D view of the CTA for column-parallel loops: nx2 column lanes x ny2 row lanes
+    const int nx2 = w <= 8 ? 8 : (w <= 16 ? 16 : 32), ny2 = nth / nx2;
+    const int tx2 = tid % nx2, ty2 = tid / nx2;
+    double *P = csm;             // [n][ldp]: rows of this CTA's columns
+    double *Lp = csm + n * ldp;  // [n][ldp]: copy of the panel being applied
+    if (tid == 0) s_fail = 0;
+    for (int e = tid; e < n * wq; e += nth) {
+        const int i = e / wq, c = e - i * wq;
+        P[i * ldp + c] = A[(size_t)i * n + c0 + c];
+    }
+    cl.sync();
+    for (int p = 0; p < kCholCluster; ++p) {
+        const int pc0 = p * w, wp = min(n, pc0 + w) - pc0;
+        if (wp <= 0) break;  // the same for every CTA
+        if (q == p) {
+            // Outer-product form on unscaled columns: with d_k the pivot,
+            // A_ij -= A_ik A_jk / d_k for the panel's later columns, one barrier
+            // per column.  The thread that updates the next diagonal entry
+            // (thread 0) forms that pivot's 1/sqrt(d) at once; the square roots
+            // and column scalings follow once per panel.
+            __syncthreads();
+            if (tid == 0) chol_pivot(P[pc0 * ldp], &s_y[0], status, &s_fail);
+            for (int c = 0; c < wp; ++c) {
+                const int k = pc0 + c;
+                __syncthreads();
+                const double y = s_y[c], idk = y * y;
+                // thread (tx, ty): panel column c + 1 + tx, rows k + 1 + ty, + ny, ... (rows >= that column)
+                const int cc = c + 1 + tx2;
+                if (cc < wp) {
+                    const int r = pc0 + cc;
+                    const double ljk = P[r * ldp + c] * idk;
+                    for (int ii = k + 1 + ty2; ii < n; ii += ny2)
+                        if (ii >= r) P[ii * ldp + cc] = fma(-P[ii * ldp + c], ljk, P[ii * ldp + cc]);
+                    if (tid == 0) chol_pivot(P[r * ldp + cc], &s_y[cc], status, &s_fail);  // next diagonal, just updated
+                }
+            }
+            __syncthreads();
+            // L_ik = A_ik / sqrt(d_k) below the diagonal, L_kk = sqrt(d_k) = d_k y_k
+            for (int e = tid; e < n * wp; e += nth) {
+                const int i = e / wp, c = e - i * wp, k = pc0 + c;
+                if (i > k) P[i * ldp + c] *= s_y[c];
+            }
+            __syncthreads();
+            for (int c = tid; c < wp; c += nth) {
+                const int k = pc0 + c;
+                const double d = P[k * ldp + c];
+                P[k * ldp + c] = (d > 0.0 && isfinite(d)) ? d * s_y[c] : 1.0;
+            }
+        }
+        cl.sync();
+        if (q > p && wq > 0) {
+            const double *rp = cl.map_shared_rank(P, p);
+            for (int e = tid; e < (n - c0) * wp; e += nth) {
+                const int i = c0 + e / wp, c = e % wp;
+                Lp[i * ldp + c] = rp[i * ldp + c];
+            }
+            __syncthreads();
+            // thread (tx, ty): own column jj = tx, tx + nx2, ...; rows j + ty, + ny2, ...
+            for (int jj = tx2; jj < wq; jj += nx2) {
+                const int j = c0 + jj;
+                for (int i = j + ty2; i < n; i += ny2) {
+                    double acc = P[i * ldp + jj];
+                    for (int c = 0; c < wp; ++c) acc = fma(-Lp[i * ldp + c], Lp[j * ldp + c], acc);
+                    P[i * ldp + jj] = acc;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (!s_fail && !*status) {
+        for (int e = tid; e < n * wq; e += nth) {
+            const int i = e / wq, c = e - i * wq, j = c0 + c;
+            const double val = i >= j ? P[i * ldp + c] : 0.0;
+            A[(size_t)i * n + j] = val;
+            Lt[(size_t)j * n + i] = val;
+        }
+    }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 void launch_cholesky(double *A, double *Lt, int n, int *status, cudaStream_t s) {
     count_launches(1);
+    if (n >= 32 && n <= 256) {
+        const size_t bytes = sizeof(double) * 2 * (size_t)n * ((n + kCholCluster - 1) / kCholCluster + 1);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_cholesky_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            attr = true;
+        }
+        k_cholesky_cluster<<<kCholCluster, 256, bytes, s>>>(A, Lt, n, status);
+        return;
+    }
     const size_t bytes = sizeof(double) * (size_t)n * (n + 1);
     if (bytes <= 210 * 1024) {
         static bool attr_set = false;

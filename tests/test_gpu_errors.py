@@ -72,9 +72,12 @@ def test_nonfinite_device_observation_leaves_state_unchanged(M):
     assert g.sync() == 0
 
 
-def test_singular_innovation_matrix_reported(M):
-    # direct form with R = 0 and n_obs > Ne - 1: Y Y^T is singular
-    w = W.burgers_custom(256, 1, 4, 12, sigma=0.0)
+@pytest.mark.parametrize("nf,n_obs", [(256, 12), (256, 64), (512, 300)])
+def test_singular_innovation_matrix_reported(M, nf, n_obs):
+    # direct form with R = 0 and n_obs > Ne - 1: Y Y^T is singular.  The three
+    # sizes take the three Cholesky paths: one CTA with the matrix in shared
+    # memory, the 8-CTA cluster (32 <= n <= 256), one CTA on global memory.
+    w = W.burgers_custom(nf, 1, 4, n_obs, sigma=0.0)
     g, inp = _handle(M, w, gain_form=M.MGENKF_GAIN_DIRECT)
     g.analyse(np.ones(w.ny), np.zeros((w.ne, w.ny)))
     g.prolong_correct()

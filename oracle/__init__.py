@@ -58,6 +58,10 @@ def lib():
             L.orc_burgers_rhs.argtypes = [P, i32, f64, f64, i32, f64, P]
             L.orc_burgers_rk3.argtypes = [P, i32, i32, f64, f64, f64, i32, i32, f64]
             L.orc_ns2d_rhs.argtypes = [P, i32, f64, f64, f64, f64, P]
+            L.orc_burgers_sweep.argtypes = [P, P, i32, f64, f64, f64, f64, i32, f64, P]
+            L.orc_burgers_gamma.argtypes = [P, P, i32, f64, f64, f64, i32, f64, P]
+            L.orc_ns2d_sweep.argtypes = [P, P, i32, f64, f64, f64, f64, f64, f64, P]
+            L.orc_ns2d_gamma.argtypes = [P, P, i32, f64, f64, f64, f64, f64, P]
             L.orc_ns2d_rk3.argtypes = [P, i32, i32, f64, f64, f64, f64, f64, i32]
             L.orc_lagrange_weights.argtypes = [i32, P, f64, P]
             L.orc_restrict.argtypes = [P, i32, i32, i32, i32, P]
@@ -125,18 +129,64 @@ def burgers_rk3(u, dx, nu, dt, nsteps, flux_kind=0, c=0.0) -> np.ndarray:
     return x2.reshape(shape)
 
 
+def _ns_side(q) -> int:
+    """Points per side of a 4 x n x n state given flat or shaped."""
+    n = q.shape[-1] if q.ndim > 1 else int(round((q.size // 4) ** 0.5))
+    if q.size % (4 * n * n):
+        raise ValueError("NS-2D state must hold 4 x n x n values per grid")
+    return n
+
+
 def ns2d_rhs(q, h, gamma, mu, prandtl) -> np.ndarray:
     q = _f64(q)
     L = np.zeros_like(q)
-    lib().orc_ns2d_rhs(_p(q), q.shape[-1], h, gamma, mu, prandtl, _p(L))
+    if q.size != 4 * _ns_side(q) ** 2:
+        raise ValueError("ns2d_rhs takes one grid")
+    lib().orc_ns2d_rhs(_p(q), _ns_side(q), h, gamma, mu, prandtl, _p(L))
     return L
+
+
+def burgers_sweep(x, xprev, dx, nu, dt, alpha, flux_kind=0, c=0.0) -> np.ndarray:
+    """One relaxed Jacobi sweep of the implicit last step (Algorithm 4 step 6; see oracle.h)."""
+    x, xp = _f64(x), _f64(xprev)
+    out = np.empty_like(x)
+    lib().orc_burgers_sweep(_p(x), _p(xp), x.size, dx, nu, dt, alpha, flux_kind, c, _p(out))
+    return out
+
+
+def burgers_gamma(x, xprev, dx, nu, dt, flux_kind=0, c=0.0) -> np.ndarray:
+    """Conservativity residual (x - x_prev)/dt - L(x) (Eq. Conservativity_rhov)."""
+    x, xp = _f64(x), _f64(xprev)
+    out = np.empty_like(x)
+    lib().orc_burgers_gamma(_p(x), _p(xp), x.size, dx, nu, dt, flux_kind, c, _p(out))
+    return out
+
+
+def ns2d_sweep(q, qprev, h, gamma, mu, prandtl, dt, alpha) -> np.ndarray:
+    q, qp = _f64(q), _f64(qprev)
+    n = _ns_side(q)
+    if q.size != 4 * n * n or qp.size != q.size:
+        raise ValueError("ns2d_sweep takes one grid and its previous state")
+    out = np.empty_like(q)
+    lib().orc_ns2d_sweep(_p(q), _p(qp), n, h, gamma, mu, prandtl, dt, alpha, _p(out))
+    return out
+
+
+def ns2d_gamma(q, qprev, h, gamma, mu, prandtl, dt) -> np.ndarray:
+    q, qp = _f64(q), _f64(qprev)
+    n = _ns_side(q)
+    if q.size != 4 * n * n or qp.size != q.size:
+        raise ValueError("ns2d_gamma takes one grid and its previous state")
+    out = np.empty_like(q)
+    lib().orc_ns2d_gamma(_p(q), _p(qp), n, h, gamma, mu, prandtl, dt, _p(out))
+    return out
 
 
 def ns2d_rk3(q, h, gamma, mu, prandtl, dt, nsteps) -> np.ndarray:
     """Advance (nprob x) 4 x n x n conserved states by nsteps SSP-RK3 steps."""
     x = _f64(q).copy()
     shape = x.shape
-    n = shape[-1]
+    n = _ns_side(x)
     x2 = x.reshape(-1, 4, n, n)
     lib().orc_ns2d_rk3(_p(x2), x2.shape[0], n, h, gamma, mu, prandtl, dt, nsteps)
     return x2.reshape(shape)
@@ -215,7 +265,7 @@ class MGEnKF:
     """
 
     def __init__(self, model, nf, ratio, length, dt, fine, members, obs_idx, obs_var, sigma,
-                 seed, nu=0.0, gamma=1.4, prandtl=0.72, gain_form=1):
+                 seed, nu=0.0, gamma=1.4, prandtl=0.72, gain_form=1, alpha=0.0):
         self.model = model
         self.dim = 1 if model == "burgers1d" else 2
         self.V = 1 if model == "burgers1d" else 4
@@ -230,6 +280,8 @@ class MGEnKF:
         self.cycle = 0
         self.xstar = None
         self.dC = None
+        self.alpha = alpha          # final fine iteration (Algorithm 4 step 6); 0 = none
+        self.fine_prev = None       # fine state one model step before the analysis time
 
     def _advance(self, x, n, nsteps):
         h = self.length / n
@@ -240,7 +292,9 @@ class MGEnKF:
 
     def forecast(self, nsteps):
         """Algorithm 4 step 2 (fine) and Algorithm 3 step 2 (members)."""
-        self.fine = self._advance(self.fine, self.nf, nsteps)
+        if nsteps > 0:
+            self.fine_prev = self._advance(self.fine, self.nf, nsteps - 1)
+            self.fine = self._advance(self.fine_prev, self.nf, 1)
         self.members = self._advance(self.members, self.nc, nsteps)
 
     def analyse(self, yo, eps=None):
@@ -257,8 +311,24 @@ class MGEnKF:
         return st
 
     def prolong_correct(self):
-        """x^F,a = x^F,f + Pi_F(x^C' - x^C*)."""
+        """x^F,a = x^F,f + Pi_F(x^C' - x^C*), then (alpha > 0) the final fine
+        iteration of Algorithm 4 step 6."""
         self.fine = prolong_add(self.dC, self.fine, self.dim, self.V, self.nc, self.r)
+        if self.alpha > 0.0 and self.fine_prev is not None:
+            self.fine = self.sweep(self.alpha)
+
+    def sweep(self, alpha):
+        h = self.length / self.nf
+        if self.model == "burgers1d":
+            return burgers_sweep(self.fine, self.fine_prev, h, self.nu, self.dt, alpha)
+        return ns2d_sweep(self.fine, self.fine_prev, h, self.gamma, self.nu, self.prandtl, self.dt, alpha)
+
+    def gamma_residual(self):
+        """Conservativity residual of the fine state (Eq. Conservativity_rhov)."""
+        h = self.length / self.nf
+        if self.model == "burgers1d":
+            return burgers_gamma(self.fine, self.fine_prev, h, self.nu, self.dt)
+        return ns2d_gamma(self.fine, self.fine_prev, h, self.gamma, self.nu, self.prandtl, self.dt)
 
     def rmse(self, truth):
         return rmse(self.fine, truth, self.V)

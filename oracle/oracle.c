@@ -592,6 +592,50 @@ void orc_pixel_unshuffle4(const double *in, int C, int n, double *out) {
 }
 
 /* Relative RMSE, Eq. L2norm_u: sqrt(sum (x - x_true)^2 / sum x_true^2) per variable. */
+/* ---- final fine-grid iteration and conservativity indicator (see oracle.h) ---- */
+void orc_burgers_gamma(const double *x, const double *xprev, int n, double dx, double nu, double dt,
+                       int flux_kind, double c, double *gamma) {
+    double *L = (double *)malloc(sizeof(double) * (size_t)n);
+    orc_burgers_rhs(x, n, dx, nu, flux_kind, c, L);
+    for (int i = 0; i < n; ++i) gamma[i] = (x[i] - xprev[i]) / dt - L[i];
+    free(L);
+}
+
+void orc_burgers_sweep(const double *x, const double *xprev, int n, double dx, double nu, double dt,
+                       double alpha, int flux_kind, double c, double *out) {
+    double *g = (double *)malloc(sizeof(double) * (size_t)n);
+    orc_burgers_gamma(x, xprev, n, dx, nu, dt, flux_kind, c, g);
+    const double D = 1.0 + 2.0 * nu * dt / (dx * dx);
+    /* x_prev + dt L(x) - x = -dt Gamma */
+    for (int i = 0; i < n; ++i) out[i] = x[i] + alpha * (-dt * g[i]) / D;
+    free(g);
+}
+
+void orc_ns2d_gamma(const double *q, const double *qprev, int n, double h, double gamma, double mu,
+                    double prandtl, double dt, double *g) {
+    const size_t np = (size_t)4 * n * n;
+    double *L = (double *)malloc(sizeof(double) * np);
+    orc_ns2d_rhs(q, n, h, gamma, mu, prandtl, L);
+    for (size_t i = 0; i < np; ++i) g[i] = (q[i] - qprev[i]) / dt - L[i];
+    free(L);
+}
+
+void orc_ns2d_sweep(const double *q, const double *qprev, int n, double h, double gamma, double mu,
+                    double prandtl, double dt, double alpha, double *out) {
+    const size_t plane = (size_t)n * n;
+    double *g = (double *)malloc(sizeof(double) * 4 * plane);
+    orc_ns2d_gamma(q, qprev, n, h, gamma, mu, prandtl, dt, g);
+    const double kappa = mu * gamma / ((gamma - 1.0) * prandtl);
+    for (size_t p = 0; p < plane; ++p) {
+        const double rho = q[p];
+        const double D[4] = {1.0, 1.0 + dt * (14.0 / 3.0) * mu / (rho * h * h),
+                             1.0 + dt * (14.0 / 3.0) * mu / (rho * h * h),
+                             1.0 + dt * 4.0 * kappa * (gamma - 1.0) / (rho * h * h)};
+        for (int v = 0; v < 4; ++v) out[v * plane + p] = q[v * plane + p] + alpha * (-dt * g[v * plane + p]) / D[v];
+    }
+    free(g);
+}
+
 void orc_rmse(const double *x, const double *truth, int V, int64_t npts, double *out) {
     for (int v = 0; v < V; ++v) {
         double num = 0.0, den = 0.0;

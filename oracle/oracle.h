@@ -105,6 +105,31 @@ void orc_conv3x3_bwd(const double *in, int cin, int n, const double *W, int cout
 void orc_pixel_shuffle4(const double *in, int C, int n, double *out);
 void orc_pixel_unshuffle4(const double *in, int C, int n, double *out);
 
+/* ---- final fine-grid iteration (Algorithm 4 step 6) and the conservativity
+ * indicator (Eq. Conservativity_rhov) ----
+ * Reading: the last model step of the observation interval in implicit-Euler
+ * form, Psi(x) = x - dt L(x) = c with c = x_prev (the fine state one step
+ * before the analysis time), and one relaxed Jacobi (matrix-splitting) sweep
+ * from the analysis state x (Sec. 3 tailoring: one iteration, alpha = 0.5):
+ *   out = x + alpha D^-1 (x_prev + dt L(x) - x),
+ * D the diagonal of dPsi/dx at x.  Burgers (central fluxes have no diagonal
+ * term): D = 1 + 2 nu dt / dx^2.  NS-2D, per point: D = 1 for rho, 1 + dt
+ * (14/3) mu / (rho h^2) for rho u and rho v (compact face derivatives: 8/3 from
+ * tau_xx or tau_yy, 2 from tau_xy), 1 + dt 4 kappa (gamma - 1) / (rho h^2) for
+ * E (heat fluxes through T = (gamma - 1)(E - rho |u|^2 / 2) / rho).
+ * Gamma = (x - x_prev) / dt - L(x): the residual of that implicit step, the
+ * paper's conservativity indicator (there for rho v).  Parity: pinned
+ * (identity at alpha = 0, implicit solution is a fixed point, closed-form
+ * damping of Fourier modes, D against a finite-difference Jacobian). */
+void orc_burgers_sweep(const double *x, const double *xprev, int n, double dx, double nu, double dt,
+                       double alpha, int flux_kind, double c, double *out);
+void orc_burgers_gamma(const double *x, const double *xprev, int n, double dx, double nu, double dt,
+                       int flux_kind, double c, double *gamma);
+void orc_ns2d_sweep(const double *q, const double *qprev, int n, double h, double gamma, double mu,
+                    double prandtl, double dt, double alpha, double *out);
+void orc_ns2d_gamma(const double *q, const double *qprev, int n, double h, double gamma, double mu,
+                    double prandtl, double dt, double *g);
+
 /* ---- relative RMSE, Eq. L2norm_u, one value per variable ---- */
 void orc_rmse(const double *x, const double *truth, int V, int64_t npts, double *out);
 

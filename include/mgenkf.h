@@ -149,12 +149,15 @@ mgenkf_status mgenkf_rmse(mgenkf_handle h, const double *truth_fine, double *out
  *   MGENKF_FIELD_T      T = Y^T (Y Y^T + R)^-1 [D | d*], column c contiguous  (Ne+1) x Ne
  *   MGENKF_FIELD_DC     dC = x^C' - x^C*                    V * N_C^dim
  *   MGENKF_FIELD_EPS    observation perturbations used      Ne x Ny
+ *   MGENKF_FIELD_GAMMA  conservativity residual of the fine  V x N_F^dim
+ *                       run (Eq. Conservativity_rhov), see mgenkf_set_regularisation
  * count: number of doubles the caller can receive (must be >= the size). */
 #define MGENKF_FIELD_XSTAR 0
 #define MGENKF_FIELD_YF 1
 #define MGENKF_FIELD_T 2
 #define MGENKF_FIELD_DC 3
 #define MGENKF_FIELD_EPS 4
+#define MGENKF_FIELD_GAMMA 5
 mgenkf_status mgenkf_get_field(mgenkf_handle h, int32_t field, double *out, size_t count);
 
 /* Wait for the handle's stream and return (and clear) the first device-side
@@ -172,6 +175,23 @@ const char *mgenkf_last_error(mgenkf_handle h);
 
 /* Free every device buffer and the handle.  NULL is accepted. */
 mgenkf_status mgenkf_destroy(mgenkf_handle h);
+
+/* Final fine-grid iteration (Algorithm 4 step 6) with relaxation alpha (the
+ * paper's tailoring in Sec. 3 uses one iteration and alpha = 0.5).  Reading:
+ * the last model step of each forecast in implicit-Euler form, x - dt L(x) =
+ * x_prev, and one relaxed Jacobi sweep from the analysed fine state:
+ *   x <- x + alpha D^-1 (x_prev + dt L(x) - x),
+ * D the diagonal of I - dt dL/dx (Burgers: 1 + 2 nu dt / dx^2; NS-2D per
+ * point: 1 for rho, 1 + dt (14/3) mu / (rho h^2) for the momenta, 1 + dt 4
+ * kappa (gamma - 1) / (rho h^2) for E).  alpha in [0, 1]: from now on every
+ * forecast records x_prev (one extra launch and a copy of the fine state) and
+ * mgenkf_prolong_correct applies the sweep after Pi_F (and after the learned
+ * correction) when alpha > 0; MGENKF_FIELD_GAMMA then returns
+ * Gamma = (x - x_prev)/dt - L(x) of the current fine state.  alpha < 0 turns
+ * recording off (the default).  Residual and sweep are evaluated in FP64.
+ * Not available for handles in a batch.  Errors: MGENKF_ERR_INVALID_ARG for
+ * alpha > 1 or not finite. */
+mgenkf_status mgenkf_set_regularisation(mgenkf_handle h, double alpha);
 
 /* ---- batches of independent problems -------------------------------------
  * Many independent NS-2D MGEnKF problems (uneven grid sizes, ensemble sizes

@@ -36,6 +36,16 @@ void launch_obs_mean(const double *yf, const double *yo, int ne, int ny, double 
 // cycle: device pointer to the analysis counter (Philox counter word 0)
 // RMS over the ny innovations d* = y^o - H^C x^C* (row ne of Z) into out[0]
 void launch_innov_rms(const double *Z, int ne, int ny, double *out, cudaStream_t s);
+// Final fine-grid iteration (Algorithm 4 step 6) and conservativity residual
+// (Eq. Conservativity_rhov) of the fine run x against x_prev, the state one
+// model step earlier: out (if not NULL) = x - alpha dt D^-1 Gamma, gamma_out
+// (if not NULL, FP64) = Gamma = (x - x_prev)/dt - L(x).  model 1 = Burgers,
+// 2 = NS-2D (n points per side, 4 planes).  out must not alias x.
+template <typename T>
+void launch_fine_residual(int model, const T *x, const T *prev, int n, double length, double nu, double gamma,
+                          double prandtl, double dt, double alpha, T *out, double *gamma_out, const int *status,
+                          cudaStream_t s);
+
 void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, double *eps,
                         int gen_eps, uint64_t seed, const uint64_t *cycle, double sigma, int ne, int ny,
                         double *Y, double *Z, cudaStream_t s);

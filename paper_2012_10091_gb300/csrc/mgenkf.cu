@@ -50,6 +50,11 @@ struct mgenkf_ctx {
     double *Tm = nullptr;                               // T, (ne+1) x ne (points at Bt or own buffer)
     double *truth_d = nullptr, *rmse_part = nullptr, *rmse_d = nullptr, *scratch = nullptr;
     void *ns_scratch = nullptr;  // NS-2D stage buffers
+    void *fine_prev = nullptr;   // fine state one model step before the end of the last forecast
+    void *fine_tmp = nullptr;    // output of the final fine iteration
+    double alpha = 0.0;          // relaxation of the final fine iteration (0: none)
+    bool record_prev = false;    // forecasts record fine_prev (regularisation enabled)
+    bool have_prev = false;      // fine_prev belongs to the current fine state
     double *gemm_part = nullptr; // split-K partial sums of the gain GEMMs
     UpdateTcPlan tc;             // tensor-core member update (mixed precision)
     mgk_cnn_t cnn = nullptr;     // learned correction added by prolong_correct (not owned)
@@ -127,7 +132,7 @@ static void free_all(mgenkf_ctx *h) {
     void *ptrs[] = {h->fine, h->members, h->xstar, h->dC, h->tap_idx, h->tap_w, h->yf, h->yo,
                     h->ybar, h->eps, h->Y, h->Z, h->X64, h->X16, h->Tt, h->S, h->Lt, h->Bt, h->C,
                     h->Ct, h->W, h->truth_d, h->rmse_part, h->rmse_d, h->scratch, h->status,
-                    h->ns_scratch, h->gemm_part, h->cycle_d};
+                    h->ns_scratch, h->gemm_part, h->cycle_d, h->fine_prev, h->fine_tmp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->Tm && h->Tm != h->Bt) cudaFree(h->Tm);
@@ -251,6 +256,8 @@ static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const 
 
     const size_t ts = tsize(h), ne = h->ne, ny = h->ny, nx = h->nx;
     H_ALLOC(h->fine, h->nxf * ts);
+    H_ALLOC(h->fine_prev, h->nxf * ts);
+    H_ALLOC(h->fine_tmp, h->nxf * ts);
     H_ALLOC(h->members, ne * nx * ts);
     H_ALLOC(h->xstar, nx * ts);
     H_ALLOC(h->dC, nx * ts);
@@ -395,6 +402,7 @@ extern "C" mgenkf_status mgenkf_set_state(mgenkf_handle h, const double *fine, c
         if (st) return st;
     }
     h->cycle = 0;
+    h->have_prev = false;
     H_CUDA(cudaMemsetAsync(h->cycle_d, 0, sizeof(uint64_t), h->stream));
     H_CUDA(cudaStreamSynchronize(h->stream));
     return MGENKF_OK;
@@ -421,8 +429,22 @@ extern "C" mgenkf_status mgenkf_get_state(mgenkf_handle h, double *fine, double 
 // ---------------------------------------------------------------------------
 // the cycle
 // ---------------------------------------------------------------------------
+static mgenkf_status advance_impl(mgenkf_ctx *h, int nsteps);
+
 static mgenkf_status forecast_impl(mgenkf_ctx *h, int nsteps) {
     if (nsteps < 0) H_FAIL(MGENKF_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return MGENKF_OK;
+    if (!h->record_prev) return advance_impl(h, nsteps);
+    // regularisation enabled: keep the fine state one step before the end
+    mgenkf_status st = advance_impl(h, nsteps - 1);
+    if (st) return st;
+    H_CUDA(cudaMemcpyAsync(h->fine_prev, h->fine, h->nxf * tsize(h), cudaMemcpyDeviceToDevice, h->stream));
+    st = advance_impl(h, 1);
+    if (st == MGENKF_OK) h->have_prev = true;
+    return st;
+}
+
+static mgenkf_status advance_impl(mgenkf_ctx *h, int nsteps) {
     if (nsteps == 0) return MGENKF_OK;
     const mgenkf_config &c = h->cfg;
     cudaError_t e;
@@ -528,6 +550,30 @@ static mgenkf_status prolong_impl(mgenkf_ctx *h) {
                                            (float *)h->fine, 1, h->stream);
         if (st) H_FAIL(st, std::string("learned correction: ") + mgk_last_error());
     }
+    if (h->alpha > 0.0 && h->have_prev) {
+        // final fine iteration (Algorithm 4 step 6), out of place, then back
+        const mgenkf_config &c = h->cfg;
+        if (h->mixed)
+            launch_fine_residual<float>(c.model, (const float *)h->fine, (const float *)h->fine_prev, h->nf, c.length,
+                                        c.nu, c.gamma, c.prandtl, c.dt, h->alpha, (float *)h->fine_tmp, nullptr,
+                                        h->status, h->stream);
+        else
+            launch_fine_residual<double>(c.model, (const double *)h->fine, (const double *)h->fine_prev, h->nf,
+                                         c.length, c.nu, c.gamma, c.prandtl, c.dt, h->alpha, (double *)h->fine_tmp,
+                                         nullptr, h->status, h->stream);
+        H_LAUNCHED();
+        H_CUDA(cudaMemcpyAsync(h->fine, h->fine_tmp, h->nxf * tsize(h), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_set_regularisation(mgenkf_handle h, double alpha) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    if (!(alpha <= 1.0) || !std::isfinite(alpha)) H_FAIL(MGENKF_ERR_INVALID_ARG, "alpha must be finite and <= 1");
+    h->record_prev = alpha >= 0.0;
+    h->alpha = alpha > 0.0 ? alpha : 0.0;
+    if (!h->record_prev) h->have_prev = false;
     return MGENKF_OK;
 }
 
@@ -608,6 +654,25 @@ extern "C" mgenkf_status mgenkf_get_field(mgenkf_handle h, int32_t field, double
         case MGENKF_FIELD_EPS:
             if (count < ne * ny) H_FAIL(MGENKF_ERR_INVALID_ARG, "count too small");
             return copy_out_f64(h, out, h->eps, ne * ny);
+        case MGENKF_FIELD_GAMMA: {
+            if (count < h->nxf) H_FAIL(MGENKF_ERR_INVALID_ARG, "count too small");
+            if (!h->have_prev)
+                H_FAIL(MGENKF_ERR_INVALID_ARG, "no recorded previous fine state: enable mgenkf_set_regularisation "
+                                               "and run a forecast first");
+            mgenkf_status st = ensure_scratch(h, h->nxf);
+            if (st) return st;
+            const mgenkf_config &c = h->cfg;
+            if (h->mixed)
+                launch_fine_residual<float>(c.model, (const float *)h->fine, (const float *)h->fine_prev, h->nf,
+                                            c.length, c.nu, c.gamma, c.prandtl, c.dt, 0.0, nullptr, h->scratch,
+                                            nullptr, h->stream);
+            else
+                launch_fine_residual<double>(c.model, (const double *)h->fine, (const double *)h->fine_prev, h->nf,
+                                             c.length, c.nu, c.gamma, c.prandtl, c.dt, 0.0, nullptr, h->scratch,
+                                             nullptr, h->stream);
+            H_LAUNCHED();
+            return copy_out_f64(h, out, h->scratch, h->nxf);
+        }
         default:
             H_FAIL(MGENKF_ERR_INVALID_ARG, "unknown field");
     }
@@ -913,6 +978,8 @@ extern "C" mgenkf_status mgenkf_batch_create(const mgenkf_handle *handles, int32
         if (!h) return fail(MGENKF_ERR_INVALID_ARG, "NULL handle");
         if (h->cfg.model != MGENKF_NS2D || !h->mixed)
             return fail(MGENKF_ERR_INVALID_ARG, "batches hold NS-2D mixed-precision handles");
+        if (h->record_prev)
+            return fail(MGENKF_ERR_INVALID_ARG, "the final fine iteration is not available in batches");
         if (i == 0) {
             b->gamma = h->cfg.gamma;
             b->mu = h->cfg.nu;

@@ -24,6 +24,7 @@ MGENKF_FP64, MGENKF_MIXED = 0, 1
 MGENKF_GAIN_ENSEMBLE, MGENKF_GAIN_DIRECT = 0, 1
 MGENKF_PROLONG_LAGRANGE4 = 0
 MGENKF_FIELD_XSTAR, MGENKF_FIELD_YF, MGENKF_FIELD_T, MGENKF_FIELD_DC, MGENKF_FIELD_EPS = 0, 1, 2, 3, 4
+MGENKF_FIELD_GAMMA = 5
 EPS_TAG = 0x45505300
 
 
@@ -75,6 +76,7 @@ def _load():
         "mgk_cnn_adam_step": [P, ctypes.c_float, P],
         "mgk_cnn_coarse_size": [P],
         "mgenkf_set_prolong_cnn": [P, P],
+        "mgenkf_set_regularisation": [P, f64],
         "mgenkf_batch_create": [P, i32, P, ctypes.POINTER(P)],
         "mgenkf_batch_cycle": [P, i32, P, P],
         "mgenkf_batch_forecast": [P, i32],
@@ -357,6 +359,17 @@ class MGEnKF:
              MGENKF_FIELD_EPS: self.ne * self.ny}[which]
         out = np.empty(n)
         mgenkf_get_field(self.h, which, out, n)
+        return out
+
+    def set_regularisation(self, alpha):
+        """Final fine iteration (Algorithm 4 step 6) with relaxation alpha; alpha < 0 turns
+        the recording of the previous fine state off.  See include/mgenkf.h."""
+        _check(lib.mgenkf_set_regularisation(self.h, float(alpha)), "mgenkf_set_regularisation", self.h)
+
+    def gamma_residual(self):
+        """Conservativity residual of the fine run (Eq. Conservativity_rhov), FP64."""
+        out = np.empty(self.nxf)
+        mgenkf_get_field(self.h, MGENKF_FIELD_GAMMA, out, self.nxf)
         return out
 
     def set_prolong_cnn(self, cnn):

@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--tiles", default=None,
                     help="batched: JSON tile table to load (autotuned and written there if missing)")
     ap.add_argument("--problems", type=int, default=96, help="batched: number of problems")
+    ap.add_argument("--regularise", type=float, default=None,
+                    help="burgers_large / ns2d: final fine iteration (Algorithm 4 step 6) with this "
+                         "relaxation in the timed cycles, plus an alpha = 0 / alpha ablation")
     return ap.parse_args()
 
 
@@ -298,11 +301,14 @@ def run_gpu(args, dist, w, inp):
     ncyc = args.warmup + args.steps
     spec = WORKLOADS[args.workload]
     with torch.cuda.stream(stream):
-        truths, yos = truth_and_obs(M, w, inp, max(ncyc, args.fp64_cycles), torch, spec["truth"])
+        truths, yos = truth_and_obs(M, w, inp, max(ncyc, args.fp64_cycles, 10 if args.regularise else 0),
+                                    torch, spec["truth"])
     torch.cuda.synchronize()
 
     g = M.MGEnKF.from_workload(w, stream=sp)
     g.set_state(inp["fine0"], inp["members0"])
+    if args.regularise is not None:
+        g.set_regularisation(args.regularise)
     rmse_dev = torch.zeros((ncyc, w.V), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
@@ -384,11 +390,42 @@ def run_gpu(args, dist, w, inp):
                       "fine_state_rel_diff": state_rel,
                       "speedup_mixed_vs_fp64": value / dist.world / fp64_cps}
 
+    # final fine iteration, on the same inputs: (a) alpha = 0 throughout
+    # (recorded, no sweep); (b) alpha = 0, then alpha on the last cycle only:
+    # the sweep's effect on the conservativity residual of one analysed state;
+    # (c) alpha throughout: its effect on the RMSE over the last half
+    regularisation = None
+    if args.regularise is not None and args.regularise > 0:
+        nab = min(max(args.fp64_cycles, 10), truths.shape[0])
+        comp = 0 if w.V == 1 else 2          # u (Burgers), rho v (NS: the paper's indicator)
+        res = {}
+        for tag, alphas in (("a", [0.0] * nab), ("b", [0.0] * (nab - 1) + [args.regularise]),
+                            ("c", [args.regularise] * nab)):
+            ga = M.MGEnKF.from_workload(w, stream=sp)
+            ga.set_state(inp["fine0"], inp["members0"])
+            ra = torch.zeros((nab, w.V), dtype=torch.float64, device="cuda")
+            with torch.cuda.stream(stream):
+                for k in range(nab):
+                    ga.set_regularisation(alphas[k])
+                    M.mgenkf_cycle(ga.h, w.steps_per_cycle, yos[k], truths[k], ra[k])
+            torch.cuda.synchronize()
+            assert ga.sync() == 0
+            gres = ga.gamma_residual().reshape(w.V, -1)
+            res[tag] = (float(np.sqrt(np.mean(gres[comp] ** 2))), float(ra[nab // 2:, 0].mean()))
+            ga.close()
+        regularisation = {"alpha": args.regularise, "cycles": nab,
+                          "gamma_component": "u" if w.V == 1 else "rho v",
+                          "gamma_rms_before_sweep": res["a"][0], "gamma_rms_after_sweep": res["b"][0],
+                          "gamma_ratio_one_sweep": res["b"][0] / res["a"][0],
+                          "rmse_last_half_alpha0": res["a"][1], "rmse_last_half": res["c"][1]}
+
     # e2e: the same cycle through the C ABI with host buffers (pinned), copies inside
     e2e = None
     if not args.no_e2e:
         ge = M.MGEnKF.from_workload(w, stream=sp)
         ge.set_state(inp["fine0"], inp["members0"])
+        if args.regularise is not None:
+            ge.set_regularisation(args.regularise)
         y_h = torch.empty((ncyc, w.ny), dtype=torch.float64, pin_memory=True)
         y_h.copy_(yos[:ncyc].cpu())
         t_h = torch.empty((ncyc, w.nxf), dtype=torch.float64, pin_memory=True)
@@ -432,6 +469,7 @@ def run_gpu(args, dist, w, inp):
             "config": {"workload": w.name, "nf": w.nf, "nc": w.nc, "ne": w.ne, "ny": w.ny,
                        "steps_per_cycle": w.steps_per_cycle, "precision": "mixed",
                        "gain_form": "ensemble-space", "replicas": dist.world,
+                       "final_fine_iteration": args.regularise if args.regularise is not None else "off",
                        "l2": "flushed between timed cycles (256 MB write)"},
             "member_steps_per_s": value * w.ne * w.steps_per_cycle,
             "forecast_ms_per_cycle": fc_mean * 1e3,
@@ -439,6 +477,7 @@ def run_gpu(args, dist, w, inp):
             "hbm_gbs_algorithmic": (2 * 4 * w.V * pts) * args.steps / t_total / 1e9,
             "fp64_plain": fp64_plain,
             "rmse_final": float(rmse_mixed[-1]),
+            "regularisation": regularisation,
             "roofline": {"bound": "alu", "kernel": spec["kernel"],
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,

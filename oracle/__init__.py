@@ -59,6 +59,7 @@ def lib():
             L.orc_burgers_rk3.argtypes = [P, i32, i32, f64, f64, f64, i32, i32, f64]
             L.orc_ns2d_rhs.argtypes = [P, i32, f64, f64, f64, f64, P]
             L.orc_burgers_sweep.argtypes = [P, P, i32, f64, f64, f64, f64, i32, f64, P]
+            L.orc_recentre.argtypes = [P, i32, i64, P]
             L.orc_burgers_gamma.argtypes = [P, P, i32, f64, f64, f64, i32, f64, P]
             L.orc_ns2d_sweep.argtypes = [P, P, i32, f64, f64, f64, f64, f64, f64, P]
             L.orc_ns2d_gamma.argtypes = [P, P, i32, f64, f64, f64, f64, f64, P]
@@ -144,6 +145,15 @@ def ns2d_rhs(q, h, gamma, mu, prandtl) -> np.ndarray:
         raise ValueError("ns2d_rhs takes one grid")
     lib().orc_ns2d_rhs(_p(q), _ns_side(q), h, gamma, mu, prandtl, _p(L))
     return L
+
+
+def recentre(members, xstar) -> np.ndarray:
+    """Members re-centred on x^C* (fine-to-coarse feedback; see oracle.h)."""
+    m = _f64(members).copy()
+    xs = _f64(xstar)
+    ne = m.shape[0]
+    lib().orc_recentre(_p(m), ne, m.size // ne, _p(xs))
+    return m
 
 
 def burgers_sweep(x, xprev, dx, nu, dt, alpha, flux_kind=0, c=0.0) -> np.ndarray:
@@ -265,7 +275,7 @@ class MGEnKF:
     """
 
     def __init__(self, model, nf, ratio, length, dt, fine, members, obs_idx, obs_var, sigma,
-                 seed, nu=0.0, gamma=1.4, prandtl=0.72, gain_form=1, alpha=0.0):
+                 seed, nu=0.0, gamma=1.4, prandtl=0.72, gain_form=1, alpha=0.0, recentre=False):
         self.model = model
         self.dim = 1 if model == "burgers1d" else 2
         self.V = 1 if model == "burgers1d" else 4
@@ -281,6 +291,7 @@ class MGEnKF:
         self.xstar = None
         self.dC = None
         self.alpha = alpha          # final fine iteration (Algorithm 4 step 6); 0 = none
+        self.recentre = recentre    # re-centre the forecast ensemble on x^C* before each analysis
         self.fine_prev = None       # fine state one model step before the analysis time
 
     def _advance(self, x, n, nsteps):
@@ -303,6 +314,8 @@ class MGEnKF:
         if eps is None:
             eps = obs_perturbations(self.seed, self.cycle, ne, ny, self.sigma)
         self.xstar = restrict(self.fine, self.dim, self.V, self.nc, self.r)
+        if self.recentre:
+            self.members = recentre(self.members, self.xstar)
         st, m, dC = enkf_analyse(self.members, self.xstar, yo, eps, self.sigma, self.obs_idx,
                                  self.obs_var, self.dim, self.V, self.nc, self.r, self.gain_form)
         if st == 0:

@@ -636,6 +636,16 @@ void orc_ns2d_sweep(const double *q, const double *qprev, int n, double h, doubl
     free(g);
 }
 
+void orc_recentre(double *members, int ne, int64_t nx, const double *xstar) {
+    for (int64_t p = 0; p < nx; ++p) {
+        double m = 0.0;
+        for (int i = 0; i < ne; ++i) m += members[(size_t)i * nx + p];
+        m /= ne;
+        const double shift = xstar[p] - m;
+        for (int i = 0; i < ne; ++i) members[(size_t)i * nx + p] += shift;
+    }
+}
+
 void orc_rmse(const double *x, const double *truth, int V, int64_t npts, double *out) {
     for (int v = 0; v < V; ++v) {
         double num = 0.0, den = 0.0;

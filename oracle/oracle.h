@@ -130,6 +130,14 @@ void orc_ns2d_sweep(const double *q, const double *qprev, int n, double h, doubl
 void orc_ns2d_gamma(const double *q, const double *qprev, int n, double h, double gamma, double mu,
                     double prandtl, double dt, double *g);
 
+/* ---- fine-to-coarse feedback (the paper's conclusion: project the fine
+ * run's information onto the members) ----
+ * Reading: before each analysis, re-centre the forecast ensemble on the
+ * restricted fine forecast x^C*: x^(i) <- x^(i) - mean_i x^(i) + x^C*.  The
+ * anomalies are unchanged.  members: ne x nx, member-major.  Parity: pinned
+ * (mean equals x^C*, anomalies unchanged, analysis mean = x^C' + K mean(eps)). */
+void orc_recentre(double *members, int ne, int64_t nx, const double *xstar);
+
 /* ---- relative RMSE, Eq. L2norm_u, one value per variable ---- */
 void orc_rmse(const double *x, const double *truth, int V, int64_t npts, double *out);
 

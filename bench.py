@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--tiles", default=None,
                     help="batched: JSON tile table to load (autotuned and written there if missing)")
     ap.add_argument("--problems", type=int, default=96, help="batched: number of problems")
+    ap.add_argument("--recentre", action="store_true",
+                    help="burgers_large / ns2d: add an ablation of the fine-to-coarse feedback "
+                         "(ensemble re-centred on the restricted fine forecast)")
     ap.add_argument("--regularise", type=float, default=None,
                     help="burgers_large / ns2d: final fine iteration (Algorithm 4 step 6) with this "
                          "relaxation in the timed cycles, plus an alpha = 0 / alpha ablation")
@@ -419,6 +422,25 @@ def run_gpu(args, dist, w, inp):
                           "gamma_ratio_one_sweep": res["b"][0] / res["a"][0],
                           "rmse_last_half_alpha0": res["a"][1], "rmse_last_half": res["c"][1]}
 
+    # fine-to-coarse feedback: RMSE over the last half with and without
+    feedback = None
+    if args.recentre:
+        nab = min(max(args.fp64_cycles, 10), truths.shape[0])
+        rm = {}
+        for on in (False, True):
+            ga = M.MGEnKF.from_workload(w, stream=sp)
+            ga.set_state(inp["fine0"], inp["members0"])
+            ga.set_recentre(on)
+            ra = torch.zeros((nab, w.V), dtype=torch.float64, device="cuda")
+            with torch.cuda.stream(stream):
+                for k in range(nab):
+                    M.mgenkf_cycle(ga.h, w.steps_per_cycle, yos[k], truths[k], ra[k])
+            torch.cuda.synchronize()
+            assert ga.sync() == 0
+            rm[on] = ra[nab // 2:].mean(dim=0).cpu().numpy().tolist()
+            ga.close()
+        feedback = {"cycles": nab, "rmse_last_half_off": rm[False], "rmse_last_half_on": rm[True]}
+
     # e2e: the same cycle through the C ABI with host buffers (pinned), copies inside
     e2e = None
     if not args.no_e2e:
@@ -478,6 +500,7 @@ def run_gpu(args, dist, w, inp):
             "fp64_plain": fp64_plain,
             "rmse_final": float(rmse_mixed[-1]),
             "regularisation": regularisation,
+            "recentre_ablation": feedback,
             "roofline": {"bound": "alu", "kernel": spec["kernel"],
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,

@@ -193,6 +193,15 @@ mgenkf_status mgenkf_destroy(mgenkf_handle h);
  * alpha > 1 or not finite. */
 mgenkf_status mgenkf_set_regularisation(mgenkf_handle h, double alpha);
 
+/* Fine-to-coarse feedback (the paper's conclusion names projecting the fine
+ * run's information onto the ensemble as the next step; reading: re-centring).
+ * on != 0: every analysis first re-centres the forecast ensemble on the
+ * restricted fine forecast, x^(i) <- x^(i) - mean_i x^(i) + x^C* (FP64 mean),
+ * which leaves the anomalies and so the gain unchanged and centres the
+ * analysed ensemble on x^C' up to the mean perturbation.  Off by default.
+ * If the analysis then fails (status), the members stay re-centred. */
+mgenkf_status mgenkf_set_recentre(mgenkf_handle h, int32_t on);
+
 /* ---- batches of independent problems -------------------------------------
  * Many independent NS-2D MGEnKF problems (uneven grid sizes, ensemble sizes
  * and observation counts) advanced together: the forecast of every problem's

@@ -178,6 +178,29 @@ void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, 
                                                                    ne, ny, Y, Z);
 }
 
+// Fine-to-coarse feedback: the forecast ensemble re-centred on the restricted
+// fine forecast, x^(i) += x^C* - mean_i x^(i) (FP64 mean and shift).  One
+// thread per point; members member-major.
+template <typename T>
+__global__ void __launch_bounds__(256) k_recentre(T *__restrict__ m, size_t nx, int ne, const T *__restrict__ xstar,
+                                                  const int *status) {
+    if (*status) return;
+    const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (p >= nx) return;
+    double s = 0.0;
+    for (int i = 0; i < ne; ++i) s += (double)m[(size_t)i * nx + p];
+    const double shift = (double)xstar[p] - s / ne;
+    for (int i = 0; i < ne; ++i) m[(size_t)i * nx + p] = (T)((double)m[(size_t)i * nx + p] + shift);
+}
+
+template <typename T>
+void launch_recentre(T *members, size_t nx, int ne, const T *xstar, const int *status, cudaStream_t s) {
+    count_launches(1);
+    k_recentre<T><<<(unsigned)ceil_div(nx, 256), 256, 0, s>>>(members, nx, ne, xstar, status);
+}
+template void launch_recentre<float>(float *, size_t, int, const float *, const int *, cudaStream_t);
+template void launch_recentre<double>(double *, size_t, int, const double *, const int *, cudaStream_t);
+
 // ---------------------------------------------------------------------------
 // ensemble mean (FP64 accumulation) and normalised anomalies X
 // ---------------------------------------------------------------------------

@@ -46,6 +46,10 @@ void launch_fine_residual(int model, const T *x, const T *prev, int n, double le
                           double prandtl, double dt, double alpha, T *out, double *gamma_out, const int *status,
                           cudaStream_t s);
 
+// fine-to-coarse feedback: members re-centred on x^C* (FP64 mean and shift)
+template <typename T>
+void launch_recentre(T *members, size_t nx, int ne, const T *xstar, const int *status, cudaStream_t s);
+
 void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, double *eps,
                         int gen_eps, uint64_t seed, const uint64_t *cycle, double sigma, int ne, int ny,
                         double *Y, double *Z, cudaStream_t s);

@@ -55,6 +55,7 @@ struct mgenkf_ctx {
     double alpha = 0.0;          // relaxation of the final fine iteration (0: none)
     bool record_prev = false;    // forecasts record fine_prev (regularisation enabled)
     bool have_prev = false;      // fine_prev belongs to the current fine state
+    bool recentre = false;       // re-centre the forecast ensemble on x^C* before each analysis
     double *gemm_part = nullptr; // split-K partial sums of the gain GEMMs
     UpdateTcPlan tc;             // tensor-core member update (mixed precision)
     mgk_cnn_t cnn = nullptr;     // learned correction added by prolong_correct (not owned)
@@ -483,6 +484,7 @@ static void analyse_kernels(mgenkf_ctx *h, int gen_eps) {
     const size_t nx = h->nx;
     T *members = (T *)h->members, *xstar = (T *)h->xstar, *dC = (T *)h->dC;
     launch_restrict<T>((const T *)h->fine, xstar, h->dim, h->V, h->nc, h->r, s);
+    if (h->recentre) launch_recentre<T>(members, nx, ne, xstar, h->status, s);
     launch_obs_apply<T>(members, xstar, nx, ne, ny, h->taps, h->tap_idx, h->tap_w, h->yf, s);
     launch_obs_mean(h->yf, h->yo, ne, ny, h->ybar, h->Z, h->status, s);
     launch_obs_perturb(h->yf, h->ybar, h->yo, h->eps, gen_eps, h->cfg.seed, h->cycle_d,
@@ -564,6 +566,13 @@ static mgenkf_status prolong_impl(mgenkf_ctx *h) {
         H_LAUNCHED();
         H_CUDA(cudaMemcpyAsync(h->fine, h->fine_tmp, h->nxf * tsize(h), cudaMemcpyDeviceToDevice, h->stream));
     }
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_set_recentre(mgenkf_handle h, int32_t on) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    h->recentre = on != 0;
     return MGENKF_OK;
 }
 

@@ -77,6 +77,7 @@ def _load():
         "mgk_cnn_coarse_size": [P],
         "mgenkf_set_prolong_cnn": [P, P],
         "mgenkf_set_regularisation": [P, f64],
+        "mgenkf_set_recentre": [P, i32],
         "mgenkf_batch_create": [P, i32, P, ctypes.POINTER(P)],
         "mgenkf_batch_cycle": [P, i32, P, P],
         "mgenkf_batch_forecast": [P, i32],
@@ -365,6 +366,10 @@ class MGEnKF:
         """Final fine iteration (Algorithm 4 step 6) with relaxation alpha; alpha < 0 turns
         the recording of the previous fine state off.  See include/mgenkf.h."""
         _check(lib.mgenkf_set_regularisation(self.h, float(alpha)), "mgenkf_set_regularisation", self.h)
+
+    def set_recentre(self, on=True):
+        """Re-centre the forecast ensemble on x^C* before each analysis (fine-to-coarse feedback)."""
+        _check(lib.mgenkf_set_recentre(self.h, 1 if on else 0), "mgenkf_set_recentre", self.h)
 
     def gamma_residual(self):
         """Conservativity residual of the fine run (Eq. Conservativity_rhov), FP64."""

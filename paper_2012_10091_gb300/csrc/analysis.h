@@ -6,7 +6,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/mgenkf.h"
+
+typedef struct mgk_cnn *mgk_cnn_t;
+
 namespace mgk {
+
+// mgk_cnn_forward with the tensor-core timeout recorded in `status` (the
+// handle's status word when the correction runs inside a cycle)
+mgenkf_status cnn_forward_status(mgk_cnn_t c, const float *dC, const float *xstar, int batch, float *residual,
+                                 int accumulate, int *status, cudaStream_t s);
 
 constexpr int kMaxRatio = 16;
 

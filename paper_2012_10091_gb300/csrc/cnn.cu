@@ -10,14 +10,20 @@
 // weights; the forward and backward passes use BF16 weights and activations
 // with FP32 accumulation.
 //
-// Kernels (one CTA per 16 x 16 pixel tile of one sample):
-//   k_cnn_input       normalised BF16 input
-//   k_conv_fwd        direct 3x3 convolution, input tile + halo and weights in
-//                     shared memory, 1 pixel x all output channels per thread
+// Activations a0 (8 channels), a1, a2 (32) are BF16 in channel groups of 8
+// ("C8": element (b, i, p) at ((b C/8 + i/8) n^2 + p) 8 + i % 8); z3 and the
+// gradients are FP32 planes [b][c][p].
+//
+// Kernels:
+//   k_cnn_input       normalised BF16 input, C8
+//   k_conv_fwd_tc     the three forward convolutions on the tensor cores
+//                     (conv_tc.cu: implicit GEMM, TMEM accumulators)
 //   k_cnn_out_grad    residual, loss partials and dz3 through the shuffle
-//   k_conv_bwd_data   adjoint convolution (same tiling), ReLU mask of the input
+//   (one CTA per 16 x 16 pixel tile of one sample from here on)
+//   k_conv_bwd_data   adjoint convolution, ReLU mask of the input
 //   k_conv_bwd_weight per-tile partial dW, db; k_reduce_partials sums tiles in order
-//   k_adam            Adam step on FP32 master weights, BF16 copy
+//   k_adam            Adam step on FP32 master weights, BF16 copy; the packed
+//                     tensor-core copy of the weights follows every change
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -28,6 +34,7 @@
 #include "../../include/mgenkf_ops.h"
 #include "analysis.h"
 #include "common.cuh"
+#include "conv_tc.h"
 
 namespace mgk {
 
@@ -41,6 +48,11 @@ struct CnnLayer {
 };
 static const CnnLayer kLayers[3] = {{8, 32, 0, 2304}, {32, 32, 2336, 11552}, {32, 64, 11584, 30016}};
 
+// element (b, i, p) of a C-channel BF16 activation in the C8 layout
+__device__ __forceinline__ size_t c8_at(int b, int i, size_t p, int C, size_t pl) {
+    return (((size_t)b * (C / 8) + i / 8) * pl + p) * 8 + (i & 7);
+}
+
 __device__ __forceinline__ int wrap(int v, int n) {
     while (v < 0) v += n;
     while (v >= n) v -= n;
@@ -51,55 +63,24 @@ __device__ __forceinline__ int wrap(int v, int n) {
 __global__ void k_cnn_input(const float *__restrict__ dC, const float *__restrict__ xs, int n, int B,
                             const float *__restrict__ mu, const float *__restrict__ sc,
                             __nv_bfloat16 *__restrict__ a0) {
-    const size_t pl = (size_t)n * n, total = (size_t)B * 8 * pl;
+    const size_t pl = (size_t)n * n, total = (size_t)B * pl;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t b = e / (8 * pl), r = e % (8 * pl), c = r / pl, k = r % pl;
-        const float v = c < 4 ? dC[(b * 4 + c) * pl + k] : xs[(b * 4 + c - 4) * pl + k];
-        a0[e] = __float2bfloat16((v - mu[c]) / sc[c]);
-    }
-}
-
-// out[b][o][p] = bias[o] + sum_{i,t} W[o][i][t] in[b][i][p + tap t]  (+ ReLU)
-template <int CIN, int COUT, bool RELU, bool OUT_BF16>
-__global__ void __launch_bounds__(256) k_conv_fwd(const __nv_bfloat16 *__restrict__ in,
-                                                  const __nv_bfloat16 *__restrict__ W,
-                                                  const float *__restrict__ bias, void *out, int n) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    float *xs = reinterpret_cast<float *>(sm);                                   // [CIN][kTH][kTH]
-    __nv_bfloat16 *ws = reinterpret_cast<__nv_bfloat16 *>(xs + CIN * kTH * kTH);  // [COUT][CIN][9]
-    const int b = blockIdx.z, x0 = blockIdx.x * kT, y0 = blockIdx.y * kT;
-    const size_t pl = (size_t)n * n;
-    const __nv_bfloat16 *inb = in + (size_t)b * CIN * pl;
-    for (int e = threadIdx.x; e < CIN * kTH * kTH; e += blockDim.x) {
-        const int i = e / (kTH * kTH), r = e % (kTH * kTH), ly = r / kTH, lx = r % kTH;
-        const int gy = wrap(y0 + ly - 1, n), gx = wrap(x0 + lx - 1, n);
-        xs[e] = __bfloat162float(inb[i * pl + (size_t)gy * n + gx]);
-    }
-    for (int e = threadIdx.x; e < COUT * CIN * 9; e += blockDim.x) ws[e] = W[e];
-    __syncthreads();
-    const int tx = threadIdx.x % kT, ty = threadIdx.x / kT;
-    const int x = x0 + tx, y = y0 + ty;
-    if (x >= n || y >= n) return;
-    float acc[COUT];
+        const size_t b = e / pl, k = e % pl;
+        uint4 pk;
+        uint32_t *w = reinterpret_cast<uint32_t *>(&pk);
 #pragma unroll
-    for (int o = 0; o < COUT; ++o) acc[o] = bias[o];
-    for (int i = 0; i < CIN; ++i) {
+        for (int q = 0; q < 4; ++q) {
+            float v[2];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const float v = xs[(i * kTH + ty + t / 3) * kTH + tx + t % 3];
-#pragma unroll
-            for (int o = 0; o < COUT; ++o) acc[o] = fmaf(__bfloat162float(ws[(o * CIN + i) * 9 + t]), v, acc[o]);
+            for (int h = 0; h < 2; ++h) {
+                const int c = 2 * q + h;
+                const float x = c < 4 ? dC[(b * 4 + c) * pl + k] : xs[(b * 4 + c - 4) * pl + k];
+                v[h] = (x - mu[c]) / sc[c];
+            }
+            const __nv_bfloat162 two = __floats2bfloat162_rn(v[0], v[1]);
+            w[q] = *reinterpret_cast<const uint32_t *>(&two);
         }
-    }
-    const size_t p = (size_t)y * n + x;
-#pragma unroll
-    for (int o = 0; o < COUT; ++o) {
-        float v = acc[o];
-        if (RELU) v = fmaxf(v, 0.f);
-        if (OUT_BF16)
-            reinterpret_cast<__nv_bfloat16 *>(out)[((size_t)b * COUT + o) * pl + p] = __float2bfloat16(v);
-        else
-            reinterpret_cast<float *>(out)[((size_t)b * COUT + o) * pl + p] = v;
+        reinterpret_cast<uint4 *>(a0)[e] = pk;  // C8 with one group: [b][p][8]
     }
 }
 
@@ -142,7 +123,7 @@ __global__ void __launch_bounds__(256) k_conv_bwd_data(const float *__restrict__
 #pragma unroll
     for (int i = 0; i < CIN; ++i) {
         float v = acc[i];
-        if (MASK && !(__bfloat162float(mask[((size_t)b * CIN + i) * pl + p]) > 0.f)) v = 0.f;
+        if (MASK && !(__bfloat162float(mask[c8_at(b, i, p, CIN, pl)]) > 0.f)) v = 0.f;
         din[((size_t)b * CIN + i) * pl + p] = v;
     }
 }
@@ -161,7 +142,7 @@ __global__ void __launch_bounds__(256) k_conv_bwd_weight(const __nv_bfloat16 *__
     for (int e = threadIdx.x; e < CIN * kTH * kTH; e += blockDim.x) {
         const int i = e / (kTH * kTH), r = e % (kTH * kTH), ly = r / kTH, lx = r % kTH;
         const int gy = wrap(y0 + ly - 1, n), gx = wrap(x0 + lx - 1, n);
-        xs[e] = __bfloat162float(in[((size_t)b * CIN + i) * pl + (size_t)gy * n + gx]);
+        xs[e] = __bfloat162float(in[c8_at(b, i, (size_t)gy * n + gx, CIN, pl)]);
     }
     for (int e = threadIdx.x; e < COUT * kT * kT; e += blockDim.x) {
         const int o = e / (kT * kT), r = e % (kT * kT), ly = r / kT, lx = r % kT;
@@ -286,15 +267,28 @@ struct mgk_cnn {
     __nv_bfloat16 *a0 = nullptr, *a1 = nullptr, *a2 = nullptr;
     float *z3 = nullptr, *d3 = nullptr, *d2 = nullptr, *d1 = nullptr, *tres = nullptr, *res = nullptr;
     float *part = nullptr, *loss_part = nullptr;
+    __nv_bfloat16 *wp = nullptr;  // tensor-core copies of the three layers' weights (conv_tc.cu)
     int *zero_status = nullptr;  // an always-zero status word for the shared prolongation kernel
+    int *status = nullptr;       // MGENKF_ERR_TIMEOUT from a tensor-core wait, sticky
     int step = 0;
     std::string err;
 };
 
 static int tiles_of(int n) { return (n + kT - 1) / kT; }
 
-template <int CIN, int COUT>
-static size_t smem_fwd() { return sizeof(float) * CIN * kTH * kTH + sizeof(__nv_bfloat16) * COUT * CIN * 9; }
+// packed tensor-core weights: layer l starts at wp_off(l) elements (16-byte aligned)
+static int wp_off(int l) {
+    int o = 0;
+    for (int q = 0; q < l; ++q) o += conv_packed_elems(kLayers[q].cin, kLayers[q].cout);
+    return o;
+}
+static int wp_elems() { return wp_off(3); }
+
+static void pack_weights(mgk_cnn *c, cudaStream_t s) {
+    for (int l = 0; l < 3; ++l)
+        launch_pack_conv_weights(c->w16 + kLayers[l].w_off, kLayers[l].cin, kLayers[l].cout, c->wp + wp_off(l), s);
+}
+
 template <int CIN, int COUT>
 static size_t smem_bwd_data() { return sizeof(float) * COUT * kTH * kTH + sizeof(__nv_bfloat16) * COUT * CIN * 9; }
 template <int CIN, int COUT>
@@ -304,9 +298,6 @@ static void set_smem_attrs() {
     static bool done = false;
     if (done) return;
     done = true;
-    cudaFuncSetAttribute(k_conv_fwd<32, 32, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_conv_fwd<32, 64, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_conv_fwd<8, 32, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_conv_bwd_data<32, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_conv_bwd_data<32, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_conv_bwd_weight<32, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -316,7 +307,7 @@ static void set_smem_attrs() {
 
 static void cnn_free(mgk_cnn *c) {
     void *ptrs[] = {c->w, c->m, c->v, c->g, c->w16, c->stats, c->a0, c->a1, c->a2, c->z3, c->d3,
-                    c->d2, c->d1, c->tres, c->res, c->part, c->loss_part, c->zero_status};
+                    c->d2, c->d1, c->tres, c->res, c->part, c->loss_part, c->wp, c->zero_status, c->status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -347,6 +338,7 @@ extern "C" mgenkf_status mgk_cnn_create(int32_t n_coarse, int32_t batch_max, mgk
         {(void **)&c->d1, B * 32 * pl * 4},             {(void **)&c->tres, B * 4 * 16 * pl * 4},
         {(void **)&c->res, B * 4 * 16 * pl * 4},        {(void **)&c->part, tiles * plen * 4},
         {(void **)&c->loss_part, 4096 * sizeof(float)},  {(void **)&c->zero_status, sizeof(int)},
+        {(void **)&c->wp, (size_t)wp_elems() * 2},         {(void **)&c->status, sizeof(int)},
     };
     for (auto &a : allocs) {
         if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
@@ -362,6 +354,8 @@ extern "C" mgenkf_status mgk_cnn_create(int32_t n_coarse, int32_t batch_max, mgk
     cudaMemset(c->v, 0, kCnnParams * sizeof(float));
     cudaMemset(c->w16, 0, kCnnParams * 2);
     cudaMemset(c->zero_status, 0, sizeof(int));
+    cudaMemset(c->status, 0, sizeof(int));
+    cudaMemset(c->wp, 0, (size_t)wp_elems() * 2);
     const float st[20] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
     cudaMemcpy(c->stats, st, sizeof(st), cudaMemcpyHostToDevice);
     set_smem_attrs();
@@ -394,6 +388,7 @@ extern "C" mgenkf_status mgk_cnn_set_params(mgk_cnn_t c, const float *params, co
         c->step = 0;
         count_launches(1);
         k_to_bf16<<<64, 256>>>(c->w, c->w16, kCnnParams);
+        pack_weights(c, 0);
     }
     if (stats && cudaMemcpy(c->stats, stats, 20 * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
         return MGENKF_ERR_CUDA;
@@ -403,6 +398,12 @@ extern "C" mgenkf_status mgk_cnn_set_params(mgk_cnn_t c, const float *params, co
 extern "C" mgenkf_status mgk_cnn_get_params(mgk_cnn_t c, float *params, float *grads) {
     if (!c) return MGENKF_ERR_INVALID_ARG;
     if (cudaDeviceSynchronize() != cudaSuccess) return MGENKF_ERR_CUDA;  // training launches on any stream
+    int st = 0;
+    if (cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MGENKF_ERR_CUDA;
+    if (st) {
+        mgk_set_error("mgk_cnn: a tensor-core wait expired in an earlier call");
+        return (mgenkf_status)st;
+    }
     if (params && cudaMemcpy(params, c->w, kCnnParams * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
         return MGENKF_ERR_CUDA;
     if (grads && cudaMemcpy(grads, c->g, kCnnParams * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
@@ -411,29 +412,33 @@ extern "C" mgenkf_status mgk_cnn_get_params(mgk_cnn_t c, float *params, float *g
 }
 
 // forward of B samples; fills c->z3 (and c->a0..a2)
-static void cnn_forward_impl(mgk_cnn *c, const float *dC, const float *xs, int B, cudaStream_t s) {
+static void cnn_forward_impl(mgk_cnn *c, const float *dC, const float *xs, int B, int *status, cudaStream_t s) {
     const int n = c->nc;
-    const dim3 grid(tiles_of(n), tiles_of(n), B);
     const float *mu = c->stats, *sc = c->stats + 8;
-    count_launches(4);
+    count_launches(1);
     k_cnn_input<<<256, 256, 0, s>>>(dC, xs, n, B, mu, sc, c->a0);
-    k_conv_fwd<8, 32, true, true><<<grid, 256, smem_fwd<8, 32>(), s>>>(c->a0, c->w16 + kLayers[0].w_off,
-                                                                      c->w + kLayers[0].b_off, c->a1, n);
-    k_conv_fwd<32, 32, true, true><<<grid, 256, smem_fwd<32, 32>(), s>>>(c->a1, c->w16 + kLayers[1].w_off,
-                                                                        c->w + kLayers[1].b_off, c->a2, n);
-    k_conv_fwd<32, 64, false, false><<<grid, 256, smem_fwd<32, 64>(), s>>>(c->a2, c->w16 + kLayers[2].w_off,
-                                                                          c->w + kLayers[2].b_off, c->z3, n);
+    launch_conv_fwd_tc<8, 32, true, true>(c->a0, c->wp + wp_off(0), c->w + kLayers[0].b_off, c->a1, n, B, status, s);
+    launch_conv_fwd_tc<32, 32, true, true>(c->a1, c->wp + wp_off(1), c->w + kLayers[1].b_off, c->a2, n, B, status, s);
+    launch_conv_fwd_tc<32, 64, false, false>(c->a2, c->wp + wp_off(2), c->w + kLayers[2].b_off, c->z3, n, B, status,
+                                             s);
 }
 
-extern "C" mgenkf_status mgk_cnn_forward(mgk_cnn_t c, const float *dC, const float *xstar, int32_t batch,
-                                         float *residual, int32_t accumulate, void *stream) {
+namespace mgk {
+mgenkf_status cnn_forward_status(mgk_cnn_t c, const float *dC, const float *xstar, int batch, float *residual,
+                                 int accumulate, int *status, cudaStream_t s) {
     if (!c || !dC || !xstar || !residual || batch < 1 || batch > c->bmax) return MGENKF_ERR_INVALID_ARG;
-    const cudaStream_t s = (cudaStream_t)stream;
-    cnn_forward_impl(c, dC, xstar, batch, s);
+    cnn_forward_impl(c, dC, xstar, batch, status, s);
     count_launches(1);
     k_cnn_out_grad<<<512, 256, 0, s>>>(c->z3, c->nc, batch, c->stats + 16, nullptr, residual, accumulate, nullptr,
                                        nullptr, 0.f);
     return cudaGetLastError() == cudaSuccess ? MGENKF_OK : MGENKF_ERR_CUDA;
+}
+}  // namespace mgk
+
+extern "C" mgenkf_status mgk_cnn_forward(mgk_cnn_t c, const float *dC, const float *xstar, int32_t batch,
+                                         float *residual, int32_t accumulate, void *stream) {
+    if (!c) return MGENKF_ERR_INVALID_ARG;
+    return cnn_forward_status(c, dC, xstar, batch, residual, accumulate, c->status, (cudaStream_t)stream);
 }
 
 extern "C" mgenkf_status mgk_cnn_loss_grad(mgk_cnn_t c, const float *dC, const float *xstar, const float *target,
@@ -459,7 +464,7 @@ extern "C" mgenkf_status mgk_cnn_loss_grad(mgk_cnn_t c, const float *dC, const f
     k_negate<<<512, 256, 0, s>>>(c->tres, fine);
     count_launches(1);
     k_sub_prolong<<<512, 256, 0, s>>>(target, c->tres, fine);
-    cnn_forward_impl(c, dC, xstar, B, s);
+    cnn_forward_impl(c, dC, xstar, B, c->status, s);
     count_launches(1);
     const float inv_count = 1.f / (float)fine;
     k_cnn_out_grad<<<512, 256, 0, s>>>(c->z3, n, B, c->stats + 16, c->tres, c->res, 0, c->d3, c->loss_part,
@@ -495,5 +500,6 @@ extern "C" mgenkf_status mgk_cnn_adam_step(mgk_cnn_t c, float lr, void *stream) 
     const float c1 = 1.f - powf(b1, (float)c->step), c2 = 1.f - powf(b2, (float)c->step);
     count_launches(1);
     k_adam<<<128, 256, 0, (cudaStream_t)stream>>>(c->w, c->m, c->v, c->g, c->w16, kCnnParams, lr, b1, b2, 1e-8f, c1, c2);
+    pack_weights(c, (cudaStream_t)stream);
     return cudaGetLastError() == cudaSuccess ? MGENKF_OK : MGENKF_ERR_CUDA;
 }

@@ -548,8 +548,8 @@ static mgenkf_status prolong_impl(mgenkf_ctx *h) {
         launch_prolong_add<double>((double *)h->fine, (const double *)h->dC, h->dim, h->V, h->nc, h->r, h->pw, h->status, h->stream);
     H_LAUNCHED();
     if (h->cnn) {
-        mgenkf_status st = mgk_cnn_forward(h->cnn, (const float *)h->dC, (const float *)h->xstar, 1,
-                                           (float *)h->fine, 1, h->stream);
+        mgenkf_status st = cnn_forward_status(h->cnn, (const float *)h->dC, (const float *)h->xstar, 1,
+                                              (float *)h->fine, 1, h->status, h->stream);
         if (st) H_FAIL(st, std::string("learned correction: ") + mgk_last_error());
     }
     if (h->alpha > 0.0 && h->have_prev) {

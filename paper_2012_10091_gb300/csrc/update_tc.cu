@@ -27,6 +27,7 @@
 
 #include "analysis.h"
 #include "common.cuh"
+#include "tc_common.cuh"
 #include "update_tc.h"
 
 namespace mgk {
@@ -35,69 +36,7 @@ namespace {
 
 constexpr int kTileM = 128;
 constexpr int kAtomK = 64;                        // bf16 values per 128-byte swizzle row
-constexpr long long kWaitLimitCycles = 2000000000LL;  // ~1 s at 2 GHz
-constexpr int kStTimeout = 7;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// bounded wait on phase `parity`; returns false if the limit expired
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > kWaitLimitCycles) return false;
-    }
-}
-
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(x), "r"(y), "r"(smem_u32(src))
-                 : "memory");
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);        // start address
-    d |= (uint64_t)1 << 16;                       // leading byte offset (unused with swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset
-    d |= (uint64_t)1 << 46;                       // version
-    d |= (uint64_t)2 << 61;                       // layout: 128-byte swizzle
-    return d;
-}
-
-// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
+using namespace tc;
 
 }  // namespace
 
@@ -117,16 +56,16 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ CUten
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
     __shared__ int s_fail;
 
-    if (*status) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kTileM;
     if (tid == 0) {
-        s_fail = 0;
+        s_fail = *status;  // one read: the whole CTA leaves or none of it
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    if (s_fail) return;  // s_fail is 0 from here on until the TMA wait below
     const uint32_t tx_bytes = (uint32_t)kblocks * (kTileM + ntile) * 128 + (uint32_t)ne * kTileM * 4;
     if (tid == 0) {
         mbar_expect_tx(&bars[0], tx_bytes);
@@ -158,21 +97,15 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ CUten
                 const int kb = j / (kAtomK / 16), kk = j % (kAtomK / 16);
                 const uint64_t adesc = smem_desc_sw128(smem_u32(sa + (size_t)kb * kTileM * 128 + kk * 32));
                 const uint64_t bdesc = smem_desc_sw128(smem_u32(sb + (size_t)kb * ntile * 128 + kk * 32));
-                const uint32_t acc = j > 0 ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-                    : "memory");
+                mma_bf16(tmem, adesc, bdesc, idesc, j > 0 ? 1u : 0u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&bars[1]))
-                         : "memory");
+            mma_commit(&bars[1]);
         }
     }
     __syncthreads();
     bool ok = s_fail == 0;
     if (ok && !mbar_wait(&bars[1], 0)) ok = false;
+    ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the TMEM loads below are warp-collective
     if (!ok) {
         if (tid == 0) {
             atomicCAS(status, 0, kStTimeout);

@@ -48,7 +48,9 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("nc,B", [(8, 2), (20, 1), (32, 3)])
+# 130: two 128-pixel tiles per row (the second ragged) and a ragged last row
+# block; 256: the learned-correction configuration (256^2 coarse, 1024^2 fine)
+@pytest.mark.parametrize("nc,B", [(8, 2), (20, 1), (32, 3), (130, 1), (256, 1)])
 def test_forward_matches_oracle(M, nc, B):
     import torch
     params, stats, dC, xs, _ = _case(nc, B, nc)

@@ -7,7 +7,9 @@
 // row ne = y^o - H^C x^C*), gain coefficients T [(ne+1)][ne] (column c of
 // T = Y^T C^-1 [D | d*] contiguous).  Every covariance-type reduction, the
 // Cholesky factorisation and the triangular solves run in FP64.
+#include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include <cooperative_groups.h>
 
@@ -84,7 +86,7 @@ void launch_obs_apply(const T *members, const T *xstar, size_t nx, int ne, int n
 // observation means and innovations (Algorithm 1 step 4; Algorithm 4 step 5)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_obs_mean(const double *__restrict__ yf,
-                                                  const double *__restrict__ yo, int ne, int ny,
+                                                  const double *__restrict__ yo, int ne, double inv_ne, int ny,
                                                   double *__restrict__ ybar, double *__restrict__ Z,
                                                   int *status) {
     // 32 observations per CTA (lane), 8 slices of the members (warp); the slice
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(256) k_obs_mean(const double *__restrict__ yf,
         double sum = 0.0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) sum += part[q][lane];
-        ybar[j] = sum / ne;
+        ybar[j] = sum * inv_ne;
         const double y = yo[j];
         if (!isfinite(y)) atomicCAS(status, 0, kStNonFinite);
         Z[(size_t)ne * ny + j] = y - yf[(size_t)ne * ny + j];
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(256) k_obs_mean(const double *__restrict__ yf,
 void launch_obs_mean(const double *yf, const double *yo, int ne, int ny, double *ybar, double *Z,
                      int *status, cudaStream_t s) {
     count_launches(1);
-    k_obs_mean<<<ceil_div(ny, 32), 256, 0, s>>>(yf, yo, ne, ny, ybar, Z, status);
+    k_obs_mean<<<ceil_div(ny, 32), 256, 0, s>>>(yf, yo, ne, 1.0 / ne, ny, ybar, Z, status);
 }
 
 // RMS of the innovation d* = y^o - H^C x^C* (one value; fixed-order FP64 sums)
@@ -139,13 +141,12 @@ void launch_innov_rms(const double *Z, int ne, int ny, double *out, cudaStream_t
 __global__ void k_obs_perturb(const double *__restrict__ yf, const double *__restrict__ ybar,
                               const double *__restrict__ yo, double *__restrict__ eps, int gen_eps,
                               uint64_t seed, const uint64_t *__restrict__ cycle, double sigma, int ne,
-                              int ny, double *__restrict__ Y, double *__restrict__ Z) {
+                              int ny, double isq, double *__restrict__ Y, double *__restrict__ Z) {
     const size_t total = (size_t)ne * ny;
     const size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (4 * b >= total) return;
     double z[4];
     if (gen_eps) philox_normals4(seed, kEpsTag, *cycle, (uint64_t)b, z);
-    const double isq = 1.0 / sqrt((double)(ne - 1));
     int i = (int)((4 * b) / ny), j = (int)(4 * b - (size_t)i * ny);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
@@ -174,8 +175,9 @@ void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, 
                         double *Y, double *Z, cudaStream_t s) {
     count_launches(1);
     const size_t blocks = ((size_t)ne * ny + 3) / 4;
+    // isq = 1/sqrt(Ne - 1) from the host (an FP64 division and square root per thread on the device)
     k_obs_perturb<<<(unsigned)ceil_div(blocks, 128), 128, 0, s>>>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma,
-                                                                   ne, ny, Y, Z);
+                                                                   ne, ny, 1.0 / std::sqrt((double)(ne - 1)), Y, Z);
 }
 
 // Fine-to-coarse feedback: the forecast ensemble re-centred on the restricted
@@ -202,46 +204,68 @@ template void launch_recentre<float>(float *, size_t, int, const float *, const 
 template void launch_recentre<double>(double *, size_t, int, const double *, const int *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// ensemble mean (FP64 accumulation) and normalised anomalies X
+// ensemble mean (FP64 accuracy) and normalised anomalies X
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_ens_anom(const T *__restrict__ m, size_t nx, int ne,
-                                                  double *__restrict__ X64,
+__global__ void __launch_bounds__(256) k_ens_anom(const T *__restrict__ m, size_t nx, int ne, double inv_ne,
+                                                  double isq, double *__restrict__ X64,
                                                   __nv_bfloat16 *__restrict__ X16, int ldx,
                                                   const int *status) {
     // CTA: 32 consecutive points (lane) x the members split over the 8 warps.
-    // FP64 mean (slice sums combined in a fixed order), then the normalised
-    // anomalies: FP64 member-major rows, or BF16 point-major rows assembled in
-    // shared memory so every row of ldx values is stored contiguously.
+    // Mean: per-warp slice sums combined in FP64 in a fixed order by warp 0;
+    // then the normalised anomalies: FP64 member-major rows, or BF16
+    // point-major rows assembled in shared memory so every row of ldx values
+    // is stored contiguously.  GB300 runs about 2 FP64 FMAs per clock per SM,
+    // so FP32 states are summed per slice in FP32 with an error-free two-sum
+    // (the running sum and its rounding errors, both exact in FP32), and
+    // 1/Ne and 1/sqrt(Ne - 1) come from the host: 3 FP64 operations per
+    // thread instead of one per member plus a division and a square root.
     extern __shared__ __align__(16) unsigned char sm_raw[];
     double *part = reinterpret_cast<double *>(sm_raw);                        // [8][32]
-    __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(part + 8 * 32);  // [32][ldx + 8]
+    double *mean = part + 8 * 32;                                             // [32]
+    __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(mean + 32);      // [32][ldx + 8]
     if (*status) return;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const size_t p0 = blockIdx.x * (size_t)32;
     const size_t p = p0 + lane;
     const bool ok = p < nx;
-    double acc = 0.0;
-    if (ok)
-        for (int i = wp; i < ne; i += 8) acc += (double)m[(size_t)i * nx + p];
-    part[wp * 32 + lane] = acc;
+    double slice;
+    if constexpr (std::is_same<T, float>::value) {
+        float sh = 0.f, sl = 0.f;
+        if (ok)
+            for (int i = wp; i < ne; i += 8) {
+                const float a = m[(size_t)i * nx + p];
+                const float t = sh + a, bv = t - sh;
+                sl += (sh - (t - bv)) + (a - bv);  // rounding error of sh + a, exact
+                sh = t;
+            }
+        slice = (double)sh + (double)sl;
+    } else {
+        double acc = 0.0;
+        if (ok)
+            for (int i = wp; i < ne; i += 8) acc += (double)m[(size_t)i * nx + p];
+        slice = acc;
+    }
+    part[wp * 32 + lane] = slice;
     __syncthreads();
-    double sum = 0.0;
+    if (wp == 0) {
+        double sum = 0.0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) sum += part[q * 32 + lane];
-    const double xb = sum / ne;
-    // 1/sqrt(Ne - 1) once: GB300's FP64 division is a long DFMA sequence
-    const double isq = 1.0 / sqrt((double)(ne - 1));
+        for (int q = 0; q < 8; ++q) sum += part[q * 32 + lane];
+        mean[lane] = sum * inv_ne;
+    }
+    __syncthreads();
+    const double xb = mean[lane];
     const int ldt = ldx + 8;
     if (X64) {
         if (ok)
             for (int i = wp; i < ne; i += 8) X64[(size_t)i * nx + p] = ((double)m[(size_t)i * nx + p] - xb) * isq;
         return;
     }
-    // BF16 path: FP64 mean, FP32 centring and scaling.  The FP32 rounding of
-    // the mean (2^-24 of the state) is far below the BF16 rounding of the
-    // anomaly (2^-9 of the anomaly) for any spread above 2^-15 of the state,
-    // and GB300's FP64 pipe is 64x slower than its FP32 pipes.
+    // BF16 path: FP64-accurate mean, FP32 centring and scaling.  The FP32
+    // rounding of the mean (2^-24 of the state) is far below the BF16 rounding
+    // of the anomaly (2^-9 of the anomaly) for any spread above 2^-15 of the
+    // state.
     const float isqf = (float)isq, xbf = (float)xb;
     for (int i = wp; i < ldx; i += 8)
         tile[lane * ldt + i] = __float2bfloat16((ok && i < ne) ? ((float)m[(size_t)i * nx + p] - xbf) * isqf : 0.f);
@@ -261,10 +285,11 @@ void launch_ens_anom(const T *members, size_t nx, int ne, double *X64, __nv_bflo
                      const int *status, cudaStream_t s) {
     count_launches(1);
     const int ldx = (ne + 15) / 16 * 16;
-    const size_t smem = sizeof(double) * 8 * 32 + sizeof(__nv_bfloat16) * 32 * (size_t)(ldx + 8);
+    const size_t smem = sizeof(double) * 9 * 32 + sizeof(__nv_bfloat16) * 32 * (size_t)(ldx + 8);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_ens_anom<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ens_anom<T><<<ceil_div(nx, 32), 256, smem, s>>>(members, nx, ne, X64, X16, ldx, status);
+    k_ens_anom<T><<<ceil_div(nx, 32), 256, smem, s>>>(members, nx, ne, 1.0 / ne, 1.0 / std::sqrt((double)(ne - 1)),
+                                                       X64, X16, ldx, status);
 }
 
 // ---------------------------------------------------------------------------

@@ -55,11 +55,11 @@ WORKLOADS = {
     # move 128 algorithmic bytes (stage 0: read u0, write s1; stages 1 and 2:
     # read the stage input and u0, write the output; 16 B per point each)
     # traffic: DRAM bytes per point-step of the three stage launches, measured
-    # by ncu on the 32x16-tile class of the 8-problem batch (12.5 M points,
-    # working set above L2) and scaled to the full batch by its point count;
-    # None once the kernel changes
+    # by ncu on the 32x16-tile class of the 8-problem batch (10.6 M points of
+    # 64^2 and 192^2 grids, working set above L2) and scaled to the full batch
+    # by its point count; None once the kernel changes
     "batched": dict(flops=600, bytes=128, kernel="ns2d_stage_x2<*,*,*,TableTiles>",
-                    launches_per_step=3, traffic=None, traffic_per_point_step=116.6, truth="fp32"),
+                    launches_per_step=3, traffic=None, traffic_per_point_step=151.0, truth="fp32"),
 }
 CNN_FLOPS_PER_PIXEL = 2 * 9 * (8 * 32 + 32 * 32 + 32 * 64)  # three 3x3 convolutions per coarse pixel
 

@@ -295,36 +295,74 @@ void launch_ens_anom(const T *members, size_t nx, int ne, double *X64, __nv_bflo
 // ---------------------------------------------------------------------------
 // FP64 GEMMs of the gain (Algorithm 3 step 8)
 // ---------------------------------------------------------------------------
-__global__ void k_gemm_nt(const double *__restrict__ A, int m, const double *__restrict__ B1, int n1,
-                          const double *__restrict__ B2, int n2, int K, double divisor, double diag,
-                          double *__restrict__ out1, double *__restrict__ out2, const int *status) {
-    if (status && *status) return;
-    __shared__ double As[16][33];
-    __shared__ double Bs[16][33];
-    const int a0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+// [out1 | out2^T] = A [B1; B2]^T / divisor (+ diag on out1's diagonal), FP64.
+// One 16 x 16 output tile per CTA of 256 threads, one output per thread, k in
+// chunks of 32 staged in shared memory; the next chunk's loads are issued
+// before the current chunk's FMAs, so they are in flight while GB300's slow
+// FP64 pipe works.  When B1 is A and n1 = m, out1 = A A^T / divisor + diag I is
+// symmetric: tiles strictly below its diagonal are not computed (a quarter of
+// the FMAs of S = I + Y^T R^-1 Y [Y | D | d*]), their values are the mirror
+// of the tiles above (the same products, so the same bits).
+__device__ __forceinline__ double gemm_nt_tile(const double *__restrict__ A, int m, const double *__restrict__ B1,
+                                               int n1, const double *__restrict__ B2, int n2, int K, int kb,
+                                               int ke, int a0, int c0, double (&As)[16][33],
+                                               double (&Bs)[16][33]) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const double *arow[2], *brow[2];
+    int rr[2], kq[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        rr[q] = e >> 5;
+        kq[q] = e & 31;
+        const int a = a0 + rr[q], c = c0 + rr[q];
+        arow[q] = a < m ? A + (size_t)a * K : nullptr;
+        brow[q] = c < n1 ? B1 + (size_t)c * K : (c < n1 + n2 ? B2 + (size_t)(c - n1) * K : nullptr);
+    }
+    double va[2], vb[2];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int k = k0 + kq[q];
+            va[q] = (arow[q] && k < ke) ? arow[q][k] : 0.0;
+            vb[q] = (brow[q] && k < ke) ? brow[q][k] : 0.0;
+        }
+    };
+    fetch(kb);
     double acc = 0.0;
-    for (int k0 = 0; k0 < K; k0 += 32) {
-        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
-            const int r = e >> 5, kk = e & 31, k = k0 + kk;
-            const int a = a0 + r;
-            As[r][kk] = (a < m && k < K) ? A[(size_t)a * K + k] : 0.0;
-            const int c = c0 + r;
-            const double *brow = c < n1 ? B1 + (size_t)c * K
-                                        : (c < n1 + n2 ? B2 + (size_t)(c - n1) * K : nullptr);
-            Bs[r][kk] = (brow && k < K) ? brow[k] : 0.0;
+    for (int k0 = kb; k0 < ke; k0 += 32) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            As[rr[q]][kq[q]] = va[q];
+            Bs[rr[q]][kq[q]] = vb[q];
         }
         __syncthreads();
+        if (k0 + 32 < ke) fetch(k0 + 32);
 #pragma unroll
         for (int kk = 0; kk < 32; ++kk) acc = fma(As[ty][kk], Bs[tx][kk], acc);
         __syncthreads();
     }
-    const int a = a0 + ty, c = c0 + tx;
+    return acc;
+}
+
+__global__ void k_gemm_nt(const double *__restrict__ A, int m, const double *__restrict__ B1, int n1,
+                          const double *__restrict__ B2, int n2, int K, double divisor, double diag,
+                          double *__restrict__ out1, double *__restrict__ out2, const int *status) {
+    if (status && *status) return;
+    const bool sym = B1 == A && n1 == m;
+    if (sym && blockIdx.x < blockIdx.y) return;  // mirrored from tile (x, y)
+    __shared__ double As[16][33];
+    __shared__ double Bs[16][33];
+    const int a0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+    const double acc = gemm_nt_tile(A, m, B1, n1, B2, n2, K, 0, K, a0, c0, As, Bs);
+    const int a = a0 + (threadIdx.x >> 4), c = c0 + (threadIdx.x & 15);
     if (a < m) {
-        if (c < n1)
+        if (c < n1) {
             out1[(size_t)a * n1 + c] = (a == c ? diag : 0.0) + acc / divisor;
-        else if (c < n1 + n2)
+            if (sym && blockIdx.x > blockIdx.y) out1[(size_t)c * n1 + a] = acc / divisor;
+        } else if (c < n1 + n2) {
             out2[(size_t)(c - n1) * m + a] = acc / divisor;
+        }
     }
 }
 
@@ -333,40 +371,28 @@ __global__ void k_gemm_nt_split(const double *__restrict__ A, int m, const doubl
                                 int n1, const double *__restrict__ B2, int n2, int K, int kchunk,
                                 double *__restrict__ part, const int *status) {
     if (status && *status) return;
+    if (B1 == A && n1 == m && blockIdx.x < blockIdx.y) return;  // symmetric: the reduce mirrors
     __shared__ double As[16][33];
     __shared__ double Bs[16][33];
     const int a0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    double acc = 0.0;
-    for (int k0 = kb; k0 < ke; k0 += 32) {
-        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
-            const int r = e >> 5, kk = e & 31, k = k0 + kk;
-            const int a = a0 + r;
-            As[r][kk] = (a < m && k < ke) ? A[(size_t)a * K + k] : 0.0;
-            const int c = c0 + r;
-            const double *brow = c < n1 ? B1 + (size_t)c * K
-                                        : (c < n1 + n2 ? B2 + (size_t)(c - n1) * K : nullptr);
-            Bs[r][kk] = (brow && k < ke) ? brow[k] : 0.0;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 32; ++kk) acc = fma(As[ty][kk], Bs[tx][kk], acc);
-        __syncthreads();
-    }
-    const int a = a0 + ty, c = c0 + tx;
+    const double acc = gemm_nt_tile(A, m, B1, n1, B2, n2, K, kb, ke, a0, c0, As, Bs);
+    const int a = a0 + (threadIdx.x >> 4), c = c0 + (threadIdx.x & 15);
     if (a < m && c < n1 + n2) part[((size_t)blockIdx.z * m + a) * (n1 + n2) + c] = acc;
 }
 
-__global__ void k_gemm_nt_reduce(const double *__restrict__ part, int nsplit, int m, int n1, int n2,
+__global__ void k_gemm_nt_reduce(const double *__restrict__ part, int nsplit, int m, int n1, int n2, bool sym,
                                  double divisor, double diag, double *__restrict__ out1,
                                  double *__restrict__ out2, const int *status) {
     if (status && *status) return;
     const int ncol = n1 + n2;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * ncol; e += gridDim.x * blockDim.x) {
         const int a = e / ncol, c = e % ncol;
+        // below the diagonal tiles of a symmetric out1: the mirrored element
+        const bool mirror = sym && c < n1 && (c >> 4) < (a >> 4);
+        const int ra = mirror ? c : a, rc = mirror ? a : c;
         double acc = 0.0;
-        for (int z = 0; z < nsplit; ++z) acc += part[((size_t)z * m + a) * ncol + c];
+        for (int z = 0; z < nsplit; ++z) acc += part[((size_t)z * m + ra) * ncol + rc];
         if (c < n1)
             out1[(size_t)a * n1 + c] = (a == c ? diag : 0.0) + acc / divisor;
         else
@@ -390,8 +416,8 @@ void launch_gemm_nt_f64(const double *A, int m, const double *B1, int n1, const 
         const int kchunk = ceil_div(ceil_div(K, splits), 32) * 32;
         dim3 grid(ceil_div(n1 + n2, 16), ceil_div(m, 16), splits);
         k_gemm_nt_split<<<grid, 256, 0, s>>>(A, m, B1, n1, B2, n2, K, kchunk, part, status);
-        k_gemm_nt_reduce<<<grid_for((size_t)m * (n1 + n2), 256), 256, 0, s>>>(part, splits, m, n1, n2,
-                                                                           scale_div, diag, out1, out2, status);
+        k_gemm_nt_reduce<<<grid_for((size_t)m * (n1 + n2), 256), 256, 0, s>>>(
+            part, splits, m, n1, n2, B1 == A && n1 == m, scale_div, diag, out1, out2, status);
         return;
     }
     count_launches(1);

@@ -76,8 +76,15 @@ def lib():
             L.orc_enkf_gain.argtypes = [i32, i32, i32, P, P, P, P]
             L.orc_enkf_gain.restype = i32
             L.orc_rmse.argtypes = [P, P, i32, i64, P]
+            L.orc_set_threads.argtypes = [i32]
             _LIB = L
     return _LIB
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's parallel loops (timing only: every
+    parallel loop runs over independent problems or members)."""
+    lib().orc_set_threads(int(n))
 
 
 def _p(a: np.ndarray):

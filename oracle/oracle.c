@@ -13,6 +13,20 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the OpenMP loops below.  Every parallel loop runs over
+ * independent problems or members, so no result depends on the count; it is
+ * set only to time the oracle on one core and on all of them. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
 
 /* ======================================================================== */
 /* Philox4x64-10, from the published definition (Salmon et al., SC'11):      */

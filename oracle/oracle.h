@@ -23,6 +23,10 @@
 #define MGENKF_ORACLE_H
 #include <stdint.h>
 
+/* OpenMP threads of the parallel loops (over independent problems/members:
+ * results do not depend on it); used to time the oracle on one core. */
+void orc_set_threads(int n);
+
 /* ---- counter-based RNG: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) ----
  * Pinned: against numpy.random.Philox (library) and published known answers. */
 void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);

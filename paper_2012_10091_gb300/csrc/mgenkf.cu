@@ -838,7 +838,7 @@ extern "C" uint64_t mgk_kernel_launches(void) { return g_launches.load(std::memo
 // batched cycles of independent NS-2D handles: one CUDA graph launch per cycle
 // ===========================================================================
 namespace {
-// analysis branches of the captured cycle (problem j on branch j mod count)
+// analysis branches of the captured cycle (problems spread by estimated cost)
 constexpr int kMaxBatchStreams = 128;
 constexpr int kDefaultBatchBranches = 16;  // measured best for the 96-problem batch (1, 4, 16, 128 tried)
 }
@@ -849,6 +849,7 @@ struct mgenkf_batch {
     bool own_s0 = false;  // created here when the caller passed the legacy stream
     std::vector<cudaStream_t> aux;
     int nbranch = 1;  // analysis branches (streams aux[0 .. nbranch))
+    std::vector<int> branch;  // branch of each problem
     std::vector<cudaEvent_t> ev;
     double *obs_stage = nullptr;
     double *innov = nullptr;  // per-problem innovation RMS of the last cycle
@@ -1023,6 +1024,28 @@ extern "C" mgenkf_status mgenkf_batch_create(const mgenkf_handle *handles, int32
     int cap = kDefaultBatchBranches;
     if (const char *e = getenv("MGENKF_BATCH_STREAMS")) cap = std::max(1, std::min(kMaxBatchStreams, atoi(e)));
     b->nbranch = std::min(n, cap);
+    // longest-processing-time-first: problems in decreasing order of their
+    // analysis cost, each onto the least-loaded branch.  Cost: the FP64 FMAs
+    // of S and Y^T R^-1 [D | d*] plus the Cholesky's, and the ensemble
+    // traffic of the anomalies and update at an eighth of the weight.
+    {
+        std::vector<double> cost(n);
+        std::vector<int> order(n);
+        for (int j = 0; j < n; ++j) {
+            const mgenkf_ctx *h = b->hs[j];
+            const double ne = h->ne, ny = h->ny, nx = (double)h->nx;
+            cost[j] = ne * (2 * ne + 1) * ny + ne * ne * ne / 3 + nx * ne / 8;
+            order[j] = j;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        std::vector<double> load(b->nbranch, 0.0);
+        b->branch.assign(n, 0);
+        for (int j : order) {
+            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            b->branch[j] = k;
+            load[k] += cost[j];
+        }
+    }
     const int nstreams = std::max(kNsTileShapes, b->nbranch);
     for (int k = 0; k < nstreams; ++k) {
         cudaStream_t s;
@@ -1081,7 +1104,7 @@ static mgenkf_status batch_analyse(mgenkf_batch *b) {
     for (size_t j = 0; j < b->hs.size(); ++j) {
         mgenkf_ctx *h = b->hs[j];
         cudaStream_t keep = h->stream;
-        h->stream = b->aux[j % ns];
+        h->stream = b->aux[b->branch[j]];
         mgenkf_status st = analyse_impl(h, b->obs_stage + b->obs_off[j], nullptr);
         if (st == MGENKF_OK) {
             launch_innov_rms(h->Z, h->ne, h->ny, b->innov + j, h->stream);

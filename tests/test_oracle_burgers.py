@@ -2,6 +2,7 @@
 differences + SSP-RK3): Fourier amplification factor, Cole-Hopf convergence
 and conservation of the discrete mass."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -70,3 +71,19 @@ def test_rhs_matches_hand_computed_three_point_case():
     assert L[0] == pytest.approx(-1.9, abs=1e-15)
     # point 1: F(+1) = 0.5 (u=-1), F(-1) = 0.5 (u=1) -> 0 ; diffusion 0.1*(-1 - 4 + 1)/0.25 = -1.6
     assert L[1] == pytest.approx(-1.6, abs=1e-15)
+
+
+def test_thread_count_changes_no_result():
+    # the OpenMP loops run over independent problems: one thread and several
+    # give the same bits (the CPU baseline times both)
+    rng = np.random.default_rng(3)
+    n, dx = 96, 2 * math.pi / 96
+    u0 = 0.5 + 0.3 * rng.standard_normal((7, n))
+    try:
+        O.set_threads(1)
+        one = O.burgers_rk3(u0, dx, 0.02, 1e-3, 50)
+        O.set_threads(4)
+        four = O.burgers_rk3(u0, dx, 0.02, 1e-3, 50)
+    finally:
+        O.set_threads(os.cpu_count() or 1)
+    assert np.array_equal(one, four)

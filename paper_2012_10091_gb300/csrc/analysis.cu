@@ -916,40 +916,63 @@ void launch_update_bf16(float *members, float *dC, const __nv_bfloat16 *Xt, cons
 // ---------------------------------------------------------------------------
 // prolongation of the coarse correction, Algorithm 4 step 5 second line
 // ---------------------------------------------------------------------------
+// periodic index of a 4-point stencil tap: c in [-1, nc + 2)
+__device__ __forceinline__ int wrap_tap(int c, int nc) {
+    if (c < 0) c += nc;
+    while (c >= nc) c -= nc;
+    return c;
+}
+
+// fine (+)= Pi_F(dC): the 4-point Lagrange interpolant at fine offset m of
+// coarse interval J (nodes J - 1 .. J + 2).  2-D is the tensor product,
+// evaluated separably: four 4-tap sums along x, then one 4-tap sum along y.
+// 2-D launch: x over the points of a fine row, y over the rows of all
+// variables, so the only divisions are by r and the periodic wraps are
+// compares.
 template <typename T>
 __global__ void k_prolong_add(T *__restrict__ fine, const T *__restrict__ dC, int dim, int V, int nc,
                               int r, ProlongWeights w, const int *status) {
     if (*status) return;
-    const size_t nf = (size_t)nc * r;
-    const size_t fpl = dim == 1 ? nf : nf * nf;
-    const size_t cpl = dim == 1 ? (size_t)nc : (size_t)nc * nc;
-    const size_t total = (size_t)V * fpl;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const size_t v = idx / fpl, k = idx % fpl;
-        const T *d = dC + v * cpl;
-        T acc = T(0);
-        if (dim == 1) {
-            const int J = (int)(k / r), m = (int)(k % r);
+    const int nf = nc * r;
+    if (dim == 1) {
+        const size_t total = (size_t)V * nf;
+        for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+             idx += (size_t)gridDim.x * blockDim.x) {
+            const int v = (int)(idx / nf), k = (int)(idx - (size_t)v * nf);
+            const T *d = dC + (size_t)v * nc;
+            const int J = k / r, m = k - J * r;
+            T acc = T(0);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) acc += (T)w.w[m][t] * d[(J - 1 + t + nc) % nc];
-        } else {
-            const int fy = (int)(k / nf), fx = (int)(k % nf);
-            const int Jy = fy / r, my = fy % r, Jx = fx / r, mx = fx % r;
-            T wx[4], wy[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                wx[t] = (T)w.w[mx][t];
-                wy[t] = (T)w.w[my][t];
-            }
-#pragma unroll
-            for (int ty = 0; ty < 4; ++ty) {
-                const size_t row = (size_t)((Jy - 1 + ty + nc) % nc) * nc;
-#pragma unroll
-                for (int tx = 0; tx < 4; ++tx) acc += (wy[ty] * wx[tx]) * d[row + (Jx - 1 + tx + nc) % nc];
-            }
+            for (int t = 0; t < 4; ++t) acc += (T)w.w[m][t] * d[wrap_tap(J - 1 + t, nc)];
+            fine[idx] += acc;
         }
-        fine[idx] += acc;
+        return;
+    }
+    const int fx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (fx >= nf) return;
+    const int Jx = fx / r, mx = fx - Jx * r;
+    int cx[4];
+    T wx[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        cx[t] = wrap_tap(Jx - 1 + t, nc);
+        wx[t] = (T)w.w[mx][t];
+    }
+    const size_t cpl = (size_t)nc * nc, fpl = (size_t)nf * nf;
+    for (int row = blockIdx.y; row < V * nf; row += gridDim.y) {
+        const int v = row / nf, fy = row - v * nf;
+        const int Jy = fy / r, my = fy - Jy * r;
+        const T *d = dC + (size_t)v * cpl;
+        T acc = T(0);
+#pragma unroll
+        for (int ty = 0; ty < 4; ++ty) {
+            const T *dr = d + (size_t)wrap_tap(Jy - 1 + ty, nc) * nc;
+            T sx = T(0);
+#pragma unroll
+            for (int tx = 0; tx < 4; ++tx) sx += wx[tx] * dr[cx[tx]];
+            acc += (T)w.w[my][ty] * sx;
+        }
+        fine[(size_t)v * fpl + (size_t)fy * nf + fx] += acc;
     }
 }
 
@@ -957,9 +980,13 @@ template <typename T>
 void launch_prolong_add(T *fine, const T *dC, int dim, int V, int nc, int r,
                         const ProlongWeights &w, const int *status, cudaStream_t s) {
     count_launches(1);
-    const size_t nf = (size_t)nc * r;
-    const size_t total = (size_t)V * (dim == 1 ? nf : nf * nf);
-    k_prolong_add<T><<<grid_for(total, 256), 256, 0, s>>>(fine, dC, dim, V, nc, r, w, status);
+    const int nf = nc * r;
+    if (dim == 1) {
+        k_prolong_add<T><<<grid_for((size_t)V * nf, 256), 256, 0, s>>>(fine, dC, dim, V, nc, r, w, status);
+    } else {
+        const dim3 grid(ceil_div(nf, 128), std::min(V * nf, 65535));
+        k_prolong_add<T><<<grid, 128, 0, s>>>(fine, dC, dim, V, nc, r, w, status);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -42,14 +42,18 @@ MAX_SM_MHZ = 2070.0
 # captured), and the precision of the synthetic truth run.
 WORKLOADS = {
     # SSP-RK3 Burgers, k-form: 3 x 9 (dt L) + 1 + 3 + 3 (stages) + 4 (Fast2Sum) = 38
-    "burgers_large": dict(flops=38, kernel="burgers_f32x2_kernel<8>", launches_per_step=None,
+    # flops (an FMA counts 2); as FP32 operations (FADD, FMUL, FFMA one each):
+    # 3 x 8 (dt L) + 1 + 2 + 6 (stages with the Fast2Sum compensation) = 33
+    "burgers_large": dict(flops=38, ops=33, kernel="burgers_f32x2_kernel<8>", launches_per_step=None,
                           traffic=2175232, truth="fp32"),
     # NS-2D: ~200 flops per point and stage (primitives, nodal fluxes, four
-    # face fluxes, stage update), 3 stages per step
-    "ns2d": dict(flops=600, kernel="ns2d_stage_x2<*,32,8,PairTiles>", launches_per_step=3,
+    # face fluxes, stage update), 3 stages per step; as FP32 operations per
+    # point and stage, counted from the kernel: 9 (primitives) + 28 (inviscid)
+    # + 66 (four faces) + 16 (sums, dt) + 4 or 12 (stage) = 128 on average
+    "ns2d": dict(flops=600, ops=385, kernel="ns2d_stage_x2<*,32,8,PairTiles>", launches_per_step=3,
                  traffic=None, truth="fp64"),
     # NS-2D 1024^2 / 256^2 with the learned correction of the prolongation
-    "ns2d_cnn": dict(flops=600, kernel="ns2d_stage_x2<*,32,8,PairTiles>", launches_per_step=3,
+    "ns2d_cnn": dict(flops=600, ops=385, kernel="ns2d_stage_x2<*,32,8,PairTiles>", launches_per_step=3,
                      traffic=None, truth="fp64"),
     # 96 independent NS-2D problems; per point-step the three stage kernels
     # move 128 algorithmic bytes (stage 0: read u0, write s1; stages 1 and 2:
@@ -483,9 +487,17 @@ def run_gpu(args, dist, w, inp):
     pts = w.ne * w.nc ** w.dim + w.nf ** w.dim
     lps = spec["launches_per_step"]
     launches_fc = 1 if lps is None else lps * w.steps_per_cycle
-    flops = spec["flops"] * pts * w.steps_per_cycle / launches_fc   # per launch
-    achieved = flops / (fc_mean / launches_fc) / 1e12
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    # FP32 operations per launch (FADD, FMUL, FFMA one each, counted from the
+    # scheme without the halo recomputation) against the FP32 pipes' rate of
+    # one operation per lane and clock: the kernels' mixes are mostly adds and
+    # multiplies, so the flop view (an FMA counts 2, against twice that peak)
+    # is reported beside it
+    launch_t = fc_mean / launches_fc
+    ops = spec["ops"] * pts * w.steps_per_cycle / launches_fc
+    achieved = ops / launch_t / 1e12
+    peak = NUM_SMS * FP32_LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
+    flops = spec["flops"] * pts * w.steps_per_cycle / launches_fc
+    peak_flops = 2 * peak
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the current
     # forecast kernel, from an ncu capture of this workload (Burgers); None until
     # captured, and reset whenever the kernel changes
@@ -513,9 +525,13 @@ def run_gpu(args, dist, w, inp):
             "regularisation": regularisation,
             "recentre_ablation": feedback,
             "roofline": {"bound": "alu", "kernel": spec["kernel"],
-                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "achieved": achieved, "peak": peak, "unit": "TOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": "FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+                         "peak_source": "FP32 operations: 152 SMs x 128 lanes x 2070 MHz",
+                         "ops_per_point_step": spec["ops"],
+                         "flop_view": {"achieved_tflops": flops / launch_t / 1e12, "peak_tflops": peak_flops,
+                                       "frac": flops / launch_t / 1e12 / peak_flops,
+                                       "flops_per_point_step": spec["flops"]},
                          "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": peak_src},
             "clocks": clk,
             "gpu_launches": int(launches),

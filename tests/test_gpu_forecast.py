@@ -106,3 +106,26 @@ def test_fp32_forecast_has_no_drift_over_long_horizon(M):
     torch.cuda.synchronize()
     err = np.max(np.abs(d.cpu().double().numpy() - ref)) / np.max(np.abs(ref))
     assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("nf", [8192, 16384, 32768])
+def test_split_grid_halo_exchange_paths_agree(M, nf):
+    # A handle's mixed forecast advances its split fine grid (a cluster of
+    # CTAs exchanging halos over distributed shared memory) in one launch with
+    # the members; the stateless forecast advances it alone.  Same arithmetic
+    # on every segment: the same bits.
+    import torch
+    from paper_2012_10091_gb300 import workloads as W
+    w = W.burgers_custom(nf, 8 if nf > 16384 else 4, 8, 16, precision="mixed",
+                         dt=0.3 * (2 * math.pi / nf) ** 2 / 0.01)
+    inp = W.make_inputs(w)
+    g = M.MGEnKF.from_workload(w, precision="mixed")
+    g.set_state(inp["fine0"], inp["members0"])
+    g.forecast(300)
+    assert g.sync() == 0
+    fine, _ = g.get_state()
+    d = torch.tensor(inp["fine0"], dtype=torch.float32, device="cuda")
+    M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_MIXED, d, 1, nf, w.length, w.dt, w.nu, nsteps=300)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(fine.astype(np.float32), d.cpu().numpy())
+    g.close()

@@ -58,33 +58,45 @@ __device__ __forceinline__ NsNode ns_node(const T *q, int n, int x, int y, doubl
     a.mx = (double)q[plane + o];
     a.my = (double)q[2 * plane + o];
     a.E = (double)q[3 * plane + o];
-    a.u = a.mx / a.rho;
-    a.v = a.my / a.rho;
+    // one FP64 division per node (GB300 runs about 2 FP64 FMAs per clock per SM)
+    const double ri = 1.0 / a.rho;
+    a.u = a.mx * ri;
+    a.v = a.my * ri;
     a.p = gm1 * (a.E - 0.5 * a.rho * (a.u * a.u + a.v * a.v));
-    a.T = a.p / a.rho;
+    a.T = a.p * ri;
     return a;
 }
+
+constexpr int kResTile = 16;  // points per side of a CTA's tile (16 x 16 threads)
 
 // Eqs. Mass, Momentum, Energy discretised as the forecast does it: central
 // differences of the nodal inviscid fluxes, viscous and heat fluxes on the
 // four faces (compact normal derivative, averaged central tangential one).
+// A CTA derives the primitives of its 18 x 18 nodes (tile and halo) once, in
+// shared memory, then every thread reads its 3 x 3 neighbourhood from there.
 template <typename T>
 __global__ void __launch_bounds__(256) k_ns2d_residual(const T *__restrict__ q, const T *__restrict__ prev, int n,
                                                        double h, double gamma, double mu, double prandtl,
                                                        double dt, double alpha, T *__restrict__ out,
                                                        double *__restrict__ gamma_out, const int *status) {
-    if (status && *status) return;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * n) return;
-    const int x = idx % n, y = idx / n;
+    constexpr int HW = kResTile + 2;
+    __shared__ NsNode nodes[HW * HW];
+    if (status && *status) return;  // set only by earlier launches: the same for the whole CTA
     const double gm1 = gamma - 1.0, kap = mu * gamma / (gm1 * prandtl);
     const double ih = 1.0 / h, i2h = 0.5 / h;
-    NsNode nd[3][3];  // [dy + 1][dx + 1]
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) nd[dy + 1][dx + 1] = ns_node(q, n, x + dx, y + dy, gm1);
-    const NsNode &C = nd[1][1], &Ee = nd[1][2], &Ww = nd[1][0], &Nn = nd[2][1], &Ss = nd[0][1];
+    const int x0 = blockIdx.x * kResTile, y0 = blockIdx.y * kResTile;
+    for (int e = threadIdx.x; e < HW * HW; e += blockDim.x) {
+        const int ly = e / HW, lx = e - ly * HW;
+        nodes[e] = ns_node(q, n, x0 - 1 + lx, y0 - 1 + ly, gm1);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % kResTile, ty = threadIdx.x / kResTile;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= n || y >= n) return;
+    const size_t idx = (size_t)y * n + x;
+    // nd(dy, dx): the node at offset (dx, dy) from this thread's point
+    auto nd = [&](int dy, int dx) -> const NsNode & { return nodes[(ty + 1 + dy) * HW + tx + 1 + dx]; };
+    const NsNode &C = nd(0, 0), &Ee = nd(0, 1), &Ww = nd(0, -1), &Nn = nd(1, 0), &Ss = nd(-1, 0);
     double L[4];
     L[0] = -((Ee.mx - Ww.mx) + (Nn.my - Ss.my)) * i2h;
     L[1] = -(((Ee.mx * Ee.u + Ee.p) - (Ww.mx * Ww.u + Ww.p)) + (Nn.my * Nn.u - Ss.my * Ss.u)) * i2h;
@@ -94,8 +106,8 @@ __global__ void __launch_bounds__(256) k_ns2d_residual(const T *__restrict__ q, 
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
         {   // x-face between columns a = side - 1 and b = side (offsets from the node)
-            const NsNode &a = nd[1][side], &b = nd[1][side + 1];
-            const NsNode &an = nd[2][side], &as = nd[0][side], &bn = nd[2][side + 1], &bs = nd[0][side + 1];
+            const NsNode &a = nd(0, side - 1), &b = nd(0, side);
+            const NsNode &an = nd(1, side - 1), &as = nd(-1, side - 1), &bn = nd(1, side), &bs = nd(-1, side);
             const double ux = (b.u - a.u) * ih, vx = (b.v - a.v) * ih;
             const double uy = 0.5 * ((an.u - as.u) + (bn.u - bs.u)) * i2h;
             const double vy = 0.5 * ((an.v - as.v) + (bn.v - bs.v)) * i2h;
@@ -106,8 +118,8 @@ __global__ void __launch_bounds__(256) k_ns2d_residual(const T *__restrict__ q, 
             fx[side][2] = txx * uf + txy * vf + kap * (b.T - a.T) * ih;
         }
         {   // y-face between rows a = side - 1 and b = side
-            const NsNode &a = nd[side][1], &b = nd[side + 1][1];
-            const NsNode &ae = nd[side][2], &aw = nd[side][0], &be = nd[side + 1][2], &bw = nd[side + 1][0];
+            const NsNode &a = nd(side - 1, 0), &b = nd(side, 0);
+            const NsNode &ae = nd(side - 1, 1), &aw = nd(side - 1, -1), &be = nd(side, 1), &bw = nd(side, -1);
             const double uy = (b.u - a.u) * ih, vy = (b.v - a.v) * ih;
             const double ux = 0.5 * ((ae.u - aw.u) + (be.u - bw.u)) * i2h;
             const double vx = 0.5 * ((ae.v - aw.v) + (be.v - bw.v)) * i2h;
@@ -142,8 +154,9 @@ void launch_fine_residual(int model, const T *x, const T *prev, int n, double le
     if (model == 1) {
         k_burgers_residual<T><<<ceil_div(n, 256), 256, 0, s>>>(x, prev, n, h, nu, dt, alpha, out, gamma_out, status);
     } else {
-        k_ns2d_residual<T><<<ceil_div(n * n, 256), 256, 0, s>>>(x, prev, n, h, gamma, nu, prandtl, dt, alpha, out,
-                                                               gamma_out, status);
+        const dim3 grid(ceil_div(n, kResTile), ceil_div(n, kResTile));
+        k_ns2d_residual<T><<<grid, 256, 0, s>>>(x, prev, n, h, gamma, nu, prandtl, dt, alpha, out, gamma_out,
+                                                status);
     }
 }
 

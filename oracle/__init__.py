@@ -77,6 +77,7 @@ def lib():
             L.orc_enkf_gain.restype = i32
             L.orc_rmse.argtypes = [P, P, i32, i64, P]
             L.orc_set_threads.argtypes = [i32]
+            L.orc_ns2d_filter6.argtypes = [P, i32, i32, f64]
             _LIB = L
     return _LIB
 
@@ -209,6 +210,16 @@ def ns2d_rk3(q, h, gamma, mu, prandtl, dt, nsteps) -> np.ndarray:
     return x2.reshape(shape)
 
 
+def ns2d_filter6(q, sigma) -> np.ndarray:
+    """Centred sixth-order filter (Secs. 5, 6) of (nprob x) 4 x n x n conserved states."""
+    x = _f64(q).copy()
+    shape = x.shape
+    n = _ns_side(x)
+    x2 = x.reshape(-1, 4, n, n)
+    lib().orc_ns2d_filter6(_p(x2), x2.shape[0], n, float(sigma))
+    return x2.reshape(shape)
+
+
 def lagrange_weights(nodes, s) -> np.ndarray:
     nd = _f64(nodes)
     w = np.zeros_like(nd)
@@ -282,7 +293,8 @@ class MGEnKF:
     """
 
     def __init__(self, model, nf, ratio, length, dt, fine, members, obs_idx, obs_var, sigma,
-                 seed, nu=0.0, gamma=1.4, prandtl=0.72, gain_form=1, alpha=0.0, recentre=False):
+                 seed, nu=0.0, gamma=1.4, prandtl=0.72, gain_form=1, alpha=0.0, recentre=False,
+                 filter_sigma=0.0):
         self.model = model
         self.dim = 1 if model == "burgers1d" else 2
         self.V = 1 if model == "burgers1d" else 4
@@ -300,13 +312,19 @@ class MGEnKF:
         self.alpha = alpha          # final fine iteration (Algorithm 4 step 6); 0 = none
         self.recentre = recentre    # re-centre the forecast ensemble on x^C* before each analysis
         self.fine_prev = None       # fine state one model step before the analysis time
+        self.filter_sigma = filter_sigma  # NS: sixth-order filter after every model step (0 = off)
 
     def _advance(self, x, n, nsteps):
         h = self.length / n
         if self.model == "burgers1d":
             return burgers_rk3(x, h, self.nu, self.dt, nsteps)
-        return ns2d_rk3(x.reshape(-1, 4, n, n), h, self.gamma, self.nu, self.prandtl, self.dt,
-                        nsteps).reshape(x.shape)
+        q = x.reshape(-1, 4, n, n)
+        if self.filter_sigma > 0:
+            for _ in range(nsteps):   # the model step is the RK3 step followed by the filter
+                q = ns2d_filter6(ns2d_rk3(q, h, self.gamma, self.nu, self.prandtl, self.dt, 1),
+                                 self.filter_sigma)
+            return q.reshape(x.shape)
+        return ns2d_rk3(q, h, self.gamma, self.nu, self.prandtl, self.dt, nsteps).reshape(x.shape)
 
     def forecast(self, nsteps):
         """Algorithm 4 step 2 (fine) and Algorithm 3 step 2 (members)."""

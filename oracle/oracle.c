@@ -214,6 +214,40 @@ void orc_ns2d_rhs(const double *q, int n, double h, double gamma, double mu, dou
     free(T);
 }
 
+/* Centred sixth-order explicit filter of the Euler and Navier-Stokes models
+ * (Secs. 5 and 6; the paper cites Bogey and Bailly 2004 and prints no
+ * coefficients).  Reading: the standard 7-point centred stencil
+ *   u_j <- u_j - sigma/64 (-u_{j-3} + 6 u_{j-2} - 15 u_{j-1} + 20 u_j
+ *                          - 15 u_{j+1} + 6 u_{j+2} - u_{j+3}),
+ * whose transfer function is 1 - sigma sin^6(k h / 2) (exact on Fourier modes,
+ * zero-sum stencil: totals conserved), applied along x and then along y to
+ * each of the four conserved planes of an n x n periodic grid. */
+void orc_ns2d_filter6(double *q, int nprob, int n, double sigma) {
+    static const double d[7] = {-1.0, 6.0, -15.0, 20.0, -15.0, 6.0, -1.0};
+    const size_t plane = (size_t)n * n;
+    double *line = malloc(sizeof(double) * (size_t)n);
+    for (size_t pl = 0; pl < (size_t)nprob * 4; ++pl) {
+        double *u = q + pl * plane;
+        for (int y = 0; y < n; ++y) {          /* along x */
+            for (int x = 0; x < n; ++x) line[x] = u[(size_t)y * n + x];
+            for (int x = 0; x < n; ++x) {
+                double D = 0.0;
+                for (int m = -3; m <= 3; ++m) D += d[m + 3] * line[((x + m) % n + n) % n];
+                u[(size_t)y * n + x] = line[x] - sigma / 64.0 * D;
+            }
+        }
+        for (int x = 0; x < n; ++x) {          /* along y */
+            for (int y = 0; y < n; ++y) line[y] = u[(size_t)y * n + x];
+            for (int y = 0; y < n; ++y) {
+                double D = 0.0;
+                for (int m = -3; m <= 3; ++m) D += d[m + 3] * line[((y + m) % n + n) % n];
+                u[(size_t)y * n + x] = line[y] - sigma / 64.0 * D;
+            }
+        }
+    }
+    free(line);
+}
+
 void orc_ns2d_rk3(double *q, int nprob, int n, double h, double gamma, double mu,
                   double prandtl, double dt, int nsteps) {
     size_t sz = (size_t)4 * n * n;

@@ -56,6 +56,12 @@ void orc_burgers_rk3(double *u, int nprob, int n, double dx, double nu, double d
  * and differenced across the cell, so every flux telescopes.  SSP-RK3. */
 void orc_ns2d_rhs(const double *q, int n, double h, double gamma, double mu, double prandtl,
                   double *L);
+/* Centred sixth-order filter of the NS model (Secs. 5, 6; Bogey and Bailly):
+ * reading: the 7-point stencil with transfer function 1 - sigma sin^6(k h/2),
+ * along x then y on the 4 conserved planes of nprob periodic n x n grids.
+ * Parity: pinned (Fourier-mode damping in closed form, conservation of the
+ * totals, constants kept, grid-scale mode removed at sigma = 1). */
+void orc_ns2d_filter6(double *q, int nprob, int n, double sigma);
 void orc_ns2d_rk3(double *q, int nprob, int n, double h, double gamma, double mu,
                   double prandtl, double dt, int nsteps);
 

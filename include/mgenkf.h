@@ -193,6 +193,17 @@ mgenkf_status mgenkf_destroy(mgenkf_handle h);
  * alpha > 1 or not finite. */
 mgenkf_status mgenkf_set_regularisation(mgenkf_handle h, double alpha);
 
+/* Centred sixth-order filter of the NS-2D model (the paper's Euler and NS runs
+ * damp spurious oscillations with one, Secs. 5 and 6, citing Bogey and
+ * Bailly).  Reading: the 7-point stencil u_j -= sigma/64 (-u_{j-3} + 6u_{j-2}
+ * - 15u_{j-1} + 20u_j - 15u_{j+1} + 6u_{j+2} - u_{j+3}), transfer function
+ * 1 - sigma sin^6(k h/2), along x then y on the four conserved planes.  With
+ * sigma > 0 every model step of the members and the fine run (forecast) is the
+ * RK3 step followed by the filter; sigma = 0 (default) turns it off.  Not
+ * available for handles in a batch.  Errors: MGENKF_ERR_INVALID_ARG for a
+ * Burgers handle, sigma outside [0, 1], or grids under 7 points per side. */
+mgenkf_status mgenkf_set_filter(mgenkf_handle h, double sigma);
+
 /* Fine-to-coarse feedback (the paper's conclusion names projecting the fine
  * run's information onto the ensemble as the next step; reading: re-centring).
  * on != 0: every analysis first re-centres the forecast ensemble on the

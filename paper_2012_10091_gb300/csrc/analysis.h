@@ -55,6 +55,11 @@ void launch_fine_residual(int model, const T *x, const T *prev, int n, double le
                           double prandtl, double dt, double alpha, T *out, double *gamma_out, const int *status,
                           cudaStream_t s);
 
+// centred sixth-order filter (Secs. 5, 6) of nprob NS grids of n x n points,
+// 4 conserved planes each, in place; tmp holds one copy of them
+template <typename T>
+cudaError_t launch_ns2d_filter6(T *q, T *tmp, int n, int nprob, double sigma, cudaStream_t s);
+
 // fine-to-coarse feedback: members re-centred on x^C* (FP64 mean and shift)
 template <typename T>
 void launch_recentre(T *members, size_t nx, int ne, const T *xstar, const int *status, cudaStream_t s);

@@ -56,6 +56,7 @@ struct mgenkf_ctx {
     bool record_prev = false;    // forecasts record fine_prev (regularisation enabled)
     bool have_prev = false;      // fine_prev belongs to the current fine state
     bool recentre = false;       // re-centre the forecast ensemble on x^C* before each analysis
+    double filter_sigma = 0.0;   // NS: sixth-order filter after every model step (0: off)
     double *gemm_part = nullptr; // split-K partial sums of the gain GEMMs
     UpdateTcPlan tc;             // tensor-core member update (mixed precision)
     mgk_cnn_t cnn = nullptr;     // learned correction added by prolong_correct (not owned)
@@ -457,14 +458,33 @@ static mgenkf_status advance_impl(mgenkf_ctx *h, int nsteps) {
             e = burgers_forecast<double>((double *)h->members, h->nc, h->ne, (double *)h->fine, h->nf, 1,
                                          c.length, c.dt, c.nu, nsteps, h->stream);
     } else {
-        if (h->mixed)
-            e = ns2d_forecast_scratch<float>((float *)h->members, h->nc, h->ne, (float *)h->fine, h->nf, 1,
-                                             c.length, c.dt, c.nu, c.gamma, c.prandtl, nsteps,
-                                             (float *)h->ns_scratch, h->stream);
-        else
-            e = ns2d_forecast_scratch<double>((double *)h->members, h->nc, h->ne, (double *)h->fine, h->nf, 1,
-                                              c.length, c.dt, c.nu, c.gamma, c.prandtl, nsteps,
-                                              (double *)h->ns_scratch, h->stream);
+        // with the filter the model step is an RK3 step followed by the filter
+        // of every grid (the stage buffers are free in between)
+        const int chunk = h->filter_sigma > 0.0 ? 1 : nsteps;
+        e = cudaSuccess;
+        for (int done = 0; done < nsteps && e == cudaSuccess; done += chunk) {
+            if (h->mixed) {
+                e = ns2d_forecast_scratch<float>((float *)h->members, h->nc, h->ne, (float *)h->fine, h->nf, 1,
+                                                 c.length, c.dt, c.nu, c.gamma, c.prandtl, chunk,
+                                                 (float *)h->ns_scratch, h->stream);
+                if (e == cudaSuccess && h->filter_sigma > 0.0)
+                    e = launch_ns2d_filter6<float>((float *)h->members, (float *)h->ns_scratch, h->nc, h->ne,
+                                                   h->filter_sigma, h->stream);
+                if (e == cudaSuccess && h->filter_sigma > 0.0)
+                    e = launch_ns2d_filter6<float>((float *)h->fine, (float *)h->ns_scratch, h->nf, 1,
+                                                   h->filter_sigma, h->stream);
+            } else {
+                e = ns2d_forecast_scratch<double>((double *)h->members, h->nc, h->ne, (double *)h->fine, h->nf, 1,
+                                                  c.length, c.dt, c.nu, c.gamma, c.prandtl, chunk,
+                                                  (double *)h->ns_scratch, h->stream);
+                if (e == cudaSuccess && h->filter_sigma > 0.0)
+                    e = launch_ns2d_filter6<double>((double *)h->members, (double *)h->ns_scratch, h->nc, h->ne,
+                                                    h->filter_sigma, h->stream);
+                if (e == cudaSuccess && h->filter_sigma > 0.0)
+                    e = launch_ns2d_filter6<double>((double *)h->fine, (double *)h->ns_scratch, h->nf, 1,
+                                                    h->filter_sigma, h->stream);
+            }
+        }
     }
     if (e != cudaSuccess) H_FAIL(MGENKF_ERR_CUDA, std::string("forecast launch: ") + cudaGetErrorString(e));
     H_LAUNCHED();
@@ -573,6 +593,16 @@ extern "C" mgenkf_status mgenkf_set_recentre(mgenkf_handle h, int32_t on) {
     if (!h) return MGENKF_ERR_INVALID_ARG;
     h->err.clear();
     h->recentre = on != 0;
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_set_filter(mgenkf_handle h, double sigma) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    if (h->cfg.model != MGENKF_NS2D) H_FAIL(MGENKF_ERR_INVALID_ARG, "the sixth-order filter belongs to the NS-2D model");
+    if (!(sigma >= 0.0 && sigma <= 1.0)) H_FAIL(MGENKF_ERR_INVALID_ARG, "filter strength sigma must be in [0, 1]");
+    if (sigma > 0.0 && (h->nc < 7 || h->nf < 7)) H_FAIL(MGENKF_ERR_INVALID_ARG, "the 7-point filter needs >= 7 points per side");
+    h->filter_sigma = sigma;
     return MGENKF_OK;
 }
 
@@ -990,6 +1020,8 @@ extern "C" mgenkf_status mgenkf_batch_create(const mgenkf_handle *handles, int32
             return fail(MGENKF_ERR_INVALID_ARG, "batches hold NS-2D mixed-precision handles");
         if (h->record_prev)
             return fail(MGENKF_ERR_INVALID_ARG, "the final fine iteration is not available in batches");
+        if (h->filter_sigma > 0.0)
+            return fail(MGENKF_ERR_INVALID_ARG, "the sixth-order filter is not available in batches");
         if (i == 0) {
             b->gamma = h->cfg.gamma;
             b->mu = h->cfg.nu;

@@ -78,6 +78,7 @@ def _load():
         "mgenkf_set_prolong_cnn": [P, P],
         "mgenkf_set_regularisation": [P, f64],
         "mgenkf_set_recentre": [P, i32],
+        "mgenkf_set_filter": [P, f64],
         "mgenkf_batch_create": [P, i32, P, ctypes.POINTER(P)],
         "mgenkf_batch_cycle": [P, i32, P, P],
         "mgenkf_batch_forecast": [P, i32],
@@ -366,6 +367,11 @@ class MGEnKF:
         """Final fine iteration (Algorithm 4 step 6) with relaxation alpha; alpha < 0 turns
         the recording of the previous fine state off.  See include/mgenkf.h."""
         _check(lib.mgenkf_set_regularisation(self.h, float(alpha)), "mgenkf_set_regularisation", self.h)
+
+    def set_filter(self, sigma):
+        """Centred sixth-order filter of the NS model after every model step (sigma in
+        [0, 1]; 0 = off).  See include/mgenkf.h."""
+        _check(lib.mgenkf_set_filter(self.h, float(sigma)), "mgenkf_set_filter", self.h)
 
     def set_recentre(self, on=True):
         """Re-centre the forecast ensemble on x^C* before each analysis (fine-to-coarse feedback)."""

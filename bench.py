@@ -89,6 +89,9 @@ def parse():
     ap.add_argument("--tiles", default=None,
                     help="batched: JSON tile table to load (autotuned and written there if missing)")
     ap.add_argument("--problems", type=int, default=96, help="batched: number of problems")
+    ap.add_argument("--filter", type=float, default=None,
+                    help="ns2d: add an ablation of the centred sixth-order filter of the NS model "
+                         "(this strength after every model step): cycles/s and RMSE against no filter")
     ap.add_argument("--recentre", action="store_true",
                     help="burgers_large / ns2d: add an ablation of the fine-to-coarse feedback "
                          "(ensemble re-centred on the restricted fine forecast)")
@@ -456,6 +459,33 @@ def run_gpu(args, dist, w, inp):
             ga.close()
         feedback = {"cycles": nab, "rmse_last_half_off": rm[False], "rmse_last_half_on": rm[True]}
 
+    # sixth-order filter of the NS model: cost and RMSE over the last half with and without
+    filt = None
+    if args.filter is not None and w.V == 4:
+        nab = min(max(args.fp64_cycles, 10), truths.shape[0])
+        rm, cps = {}, {}
+        for sg in (0.0, args.filter):
+            ga = M.MGEnKF.from_workload(w, stream=sp)
+            ga.set_state(inp["fine0"], inp["members0"])
+            ga.set_filter(sg)
+            ra = torch.zeros((nab, w.V), dtype=torch.float64, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                M.mgenkf_cycle(ga.h, w.steps_per_cycle, yos[0], truths[0], ra[0])   # warm-up
+                e0.record(stream)
+                for k in range(1, nab):
+                    M.mgenkf_cycle(ga.h, w.steps_per_cycle, yos[k], truths[k], ra[k])
+                e1.record(stream)
+            torch.cuda.synchronize()
+            assert ga.sync() == 0
+            cps[sg] = (nab - 1) / (e0.elapsed_time(e1) / 1e3)
+            rm[sg] = ra[nab // 2:].mean(dim=0).cpu().numpy().tolist()
+            ga.close()
+        filt = {"sigma": args.filter, "cycles": nab, "cycles_per_s_off": cps[0.0],
+                "cycles_per_s_on": cps[args.filter], "rmse_last_half_off": rm[0.0],
+                "rmse_last_half_on": rm[args.filter],
+                "note": "mgenkf_cycle on device buffers, CUDA events; the truth run is unfiltered"}
+
     # e2e: the same cycle through the C ABI with host buffers (pinned), copies inside
     e2e = None
     if not args.no_e2e:
@@ -524,6 +554,7 @@ def run_gpu(args, dist, w, inp):
             "rmse_final": float(rmse_mixed[-1]),
             "regularisation": regularisation,
             "recentre_ablation": feedback,
+            "filter_ablation": filt,
             "roofline": {"bound": "alu", "kernel": spec["kernel"],
                          "achieved": achieved, "peak": peak, "unit": "TOP/s",
                          "frac": achieved / peak, "traffic": traffic,

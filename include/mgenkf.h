@@ -201,7 +201,7 @@ mgenkf_status mgenkf_set_regularisation(mgenkf_handle h, double alpha);
  * sigma > 0 every model step of the members and the fine run (forecast) is the
  * RK3 step followed by the filter; sigma = 0 (default) turns it off.  Not
  * available for handles in a batch.  Errors: MGENKF_ERR_INVALID_ARG for a
- * Burgers handle, sigma outside [0, 1], or grids under 7 points per side. */
+ * Burgers handle or sigma outside [0, 1]. */
 mgenkf_status mgenkf_set_filter(mgenkf_handle h, double sigma);
 
 /* Fine-to-coarse feedback (the paper's conclusion names projecting the fine

@@ -601,7 +601,7 @@ extern "C" mgenkf_status mgenkf_set_filter(mgenkf_handle h, double sigma) {
     h->err.clear();
     if (h->cfg.model != MGENKF_NS2D) H_FAIL(MGENKF_ERR_INVALID_ARG, "the sixth-order filter belongs to the NS-2D model");
     if (!(sigma >= 0.0 && sigma <= 1.0)) H_FAIL(MGENKF_ERR_INVALID_ARG, "filter strength sigma must be in [0, 1]");
-    if (sigma > 0.0 && (h->nc < 7 || h->nf < 7)) H_FAIL(MGENKF_ERR_INVALID_ARG, "the 7-point filter needs >= 7 points per side");
+    if (sigma > 0.0 && (h->nc < 8 || h->nf < 8)) H_FAIL(MGENKF_ERR_INVALID_ARG, "the 7-point filter needs >= 8 points per side");
     h->filter_sigma = sigma;
     return MGENKF_OK;
 }

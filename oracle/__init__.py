@@ -200,6 +200,16 @@ def ns2d_gamma(q, qprev, h, gamma, mu, prandtl, dt) -> np.ndarray:
     return out
 
 
+def gamma_normalised(gamma, x, xprev, dt, V) -> np.ndarray:
+    """Gamma* = Gamma / C per variable with C = max over the grid of
+    |(x - x_prev)/dt| (Sec. 6, the normalisation of the conservativity maps;
+    reading: the maximum is over the grid points at the analysis time)."""
+    g = _f64(gamma).reshape(V, -1)
+    rate = (_f64(x) - _f64(xprev)).reshape(V, -1) / dt
+    c = np.abs(rate).max(axis=1, keepdims=True)
+    return (g / np.where(c > 0, c, 1.0)).reshape(-1)
+
+
 def ns2d_rk3(q, h, gamma, mu, prandtl, dt, nsteps) -> np.ndarray:
     """Advance (nprob x) 4 x n x n conserved states by nsteps SSP-RK3 steps."""
     x = _f64(q).copy()

@@ -60,6 +60,10 @@ void launch_fine_residual(int model, const T *x, const T *prev, int n, double le
 template <typename T>
 cudaError_t launch_ns2d_filter6(T *q, T *tmp, int n, int nprob, double sigma, cudaStream_t s);
 
+// out = (x - prev) / dt in FP64 (count values)
+template <typename T>
+void launch_state_rate(const T *x, const T *prev, size_t count, double dt, double *out, cudaStream_t s);
+
 // fine-to-coarse feedback: members re-centred on x^C* (FP64 mean and shift)
 template <typename T>
 void launch_recentre(T *members, size_t nx, int ne, const T *xstar, const int *status, cudaStream_t s);

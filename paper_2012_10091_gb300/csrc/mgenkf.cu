@@ -712,6 +712,22 @@ extern "C" mgenkf_status mgenkf_get_field(mgenkf_handle h, int32_t field, double
             H_LAUNCHED();
             return copy_out_f64(h, out, h->scratch, h->nxf);
         }
+        case MGENKF_FIELD_RATE: {
+            if (count < h->nxf) H_FAIL(MGENKF_ERR_INVALID_ARG, "count too small");
+            if (!h->have_prev)
+                H_FAIL(MGENKF_ERR_INVALID_ARG, "no recorded previous fine state: enable mgenkf_set_regularisation "
+                                               "and run a forecast first");
+            mgenkf_status st = ensure_scratch(h, h->nxf);
+            if (st) return st;
+            if (h->mixed)
+                launch_state_rate<float>((const float *)h->fine, (const float *)h->fine_prev, h->nxf, h->cfg.dt,
+                                         h->scratch, h->stream);
+            else
+                launch_state_rate<double>((const double *)h->fine, (const double *)h->fine_prev, h->nxf, h->cfg.dt,
+                                          h->scratch, h->stream);
+            H_LAUNCHED();
+            return copy_out_f64(h, out, h->scratch, h->nxf);
+        }
         default:
             H_FAIL(MGENKF_ERR_INVALID_ARG, "unknown field");
     }

@@ -145,6 +145,24 @@ __global__ void __launch_bounds__(256) k_ns2d_residual(const T *__restrict__ q, 
     }
 }
 
+// (x - x_prev) / dt in FP64: the time-derivative term of Eq. Conservativity_rhov,
+// whose largest magnitude over the grid normalises Gamma (the paper's Gamma*)
+template <typename T>
+__global__ void k_state_rate(const T *__restrict__ x, const T *__restrict__ prev, size_t count, double inv_dt,
+                             double *__restrict__ out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = ((double)x[i] - (double)prev[i]) * inv_dt;
+}
+
+template <typename T>
+void launch_state_rate(const T *x, const T *prev, size_t count, double dt, double *out, cudaStream_t s) {
+    count_launches(1);
+    k_state_rate<T><<<ceil_div((long long)count, 256) < 4096 ? ceil_div((long long)count, 256) : 4096, 256, 0, s>>>(
+        x, prev, count, 1.0 / dt, out);
+}
+template void launch_state_rate<float>(const float *, const float *, size_t, double, double *, cudaStream_t);
+template void launch_state_rate<double>(const double *, const double *, size_t, double, double *, cudaStream_t);
+
 template <typename T>
 void launch_fine_residual(int model, const T *x, const T *prev, int n, double length, double nu, double gamma,
                           double prandtl, double dt, double alpha, T *out, double *gamma_out, const int *status,

@@ -25,6 +25,7 @@ MGENKF_GAIN_ENSEMBLE, MGENKF_GAIN_DIRECT = 0, 1
 MGENKF_PROLONG_LAGRANGE4 = 0
 MGENKF_FIELD_XSTAR, MGENKF_FIELD_YF, MGENKF_FIELD_T, MGENKF_FIELD_DC, MGENKF_FIELD_EPS = 0, 1, 2, 3, 4
 MGENKF_FIELD_GAMMA = 5
+MGENKF_FIELD_RATE = 6
 EPS_TAG = 0x45505300
 
 
@@ -382,6 +383,20 @@ class MGEnKF:
         out = np.empty(self.nxf)
         mgenkf_get_field(self.h, MGENKF_FIELD_GAMMA, out, self.nxf)
         return out
+
+    def state_rate(self):
+        """(x - x_prev)/dt of the fine run, FP64 (the time-derivative term of Gamma)."""
+        out = np.empty(self.nxf)
+        mgenkf_get_field(self.h, MGENKF_FIELD_RATE, out, self.nxf)
+        return out
+
+    def gamma_normalised(self):
+        """Gamma* = Gamma / C per variable, C = max over the grid of |(x - x_prev)/dt|
+        (the normalisation of the paper's conservativity maps)."""
+        g = self.gamma_residual().reshape(self.V, -1)
+        r = self.state_rate().reshape(self.V, -1)
+        c = np.abs(r).max(axis=1, keepdims=True)
+        return (g / np.where(c > 0, c, 1.0)).reshape(-1)
 
     def set_prolong_cnn(self, cnn):
         """Attach a CNN (or None) whose residual prolong_correct adds to Pi_F(dC)."""

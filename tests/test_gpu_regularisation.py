@@ -130,3 +130,21 @@ def test_batches_refuse_regularised_handles(M):
         M.Batch(runs)
     for g in runs:
         g.close()
+
+
+@pytest.mark.parametrize("model", ["burgers", "ns2d"])
+def test_normalised_gamma_matches_oracle(M, model):
+    """Gamma* = Gamma / max |(x - x_prev)/dt| (the paper's normalisation of its
+    conservativity maps) and the rate field itself, FP64, against the oracle."""
+    if model == "burgers":
+        w = W.burgers_small()
+    else:
+        w = W.ns2d_shear(nf=64, ratio=4, ne=12, n_probes=20, cycles=2, precision="fp64", delta=0.08)
+    g, mg = _runs(M, w, 2, 0.0, "fp64")
+    rate = g.state_rate()
+    assert rel_err(rate, (mg.fine - mg.fine_prev) / w.dt) < 1e-7   # difference quotient over one step
+    got = g.gamma_normalised().reshape(w.V, -1)
+    ref = O.gamma_normalised(mg.gamma_residual(), mg.fine, mg.fine_prev, w.dt, w.V).reshape(w.V, -1)
+    for v in range(w.V):
+        assert rel_err(got[v], ref[v]) < 1e-5, v
+    g.close()

@@ -28,6 +28,8 @@ _LIB = None
 
 # tag of the observation-perturbation stream in the Philox key (ASCII "EPS\0")
 EPS_TAG = 0x45505300
+# tag of the parameter random walk of the Dual EnKF (ASCII "THTA")
+THETA_TAG = 0x54485441
 
 
 def build(force: bool = False) -> str:
@@ -78,6 +80,7 @@ def lib():
             L.orc_rmse.argtypes = [P, P, i32, i64, P]
             L.orc_set_threads.argtypes = [i32]
             L.orc_ns2d_filter6.argtypes = [P, i32, i32, f64]
+            L.orc_burgers_inlet_rk3.argtypes = [P, i32, i32, f64, f64, f64, i32, f64, P, f64, f64]
             _LIB = L
     return _LIB
 
@@ -135,6 +138,17 @@ def burgers_rk3(u, dx, nu, dt, nsteps, flux_kind=0, c=0.0) -> np.ndarray:
     shape = x.shape
     x2 = x.reshape(-1, shape[-1])
     lib().orc_burgers_rk3(_p(x2), x2.shape[0], x2.shape[1], dx, nu, dt, nsteps, flux_kind, c)
+    return x2.reshape(shape)
+
+
+def burgers_inlet_rk3(u, dx, nu, dt, nsteps, t0, theta, u0=1.0, omega=2 * np.pi) -> np.ndarray:
+    """Advance every row of u (nprob x n, or n) with its inlet parameters
+    theta (nprob x 2: amplitude, phase) from time t0 (see oracle.h)."""
+    x = _f64(u).copy()
+    shape = x.shape
+    x2 = x.reshape(-1, shape[-1])
+    th = _f64(theta).reshape(x2.shape[0], 2)
+    lib().orc_burgers_inlet_rk3(_p(x2), x2.shape[0], x2.shape[1], dx, nu, dt, nsteps, t0, _p(th), u0, omega)
     return x2.reshape(shape)
 
 
@@ -490,3 +504,123 @@ def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         vh = v / (1 - b2**t)
         params[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
     return params
+
+
+# --------------------------------------------------------------------------
+# Dual EnKF parameter estimation (Algorithm 3 with its parameter rows, inside
+# Algorithm 4) on the Burgers inlet model of Sec. 4
+# --------------------------------------------------------------------------
+def open_prolong_rows(nc: int, r: int):
+    """Pi_F on an open 1-D grid (coarse node J at fine node r J, no wrap): for
+    every fine node k the first of its 4 coarse nodes j0 = clamp(k // r - 1,
+    0, nc - 4) and the cubic Lagrange weights through j0 .. j0 + 3 at k / r
+    (one-sided near the ends; beyond the last coarse node it extrapolates)."""
+    j0 = np.empty(nc * r, dtype=np.int64)
+    w = np.empty((nc * r, 4))
+    for k in range(nc * r):
+        j0[k] = min(max(k // r - 1, 0), nc - 4)
+        w[k] = lagrange_weights(np.arange(j0[k], j0[k] + 4, dtype=np.float64), k / r)
+    return j0, w
+
+
+def open_prolong(dC, nc: int, r: int) -> np.ndarray:
+    j0, w = open_prolong_rows(nc, r)
+    idx = j0[:, None] + np.arange(4)[None, :]
+    return (w * _f64(dC)[idx]).sum(axis=1)
+
+
+def open_obs_rows(obs_idx, nc: int, r: int):
+    """H^C rows of fine-node observations: the open Pi_F row at each node."""
+    j0, w = open_prolong_rows(nc, r)
+    k = np.asarray(obs_idx, dtype=np.int64)
+    return j0[k], w[k]
+
+
+def _anomalies(A) -> np.ndarray:
+    """Normalised anomalies (Eq. Ensemble_Anomaly) of the ensemble rows of A (ne x p), p x ne."""
+    A = _f64(A)
+    return (A - A.mean(axis=0)).T / np.sqrt(A.shape[0] - 1)
+
+
+class DualMGEnKF:
+    """FP64 oracle of the multigrid Dual EnKF on the Burgers inlet model.
+
+    One cycle follows Algorithm 4 with Algorithm 3 on the coarse grid:
+      step 2 (Alg. 4): fine forecast with the analysed parameter mean;
+      step 2 (Alg. 3): parameter forecast theta^f = theta^a + tau (random walk,
+        tau ~ N(0, q I)) and member forecast with theta^f;
+      steps 3-5: observation ensemble y^o + eps^(i), parameter gain
+        K^theta = Theta Y^T (Y Y^T + R)^-1, theta^a = theta^f + K^theta (y^o,(i) - y^f,(i));
+      steps 6-8: member forecast again from the previous analysis with theta^a,
+        state gain K^x = X Y^T (Y Y^T + R)^-1 from it, member update;
+      steps 4-5 (Alg. 4): x^C' - x^C* = K^x (y^o - H^C x^C*), fine correction Pi_F.
+    R is the exact sigma^2 I (the reading of the build); projections are the
+    open-grid 4-point Lagrange interpolants (one-sided at the ends)."""
+
+    def __init__(self, nf, ratio, length, dt, nu, fine, members, theta, theta_fine, obs_idx, sigma,
+                 seed, theta_q, u0=1.0, omega=2 * np.pi, t0=0.0):
+        self.nf, self.r = nf, ratio
+        self.nc = nf // ratio
+        self.length, self.dt, self.nu = length, dt, nu
+        self.u0, self.omega = u0, omega
+        self.fine = _f64(fine).copy()
+        self.members = _f64(members).copy()
+        self.theta = _f64(theta).reshape(-1, 2).copy()
+        self.theta_fine = _f64(theta_fine).reshape(2).copy()
+        self.obs_idx = np.asarray(obs_idx, dtype=np.int64)
+        self.sigma, self.seed, self.theta_q = sigma, seed, theta_q
+        self.t = t0
+        self.cycle = 0
+        self.hj0, self.hw = open_obs_rows(self.obs_idx, self.nc, self.r)
+
+    def observe(self, xc) -> np.ndarray:
+        """H^C of coarse states (rows of xc), ne x ny (or ny)."""
+        xc = _f64(xc)
+        idx = self.hj0[:, None] + np.arange(4)[None, :]
+        return (self.hw * xc[..., idx]).sum(axis=-1)
+
+    def _gain(self, A, Yf) -> np.ndarray:
+        Y = _anomalies(Yf)                       # ny x ne
+        C = Y @ Y.T + self.sigma ** 2 * np.eye(Y.shape[0])
+        return np.linalg.solve(C, (A @ Y.T).T).T  # A Y^T C^-1
+
+    def free_run(self, nsteps):
+        """Forecast without analysis (spin-up): fine with its parameters, members with theirs."""
+        dxf, dxc = self.length / self.nf, self.length / self.nc
+        self.fine = burgers_inlet_rk3(self.fine, dxf, self.nu, self.dt, nsteps, self.t, self.theta_fine,
+                                      self.u0, self.omega)
+        self.members = burgers_inlet_rk3(self.members, dxc, self.nu, self.dt, nsteps, self.t, self.theta,
+                                         self.u0, self.omega)
+        self.t += nsteps * self.dt
+
+    def cycle_step(self, nsteps, yo, eps=None, tau=None):
+        ne = self.members.shape[0]
+        ny = self.obs_idx.size
+        dxf, dxc = self.length / self.nf, self.length / self.nc
+        yo = _f64(yo)
+        fine_f = burgers_inlet_rk3(self.fine, dxf, self.nu, self.dt, nsteps, self.t, self.theta_fine,
+                                   self.u0, self.omega)
+        if tau is None:
+            tau = np.sqrt(self.theta_q) * normals(self.seed, THETA_TAG, self.cycle, 2 * ne).reshape(ne, 2)
+        theta_f = self.theta + tau
+        xf = burgers_inlet_rk3(self.members, dxc, self.nu, self.dt, nsteps, self.t, theta_f,
+                               self.u0, self.omega)
+        if eps is None:
+            eps = obs_perturbations(self.seed, self.cycle, ne, ny, self.sigma)
+        Yf = self.observe(xf)
+        Kt = self._gain(_anomalies(theta_f), Yf)               # 2 x ny
+        theta_a = theta_f + (yo[None, :] + eps - Yf) @ Kt.T
+        xf2 = burgers_inlet_rk3(self.members, dxc, self.nu, self.dt, nsteps, self.t, theta_a,
+                                self.u0, self.omega)
+        Yf2 = self.observe(xf2)
+        Kx = self._gain(_anomalies(xf2), Yf2)                  # nc x ny
+        self.members = xf2 + (yo[None, :] + eps - Yf2) @ Kx.T
+        xs = fine_f[::self.r][:self.nc]
+        dC = Kx @ (yo - self.observe(xs))
+        self.fine = fine_f + open_prolong(dC, self.nc, self.r)
+        self.theta = theta_a
+        self.theta_fine = theta_a.mean(axis=0)
+        self.t += nsteps * self.dt
+        self.cycle += 1
+        self.xstar, self.dC = xs, dC
+        return theta_a

@@ -111,6 +111,51 @@ void orc_burgers_rhs(const double *u, int n, double dx, double nu, int flux_kind
     }
 }
 
+/* Burgers with an inlet (Sec. 4, Eq. burgers with Eq. inlet-1D-Burgers): nodes
+ * x_j = j dx, j = 0..n-1; node 0 holds the Dirichlet inlet value
+ * u(0, t) = u0 (1 + theta1 sin(omega t + theta2)), the outlet node n-1 is
+ * extrapolated linearly from its two neighbours, the interior nodes follow the
+ * flux-form central scheme of orc_burgers_rhs (without wrap-around).  SSP-RK3
+ * in Shu-Osher form with the inlet set at each stage's time (t + dt, t + dt/2,
+ * t + dt).  theta: nprob x 2 (theta1, theta2), one pair per problem. */
+static void inlet_bc(double *u, int n, double t, double u0, double omega, const double *th) {
+    u[0] = u0 * (1.0 + th[0] * sin(omega * t + th[1]));
+    u[n - 1] = 2.0 * u[n - 2] - u[n - 3];
+}
+
+static void inlet_rhs(const double *u, int n, double dx, double nu, double *L) {
+    for (int j = 1; j < n - 1; ++j) {
+        const double fp = 0.5 * u[j + 1] * u[j + 1], fm = 0.5 * u[j - 1] * u[j - 1];
+        L[j] = -(fp - fm) / (2.0 * dx) + nu * (u[j + 1] - 2.0 * u[j] + u[j - 1]) / (dx * dx);
+    }
+    L[0] = L[n - 1] = 0.0;
+}
+
+void orc_burgers_inlet_rk3(double *u, int nprob, int n, double dx, double nu, double dt, int nsteps,
+                           double t0, const double *theta, double u0, double omega) {
+#pragma omp parallel for schedule(static)
+    for (int p = 0; p < nprob; ++p) {
+        double *x = u + (size_t)p * n;
+        const double *th = theta + 2 * (size_t)p;
+        double *u1 = malloc(sizeof(double) * n), *u2 = malloc(sizeof(double) * n), *L = malloc(sizeof(double) * n);
+        for (int s = 0; s < nsteps; ++s) {
+            const double t = t0 + s * dt;
+            inlet_rhs(x, n, dx, nu, L);
+            for (int j = 0; j < n; ++j) u1[j] = x[j] + dt * L[j];
+            inlet_bc(u1, n, t + dt, u0, omega, th);
+            inlet_rhs(u1, n, dx, nu, L);
+            for (int j = 0; j < n; ++j) u2[j] = 0.75 * x[j] + 0.25 * (u1[j] + dt * L[j]);
+            inlet_bc(u2, n, t + 0.5 * dt, u0, omega, th);
+            inlet_rhs(u2, n, dx, nu, L);
+            for (int j = 0; j < n; ++j) x[j] = x[j] / 3.0 + 2.0 / 3.0 * (u2[j] + dt * L[j]);
+            inlet_bc(x, n, t + dt, u0, omega, th);
+        }
+        free(u1);
+        free(u2);
+        free(L);
+    }
+}
+
 /* SSP-RK3 in Shu-Osher form:
  *   u1 = u + dt L(u);  u2 = 3/4 u + 1/4 (u1 + dt L(u1));
  *   u_new = 1/3 u + 2/3 (u2 + dt L(u2)). */

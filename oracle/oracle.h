@@ -56,6 +56,15 @@ void orc_burgers_rk3(double *u, int nprob, int n, double dx, double nu, double d
  * and differenced across the cell, so every flux telescopes.  SSP-RK3. */
 void orc_ns2d_rhs(const double *q, int n, double h, double gamma, double mu, double prandtl,
                   double *L);
+/* Burgers with a time-varying inlet (Sec. 4, Eqs. burgers and
+ * inlet-1D-Burgers): node 0 = u0 (1 + theta1 sin(omega t + theta2)), outlet
+ * extrapolated linearly, flux-form central interior, SSP-RK3 with the inlet at
+ * each stage time; theta is nprob x 2.  Parity: pinned (a uniform state with
+ * theta1 = 0 stays exact; the small-amplitude inlet signal converges at second
+ * order to the closed-form time-harmonic solution of the linearised equation). */
+void orc_burgers_inlet_rk3(double *u, int nprob, int n, double dx, double nu, double dt, int nsteps,
+                           double t0, const double *theta, double u0, double omega);
+
 /* Centred sixth-order filter of the NS model (Secs. 5, 6; Bogey and Bailly):
  * reading: the 7-point stencil with transfer function 1 - sigma sin^6(k h/2),
  * along x then y on the 4 conserved planes of nprob periodic n x n grids.

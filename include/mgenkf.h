@@ -217,6 +217,46 @@ mgenkf_status mgenkf_set_filter(mgenkf_handle h, double sigma);
  * If the analysis then fails (status), the members stay re-centred. */
 mgenkf_status mgenkf_set_recentre(mgenkf_handle h, int32_t on);
 
+/* ---- Dual EnKF parameter estimation on the Burgers inlet model -----------
+ * Sec. 4 (Eq. burgers with the inlet condition Eq. inlet-1D-Burgers:
+ * u(0, t) = u0 (1 + theta1 sin(omega t + theta2)), outlet extrapolated) and
+ * Algorithm 3 with its parameter rows, run inside Algorithm 4, FP64.  Model:
+ * nodes x_j = j length / n_fine, flux-form central scheme, SSP-RK3 with the
+ * inlet set at each stage time.  One cycle: fine forecast with the analysed
+ * parameter mean; parameter random walk theta^f = theta^a + tau, tau ~ N(0,
+ * theta_q I) (Philox4x64-10, key (seed, "THTA"), counter (cycle, n/4, 0, 0));
+ * member forecast with theta^f; parameter update theta^a = theta^f + Theta T
+ * with T = (I + Y^T R^-1 Y)^-1 Y^T R^-1 D (R = obs_sigma^2 I, perturbations as
+ * in mgenkf_analyse); member forecast again from the previous analysis with
+ * theta^a and state update with the same perturbations; fine correction with
+ * the open-grid 4-point Lagrange Pi_F (one-sided at the ends).  H^C is the
+ * Pi_F row at each observed fine node.  Limits: n_fine <= 1024 (one CTA per
+ * grid), n_fine / ratio >= 8, ratio in [1, 16], 2 <= n_members <= 256. */
+typedef struct mgenkf_dual *mgenkf_dual_t;
+typedef struct {
+    int32_t n_fine, ratio, n_members, n_obs;
+    double length, dt, nu, u0, omega, obs_sigma, theta_q;
+    uint64_t seed;
+} mgenkf_dual_config;
+/* obs_index: n_obs fine-node indices (host); cuda_stream: the stream of every
+ * call (NULL = legacy stream).  Errors: MGENKF_ERR_INVALID_ARG, MGENKF_ERR_OOM. */
+mgenkf_status mgenkf_dual_create(const mgenkf_dual_config *cfg, const int32_t *obs_index, void *cuda_stream,
+                                 mgenkf_dual_t *out);
+/* fine (n_fine), members (n_members x n_fine/ratio), theta (n_members x 2:
+ * amplitude, phase), theta_fine (2): host or device; t0: the model time. */
+mgenkf_status mgenkf_dual_set_state(mgenkf_dual_t d, const double *fine, const double *members,
+                                    const double *theta, const double *theta_fine, double t0);
+/* nsteps model steps without analysis (fine with theta_fine, members with theirs) */
+mgenkf_status mgenkf_dual_free_run(mgenkf_dual_t d, int32_t nsteps);
+/* one forecast / analysis cycle of nsteps model steps; y_obs: n_obs values (host or device) */
+mgenkf_status mgenkf_dual_cycle(mgenkf_dual_t d, int32_t nsteps, const double *y_obs);
+/* copies out (host or device; NULL skips) after waiting for the stream; returns
+ * a device-side failure (non-positive pivot) recorded since creation */
+mgenkf_status mgenkf_dual_get_state(mgenkf_dual_t d, double *fine, double *members, double *theta,
+                                    double *theta_fine);
+const char *mgenkf_dual_last_error(mgenkf_dual_t d);
+mgenkf_status mgenkf_dual_destroy(mgenkf_dual_t d);
+
 /* ---- batches of independent problems -------------------------------------
  * Many independent NS-2D MGEnKF problems (uneven grid sizes, ensemble sizes
  * and observation counts) advanced together: the forecast of every problem's

@@ -44,6 +44,13 @@ class mgenkf_config(ctypes.Structure):
                 ("obs_sigma", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
+class mgenkf_dual_config(ctypes.Structure):
+    _fields_ = [("n_fine", ctypes.c_int32), ("ratio", ctypes.c_int32), ("n_members", ctypes.c_int32),
+                ("n_obs", ctypes.c_int32), ("length", ctypes.c_double), ("dt", ctypes.c_double),
+                ("nu", ctypes.c_double), ("u0", ctypes.c_double), ("omega", ctypes.c_double),
+                ("obs_sigma", ctypes.c_double), ("theta_q", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with "
@@ -88,6 +95,12 @@ def _load():
         "mgenkf_batch_tiles": [P, P, P, i32, P],
         "mgenkf_batch_set_tiles": [P, P, P, i32],
         "mgenkf_batch_destroy": [P],
+        "mgenkf_dual_create": [ctypes.POINTER(mgenkf_dual_config), P, P, ctypes.POINTER(P)],
+        "mgenkf_dual_set_state": [P, P, P, P, P, f64],
+        "mgenkf_dual_free_run": [P, i32],
+        "mgenkf_dual_cycle": [P, i32, P],
+        "mgenkf_dual_get_state": [P, P, P, P, P],
+        "mgenkf_dual_destroy": [P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -95,6 +108,8 @@ def _load():
         fn.restype = ctypes.c_int
     L.mgenkf_last_error.argtypes = [P]
     L.mgenkf_last_error.restype = ctypes.c_char_p
+    L.mgenkf_dual_last_error.argtypes = [P]
+    L.mgenkf_dual_last_error.restype = ctypes.c_char_p
     L.mgenkf_batch_last_error.argtypes = [P]
     L.mgenkf_batch_last_error.restype = ctypes.c_char_p
     L.mgk_kernel_launches.argtypes = []
@@ -496,3 +511,49 @@ class Batch:
         import json
         with open(path) as f:
             self.set_tiles({int(k): int(v) for k, v in json.load(f)["tiles"].items()})
+
+
+class DualMGEnKF:
+    """Dual EnKF parameter estimation on the Burgers inlet model (the
+    mgenkf_dual_* entry points; see include/mgenkf.h).  FP64."""
+
+    def __init__(self, n_fine, ratio, n_members, obs_index, length, dt, nu, obs_sigma, theta_q, seed,
+                 u0=1.0, omega=2 * np.pi, stream=None):
+        oi = np.ascontiguousarray(obs_index, dtype=np.int32)
+        cfg = mgenkf_dual_config(n_fine, ratio, n_members, oi.size, length, dt, nu, u0, omega, obs_sigma,
+                                 theta_q, seed)
+        h = ctypes.c_void_p()
+        st = lib.mgenkf_dual_create(ctypes.byref(cfg), oi.ctypes.data, stream, ctypes.byref(h))
+        _check(st, "mgenkf_dual_create")
+        self.h = h.value
+        self.nf, self.nc, self.ne = n_fine, n_fine // ratio, n_members
+
+    def _chk(self, st, where):
+        if st != MGENKF_OK:
+            raise MGEnKFError(st, where, (lib.mgenkf_dual_last_error(self.h) or b"").decode())
+
+    def set_state(self, fine, members, theta, theta_fine, t0):
+        f, m, th, tf = (_as_f64(a) for a in (fine, members, theta, theta_fine))
+        self._chk(lib.mgenkf_dual_set_state(self.h, _ptr(f), _ptr(m), _ptr(th), _ptr(tf), float(t0)),
+                  "mgenkf_dual_set_state")
+
+    def free_run(self, nsteps):
+        self._chk(lib.mgenkf_dual_free_run(self.h, int(nsteps)), "mgenkf_dual_free_run")
+
+    def cycle(self, nsteps, y_obs):
+        y = _as_f64(y_obs)
+        self._chk(lib.mgenkf_dual_cycle(self.h, int(nsteps), _ptr(y)), "mgenkf_dual_cycle")
+
+    def get_state(self):
+        fine = np.empty(self.nf)
+        mem = np.empty((self.ne, self.nc))
+        th = np.empty((self.ne, 2))
+        tf = np.empty(2)
+        self._chk(lib.mgenkf_dual_get_state(self.h, _ptr(fine), _ptr(mem), _ptr(th), _ptr(tf)),
+                  "mgenkf_dual_get_state")
+        return fine, mem, th, tf
+
+    def close(self):
+        if self.h:
+            lib.mgenkf_dual_destroy(self.h)
+            self.h = None

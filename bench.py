@@ -62,6 +62,8 @@ WORKLOADS = {
     # by ncu on the 32x16-tile class of the 8-problem batch (10.6 M points of
     # 64^2 and 192^2 grids, working set above L2) and scaled to the full batch
     # by its point count; None once the kernel changes
+    # Dual EnKF parameter estimation on the Burgers inlet model (latency-bound: small grids)
+    "dual": dict(kernel="k_burgers_inlet"),
     "batched": dict(flops=600, bytes=128, kernel="ns2d_stage_x2<*,*,*,TableTiles>",
                     launches_per_step=3, traffic=None, traffic_per_point_step=151.0, truth="fp32"),
 }
@@ -82,7 +84,8 @@ def parse():
                     help="burgers_large (default: fine 16384 / coarse 4096, Ne=128), ns2d "
                          "(fine 512^2 / coarse 128^2, Ne=64, 2048 observations), ns2d_cnn "
                          "(fine 1024^2 / coarse 256^2, Ne=64, learned prolongation correction) or "
-                         "batched (96 independent NS-2D problems of uneven sizes, one graph launch per cycle)")
+                         "batched (96 independent NS-2D problems of uneven sizes, one graph launch per cycle) or "
+                         "dual (inlet-parameter estimation on the Burgers inlet model, 800 nodes, ratio 4)")
     ap.add_argument("--cnn-pairs", type=int, default=400,
                     help="training pairs generated for ns2d_cnn (cycles of lockstep runs)")
     ap.add_argument("--cnn-epochs", type=int, default=10)
@@ -583,7 +586,134 @@ METRIC = {
     "ns2d_cnn": "MGEnKF analysis cycles/s with learned prolongation (2-D NS 1024^2/256^2, Ne=64)",
     "batched": "MGEnKF problem-cycles/s (96 independent 2-D NS problems, coarse 64^2..192^2, fine x4, "
                "Ne 16..128, 256..2048 obs, one graph launch per cycle)",
+    "dual": "Dual MGEnKF analysis cycles/s with inlet-parameter estimation (Burgers inlet, 800 fine nodes, "
+            "ratio 4, Ne=100, 80 sensors)",
 }
+
+
+# --------------------------------------------------------------------------
+# Dual EnKF parameter estimation on the Burgers inlet model (Sec. 4 setting)
+# --------------------------------------------------------------------------
+DUAL = dict(nf=800, length=10.0, dt=2e-4, nu=1 / 200, ne=100, sigma=0.05, q=1e-6, nsteps=30, spin=50000,
+            theta_true=(0.2, 0.0), theta_fine0=(0.0, 0.3))
+
+
+def dual_inputs(seed):
+    rng = np.random.default_rng(seed)
+    ne = DUAL["ne"]
+    theta0 = np.stack([rng.normal(0.0, 0.05, ne), rng.normal(0.3, 0.05, ne)], axis=1)
+    return rng, theta0, np.arange(1, 81)
+
+
+def dual_truth_obs(M, ncyc, rng, obs):
+    """Observations of the truth run (theta = (0.2, 0), the fine model) for
+    ncyc cycles after the spin-up, each with N(0, sigma^2) noise: a one-member
+    dual object's fine run, advanced freely."""
+    d = DUAL
+    tr = M.DualMGEnKF(d["nf"], 1, 2, obs, d["length"], d["dt"], d["nu"], d["sigma"], 0.0, 1)
+    tr.set_state(np.ones(d["nf"]), np.ones((2, d["nf"])), np.zeros((2, 2)), d["theta_true"], 0.0)
+    tr.free_run(d["spin"])
+    ys = np.empty((ncyc, obs.size))
+    for k in range(ncyc):
+        tr.free_run(d["nsteps"])
+        ys[k] = tr.get_state()[0][obs] + d["sigma"] * rng.standard_normal(obs.size)
+    tr.close()
+    return ys
+
+
+def run_gpu_dual(args, dist):
+    import torch
+    from paper_2012_10091_gb300 import mgenkf as M
+    d = DUAL
+    torch.cuda.set_device(dist.local)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    ncyc = args.warmup + args.steps
+    nest = 500                                   # cycles of the parameter-estimation runs (3 t_c)
+    rng, theta0, obs = dual_inputs(dist.rank)
+    ys = dual_truth_obs(M, max(ncyc, nest), rng, obs)
+    yd = torch.tensor(ys, dtype=torch.float64, device="cuda")
+
+    def fresh(r):
+        g = M.DualMGEnKF(d["nf"], r, d["ne"], obs, d["length"], d["dt"], d["nu"], d["sigma"], d["q"], 7,
+                         stream=sp)
+        g.set_state(np.ones(d["nf"]), np.ones((d["ne"], d["nf"] // r)), theta0, d["theta_fine0"], 0.0)
+        g.free_run(d["spin"])
+        return g
+
+    g = fresh(4)
+    for k in range(args.warmup):
+        g.cycle(d["nsteps"], yd[k])
+    torch.cuda.synchronize()
+    dev = torch.cuda.current_device()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    n0 = M.mgk_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    e0.record(stream)
+    for j in range(args.steps):
+        g.cycle(d["nsteps"], yd[args.warmup + j])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = M.mgk_kernel_launches() - n0
+    t = dist.max(e0.elapsed_time(e1) / 1e3)
+    g.close()
+    # end to end: host observations in, the analysed parameter mean out, every cycle
+    ge = fresh(4)
+    th = np.empty(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        ge.cycle(d["nsteps"], ys[j])
+        M.lib.mgenkf_dual_get_state(ge.h, None, None, None, th.ctypes.data)
+    te = dist.max(time.perf_counter() - t0)
+    ge.close()
+    # parameter estimates over 3 t_c for the paper's coarsening ratios
+    est = {}
+    for r in (1, 2, 4, 8, 16):
+        ga = fresh(r)
+        hist = np.empty((nest, 2))
+        for k in range(nest):
+            ga.cycle(d["nsteps"], yd[k])
+            if k >= nest - 100:
+                M.lib.mgenkf_dual_get_state(ga.h, None, None, None, hist[k].ctypes.data)
+        ga.close()
+        est[str(r)] = hist[-100:].mean(axis=0).tolist()
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        mg = O.DualMGEnKF(d["nf"], 4, d["length"], d["dt"], d["nu"], np.ones(d["nf"]), np.ones((d["ne"], d["nf"] // 4)),
+                          theta0, d["theta_fine0"], obs, d["sigma"], 7, d["q"])
+        mg.free_run(3000)
+        nc_cpu = 20
+        t0 = time.perf_counter()
+        for k in range(nc_cpu):
+            mg.cycle_step(d["nsteps"], ys[k])
+        tc = time.perf_counter() - t0
+        cpu = {"value": nc_cpu / tc, "unit": "cycles/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{nc_cpu} cycles of the ratio-4 dual run after 3000 free-run steps, OpenMP over members"}
+    if dist.rank == 0:
+        line = {"metric": METRIC["dual"], "value": dist.sum(args.steps) / t, "unit": "cycles/s",
+                "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "burgers_inlet_800_r4_ne100_dual", "nf": d["nf"], "ratio": 4,
+                           "ne": d["ne"], "ny": int(obs.size), "steps_per_cycle": d["nsteps"],
+                           "theta_q": d["q"], "spin_up_steps": d["spin"],
+                           "l2": "not flushed: the working set (< 2 MB) lives in L2 by design"},
+                "theta_true": list(d["theta_true"]),
+                "theta_estimate_last_100_of_500_cycles": est,
+                "roofline": None,
+                "roofline_note": "latency-bound: 800-node grids, one CTA each; see DESIGN",
+                "clocks": clk, "gpu_launches": int(launches),
+                "e2e": {"value": args.steps / te, "unit": "cycles/s", "h2d_bytes_per_step": 8 * int(obs.size),
+                        "d2h_bytes_per_step": 16},
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+
 
 
 # --------------------------------------------------------------------------
@@ -999,6 +1129,12 @@ def main():
                 run_reference_batched(args, dist)
             else:
                 run_gpu_batched(args, dist)
+        finally:
+            dist.close()
+        return
+    if args.workload == "dual":
+        try:
+            run_gpu_dual(args, dist)
         finally:
             dist.close()
         return

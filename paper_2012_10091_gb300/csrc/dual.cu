@@ -131,6 +131,9 @@ struct mgenkf_dual {
     double t = 0.0;
     uint64_t cycle = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t aux = nullptr;  // the fine forecast runs beside the members' forecasts and first analysis
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    double *xstar_a = nullptr;   // x^C* stand-in of the parameter analysis (its d* column is not used)
     double *fine = nullptr, *members = nullptr, *prev = nullptr, *theta = nullptr, *theta_f = nullptr;
     double *theta_mean = nullptr, *tau = nullptr, *xstar = nullptr, *dC = nullptr;
     double *yf = nullptr, *yo = nullptr, *ybar = nullptr, *eps = nullptr, *Y = nullptr, *Z = nullptr;
@@ -167,19 +170,24 @@ void free_dual(mgenkf_dual *d) {
                  d->pro_w, d->tap_idx, d->pro_j0, d->cycle_d, d->status};
     for (void *q : p)
         if (q) cudaFree(q);
+    if (d->xstar_a) cudaFree(d->xstar_a);
+    for (cudaEvent_t e : d->ev)
+        if (e) cudaEventDestroy(e);
+    if (d->aux) cudaStreamDestroy(d->aux);
 }
 
-void forecast(mgenkf_dual *d, double *grids, int nprob, int n, const double *theta, int nsteps) {
+void forecast(mgenkf_dual *d, double *grids, int nprob, int n, const double *theta, int nsteps,
+              cudaStream_t s = nullptr) {
     count_launches(1);
-    k_burgers_inlet<<<nprob, ((n + 31) / 32) * 32, 3 * n * sizeof(double), d->stream>>>(
+    k_burgers_inlet<<<nprob, ((n + 31) / 32) * 32, 3 * n * sizeof(double), s ? s : d->stream>>>(
         grids, n, d->cfg.length / n, d->cfg.nu, d->cfg.dt, nsteps, d->t, theta, d->cfg.u0, d->cfg.omega);
 }
 
 // perturbations (generated once per cycle), anomalies and T = S^-1 B (ensemble space)
-void gain_solve(mgenkf_dual *d, int gen_eps) {
+void gain_solve(mgenkf_dual *d, int gen_eps, const double *xstar) {
     const cudaStream_t s = d->stream;
     const int ne = d->ne, ny = d->ny;
-    launch_obs_apply<double>(d->members, d->xstar, d->nc, ne, ny, 4, d->tap_idx, d->tap_w, d->yf, s);
+    launch_obs_apply<double>(d->members, xstar, d->nc, ne, ny, 4, d->tap_idx, d->tap_w, d->yf, s);
     launch_obs_mean(d->yf, d->yo, ne, ny, d->ybar, d->Z, d->status, s);
     launch_obs_perturb(d->yf, d->ybar, d->yo, d->eps, gen_eps, d->cfg.seed, d->cycle_d, d->cfg.obs_sigma, ne,
                        ny, d->Y, d->Z, s);
@@ -240,6 +248,7 @@ extern "C" mgenkf_status mgenkf_dual_create(const mgenkf_dual_config *cfg, const
         {(void **)&d->part, (size_t)gemm_nt_splits((int)ne, (int)ne, (int)ne + 1, (int)ny) * ne * (2 * ne + 1) * 8},
         {(void **)&d->tap_w, ny * 4 * 8}, {(void **)&d->pro_w, nf * 4 * 8}, {(void **)&d->tap_idx, ny * 4 * 4},
         {(void **)&d->pro_j0, nf * 4}, {(void **)&d->cycle_d, 8}, {(void **)&d->status, 4},
+        {(void **)&d->xstar_a, nc * 8},
     };
     for (auto &a : al) {
         if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
@@ -264,6 +273,16 @@ extern "C" mgenkf_status mgenkf_dual_create(const mgenkf_dual_config *cfg, const
             ti[4 * j + t] = pj[k] + t;
             tw[4 * j + t] = pw[4 * (size_t)k + t];
         }
+    }
+    if (cudaStreamCreateWithFlags(&d->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d->ev[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaMemsetAsync(d->xstar_a, 0, nc * 8, d->stream) != cudaSuccess) {
+        cudaGetLastError();
+        free_dual(d);
+        delete d;
+        mgk_set_error("mgenkf_dual_create: stream or event creation failed");
+        return MGENKF_ERR_CUDA;
     }
     const uint64_t zero = 0;
     const int zs = 0;
@@ -314,9 +333,14 @@ extern "C" mgenkf_status mgenkf_dual_cycle(mgenkf_dual_t d, int32_t nsteps, cons
     const cudaStream_t s = d->stream;
     const int ne = d->ne, nc = d->nc;
     D_CUDA(cudaMemcpyAsync(d->yo, y_obs, d->ny * sizeof(double), cudaMemcpyDefault, s));
-    // Algorithm 4 step 2: the fine run with the analysed parameter mean
-    forecast(d, d->fine, 1, d->nf, d->theta_mean, nsteps);
-    launch_restrict<double>(d->fine, d->xstar, 1, 1, nc, d->cfg.ratio, s);
+    // Algorithm 4 step 2: the fine run with the analysed parameter mean, on the
+    // auxiliary stream beside the members' forecasts and the parameter analysis
+    // (theta_mean is rewritten only after the join below)
+    D_CUDA(cudaEventRecord(d->ev[0], s));
+    D_CUDA(cudaStreamWaitEvent(d->aux, d->ev[0], 0));
+    forecast(d, d->fine, 1, d->nf, d->theta_mean, nsteps, d->aux);
+    launch_restrict<double>(d->fine, d->xstar, 1, 1, nc, d->cfg.ratio, d->aux);
+    D_CUDA(cudaEventRecord(d->ev[1], d->aux));
     // Algorithm 3 step 2: parameter random walk, members forecast with theta^f
     D_CUDA(cudaMemcpyAsync(d->prev, d->members, (size_t)ne * nc * 8, cudaMemcpyDeviceToDevice, s));
     launch_normals(d->cfg.seed, kThetaTag, d->cycle, 2 * (int64_t)ne, d->tau, s);
@@ -325,13 +349,14 @@ extern "C" mgenkf_status mgenkf_dual_cycle(mgenkf_dual_t d, int32_t nsteps, cons
                                                         d->theta_f);
     forecast(d, d->members, ne, nc, d->theta_f, nsteps);
     // steps 3-5: perturbed observations, parameter update theta^a = theta^f + Theta T
-    gain_solve(d, 1);
+    gain_solve(d, 1, d->xstar_a);
+    D_CUDA(cudaStreamWaitEvent(s, d->ev[1], 0));  // join: the fine forecast has read theta_mean
     count_launches(1);
     k_theta_update<<<1, 256, 0, s>>>(d->theta_f, d->Bt, ne, d->theta, d->theta_mean, d->status);
     // steps 6-8: members forecast again from the previous analysis with theta^a, state update
     D_CUDA(cudaMemcpyAsync(d->members, d->prev, (size_t)ne * nc * 8, cudaMemcpyDeviceToDevice, s));
     forecast(d, d->members, ne, nc, d->theta, nsteps);
-    gain_solve(d, 0);  // the same perturbations
+    gain_solve(d, 0, d->xstar);  // the same perturbations
     launch_ens_anom<double>(d->members, nc, ne, d->X, nullptr, d->status, s);
     D_CUDA(cudaMemsetAsync(d->dC, 0, nc * sizeof(double), s));
     launch_update_f64<double>(d->members, d->dC, d->X, d->Bt, nc, ne, d->status, s);

@@ -83,3 +83,17 @@ def test_paper_setting_matches_oracle_and_estimates_the_amplitude(M):
     assert rel_err(fine, mg.fine) < 1e-9
     assert abs(tf[0] - 0.2) < 0.03                 # the inlet amplitude moves from 0 to the true 0.2
     g.close()
+
+
+def test_invalid_configurations_are_refused(M):
+    obs = np.arange(1, 11)
+    bad = [dict(n_fine=2048), dict(ratio=3), dict(ratio=32), dict(n_members=1), dict(obs_sigma=0.0),
+           dict(theta_q=-1.0)]
+    for b in bad:
+        kw = dict(n_fine=400, ratio=4, n_members=8, obs_sigma=0.05, theta_q=1e-6)
+        kw.update(b)
+        with pytest.raises(M.MGEnKFError):
+            M.DualMGEnKF(kw["n_fine"], kw["ratio"], kw["n_members"], obs, 10.0, 4e-4, 0.005, kw["obs_sigma"],
+                         kw["theta_q"], 1)
+    with pytest.raises(M.MGEnKFError):
+        M.DualMGEnKF(400, 4, 8, np.array([5, 400]), 10.0, 4e-4, 0.005, 0.05, 1e-6, 1)   # sensor off the grid

@@ -289,6 +289,11 @@ __device__ __forceinline__ void step_x2(float2 (&hv)[Q + 6], float2 (&lo)[Q], fl
 
 template <int Q>
 __global__ void __launch_bounds__(512) burgers_f32x2_kernel(BurgersArgs<float> A) {
+    // A launch that follows this one with programmatic serialisation (the
+    // members after the fine run, see launch_burgers) may start once every CTA
+    // here is resident; before leaving, a CTA waits for the grid it follows
+    // (a no-op for a launch that follows none).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *sh = reinterpret_cast<float2 *>(smem_raw);  // [2 buffers][first 3 | last 3][blockDim]
     const int t = threadIdx.x, nt = blockDim.x;
@@ -379,6 +384,7 @@ __global__ void __launch_bounds__(512) burgers_f32x2_kernel(BurgersArgs<float> A
         }
     }
     if (split) cg::this_cluster().sync();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Q (pairs per thread) for the folded kernel, or 0 if it does not apply:
@@ -404,12 +410,22 @@ static int choose_q(const BurgersArgs<float> &A) {
 }
 
 template <int Q>
-static cudaError_t launch_f32x2(const BurgersArgs<float> &A, cudaStream_t stream) {
+static cudaError_t launch_f32x2(const BurgersArgs<float> &A, cudaStream_t stream, bool follows = false,
+                                bool whole_sm = false) {
     int te = 0;
     if (A.n_whole_probs > 0) te = A.n_whole / (2 * Q);
     if (A.n_split_probs > 0) te = max(te, A.n_split / A.cs / (2 * Q));
     const int nt = ceil_div(te, 32) * 32;
-    const size_t smem = sizeof(float2) * 12 * (size_t)nt;  // <= 48 KB for nt <= 512
+    size_t smem = sizeof(float2) * 12 * (size_t)nt;  // <= 48 KB for nt <= 512
+    if (whole_sm) {
+        // enough shared memory that no other CTA fits beside this one on its SM
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(burgers_f32x2_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+            attr = true;
+        }
+        smem = 210 * 1024;
+    }
     const int grid = A.whole_ctas + A.n_split_probs * A.cs;
     if (grid == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
@@ -417,15 +433,20 @@ static cudaError_t launch_f32x2(const BurgersArgs<float> &A, cudaStream_t stream
     cfg.blockDim = dim3(nt);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     cfg.attrs = attr;
     cfg.numAttrs = 0;
     if (A.cs > 1) {
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = A.cs;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.numAttrs = 1;
+        attr[cfg.numAttrs].id = cudaLaunchAttributeClusterDimension;
+        attr[cfg.numAttrs].val.clusterDim.x = A.cs;
+        attr[cfg.numAttrs].val.clusterDim.y = 1;
+        attr[cfg.numAttrs].val.clusterDim.z = 1;
+        ++cfg.numAttrs;
+    }
+    if (follows) {  // may start while the previous launch on the stream runs (see the kernel)
+        attr[cfg.numAttrs].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[cfg.numAttrs].val.programmaticStreamSerializationAllowed = 1;
+        ++cfg.numAttrs;
     }
     count_launches(1);
     return cudaLaunchKernelEx(&cfg, burgers_f32x2_kernel<Q>, A);
@@ -486,6 +507,31 @@ static cudaError_t launch_burgers(BurgersArgs<T> A, cudaStream_t stream) {
     if constexpr (std::is_same<T, float>::value) {
         static int off = -1;
         if (off < 0) off = getenv("MGENKF_BURGERS_GENERIC") ? 1 : 0;
+        if (!off && A.nsteps > 0 && A.n_whole_probs > 0 && A.n_split_probs > 0 && A.n_whole % 16 == 0 &&
+            A.n_whole / 16 <= 512) {
+            // Members and a split fine run: a split grid's step costs its
+            // cluster barrier (1.01 us per step at 4096 points per CTA against
+            // 0.82 us for a whole grid), so the fine run gets segments of at most
+            // 2048 points on its own cluster launch, and the members follow it
+            // with programmatic serialisation: they start once the fine run's
+            // CTAs are resident (the cluster is placed first) and run beside it.
+            int cs2 = 0;
+            for (int cs = 2; cs <= 8 && !cs2; cs <<= 1)
+                if (A.n_split % cs == 0 && A.n_split / cs <= kBurgersMaxPtsPerCta / 2 && (A.n_split / cs) % 16 == 0)
+                    cs2 = cs;
+            if (cs2) {
+                BurgersArgs<float> F = A, W = A;
+                F.n_whole_probs = 0;
+                F.whole_ctas = 0;
+                F.cs = cs2;
+                W.n_split_probs = 0;
+                W.cs = 1;
+                W.whole_ctas = A.n_whole_probs;
+                cudaError_t e = launch_f32x2<8>(F, stream, false, true);
+                if (e != cudaSuccess) return e;
+                return launch_f32x2<8>(W, stream, true);
+            }
+        }
         if (!off && A.nsteps > 0) {
             switch (choose_q(A)) {
                 case 4: return launch_f32x2<4>(A, stream);

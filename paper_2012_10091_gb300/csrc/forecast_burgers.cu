@@ -236,53 +236,78 @@ __global__ void __launch_bounds__(burgers_max_threads<T, P>())
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 
-__device__ __forceinline__ float2 dtl_x2(float2 prev, float2 cur, float2 nxt, float2 ca, float2 cb) {
+// The folded kernel carries the scaled variable v = a u (a = dt / (4 dx); the
+// load and the store convert, see burgers_f32x2_kernel).  In v the stage
+// increment a dt L(u)_j needs no multiplication by a:
+//   a dt L(u)_j = b (v_{j+1} - 2 v_j + v_{j-1}) + (v_{j-1} - v_{j+1}) (v_{j-1} + v_{j+1})
+//              = b (d_{j-1} - d_j) + (d_{j-1} + d_j) (v_{j-1} + v_{j+1}),   d_j = v_j - v_{j+1},
+// and the edge difference d_j serves points j and j + 1: six operations per
+// point (d_j, the two edge combinations, the neighbour sum, the product and one
+// FMA) against eight for the unscaled form.  d_j is exact for neighbours within
+// a factor 2, so the diffusion term keeps the accuracy of the difference form.
+__device__ __forceinline__ float2 dtl_x2(float2 prev, float2 nxt, float2 dl, float2 dr, float2 cb) {
     const float2 m1 = f2(-1.f);
-    const float2 lap = __fadd2_rn(__ffma2_rn(cur, m1, nxt), __ffma2_rn(cur, m1, prev));
-    const float2 adv = __fmul2_rn(__ffma2_rn(nxt, m1, prev), __fadd2_rn(prev, nxt));
-    return __ffma2_rn(ca, adv, __fmul2_rn(cb, lap));
+    const float2 lap = __ffma2_rn(dr, m1, dl);  // d_{j-1} - d_j
+    const float2 dif = __fadd2_rn(dl, dr);      // v_{j-1} - v_{j+1}
+    return __ffma2_rn(cb, lap, __fmul2_rn(dif, __fadd2_rn(prev, nxt)));
+}
+
+__device__ __forceinline__ float2 edge_x2(float2 left, float2 right) {
+    return __ffma2_rn(right, f2(-1.f), left);  // left - right
 }
 
 // One time step on the pairs a thread holds: hv = hi parts at the start of the
 // step (own pairs at [3, Q+3), halo pairs around them), lo = low parts of the
 // own pairs, sv = stage inputs, kk = k0 then k0 + k1 (index i-1 for pair i).
 // Stage ranges shrink by one pair per side: [1, Q+5), [2, Q+4), [3, Q+3).
+// All values are in the scaled variable v.
 template <int Q>
 __device__ __forceinline__ void step_x2(float2 (&hv)[Q + 6], float2 (&lo)[Q], float2 (&sv)[Q + 6],
-                                        float2 (&kk)[Q + 4], float2 ca, float2 cb) {
+                                        float2 (&kk)[Q + 4], float2 cb) {
     const float2 m1 = f2(-1.f);
-    // stage 1: k0 = dt L(u0), u1 = u0 + k0
+    // stage 1: k0 = a dt L(u0), v1 = v0 + k0
+    {
+        float2 dl = edge_x2(hv[0], hv[1]);
 #pragma unroll
-    for (int i = 1; i < Q + 5; ++i) {
-        const float2 k0 = dtl_x2(hv[i - 1], hv[i], hv[i + 1], ca, cb);
-        kk[i - 1] = k0;
-        sv[i] = __fadd2_rn(hv[i], k0);
+        for (int i = 1; i < Q + 5; ++i) {
+            const float2 dr = edge_x2(hv[i], hv[i + 1]);
+            const float2 k0 = dtl_x2(hv[i - 1], hv[i + 1], dl, dr, cb);
+            kk[i - 1] = k0;
+            sv[i] = __fadd2_rn(hv[i], k0);
+            dl = dr;
+        }
     }
-    // stage 2: k1 = dt L(u1), u2 = u0 + (k0 + k1) / 4   (in place, previous input kept)
+    // stage 2: k1 = a dt L(u1), v2 = v0 + (k0 + k1) / 4   (in place, previous input kept)
     {
         float2 prev = sv[1];
+        float2 dl = edge_x2(sv[1], sv[2]);
 #pragma unroll
         for (int i = 2; i < Q + 4; ++i) {
             const float2 cur = sv[i];
-            const float2 k1 = dtl_x2(prev, cur, sv[i + 1], ca, cb);
+            const float2 dr = edge_x2(cur, sv[i + 1]);
+            const float2 k1 = dtl_x2(prev, sv[i + 1], dl, dr, cb);
             kk[i - 1] = __fadd2_rn(kk[i - 1], k1);
             sv[i] = __ffma2_rn(f2(0.25f), kk[i - 1], hv[i]);
             prev = cur;
+            dl = dr;
         }
     }
-    // stage 3: k2 = dt L(u2), u' = u0 + (k0 + k1)/6 + 2/3 k2, added by Fast2Sum
+    // stage 3: k2 = a dt L(u2), v' = v0 + (k0 + k1)/6 + 2/3 k2, added by Fast2Sum
     {
         float2 prev = sv[2];
+        float2 dl = edge_x2(sv[2], sv[3]);
 #pragma unroll
         for (int i = 3; i < Q + 3; ++i) {
             const float2 cur = sv[i];
-            const float2 k2 = dtl_x2(prev, cur, sv[i + 1], ca, cb);
+            const float2 dr = edge_x2(cur, sv[i + 1]);
+            const float2 k2 = dtl_x2(prev, sv[i + 1], dl, dr, cb);
             const float2 d = __ffma2_rn(f2(2.0f / 3.0f), k2, __fmul2_rn(f2(1.0f / 6.0f), kk[i - 1]));
             const float2 t = __fadd2_rn(lo[i - 3], d);
             const float2 sum = __fadd2_rn(hv[i], t);
             lo[i - 3] = __ffma2_rn(__ffma2_rn(hv[i], m1, sum), m1, t);  // t - (sum - hi)
             hv[i] = sum;
             prev = cur;
+            dl = dr;
         }
     }
 }
@@ -322,15 +347,18 @@ __global__ void __launch_bounds__(512) burgers_f32x2_kernel(BurgersArgs<float> A
     const int h = npts / 2;
     const int te = h / Q;  // threads owning pairs; the others only join the barriers
     const bool active = t < te;
-    const float2 ca = f2(a), cb = f2(b);
+    const float2 cb = f2(b);
 
+    // v = a u as the compensated pair (hi, lo): the rounding error of a u is
+    // exact in one FMA
     float2 w[Q + 6], lo[Q], sv[Q + 6], kk[Q + 4];
     if (active) {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const int j = t * Q + k;
-            w[3 + k] = make_float2(base[j], base[h + j]);
-            lo[k] = f2(0.f);
+            const float2 u = make_float2(base[j], base[h + j]);
+            w[3 + k] = __fmul2_rn(f2(a), u);
+            lo[k] = __ffma2_rn(f2(a), u, make_float2(-w[3 + k].x, -w[3 + k].y));
         }
     }
     int buf = 0;
@@ -371,16 +399,20 @@ __global__ void __launch_bounds__(512) burgers_f32x2_kernel(BurgersArgs<float> A
                     w[Q + 3 + m] = make_float2(l.y, r.x);
                 }
             }
-            step_x2<Q>(w, lo, sv, kk, ca, cb);
+            step_x2<Q>(w, lo, sv, kk, cb);
         }
         buf ^= 1;
     }
     if (active) {
+        // u = (hi + lo) / a: q = hi / a correctly rounded, its remainder
+        // hi - q a exact in one FMA, then the remainder and lo divided and added
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const int j = t * Q + k;
-            base[j] = w[3 + k].x + lo[k].x;
-            base[h + j] = w[3 + k].y + lo[k].y;
+            const float qx = __fdiv_rn(w[3 + k].x, a), qy = __fdiv_rn(w[3 + k].y, a);
+            const float rx = fmaf(-qx, a, w[3 + k].x), ry = fmaf(-qy, a, w[3 + k].y);
+            base[j] = qx + __fdiv_rn(rx + lo[k].x, a);
+            base[h + j] = qy + __fdiv_rn(ry + lo[k].y, a);
         }
     }
     if (split) cg::this_cluster().sync();
@@ -407,6 +439,14 @@ static int choose_q(const BurgersArgs<float> &A) {
         if (ok) return c;
     }
     return 0;
+}
+
+// The folded kernel works in v = a u: a must keep v and the products of v in
+// the normal FP32 range (a = dt / (4 dx) lies far inside this for any usable
+// step); other a go to the generic kernel.
+static bool fold_scale_ok(const BurgersArgs<float> &A) {
+    auto ok = [](float a) { return a >= 0x1p-40f && a <= 0x1p40f; };
+    return (A.n_whole_probs == 0 || ok(A.aw)) && (A.n_split_probs == 0 || ok(A.as));
 }
 
 template <int Q>
@@ -507,7 +547,8 @@ static cudaError_t launch_burgers(BurgersArgs<T> A, cudaStream_t stream) {
     if constexpr (std::is_same<T, float>::value) {
         static int off = -1;
         if (off < 0) off = getenv("MGENKF_BURGERS_GENERIC") ? 1 : 0;
-        if (!off && A.nsteps > 0 && A.n_whole_probs > 0 && A.n_split_probs > 0 && A.n_whole % 16 == 0 &&
+        const bool fold = !off && fold_scale_ok(A);
+        if (fold && A.nsteps > 0 && A.n_whole_probs > 0 && A.n_split_probs > 0 && A.n_whole % 16 == 0 &&
             A.n_whole / 16 <= 512) {
             // Members and a split fine run: a split grid's step costs its
             // cluster barrier (1.01 us per step at 4096 points per CTA against
@@ -532,7 +573,7 @@ static cudaError_t launch_burgers(BurgersArgs<T> A, cudaStream_t stream) {
                 return launch_f32x2<8>(W, stream, true);
             }
         }
-        if (!off && A.nsteps > 0) {
+        if (fold && A.nsteps > 0) {
             switch (choose_q(A)) {
                 case 4: return launch_f32x2<4>(A, stream);
                 case 8: return launch_f32x2<8>(A, stream);

@@ -6,19 +6,22 @@
 // Time (SSP-RK3, Shu-Osher form):
 //   u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1)); u' = 1/3 u + 2/3 (u2 + dt L(u2)).
 //
-// GPU design.  One launch advances every grid of the cycle (the Ne coarse
-// members, Algorithm 3 step 2, and the fine run, Algorithm 4 step 2) by all
-// nsteps of an observation interval:
-//   * a grid segment lives in registers for the whole launch: thread t owns P
+// GPU design.  The grids of the cycle (the Ne coarse members, Algorithm 3
+// step 2, and the fine run, Algorithm 4 step 2) advance by all nsteps of an
+// observation interval inside one kernel pass:
+//   * a grid segment lives in registers for the whole launch: thread t owns
 //     consecutive points, so a member is read from and written to memory once
-//     per interval; only the two edge values of each thread go through shared
-//     memory at every RK stage (one barrier per stage, double-buffered);
+//     per interval; only the edge values of each thread go through shared
+//     memory (double-buffered);
 //   * a member grid (<= 4096 points) is one CTA ("whole" CTAs);
 //   * a fine grid larger than that is split over a thread-block cluster of cs
 //     CTAs ("split" CTAs); the CTA-edge values are read from the neighbouring
 //     CTA's shared memory (DSMEM) after a cluster barrier.  This keeps every SM
-//     at the same per-step work instead of letting the fine run, r_C times a
-//     member, set the pace on a single SM.
+//     at about the same per-step work instead of letting the fine run, r_C
+//     times a member, set the pace on a single SM;
+//   * the FP32 path (burgers_f32x2_kernel) runs the fine run on its own
+//     cluster launch and the members in a second launch beside it (see
+//     launch_burgers); the generic kernel runs both in one launch.
 #include <cooperative_groups.h>
 
 #include <cstdio>
@@ -301,8 +304,8 @@ __device__ __forceinline__ void step_x2(float2 (&hv)[Q + 6], float2 (&lo)[Q], fl
             const float2 cur = sv[i];
             const float2 dr = edge_x2(cur, sv[i + 1]);
             const float2 k2 = dtl_x2(prev, sv[i + 1], dl, dr, cb);
-            const float2 d = __ffma2_rn(f2(2.0f / 3.0f), k2, __fmul2_rn(f2(1.0f / 6.0f), kk[i - 1]));
-            const float2 t = __fadd2_rn(lo[i - 3], d);
+            // t = lo + (k0 + k1)/6 + 2/3 k2 in two FMAs
+            const float2 t = __ffma2_rn(f2(2.0f / 3.0f), k2, __ffma2_rn(f2(1.0f / 6.0f), kk[i - 1], lo[i - 3]));
             const float2 sum = __fadd2_rn(hv[i], t);
             lo[i - 3] = __ffma2_rn(__ffma2_rn(hv[i], m1, sum), m1, t);  // t - (sum - hi)
             hv[i] = sum;

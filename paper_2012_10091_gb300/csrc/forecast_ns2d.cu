@@ -393,12 +393,19 @@ __global__ void __launch_bounds__(256, 3) ns2d_stage_x2(Tiles src, int total_til
     float2 *fold_base = reinterpret_cast<float2 *>(raw_base + 2 * S::RAW);
     TileDesc *desc = reinterpret_cast<TileDesc *>(fold_base + 2 * 8 * HALO);
     const int G = gridDim.x;
+    // Stage launches follow one another with programmatic serialisation (see
+    // x2_launch): the next stage may be scheduled from here on, and its CTAs
+    // take the SMs as this launch's CTAs leave; each CTA prepares its first tile
+    // descriptors (static tables only) before it waits for the previous launch
+    // to complete and its writes to be visible.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     int tile = blockIdx.x;
     if (tile >= total_tiles) return;
     int gi = 0;  // thread 0: group of the last tile it described
     if (threadIdx.x == 0)
         for (int q = 0; q < 3; ++q)
             if (tile + q * G < total_tiles) make_desc<TX, H>(src, tile + q * G, gi, STAGE, &desc[q]);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int ck[S::COPIES], cr[S::COPIES], cx[S::COPIES];  // plane, raw row, first column of the thread's copies
 #pragma unroll
     for (int q = 0; q < S::COPIES; ++q) {
@@ -480,7 +487,20 @@ static int x2_grid(int total_tiles) {
 template <int STAGE, int TX, int H, class Tiles>
 static void x2_launch(const Tiles &src, int total_tiles, float gm1, float mu, float kap, cudaStream_t s) {
     const int grid = x2_grid<STAGE, TX, H, Tiles>(total_tiles);
-    ns2d_stage_x2<STAGE, TX, H, Tiles><<<grid, 256, X2Smem<TX, H>::bytes(), s>>>(src, total_tiles, gm1, mu, kap);
+    // programmatic stream serialisation: the launch may start while the
+    // previous kernel on the stream finishes; the kernel waits for it before
+    // it touches the state (griddepcontrol.wait)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = X2Smem<TX, H>::bytes();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, ns2d_stage_x2<STAGE, TX, H, Tiles>, src, total_tiles, gm1, mu, kap);
 }
 
 // per-handle FP64 launch: two groups (members, fine run) passed by value, 32 x 8 tiles

@@ -510,7 +510,9 @@ __global__ void __launch_bounds__(256) k_cholesky(double *A, double *Lt, int n, 
 // [q w, q w + w), w = ceil(n / 8), all n rows, in shared memory.  Panel p is
 // CTA p's block of columns.  For p = 0 .. 7: CTA p factors its panel column by
 // column (pivot sqrt and one reciprocal, scale the column, rank-1 update of
-// the panel's remaining columns); cluster barrier; every CTA q > p copies the
+// the panel's remaining columns; a ninth warp updates the next diagonal entry
+// and forms its pivot while the eight others update the rest, so the pivot's
+// FP64 chain is off the update's path); cluster barrier; every CTA q > p copies the
 // rows >= q w of panel p from CTA p's shared memory (distributed shared
 // memory) and subtracts the panel's rank-w product from its own columns.  One
 // cluster barrier per panel; the FP64 work of the trailing updates spreads
@@ -540,7 +542,7 @@ __device__ __forceinline__ void chol_pivot(double d, double *y_out, int *status,
     *y_out = y;
 }
 
-__global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(256)
+__global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(288)
     k_cholesky_cluster(double *A, double *Lt, int n, int *status) {
     extern __shared__ double csm[];
     __shared__ int s_fail;
@@ -552,7 +554,8 @@ __global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(256)
     const int c0 = q * w, c1 = min(n, c0 + w), wq = max(0, c1 - c0);
     const int tid = threadIdx.x, nth = blockDim.x;
     // 2-D view of the CTA for column-parallel loops: nx2 column lanes x ny2 row lanes
-    const int nx2 = w <= 8 ? 8 : (w <= 16 ? 16 : 32), ny2 = nth / nx2;
+    const int nupd = 256, kPiv = 256;  // threads [0, 256) update, thread 256 forms the pivots
+    const int nx2 = w <= 8 ? 8 : (w <= 16 ? 16 : 32), ny2 = nupd / nx2;
     const int tx2 = tid % nx2, ty2 = tid / nx2;
     double *P = csm;             // [n][ldp]: rows of this CTA's columns
     double *Lp = csm + n * ldp;  // [n][ldp]: copy of the panel being applied
@@ -572,19 +575,27 @@ __global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(256)
             // (thread 0) forms that pivot's 1/sqrt(d) at once; the square roots
             // and column scalings follow once per panel.
             __syncthreads();
-            if (tid == 0) chol_pivot(P[pc0 * ldp], &s_y[0], status, &s_fail);
+            if (tid == kPiv) chol_pivot(P[pc0 * ldp], &s_y[0], status, &s_fail);
             for (int c = 0; c < wp; ++c) {
                 const int k = pc0 + c;
                 __syncthreads();
                 const double y = s_y[c], idk = y * y;
-                // thread (tx, ty): panel column c + 1 + tx, rows k + 1 + ty, + ny, ... (rows >= that column)
-                const int cc = c + 1 + tx2;
-                if (cc < wp) {
-                    const int r = pc0 + cc;
+                if (tid < nupd) {
+                    // thread (tx, ty): panel column c + 1 + tx, rows k + 1 + ty, + ny, ... (rows >= that column)
+                    const int cc = c + 1 + tx2;
+                    if (cc < wp) {
+                        const int r = pc0 + cc;
+                        const double ljk = P[r * ldp + c] * idk;
+                        for (int ii = k + 1 + ty2; ii < n; ii += ny2)
+                            if (ii > r || (ii == r && cc != c + 1)) P[ii * ldp + cc] = fma(-P[ii * ldp + c], ljk, P[ii * ldp + cc]);
+                    }
+                } else if (tid == kPiv && c + 1 < wp) {
+                    // the next diagonal entry, updated here, and its pivot
+                    const int r = k + 1;
                     const double ljk = P[r * ldp + c] * idk;
-                    for (int ii = k + 1 + ty2; ii < n; ii += ny2)
-                        if (ii >= r) P[ii * ldp + cc] = fma(-P[ii * ldp + c], ljk, P[ii * ldp + cc]);
-                    if (tid == 0) chol_pivot(P[r * ldp + cc], &s_y[cc], status, &s_fail);  // next diagonal, just updated
+                    const double dn = fma(-P[r * ldp + c], ljk, P[r * ldp + c + 1]);
+                    P[r * ldp + c + 1] = dn;
+                    chol_pivot(dn, &s_y[c + 1], status, &s_fail);
                 }
             }
             __syncthreads();
@@ -609,7 +620,7 @@ __global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(256)
             }
             __syncthreads();
             // thread (tx, ty): own column jj = tx, tx + nx2, ...; rows j + ty, + ny2, ...
-            for (int jj = tx2; jj < wq; jj += nx2) {
+            for (int jj = tx2; tid < nupd && jj < wq; jj += nx2) {
                 const int j = c0 + jj;
                 for (int i = j + ty2; i < n; i += ny2) {
                     double acc = P[i * ldp + jj];
@@ -640,7 +651,7 @@ void launch_cholesky(double *A, double *Lt, int n, int *status, cudaStream_t s) 
             cudaFuncSetAttribute(k_cholesky_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
             attr = true;
         }
-        k_cholesky_cluster<<<kCholCluster, 256, bytes, s>>>(A, Lt, n, status);
+        k_cholesky_cluster<<<kCholCluster, 288, bytes, s>>>(A, Lt, n, status);
         return;
     }
     const size_t bytes = sizeof(double) * (size_t)n * (n + 1);

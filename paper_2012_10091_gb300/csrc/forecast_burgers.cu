@@ -561,7 +561,7 @@ static cudaError_t launch_burgers(BurgersArgs<T> A, cudaStream_t stream) {
             // CTAs are resident (the cluster is placed first) and run beside it.
             int cs2 = 0;
             for (int cs = 2; cs <= 8 && !cs2; cs <<= 1)
-                if (A.n_split % cs == 0 && A.n_split / cs <= kBurgersMaxPtsPerCta / 2 && (A.n_split / cs) % 16 == 0)
+                if (A.n_split % cs == 0 && A.n_split / cs <= kBurgersMaxPtsPerCta / 2 && (A.n_split / cs) % 8 == 0)
                     cs2 = cs;
             if (cs2) {
                 BurgersArgs<float> F = A, W = A;
@@ -571,7 +571,10 @@ static cudaError_t launch_burgers(BurgersArgs<T> A, cudaStream_t stream) {
                 W.n_split_probs = 0;
                 W.cs = 1;
                 W.whole_ctas = A.n_whole_probs;
-                cudaError_t e = launch_f32x2<8>(F, stream, false, true);
+                // four pairs per thread on the fine run (256 threads per 2048-point
+                // segment: two warps per SM sub-partition instead of one), eight on
+                // the members
+                cudaError_t e = launch_f32x2<4>(F, stream, false, true);
                 if (e != cudaSuccess) return e;
                 return launch_f32x2<8>(W, stream, true);
             }

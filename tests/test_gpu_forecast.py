@@ -60,6 +60,31 @@ def test_burgers_fp32_matches_oracle(M, n, nprob):
     assert np.max(np.abs(d.cpu().double().numpy() - ref)) <= 2e-5 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("amp,dt", [(50.0, 2e-5), (1e-3, 1e-4), (1.0, 0.0), (1.0, 1e-16)])
+def test_burgers_fp32_scaled_state_edge_cases(M, amp, dt):
+    # The folded FP32 kernel carries v = a u with a = dt / (4 dx): large and
+    # small states and a step so small that a falls below 2^-40 (the generic
+    # kernel takes over) match the oracle; dt = 0 is refused before any launch.
+    import torch
+    n, nprob = 4096, 3
+    u0 = amp * _init(nprob, n, 11)
+    dx, nu = 2 * math.pi / n, 0.01
+    steps = 50
+    d = torch.tensor(u0, dtype=torch.float32, device="cuda")
+    if dt == 0.0:
+        with pytest.raises(M.MGEnKFError) as e:
+            M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_MIXED, d, nprob, n, 2 * math.pi, dt, nu, nsteps=steps)
+        assert e.value.status == 1
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(d.cpu().double().numpy(), u0.astype(np.float32).astype(np.float64))
+        return
+    ref = O.burgers_rk3(u0, dx, nu, dt, steps)
+    M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_MIXED, d, nprob, n, 2 * math.pi, dt, nu, nsteps=steps)
+    torch.cuda.synchronize()
+    got = d.cpu().double().numpy()
+    assert np.max(np.abs(got - ref)) <= 2e-6 * np.max(np.abs(ref))
+
+
 def test_burgers_zero_steps_and_empty_batch(M):
     import torch
     u0 = _init(2, 128, 3)

@@ -554,11 +554,12 @@ static cudaError_t launch_burgers(BurgersArgs<T> A, cudaStream_t stream) {
         if (fold && A.nsteps > 0 && A.n_whole_probs > 0 && A.n_split_probs > 0 && A.n_whole % 16 == 0 &&
             A.n_whole / 16 <= 512) {
             // Members and a split fine run: a split grid's step costs its
-            // cluster barrier (1.01 us per step at 4096 points per CTA against
-            // 0.82 us for a whole grid), so the fine run gets segments of at most
-            // 2048 points on its own cluster launch, and the members follow it
-            // with programmatic serialisation: they start once the fine run's
-            // CTAs are resident (the cluster is placed first) and run beside it.
+            // cluster barrier (a 4096-point segment under a cluster barrier
+            // steps about a quarter slower than a whole 4096-point grid under its
+            // CTA barrier), so the fine run gets segments of at most 2048 points
+            // on its own cluster launch, and the members follow it with
+            // programmatic serialisation: they start once the fine run's CTAs
+            // are resident (the cluster is placed first) and run beside it.
             int cs2 = 0;
             for (int cs = 2; cs <= 8 && !cs2; cs <<= 1)
                 if (A.n_split % cs == 0 && A.n_split / cs <= kBurgersMaxPtsPerCta / 2 && (A.n_split / cs) % 8 == 0)

@@ -50,8 +50,8 @@ WORKLOADS = {
     # run on its own cluster, the members after it by programmatic
     # serialisation); the roofline takes them as one unit, and traffic is the sum
     # of the two launches' DRAM bytes
-    "burgers_large": dict(flops=32, ops=26, kernel="burgers_f32x2_kernel<8> (fine run + members)",
-                          launches_per_step=None, traffic=2345152, truth="fp32"),
+    "burgers_large": dict(flops=32, ops=26, kernel="burgers_f32x2_kernel<4> fine run + <8> members",
+                          launches_per_step=None, traffic=2410752, truth="fp32"),
     # NS-2D: ~200 flops per point and stage (primitives, nodal fluxes, four
     # face fluxes, stage update), 3 stages per step; as FP32 operations per
     # point and stage, counted from the kernel: 9 (primitives) + 28 (inviscid)

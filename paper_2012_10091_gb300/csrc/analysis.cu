@@ -137,7 +137,9 @@ void launch_innov_rms(const double *Z, int ne, int ny, double *out, cudaStream_t
 
 // perturbed observations (Eq. perturbed_y) and normalised anomalies Y (Algorithm 3 step 7)
 // One thread per Philox block: the 4 consecutive elements o = 4b .. 4b + 3 of
-// the Ne x Ny perturbation matrix (flat index o = i Ny + j).
+// the Ne x Ny perturbation matrix (flat index o = i Ny + j).  gen_eps: 0 = eps
+// given, 1 = normals in FP64, 2 = Box-Muller in FP32 (the mixed path).
+template <bool F32>
 __global__ void k_obs_perturb(const double *__restrict__ yf, const double *__restrict__ ybar,
                               const double *__restrict__ yo, double *__restrict__ eps, int gen_eps,
                               uint64_t seed, const uint64_t *__restrict__ cycle, double sigma, int ne,
@@ -146,7 +148,12 @@ __global__ void k_obs_perturb(const double *__restrict__ yf, const double *__res
     const size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (4 * b >= total) return;
     double z[4];
-    if (gen_eps) philox_normals4(seed, kEpsTag, *cycle, (uint64_t)b, z);
+    if (gen_eps) {
+        if (F32)
+            philox_normals4_f32(seed, kEpsTag, *cycle, (uint64_t)b, z);
+        else
+            philox_normals4(seed, kEpsTag, *cycle, (uint64_t)b, z);
+    }
     int i = (int)((4 * b) / ny), j = (int)(4 * b - (size_t)i * ny);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
@@ -176,8 +183,12 @@ void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, 
     count_launches(1);
     const size_t blocks = ((size_t)ne * ny + 3) / 4;
     // isq = 1/sqrt(Ne - 1) from the host (an FP64 division and square root per thread on the device)
-    k_obs_perturb<<<(unsigned)ceil_div(blocks, 128), 128, 0, s>>>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma,
-                                                                   ne, ny, 1.0 / std::sqrt((double)(ne - 1)), Y, Z);
+    const unsigned grid = (unsigned)ceil_div(blocks, 128);
+    const double isq = 1.0 / std::sqrt((double)(ne - 1));
+    if (gen_eps == 2)
+        k_obs_perturb<true><<<grid, 128, 0, s>>>(yf, ybar, yo, eps, 1, seed, cycle, sigma, ne, ny, isq, Y, Z);
+    else
+        k_obs_perturb<false><<<grid, 128, 0, s>>>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma, ne, ny, isq, Y, Z);
 }
 
 // Fine-to-coarse feedback: the forecast ensemble re-centred on the restricted

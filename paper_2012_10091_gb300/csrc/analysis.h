@@ -68,6 +68,8 @@ void launch_state_rate(const T *x, const T *prev, size_t count, double dt, doubl
 template <typename T>
 void launch_recentre(T *members, size_t nx, int ne, const T *xstar, const int *status, cudaStream_t s);
 
+// gen_eps: 0 = eps given, 1 = perturbations drawn in FP64, 2 = the same Philox
+// words with the Box-Muller transform in FP32 (mixed precision)
 void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, double *eps,
                         int gen_eps, uint64_t seed, const uint64_t *cycle, double sigma, int ne, int ny,
                         double *Y, double *Z, cudaStream_t s);

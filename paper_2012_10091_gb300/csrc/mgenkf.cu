@@ -547,7 +547,7 @@ static mgenkf_status analyse_impl(mgenkf_ctx *h, const double *y_obs, const doub
     H_CUDA(cudaMemcpyAsync(h->yo, y_obs, h->ny * sizeof(double), cudaMemcpyDefault, h->stream));
     if (eps) H_CUDA(cudaMemcpyAsync(h->eps, eps, (size_t)h->ne * h->ny * sizeof(double), cudaMemcpyDefault, h->stream));
     if (h->mixed)
-        analyse_kernels<float>(h, eps ? 0 : 1);
+        analyse_kernels<float>(h, eps ? 0 : 2);  // FP32 Box-Muller on the mixed path
     else
         analyse_kernels<double>(h, eps ? 0 : 1);
     H_LAUNCHED();

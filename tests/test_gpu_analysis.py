@@ -92,6 +92,25 @@ def test_mixed_analysis_matches_oracle(M, nf, ratio, ne, npr):
     assert np.max(np.abs(r["fine"] - r["fine_ref"])) < bound_f
 
 
+def test_mixed_perturbations_follow_the_oracle_stream(M):
+    # The mixed path draws the same Philox words and evaluates Box-Muller in
+    # FP32 (each uniform rounded to FP32): the perturbations stay within FP32
+    # rounding of the oracle's FP64 normals, element by element, over two
+    # analyses (the device counter advances the stream).
+    w = W.burgers_custom(1024, 4, 37, 130, obs_kind="random", sigma=0.3, precision="mixed")
+    inp = W.make_inputs(w)
+    g = M.MGEnKF.from_workload(w, precision="mixed")
+    g.set_state(inp["fine0"], inp["members0"])
+    for k in range(2):
+        g.analyse(np.zeros(w.ny))
+        assert g.sync() == 0
+        got = g.field(M.MGENKF_FIELD_EPS).reshape(w.ne, w.ny)
+        ref = O.obs_perturbations(w.seed, k, w.ne, w.ny, w.sigma)
+        np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-5 * w.sigma)
+        assert np.max(np.abs(got - ref)) > 0.0  # FP32 arithmetic, not the FP64 values
+    g.close()
+
+
 def test_explicit_perturbations_are_used(M):
     w = W.burgers_custom(256, 4, 9, 7, obs_kind="random", sigma=0.2)
     r = _one_analysis(M, w, 0, "fp64", explicit_eps=True)

@@ -63,6 +63,9 @@ struct mgenkf_ctx {
     size_t scratch_n = 0;
     int *status = nullptr;
     uint64_t *cycle_d = nullptr;  // analysis counter on the device (keys the perturbation stream)
+    // mgenkf_cycle with a host truth: its copy runs on cstream beside the forecast
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_prev = nullptr, ev_truth = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -138,6 +141,9 @@ static void free_all(mgenkf_ctx *h) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->Tm && h->Tm != h->Bt) cudaFree(h->Tm);
+    if (h->cstream) cudaStreamDestroy(h->cstream);
+    if (h->ev_prev) cudaEventDestroy(h->ev_prev);
+    if (h->ev_truth) cudaEventDestroy(h->ev_truth);
 }
 
 // copy n doubles from a host or device pointer into device buffer dst (FP64)
@@ -656,20 +662,47 @@ extern "C" mgenkf_status mgenkf_rmse(mgenkf_handle h, const double *truth_fine, 
     return rmse_impl(h, truth_fine, out);
 }
 
+// A host truth is copied on a side stream while the forecast runs (after the
+// previous work on the handle's stream, which may still read the buffer), and
+// the RMSE waits for that copy.
+static mgenkf_status stage_truth(mgenkf_ctx *h, const double *truth) {
+    if (!h->truth_d) H_ALLOC(h->truth_d, h->nxf * sizeof(double));
+    if (!h->cstream) {
+        H_CUDA(cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+        H_CUDA(cudaEventCreateWithFlags(&h->ev_prev, cudaEventDisableTiming));
+        H_CUDA(cudaEventCreateWithFlags(&h->ev_truth, cudaEventDisableTiming));
+    }
+    H_CUDA(cudaEventRecord(h->ev_prev, h->stream));
+    H_CUDA(cudaStreamWaitEvent(h->cstream, h->ev_prev, 0));
+    H_CUDA(cudaMemcpyAsync(h->truth_d, truth, h->nxf * sizeof(double), cudaMemcpyHostToDevice, h->cstream));
+    H_CUDA(cudaEventRecord(h->ev_truth, h->cstream));
+    return MGENKF_OK;
+}
+
 extern "C" mgenkf_status mgenkf_cycle(mgenkf_handle h, int32_t nsteps, const double *y_obs,
                                       const double *truth_fine, double *rmse_out) {
     if (!h) return MGENKF_ERR_INVALID_ARG;
     h->err.clear();
-    mgenkf_status st = forecast_impl(h, nsteps);
-    if (st) return st;
-    st = analyse_impl(h, y_obs, nullptr);
-    if (st) return st;
-    st = prolong_impl(h);
-    if (st) return st;
-    if (truth_fine) {
-        if (!rmse_out) H_FAIL(MGENKF_ERR_INVALID_ARG, "rmse_out is required with truth_fine");
-        st = rmse_impl(h, truth_fine, rmse_out);
+    if (truth_fine && !rmse_out) H_FAIL(MGENKF_ERR_INVALID_ARG, "rmse_out is required with truth_fine");
+    const bool staged = truth_fine && !is_device_ptr(truth_fine);
+    mgenkf_status st = staged ? stage_truth(h, truth_fine) : MGENKF_OK;
+    if (st == MGENKF_OK) st = forecast_impl(h, nsteps);
+    if (st == MGENKF_OK) st = analyse_impl(h, y_obs, nullptr);
+    if (st == MGENKF_OK) st = prolong_impl(h);
+    if (st == MGENKF_OK && truth_fine) {
+        if (staged) {
+            const cudaError_t e = cudaStreamWaitEvent(h->stream, h->ev_truth, 0);
+            if (e != cudaSuccess) {
+                h->err = std::string("truth copy: ") + cudaGetErrorString(e);
+                st = MGENKF_ERR_CUDA;
+            } else
+                st = rmse_impl(h, h->truth_d, rmse_out);
+        } else {
+            st = rmse_impl(h, truth_fine, rmse_out);
+        }
     }
+    // the caller's truth buffer is free again when this returns
+    if (staged && h->cstream) cudaStreamSynchronize(h->cstream);
     return st;
 }
 

@@ -73,3 +73,34 @@ def test_checkpoint_resume_is_bit_exact(tmp_path):
     b_fine, b_mem = g2.get_state()
     np.testing.assert_array_equal(a_fine, b_fine)
     np.testing.assert_array_equal(a_mem, b_mem)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cycle_with_host_truth_matches_separate_rmse(precision):
+    # mgenkf_cycle copies a host truth beside the forecast (side stream) and
+    # reads the RMSE after it: the same states and RMSE values as a cycle
+    # without truth followed by mgenkf_rmse, over several cycles with a fresh
+    # truth buffer each time.
+    import torch
+    from paper_2012_10091_gb300 import mgenkf as M
+    w = W.burgers_custom(1024, 4, 16, 40, precision=precision)
+    inp = W.make_inputs(w)
+    ga = M.MGEnKF.from_workload(w, precision=precision)
+    gb = M.MGEnKF.from_workload(w, precision=precision)
+    for g in (ga, gb):
+        g.set_state(inp["fine0"], inp["members0"])
+    truth = torch.tensor(inp["truth0"], dtype=torch.float64, device="cuda")
+    for k in range(4):
+        M.mgk_forecast(M.MGENKF_BURGERS1D, M.MGENKF_FP64, truth, 1, w.nf, w.length, w.dt, w.nu,
+                       nsteps=w.steps_per_cycle)
+        th = truth.cpu().numpy().copy()
+        yo = W.sample_truth(w, th, inp["obs_idx"], inp["obs_var"]) + W.observation_noise(w, k)
+        ra = np.empty(w.V)
+        ga.cycle(w.steps_per_cycle, yo, th, ra)
+        gb.cycle(w.steps_per_cycle, yo)
+        rb = gb.rmse(th)
+        np.testing.assert_array_equal(ra, rb)
+    for a, b in zip(ga.get_state(), gb.get_state()):
+        np.testing.assert_array_equal(a, b)
+    ga.close()
+    gb.close()

@@ -131,7 +131,10 @@ mgenkf_status mgenkf_set_prolong_cnn(mgenkf_handle h, void *cnn);
 /* One whole cycle: forecast(nsteps), analyse(y_obs, NULL), prolong_correct,
  * and, if truth_fine != NULL, the relative RMSE of the fine run written to
  * rmse_out (V FP64 values; device pointer, or host pointer which makes the
- * call synchronous).  All pointers host or device. */
+ * call synchronous).  All pointers host or device.  A host truth_fine is copied
+ * to the device beside the forecast; the copy has finished when the call
+ * returns, so the caller may reuse that buffer at once.  rmse_out is required
+ * with truth_fine (MGENKF_ERR_INVALID_ARG otherwise, before any work). */
 mgenkf_status mgenkf_cycle(mgenkf_handle h, int32_t nsteps, const double *y_obs,
                            const double *truth_fine, double *rmse_out);
 

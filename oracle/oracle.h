@@ -87,7 +87,9 @@ void orc_prolong_add(const double *dc, int dim, int V, int nc, int r, double *fi
 void orc_obs_coarse(const double *xc, int dim, int V, int nc, int r, int ny,
                     const int32_t *obs_idx, const int32_t *obs_var, double *y);
 
-/* ---- Cholesky (textbook), returns 0 or the failing pivot index + 1 ---- */
+/* ---- Cholesky (textbook), returns 0 or the failing pivot index + 1 ----
+ * Parity: pinned (L L^T = A by brute force, the library factor, the index of a
+ * failing pivot); the solve through the EnKF analysis's dense brute force. */
 int orc_cholesky(double *A, int n);
 void orc_chol_solve(const double *Lf, int n, double *b, int nrhs);
 
@@ -157,7 +159,9 @@ void orc_ns2d_gamma(const double *q, const double *qprev, int n, double h, doubl
  * (mean equals x^C*, anomalies unchanged, analysis mean = x^C' + K mean(eps)). */
 void orc_recentre(double *members, int ne, int64_t nx, const double *xstar);
 
-/* ---- relative RMSE, Eq. L2norm_u, one value per variable ---- */
+/* ---- relative RMSE, Eq. L2norm_u, one value per variable ----
+ * Parity: pinned (closed forms: uniform relative error per plane, an offset
+ * on a sine, the truth as the denominator). */
 void orc_rmse(const double *x, const double *truth, int V, int64_t npts, double *out);
 
 #endif

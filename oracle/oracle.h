@@ -35,6 +35,7 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
  * blocks ctr = (ctr0, n/4, 0, 0), key = (seed, tag); lanes (0,1) and (2,3)
  * of a block give one Box-Muller pair each.  u = ((x >> 11) + 1) * 2^-53. */
 void orc_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count, double *z);
+/* Parity: pinned (moments, kurtosis, Kolmogorov-Smirnov, lag correlations). */
 
 /* ---- 1-D viscous Burgers (Eq. burgers), periodic, flux form ----
  * L(u)_j = -(F_{j+1} - F_{j-1}) / (2 dx) + nu (u_{j+1} - 2 u_j + u_{j-1}) / dx^2
@@ -46,6 +47,9 @@ void orc_burgers_rhs(const double *u, int n, double dx, double nu, int flux_kind
                      double *L);
 void orc_burgers_rk3(double *u, int nprob, int n, double dx, double nu, double dt, int nsteps,
                      int flux_kind, double c);
+/* Parity: pinned (Fourier amplification factor of the linear-flux scheme,
+ * second-order convergence to the Cole-Hopf solution, mass conservation, a
+ * hand-computed right-hand side). */
 
 /* ---- 2-D compressible Navier-Stokes (Eqs. Mass, Momentum, Energy) ----
  * Periodic square, q = (rho, rho u, rho v, E) as 4 planes of n x n (x fastest).
@@ -73,6 +77,8 @@ void orc_burgers_inlet_rk3(double *u, int nprob, int n, double dx, double nu, do
 void orc_ns2d_filter6(double *q, int nprob, int n, double sigma);
 void orc_ns2d_rk3(double *q, int nprob, int n, double h, double gamma, double mu,
                   double prandtl, double dt, int nsteps);
+/* Parity: pinned (conservation of the four totals, steady uniform state,
+ * x-y transpose symmetry, acoustic dispersion, viscous decay of a shear mode). */
 
 /* ---- projectors Pi_C, Pi_F (end of Sec. 2.2) ----
  * Vertex-centred nested periodic grids, coarse node J at fine node r J.
@@ -86,6 +92,8 @@ void orc_prolong_add(const double *dc, int dim, int V, int nc, int r, double *fi
  * (y*nf + x in 2-D), obs_var = variable.  y[j] = (Pi_F xc)[obs_var[j]][obs_idx[j]] */
 void orc_obs_coarse(const double *xc, int dim, int V, int nc, int r, int ny,
                     const int32_t *obs_idx, const int32_t *obs_var, double *y);
+/* Parity: pinned (Pi_C Pi_F = I, exactness on cubics, fourth-order error on
+ * Fourier modes, H^C equal to the Pi_F row). */
 
 /* ---- Cholesky (textbook), returns 0 or the failing pivot index + 1 ----
  * Parity: pinned (L L^T = A by brute force, the library factor, the index of a
@@ -106,6 +114,8 @@ void orc_chol_solve(const double *Lf, int n, double *b, int nrhs);
 int orc_enkf_analyse(int dim, int V, int nc, int r, int ne, int ny, const int32_t *obs_idx,
                      const int32_t *obs_var, const double *yo, const double *eps, double sigma,
                      int gain_form, double *members, const double *xstar, double *dC);
+/* Parity: pinned (dense brute force for the three gain forms at small sizes,
+ * the sigma limits, convergence to the Kalman filter as Ne grows). */
 
 /* Dense Kalman gain K (nx x ny) of the literal form, for brute-force pins. */
 int orc_enkf_gain(int nx, int ne, int ny, const double *X, const double *Y, const double *Rm,
@@ -125,6 +135,9 @@ void orc_conv3x3_bwd(const double *in, int cin, int n, const double *W, int cout
  * out[c][4y + sy][4x + sx] = in[16 c + 4 sy + sx][y][x]; unshuffle is its adjoint. */
 void orc_pixel_shuffle4(const double *in, int C, int n, double *out);
 void orc_pixel_unshuffle4(const double *in, int C, int n, double *out);
+/* Parity: pinned (a library convolution, automatic differentiation of the
+ * backward pass, a library pixel shuffle, central differences of the loss
+ * gradient). */
 
 /* ---- final fine-grid iteration (Algorithm 4 step 6) and the conservativity
  * indicator (Eq. Conservativity_rhov) ----

@@ -679,46 +679,55 @@ void launch_cholesky(double *A, double *Lt, int n, int *status, cudaStream_t s) 
     }
 }
 
-// Triangular solves with L staged in shared memory: one warp per right-hand
-// side (one CTA each, so the FP64 work of the columns spreads over the SMs),
-// lanes own rows lane + 32 m, the diagonal reciprocals precomputed.
+// Triangular solves with the factor staged in shared memory: one warp per
+// right-hand side (one CTA each, so the FP64 work of the columns spreads over
+// the SMs), lanes own rows lane + 32 m.
 template <int MAXR>
 __global__ void __launch_bounds__(256) k_chol_solve_smem(const double *__restrict__ L, int n,
                                                          const double *rhs, double *out, int ncol,
                                                          __nv_bfloat16 *out16, int ld16,
                                                          const int *status) {
-    // 256 threads copy the lower triangle of L into shared memory, then warp 0
-    // runs both substitutions for right-hand side blockIdx.x.
-    extern __shared__ double sL[];  // [n][n+1] then inv_diag[n]
+    // 256 threads stage the unit lower factor U = L D^-1 (D = diag L) in shared
+    // memory, then warp 0 runs both substitutions for right-hand side
+    // blockIdx.x: S x = U D^2 U^T x = b as U y = b, then U^T x = D^-2 y.  With
+    // the unit diagonal no step of either substitution waits on an FP64
+    // multiplication before its broadcast.
+    extern __shared__ double sL[];  // [n][n+1]: U strictly below the diagonal; then inv_diag[n]
     if (*status) return;
     const int c = blockIdx.x, lane = threadIdx.x & 31, ld = n + 1;
     double *inv = sL + (size_t)n * ld;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) inv[j] = 1.0 / L[(size_t)j * n + j];
+    __syncthreads();
     for (int i = threadIdx.x >> 5; i < n; i += blockDim.x >> 5)
-        for (int j = lane; j <= i; j += 32) sL[(size_t)i * ld + j] = L[(size_t)i * n + j];
+        for (int j = lane; j < i; j += 32) sL[(size_t)i * ld + j] = L[(size_t)i * n + j] * inv[j];
     __syncthreads();
     if (threadIdx.x >= 32) return;
-    for (int j = lane; j < n; j += 32) inv[j] = 1.0 / sL[(size_t)j * ld + j];
-    __syncwarp();
     double b[MAXR];
 #pragma unroll
     for (int m = 0; m < MAXR; ++m) {
         const int i = lane + 32 * m;
         b[m] = i < n ? rhs[(size_t)c * n + i] : 0.0;
     }
+    // forward, column by column: y_j is final once the columns before j are applied
 #pragma unroll
     for (int s = 0; s < MAXR; ++s) {
         if (s * 32 >= n) break;
         for (int l = 0; l < 32; ++l) {
             const int j = s * 32 + l;
             if (j >= n) break;
-            if (lane == l) b[s] *= inv[j];
-            const double zj = __shfl_sync(0xffffffffu, b[s], l);
+            const double yj = __shfl_sync(0xffffffffu, b[s], l);
 #pragma unroll
             for (int m = s; m < MAXR; ++m) {
                 const int i = lane + 32 * m;
-                if (i > j && i < n) b[m] = fma(-sL[(size_t)i * ld + j], zj, b[m]);
+                if (i > j && i < n) b[m] = fma(-sL[(size_t)i * ld + j], yj, b[m]);
             }
         }
+    }
+    // right-hand side of the backward substitution: D^-2 y
+#pragma unroll
+    for (int m = 0; m < MAXR; ++m) {
+        const int i = lane + 32 * m;
+        if (i < n) b[m] *= inv[i] * inv[i];
     }
 #pragma unroll
     for (int s = MAXR - 1; s >= 0; --s) {
@@ -726,7 +735,6 @@ __global__ void __launch_bounds__(256) k_chol_solve_smem(const double *__restric
         for (int l = 31; l >= 0; --l) {
             const int j = s * 32 + l;
             if (j >= n) continue;
-            if (lane == l) b[s] *= inv[j];
             const double xj = __shfl_sync(0xffffffffu, b[s], l);
 #pragma unroll
             for (int m = 0; m <= s; ++m) {

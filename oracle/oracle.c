@@ -184,7 +184,10 @@ void orc_burgers_rk3(double *u, int nprob, int n, double dx, double nu, double d
 /* ======================================================================== */
 /* Compressible NS, Eqs. Mass, Momentum, Energy (Sec. 6), periodic square.   */
 /* Parity: pinned (conservation of the four totals, uniform-state and        */
-/* x<->y symmetry invariants, linear acoustic/shear mode decay).             */
+/* x<->y symmetry invariants, linear acoustic/shear mode decay, the 4 x 4    */
+/* discrete symbol of the operator linearised about rest, which fixes the    */
+/* 4/3 and -2/3 stress factors, the cross terms and kappa; exact states that */
+/* fix the heat flux kappa lap T and the viscous work tau . u).              */
 /* ======================================================================== */
 #define IDX(y, x) ((size_t)(((y) + n) % n) * n + (size_t)(((x) + n) % n))
 

@@ -78,7 +78,11 @@ void orc_ns2d_filter6(double *q, int nprob, int n, double sigma);
 void orc_ns2d_rk3(double *q, int nprob, int n, double h, double gamma, double mu,
                   double prandtl, double dt, int nsteps);
 /* Parity: pinned (conservation of the four totals, steady uniform state,
- * x-y transpose symmetry, acoustic dispersion, viscous decay of a shear mode). */
+ * x-y transpose symmetry, acoustic dispersion, viscous decay of a shear mode;
+ * the 4 x 4 discrete symbol of the right-hand side linearised about rest,
+ * which fixes the 4/3 and -2/3 stress factors, the cross terms and kappa;
+ * exact states for the heat flux kappa lap T (density wave at constant p)
+ * and for the viscous work tau . u (transverse shear, longitudinal stretch)). */
 
 /* ---- projectors Pi_C, Pi_F (end of Sec. 2.2) ----
  * Vertex-centred nested periodic grids, coarse node J at fine node r J.

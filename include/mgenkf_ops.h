@@ -88,6 +88,10 @@ mgenkf_status mgk_cnn_adam_step(mgk_cnn_t cnn, float lr, void *stream);
  *   Z: device, (n_members + 1) x n_obs, rows D_i = y^o + eps_i - y^f_i, last row d* = y^o - H^C x^C*;
  *   T: device output, (n_members + 1) x n_members, column c of T contiguous (T[c * n_members + a]);
  *   info: optional device int32 set to 0, or MGENKF_ERR_NOT_SPD if a pivot was not positive.
+ * Y, Z, T and info must be device (or managed) memory of the current device:
+ * other pointers return MGENKF_ERR_INVALID_ARG before any work.  A CUDA error
+ * left pending by earlier work is reported as MGENKF_ERR_CUDA (and left
+ * pending for its owner) without launching anything.
  * Scratch (S, L^T, status) lives in a fixed array compiled into the library,
  * held by every GPU that loads it until exit (256 KB); hence n_members <= 128,
  * larger sizes return MGENKF_ERR_INVALID_ARG with a message.  The first call on

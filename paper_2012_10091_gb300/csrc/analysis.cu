@@ -657,22 +657,19 @@ void launch_cholesky(double *A, double *Lt, int n, int *status, cudaStream_t s) 
     count_launches(1);
     if (n >= 32 && n <= 256) {
         const size_t bytes = sizeof(double) * 2 * (size_t)n * ((n + kCholCluster - 1) / kCholCluster + 1);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_cholesky_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-            attr = true;
-        }
+        static OncePerDevice attr;
+        attr.run([](int) {
+            return cudaFuncSetAttribute(k_cholesky_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        });
         k_cholesky_cluster<<<kCholCluster, 288, bytes, s>>>(A, Lt, n, status);
         return;
     }
     const size_t bytes = sizeof(double) * (size_t)n * (n + 1);
     if (bytes <= 210 * 1024) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_cholesky<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 210 * 1024);
-            attr_set = true;
-        }
+        static OncePerDevice attr;
+        attr.run([](int) {
+            return cudaFuncSetAttribute(k_cholesky<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+        });
         k_cholesky<true><<<1, 256, bytes, s>>>(A, Lt, n, status);
     } else {
         k_cholesky<false><<<1, 256, 0, s>>>(A, Lt, n, status);
@@ -816,18 +813,18 @@ void launch_chol_solve(const double *L, const double *Lt, int n, const double *r
     count_launches(1);
     const size_t smem = sizeof(double) * ((size_t)n * (n + 1) + n);
     if (n <= 160 && smem <= 210 * 1024) {
-        static bool attr_set[2] = {false, false};
+        static OncePerDevice attr[2];
         if (n <= 128) {
-            if (!attr_set[0]) {
-                cudaFuncSetAttribute(k_chol_solve_smem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-                attr_set[0] = true;
-            }
+            attr[0].run([](int) {
+                return cudaFuncSetAttribute(k_chol_solve_smem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            210 * 1024);
+            });
             k_chol_solve_smem<4><<<ncol, 256, smem, s>>>(L, n, rhs, out, ncol, out16, ld16, status);
         } else {
-            if (!attr_set[1]) {
-                cudaFuncSetAttribute(k_chol_solve_smem<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-                attr_set[1] = true;
-            }
+            attr[1].run([](int) {
+                return cudaFuncSetAttribute(k_chol_solve_smem<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            210 * 1024);
+            });
             k_chol_solve_smem<8><<<ncol, 256, smem, s>>>(L, n, rhs, out, ncol, out16, ld16, status);
         }
         return;

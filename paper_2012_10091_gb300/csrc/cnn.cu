@@ -295,14 +295,16 @@ template <int CIN, int COUT>
 static size_t smem_bwd_w() { return sizeof(float) * (CIN * kTH * kTH + COUT * kT * kT); }
 
 static void set_smem_attrs() {
-    static bool done = false;
-    if (done) return;
-    done = true;
-    cudaFuncSetAttribute(k_conv_bwd_data<32, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_conv_bwd_data<32, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_conv_bwd_weight<32, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_conv_bwd_weight<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_conv_bwd_weight<8, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    static OncePerDevice once;
+    once.run([](int) {
+        const int b = 200 * 1024;
+        cudaError_t e = cudaFuncSetAttribute(k_conv_bwd_data<32, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_bwd_data<32, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_bwd_weight<32, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_bwd_weight<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_bwd_weight<8, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        return e;
+    });
 }
 
 static void cnn_free(mgk_cnn *c) {

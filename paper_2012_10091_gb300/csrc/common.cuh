@@ -5,11 +5,44 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 
 #include "../../include/mgenkf.h"
 
 namespace mgk {
+
+// ---------------------------------------------------------------------------
+// Host: run a set-up step once per device.  Kernel attributes (the dynamic
+// shared-memory limit) and occupancy figures belong to one device context, so
+// a flag shared by all devices would skip the step on the second device.  The
+// step runs with the device current; it is retried on the next call if it
+// failed.  Thread-safe.
+// ---------------------------------------------------------------------------
+constexpr int kMaxDevices = 128;
+class OncePerDevice {
+  public:
+    // index of the current device in [0, kMaxDevices), or -1 on error
+    static int current() {
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+        return dev;
+    }
+    template <class F>
+    cudaError_t run(F &&f) {
+        const int dev = current();
+        if (dev < 0) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lock(mu_);
+        if (done_[dev]) return cudaSuccess;
+        const cudaError_t e = f(dev);
+        if (e == cudaSuccess) done_[dev] = true;
+        return e;
+    }
+
+  private:
+    std::mutex mu_;
+    bool done_[kMaxDevices] = {};
+};
 
 // ---------------------------------------------------------------------------
 // launch helpers

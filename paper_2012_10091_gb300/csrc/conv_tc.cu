@@ -203,12 +203,11 @@ template <int CIN, int COUT, bool RELU, bool OUT_BF16>
 cudaError_t launch_conv_fwd_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wp, const float *bias, void *out, int n,
                                int batch, int *status, cudaStream_t s) {
     using S = ConvTcShape<CIN, COUT>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_conv_fwd_tc<CIN, COUT, RELU, OUT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             S::SMEM);
-        attr = true;
-    }
+    static OncePerDevice attr;
+    attr.run([](int) {
+        return cudaFuncSetAttribute(k_conv_fwd_tc<CIN, COUT, RELU, OUT_BF16>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    });
     count_launches(1);
     const dim3 grid(ceil_div(n, kPix), ceil_div(n, kConvRows), batch);
     k_conv_fwd_tc<CIN, COUT, RELU, OUT_BF16><<<grid, 128, S::SMEM, s>>>(in, wp, bias, out, n, status);

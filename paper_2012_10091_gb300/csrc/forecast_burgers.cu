@@ -462,11 +462,11 @@ static cudaError_t launch_f32x2(const BurgersArgs<float> &A, cudaStream_t stream
     size_t smem = sizeof(float2) * 12 * (size_t)nt;  // <= 48 KB for nt <= 512
     if (whole_sm) {
         // enough shared memory that no other CTA fits beside this one on its SM
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(burgers_f32x2_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-            attr = true;
-        }
+        static OncePerDevice attr;
+        attr.run([](int) {
+            return cudaFuncSetAttribute(burgers_f32x2_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        210 * 1024);
+        });
         smem = 210 * 1024;
     }
     const int grid = A.whole_ctas + A.n_split_probs * A.cs;

@@ -470,18 +470,22 @@ __global__ void __launch_bounds__(256, 3) ns2d_stage_x2(Tiles src, int total_til
 // CTAs per launch of a persistent stage kernel: resident CTAs per SM x SMs
 template <int STAGE, int TX, int H, class Tiles>
 static int x2_grid(int total_tiles) {
-    static int per_sm = 0, sms = 0;
-    if (!per_sm) {
+    static OncePerDevice once;
+    static int ctas[kMaxDevices];  // resident CTAs per SM x SMs, per device
+    once.run([](int dev) {
         const size_t smem = X2Smem<TX, H>::bytes();
-        cudaFuncSetAttribute(ns2d_stage_x2<STAGE, TX, H, Tiles>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ns2d_stage_x2<STAGE, TX, H, Tiles>, 256, smem);
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (per_sm < 1) per_sm = 1;
-    }
-    return std::min(total_tiles, per_sm * sms);
+        int per_sm = 0, sms = 0;
+        cudaError_t e = cudaFuncSetAttribute(ns2d_stage_x2<STAGE, TX, H, Tiles>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ns2d_stage_x2<STAGE, TX, H, Tiles>, 256, smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        ctas[dev] = std::max(per_sm, 1) * std::max(sms, 1);
+        return e;
+    });
+    const int dev = OncePerDevice::current();
+    const int c = dev >= 0 && ctas[dev] > 0 ? ctas[dev] : kNumSMs;
+    return std::min(total_tiles, c);
 }
 
 template <int STAGE, int TX, int H, class Tiles>

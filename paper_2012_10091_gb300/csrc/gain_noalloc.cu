@@ -58,6 +58,18 @@ cudaError_t scratch_address(double **out) {
     return cudaSuccess;
 }
 
+// true if p is device (or managed) memory of the current device
+bool on_current_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // the query's own error, raised just now
+        return false;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" mgenkf_status mgk_gain_ensemble_noalloc(const double *Y, const double *Z, int32_t n_members,
@@ -78,8 +90,23 @@ extern "C" mgenkf_status mgk_gain_ensemble_noalloc(const double *Y, const double
         mgk_set_error("mgk_gain_ensemble_noalloc: n_obs must be >= 1 and obs_sigma > 0");
         return MGENKF_ERR_INVALID_ARG;
     }
+    if (!on_current_device(Y) || !on_current_device(Z) || !on_current_device(T) ||
+        (info && !on_current_device(info))) {
+        mgk_set_error("mgk_gain_ensemble_noalloc: Y, Z, T (and info, if given) must be device memory "
+                      "of the current device");
+        return MGENKF_ERR_INVALID_ARG;
+    }
+    // An error left pending by earlier, unrelated work would be read back by
+    // the launch check below and reported as this call's failure: report it
+    // now instead, without clearing it, and do nothing.
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        mgk_set_error(std::string("mgk_gain_ensemble_noalloc: an earlier CUDA error is pending (not raised by "
+                                  "this call): ") + cudaGetErrorString(e));
+        return MGENKF_ERR_CUDA;
+    }
     double *base = nullptr;
-    cudaError_t e = scratch_address(&base);
+    e = scratch_address(&base);
     if (e != cudaSuccess) {
         mgk_set_error(std::string("mgk_gain_ensemble_noalloc: scratch address: ") + cudaGetErrorString(e));
         return MGENKF_ERR_CUDA;

@@ -228,6 +228,19 @@ def mgk_normals(seed, tag, ctr0, count, out, stream=None):
 
 
 def mgk_gain_ensemble_noalloc(Y, Z, n_members, n_obs, obs_sigma, T, info=None, stream=None):
+    """Y, Z, T: contiguous float64 CUDA tensors of at least n_members*n_obs,
+    (n_members+1)*n_obs and (n_members+1)*n_members elements; info: optional
+    int32 CUDA tensor.  The library reads and writes exactly those counts."""
+    import torch
+    need = {"Y": (Y, torch.float64, n_members * n_obs), "Z": (Z, torch.float64, (n_members + 1) * n_obs),
+            "T": (T, torch.float64, (n_members + 1) * n_members)}
+    if info is not None:
+        need["info"] = (info, torch.int32, 1)
+    for name, (t, dt, count) in need.items():
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise MGEnKFError(1, "mgk_gain_ensemble_noalloc", f"{name} must be a contiguous {dt} CUDA tensor")
+        if t.numel() < max(count, 0):
+            raise MGEnKFError(1, "mgk_gain_ensemble_noalloc", f"{name} holds {t.numel()} elements, needs {count}")
     _check(lib.mgk_gain_ensemble_noalloc(_ptr(Y), _ptr(Z), n_members, n_obs, obs_sigma, _ptr(T),
                                          _ptr(info), stream), "mgk_gain_ensemble_noalloc")
 

@@ -7,8 +7,12 @@ serves them with a fixed scratch array inside the library.  The test feeds it
 the observation anomalies Y and innovations Z of one analysis of the existing
 entry point (mgenkf_analyse, ensemble-space form, FP64) and compares the two T
 on two calls in a row, so that a stale status word or leftover scratch from
-the first call would show up in the second.  This file sorts last so that a
-run stopping at its first failure has already run every other test."""
+the first call would show up in the second.  The member counts cover the
+smallest ensemble, the one-CTA Cholesky and the largest size the scratch holds
+(the clustered Cholesky and the largest shared-memory solve).  This file sorts
+last so that a run stopping at its first failure has already run every other
+test."""
+import ctypes
 import math
 
 import numpy as np
@@ -30,13 +34,14 @@ def M():
     return mgenkf
 
 
-def test_noalloc_gain_matches_handle_analysis_twice(M):
+@pytest.mark.parametrize("ne", [2, 16, 96, 128])
+def test_noalloc_gain_matches_handle_analysis_twice(M, ne):
     import torch
-    w = W.burgers_custom(512, 4, 96, 70, obs_kind="random", sigma=0.07)
+    w = W.burgers_custom(512, 4, ne, 70, obs_kind="random", sigma=0.07)
     inp = W.make_inputs(w)
     g = M.MGEnKF.from_workload(w, gain_form=M.MGENKF_GAIN_ENSEMBLE, precision="fp64")
     g.set_state(inp["fine0"], inp["members0"])
-    rng = np.random.default_rng(3)
+    rng = np.random.default_rng(3 + ne)
     yo = rng.standard_normal(w.ny) * 0.3
     eps = w.sigma * rng.standard_normal((w.ne, w.ny))
     g.analyse(yo, eps)
@@ -68,3 +73,24 @@ def test_noalloc_gain_rejects_sizes_beyond_its_scratch(M):
     with pytest.raises(M.MGEnKFError) as e:
         M.mgk_gain_ensemble_noalloc(Y, Z, 129, 4, 0.1, T)
     assert e.value.status == 1 and "128" in str(e.value)
+
+
+def test_noalloc_gain_rejects_host_and_short_buffers(M):
+    import torch
+    ne, ny = 8, 5
+    Y = torch.zeros((ne, ny), dtype=torch.float64, device="cuda")
+    Z = torch.zeros((ne + 1, ny), dtype=torch.float64, device="cuda")
+    T = torch.zeros((ne + 1, ne), dtype=torch.float64, device="cuda")
+    # the binding refuses wrong dtypes, host tensors and short buffers
+    for bad in (Y.float(), Y.cpu(), Y[:, :2].contiguous()):
+        with pytest.raises(M.MGEnKFError) as e:
+            M.mgk_gain_ensemble_noalloc(bad, Z, ne, ny, 0.1, T)
+        assert e.value.status == 1
+    # the C entry point itself refuses host memory before launching anything
+    host = np.zeros((ne + 1) * ny)
+    st = M.lib.mgk_gain_ensemble_noalloc(ctypes.c_void_p(host.ctypes.data), ctypes.c_void_p(Z.data_ptr()),
+                                         ne, ny, 0.1, ctypes.c_void_p(T.data_ptr()), None, None)
+    assert st == 1 and b"device memory" in M.lib.mgk_last_error()
+    # and still works afterwards
+    M.mgk_gain_ensemble_noalloc(Y, Z, ne, ny, 0.1, T)
+    torch.cuda.synchronize()

@@ -104,6 +104,20 @@ mgenkf_status mgk_gain_ensemble_noalloc(const double *Y, const double *Z, int32_
                                         int32_t n_obs, double obs_sigma, double *T, int32_t *info,
                                         void *stream);
 
+/* Throughput probe of the FMA pipes.  The paper has no counterpart: this is
+ * the denominator of the arithmetic roofline that the forecast (FP32) and the
+ * Cholesky (FP64) are measured against, since no library routine has the
+ * same pipe mix.  Launches four 256-thread CTAs per SM on `stream`, each thread
+ * running eight independent chains of `iters` fused multiply-adds (FP64 if
+ * fp64 != 0, else FP32), and writes one value per thread into `sink` (device,
+ * mgk_fma_probe_threads() elements of double or float).  *flops (host) is set
+ * to the floating-point operations of the launch (an FMA counts two); the
+ * caller times the launch and divides.  Errors: MGENKF_ERR_INVALID_ARG for
+ * iters < 1 or null pointers, MGENKF_ERR_CUDA for a failed launch. */
+mgenkf_status mgk_fma_probe(int32_t fp64, int32_t iters, void *sink, double *flops, void *stream);
+/* Elements `sink` must hold on the current device (-1 on a CUDA error). */
+int32_t mgk_fma_probe_threads(void);
+
 /* Number of GPU kernels the library has launched in this process so far
  * (every entry point counts its own launches; memsets and copies excluded). */
 uint64_t mgk_kernel_launches(void);

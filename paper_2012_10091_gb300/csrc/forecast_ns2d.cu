@@ -13,21 +13,29 @@
 // t_xx = mu (4/3 u_x - 2/3 v_y), t_xy = mu (u_y + v_x), kappa = mu gamma /
 // ((gamma - 1) Pr).  Every flux telescopes, so the four totals are conserved.
 //
-// GPU design: one launch per RK stage over every grid of the cycle (Ne members
-// and the fine run).  A CTA owns a 32 x 8 tile: it loads the stage input of
-// the tile and its one-point halo (periodic wrap) into shared memory, forms the
-// primitives once per loaded point, and each thread evaluates the 9-point
-// stencil of its point.  Stages: s1 = u0 + k(u0), s2 = u0 + ((s1 - u0) + k(s1))/4,
-// u' = u0 + 2/3 ((s2 - u0) + k(s2)), k = dt L (Shu-Osher form rearranged);
-// s1 and s2 live in two scratch buffers so a stage never overwrites a value
-// another CTA still reads.
+// GPU design, FP32 (the mixed path): one launch per time step over every grid
+// of the cycle (Ne members and the fine run, or every grid of a batch), the
+// three RK stages fused.  A persistent CTA walks tiles of TX x 2H points.  For
+// each tile it copies the step-start state of the tile and a 3-point halo
+// (periodic wrap) into shared memory, then evaluates stage 1 on the tile grown
+// by 2 points, stage 2 on the tile grown by 1 and stage 3 on the tile, each
+// stage reading the previous one from shared memory (the halo points are
+// recomputed by the neighbouring tiles): per point and step the state is read
+// once and written once.  Stages: s1 = u0 + k(u0), s2 = u0 + ((s1 - u0) +
+// k(s1))/4, u' = u0 + 2/3 ((s2 - u0) + k(s2)), k = dt L (Shu-Osher form
+// rearranged).  The step writes a second state buffer (a neighbouring tile may
+// still read the old state's halo), so the steps alternate between the state
+// and one scratch buffer; an odd step count ends with a copy back.
 //
-// FP32 states use a folded variant: a CTA of TX x H threads owns a TX x 2H
-// tile and each thread the two points (x, y) and (x, y + H), held as one
-// float2, so every shared-memory load is 64 bits wide and every arithmetic
-// instruction is a packed FFMA2 / FADD2 / FMUL2 on both points; shared row r
-// of the folded halo holds rows y0 + r - 1 and y0 + H + r - 1.  FP64 states
-// use the scalar tile above.
+// Every thread works on pairs of points folded into float2: shared element
+// (r, c) holds rows r and r + H of the tile's halo block, so every
+// shared-memory access is 64 bits wide and every arithmetic instruction is a
+// packed FFMA2 / FADD2 / FMUL2 on both points.
+//
+// FP64 states use one launch per stage: a CTA owns a 32 x 8 tile, loads the
+// stage input of the tile and its one-point halo into shared memory, forms the
+// primitives once per loaded point, and each thread evaluates the 9-point
+// stencil of its point; s1 and s2 live in two scratch buffers.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -40,9 +48,10 @@
 namespace mgk {
 
 constexpr int kNsTx = 32;
-// tile rows of the per-handle kernel: 16 folded FP32 rows, 8 FP64 rows
+// tile rows of the per-handle kernels: 32 FP32 rows (the fused step, 32 x 32
+// points), 8 FP64 rows
 template <typename T>
-constexpr int ns_tile_rows() { return std::is_same<T, float>::value ? 16 : 8; }
+constexpr int ns_tile_rows() { return std::is_same<T, float>::value ? 32 : 8; }
 
 template <typename T>
 struct NsArgs {
@@ -165,7 +174,7 @@ __device__ __forceinline__ void ns2d_stage_tile(const NsGroup<T> &G, int tile, T
 }
 
 // ---------------------------------------------------------------------------
-// FP32: folded pairs of points in float2, packed arithmetic
+// FP32: folded pairs of points in float2, packed arithmetic, fused RK stages
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -183,14 +192,13 @@ __device__ __forceinline__ int wrap_index(int g, int n) {
     return g;
 }
 
-// 4-byte asynchronous global -> shared copy (cached in L1, where the halo
-// re-reads of neighbouring tiles hit)
-__device__ __forceinline__ void cp_async4(void *smem, const float *gmem) {
+// 16-byte asynchronous global -> shared copy (L2 only: each chunk is read once per tile)
+__device__ __forceinline__ void cp_async16(void *smem, const float *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // where the tiles of a launch come from: a device table of groups (batched
 // path) or the two groups of one handle.  next() moves gi forward to the
@@ -212,15 +220,16 @@ struct PairTiles {
 
 // what every thread needs of one tile, prepared by thread 0 two tiles ahead
 struct TileDesc {
-    const float *in;  // stage input (4 planes of the grid)
-    float *u0;        // state of the grid
-    float *out;       // stage output
+    const float *in;  // step-start state (4 planes of the grid)
+    float *out;       // state after the step
     int n, x0, y0, pad;
     float inv_h, inv_2h, dt, pad2;
 };
 
+// Steps alternate between the grid's state (u0) and its scratch buffer (s1):
+// parity 0 reads u0 and writes s1, parity 1 the reverse.
 template <int TX, int H, class Tiles>
-__device__ __forceinline__ void make_desc(const Tiles &src, int tile, int &gi, int stage, TileDesc *d) {
+__device__ __forceinline__ void make_desc(const Tiles &src, int tile, int &gi, int parity, TileDesc *d) {
     src.next(tile, gi);
     const NsGroup<float> G = src.group(gi);
     const int local = tile - G.tile_begin;
@@ -230,10 +239,9 @@ __device__ __forceinline__ void make_desc(const Tiles &src, int tile, int &gi, i
     const int ty = tt / G.tx;
     const int n = G.n;
     const size_t off = (size_t)prob * 4 * n * n;
-    float *u0 = G.u0 + off;
-    d->u0 = u0;
-    d->in = stage == 0 ? u0 : (stage == 1 ? G.s1 : G.s2) + off;
-    d->out = stage == 0 ? G.s1 + off : (stage == 1 ? G.s2 + off : u0);
+    float *u0 = G.u0 + off, *other = G.s1 + off;
+    d->in = parity ? other : u0;
+    d->out = parity ? u0 : other;
     d->n = n;
     d->x0 = (tt - ty * G.tx) * TX;
     d->y0 = ty * (2 * H);
@@ -242,84 +250,16 @@ __device__ __forceinline__ void make_desc(const Tiles &src, int tile, int &gi, i
     d->dt = G.dt;
 }
 
-template <int TX, int H>
-struct X2Smem {
-    static constexpr int HX = TX + 2, HALO = HX * (H + 2), NT = TX * H;
-    // raw halo: rows y0 - 1 .. y0 + 2H, columns x0 - 4 .. x0 + TX + 3 (16-byte
-    // aligned), 4 planes, row-major
-    static constexpr int RW = TX + 8, RR = 2 * H + 2, RAW = 4 * RR * RW;  // floats
-    static constexpr int CHUNKS = 4 * RR * (RW / 4);                      // 16-byte copies per tile
-    static constexpr int COPIES = (CHUNKS + NT - 1) / NT;                 // per thread
-    // 2 raw buffers, 2 folded buffers of 8 arrays (rho, rho u, rho v, E, u, v, p, T), 4 descriptors
-    static constexpr size_t bytes() {
-        return sizeof(float) * 2 * RAW + sizeof(float2) * 2 * 8 * HALO + 4 * sizeof(TileDesc);
-    }
-};
-
-// 16-byte asynchronous global -> shared copy (L2 only: each chunk is read once per tile)
-__device__ __forceinline__ void cp_async16(void *smem, const float *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-
-// Issue the 16-byte copies of one tile's raw halo into one buffer.  Copy c of
-// a thread is (plane, row, chunk); x0 - 4 and n are multiples of 4, so a
-// chunk never straddles the periodic wrap.
-template <int TX, int H>
-__device__ __forceinline__ void x2_issue(const TileDesc &d, const int (&ck)[X2Smem<TX, H>::COPIES],
-                                         const int (&cr)[X2Smem<TX, H>::COPIES],
-                                         const int (&cx)[X2Smem<TX, H>::COPIES], float *raw) {
-    using S = X2Smem<TX, H>;
-    const int n = d.n, plane = n * n;  // 4 planes of one grid stay below 2^31 elements
-#pragma unroll
-    for (int q = 0; q < S::COPIES; ++q) {
-        const int c = threadIdx.x + q * S::NT;
-        if (c < S::CHUNKS) {
-            const float *src = d.in + ck[q] * plane + wrap_index(d.y0 - 1 + cr[q], n) * n + wrap_index(d.x0 - 4 + cx[q], n);
-            cp_async16(raw + (ck[q] * S::RR + cr[q]) * S::RW + cx[q], src);
-        }
-    }
-}
-
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Fold the raw halo and form the primitives: folded element e (row r, column
-// lx) holds rows r and r + H of the raw block at column lx + 3.  Writes the 8
-// folded arrays rho, rho u, rho v, E, u, v, p, T.
-template <int TX, int H>
-__device__ __forceinline__ void x2_fold(const float *raw, float2 *fold, float gm1) {
-    using S = X2Smem<TX, H>;
-    constexpr int HALO = S::HALO;
-    for (int e = threadIdx.x; e < HALO; e += S::NT) {
-        const int r = e / S::HX, lx = e - r * S::HX;
-        const float *pa = raw + r * S::RW + lx + 3, *pb = pa + H * S::RW;
-        const float2 rho = make_float2(pa[0], pb[0]);
-        const float2 mx = make_float2(pa[S::RR * S::RW], pb[S::RR * S::RW]);
-        const float2 my = make_float2(pa[2 * S::RR * S::RW], pb[2 * S::RR * S::RW]);
-        const float2 E = make_float2(pa[3 * S::RR * S::RW], pb[3 * S::RR * S::RW]);
-        const float2 rinv = make_float2(__fdividef(1.f, rho.x), __fdividef(1.f, rho.y));
-        const float2 u = mul2(mx, rinv), v = mul2(my, rinv);
-        const float2 ke = mul2(mul2(f2(0.5f), rho), fma2(u, u, mul2(v, v)));
-        const float2 p = mul2(f2(gm1), sub2(E, ke));
-        fold[e] = rho;
-        fold[HALO + e] = mx;
-        fold[2 * HALO + e] = my;
-        fold[3 * HALO + e] = E;
-        fold[4 * HALO + e] = u;
-        fold[5 * HALO + e] = v;
-        fold[6 * HALO + e] = p;
-        fold[7 * HALO + e] = mul2(p, rinv);
-    }
-}
-
-// dq/dt of the folded pair at shared index c (9-point stencil)
+// dq/dt of the folded pair at shared index c (9-point stencil); `cons` holds
+// the conserved planes (rho, rho u, rho v, E), `prim` u, v, p, T, each HALO
+// elements long
 template <int HX, int HALO>
-__device__ __forceinline__ void x2_rhs(const float2 *raw, const float2 *prim, int c, float inv_h, float inv_2h,
+__device__ __forceinline__ void x2_rhs(const float2 *cons, const float2 *prim, int c, float inv_h, float inv_2h,
                                        float mu, float kap, float2 (&L)[4]) {
     const int e_ = c + 1, w_ = c - 1, n_ = c + HX, s_ = c - HX;
-    const float2 *Q1 = raw + HALO, *Q2 = raw + 2 * HALO, *Q3 = raw + 3 * HALO;
+    const float2 *Q1 = cons + HALO, *Q2 = cons + 2 * HALO, *Q3 = cons + 3 * HALO;
     const float2 *U = prim, *V = prim + HALO, *P = prim + 2 * HALO, *TT = prim + 3 * HALO;
-    const float2 ih = f2(inv_h), mi2h = f2(-inv_2h);
+    const float2 mi2h = f2(-inv_2h);
     float2 r[4];
     {   // inviscid part: central differences of the nodal fluxes
         const float2 mxe = Q1[e_], mxw = Q1[w_], myn = Q2[n_], mys = Q2[s_];
@@ -377,108 +317,222 @@ __device__ __forceinline__ void x2_rhs(const float2 *raw, const float2 *prim, in
     L[3] = fma2(add2(sub2(fx[1][2], fx[0][2]), sub2(fy[1][2], fy[0][2])), hmh2, r[3]);
 }
 
-// Persistent stage kernel: each CTA walks tiles blockIdx.x, + gridDim.x, ...
-// with one barrier per tile.  In iteration i it copies the raw halo of tile
-// i + 2 (2 raw buffers), folds tile i + 1 and forms its primitives (2 folded
-// buffers) and computes tile i; thread 0 describes tile i + 3 (4 descriptor
-// slots).  Stages 1 and 2 load u0 at the thread's points at the start of the
-// iteration and use it at the end.  At most 85 registers: three CTAs per SM.
-template <int STAGE, int TX, int H, class Tiles>
-__global__ void __launch_bounds__(256, 3) ns2d_stage_x2(Tiles src, int total_tiles, float gm1, float mu, float kap) {
-    using S = X2Smem<TX, H>;
-    constexpr int HX = S::HX, HALO = S::HALO, NT = S::NT;
-    static_assert(NT == 256, "256 threads per CTA");
-    extern __shared__ float4 x2_smem4[];
-    float *raw_base = reinterpret_cast<float *>(x2_smem4);
-    float2 *fold_base = reinterpret_cast<float2 *>(raw_base + 2 * S::RAW);
-    TileDesc *desc = reinterpret_cast<TileDesc *>(fold_base + 2 * 8 * HALO);
+// primitives u, v, p, T of a folded pair of conserved values (one approximate
+// reciprocal of rho per point)
+template <int HALO>
+__device__ __forceinline__ void put_prims(float2 *prim, int f, float2 rho, float2 mx, float2 my, float2 E, float gm1) {
+    const float2 rinv = make_float2(__fdividef(1.f, rho.x), __fdividef(1.f, rho.y));
+    const float2 u = mul2(mx, rinv), v = mul2(my, rinv);
+    const float2 ke = mul2(mul2(f2(0.5f), rho), fma2(u, u, mul2(v, v)));
+    const float2 p = mul2(f2(gm1), sub2(E, ke));
+    prim[f] = u;
+    prim[HALO + f] = v;
+    prim[2 * HALO + f] = p;
+    prim[3 * HALO + f] = mul2(p, rinv);
+}
+
+// Shared memory of the fused step for tiles of TX x 2H points (TX x H folded
+// pairs) with a 3-point halo.
+template <int TX, int H>
+struct StepSmem {
+    static constexpr int NT = 256;                 // threads per CTA
+    static constexpr int FX = TX + 6, FR = H + 6;  // folded block: columns x0-3 .., rows r and r + H of rows y0-3 ..
+    static constexpr int NF = FX * FR;             // folded elements per array
+    // raw block of the step-start state: rows y0 - 3 .. y0 + 2H + 2, columns
+    // x0 - 4 .. x0 + TX + 3 (16-byte aligned), 4 planes, row-major
+    static constexpr int RW = TX + 8, RR = 2 * H + 6, RAW = 4 * RR * RW;  // floats
+    static constexpr int CHUNKS = 4 * RR * (RW / 4);                      // 16-byte copies per tile
+    static constexpr int COPIES = (CHUNKS + NT - 1) / NT;                 // per thread
+    // u0 (4 arrays), the current stage (4), its primitives (4), raw block, 4 descriptors
+    static constexpr size_t bytes() { return sizeof(float2) * 12 * NF + sizeof(float) * RAW + 4 * sizeof(TileDesc); }
+    static_assert((TX * H) % NT == 0, "the last stage gives every thread the same number of pairs");
+};
+
+// Issue the 16-byte copies of one tile's raw block.  Copy c of a thread is
+// (plane, row, chunk); x0 - 4 and n are multiples of 4, so a chunk never
+// straddles the periodic wrap.
+template <int TX, int H>
+__device__ __forceinline__ void step_issue(const TileDesc &d, float *raw) {
+    using S = StepSmem<TX, H>;
+    const int n = d.n, plane = n * n;  // 4 planes of one grid stay below 2^31 elements
+#pragma unroll
+    for (int q = 0; q < S::COPIES; ++q) {
+        const int c = threadIdx.x + q * S::NT;
+        if (c < S::CHUNKS) {
+            // plane k, raw row r, first column x of the chunk (divisions by constants)
+            const int row = c / (S::RW / 4), k = row / S::RR, r = row - k * S::RR, x = 4 * (c - row * (S::RW / 4));
+            const float *src = d.in + k * plane + wrap_index(d.y0 - 3 + r, n) * n + wrap_index(d.x0 - 4 + x, n);
+            cp_async16(raw + row * S::RW + x, src);
+        }
+    }
+}
+
+// Fold the raw block (folded element (r, c) holds raw rows r and r + H at raw
+// column c + 1) into u0 and form its primitives.
+template <int TX, int H>
+__device__ __forceinline__ void step_fold(const float *raw, float2 *Q0, float2 *PR, float gm1) {
+    using S = StepSmem<TX, H>;
+    constexpr int NF = S::NF, PL = S::RR * S::RW;
+    for (int e = threadIdx.x; e < NF; e += S::NT) {
+        const int r = e / S::FX, c = e - r * S::FX;
+        const float *pa = raw + r * S::RW + c + 1, *pb = pa + H * S::RW;
+        const float2 rho = make_float2(pa[0], pb[0]);
+        const float2 mx = make_float2(pa[PL], pb[PL]);
+        const float2 my = make_float2(pa[2 * PL], pb[2 * PL]);
+        const float2 E = make_float2(pa[3 * PL], pb[3 * PL]);
+        Q0[e] = rho;
+        Q0[NF + e] = mx;
+        Q0[2 * NF + e] = my;
+        Q0[3 * NF + e] = E;
+        put_prims<NF>(PR, e, rho, mx, my, E, gm1);
+    }
+}
+
+// Stage K (1 or 2) on the folded block shrunk by K on every side: reads the
+// previous stage (u0 for K = 1) and its primitives, and after a barrier
+// replaces them with this stage's values (the results wait in registers).
+template <int TX, int H, int K>
+__device__ __forceinline__ void step_stage(const float2 *Q0, float2 *QS, float2 *PR, const TileDesc &d, float gm1,
+                                           float mu, float kap) {
+    using S = StepSmem<TX, H>;
+    constexpr int W = S::FX - 2 * K, R = S::FR - 2 * K, N = W * R, E = (N + S::NT - 1) / S::NT, NF = S::NF;
+    const float2 *cons = K == 1 ? Q0 : QS;
+    const float2 dt = f2(d.dt);
+    float2 res[E][4];
+    int fo[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const int e = threadIdx.x + q * S::NT;
+        fo[q] = -1;
+        if (e < N) {
+            const int r = e / W, c = e - r * W;
+            const int f = (r + K) * S::FX + c + K;
+            fo[q] = f;
+            float2 L[4];
+            x2_rhs<S::FX, NF>(cons, PR, f, d.inv_h, d.inv_2h, mu, kap, L);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 kq = mul2(dt, L[k]);
+                const float2 base = Q0[k * NF + f];
+                res[q][k] = K == 1 ? add2(base, kq) : fma2(f2(0.25f), add2(sub2(QS[k * NF + f], base), kq), base);
+            }
+        }
+    }
+    __syncthreads();  // every read of the previous stage is done
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const int f = fo[q];
+        if (f >= 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) QS[k * NF + f] = res[q][k];
+            put_prims<NF>(PR, f, res[q][0], res[q][1], res[q][2], res[q][3], gm1);
+        }
+    }
+    __syncthreads();  // this stage is complete
+}
+
+// Stage 3 on the tile itself, straight to the output state.
+template <int TX, int H>
+__device__ __forceinline__ void step_last(const float2 *Q0, const float2 *QS, const float2 *PR, const TileDesc &d,
+                                          float mu, float kap) {
+    using S = StepSmem<TX, H>;
+    constexpr int E = TX * H / S::NT, NF = S::NF;
+    const float2 dt = f2(d.dt);
+    const int n = d.n, plane = n * n;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const int e = threadIdx.x + q * S::NT;
+        const int r = e / TX, c = e - r * TX;
+        const int f = (r + 3) * S::FX + c + 3;
+        const int x = d.x0 + c, ya = d.y0 + r, yb = ya + H;
+        if (x >= n || ya >= n) continue;
+        float2 L[4];
+        x2_rhs<S::FX, NF>(QS, PR, f, d.inv_h, d.inv_2h, mu, kap, L);
+        float *oa = d.out + ya * n + x, *ob = oa + H * n;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 kq = mul2(dt, L[k]);
+            const float2 base = Q0[k * NF + f];
+            const float2 res = fma2(f2(2.f / 3.f), add2(sub2(QS[k * NF + f], base), kq), base);
+            oa[k * plane] = res.x;
+            if (yb < n) ob[k * plane] = res.y;
+        }
+    }
+}
+
+// One SSP-RK3 step of every tile of a launch.  Persistent: each CTA walks
+// tiles blockIdx.x, + gridDim.x, ...; the raw block of the next tile is
+// copied while the three stages of the current one run; thread 0 describes
+// tiles two ahead (4 descriptor slots).
+template <int TX, int H, int MINB, class Tiles>
+__global__ void __launch_bounds__(256, MINB)
+    ns2d_rk3_step(Tiles src, int total_tiles, int parity, float gm1, float mu, float kap) {
+    using S = StepSmem<TX, H>;
+    constexpr int NF = S::NF;
+    extern __shared__ float4 step_smem4[];
+    float2 *Q0 = reinterpret_cast<float2 *>(step_smem4);
+    float2 *QS = Q0 + 4 * NF;
+    float2 *PR = QS + 4 * NF;
+    float *raw = reinterpret_cast<float *>(PR + 4 * NF);
+    TileDesc *desc = reinterpret_cast<TileDesc *>(raw + S::RAW);
     const int G = gridDim.x;
-    // Stage launches follow one another with programmatic serialisation (see
-    // x2_launch): the next stage may be scheduled from here on, and its CTAs
-    // take the SMs as this launch's CTAs leave; each CTA prepares its first tile
-    // descriptors (static tables only) before it waits for the previous launch
-    // to complete and its writes to be visible.
+    // Steps follow one another with programmatic serialisation (see
+    // step_launch): the next step may be scheduled from here on, and its CTAs
+    // take the SMs as this launch's CTAs leave; each CTA describes its first
+    // tiles (static tables only) before it waits for the previous launch to
+    // complete and its writes to be visible.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     int tile = blockIdx.x;
     if (tile >= total_tiles) return;
     int gi = 0;  // thread 0: group of the last tile it described
     if (threadIdx.x == 0)
-        for (int q = 0; q < 3; ++q)
-            if (tile + q * G < total_tiles) make_desc<TX, H>(src, tile + q * G, gi, STAGE, &desc[q]);
+        for (int q = 0; q < 2; ++q)
+            if (tile + q * G < total_tiles) make_desc<TX, H>(src, tile + q * G, gi, parity, &desc[q]);
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    int ck[S::COPIES], cr[S::COPIES], cx[S::COPIES];  // plane, raw row, first column of the thread's copies
-#pragma unroll
-    for (int q = 0; q < S::COPIES; ++q) {
-        const int c = threadIdx.x + q * NT, row = c / (S::RW / 4), k = row / S::RR;
-        ck[q] = k;
-        cr[q] = row - k * S::RR;
-        cx[q] = 4 * (c - row * (S::RW / 4));
-    }
-    const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-    const int c = (ly + 1) * HX + (lx + 1);
     __syncthreads();
-    x2_issue<TX, H>(desc[0], ck, cr, cx, raw_base);
+    step_issue<TX, H>(desc[0], raw);
     cp_async_commit();
-    if (tile + G < total_tiles) x2_issue<TX, H>(desc[1], ck, cr, cx, raw_base + S::RAW);
-    cp_async_commit();
-    cp_async_wait1();  // tile 0's halo has landed
-    __syncthreads();
-    x2_fold<TX, H>(raw_base, fold_base, gm1);
     for (int it = 0; tile < total_tiles; ++it, tile += G) {
-        cp_async_wait0();  // tile it + 1's halo has landed
-        __syncthreads();   // publishes it and the folded tile it; iteration it - 1 is done everywhere
-        const TileDesc &d = desc[it & 3];
-        const int n = d.n, plane = n * n;
-        const int x = d.x0 + lx, ya = d.y0 + ly, yb = ya + H;
-        const bool ok = x < n && ya < n, has_b = ok && yb < n;
-        float2 b[4];  // u0 at the thread's two points (stages 1, 2), consumed at the end of the iteration
-        if (STAGE != 0) {
-            const float *pa = d.u0 + (ok ? ya * n + x : 0);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                b[k] = make_float2(ok ? pa[k * plane] : 0.f, has_b ? pa[k * plane + H * n] : 0.f);
-        }
-        const bool has1 = tile + G < total_tiles, has2 = tile + 2 * G < total_tiles;
-        if (threadIdx.x == 0 && tile + 3 * G < total_tiles) make_desc<TX, H>(src, tile + 3 * G, gi, STAGE, &desc[(it + 3) & 3]);
-        // tile it + 2 goes to the raw buffer of tile it, folded in iteration it - 1
-        if (has2) x2_issue<TX, H>(desc[(it + 2) & 3], ck, cr, cx, raw_base + (it & 1) * S::RAW);
+        cp_async_wait0();  // this tile's raw block has landed
+        __syncthreads();   // ... for every thread; the previous tile is done everywhere
+        step_fold<TX, H>(raw, Q0, PR, gm1);
+        __syncthreads();   // the raw block is free, u0 and its primitives are ready
+        if (tile + G < total_tiles) step_issue<TX, H>(desc[(it + 1) & 3], raw);
         cp_async_commit();
-        if (has1) x2_fold<TX, H>(raw_base + ((it + 1) & 1) * S::RAW, fold_base + ((it + 1) & 1) * 8 * HALO, gm1);
-        const float2 *fq = fold_base + (it & 1) * 8 * HALO;
-
-        if (ok) {
-            float2 L[4];
-            x2_rhs<HX, HALO>(fq, fq + 4 * HALO, c, d.inv_h, d.inv_2h, mu, kap, L);
-            float *oa = d.out + ya * n + x, *ob = oa + H * n;
-            const float2 dt = f2(d.dt);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float2 kq = mul2(dt, L[k]);
-                const float2 sv = fq[k * HALO + c];
-                float2 res;
-                if (STAGE == 0)
-                    res = add2(sv, kq);
-                else
-                    res = fma2(f2(STAGE == 1 ? 0.25f : 2.f / 3.f), add2(sub2(sv, b[k]), kq), b[k]);
-                oa[k * plane] = res.x;
-                if (has_b) ob[k * plane] = res.y;
-            }
-        }
+        if (threadIdx.x == 0 && tile + 2 * G < total_tiles)
+            make_desc<TX, H>(src, tile + 2 * G, gi, parity, &desc[(it + 2) & 3]);
+        const TileDesc &d = desc[it & 3];
+        step_stage<TX, H, 1>(Q0, QS, PR, d, gm1, mu, kap);
+        step_stage<TX, H, 2>(Q0, QS, PR, d, gm1, mu, kap);
+        step_last<TX, H>(Q0, QS, PR, d, mu, kap);
     }
 }
 
-// CTAs per launch of a persistent stage kernel: resident CTAs per SM x SMs
-template <int STAGE, int TX, int H, class Tiles>
-static int x2_grid(int total_tiles) {
+// After an odd number of steps the states sit in the scratch buffers: copy
+// them back (group blockIdx.y).
+template <class Tiles>
+__global__ void __launch_bounds__(256) ns2d_copy_back(Tiles src) {
+    const NsGroup<float> G = src.group(blockIdx.y);
+    const size_t count = (size_t)G.n * G.n * G.nprob;  // float4 per group: 4 n^2 nprob floats
+    const float4 *s = reinterpret_cast<const float4 *>(G.s1);
+    float4 *d = reinterpret_cast<float4 *>(G.u0);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        d[i] = s[i];
+}
+
+// CTAs per launch of the persistent step kernel: resident CTAs per SM x SMs
+// (per device: the attribute and the occupancy belong to a device context)
+template <int TX, int H, int MINB, class Tiles>
+static int step_grid(int total_tiles) {
     static OncePerDevice once;
-    static int ctas[kMaxDevices];  // resident CTAs per SM x SMs, per device
+    static int ctas[kMaxDevices];
     once.run([](int dev) {
-        const size_t smem = X2Smem<TX, H>::bytes();
+        const size_t smem = StepSmem<TX, H>::bytes();
         int per_sm = 0, sms = 0;
-        cudaError_t e = cudaFuncSetAttribute(ns2d_stage_x2<STAGE, TX, H, Tiles>,
+        cudaError_t e = cudaFuncSetAttribute(ns2d_rk3_step<TX, H, MINB, Tiles>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ns2d_stage_x2<STAGE, TX, H, Tiles>, 256, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ns2d_rk3_step<TX, H, MINB, Tiles>, 256, smem);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         ctas[dev] = std::max(per_sm, 1) * std::max(sms, 1);
         return e;
@@ -488,23 +542,36 @@ static int x2_grid(int total_tiles) {
     return std::min(total_tiles, c);
 }
 
-template <int STAGE, int TX, int H, class Tiles>
-static void x2_launch(const Tiles &src, int total_tiles, float gm1, float mu, float kap, cudaStream_t s) {
-    const int grid = x2_grid<STAGE, TX, H, Tiles>(total_tiles);
+template <int TX, int H, int MINB, class Tiles>
+static void step_launch(const Tiles &src, int total_tiles, int parity, float gm1, float mu, float kap,
+                        cudaStream_t s) {
+    const int grid = step_grid<TX, H, MINB, Tiles>(total_tiles);
     // programmatic stream serialisation: the launch may start while the
     // previous kernel on the stream finishes; the kernel waits for it before
     // it touches the state (griddepcontrol.wait)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = X2Smem<TX, H>::bytes();
+    cfg.dynamicSmemBytes = StepSmem<TX, H>::bytes();
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, ns2d_stage_x2<STAGE, TX, H, Tiles>, src, total_tiles, gm1, mu, kap);
+    cudaLaunchKernelEx(&cfg, ns2d_rk3_step<TX, H, MINB, Tiles>, src, total_tiles, parity, gm1, mu, kap);
+}
+
+// nsteps steps of every tile (the states end in u0), FP32
+template <int TX, int H, int MINB, class Tiles>
+static void step_sequence(const Tiles &src, int ngroups, int total_tiles, int nsteps, float gm1, float mu,
+                          float kap, cudaStream_t s) {
+    for (int st = 0; st < nsteps; ++st) step_launch<TX, H, MINB>(src, total_tiles, st & 1, gm1, mu, kap, s);
+    count_launches(nsteps);
+    if (nsteps & 1) {
+        ns2d_copy_back<Tiles><<<dim3(2 * kNumSMs, ngroups), 256, 0, s>>>(src);
+        count_launches(1);
+    }
 }
 
 // per-handle FP64 launch: two groups (members, fine run) passed by value, 32 x 8 tiles
@@ -564,19 +631,15 @@ cudaError_t ns2d_forecast_scratch(T *whole, int n_whole, int n_whole_probs, T *s
     const int grid = tiles[0] + tiles[1];
     if (grid == 0 || nsteps == 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
-        // the halo is copied in 16-byte chunks
+        // the halo is copied in 16-byte chunks, the copy back in float4
         if ((reinterpret_cast<uintptr_t>(whole) | reinterpret_cast<uintptr_t>(split) |
              reinterpret_cast<uintptr_t>(scratch)) & 15)
             return cudaErrorMisalignedAddress;
         PairTiles P{{A.g[0], A.g[1]}};
         P.g[0].tile_begin = 0;
         P.g[1].tile_begin = tiles[0];
-        for (int s = 0; s < nsteps; ++s) {
-            x2_launch<0, 32, 8>(P, grid, A.gm1, A.mu, A.kappa, stream);
-            x2_launch<1, 32, 8>(P, grid, A.gm1, A.mu, A.kappa, stream);
-            x2_launch<2, 32, 8>(P, grid, A.gm1, A.mu, A.kappa, stream);
-            count_launches(3);
-        }
+        // a group without grids copies nothing back (count 0)
+        step_sequence<32, 16, 2>(P, 2, grid, nsteps, A.gm1, A.mu, A.kappa, stream);
     } else {
         for (int s = 0; s < nsteps; ++s) {
             ns2d_stage_kernel<T, 0><<<grid, 256, 0, stream>>>(A);
@@ -604,46 +667,41 @@ cudaError_t ns2d_forecast(T *whole, int n_whole, int n_whole_probs, T *split, in
     return e != cudaSuccess ? e : e2;
 }
 
-// batched FP32 shapes: threads TX x H, tiles TX x 2H points
-int ns2d_tile_x(int shape) { return shape == 1 ? 16 : (shape == 2 ? 64 : 32); }
-int ns2d_tile_y(int shape) { return 2 * (shape == 1 ? 16 : (shape == 2 ? 4 : 8)); }
+// batched FP32 tile shapes (points per tile): 0 = 32 x 32, 1 = 16 x 32, 2 = 32 x 16
+int ns2d_tile_x(int shape) { return shape == 1 ? 16 : 32; }
+int ns2d_tile_y(int shape) { return shape == 2 ? 16 : 32; }
 
-template <int TX, int H>
-static void launch_table(const NsGroup<float> *groups, int ngroups, int tiles, int nsteps, int first_stage,
-                         int last_stage, float gm1, float mu, float kappa, cudaStream_t s) {
-    const TableTiles src{groups, ngroups};
-    for (int st = 0; st < nsteps; ++st) {
-        for (int k = first_stage; k <= last_stage; ++k) {
-            if (k == 0) x2_launch<0, TX, H>(src, tiles, gm1, mu, kappa, s);
-            if (k == 1) x2_launch<1, TX, H>(src, tiles, gm1, mu, kappa, s);
-            if (k == 2) x2_launch<2, TX, H>(src, tiles, gm1, mu, kappa, s);
-        }
-        count_launches(last_stage - first_stage + 1);
-    }
-}
-
-static cudaError_t table_stages(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, int nsteps,
-                                int first_stage, int last_stage, double gamma, double mu, double prandtl,
-                                cudaStream_t s) {
+static cudaError_t table_steps(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, int nsteps,
+                               bool probe, double gamma, double mu, double prandtl, cudaStream_t s) {
     if (tiles == 0 || nsteps == 0) return cudaSuccess;
     const float gm1 = (float)(gamma - 1.0), m = (float)mu, kap = (float)(mu * gamma / ((gamma - 1.0) * prandtl));
-    if (shape == 1)
-        launch_table<16, 16>(d_groups, ngroups, tiles, nsteps, first_stage, last_stage, gm1, m, kap, s);
-    else if (shape == 2)
-        launch_table<64, 4>(d_groups, ngroups, tiles, nsteps, first_stage, last_stage, gm1, m, kap, s);
-    else
-        launch_table<32, 8>(d_groups, ngroups, tiles, nsteps, first_stage, last_stage, gm1, m, kap, s);
+    const TableTiles src{d_groups, ngroups};
+    if (probe) {  // one step into the scratch buffers: the states stay as they are
+        if (shape == 1)
+            step_launch<16, 16, 2>(src, tiles, 0, gm1, m, kap, s);
+        else if (shape == 2)
+            step_launch<32, 8, 2>(src, tiles, 0, gm1, m, kap, s);
+        else
+            step_launch<32, 16, 2>(src, tiles, 0, gm1, m, kap, s);
+        count_launches(1);
+    } else if (shape == 1) {
+        step_sequence<16, 16, 2>(src, ngroups, tiles, nsteps, gm1, m, kap, s);
+    } else if (shape == 2) {
+        step_sequence<32, 8, 2>(src, ngroups, tiles, nsteps, gm1, m, kap, s);
+    } else {
+        step_sequence<32, 16, 2>(src, ngroups, tiles, nsteps, gm1, m, kap, s);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t ns2d_forecast_table(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, int nsteps,
                                 double gamma, double mu, double prandtl, cudaStream_t s) {
-    return table_stages(d_groups, ngroups, tiles, shape, nsteps, 0, 2, gamma, mu, prandtl, s);
+    return table_steps(d_groups, ngroups, tiles, shape, nsteps, false, gamma, mu, prandtl, s);
 }
 
-cudaError_t ns2d_probe_stages01(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, double gamma,
-                                double mu, double prandtl, cudaStream_t s) {
-    return table_stages(d_groups, ngroups, tiles, shape, 1, 0, 1, gamma, mu, prandtl, s);
+cudaError_t ns2d_probe_step(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, double gamma,
+                            double mu, double prandtl, cudaStream_t s) {
+    return table_steps(d_groups, ngroups, tiles, shape, 1, true, gamma, mu, prandtl, s);
 }
 
 #define MGK_NS_INST(T)                                                                            \

@@ -1251,8 +1251,8 @@ extern "C" mgenkf_status mgenkf_batch_sync(mgenkf_batch_t b) {
     return first;
 }
 
-// Time stages 0 and 1 (they write only the stage buffers) of every grid size
-// with every tile shape and keep the fastest shape per size.
+// Time one step into the scratch buffers (the states are not touched) of
+// every grid size with every tile shape and keep the fastest shape per size.
 extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
     if (!b || reps < 1) return MGENKF_ERR_INVALID_ARG;
     b->err.clear();
@@ -1274,7 +1274,7 @@ extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
             float ms = 0.f;
             for (int r = 0; r <= reps; ++r) {  // first repetition warms up
                 B_CUDA(cudaEventRecord(t0, b->s0));
-                cudaError_t e = ns2d_probe_stages01(d, ng, tiles, sh, b->gamma, b->mu, b->prandtl, b->s0);
+                cudaError_t e = ns2d_probe_step(d, ng, tiles, sh, b->gamma, b->mu, b->prandtl, b->s0);
                 if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
                 B_CUDA(cudaEventRecord(t1, b->s0));
                 B_CUDA(cudaEventSynchronize(t1));

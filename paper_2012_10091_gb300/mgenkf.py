@@ -75,6 +75,7 @@ def _load():
         "mgk_forecast": [i32, i32, P, i32, i32, f64, f64, f64, f64, f64, i32, P],
         "mgk_normals": [u64, u64, u64, i64, P, P],
         "mgk_gain_ensemble_noalloc": [P, P, i32, i32, f64, P, P, P],
+        "mgk_fma_probe": [i32, i32, P, ctypes.POINTER(f64), P],
         "mgk_cnn_create": [i32, i32, ctypes.POINTER(P)],
         "mgk_cnn_destroy": [P],
         "mgk_cnn_set_params": [P, P, P],
@@ -116,6 +117,8 @@ def _load():
     L.mgk_kernel_launches.restype = ctypes.c_uint64
     L.mgk_last_error.argtypes = []
     L.mgk_last_error.restype = ctypes.c_char_p
+    L.mgk_fma_probe_threads.argtypes = []
+    L.mgk_fma_probe_threads.restype = ctypes.c_int32
     return L
 
 
@@ -225,6 +228,17 @@ def mgk_forecast(model, precision, state, nprob, n, length, dt, nu, gamma=1.4, p
 
 def mgk_normals(seed, tag, ctr0, count, out, stream=None):
     _check(lib.mgk_normals(seed, tag, ctr0, count, _ptr(out), stream), "mgk_normals")
+
+
+def mgk_fma_probe(fp64, iters, sink, stream=None) -> float:
+    """Launch the FMA throughput probe; returns the launch's flop count."""
+    fl = ctypes.c_double()
+    _check(lib.mgk_fma_probe(int(bool(fp64)), iters, _ptr(sink), ctypes.byref(fl), stream), "mgk_fma_probe")
+    return fl.value
+
+
+def mgk_fma_probe_threads() -> int:
+    return int(lib.mgk_fma_probe_threads())
 
 
 def mgk_gain_ensemble_noalloc(Y, Z, n_members, n_obs, obs_sigma, T, info=None, stream=None):
@@ -447,7 +461,7 @@ class MGEnKF:
 # ---------------------------------------------------------------------------
 # batches of independent NS-2D problems (mgenkf_batch_* in include/mgenkf.h)
 # ---------------------------------------------------------------------------
-TILE_SHAPES = {0: (32, 16), 1: (16, 32), 2: (64, 8)}   # points per tile (x, y)
+TILE_SHAPES = {0: (32, 32), 1: (16, 32), 2: (32, 16)}   # points per tile (x, y)
 
 
 def _bcheck(st, where, b):

@@ -196,3 +196,25 @@ def test_batch_on_a_nonblocking_stream(M):
         np.testing.assert_array_equal(f1, f0)
         np.testing.assert_array_equal(m1, m0)
     b.close()
+
+
+def test_batch_at_multi_tile_sizes_matches_oracle(M):
+    """Problems of the batched workload's own sizes (coarse 64^2-128^2, fine 4x
+    per side, 16-32 members), so that each persistent stage CTA walks many
+    tiles (about 7,000 tiles of 32 x 32 points per launch over 2 x 152
+    resident CTAs), against the CPU oracle over two cycles."""
+    ws = W.ns2d_batch(nprob=8, seed=5, coarse=(64, 96, 128), members=(16, 32), n_obs=(256, 512))
+    cycles = 2
+    inps, yos = _inputs(ws, cycles)
+    b = M.Batch(_runs(M, ws, inps))
+    got = _batched(M, b, ws, yos, [10] * cycles)
+    for j, (w, inp) in enumerate(zip(ws, inps)):
+        mg = O.MGEnKF(w.model, w.nf, w.ratio, w.length, w.dt, inp["fine0"], inp["members0"], inp["obs_idx"],
+                      inp["obs_var"], w.sigma, w.seed, nu=w.nu, gamma=w.gamma, prandtl=w.prandtl, gain_form=1)
+        for k in range(cycles):
+            mg.forecast(10)
+            assert mg.analyse(yos[j][k]) == 0
+            mg.prolong_correct()
+        assert rel_err(got[j][0], mg.fine) < 1e-3
+        assert rel_err(got[j][1], mg.members) < 1e-3
+    b.close()

@@ -74,6 +74,35 @@ def test_ns2d_fp32_matches_oracle(M):
         assert np.max(np.abs(got[:, k] - ref[:, k])) <= 2e-5 * np.max(np.abs(ref[:, k])), k
 
 
+@pytest.mark.parametrize("n,nprob", [(264, 16), (1032, 1)])
+def test_ns2d_fp32_multi_tile_matches_oracle(M, n, nprob):
+    # Sizes at which the persistent FP32 forecast walks several tiles per CTA
+    # with a ragged last tile in x and y (264 = 8.25 x 32, 1032 = 32.25 x 32):
+    # 16 x 264^2 is 16 x 9 x 9 = 1296 tiles of 32 x 32 points over 2 x 152
+    # resident CTAs (4.3 tiles per CTA); 1032^2 is 33 x 33 = 1089 (3.6 per CTA).
+    import torch
+    q0 = _smooth_states(nprob, n, 11)
+    h, mu, steps = 1.0 / n, 1e-3, 10
+    dt = min(0.2 * h, 0.1 * h * h * (GAMMA - 1) * PR / (mu * GAMMA) * 2)
+    ref = O.ns2d_rk3(q0, h, GAMMA, mu, PR, dt, steps)
+    d = torch.tensor(q0, dtype=torch.float32, device="cuda")
+    M.mgk_forecast(M.MGENKF_NS2D, M.MGENKF_MIXED, d, nprob, n, 1.0, dt, mu, GAMMA, PR, nsteps=steps)
+    torch.cuda.synchronize()
+    got = d.cpu().double().numpy()
+    # element-wise, each plane against its own maximum: FP32 rounding of O(10)
+    # energies over 10 steps of 3 stages
+    for k in range(4):
+        assert np.max(np.abs(got[:, k] - ref[:, k])) <= 2e-5 * np.max(np.abs(ref[:, k])), k
+    # an odd step count ends in the state buffer as well
+    d = torch.tensor(q0, dtype=torch.float32, device="cuda")
+    M.mgk_forecast(M.MGENKF_NS2D, M.MGENKF_MIXED, d, nprob, n, 1.0, dt, mu, GAMMA, PR, nsteps=3)
+    torch.cuda.synchronize()
+    ref3 = O.ns2d_rk3(q0, h, GAMMA, mu, PR, dt, 3)
+    got3 = d.cpu().double().numpy()
+    for k in range(4):
+        assert np.max(np.abs(got3[:, k] - ref3[:, k])) <= 1e-5 * np.max(np.abs(ref3[:, k])), k
+
+
 def test_ns2d_rejects_bad_sizes(M):
     import torch
     d = torch.zeros(4 * 12 * 12, dtype=torch.float64, device="cuda")

@@ -989,7 +989,7 @@ def run_gpu_batched(args, dist):
             "data": "synthetic",
             "config": {"workload": f"ns2d_batch{len(ws_all)}_seed0", "problems": len(ws_all),
                        "problems_rank0": len(ws), "steps_per_cycle": nsteps, "precision": "mixed",
-                       "gain_form": "ensemble-space", "tiles": {str(k): list(M.TILE_SHAPES[v]) for k, v in
+                       "gain_form": "ensemble-space", "segment_rows": {str(k): M.SEGMENT_ROWS[v] for k, v in
                                                                 sorted(tiles.items())},
                        "tile_table": tuned, "autotune_s": t_tune,
                        "l2": f"not flushed: working set {sum(4 * 4 * (3 * problem_work(w)) for w in ws) / 1e9:.2f} GB "

@@ -263,8 +263,9 @@ mgenkf_status mgenkf_dual_destroy(mgenkf_dual_t d);
 /* ---- batches of independent problems -------------------------------------
  * Many independent NS-2D MGEnKF problems (uneven grid sizes, ensemble sizes
  * and observation counts) advanced together: the forecast of every problem's
- * members and fine run is one launch sequence per tile shape over a table of
- * all grids, and each problem's analysis and prolongation run on one of 16
+ * members and fine run is one launch per model step and grid size over a
+ * table of all grids of that size (the sizes on separate streams), and each
+ * problem's analysis and prolongation run on one of 16
  * streams (MGENKF_BATCH_STREAMS overrides: 1 to 128).  The whole cycle is captured once into a CUDA graph and replayed by
  * one graph launch per cycle (recaptured if nsteps changes).  The handles stay
  * owned by the caller and must outlive the batch; they must all be
@@ -286,11 +287,12 @@ mgenkf_status mgenkf_batch_cycle(mgenkf_batch_t b, int32_t nsteps, const double 
 mgenkf_status mgenkf_batch_forecast(mgenkf_batch_t b, int32_t nsteps);
 /* wait for the batch stream; returns the first device status of any problem */
 mgenkf_status mgenkf_batch_sync(mgenkf_batch_t b);
-/* Autotuner: for every grid size time `reps` repetitions of the first two RK
- * stages (which write only scratch) with each tile shape (points per tile
- * 0 = 32x16, 1 = 16x32, 2 = 64x8) and keep the fastest.  Synchronous; invalidates the captured graph. */
+/* Autotuner: for every grid size time `reps` repetitions of one model step
+ * (written to scratch: the states are not touched) with each segment choice
+ * of the forecast (rows per segment of the column march: 0 = 32, 1 = 16,
+ * 2 = 64) and keep the fastest.  Synchronous; invalidates the captured graph. */
 mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps);
-/* read (up to max entries) / set the tile shape chosen per grid size */
+/* read (up to max entries) / set the segment choice per grid size (`shapes`) */
 mgenkf_status mgenkf_batch_tiles(mgenkf_batch_t b, int32_t *sizes, int32_t *shapes, int32_t max, int32_t *count);
 mgenkf_status mgenkf_batch_set_tiles(mgenkf_batch_t b, const int32_t *sizes, const int32_t *shapes, int32_t count);
 const char *mgenkf_batch_last_error(mgenkf_batch_t b);

@@ -39,6 +39,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <algorithm>
 #include <type_traits>
 
@@ -178,8 +179,16 @@ __device__ __forceinline__ void ns2d_stage_tile(const NsGroup<T> &G, int tile, T
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-// a - b with one rounding (b * -1 is exact)
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
+// a - b with one rounding (packed subtraction; no constant operand)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
@@ -200,17 +209,18 @@ __device__ __forceinline__ void cp_async16(void *smem, const float *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// ---------------------------------------------------------------------------
+// The FP32 step on 2-D tiles (the per-handle path: the members and the fine
+// run in one persistent launch).  A CTA walks tiles of TX x 2H points; for each
+// it copies the step-start state of the tile and a 3-point halo into shared
+// memory, evaluates stage 1 on the tile grown by 2 points, stage 2 on the
+// tile grown by 1 and stage 3 on the tile, each stage reading the previous
+// one from shared memory.  Shared element (r, c) holds rows r and r + H of the
+// halo block (one float2).
+// ---------------------------------------------------------------------------
 // where the tiles of a launch come from: a device table of groups (batched
 // path) or the two groups of one handle.  next() moves gi forward to the
 // group holding `tile`; a CTA visits its tiles in increasing order.
-struct TableTiles {
-    const NsGroup<float> *groups;
-    int ngroups;
-    __device__ __forceinline__ void next(int tile, int &gi) const {
-        while (gi + 1 < ngroups && groups[gi + 1].tile_begin <= tile) ++gi;
-    }
-    __device__ __forceinline__ NsGroup<float> group(int gi) const { return groups[gi]; }
-};
 struct PairTiles {
     NsGroup<float> g[2];  // g[1].tile_begin = tiles of g[0]
     __device__ __forceinline__ void next(int tile, int &gi) const { gi = tile < g[1].tile_begin ? 0 : 1; }
@@ -508,10 +518,359 @@ __global__ void __launch_bounds__(256, MINB)
     }
 }
 
+// ---------------------------------------------------------------------------
+// The FP32 step as a column march.  A CTA owns a band of columns of one grid
+// and a segment of its rows; thread t owns the column pair (c0 + t, c0 + t +
+// T) as one float2 (T = blockDim.x).  With one band the pair spans the whole
+// periodic width (c0 = 0, 2T = n); with several bands (n > 512) each band
+// carries a 3-column halo on both sides, recomputed by its neighbours.  The
+// CTA marches down the rows of its segment: in step j it loads row j of the
+// step-start state (3 rows above the segment first), evaluates stage 1 one row
+// behind, stage 2 three rows behind and stage 3 five rows behind, and stores
+// the new state's row.  Each stage keeps the three rows of its input around
+// the row it evaluates in registers (its own columns); only the east and west
+// neighbours come from shared memory, through ring buffers of the last rows
+// each stage published (one barrier per step).  The face between two rows is
+// evaluated once and carried to the next row.
+// ---------------------------------------------------------------------------
+// one row of a stage input at the thread's column pair
+struct Rec {
+    float2 rho, mx, my, E, U, V, P, T;
+};
+
+// primitives u, v, p, T of a pair of conserved values (one approximate
+// reciprocal of rho per point)
+__device__ __forceinline__ Rec make_rec(float2 rho, float2 mx, float2 my, float2 E, float gm1) {
+    Rec r;
+    r.rho = rho;
+    r.mx = mx;
+    r.my = my;
+    r.E = E;
+    const float2 rinv = make_float2(__fdividef(1.f, rho.x), __fdividef(1.f, rho.y));
+    r.U = mul2(mx, rinv);
+    r.V = mul2(my, rinv);
+    const float2 ke = mul2(mul2(f2(0.5f), rho), fma2(r.U, r.U, mul2(r.V, r.V)));
+    r.P = mul2(f2(gm1), sub2(E, ke));
+    r.T = mul2(r.P, rinv);
+    return r;
+}
+
+// Viscous and heat fluxes of one face, in units of mu/h (pure-number stress
+// coefficients; the 1/2 of the face velocities and a factor 2 on the heat
+// flux are in the final 1/(2h) of the energy equation).  tU, tV: sums of the
+// two central tangential differences of u and v across the face.
+struct Face {
+    float2 f0, f1, f2;
+};
+// x-face between columns a and b = a + 1: (t_xx, t_xy, 2 x (work + heat))
+__device__ __forceinline__ Face face_x(float2 Ua, float2 Ub, float2 Va, float2 Vb, float2 tU, float2 tV, float2 Ta,
+                                       float2 Tb, float2 k2) {
+    const float2 dU = sub2(Ub, Ua), dV = sub2(Vb, Va);
+    const float2 txx = fma2(f2(4.f / 3.f), dU, mul2(f2(-1.f / 6.f), tV)), txy = fma2(f2(0.25f), tU, dV);
+    Face F;
+    F.f0 = txx;
+    F.f1 = txy;
+    F.f2 = fma2(txx, add2(Ua, Ub), fma2(txy, add2(Va, Vb), mul2(k2, sub2(Tb, Ta))));
+    return F;
+}
+// y-face between rows a and b = a + 1: (t_xy, t_yy, 2 x (work + heat))
+__device__ __forceinline__ Face face_y(float2 Ua, float2 Ub, float2 Va, float2 Vb, float2 tU, float2 tV, float2 Ta,
+                                       float2 Tb, float2 k2) {
+    const float2 dU = sub2(Ub, Ua), dV = sub2(Vb, Va);
+    const float2 tyy = fma2(f2(4.f / 3.f), dV, mul2(f2(-1.f / 6.f), tU)), txy = fma2(f2(0.25f), tV, dU);
+    Face F;
+    F.f0 = txy;
+    F.f1 = tyy;
+    F.f2 = fma2(txy, add2(Ua, Ub), fma2(tyy, add2(Va, Vb), mul2(k2, sub2(Tb, Ta))));
+    return F;
+}
+
+// Shared ring buffers of the march, float2 per thread (T threads; each ring
+// row holds T + 2 pairs: slot t + 1 is thread t's pair, slot 0 the last
+// thread's pair and slot T + 1 the first thread's pair, both with their halves
+// swapped, so that the east and west neighbours across the fold are plain
+// loads):
+//   rows [4k + s]:           u of stage input k (k = 0 u0, 1 s1, 2 s2), ring slot s of 4
+//   rows [12 + 4k + s]:      v
+//   rows [24 + 12k + 3f + s]: rho u, E, p, T (f = 0..3) of stage input k, ring slot s of 3
+//   rows [60 + 4s + f]:      rho, rho u, rho v, E of u0, ring slot s of 8 (own column only)
+constexpr int kMarchRows = 92;
+// shared bytes of a march CTA of T threads
+__host__ __device__ __forceinline__ size_t march_smem_bytes(int threads) {
+    return sizeof(float2) * kMarchRows * (size_t)(threads + 2);
+}
+constexpr int kMarchMaxThreads = 256;
+constexpr int kMarchBandMax = 2 * kMarchMaxThreads - 6;  // output columns of a band (even)
+
+// Thread t's slot in a ring row (row pitch T + 2), and the slot that holds its
+// pair swapped for the thread at the other end of the fold (-1: none).
+struct Slot {
+    int own, mirror;
+};
+
+__device__ __forceinline__ void put_pair(float2 *row, const Slot &sl, float2 v) {
+    row[sl.own] = v;
+    if (sl.mirror >= 0) row[sl.mirror] = make_float2(v.y, v.x);
+}
+
+__device__ __forceinline__ void march_publish(float2 *X, int P, const Slot &sl, int k, int j, const Rec &r) {
+    put_pair(X + (4 * k + (j & 3)) * P, sl, r.U);
+    put_pair(X + (12 + 4 * k + (j & 3)) * P, sl, r.V);
+    float2 *F = X + (24 + 12 * k + j % 3) * P;
+    put_pair(F, sl, r.mx);
+    put_pair(F + 3 * P, sl, r.E);
+    put_pair(F + 6 * P, sl, r.P);
+    put_pair(F + 9 * P, sl, r.T);
+}
+
+// east / west neighbour of the thread's pair in a ring row: the pair of thread
+// t + 1 (t - 1), across the fold the mirrored pair of the other end
+struct Nbr {
+    int te, tw;  // slots t + 2 and t
+    __device__ __forceinline__ float2 e(const float2 *row) const { return row[te]; }
+    __device__ __forceinline__ float2 w(const float2 *row) const { return row[tw]; }
+};
+
+// Stage input k, evaluated in step j at the centre row c of the window
+// (T: ring row pitch)
+// (m1, c, p1 published in steps j - 2, j - 1, j).  yf: in, the face between
+// m1 and c (carried from the previous step); out, the face between c and p1.
+// FULL = false computes only that face (the step before a stage's first row).
+template <bool FULL>
+__device__ __forceinline__ void march_rhs(const float2 *X, int T, const Nbr &nb, int k, int j, const Rec &m1,
+                                          const Rec &c, const Rec &p1, float inv_h, float inv_2h, float mu,
+                                          float kap, Face &yf, float2 (&L)[4]) {
+    const float2 *XU = X + 4 * k * T, *XV = X + (12 + 4 * k) * T;
+    const int sm = ((j - 2) & 3) * T, sc = ((j - 1) & 3) * T, sp = (j & 3) * T;
+    const float2 k2 = f2(mu > 0.f ? 2.f * kap / mu : 0.f);
+    const float2 Uec = nb.e(XU + sc), Uwc = nb.w(XU + sc), Vec = nb.e(XV + sc), Vwc = nb.w(XV + sc);
+    const float2 Uep = nb.e(XU + sp), Uwp = nb.w(XU + sp), Vep = nb.e(XV + sp), Vwp = nb.w(XV + sp);
+    // face between c and p1
+    const Face top = face_y(c.U, p1.U, c.V, p1.V, add2(sub2(Uec, Uwc), sub2(Uep, Uwp)),
+                            add2(sub2(Vec, Vwc), sub2(Vep, Vwp)), c.T, p1.T, k2);
+    if (FULL) {
+        const float2 Uem = nb.e(XU + sm), Uwm = nb.w(XU + sm), Vem = nb.e(XV + sm), Vwm = nb.w(XV + sm);
+        const float2 *XF = X + (24 + 12 * k + (j - 1) % 3) * T;
+        const float2 mxe = nb.e(XF), mxw = nb.w(XF), Ee = nb.e(XF + 3 * T), Ew = nb.w(XF + 3 * T);
+        const float2 Pe = nb.e(XF + 6 * T), Pw = nb.w(XF + 6 * T), Te = nb.e(XF + 9 * T), Tw = nb.w(XF + 9 * T);
+        // inviscid part: central differences of the nodal fluxes
+        const float2 mi2h = f2(-inv_2h);
+        const float2 myn = p1.my, mys = m1.my;
+        const float2 Fe1 = fma2(mxe, Uec, Pe), Fw1 = fma2(mxw, Uwc, Pw);
+        const float2 Fe2 = mul2(mxe, Vec), Fw2 = mul2(mxw, Vwc);
+        const float2 Fe3 = mul2(add2(Ee, Pe), Uec), Fw3 = mul2(add2(Ew, Pw), Uwc);
+        const float2 Gn1 = mul2(myn, p1.U), Gs1 = mul2(mys, m1.U);
+        const float2 Gn2 = fma2(myn, p1.V, p1.P), Gs2 = fma2(mys, m1.V, m1.P);
+        const float2 Gn3 = mul2(add2(p1.E, p1.P), p1.V), Gs3 = mul2(add2(m1.E, m1.P), m1.V);
+        const float2 r0 = mul2(add2(sub2(mxe, mxw), sub2(myn, mys)), mi2h);
+        const float2 r1 = mul2(add2(sub2(Fe1, Fw1), sub2(Gn1, Gs1)), mi2h);
+        const float2 r2 = mul2(add2(sub2(Fe2, Fw2), sub2(Gn2, Gs2)), mi2h);
+        const float2 r3 = mul2(add2(sub2(Fe3, Fw3), sub2(Gn3, Gs3)), mi2h);
+        // x-faces of the centre row
+        const Face fw = face_x(Uwc, c.U, Vwc, c.V, add2(sub2(Uwp, Uwm), sub2(p1.U, m1.U)),
+                               add2(sub2(Vwp, Vwm), sub2(p1.V, m1.V)), Tw, c.T, k2);
+        const Face fe = face_x(c.U, Uec, c.V, Vec, add2(sub2(p1.U, m1.U), sub2(Uep, Uem)),
+                               add2(sub2(p1.V, m1.V), sub2(Vep, Vem)), c.T, Te, k2);
+        const float2 mh2 = f2(mu * inv_h * inv_h), hmh2 = f2(0.5f * mu * inv_h * inv_h);
+        L[0] = r0;
+        L[1] = fma2(add2(sub2(fe.f0, fw.f0), sub2(top.f0, yf.f0)), mh2, r1);
+        L[2] = fma2(add2(sub2(fe.f1, fw.f1), sub2(top.f1, yf.f1)), mh2, r2);
+        L[3] = fma2(add2(sub2(fe.f2, fw.f2), sub2(top.f2, yf.f2)), hmh2, r3);
+    }
+    yf = top;
+}
+
+// one unit of a march launch: a band and a row segment of one grid
+struct MarchUnit {
+    const float *in;  // step-start state of the grid (4 planes)
+    float *out;       // state after the step
+    int n, c0, y0, rows;  // points per side, first column (may be negative), first row, rows of the segment
+    int ilo, ihi;         // output columns: pair index i (t or t + T) in [ilo, ihi)
+    float inv_h, inv_2h, dt;
+};
+
+// bands and row segments of one n x n grid (host and device agree)
+__host__ __device__ __forceinline__ int march_bands(int n) {
+    return n <= 2 * kMarchMaxThreads ? 1 : (n + kMarchBandMax - 1) / kMarchBandMax;
+}
+__host__ __device__ __forceinline__ int march_band_width(int n, int bands) {
+    if (bands == 1) return n;
+    const int w = (n + bands - 1) / bands;
+    return w + (w & 1);
+}
+__host__ __device__ __forceinline__ int march_threads(int n) {
+    const int b = march_bands(n);
+    return b == 1 ? n / 2 : (march_band_width(n, b) + 6) / 2;
+}
+
+__device__ __forceinline__ MarchUnit march_unit(const NsGroup<float> &G, int local, int parity) {
+    const int per_grid = G.tx * G.ty;
+    const int prob = local / per_grid;
+    const int rem = local - prob * per_grid;
+    const int band = rem / G.ty, seg = rem - band * G.ty;
+    const int n = G.n;
+    const size_t off = (size_t)prob * 4 * n * n;
+    float *u0 = G.u0 + off, *other = G.s1 + off;
+    MarchUnit u;
+    u.in = parity ? other : u0;
+    u.out = parity ? u0 : other;
+    u.n = n;
+    const int S = (n + G.ty - 1) / G.ty;
+    u.y0 = seg * S;
+    u.rows = min(S, n - u.y0);
+    if (G.tx == 1) {
+        u.c0 = 0;
+        u.ilo = 0;
+        u.ihi = n;
+    } else {
+        const int bw = march_band_width(n, G.tx), bx0 = band * bw;
+        u.c0 = bx0 - 3;
+        u.ilo = 3;
+        u.ihi = 3 + min(bw, n - bx0);
+    }
+    u.inv_h = G.inv_h;
+    u.inv_2h = G.inv_2h;
+    u.dt = G.dt;
+    return u;
+}
+
+// where the units of a launch come from: a device table of groups of one grid
+// size (batched path) or one group passed by value
+struct TableUnits {
+    const NsGroup<float> *groups;
+    int ngroups;
+    __device__ __forceinline__ MarchUnit unit(int u, int parity) const {
+        int gi = 0;
+        while (gi + 1 < ngroups && groups[gi + 1].tile_begin <= u) ++gi;
+        const NsGroup<float> G = groups[gi];
+        return march_unit(G, u - G.tile_begin, parity);
+    }
+    __device__ __forceinline__ NsGroup<float> group(int gi) const { return groups[gi]; }
+};
+struct OneUnits {
+    NsGroup<float> g;
+    __device__ __forceinline__ MarchUnit unit(int u, int parity) const { return march_unit(g, u, parity); }
+    __device__ __forceinline__ NsGroup<float> group(int) const { return g; }
+};
+
+// One SSP-RK3 step of one unit per CTA (blockDim.x = march_threads(n) of the
+// launch's grid size).  Step j of the march: rows of u0 arrive in steps
+// 0 .. rows + 5 (rows y0 - 3 .. y0 + rows + 2); stage 1 evaluates row
+// y0 - 4 + j in steps 2 .. rows + 5, stage 2 row y0 - 6 + j in steps
+// 5 .. rows + 6, stage 3 row y0 - 8 + j in steps 8 .. rows + 7; a stage's
+// output row is published one step after it is computed.
+template <class Units>
+__global__ void __launch_bounds__(kMarchMaxThreads, 1)
+    ns2d_rk3_march(Units src, int parity, float gm1, float mu, float kap) {
+    extern __shared__ float4 march_smem4[];
+    float2 *X = reinterpret_cast<float2 *>(march_smem4);
+    const int T = blockDim.x, t = threadIdx.x, P = T + 2;  // threads, ring row pitch
+    // Steps follow one another with programmatic serialisation (see
+    // march_launch): the next step may be scheduled from here on; each CTA
+    // decodes its unit (static tables only) before it waits for the previous
+    // launch to complete and its writes to be visible.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const MarchUnit u = src.unit(blockIdx.x, parity);
+    Nbr nb;
+    nb.te = t + 2;
+    nb.tw = t;
+    Slot sl;
+    sl.own = t + 1;
+    sl.mirror = t == 0 ? T + 1 : (t == T - 1 ? 0 : -1);
+    if (T == 1) sl.mirror = -1;  // never: T = n/2 >= 4
+    const int n = u.n, plane = n * n;  // 4 planes of one grid stay below 2^31 elements
+    const int xa = wrap_index(u.c0 + t, n), xb = wrap_index(u.c0 + t + T, n);
+    const bool wa = t >= u.ilo && t < u.ihi, wb = t + T >= u.ilo && t + T < u.ihi;
+    const int R = u.rows;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
+    float ld[8];  // the next u0 row at the two columns: rho, rho u, rho v, E
+    auto load_row = [&](int j) {
+        const float *p = u.in + wrap_index(u.y0 - 3 + j, n) * n;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            ld[2 * q] = __ldg(p + q * plane + xa);
+            ld[2 * q + 1] = __ldg(p + q * plane + xb);
+        }
+    };
+    load_row(0);
+    const float2 dt = f2(u.dt);
+    Rec a_m1{}, a_c{}, a_p1{};  // u0 rows around stage 1's row
+    Rec b_m1{}, b_c{}, b_p1{};  // s1 rows around stage 2's row
+    Rec c_m1{}, c_c{}, c_p1{};  // s2 rows around stage 3's row
+    Face yf1{}, yf2{}, yf3{};   // carried faces
+    float2 L[4];
+    const int steps = R + 8;
+    for (int j = 0; j < steps; ++j) {
+        // publish the rows that arrive in this step
+        if (j <= R + 5) {
+            const Rec r = make_rec(make_float2(ld[0], ld[1]), make_float2(ld[2], ld[3]), make_float2(ld[4], ld[5]),
+                                   make_float2(ld[6], ld[7]), gm1);
+            a_m1 = a_c;
+            a_c = a_p1;
+            a_p1 = r;
+            march_publish(X, P, sl, 0, j, r);
+            float2 *R0 = X + (60 + 4 * (j & 7)) * P + sl.own;
+            R0[0] = r.rho;
+            R0[P] = r.mx;
+            R0[2 * P] = r.my;
+            R0[3 * P] = r.E;
+        }
+        if (j >= 3 && j <= R + 6) march_publish(X, P, sl, 1, j, b_p1);
+        if (j >= 6 && j <= R + 7) march_publish(X, P, sl, 2, j, c_p1);
+        __syncthreads();
+        if (j + 1 <= R + 5) load_row(j + 1);
+
+        // stage 3 at row y0 - 8 + j: the new state
+        if (j == 7) march_rhs<false>(X, P, nb, 2, j, c_m1, c_c, c_p1, u.inv_h, u.inv_2h, mu, kap, yf3, L);
+        if (j >= 8) {
+            march_rhs<true>(X, P, nb, 2, j, c_m1, c_c, c_p1, u.inv_h, u.inv_2h, mu, kap, yf3, L);
+            const float2 *R0 = X + (60 + 4 * ((j - 5) & 7)) * P + sl.own;
+            const float2 q[4] = {c_c.rho, c_c.mx, c_c.my, c_c.E};
+            float *o = u.out + wrap_index(u.y0 - 8 + j, n) * n;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 base = R0[k * P];
+                const float2 res = fma2(f2(2.f / 3.f), add2(sub2(q[k], base), mul2(dt, L[k])), base);
+                if (wa) o[k * plane + xa] = res.x;
+                if (wb) o[k * plane + xb] = res.y;
+            }
+        }
+        // stage 2 at row y0 - 6 + j
+        if (j == 4) march_rhs<false>(X, P, nb, 1, j, b_m1, b_c, b_p1, u.inv_h, u.inv_2h, mu, kap, yf2, L);
+        if (j >= 5 && j <= R + 6) {
+            march_rhs<true>(X, P, nb, 1, j, b_m1, b_c, b_p1, u.inv_h, u.inv_2h, mu, kap, yf2, L);
+            const float2 *R0 = X + (60 + 4 * ((j - 3) & 7)) * P + sl.own;
+            const float2 q[4] = {b_c.rho, b_c.mx, b_c.my, b_c.E};
+            float2 s[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 base = R0[k * P];
+                s[k] = fma2(f2(0.25f), add2(sub2(q[k], base), mul2(dt, L[k])), base);
+            }
+            c_m1 = c_c;
+            c_c = c_p1;
+            c_p1 = make_rec(s[0], s[1], s[2], s[3], gm1);
+        }
+        // stage 1 at row y0 - 4 + j
+        if (j == 1) march_rhs<false>(X, P, nb, 0, j, a_m1, a_c, a_p1, u.inv_h, u.inv_2h, mu, kap, yf1, L);
+        if (j >= 2 && j <= R + 5) {
+            march_rhs<true>(X, P, nb, 0, j, a_m1, a_c, a_p1, u.inv_h, u.inv_2h, mu, kap, yf1, L);
+            const float2 q[4] = {a_c.rho, a_c.mx, a_c.my, a_c.E};
+            float2 s[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s[k] = add2(q[k], mul2(dt, L[k]));
+            b_m1 = b_c;
+            b_c = b_p1;
+            b_p1 = make_rec(s[0], s[1], s[2], s[3], gm1);
+        }
+    }
+}
+
 // After an odd number of steps the states sit in the scratch buffers: copy
 // them back (group blockIdx.y).
-template <class Tiles>
-__global__ void __launch_bounds__(256) ns2d_copy_back(Tiles src) {
+template <class Units>
+__global__ void __launch_bounds__(256) ns2d_copy_back(Units src) {
     const NsGroup<float> G = src.group(blockIdx.y);
     const size_t count = (size_t)G.n * G.n * G.nprob;  // float4 per group: 4 n^2 nprob floats
     const float4 *s = reinterpret_cast<const float4 *>(G.s1);
@@ -574,6 +933,52 @@ static void step_sequence(const Tiles &src, int ngroups, int total_tiles, int ns
     }
 }
 
+template <class Units>
+static void march_launch(const Units &src, int units, int threads, int parity, float gm1, float mu, float kap,
+                         cudaStream_t s) {
+    static OncePerDevice once;
+    once.run([](int) {
+        return cudaFuncSetAttribute(ns2d_rk3_march<Units>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)march_smem_bytes(kMarchMaxThreads));
+    });
+    // programmatic stream serialisation: the launch may start while the
+    // previous kernel on the stream finishes; the kernel waits for it before
+    // it touches the state (griddepcontrol.wait)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(units);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = march_smem_bytes(threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, ns2d_rk3_march<Units>, src, parity, gm1, mu, kap);
+}
+
+// nsteps steps of every unit (the states end in u0), FP32
+template <class Units>
+static void march_sequence(const Units &src, int ngroups, int units, int threads, int nsteps, float gm1, float mu,
+                           float kap, cudaStream_t s) {
+    for (int st = 0; st < nsteps; ++st) march_launch(src, units, threads, st & 1, gm1, mu, kap, s);
+    count_launches(nsteps);
+    if (nsteps & 1) {
+        ns2d_copy_back<Units><<<dim3(2 * kNumSMs, ngroups), 256, 0, s>>>(src);
+        count_launches(1);
+    }
+}
+
+// rows per segment of the march for a segment choice (the batch's tuned "shape")
+int ns2d_seg_rows(int shape) { return shape == 1 ? 16 : (shape == 2 ? 64 : 32); }
+
+void ns2d_march_layout(int n, int shape, int *bands, int *segs, int *threads) {
+    const int S = std::min(n, ns2d_seg_rows(shape));
+    *bands = march_bands(n);
+    *segs = (n + S - 1) / S;
+    *threads = march_threads(n);
+}
+
 // per-handle FP64 launch: two groups (members, fine run) passed by value, 32 x 8 tiles
 template <typename T, int STAGE>
 __global__ void __launch_bounds__(256) ns2d_stage_kernel(NsArgs<T> A) {
@@ -631,15 +1036,28 @@ cudaError_t ns2d_forecast_scratch(T *whole, int n_whole, int n_whole_probs, T *s
     const int grid = tiles[0] + tiles[1];
     if (grid == 0 || nsteps == 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
-        // the halo is copied in 16-byte chunks, the copy back in float4
+        // the copy back moves float4
         if ((reinterpret_cast<uintptr_t>(whole) | reinterpret_cast<uintptr_t>(split) |
              reinterpret_cast<uintptr_t>(scratch)) & 15)
             return cudaErrorMisalignedAddress;
-        PairTiles P{{A.g[0], A.g[1]}};
-        P.g[0].tile_begin = 0;
-        P.g[1].tile_begin = tiles[0];
-        // a group without grids copies nothing back (count 0)
-        step_sequence<32, 16, 2>(P, 2, grid, nsteps, A.gm1, A.mu, A.kappa, stream);
+        if (n_split_probs > 0) {
+            // a handle (members and fine run): both groups in one persistent
+            // launch of the tile kernel per step
+            PairTiles P{{A.g[0], A.g[1]}};
+            P.g[0].tile_begin = 0;
+            P.g[1].tile_begin = tiles[0];
+            step_sequence<32, 16, 2>(P, 2, grid, nsteps, A.gm1, A.mu, A.kappa, stream);
+        } else {
+            // grids of one size (truth runs, the stateless entry point): the
+            // column march
+            OneUnits U{A.g[0]};
+            int bands = 0, segs = 0, threads = 0;
+            ns2d_march_layout(ns[0], np[0] == 1 ? 1 : 0, &bands, &segs, &threads);
+            U.g.tx = bands;
+            U.g.ty = segs;
+            U.g.tile_begin = 0;
+            march_sequence(U, 1, bands * segs * np[0], threads, nsteps, A.gm1, A.mu, A.kappa, stream);
+        }
     } else {
         for (int s = 0; s < nsteps; ++s) {
             ns2d_stage_kernel<T, 0><<<grid, 256, 0, stream>>>(A);
@@ -667,48 +1085,36 @@ cudaError_t ns2d_forecast(T *whole, int n_whole, int n_whole_probs, T *split, in
     return e != cudaSuccess ? e : e2;
 }
 
-// batched FP32 tile shapes (points per tile): 0 = 32 x 32, 1 = 16 x 32, 2 = 32 x 16
-int ns2d_tile_x(int shape) { return shape == 1 ? 16 : 32; }
-int ns2d_tile_y(int shape) { return shape == 2 ? 16 : 32; }
-
-static cudaError_t table_steps(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, int nsteps,
+static cudaError_t table_steps(const NsGroup<float> *d_groups, int ngroups, int units, int n, int nsteps,
                                bool probe, double gamma, double mu, double prandtl, cudaStream_t s) {
-    if (tiles == 0 || nsteps == 0) return cudaSuccess;
+    if (units == 0 || nsteps == 0) return cudaSuccess;
     const float gm1 = (float)(gamma - 1.0), m = (float)mu, kap = (float)(mu * gamma / ((gamma - 1.0) * prandtl));
-    const TableTiles src{d_groups, ngroups};
+    const TableUnits src{d_groups, ngroups};
+    const int threads = march_threads(n);
     if (probe) {  // one step into the scratch buffers: the states stay as they are
-        if (shape == 1)
-            step_launch<16, 16, 2>(src, tiles, 0, gm1, m, kap, s);
-        else if (shape == 2)
-            step_launch<32, 8, 2>(src, tiles, 0, gm1, m, kap, s);
-        else
-            step_launch<32, 16, 2>(src, tiles, 0, gm1, m, kap, s);
+        march_launch(src, units, threads, 0, gm1, m, kap, s);
         count_launches(1);
-    } else if (shape == 1) {
-        step_sequence<16, 16, 2>(src, ngroups, tiles, nsteps, gm1, m, kap, s);
-    } else if (shape == 2) {
-        step_sequence<32, 8, 2>(src, ngroups, tiles, nsteps, gm1, m, kap, s);
     } else {
-        step_sequence<32, 16, 2>(src, ngroups, tiles, nsteps, gm1, m, kap, s);
+        march_sequence(src, ngroups, units, threads, nsteps, gm1, m, kap, s);
     }
     return cudaGetLastError();
 }
 
-cudaError_t ns2d_forecast_table(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, int nsteps,
+cudaError_t ns2d_forecast_table(const NsGroup<float> *d_groups, int ngroups, int units, int n, int nsteps,
                                 double gamma, double mu, double prandtl, cudaStream_t s) {
-    return table_steps(d_groups, ngroups, tiles, shape, nsteps, false, gamma, mu, prandtl, s);
+    return table_steps(d_groups, ngroups, units, n, nsteps, false, gamma, mu, prandtl, s);
 }
 
-cudaError_t ns2d_probe_step(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, double gamma,
+cudaError_t ns2d_probe_step(const NsGroup<float> *d_groups, int ngroups, int units, int n, double gamma,
                             double mu, double prandtl, cudaStream_t s) {
-    return table_steps(d_groups, ngroups, tiles, shape, 1, true, gamma, mu, prandtl, s);
+    return table_steps(d_groups, ngroups, units, n, 1, true, gamma, mu, prandtl, s);
 }
 
 #define MGK_NS_INST(T)                                                                            \
     template cudaError_t ns2d_forecast<T>(T *, int, int, T *, int, int, double, double, double,    \
                                           double, double, int, cudaStream_t);                     \
     template cudaError_t ns2d_forecast_scratch<T>(T *, int, int, T *, int, int, double, double,    \
-                                                  double, double, double, int, T *, cudaStream_t); \
+                                                  double, double, double, int, T *, cudaStream_t);
 
 MGK_NS_INST(float)
 MGK_NS_INST(double)

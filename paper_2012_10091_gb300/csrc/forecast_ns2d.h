@@ -5,25 +5,27 @@
 
 namespace mgk {
 
-// one set of grids of the same size advanced by a stage launch
+// one set of grids of the same size advanced by a launch
 template <typename T>
 struct NsGroup {
     T *u0, *s1, *s2;       // nprob states of 4 n^2 values each, and two scratch buffers of the same size
                            // (FP64: the stage buffers; FP32: s1 is the second state of the alternating steps)
-    int n, nprob, tx, ty;  // points per side, grids, tiles per side
-    int tile_begin;        // first tile of this group in a launch over several groups
+    int n, nprob, tx, ty;  // points per side, grids; FP32: bands and row segments per grid (FP64: tiles per side)
+    int tile_begin;        // FP32: first unit of this group in a launch over several groups
     T inv_h, inv_2h, dt;
 };
 
-// tile shapes of the batched FP32 step kernel (points per tile, x by y):
-// 0 = 32 x 32, 1 = 16 x 32, 2 = 32 x 16
+// Segment choices of the FP32 step (the batch's tuned "tile shape" per grid
+// size): rows per segment of the march 0 = 32, 1 = 16, 2 = 64.
 constexpr int kNsTileShapes = 3;
-int ns2d_tile_x(int shape);
-int ns2d_tile_y(int shape);
+int ns2d_seg_rows(int shape);
+// bands, row segments and threads per CTA of the FP32 step on an n x n grid
+void ns2d_march_layout(int n, int shape, int *bands, int *segs, int *threads);
 
 // nsteps SSP-RK3 steps of every group of a device table (tile_begin ascending,
-// all tiles of the given shape), FP32 states.
-cudaError_t ns2d_forecast_table(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, int nsteps,
+// all groups of grid size n, units = bands x segments x grids in total), FP32
+// states.
+cudaError_t ns2d_forecast_table(const NsGroup<float> *d_groups, int ngroups, int units, int n, int nsteps,
                                 double gamma, double mu, double prandtl, cudaStream_t s);
 
 // NULL if grids of n_whole (one member per CTA group) and n_split points per
@@ -36,7 +38,9 @@ size_t ns2d_scratch_elems(int n_whole, int n_whole_probs, int n_split, int n_spl
 
 // Advance n_whole_probs grids of n_whole^2 x 4 and n_split_probs grids of
 // n_split^2 x 4 conserved variables by nsteps SSP-RK3 steps, with caller
-// scratch of ns2d_scratch_elems() elements.
+// scratch of ns2d_scratch_elems() elements.  FP32: with both groups (a
+// handle's members and fine run) one launch of the tile kernel per step, with
+// one group the column march.
 template <typename T>
 cudaError_t ns2d_forecast_scratch(T *whole, int n_whole, int n_whole_probs, T *split, int n_split,
                                   int n_split_probs, double length, double dt, double mu,
@@ -50,7 +54,7 @@ cudaError_t ns2d_forecast(T *whole, int n_whole, int n_whole_probs, T *split, in
                           double prandtl, int nsteps, cudaStream_t stream);
 
 // one step from u0 into s1 (it leaves the states untouched): timing probe of the autotuner
-cudaError_t ns2d_probe_step(const NsGroup<float> *d_groups, int ngroups, int tiles, int shape, double gamma,
-                                double mu, double prandtl, cudaStream_t s);
+cudaError_t ns2d_probe_step(const NsGroup<float> *d_groups, int ngroups, int units, int n, double gamma,
+                            double mu, double prandtl, cudaStream_t s);
 
 }  // namespace mgk

@@ -935,9 +935,10 @@ struct mgenkf_batch {
     std::vector<size_t> obs_off;
     size_t total_ny = 0;
     std::vector<int> sizes;  // distinct grid sizes of the members and fine runs
-    std::vector<int> shape;  // tile shape per size
-    NsGroup<float> *d_groups[kNsTileShapes] = {};
-    int ngroups[kNsTileShapes] = {}, tiles[kNsTileShapes] = {};
+    std::vector<int> shape;  // segment choice of the forecast per size (ns2d_seg_rows)
+    // per size: device table of its groups, their number and the units of a step launch
+    std::vector<NsGroup<float> *> d_groups;
+    std::vector<int> ngroups, units;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_nsteps = -1;
@@ -987,42 +988,48 @@ static void handle_groups(const mgenkf_ctx *h, NsGroup<float> g[2]) {
     }
 }
 
-// device tables of groups per tile shape (only groups whose size is in `only`, if given)
-static mgenkf_status build_tables(mgenkf_batch *b, std::vector<NsGroup<float>> (&tab)[kNsTileShapes],
-                                  int only_size, int only_shape) {
-    for (int k = 0; k < kNsTileShapes; ++k) tab[k].clear();
-    int tiles[kNsTileShapes] = {0, 0, 0};
+// host tables of groups per grid size (only the size `only_size`, with the
+// segment choice `only_shape`, if given)
+static void build_tables(mgenkf_batch *b, std::vector<std::vector<NsGroup<float>>> &tab, int only_size,
+                         int only_shape) {
+    tab.assign(b->sizes.size(), {});
+    std::vector<int> units(b->sizes.size(), 0);
     for (mgenkf_ctx *h : b->hs) {
         NsGroup<float> g[2];
         handle_groups(h, g);
         for (int k = 0; k < 2; ++k) {
-            int sh = b->shape[size_index(b, g[k].n)];
+            const int si = size_index(b, g[k].n);
+            int sh = b->shape[si];
             if (only_size > 0) {
                 if (g[k].n != only_size) continue;
                 sh = only_shape;
             }
-            g[k].tx = ceil_div(g[k].n, ns2d_tile_x(sh));
-            g[k].ty = ceil_div(g[k].n, ns2d_tile_y(sh));
-            g[k].tile_begin = tiles[sh];
-            tiles[sh] += g[k].tx * g[k].ty * g[k].nprob;
-            tab[sh].push_back(g[k]);
+            int bands = 0, segs = 0, threads = 0;
+            ns2d_march_layout(g[k].n, sh, &bands, &segs, &threads);
+            g[k].tx = bands;
+            g[k].ty = segs;
+            g[k].tile_begin = units[si];
+            units[si] += bands * segs * g[k].nprob;
+            tab[si].push_back(g[k]);
         }
     }
-    return MGENKF_OK;
 }
 
-static mgenkf_status upload_tables(mgenkf_batch *b, std::vector<NsGroup<float>> (&tab)[kNsTileShapes]) {
+static mgenkf_status upload_tables(mgenkf_batch *b, const std::vector<std::vector<NsGroup<float>>> &tab) {
     // nothing may still read the old tables
     B_CUDA(cudaStreamSynchronize(b->s0));
     for (cudaStream_t s : b->aux) B_CUDA(cudaStreamSynchronize(s));
-    for (int k = 0; k < kNsTileShapes; ++k) {
-        if (b->d_groups[k]) cudaFree(b->d_groups[k]);
-        b->d_groups[k] = nullptr;
+    for (NsGroup<float> *d : b->d_groups)
+        if (d) cudaFree(d);
+    const size_t ns = b->sizes.size();
+    b->d_groups.assign(ns, nullptr);
+    b->ngroups.assign(ns, 0);
+    b->units.assign(ns, 0);
+    for (size_t k = 0; k < ns; ++k) {
         b->ngroups[k] = (int)tab[k].size();
-        b->tiles[k] = 0;
         if (tab[k].empty()) continue;
         const NsGroup<float> &last = tab[k].back();
-        b->tiles[k] = last.tile_begin + last.tx * last.ty * last.nprob;
+        b->units[k] = last.tile_begin + last.tx * last.ty * last.nprob;
         B_CUDA(cudaMalloc(&b->d_groups[k], tab[k].size() * sizeof(NsGroup<float>)));
         // on the batch stream: a plain copy from pageable memory may return
         // before it lands and a non-blocking stream does not wait for it
@@ -1041,8 +1048,8 @@ static mgenkf_status upload_tables(mgenkf_batch *b, std::vector<NsGroup<float>> 
 static void batch_free(mgenkf_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    for (int k = 0; k < kNsTileShapes; ++k)
-        if (b->d_groups[k]) cudaFree(b->d_groups[k]);
+    for (NsGroup<float> *d : b->d_groups)
+        if (d) cudaFree(d);
     if (b->obs_stage) cudaFree(b->obs_stage);
     if (b->innov) cudaFree(b->innov);
     for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
@@ -1127,18 +1134,19 @@ extern "C" mgenkf_status mgenkf_batch_create(const mgenkf_handle *handles, int32
             load[k] += cost[j];
         }
     }
-    const int nstreams = std::max(kNsTileShapes, b->nbranch);
+    const int nsizes = (int)b->sizes.size();
+    const int nstreams = std::max(nsizes, b->nbranch);
     for (int k = 0; k < nstreams; ++k) {
         cudaStream_t s;
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(MGENKF_ERR_CUDA, "stream");
         b->aux.push_back(s);
     }
-    for (int k = 0; k < 2 * nstreams + 2 * kNsTileShapes + 2; ++k) {
+    for (int k = 0; k < 2 * nstreams + 2 * nsizes + 2; ++k) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(MGENKF_ERR_CUDA, "event");
         b->ev.push_back(e);
     }
-    std::vector<NsGroup<float>> tab[kNsTileShapes];
+    std::vector<std::vector<NsGroup<float>>> tab;
     build_tables(b, tab, 0, 0);
     if (upload_tables(b, tab) != MGENKF_OK) return fail(MGENKF_ERR_CUDA, b->err);
     *out = b;
@@ -1156,29 +1164,28 @@ extern "C" mgenkf_status mgenkf_batch_destroy(mgenkf_batch_t b) {
 
 extern "C" const char *mgenkf_batch_last_error(mgenkf_batch_t b) { return b ? b->err.c_str() : ""; }
 
-// forecast of every handle: one launch sequence per tile shape, each on its own
+// forecast of every handle: one launch sequence per grid size, each on its own
 // stream, joined back into s0
 static mgenkf_status batch_forecast(mgenkf_batch *b, int nsteps) {
     B_CUDA(cudaEventRecord(b->ev[0], b->s0));
-    int used = 0;
-    for (int k = 0; k < kNsTileShapes; ++k) {
-        if (!b->tiles[k]) continue;
+    const int ns = (int)b->sizes.size();
+    for (int k = 0; k < ns; ++k) {
+        if (!b->units[k]) continue;
         cudaStream_t s = b->aux[k];
         B_CUDA(cudaStreamWaitEvent(s, b->ev[0], 0));
-        cudaError_t e = ns2d_forecast_table(b->d_groups[k], b->ngroups[k], b->tiles[k], k, nsteps, b->gamma,
-                                                   b->mu, b->prandtl, s);
+        cudaError_t e = ns2d_forecast_table(b->d_groups[k], b->ngroups[k], b->units[k], b->sizes[k], nsteps, b->gamma,
+                                            b->mu, b->prandtl, s);
         if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("batched forecast: ") + cudaGetErrorString(e));
         B_CUDA(cudaEventRecord(b->ev[1 + k], s));
-        ++used;
     }
-    for (int k = 0; k < kNsTileShapes; ++k)
-        if (b->tiles[k]) B_CUDA(cudaStreamWaitEvent(b->s0, b->ev[1 + k], 0));
+    for (int k = 0; k < ns; ++k)
+        if (b->units[k]) B_CUDA(cudaStreamWaitEvent(b->s0, b->ev[1 + k], 0));
     return MGENKF_OK;
 }
 
 // analyses and prolongations of every handle, spread over the auxiliary streams
 static mgenkf_status batch_analyse(mgenkf_batch *b) {
-    const int base = 1 + kNsTileShapes;
+    const int base = 1 + (int)b->sizes.size();
     B_CUDA(cudaEventRecord(b->ev[base], b->s0));
     const int ns = b->nbranch;
     for (int k = 0; k < ns; ++k) B_CUDA(cudaStreamWaitEvent(b->aux[k], b->ev[base], 0));
@@ -1252,7 +1259,7 @@ extern "C" mgenkf_status mgenkf_batch_sync(mgenkf_batch_t b) {
 }
 
 // Time one step into the scratch buffers (the states are not touched) of
-// every grid size with every tile shape and keep the fastest shape per size.
+// every grid size with every segment choice and keep the fastest per size.
 extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
     if (!b || reps < 1) return MGENKF_ERR_INVALID_ARG;
     b->err.clear();
@@ -1264,17 +1271,18 @@ extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
         float best = 1e30f;
         int best_shape = 0;
         for (int sh = 0; sh < kNsTileShapes; ++sh) {
-            std::vector<NsGroup<float>> tab[kNsTileShapes];
+            std::vector<std::vector<NsGroup<float>>> tab;
             build_tables(b, tab, b->sizes[si], sh);
-            const int ng = (int)tab[sh].size();
+            const int ng = (int)tab[si].size();
             if (!ng) continue;
-            const int tiles = tab[sh].back().tile_begin + tab[sh].back().tx * tab[sh].back().ty * tab[sh].back().nprob;
+            const NsGroup<float> &last = tab[si].back();
+            const int units = last.tile_begin + last.tx * last.ty * last.nprob;
             B_CUDA(cudaMalloc(&d, ng * sizeof(NsGroup<float>)));
-            B_CUDA(cudaMemcpyAsync(d, tab[sh].data(), ng * sizeof(NsGroup<float>), cudaMemcpyHostToDevice, b->s0));
+            B_CUDA(cudaMemcpyAsync(d, tab[si].data(), ng * sizeof(NsGroup<float>), cudaMemcpyHostToDevice, b->s0));
             float ms = 0.f;
             for (int r = 0; r <= reps; ++r) {  // first repetition warms up
                 B_CUDA(cudaEventRecord(t0, b->s0));
-                cudaError_t e = ns2d_probe_step(d, ng, tiles, sh, b->gamma, b->mu, b->prandtl, b->s0);
+                cudaError_t e = ns2d_probe_step(d, ng, units, b->sizes[si], b->gamma, b->mu, b->prandtl, b->s0);
                 if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
                 B_CUDA(cudaEventRecord(t1, b->s0));
                 B_CUDA(cudaEventSynchronize(t1));
@@ -1293,7 +1301,7 @@ extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
-    std::vector<NsGroup<float>> tab[kNsTileShapes];
+    std::vector<std::vector<NsGroup<float>>> tab;
     build_tables(b, tab, 0, 0);
     return upload_tables(b, tab);
 }
@@ -1314,11 +1322,11 @@ extern "C" mgenkf_status mgenkf_batch_set_tiles(mgenkf_batch_t b, const int32_t 
     if (!b || (count > 0 && (!sizes || !shapes))) return MGENKF_ERR_INVALID_ARG;
     b->err.clear();
     for (int32_t i = 0; i < count; ++i) {
-        if (shapes[i] < 0 || shapes[i] >= kNsTileShapes) B_FAIL(MGENKF_ERR_INVALID_ARG, "tile shape out of range");
+        if (shapes[i] < 0 || shapes[i] >= kNsTileShapes) B_FAIL(MGENKF_ERR_INVALID_ARG, "segment choice out of range");
         const int si = size_index(b, sizes[i]);
         if (si >= 0) b->shape[si] = shapes[i];
     }
-    std::vector<NsGroup<float>> tab[kNsTileShapes];
+    std::vector<std::vector<NsGroup<float>>> tab;
     build_tables(b, tab, 0, 0);
     return upload_tables(b, tab);
 }

@@ -461,7 +461,8 @@ class MGEnKF:
 # ---------------------------------------------------------------------------
 # batches of independent NS-2D problems (mgenkf_batch_* in include/mgenkf.h)
 # ---------------------------------------------------------------------------
-TILE_SHAPES = {0: (32, 32), 1: (16, 32), 2: (32, 16)}   # points per tile (x, y)
+# segment choices of the batched forecast: rows per segment of the column march
+SEGMENT_ROWS = {0: 32, 1: 16, 2: 64}
 
 
 def _bcheck(st, where, b):
@@ -513,7 +514,7 @@ class Batch:
         return self.tiles()
 
     def tiles(self) -> dict:
-        """{grid size: tile shape index} (TILE_SHAPES gives the tile)."""
+        """{grid size: segment choice} (SEGMENT_ROWS gives the rows per segment)."""
         cnt = ctypes.c_int32()
         _bcheck(lib.mgenkf_batch_tiles(self.b, None, None, 0, ctypes.byref(cnt)), "mgenkf_batch_tiles", self.b)
         n = cnt.value
@@ -528,11 +529,11 @@ class Batch:
         _bcheck(lib.mgenkf_batch_set_tiles(self.b, sizes, shapes, n), "mgenkf_batch_set_tiles", self.b)
 
     def save_tiles(self, path):
-        """Persist the tile table (JSON, grid size -> shape) for later runs."""
+        """Persist the tuned table (JSON, grid size -> segment choice) for later runs."""
         import json
         with open(path, "w") as f:
             json.dump({"tiles": {str(k): v for k, v in self.tiles().items()},
-                       "shapes": {str(k): list(v) for k, v in TILE_SHAPES.items()}}, f, indent=1)
+                       "segment_rows": {str(k): v for k, v in SEGMENT_ROWS.items()}}, f, indent=1)
 
     def load_tiles(self, path):
         import json

@@ -106,7 +106,7 @@ def test_autotune_and_persisted_tiles(M, tmp_path):
     b = M.Batch(_runs(M, ws, inps))
     tiles = b.autotune(reps=2)
     assert set(tiles) == {w.nc for w in ws} | {w.nf for w in ws}
-    assert set(tiles.values()) <= set(M.TILE_SHAPES)
+    assert set(tiles.values()) <= set(M.SEGMENT_ROWS)
     path = tmp_path / "tiles.json"
     b.save_tiles(path)
     b.set_tiles({k: (v + 1) % 3 for k, v in tiles.items()})
@@ -200,9 +200,9 @@ def test_batch_on_a_nonblocking_stream(M):
 
 def test_batch_at_multi_tile_sizes_matches_oracle(M):
     """Problems of the batched workload's own sizes (coarse 64^2-128^2, fine 4x
-    per side, 16-32 members), so that each persistent stage CTA walks many
-    tiles (about 7,000 tiles of 32 x 32 points per launch over 2 x 152
-    resident CTAs), against the CPU oracle over two cycles."""
+    per side, 16-32 members): the column march of every grid size runs many
+    more CTAs than are resident (each member grid 2-4 row segments, each fine
+    grid 8-16), against the CPU oracle over two cycles."""
     ws = W.ns2d_batch(nprob=8, seed=5, coarse=(64, 96, 128), members=(16, 32), n_obs=(256, 512))
     cycles = 2
     inps, yos = _inputs(ws, cycles)

@@ -74,12 +74,12 @@ def test_ns2d_fp32_matches_oracle(M):
         assert np.max(np.abs(got[:, k] - ref[:, k])) <= 2e-5 * np.max(np.abs(ref[:, k])), k
 
 
-@pytest.mark.parametrize("n,nprob", [(264, 16), (1032, 1)])
+@pytest.mark.parametrize("n,nprob", [(264, 16), (1064, 1)])
 def test_ns2d_fp32_multi_tile_matches_oracle(M, n, nprob):
-    # Sizes at which the persistent FP32 forecast walks several tiles per CTA
-    # with a ragged last tile in x and y (264 = 8.25 x 32, 1032 = 32.25 x 32):
-    # 16 x 264^2 is 16 x 9 x 9 = 1296 tiles of 32 x 32 points over 2 x 152
-    # resident CTAs (4.3 tiles per CTA); 1032^2 is 33 x 33 = 1089 (3.6 per CTA).
+    # The stateless forecast runs the column march.  16 x 264^2: one band of
+    # 132 threads per grid, 9 row segments of 32 rows (the last one 8 rows),
+    # 144 CTAs.  1064^2: 3 bands of 356, 356 and 352 columns with 3-column
+    # halos (the last band ragged), 67 segments of 16 rows (the last 8).
     import torch
     q0 = _smooth_states(nprob, n, 11)
     h, mu, steps = 1.0 / n, 1e-3, 10
@@ -101,6 +101,35 @@ def test_ns2d_fp32_multi_tile_matches_oracle(M, n, nprob):
     got3 = d.cpu().double().numpy()
     for k in range(4):
         assert np.max(np.abs(got3[:, k] - ref3[:, k])) <= 1e-5 * np.max(np.abs(ref3[:, k])), k
+
+
+@pytest.mark.parametrize("steps", [10, 3])
+def test_ns2d_handle_forecast_at_full_size_matches_oracle(M, steps):
+    # A handle of the 512^2 / 128^2, 64-member workload advances its members
+    # and fine run with the tile kernel: 64 x 16 + 256 = 1280 tiles of 32 x 32
+    # points over 2 x 152 resident CTAs (4.2 tiles per CTA).
+    w = W.ns2d_shear(nf=512, ratio=4, ne=64, n_probes=1024, cycles=1, precision="mixed")
+    inp = W.make_inputs(w)
+    g = M.MGEnKF.from_workload(w, precision="mixed")
+    g.set_state(inp["fine0"], inp["members0"])
+    g.forecast(steps)
+    assert g.sync() == 0
+    fine, mem = g.get_state()
+    g.close()
+    h_f, h_c = w.length / w.nf, w.length / w.nc
+    ref_f = O.ns2d_rk3(inp["fine0"].reshape(4, w.nf, w.nf), h_f, w.gamma, w.nu, w.prandtl, w.dt, steps)
+    ref_m = O.ns2d_rk3(inp["members0"].reshape(w.ne, 4, w.nc, w.nc), h_c, w.gamma, w.nu, w.prandtl, w.dt, steps)
+    got_f = fine.reshape(4, w.nf, w.nf)
+    got_m = mem.reshape(w.ne, 4, w.nc, w.nc)
+    # Element-wise.  The FP32 rounding of a momentum plane is set by its fluxes
+    # (rho u u + p, rho u v), not by the plane itself: in the shear layer
+    # |rho v| <= 1e-3 while |rho u| ~ 1, so both momentum planes are measured
+    # against the larger momentum; rho and E against themselves.
+    for got, ref in ((got_f, ref_f), (got_m, ref_m)):
+        mom = max(np.max(np.abs(ref[..., 1, :, :])), np.max(np.abs(ref[..., 2, :, :])))
+        for k in range(4):
+            scale = mom if k in (1, 2) else np.max(np.abs(ref[..., k, :, :]))
+            assert np.max(np.abs(got[..., k, :, :] - ref[..., k, :, :])) <= 2e-5 * scale, k
 
 
 def test_ns2d_rejects_bad_sizes(M):

@@ -1,18 +1,22 @@
 #!/usr/bin/env python3
-"""Throughput of the MGEnKF analysis cycle on one GB300 (or N, one replica each).
+"""Throughput of the MGEnKF analysis cycle on one GB300 (or N).
 
-One "step" is one analysis cycle of Algorithm 4 on the large 1-D Burgers
-workload (fine 16384 / coarse 4096 points, Ne = 128, 512 observations):
-forecast of the fine run and all members over one observation interval, the
-coarse-mesh EnKF analysis, the prolonged correction of the fine run and its
-RMSE against the truth.  Mixed precision: FP32 states and forecasts, BF16
-anomaly products with FP32 accumulation, FP64 means, covariances, Cholesky.
+Default workload: 96 independent 2-D Navier-Stokes assimilation problems
+(coarse grids 64^2..192^2, fine grids 4x per side, 16..128 members,
+256..2048 observations each), the largest single-GPU configuration.  One
+"step" is one analysis cycle of every problem (Algorithm 4): forecast of each
+fine run and all members over 10 model steps, the coarse-mesh EnKF analysis,
+the prolonged correction of the fine run, one CUDA graph launch.  Mixed
+precision: FP32 states and forecasts, BF16 anomaly products with FP32
+accumulation, FP64 means, covariances and Cholesky.  `value` = problem-cycles
+per second over all ranks (the 96 problems are sharded over the ranks, no
+collective on the data path).  Other workloads (--workload): burgers_large
+(fine 16384 / coarse 4096, Ne = 128), ns2d (512^2 / 128^2, Ne = 64), ns2d_cnn
+(learned correction, 1024^2 / 256^2), dual (Dual EnKF on the Burgers inlet).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
-Prints one JSON line (rank 0).  `value` = analysis cycles per second over all
-ranks (each rank runs an independent replica with its own seed: weak scaling,
-no collective on the data path).  `--impl reference` times the FP64 CPU oracle
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on this host's cores on bounded samples of the same workload.
 """
 from __future__ import annotations
@@ -32,9 +36,6 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
-NUM_SMS = 152
-MAX_SM_MHZ = 2070.0
 
 # Per workload: algorithmic FP32 flops per point-step of the forecast, the
 # forecast kernel timed for the roofline, its launches per model step, the
@@ -50,28 +51,31 @@ WORKLOADS = {
     # run on its own cluster, the members after it by programmatic
     # serialisation); the roofline takes them as one unit, and traffic is the sum
     # of the two launches' DRAM bytes
-    "burgers_large": dict(flops=32, ops=26, kernel="burgers_f32x2_kernel<4> fine run + <8> members",
+    "burgers_large": dict(flops=32, bytes=8, kernel="burgers_f32x2_kernel<4> fine run + <8> members",
                           launches_per_step=None, traffic=2410752, truth="fp32"),
-    # NS-2D: ~200 flops per point and stage (primitives, nodal fluxes, four
-    # face fluxes, stage update), 3 stages per step; as FP32 operations per
-    # point and stage, counted from the kernel: 9 (primitives) + 28 (inviscid)
-    # + 66 (four faces) + 16 (sums, dt) + 4 or 12 (stage) = 128 on average
-    "ns2d": dict(flops=600, ops=385, kernel="ns2d_stage_x2<*,32,8,PairTiles>", launches_per_step=3,
+    # NS-2D, one model step (three RK stages fused in one launch): algorithmic
+    # FP32 flops per point-step counted from the kernels' arithmetic (an FMA
+    # counts 2, the halo recomputation is not counted): per stage 114 for dt L
+    # (nodal inviscid fluxes 20, their differences 16, three face fluxes of 21
+    # each, the face differences 15: each face is counted once) and 11 for the
+    # primitives of its input, plus 8 + 20 + 20 for the three stage updates:
+    # 3 x 125 + 48 = 423.  Algorithmic bytes: the state read and
+    # written once per step, 2 x 4 variables x 4 B = 32 per point-step.
+    "ns2d": dict(flops=423, bytes=32, kernel="ns2d_rk3_step<32,16,2,PairTiles>", launches_per_step=1,
                  traffic=None, truth="fp64"),
     # NS-2D 1024^2 / 256^2 with the learned correction of the prolongation
-    "ns2d_cnn": dict(flops=600, ops=385, kernel="ns2d_stage_x2<*,32,8,PairTiles>", launches_per_step=3,
+    "ns2d_cnn": dict(flops=423, bytes=32, kernel="ns2d_rk3_step<32,16,2,PairTiles>", launches_per_step=1,
                      traffic=None, truth="fp64"),
-    # 96 independent NS-2D problems; per point-step the three stage kernels
-    # move 128 algorithmic bytes (stage 0: read u0, write s1; stages 1 and 2:
-    # read the stage input and u0, write the output; 16 B per point each)
-    # traffic: DRAM bytes per point-step of the three stage launches, measured
-    # by ncu on the 32x16-tile class of the 8-problem batch (10.6 M points of
-    # 64^2 and 192^2 grids, working set above L2) and scaled to the full batch
-    # by its point count; None once the kernel changes
     # Dual EnKF parameter estimation on the Burgers inlet model (latency-bound: small grids)
     "dual": dict(kernel="k_burgers_inlet"),
-    "batched": dict(flops=600, bytes=128, kernel="ns2d_stage_x2<*,*,*,TableTiles>",
-                    launches_per_step=3, traffic=None, traffic_per_point_step=151.0, truth="fp32"),
+    # 96 independent NS-2D problems: one march launch per model step and grid
+    # size.  traffic_per_point_step: dram__bytes_read.sum + dram__bytes_write.sum
+    # per point-step of the march launches of one cycle, measured by ncu on the
+    # 8-problem batch (16.02 B read, 7.80 B written: ncu counts the lines L2
+    # evicts during a launch), scaled to this batch by its point-steps; None
+    # once the kernel changes.
+    "batched": dict(flops=423, bytes=32, kernel="ns2d_rk3_march<TableUnits>", launches_per_step=None,
+                    traffic_per_point_step=23.83, truth="fp32"),
 }
 CNN_FLOPS_PER_PIXEL = 2 * 9 * (8 * 32 + 32 * 32 + 32 * 64)  # three 3x3 convolutions per coarse pixel
 
@@ -86,11 +90,11 @@ def parse():
                     help="cycles of the plain FP64 run compared at equal RMSE")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="burgers_large",
-                    help="burgers_large (default: fine 16384 / coarse 4096, Ne=128), ns2d "
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batched",
+                    help="batched (default: 96 independent NS-2D problems of uneven sizes, one graph launch per "
+                         "cycle), burgers_large (fine 16384 / coarse 4096, Ne=128), ns2d "
                          "(fine 512^2 / coarse 128^2, Ne=64, 2048 observations), ns2d_cnn "
                          "(fine 1024^2 / coarse 256^2, Ne=64, learned prolongation correction) or "
-                         "batched (96 independent NS-2D problems of uneven sizes, one graph launch per cycle) or "
                          "dual (inlet-parameter estimation on the Burgers inlet model, 800 nodes, ratio 4)")
     ap.add_argument("--cnn-pairs", type=int, default=400,
                     help="training pairs generated for ns2d_cnn (cycles of lockstep runs)")
@@ -214,6 +218,31 @@ def measured_peaks():
         except (OSError, ValueError):
             pass
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def measure_alu_peaks(M, torch, stream):
+    """FP32 and FP64 FMA-pipe throughput on this GPU, measured with the
+    library's probe kernel (eight independent FMA chains per thread, four CTAs
+    of 256 threads per SM), best of three launches of about 5 ms each, CUDA
+    events on `stream`."""
+    out = {}
+    n = M.mgk_fma_probe_threads()
+    for name, fp64, iters, dt in (("fp32", 0, 160000, torch.float32), ("fp64", 1, 2600, torch.float64)):
+        sink = torch.empty(n, dtype=dt, device="cuda")
+        with torch.cuda.stream(stream):
+            M.mgk_fma_probe(fp64, iters, sink, stream=stream.cuda_stream)  # warm-up
+            best = 0.0
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                flops = M.mgk_fma_probe(fp64, iters, sink, stream=stream.cuda_stream)
+                b.record(stream)
+                b.synchronize()
+                best = max(best, flops / (a.elapsed_time(b) / 1e3))
+        out[f"{name}_tflops"] = best / 1e12
+    out["how"] = ("mgk_fma_probe: 8 independent FMA chains per thread, 4 x 256 threads per SM, "
+                  "best of 3 launches (CUDA events); an FMA counts 2 flops")
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -521,24 +550,24 @@ def run_gpu(args, dist, w, inp):
         e2e = {"value": cycles_all / te, "unit": "cycles/s",
                "h2d_bytes_per_step": 8 * (w.ny + w.nxf), "d2h_bytes_per_step": 8 * w.V}
 
-    # roofline of the dominant kernel (the forecast): FP32 ALU bound
+    # roofline of the dominant kernel (the forecast): algorithmic FP32 flops
+    # per launch (an FMA counts 2; counted from the scheme without the halo
+    # recomputation) over the launch's time, against the FP32 FMA throughput
+    # measured on this GPU by the probe kernel; the HBM view (algorithmic bytes,
+    # the state read and written once per launch) beside it
     peaks, peak_src = measured_peaks()
+    alu = measure_alu_peaks(M, torch, stream)
     pts = w.ne * w.nc ** w.dim + w.nf ** w.dim
     lps = spec["launches_per_step"]
     launches_fc = 1 if lps is None else lps * w.steps_per_cycle
-    # FP32 operations per launch (FADD, FMUL, FFMA one each, counted from the
-    # scheme without the halo recomputation) against the FP32 pipes' rate of
-    # one operation per lane and clock: the kernels' mixes are mostly adds and
-    # multiplies, so the flop view (an FMA counts 2, against twice that peak)
-    # is reported beside it
     launch_t = fc_mean / launches_fc
-    ops = spec["ops"] * pts * w.steps_per_cycle / launches_fc
-    achieved = ops / launch_t / 1e12
-    peak = NUM_SMS * FP32_LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
     flops = spec["flops"] * pts * w.steps_per_cycle / launches_fc
-    peak_flops = 2 * peak
+    achieved = flops / launch_t / 1e12
+    peak = alu["fp32_tflops"]
+    hbm_bytes = spec.get("bytes", 2 * w.V * 4) * pts * w.steps_per_cycle / launches_fc
+    hbm_achieved = hbm_bytes / launch_t / 1e9
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the current
-    # forecast kernel, from an ncu capture of this workload (Burgers); None until
+    # forecast kernel, from an ncu capture of this workload; None until
     # captured, and reset whenever the kernel changes
     traffic = spec["traffic"]
     g.close()
@@ -565,14 +594,16 @@ def run_gpu(args, dist, w, inp):
             "recentre_ablation": feedback,
             "filter_ablation": filt,
             "roofline": {"bound": "alu", "kernel": spec["kernel"],
-                         "achieved": achieved, "peak": peak, "unit": "TOP/s",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": "FP32 operations: 152 SMs x 128 lanes x 2070 MHz",
-                         "ops_per_point_step": spec["ops"],
-                         "flop_view": {"achieved_tflops": flops / launch_t / 1e12, "peak_tflops": peak_flops,
-                                       "frac": flops / launch_t / 1e12 / peak_flops,
-                                       "flops_per_point_step": spec["flops"]},
-                         "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": peak_src},
+                         "peak_source": "FP32 FMA throughput measured by mgk_fma_probe in this run (" +
+                                        alu["how"] + ")",
+                         "flops_per_point_step": spec["flops"],
+                         "hbm_view": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks.get("hbm_gbs"),
+                                      "frac": hbm_achieved / float(peaks.get("hbm_gbs", 6800.0)),
+                                      "bytes_per_point_step": hbm_bytes / (pts * w.steps_per_cycle / launches_fc),
+                                      "peak_source": peak_src}},
+            "alu_peaks": alu,
             "clocks": clk,
             "gpu_launches": int(launches),
             "wall_s_timed": wall,
@@ -910,11 +941,15 @@ def run_gpu_batched(args, dist):
     fc_s = fa.elapsed_time(fb) / 1e3 / reps
     spec = WORKLOADS["batched"]
     pts = sum(problem_work(w) for w in ws)
-    n_launch = spec["launches_per_step"] * nsteps * len(set(tiles[w.nc] for w in ws) | set(tiles[w.nf] for w in ws))
-    bytes_fc = spec["bytes"] * pts * nsteps
+    sizes = sorted(set(w.nc for w in ws) | set(w.nf for w in ws))
+    n_launch = nsteps * len(sizes)
     peaks, peak_src = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = bytes_fc / fc_s / 1e9
+    alu = measure_alu_peaks(M, torch, stream)
+    flops_fc = spec["flops"] * pts * nsteps
+    bytes_fc = spec["bytes"] * pts * nsteps
+    alu_achieved = flops_fc / fc_s / 1e12
+    hbm_achieved = bytes_fc / fc_s / 1e9
 
     # e2e: observations from pinned host memory, innovation RMS read back each cycle
     e2e = None
@@ -1000,14 +1035,22 @@ def run_gpu_batched(args, dist):
             "analysis_ms_per_cycle": (t_total / args.steps - fc_s) * 1e3,
             "kernels_per_cycle": int(launches_per_cycle),
             "innovation_rms_mean_last": float(innov_h[-1].mean()),
-            "roofline": {"bound": "hbm", "kernel": spec["kernel"], "achieved": achieved, "peak": hbm_peak,
-                         "unit": "GB/s", "frac": achieved / hbm_peak,
+            # the forecast's launches (one per model step and grid size, the
+            # sizes on concurrent streams) timed as one unit by CUDA events on
+            # the batch stream: algorithmic flops (FP32 view) and bytes (HBM
+            # view) of all of them over that time; bound = the larger fraction
+            "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": alu_achieved,
+                         "peak": alu["fp32_tflops"], "unit": "TFLOP/s", "frac": alu_achieved / alu["fp32_tflops"],
                          "traffic": (spec["traffic_per_point_step"] * pts * nsteps
                                      if spec.get("traffic_per_point_step") else None),
-                         "scope": f"all stage launches of one forecast ({n_launch} launches, {nsteps} steps), "
-                                  f"{spec['bytes']} B per point-step",
-                         "peak_source": f"hbm_gbs ({peak_src})",
-                         "fp32_tflops": spec["flops"] * pts * nsteps / fc_s / 1e12},
+                         "scope": f"all march launches of one forecast ({n_launch} launches: {nsteps} steps x "
+                                  f"{len(sizes)} grid sizes), {pts * nsteps / 1e9:.3f} G point-steps, "
+                                  f"{spec['flops']} flops and {spec['bytes']} B per point-step",
+                         "peak_source": "FP32 FMA throughput measured by mgk_fma_probe in this run (" +
+                                        alu["how"] + ")",
+                         "hbm_view": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak,
+                                      "frac": hbm_achieved / hbm_peak, "peak_source": f"hbm_gbs ({peak_src})"}},
+            "alu_peaks": alu,
             "fp64_plain": fp64,
             "clocks": clk,
             "gpu_launches": int(launches_per_cycle * args.steps),

@@ -155,8 +155,11 @@ mgenkf_status mgenkf_rmse(mgenkf_handle h, const double *truth_fine, double *out
  *   MGENKF_FIELD_GAMMA  conservativity residual of the fine  V x N_F^dim
  *                       run (Eq. Conservativity_rhov), see mgenkf_set_regularisation
  *   MGENKF_FIELD_RATE   its time-derivative term (x - x_prev)/dt, V x N_F^dim
- *                       whose largest magnitude per variable normalises Gamma
- *                       (the paper's Gamma* = Gamma / C, C = max |d(rho v)/dt|)
+ *   MGENKF_FIELD_GAMMA_NORM  Gamma* = Gamma / C per variable, C = the largest
+ *                       |x - x_prev| / dt of that variable over the grid (Sec. 6,
+ *                       the normalisation of the conservativity maps: C = max
+ *                       |d(rho v)/dt|; a variable that did not change keeps
+ *                       Gamma), V x N_F^dim
  * count: number of doubles the caller can receive (must be >= the size). */
 #define MGENKF_FIELD_XSTAR 0
 #define MGENKF_FIELD_YF 1
@@ -165,6 +168,7 @@ mgenkf_status mgenkf_rmse(mgenkf_handle h, const double *truth_fine, double *out
 #define MGENKF_FIELD_EPS 4
 #define MGENKF_FIELD_GAMMA 5
 #define MGENKF_FIELD_RATE 6
+#define MGENKF_FIELD_GAMMA_NORM 7
 mgenkf_status mgenkf_get_field(mgenkf_handle h, int32_t field, double *out, size_t count);
 
 /* Wait for the handle's stream and return (and clear) the first device-side

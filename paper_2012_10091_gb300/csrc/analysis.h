@@ -64,6 +64,11 @@ cudaError_t launch_ns2d_filter6(T *q, T *tmp, int n, int nprob, double sigma, cu
 template <typename T>
 void launch_state_rate(const T *x, const T *prev, size_t count, double dt, double *out, cudaStream_t s);
 
+// gamma (V planes of `plane` FP64 values) divided in place, per plane, by
+// max |x - prev| / dt of that plane (left as is where the plane did not change)
+template <typename T>
+void launch_gamma_norm(const T *x, const T *prev, int V, size_t plane, double dt, double *gamma, cudaStream_t s);
+
 // fine-to-coarse feedback: members re-centred on x^C* (FP64 mean and shift)
 template <typename T>
 void launch_recentre(T *members, size_t nx, int ne, const T *xstar, const int *status, cudaStream_t s);

@@ -745,6 +745,31 @@ extern "C" mgenkf_status mgenkf_get_field(mgenkf_handle h, int32_t field, double
             H_LAUNCHED();
             return copy_out_f64(h, out, h->scratch, h->nxf);
         }
+        case MGENKF_FIELD_GAMMA_NORM: {
+            if (count < h->nxf) H_FAIL(MGENKF_ERR_INVALID_ARG, "count too small");
+            if (!h->have_prev)
+                H_FAIL(MGENKF_ERR_INVALID_ARG, "no recorded previous fine state: enable mgenkf_set_regularisation "
+                                               "and run a forecast first");
+            mgenkf_status st = ensure_scratch(h, h->nxf);
+            if (st) return st;
+            const mgenkf_config &c = h->cfg;
+            const size_t plane = h->nxf / h->V;
+            if (h->mixed) {
+                launch_fine_residual<float>(c.model, (const float *)h->fine, (const float *)h->fine_prev, h->nf,
+                                            c.length, c.nu, c.gamma, c.prandtl, c.dt, 0.0, nullptr, h->scratch,
+                                            nullptr, h->stream);
+                launch_gamma_norm<float>((const float *)h->fine, (const float *)h->fine_prev, h->V, plane, c.dt,
+                                         h->scratch, h->stream);
+            } else {
+                launch_fine_residual<double>(c.model, (const double *)h->fine, (const double *)h->fine_prev, h->nf,
+                                             c.length, c.nu, c.gamma, c.prandtl, c.dt, 0.0, nullptr, h->scratch,
+                                             nullptr, h->stream);
+                launch_gamma_norm<double>((const double *)h->fine, (const double *)h->fine_prev, h->V, plane, c.dt,
+                                          h->scratch, h->stream);
+            }
+            H_LAUNCHED();
+            return copy_out_f64(h, out, h->scratch, h->nxf);
+        }
         case MGENKF_FIELD_RATE: {
             if (count < h->nxf) H_FAIL(MGENKF_ERR_INVALID_ARG, "count too small");
             if (!h->have_prev)

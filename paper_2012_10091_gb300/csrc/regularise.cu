@@ -163,6 +163,38 @@ void launch_state_rate(const T *x, const T *prev, size_t count, double dt, doubl
 template void launch_state_rate<float>(const float *, const float *, size_t, double, double *, cudaStream_t);
 template void launch_state_rate<double>(const double *, const double *, size_t, double, double *, cudaStream_t);
 
+// Gamma* = Gamma / C per variable (Sec. 6, the normalisation of the
+// conservativity maps): C = max over the plane's points of |x - x_prev| / dt,
+// one CTA per variable; a plane that did not change keeps Gamma.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_gamma_norm(const T *__restrict__ x, const T *__restrict__ prev,
+                                                     size_t plane, double inv_dt, double *__restrict__ g) {
+    __shared__ double wmax[32];
+    const size_t off = (size_t)blockIdx.x * plane;
+    double m = 0.0;
+    for (size_t i = threadIdx.x; i < plane; i += blockDim.x)
+        m = fmax(m, fabs(((double)x[off + i] - (double)prev[off + i]) * inv_dt));
+    for (int d = 16; d > 0; d >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, d));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.0;
+        for (int d = 16; d > 0; d >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, d));
+        if (threadIdx.x == 0) wmax[0] = m;
+    }
+    __syncthreads();
+    const double c = wmax[0] > 0.0 ? wmax[0] : 1.0;
+    for (size_t i = threadIdx.x; i < plane; i += blockDim.x) g[off + i] = g[off + i] / c;
+}
+
+template <typename T>
+void launch_gamma_norm(const T *x, const T *prev, int V, size_t plane, double dt, double *gamma, cudaStream_t s) {
+    count_launches(1);
+    k_gamma_norm<T><<<V, 1024, 0, s>>>(x, prev, plane, 1.0 / dt, gamma);
+}
+template void launch_gamma_norm<float>(const float *, const float *, int, size_t, double, double *, cudaStream_t);
+template void launch_gamma_norm<double>(const double *, const double *, int, size_t, double, double *, cudaStream_t);
+
 template <typename T>
 void launch_fine_residual(int model, const T *x, const T *prev, int n, double length, double nu, double gamma,
                           double prandtl, double dt, double alpha, T *out, double *gamma_out, const int *status,

@@ -229,11 +229,8 @@ bool update_tc_prepare(UpdateTcPlan *plan, const __nv_bfloat16 *X16, int ldx, in
 }
 
 cudaError_t launch_update_tc(const UpdateTcPlan &plan, float *members, float *dC, int *status, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static OncePerDevice attr;
+    attr.run([](int) { return cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); });
     if (members != plan.members) return cudaErrorInvalidValue;
     count_launches(1);
     const int grid = (plan.nx + kTileM - 1) / kTileM;

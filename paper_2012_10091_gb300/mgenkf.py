@@ -26,6 +26,7 @@ MGENKF_PROLONG_LAGRANGE4 = 0
 MGENKF_FIELD_XSTAR, MGENKF_FIELD_YF, MGENKF_FIELD_T, MGENKF_FIELD_DC, MGENKF_FIELD_EPS = 0, 1, 2, 3, 4
 MGENKF_FIELD_GAMMA = 5
 MGENKF_FIELD_RATE = 6
+MGENKF_FIELD_GAMMA_NORM = 7
 EPS_TAG = 0x45505300
 
 
@@ -434,11 +435,10 @@ class MGEnKF:
 
     def gamma_normalised(self):
         """Gamma* = Gamma / C per variable, C = max over the grid of |(x - x_prev)/dt|
-        (the normalisation of the paper's conservativity maps)."""
-        g = self.gamma_residual().reshape(self.V, -1)
-        r = self.state_rate().reshape(self.V, -1)
-        c = np.abs(r).max(axis=1, keepdims=True)
-        return (g / np.where(c > 0, c, 1.0)).reshape(-1)
+        (the normalisation of the paper's conservativity maps), FP64, formed by the library."""
+        out = np.empty(self.nxf)
+        mgenkf_get_field(self.h, MGENKF_FIELD_GAMMA_NORM, out, self.nxf)
+        return out
 
     def set_prolong_cnn(self, cnn):
         """Attach a CNN (or None) whose residual prolong_correct adds to Pi_F(dC)."""

@@ -135,7 +135,8 @@ def test_batches_refuse_regularised_handles(M):
 @pytest.mark.parametrize("model", ["burgers", "ns2d"])
 def test_normalised_gamma_matches_oracle(M, model):
     """Gamma* = Gamma / max |(x - x_prev)/dt| (the paper's normalisation of its
-    conservativity maps) and the rate field itself, FP64, against the oracle."""
+    conservativity maps), formed by the library (MGENKF_FIELD_GAMMA_NORM), and
+    the rate field itself, FP64, against the oracle."""
     if model == "burgers":
         w = W.burgers_small()
     else:

@@ -821,6 +821,50 @@ __global__ void __launch_bounds__(kMarchMaxThreads, 1)
         __syncthreads();
         if (j + 1 <= R + 5) load_row(j + 1);
 
+        if (j >= 8 && j <= R + 5) {
+            // steady state: the three stages without branches between them, so
+            // that the compiler interleaves their independent arithmetic (with
+            // one or two CTAs per SM the latency is hidden by this ILP)
+            float2 L3[4], L2[4], L1[4];
+            march_rhs<true>(X, P, nb, 2, j, c_m1, c_c, c_p1, u.inv_h, u.inv_2h, mu, kap, yf3, L3);
+            march_rhs<true>(X, P, nb, 1, j, b_m1, b_c, b_p1, u.inv_h, u.inv_2h, mu, kap, yf2, L2);
+            march_rhs<true>(X, P, nb, 0, j, a_m1, a_c, a_p1, u.inv_h, u.inv_2h, mu, kap, yf1, L1);
+            {
+                const float2 *R0 = X + (60 + 4 * ((j - 5) & 7)) * P + sl.own;
+                const float2 q[4] = {c_c.rho, c_c.mx, c_c.my, c_c.E};
+                float *o = u.out + wrap_index(u.y0 - 8 + j, n) * n;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 base = R0[k * P];
+                    const float2 res = fma2(f2(2.f / 3.f), add2(sub2(q[k], base), mul2(dt, L3[k])), base);
+                    if (wa) o[k * plane + xa] = res.x;
+                    if (wb) o[k * plane + xb] = res.y;
+                }
+            }
+            {
+                const float2 *R0 = X + (60 + 4 * ((j - 3) & 7)) * P + sl.own;
+                const float2 q[4] = {b_c.rho, b_c.mx, b_c.my, b_c.E};
+                float2 sv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 base = R0[k * P];
+                    sv[k] = fma2(f2(0.25f), add2(sub2(q[k], base), mul2(dt, L2[k])), base);
+                }
+                c_m1 = c_c;
+                c_c = c_p1;
+                c_p1 = make_rec(sv[0], sv[1], sv[2], sv[3], gm1);
+            }
+            {
+                const float2 q[4] = {a_c.rho, a_c.mx, a_c.my, a_c.E};
+                float2 sv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) sv[k] = add2(q[k], mul2(dt, L1[k]));
+                b_m1 = b_c;
+                b_c = b_p1;
+                b_p1 = make_rec(sv[0], sv[1], sv[2], sv[3], gm1);
+            }
+            continue;
+        }
         // stage 3 at row y0 - 8 + j: the new state
         if (j == 7) march_rhs<false>(X, P, nb, 2, j, c_m1, c_c, c_p1, u.inv_h, u.inv_2h, mu, kap, yf3, L);
         if (j >= 8) {

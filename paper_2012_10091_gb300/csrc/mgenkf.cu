@@ -952,7 +952,7 @@ struct mgenkf_batch {
     cudaStream_t s0 = nullptr;
     bool own_s0 = false;  // created here when the caller passed the legacy stream
     std::vector<cudaStream_t> aux;
-    int nbranch = 1;  // analysis branches (streams aux[0 .. nbranch))
+    int nbranch = 1;  // analysis branches (streams aux[0 .. nbranch)); the forecast of grid size k runs on aux[nbranch + k]
     std::vector<int> branch;  // branch of each problem
     std::vector<cudaEvent_t> ev;
     double *obs_stage = nullptr;
@@ -1160,7 +1160,7 @@ extern "C" mgenkf_status mgenkf_batch_create(const mgenkf_handle *handles, int32
         }
     }
     const int nsizes = (int)b->sizes.size();
-    const int nstreams = std::max(nsizes, b->nbranch);
+    const int nstreams = nsizes + b->nbranch;
     for (int k = 0; k < nstreams; ++k) {
         cudaStream_t s;
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(MGENKF_ERR_CUDA, "stream");
@@ -1190,34 +1190,40 @@ extern "C" mgenkf_status mgenkf_batch_destroy(mgenkf_batch_t b) {
 extern "C" const char *mgenkf_batch_last_error(mgenkf_batch_t b) { return b ? b->err.c_str() : ""; }
 
 // forecast of every handle: one launch sequence per grid size, each on its own
-// stream, joined back into s0
-static mgenkf_status batch_forecast(mgenkf_batch *b, int nsteps) {
+// stream; the event ev[1 + k] marks the end of size k's steps.  join: s0
+// waits for all of them (otherwise the analyses wait for their own sizes).
+static mgenkf_status batch_forecast(mgenkf_batch *b, int nsteps, bool join) {
     B_CUDA(cudaEventRecord(b->ev[0], b->s0));
     const int ns = (int)b->sizes.size();
     for (int k = 0; k < ns; ++k) {
-        if (!b->units[k]) continue;
-        cudaStream_t s = b->aux[k];
+        cudaStream_t s = b->aux[b->nbranch + k];
         B_CUDA(cudaStreamWaitEvent(s, b->ev[0], 0));
-        cudaError_t e = ns2d_forecast_table(b->d_groups[k], b->ngroups[k], b->units[k], b->sizes[k], nsteps, b->gamma,
-                                            b->mu, b->prandtl, s);
-        if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("batched forecast: ") + cudaGetErrorString(e));
+        if (b->units[k]) {
+            cudaError_t e = ns2d_forecast_table(b->d_groups[k], b->ngroups[k], b->units[k], b->sizes[k], nsteps,
+                                                b->gamma, b->mu, b->prandtl, s);
+            if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("batched forecast: ") + cudaGetErrorString(e));
+        }
         B_CUDA(cudaEventRecord(b->ev[1 + k], s));
     }
-    for (int k = 0; k < ns; ++k)
-        if (b->units[k]) B_CUDA(cudaStreamWaitEvent(b->s0, b->ev[1 + k], 0));
+    if (join)
+        for (int k = 0; k < ns; ++k) B_CUDA(cudaStreamWaitEvent(b->s0, b->ev[1 + k], 0));
     return MGENKF_OK;
 }
 
 // analyses and prolongations of every handle, spread over the auxiliary streams
+// Each problem's analysis waits only for the forecasts of its own two grid
+// sizes, so analyses of problems whose grids are done run beside the
+// remaining forecasts.
 static mgenkf_status batch_analyse(mgenkf_batch *b) {
     const int base = 1 + (int)b->sizes.size();
-    B_CUDA(cudaEventRecord(b->ev[base], b->s0));
     const int ns = b->nbranch;
-    for (int k = 0; k < ns; ++k) B_CUDA(cudaStreamWaitEvent(b->aux[k], b->ev[base], 0));
+    for (int k = 0; k < ns; ++k) B_CUDA(cudaStreamWaitEvent(b->aux[k], b->ev[0], 0));
     for (size_t j = 0; j < b->hs.size(); ++j) {
         mgenkf_ctx *h = b->hs[j];
         cudaStream_t keep = h->stream;
         h->stream = b->aux[b->branch[j]];
+        B_CUDA(cudaStreamWaitEvent(h->stream, b->ev[1 + size_index(b, h->nc)], 0));
+        B_CUDA(cudaStreamWaitEvent(h->stream, b->ev[1 + size_index(b, h->nf)], 0));
         mgenkf_status st = analyse_impl(h, b->obs_stage + b->obs_off[j], nullptr);
         if (st == MGENKF_OK) {
             launch_innov_rms(h->Z, h->ne, h->ny, b->innov + j, h->stream);
@@ -1230,13 +1236,15 @@ static mgenkf_status batch_analyse(mgenkf_batch *b) {
         B_CUDA(cudaEventRecord(b->ev[base + 1 + k], b->aux[k]));
         B_CUDA(cudaStreamWaitEvent(b->s0, b->ev[base + 1 + k], 0));
     }
+    // every forecast stream joins back too (a size no problem's analysis waited on)
+    for (int k = 0; k < (int)b->sizes.size(); ++k) B_CUDA(cudaStreamWaitEvent(b->s0, b->ev[1 + k], 0));
     return MGENKF_OK;
 }
 
 extern "C" mgenkf_status mgenkf_batch_forecast(mgenkf_batch_t b, int32_t nsteps) {
     if (!b || nsteps < 0) return MGENKF_ERR_INVALID_ARG;
     b->err.clear();
-    return batch_forecast(b, nsteps);
+    return batch_forecast(b, nsteps, true);
 }
 
 extern "C" mgenkf_status mgenkf_batch_cycle(mgenkf_batch_t b, int32_t nsteps, const double *y_obs,
@@ -1250,7 +1258,7 @@ extern "C" mgenkf_status mgenkf_batch_cycle(mgenkf_batch_t b, int32_t nsteps, co
         b->exec = nullptr;
         b->graph = nullptr;
         B_CUDA(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed));
-        mgenkf_status st = batch_forecast(b, nsteps);
+        mgenkf_status st = batch_forecast(b, nsteps, false);
         if (st == MGENKF_OK) st = batch_analyse(b);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(b->s0, &g);

@@ -175,6 +175,18 @@ mgenkf_status mgenkf_get_field(mgenkf_handle h, int32_t field, double *out, size
  * status recorded since the last call (MGENKF_OK if none). */
 mgenkf_status mgenkf_sync(mgenkf_handle h);
 
+/* Limit, in SM clock cycles, of the tensor-core member update's wait for its
+ * operands (mixed-precision handles whose update runs on the tensor cores;
+ * default about one second at 2 GHz; 0 = give up at the first unsuccessful
+ * poll).  The paper has no counterpart: every device wait of this library is
+ * bounded so that a stalled copy returns MGENKF_ERR_TIMEOUT instead of
+ * hanging the GPU, and this sets that bound.  A wait that runs out records
+ * MGENKF_ERR_TIMEOUT (reported by mgenkf_sync), issues no tensor-core work,
+ * waits with the default bound for the kernel's own copies to land, frees its
+ * tensor memory and leaves the members and the fine run unchanged.
+ * Errors: MGENKF_ERR_INVALID_ARG for cycles < 0. */
+mgenkf_status mgenkf_set_wait_limit(mgenkf_handle h, int64_t cycles);
+
 /* Checkpoint: write / read fine state, members and analysis counter to a file
  * (binary, native endianness, with a header that records the sizes). */
 mgenkf_status mgenkf_save(mgenkf_handle h, const char *path);

@@ -791,6 +791,14 @@ extern "C" mgenkf_status mgenkf_get_field(mgenkf_handle h, int32_t field, double
     }
 }
 
+extern "C" mgenkf_status mgenkf_set_wait_limit(mgenkf_handle h, int64_t cycles) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    if (cycles < 0) H_FAIL(MGENKF_ERR_INVALID_ARG, "the wait limit is a number of cycles >= 0");
+    h->tc.wait_limit = cycles > 0 ? cycles : 0;
+    return MGENKF_OK;
+}
+
 extern "C" mgenkf_status mgenkf_sync(mgenkf_handle h) {
     if (!h) return MGENKF_ERR_INVALID_ARG;
     H_CUDA(cudaStreamSynchronize(h->stream));
@@ -799,8 +807,9 @@ extern "C" mgenkf_status mgenkf_sync(mgenkf_handle h) {
     if (st != 0) {
         H_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
         H_CUDA(cudaStreamSynchronize(h->stream));
-        h->err = st == MGENKF_ERR_NOT_SPD ? "innovation matrix not SPD: members and fine run left unchanged"
-                                         : "non-finite observation: members and fine run left unchanged";
+        h->err = st == MGENKF_ERR_NOT_SPD   ? "innovation matrix not SPD: members and fine run left unchanged"
+                 : st == MGENKF_ERR_TIMEOUT ? "a bounded device wait ran out: members and fine run left unchanged"
+                                            : "non-finite observation: members and fine run left unchanged";
         return (mgenkf_status)st;
     }
     return MGENKF_OK;

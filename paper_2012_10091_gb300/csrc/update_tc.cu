@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ CUten
                                                    const __grid_constant__ CUtensorMap map_t,
                                                    const __grid_constant__ CUtensorMap map_m,
                                                    float *__restrict__ dC, int nx, int ne, int kblocks,
-                                                   int ntile, int tmem_cols, int *status) {
+                                                   int ntile, int tmem_cols, long long wait_limit, int *status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned operand buffers
     unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ CUten
     const uint32_t tmem = *tmem_slot;
 
     if (tid == 0) {
-        if (!mbar_wait(&bars[0], 0)) {
+        // the operand wait uses the plan's limit; an expired wait issues no MMA
+        if (!mbar_wait(&bars[0], 0, wait_limit)) {
             s_fail = 1;
         } else {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ CUten
     if (!ok) {
         if (tid == 0) {
             atomicCAS(status, 0, kStTimeout);
-            mbar_wait(&bars[0], 0);  // let our own copies land (bounded) before the CTA exits
+            mbar_wait(&bars[0], 0);  // let our own copies land (default bound) before the CTA exits
         }
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -220,6 +221,7 @@ bool update_tc_prepare(UpdateTcPlan *plan, const __nv_bfloat16 *X16, int ldx, in
     if (plan->smem < min_smem) plan->smem = min_smem;
     plan->nx = nx;
     plan->ne = ne;
+    plan->wait_limit = kWaitLimitCycles;
     if (!encode_kmajor(&plan->map_x, X16, ldx, nx, kTileM)) return false;
     if (!encode_kmajor(&plan->map_t, Tt, ldx, ntpad, ntpad)) return false;
     if (!encode_members(&plan->map_m, members, nx, ne)) return false;
@@ -235,7 +237,7 @@ cudaError_t launch_update_tc(const UpdateTcPlan &plan, float *members, float *dC
     count_launches(1);
     const int grid = (plan.nx + kTileM - 1) / kTileM;
     k_update_tc<<<grid, 128, plan.smem, s>>>(plan.map_x, plan.map_t, plan.map_m, dC, plan.nx, plan.ne, plan.kblocks,
-                                             plan.ntile, plan.tmem_cols, status);
+                                             plan.ntile, plan.tmem_cols, plan.wait_limit, status);
     return cudaGetLastError();
 }
 

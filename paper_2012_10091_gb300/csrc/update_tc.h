@@ -17,6 +17,7 @@ struct UpdateTcPlan {
     const float *members;
     int kblocks, ntile, tmem_cols, nx, ne;
     size_t smem;
+    long long wait_limit;  // SM clock cycles the kernel waits for its operands (default about a second)
     bool ready;
 };
 

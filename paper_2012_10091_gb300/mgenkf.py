@@ -88,6 +88,7 @@ def _load():
         "mgenkf_set_prolong_cnn": [P, P],
         "mgenkf_set_regularisation": [P, f64],
         "mgenkf_set_recentre": [P, i32],
+        "mgenkf_set_wait_limit": [P, ctypes.c_int64],
         "mgenkf_set_filter": [P, f64],
         "mgenkf_batch_create": [P, i32, P, ctypes.POINTER(P)],
         "mgenkf_batch_cycle": [P, i32, P, P],
@@ -420,6 +421,10 @@ class MGEnKF:
     def set_recentre(self, on=True):
         """Re-centre the forecast ensemble on x^C* before each analysis (fine-to-coarse feedback)."""
         _check(lib.mgenkf_set_recentre(self.h, 1 if on else 0), "mgenkf_set_recentre", self.h)
+
+    def set_wait_limit(self, cycles):
+        """Bound (SM clock cycles) of the tensor-core member update's operand wait."""
+        _check(lib.mgenkf_set_wait_limit(self.h, int(cycles)), "mgenkf_set_wait_limit", self.h)
 
     def gamma_residual(self):
         """Conservativity residual of the fine run (Eq. Conservativity_rhov), FP64."""

@@ -104,3 +104,33 @@ def test_misaligned_fp32_ns_state_is_rejected(M):
     M.mgk_forecast(M.MGENKF_NS2D, M.MGENKF_MIXED, x, 1, n, 1.0, 1e-4, 1e-3, 1.4, 0.72, nsteps=1)
     torch.cuda.synchronize()
     assert torch.allclose(x[3 * n * n:], torch.full_like(x[3 * n * n:], 10.0))
+
+
+def test_tensor_core_wait_that_runs_out_is_reported(M):
+    """The member update's operand wait is bounded.  With its bound set to 0
+    cycles the wait runs out at the first poll (the copy it waits for was just
+    issued): the kernel records MGENKF_ERR_TIMEOUT, issues no tensor-core work,
+    lets its own copies land, frees its tensor memory and returns; the members
+    and the fine run are unchanged and the next analysis with the default
+    bound succeeds.  No GPU fault or hang is involved."""
+    w = W.burgers_custom(1024, 4, 32, 64, obs_kind="random", precision="mixed")
+    g, inp = _handle(M, w, precision="mixed")
+    f0, m0 = g.get_state()
+    rng = np.random.default_rng(5)
+    yo = rng.standard_normal(w.ny) * 0.3
+    g.set_wait_limit(0)
+    g.analyse(yo)
+    g.prolong_correct()
+    assert g.sync() == 7  # MGENKF_ERR_TIMEOUT
+    f1, m1 = g.get_state()
+    np.testing.assert_array_equal(f1, f0)
+    np.testing.assert_array_equal(m1, m0)
+    g.set_wait_limit(2_000_000_000)
+    g.analyse(yo)
+    g.prolong_correct()
+    assert g.sync() == 0
+    f2, m2 = g.get_state()
+    assert np.max(np.abs(m2 - m0)) > 0 and np.max(np.abs(f2 - f0)) > 0
+    with pytest.raises(M.MGEnKFError):
+        g.set_wait_limit(-1)
+    g.close()

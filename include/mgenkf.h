@@ -181,9 +181,12 @@ mgenkf_status mgenkf_sync(mgenkf_handle h);
  * poll).  The paper has no counterpart: every device wait of this library is
  * bounded so that a stalled copy returns MGENKF_ERR_TIMEOUT instead of
  * hanging the GPU, and this sets that bound.  A wait that runs out records
- * MGENKF_ERR_TIMEOUT (reported by mgenkf_sync), issues no tensor-core work,
- * waits with the default bound for the kernel's own copies to land, frees its
- * tensor memory and leaves the members and the fine run unchanged.
+ * MGENKF_ERR_TIMEOUT (reported by mgenkf_sync); the CTA issues no further
+ * tensor-core work, waits with the default bound for the copies and products
+ * it has in flight, frees its tensor memory and returns, and the kernels after
+ * it in the cycle leave the fine run unchanged.  Member tiles a CTA finished
+ * before its wait ran out keep their update; with a bound of 0 the first wait
+ * runs out before any tile is updated and the members stay unchanged.
  * Errors: MGENKF_ERR_INVALID_ARG for cycles < 0. */
 mgenkf_status mgenkf_set_wait_limit(mgenkf_handle h, int64_t cycles);
 

@@ -96,8 +96,9 @@ def parse():
                          "(fine 512^2 / coarse 128^2, Ne=64, 2048 observations), ns2d_cnn "
                          "(fine 1024^2 / coarse 256^2, Ne=64, learned prolongation correction) or "
                          "dual (inlet-parameter estimation on the Burgers inlet model, 800 nodes, ratio 4)")
-    ap.add_argument("--cnn-pairs", type=int, default=400,
-                    help="training pairs generated for ns2d_cnn (cycles of lockstep runs)")
+    ap.add_argument("--cnn-pairs", type=int, default=2000,
+                    help="training pairs generated for ns2d_cnn (cycles of lockstep runs; 2000 take "
+                         "about 90 s to generate on one GB300)")
     ap.add_argument("--cnn-epochs", type=int, default=10)
     ap.add_argument("--tiles", default=None,
                     help="batched: JSON tile table to load (autotuned and written there if missing)")

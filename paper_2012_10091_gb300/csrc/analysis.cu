@@ -7,14 +7,18 @@
 // row ne = y^o - H^C x^C*), gain coefficients T [(ne+1)][ne] (column c of
 // T = Y^T C^-1 [D | d*] contiguous).  Every covariance-type reduction, the
 // Cholesky factorisation and the triangular solves run in FP64.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <type_traits>
+#include <vector>
 
 #include <cooperative_groups.h>
 
 #include "analysis.h"
+#include "batch_analysis.h"
 #include "common.cuh"
+#include "update_tc.h"
 
 namespace mgk {
 namespace cg = cooperative_groups;
@@ -29,15 +33,17 @@ static inline int grid_for(size_t n, int block, int cap = 8 * kNumSMs) {
 // ---------------------------------------------------------------------------
 // restriction Pi_C (injection), Algorithm 4 step 4
 // ---------------------------------------------------------------------------
+// Kernel bodies take their block index and block count as arguments, so that
+// the grouped analysis of many problems (one launch per step, blocks mapped to
+// problems by a table) runs the same per-element arithmetic as one handle.
 template <typename T>
-__global__ void k_restrict(const T *__restrict__ fine, T *__restrict__ xs, int dim, int V, int nc,
-                           int r) {
+__device__ __forceinline__ void restrict_body(const T *__restrict__ fine, T *__restrict__ xs, int dim, int V,
+                                              int nc, int r, size_t blk, size_t nblk, T *__restrict__ zero) {
     const size_t nf = (size_t)nc * r;
     const size_t cpl = dim == 1 ? (size_t)nc : (size_t)nc * nc;
     const size_t fpl = dim == 1 ? nf : nf * nf;
     const size_t total = (size_t)V * cpl;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = blk * blockDim.x + threadIdx.x; i < total; i += nblk * blockDim.x) {
         const size_t v = i / cpl, k = i % cpl;
         size_t src;
         if (dim == 1) {
@@ -47,7 +53,13 @@ __global__ void k_restrict(const T *__restrict__ fine, T *__restrict__ xs, int d
             src = (size_t)r * jy * nf + (size_t)r * jx;
         }
         xs[i] = fine[v * fpl + src];
+        if (zero) zero[i] = T(0);  // the coarse correction, cleared before the analysis writes it
     }
+}
+
+template <typename T>
+__global__ void k_restrict(const T *__restrict__ fine, T *__restrict__ xs, int dim, int V, int nc, int r) {
+    restrict_body<T>(fine, xs, dim, V, nc, r, blockIdx.x, gridDim.x, nullptr);
 }
 
 template <typename T>
@@ -61,17 +73,24 @@ void launch_restrict(const T *fine, T *xstar, int dim, int V, int nc, int r, cud
 // predicted observations H^C x (Algorithm 3 step 2): sparse 4- or 16-tap rows
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_obs_apply(const T *__restrict__ members, const T *__restrict__ xstar, size_t nx,
-                            int ne, int ny, int taps, const int32_t *__restrict__ tap_idx,
-                            const double *__restrict__ tap_w, double *__restrict__ yf) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y;
+__device__ __forceinline__ void obs_apply_body(const T *__restrict__ members, const T *__restrict__ xstar,
+                                               size_t nx, int ne, int ny, int taps,
+                                               const int32_t *__restrict__ tap_idx,
+                                               const double *__restrict__ tap_w, double *__restrict__ yf, int bx,
+                                               int i) {
+    const int j = bx * blockDim.x + threadIdx.x;
     if (j >= ny) return;
     const T *x = i < ne ? members + (size_t)i * nx : xstar;
     double acc = 0.0;
-    for (int t = 0; t < taps; ++t)
-        acc += tap_w[(size_t)j * taps + t] * (double)x[tap_idx[(size_t)j * taps + t]];
+    for (int t = 0; t < taps; ++t) acc = fma(tap_w[(size_t)j * taps + t], (double)x[tap_idx[(size_t)j * taps + t]], acc);
     yf[(size_t)i * ny + j] = acc;
+}
+
+template <typename T>
+__global__ void k_obs_apply(const T *__restrict__ members, const T *__restrict__ xstar, size_t nx, int ne, int ny,
+                            int taps, const int32_t *__restrict__ tap_idx, const double *__restrict__ tap_w,
+                            double *__restrict__ yf) {
+    obs_apply_body<T>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf, blockIdx.x, blockIdx.y);
 }
 
 template <typename T>
@@ -85,15 +104,16 @@ void launch_obs_apply(const T *members, const T *xstar, size_t nx, int ne, int n
 // ---------------------------------------------------------------------------
 // observation means and innovations (Algorithm 1 step 4; Algorithm 4 step 5)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_obs_mean(const double *__restrict__ yf,
-                                                  const double *__restrict__ yo, int ne, double inv_ne, int ny,
-                                                  double *__restrict__ ybar, double *__restrict__ Z,
-                                                  int *status) {
+// yo_copy (if not NULL) receives y^o as read
+__device__ __forceinline__ void obs_mean_body(const double *__restrict__ yf, const double *__restrict__ yo, int ne,
+                                              double inv_ne, int ny, double *__restrict__ ybar,
+                                              double *__restrict__ Z, int *status, int blk,
+                                              double *__restrict__ yo_copy) {
     // 32 observations per CTA (lane), 8 slices of the members (warp); the slice
     // sums are combined in a fixed order.
     __shared__ double part[8][33];
     const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
-    const int j = blockIdx.x * 32 + lane;
+    const int j = blk * 32 + lane;
     double acc = 0.0;
     if (j < ny)
         for (int i = slice; i < ne; i += 8) acc += yf[(size_t)i * ny + j];
@@ -106,8 +126,15 @@ __global__ void __launch_bounds__(256) k_obs_mean(const double *__restrict__ yf,
         ybar[j] = sum * inv_ne;
         const double y = yo[j];
         if (!isfinite(y)) atomicCAS(status, 0, kStNonFinite);
+        if (yo_copy) yo_copy[j] = y;
         Z[(size_t)ne * ny + j] = y - yf[(size_t)ne * ny + j];
     }
+}
+
+__global__ void __launch_bounds__(256) k_obs_mean(const double *__restrict__ yf, const double *__restrict__ yo,
+                                                  int ne, double inv_ne, int ny, double *__restrict__ ybar,
+                                                  double *__restrict__ Z, int *status) {
+    obs_mean_body(yf, yo, ne, inv_ne, ny, ybar, Z, status, blockIdx.x, nullptr);
 }
 
 void launch_obs_mean(const double *yf, const double *yo, int ne, int ny, double *ybar, double *Z,
@@ -117,7 +144,7 @@ void launch_obs_mean(const double *yf, const double *yo, int ne, int ny, double 
 }
 
 // RMS of the innovation d* = y^o - H^C x^C* (one value; fixed-order FP64 sums)
-__global__ void __launch_bounds__(256) k_innov_rms(const double *__restrict__ d, int ny, double *__restrict__ out) {
+__device__ __forceinline__ void innov_rms_body(const double *__restrict__ d, int ny, double *__restrict__ out) {
     __shared__ double part[256];
     double acc = 0.0;
     for (int j = threadIdx.x; j < ny; j += 256) acc = fma(d[j], d[j], acc);
@@ -130,6 +157,10 @@ __global__ void __launch_bounds__(256) k_innov_rms(const double *__restrict__ d,
     if (threadIdx.x == 0) out[0] = sqrt(part[0] / ny);
 }
 
+__global__ void __launch_bounds__(256) k_innov_rms(const double *__restrict__ d, int ny, double *__restrict__ out) {
+    innov_rms_body(d, ny, out);
+}
+
 void launch_innov_rms(const double *Z, int ne, int ny, double *out, cudaStream_t s) {
     k_innov_rms<<<1, 256, 0, s>>>(Z + (size_t)ne * ny, ny, out);
     count_launches(1);
@@ -140,12 +171,13 @@ void launch_innov_rms(const double *Z, int ne, int ny, double *out, cudaStream_t
 // the Ne x Ny perturbation matrix (flat index o = i Ny + j).  gen_eps: 0 = eps
 // given, 1 = normals in FP64, 2 = Box-Muller in FP32 (the mixed path).
 template <bool F32>
-__global__ void k_obs_perturb(const double *__restrict__ yf, const double *__restrict__ ybar,
-                              const double *__restrict__ yo, double *__restrict__ eps, int gen_eps,
-                              uint64_t seed, const uint64_t *__restrict__ cycle, double sigma, int ne,
-                              int ny, double isq, double *__restrict__ Y, double *__restrict__ Z) {
+__device__ __forceinline__ void obs_perturb_body(const double *__restrict__ yf, const double *__restrict__ ybar,
+                                                 const double *__restrict__ yo, double *__restrict__ eps,
+                                                 int gen_eps, uint64_t seed, const uint64_t *__restrict__ cycle,
+                                                 double sigma, int ne, int ny, double isq, double *__restrict__ Y,
+                                                 double *__restrict__ Z, size_t blk) {
     const size_t total = (size_t)ne * ny;
-    const size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t b = blk * blockDim.x + threadIdx.x;
     if (4 * b >= total) return;
     double z[4];
     if (gen_eps) {
@@ -159,22 +191,32 @@ __global__ void k_obs_perturb(const double *__restrict__ yf, const double *__res
     for (int l = 0; l < 4; ++l) {
         const size_t o = 4 * b + l;
         if (o < total) {
+            // explicit roundings: no contraction into an FMA, whatever the
+            // kernel the body is inlined into
             double e;
             if (gen_eps) {
-                e = sigma * z[l];
+                e = __dmul_rn(sigma, z[l]);
                 eps[o] = e;
             } else {
                 e = eps[o];
             }
             const double f = yf[o];
-            Y[o] = (f - ybar[j]) * isq;
-            Z[o] = yo[j] + e - f;
+            Y[o] = __dmul_rn(__dsub_rn(f, ybar[j]), isq);
+            Z[o] = __dsub_rn(__dadd_rn(yo[j], e), f);
         }
         if (++j == ny) {
             j = 0;
             ++i;
         }
     }
+}
+
+template <bool F32>
+__global__ void k_obs_perturb(const double *__restrict__ yf, const double *__restrict__ ybar,
+                              const double *__restrict__ yo, double *__restrict__ eps, int gen_eps, uint64_t seed,
+                              const uint64_t *__restrict__ cycle, double sigma, int ne, int ny, double isq,
+                              double *__restrict__ Y, double *__restrict__ Z) {
+    obs_perturb_body<F32>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma, ne, ny, isq, Y, Z, blockIdx.x);
 }
 
 void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, double *eps,
@@ -218,10 +260,9 @@ template void launch_recentre<double>(double *, size_t, int, const double *, con
 // ensemble mean (FP64 accuracy) and normalised anomalies X
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_ens_anom(const T *__restrict__ m, size_t nx, int ne, double inv_ne,
-                                                  double isq, double *__restrict__ X64,
-                                                  __nv_bfloat16 *__restrict__ X16, int ldx,
-                                                  const int *status) {
+__device__ __forceinline__ void ens_anom_body(const T *__restrict__ m, size_t nx, int ne, double inv_ne, double isq,
+                                              double *__restrict__ X64, __nv_bfloat16 *__restrict__ X16, int ldx,
+                                              const int *status, size_t blk) {
     // CTA: 32 consecutive points (lane) x the members split over the 8 warps.
     // Mean: per-warp slice sums combined in FP64 in a fixed order by warp 0;
     // then the normalised anomalies: FP64 member-major rows, or BF16
@@ -237,7 +278,7 @@ __global__ void __launch_bounds__(256) k_ens_anom(const T *__restrict__ m, size_
     __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(mean + 32);      // [32][ldx + 8]
     if (*status) return;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const size_t p0 = blockIdx.x * (size_t)32;
+    const size_t p0 = blk * 32;
     const size_t p = p0 + lane;
     const bool ok = p < nx;
     double slice;
@@ -292,11 +333,23 @@ __global__ void __launch_bounds__(256) k_ens_anom(const T *__restrict__ m, size_
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) k_ens_anom(const T *__restrict__ m, size_t nx, int ne, double inv_ne,
+                                                  double isq, double *__restrict__ X64,
+                                                  __nv_bfloat16 *__restrict__ X16, int ldx, const int *status) {
+    ens_anom_body<T>(m, nx, ne, inv_ne, isq, X64, X16, ldx, status, blockIdx.x);
+}
+
+// dynamic shared memory of the anomaly kernel for BF16 rows of ldx values
+static size_t ens_anom_smem(int ldx) {
+    return sizeof(double) * 9 * 32 + sizeof(__nv_bfloat16) * 32 * (size_t)(ldx + 8);
+}
+
+template <typename T>
 void launch_ens_anom(const T *members, size_t nx, int ne, double *X64, __nv_bfloat16 *X16,
                      const int *status, cudaStream_t s) {
     count_launches(1);
     const int ldx = (ne + 15) / 16 * 16;
-    const size_t smem = sizeof(double) * 9 * 32 + sizeof(__nv_bfloat16) * 32 * (size_t)(ldx + 8);
+    const size_t smem = ens_anom_smem(ldx);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_ens_anom<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_ens_anom<T><<<ceil_div(nx, 32), 256, smem, s>>>(members, nx, ne, 1.0 / ne, 1.0 / std::sqrt((double)(ne - 1)),
@@ -356,25 +409,39 @@ __device__ __forceinline__ double gemm_nt_tile(const double *__restrict__ A, int
     return acc;
 }
 
-__global__ void k_gemm_nt(const double *__restrict__ A, int m, const double *__restrict__ B1, int n1,
-                          const double *__restrict__ B2, int n2, int K, double divisor, double diag,
-                          double *__restrict__ out1, double *__restrict__ out2, const int *status) {
-    if (status && *status) return;
+// Output tile (bx, by) of [out1 | out2^T]: over the whole of K with the
+// epilogue (part == NULL), or over K chunk bz into the split-K partial sums.
+__device__ __forceinline__ void gemm_nt_block(const double *__restrict__ A, int m, const double *__restrict__ B1,
+                                              int n1, const double *__restrict__ B2, int n2, int K, double divisor,
+                                              double diag, double *__restrict__ out1, double *__restrict__ out2,
+                                              int bx, int by, int bz, int kchunk, double *__restrict__ part) {
     const bool sym = B1 == A && n1 == m;
-    if (sym && blockIdx.x < blockIdx.y) return;  // mirrored from tile (x, y)
+    if (sym && bx < by) return;  // mirrored from tile (by, bx) (by the reduce when split)
     __shared__ double As[16][33];
     __shared__ double Bs[16][33];
-    const int a0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
-    const double acc = gemm_nt_tile(A, m, B1, n1, B2, n2, K, 0, K, a0, c0, As, Bs);
+    const int a0 = by * 16, c0 = bx * 16;
+    const int kb = part ? bz * kchunk : 0, ke = part ? min(K, kb + kchunk) : K;
+    const double acc = gemm_nt_tile(A, m, B1, n1, B2, n2, K, kb, ke, a0, c0, As, Bs);
     const int a = a0 + (threadIdx.x >> 4), c = c0 + (threadIdx.x & 15);
+    if (part) {
+        if (a < m && c < n1 + n2) part[((size_t)bz * m + a) * (n1 + n2) + c] = acc;
+        return;
+    }
     if (a < m) {
         if (c < n1) {
             out1[(size_t)a * n1 + c] = (a == c ? diag : 0.0) + acc / divisor;
-            if (sym && blockIdx.x > blockIdx.y) out1[(size_t)c * n1 + a] = acc / divisor;
+            if (sym && bx > by) out1[(size_t)c * n1 + a] = acc / divisor;
         } else if (c < n1 + n2) {
             out2[(size_t)(c - n1) * m + a] = acc / divisor;
         }
     }
+}
+
+__global__ void k_gemm_nt(const double *__restrict__ A, int m, const double *__restrict__ B1, int n1,
+                          const double *__restrict__ B2, int n2, int K, double divisor, double diag,
+                          double *__restrict__ out1, double *__restrict__ out2, const int *status) {
+    if (status && *status) return;
+    gemm_nt_block(A, m, B1, n1, B2, n2, K, divisor, diag, out1, out2, blockIdx.x, blockIdx.y, 0, K, nullptr);
 }
 
 // Partial sums of k_gemm_nt over K chunks (split-K), combined in chunk order.
@@ -382,22 +449,16 @@ __global__ void k_gemm_nt_split(const double *__restrict__ A, int m, const doubl
                                 int n1, const double *__restrict__ B2, int n2, int K, int kchunk,
                                 double *__restrict__ part, const int *status) {
     if (status && *status) return;
-    if (B1 == A && n1 == m && blockIdx.x < blockIdx.y) return;  // symmetric: the reduce mirrors
-    __shared__ double As[16][33];
-    __shared__ double Bs[16][33];
-    const int a0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
-    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    const double acc = gemm_nt_tile(A, m, B1, n1, B2, n2, K, kb, ke, a0, c0, As, Bs);
-    const int a = a0 + (threadIdx.x >> 4), c = c0 + (threadIdx.x & 15);
-    if (a < m && c < n1 + n2) part[((size_t)blockIdx.z * m + a) * (n1 + n2) + c] = acc;
+    gemm_nt_block(A, m, B1, n1, B2, n2, K, 1.0, 0.0, nullptr, nullptr, blockIdx.x, blockIdx.y, blockIdx.z, kchunk,
+                  part);
 }
 
-__global__ void k_gemm_nt_reduce(const double *__restrict__ part, int nsplit, int m, int n1, int n2, bool sym,
-                                 double divisor, double diag, double *__restrict__ out1,
-                                 double *__restrict__ out2, const int *status) {
-    if (status && *status) return;
+__device__ __forceinline__ void gemm_nt_reduce_body(const double *__restrict__ part, int nsplit, int m, int n1,
+                                                    int n2, bool sym, double divisor, double diag,
+                                                    double *__restrict__ out1, double *__restrict__ out2, int blk,
+                                                    int nblk) {
     const int ncol = n1 + n2;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * ncol; e += gridDim.x * blockDim.x) {
+    for (int e = blk * blockDim.x + threadIdx.x; e < m * ncol; e += nblk * blockDim.x) {
         const int a = e / ncol, c = e % ncol;
         // below the diagonal tiles of a symmetric out1: the mirrored element
         const bool mirror = sym && c < n1 && (c >> 4) < (a >> 4);
@@ -409,6 +470,13 @@ __global__ void k_gemm_nt_reduce(const double *__restrict__ part, int nsplit, in
         else
             out2[(size_t)(c - n1) * m + a] = acc / divisor;
     }
+}
+
+__global__ void k_gemm_nt_reduce(const double *__restrict__ part, int nsplit, int m, int n1, int n2, bool sym,
+                                 double divisor, double diag, double *__restrict__ out1,
+                                 double *__restrict__ out2, const int *status) {
+    if (status && *status) return;
+    gemm_nt_reduce_body(part, nsplit, m, n1, n2, sym, divisor, diag, out1, out2, blockIdx.x, gridDim.x);
 }
 
 int gemm_nt_splits(int m, int n1, int n2, int K) {
@@ -470,7 +538,7 @@ void launch_gemm_tn_f64(const double *Y, int ne, int ny, double diag, double *C,
 // Cholesky (right-looking, one CTA) and the two triangular solves
 // ---------------------------------------------------------------------------
 template <bool SMEM>
-__global__ void __launch_bounds__(256) k_cholesky(double *A, double *Lt, int n, int *status) {
+__device__ __forceinline__ void cholesky_body(double *A, double *Lt, int n, int *status) {
     // Right-looking Cholesky by one CTA.  Column k: pivot l = sqrt(A_kk) and its
     // reciprocal (one division per column), scale the column below it, then the
     // rank-1 update of the trailing lower triangle.  Rows padded to n+1 doubles
@@ -517,6 +585,11 @@ __global__ void __launch_bounds__(256) k_cholesky(double *A, double *Lt, int n, 
     }
 }
 
+template <bool SMEM>
+__global__ void __launch_bounds__(256) k_cholesky(double *A, double *Lt, int n, int *status) {
+    cholesky_body<SMEM>(A, Lt, n, status);
+}
+
 // Cholesky by a cluster of 8 CTAs (n <= 256).  CTA q owns the columns
 // [q w, q w + w), w = ceil(n / 8), all n rows, in shared memory.  Panel p is
 // CTA p's block of columns.  For p = 0 .. 7: CTA p factors its panel column by
@@ -553,8 +626,7 @@ __device__ __forceinline__ void chol_pivot(double d, double *y_out, int *status,
     *y_out = y;
 }
 
-__global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(288)
-    k_cholesky_cluster(double *A, double *Lt, int n, int *status) {
+__device__ __forceinline__ void cholesky_cluster_body(double *A, double *Lt, int n, int *status) {
     extern __shared__ double csm[];
     __shared__ int s_fail;
     __shared__ double s_y[32];  // 1/sqrt of the panel's pivots
@@ -653,10 +725,20 @@ __global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(288)
     cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
+__global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(288)
+    k_cholesky_cluster(double *A, double *Lt, int n, int *status) {
+    cholesky_cluster_body(A, Lt, n, status);
+}
+
+// dynamic shared memory of the clustered Cholesky of order n
+static size_t cholesky_cluster_smem(int n) {
+    return sizeof(double) * 2 * (size_t)n * ((n + kCholCluster - 1) / kCholCluster + 1);
+}
+
 void launch_cholesky(double *A, double *Lt, int n, int *status, cudaStream_t s) {
     count_launches(1);
     if (n >= 32 && n <= 256) {
-        const size_t bytes = sizeof(double) * 2 * (size_t)n * ((n + kCholCluster - 1) / kCholCluster + 1);
+        const size_t bytes = cholesky_cluster_smem(n);
         static OncePerDevice attr;
         attr.run([](int) {
             return cudaFuncSetAttribute(k_cholesky_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
@@ -677,28 +759,29 @@ void launch_cholesky(double *A, double *Lt, int n, int *status, cudaStream_t s) 
 }
 
 // Triangular solves with the factor staged in shared memory: one warp per
-// right-hand side (one CTA each, so the FP64 work of the columns spreads over
-// the SMs), lanes own rows lane + 32 m.
+// right-hand side, lanes own rows lane + 32 m.  A CTA solves the columns
+// c0 .. c0 + ncols - 1 (warp w: column c0 + w): one column per CTA spreads the
+// FP64 work of one problem's columns over the SMs; the grouped analysis of many
+// problems gives each CTA several columns, so the factor is staged once for them.
 template <int MAXR>
-__global__ void __launch_bounds__(256) k_chol_solve_smem(const double *__restrict__ L, int n,
-                                                         const double *rhs, double *out, int ncol,
-                                                         __nv_bfloat16 *out16, int ld16,
-                                                         const int *status) {
-    // 256 threads stage the unit lower factor U = L D^-1 (D = diag L) in shared
-    // memory, then warp 0 runs both substitutions for right-hand side
-    // blockIdx.x: S x = U D^2 U^T x = b as U y = b, then U^T x = D^-2 y.  With
-    // the unit diagonal no step of either substitution waits on an FP64
+__device__ __forceinline__ void chol_solve_body(const double *__restrict__ L, int n, const double *rhs, double *out,
+                                                int ncol, __nv_bfloat16 *out16, int ld16, const int *status, int c0,
+                                                int ncols) {
+    // the CTA stages the unit lower factor U = L D^-1 (D = diag L) in shared
+    // memory, then each solving warp runs both substitutions for its
+    // right-hand side: S x = U D^2 U^T x = b as U y = b, then U^T x = D^-2 y.
+    // With the unit diagonal no step of either substitution waits on an FP64
     // multiplication before its broadcast.
     extern __shared__ double sL[];  // [n][n+1]: U strictly below the diagonal; then inv_diag[n]
     if (*status) return;
-    const int c = blockIdx.x, lane = threadIdx.x & 31, ld = n + 1;
+    const int c = c0 + (threadIdx.x >> 5), lane = threadIdx.x & 31, ld = n + 1;
     double *inv = sL + (size_t)n * ld;
     for (int j = threadIdx.x; j < n; j += blockDim.x) inv[j] = 1.0 / L[(size_t)j * n + j];
     __syncthreads();
     for (int i = threadIdx.x >> 5; i < n; i += blockDim.x >> 5)
         for (int j = lane; j < i; j += 32) sL[(size_t)i * ld + j] = L[(size_t)i * n + j] * inv[j];
     __syncthreads();
-    if (threadIdx.x >= 32) return;
+    if ((threadIdx.x >> 5) >= ncols || c >= ncol) return;
     double b[MAXR];
 #pragma unroll
     for (int m = 0; m < MAXR; ++m) {
@@ -749,6 +832,16 @@ __global__ void __launch_bounds__(256) k_chol_solve_smem(const double *__restric
         }
     }
 }
+
+template <int MAXR>
+__global__ void __launch_bounds__(256) k_chol_solve_smem(const double *__restrict__ L, int n, const double *rhs,
+                                                         double *out, int ncol, __nv_bfloat16 *out16, int ld16,
+                                                         const int *status) {
+    chol_solve_body<MAXR>(L, n, rhs, out, ncol, out16, ld16, status, blockIdx.x, 1);
+}
+
+// shared memory of the staged factor of order n
+static size_t chol_solve_smem(int n) { return sizeof(double) * ((size_t)n * (n + 1) + n); }
 
 template <int MAXR>
 __global__ void __launch_bounds__(32) k_chol_solve(const double *__restrict__ L,
@@ -811,7 +904,7 @@ __global__ void __launch_bounds__(32) k_chol_solve(const double *__restrict__ L,
 void launch_chol_solve(const double *L, const double *Lt, int n, const double *rhs, double *out,
                        int ncol, __nv_bfloat16 *out16, int ld16, const int *status, cudaStream_t s) {
     count_launches(1);
-    const size_t smem = sizeof(double) * ((size_t)n * (n + 1) + n);
+    const size_t smem = chol_solve_smem(n);
     if (n <= 160 && smem <= 210 * 1024) {
         static OncePerDevice attr[2];
         if (n <= 128) {
@@ -943,6 +1036,15 @@ void launch_update_bf16(float *members, float *dC, const __nv_bfloat16 *Xt, cons
 // ---------------------------------------------------------------------------
 // prolongation of the coarse correction, Algorithm 4 step 5 second line
 // ---------------------------------------------------------------------------
+// a b + c rounded once, in the precision of T
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c) {
+    if constexpr (std::is_same<T, float>::value)
+        return fmaf(a, b, c);
+    else
+        return fma(a, b, c);
+}
+
 // periodic index of a 4-point stencil tap: c in [-1, nc + 2)
 __device__ __forceinline__ int wrap_tap(int c, int nc) {
     if (c < 0) c += nc;
@@ -956,6 +1058,40 @@ __device__ __forceinline__ int wrap_tap(int c, int nc) {
 // 2-D launch: x over the points of a fine row, y over the rows of all
 // variables, so the only divisions are by r and the periodic wraps are
 // compares.
+// 2-D: fine points bx * blockDim.x + threadIdx.x of the rows row0, row0 +
+// rstep, ... (row = v nf + fine y)
+template <typename T>
+__device__ __forceinline__ void prolong2d_rows(T *__restrict__ fine, const T *__restrict__ dC, int V, int nc, int r,
+                                               const ProlongWeights &w, int bx, int row0, int rstep) {
+    const int nf = nc * r;
+    const int fx = bx * blockDim.x + threadIdx.x;
+    if (fx >= nf) return;
+    const int Jx = fx / r, mx = fx - Jx * r;
+    int cx[4];
+    T wx[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        cx[t] = wrap_tap(Jx - 1 + t, nc);
+        wx[t] = (T)w.w[mx][t];
+    }
+    const size_t cpl = (size_t)nc * nc, fpl = (size_t)nf * nf;
+    for (int row = row0; row < V * nf; row += rstep) {
+        const int v = row / nf, fy = row - v * nf;
+        const int Jy = fy / r, my = fy - Jy * r;
+        const T *d = dC + (size_t)v * cpl;
+        T acc = T(0);
+#pragma unroll
+        for (int ty = 0; ty < 4; ++ty) {
+            const T *dr = d + (size_t)wrap_tap(Jy - 1 + ty, nc) * nc;
+            T sx = T(0);
+#pragma unroll
+            for (int tx = 0; tx < 4; ++tx) sx = fma_t(wx[tx], dr[cx[tx]], sx);
+            acc = fma_t((T)w.w[my][ty], sx, acc);
+        }
+        fine[(size_t)v * fpl + (size_t)fy * nf + fx] += acc;
+    }
+}
+
 template <typename T>
 __global__ void k_prolong_add(T *__restrict__ fine, const T *__restrict__ dC, int dim, int V, int nc,
                               int r, ProlongWeights w, const int *status) {
@@ -975,32 +1111,7 @@ __global__ void k_prolong_add(T *__restrict__ fine, const T *__restrict__ dC, in
         }
         return;
     }
-    const int fx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (fx >= nf) return;
-    const int Jx = fx / r, mx = fx - Jx * r;
-    int cx[4];
-    T wx[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        cx[t] = wrap_tap(Jx - 1 + t, nc);
-        wx[t] = (T)w.w[mx][t];
-    }
-    const size_t cpl = (size_t)nc * nc, fpl = (size_t)nf * nf;
-    for (int row = blockIdx.y; row < V * nf; row += gridDim.y) {
-        const int v = row / nf, fy = row - v * nf;
-        const int Jy = fy / r, my = fy - Jy * r;
-        const T *d = dC + (size_t)v * cpl;
-        T acc = T(0);
-#pragma unroll
-        for (int ty = 0; ty < 4; ++ty) {
-            const T *dr = d + (size_t)wrap_tap(Jy - 1 + ty, nc) * nc;
-            T sx = T(0);
-#pragma unroll
-            for (int tx = 0; tx < 4; ++tx) sx += wx[tx] * dr[cx[tx]];
-            acc += (T)w.w[my][ty] * sx;
-        }
-        fine[(size_t)v * fpl + (size_t)fy * nf + fx] += acc;
-    }
+    prolong2d_rows<T>(fine, dC, V, nc, r, w, blockIdx.x, blockIdx.y, gridDim.y);
 }
 
 template <typename T>
@@ -1139,6 +1250,256 @@ void launch_normals(uint64_t seed, uint64_t tag, uint64_t ctr0, int64_t count, d
     if (count <= 0) return;
     count_launches(1);
     k_normals<<<grid_for((size_t)((count + 3) / 4), 256), 256, 0, s>>>(seed, tag, ctr0, count, out);
+}
+
+// ---------------------------------------------------------------------------
+// grouped analysis of many problems: one launch per step, block b working on
+// block map[b].y of problem map[b].x with the single-problem kernel body
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) kg_restrict(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    const int2 e = map[blockIdx.x];
+    const GroupProb &g = P[e.x];
+    restrict_body<float>(g.fine, g.xstar, 2, 4, g.nc, g.r, e.y, ceil_div(g.nx, 256), g.dC);
+}
+
+__global__ void __launch_bounds__(128) kg_obs_apply(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    const int2 e = map[blockIdx.x];
+    const GroupProb &g = P[e.x];
+    const int gx = ceil_div(g.ny, 128);
+    obs_apply_body<float>(g.members, g.xstar, g.nx, g.ne, g.ny, g.taps, g.tap_idx, g.tap_w, g.yf, e.y % gx, e.y / gx);
+}
+
+__global__ void __launch_bounds__(256) kg_obs_mean(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    const int2 e = map[blockIdx.x];
+    const GroupProb &g = P[e.x];
+    obs_mean_body(g.yf, g.yo_in, g.ne, g.inv_ne, g.ny, g.ybar, g.Z, g.status, e.y, g.yo);
+}
+
+__global__ void __launch_bounds__(128) kg_obs_perturb(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    const int2 e = map[blockIdx.x];
+    const GroupProb &g = P[e.x];
+    obs_perturb_body<true>(g.yf, g.ybar, g.yo, g.eps, 1, g.seed, g.cycle, g.sigma, g.ne, g.ny, g.isq, g.Y, g.Z, e.y);
+}
+
+__global__ void __launch_bounds__(256) kg_innov_rms(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    const GroupProb &g = P[map[blockIdx.x].x];
+    innov_rms_body(g.Z + (size_t)g.ne * g.ny, g.ny, g.innov);
+}
+
+// block e.y = (z ty + by) tx + bx over the tiles of [S | Y^T R^-1 [D | d*]]
+// and the K chunks z (tiles strictly below the diagonal of S are not listed)
+__global__ void __launch_bounds__(256) kg_gemm(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    const int2 e = map[blockIdx.x];
+    const GroupProb &g = P[e.x];
+    if (*g.status) return;
+    const int ne = g.ne, tx = ceil_div(2 * ne + 1, 16), ty = ceil_div(ne, 16);
+    const int bx = e.y % tx, by = (e.y / tx) % ty, bz = e.y / (tx * ty);
+    gemm_nt_block(g.Y, ne, g.Y, ne, g.Z, ne + 1, g.ny, g.s2, 1.0, g.S, g.Bt, bx, by, bz, g.kchunk,
+                  g.splits > 1 ? g.part : nullptr);
+}
+
+__global__ void __launch_bounds__(256) kg_gemm_reduce(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    const int2 e = map[blockIdx.x];
+    const GroupProb &g = P[e.x];
+    if (*g.status) return;
+    gemm_nt_reduce_body(g.part, g.splits, g.ne, g.ne, g.ne + 1, true, g.s2, 1.0, g.S, g.Bt, e.y,
+                        ceil_div((size_t)g.ne * (2 * g.ne + 1), 256));
+}
+
+// cluster c = blocks 8 c .. 8 c + 7, all of one problem (map entry per cluster)
+__global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(288)
+    kg_cholesky_cluster(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    const GroupProb &g = P[map[blockIdx.x / kCholCluster].x];
+    cholesky_cluster_body(g.S, g.Lt, g.ne, g.status);
+}
+
+__global__ void __launch_bounds__(256) kg_cholesky(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    const GroupProb &g = P[map[blockIdx.x].x];
+    cholesky_body<true>(g.S, g.Lt, g.ne, g.status);
+}
+
+template <int MAXR>
+__global__ void __launch_bounds__(32 * kSolveColsPerCta)
+    kg_chol_solve(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    const int2 e = map[blockIdx.x];
+    const GroupProb &g = P[e.x];
+    chol_solve_body<MAXR>(g.S, g.ne, g.Bt, g.Bt, g.ne + 1, g.Tt, g.ldx, g.status, e.y * kSolveColsPerCta,
+                          kSolveColsPerCta);
+}
+
+// prolongation rows ry, ry + R, ... (R = ceil(4 nf / 8)) of fine column block
+// bx; block 0 of each problem advances its analysis counter
+__global__ void __launch_bounds__(128) kg_prolong(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    const int2 e = map[blockIdx.x];
+    const GroupProb &g = P[e.x];
+    if (e.y == 0 && threadIdx.x == 0) *g.cycle += 1;
+    if (*g.status) return;
+    const int nf = g.nc * g.r, gx = ceil_div(nf, 128), R = ceil_div(4 * nf, 8);
+    prolong2d_rows<float>(g.fine, g.dC, 4, g.nc, g.r, g.pw, e.y % gx, e.y / gx, R);
+}
+
+bool group_supported(int ne, int ny) {
+    // the solve's registers hold 32 MAXR rows (MAXR <= 8) and its staged
+    // factor fits shared memory; the anomalies' BF16 rows fit the update
+    return ne >= 2 && ne <= 160 && ny >= 1 && chol_solve_smem(ne) <= 210 * 1024;
+}
+
+void group_plan_free(GroupPlan *plan) {
+    if (plan->d_probs) cudaFree(plan->d_probs);
+    if (plan->d_maps) cudaFree(plan->d_maps);
+    *plan = GroupPlan();
+}
+
+bool group_plan_build(GroupPlan *plan, const std::vector<GroupProb> &probs, const std::vector<CUtensorMap> &maps,
+                      cudaStream_t s) {
+    group_plan_free(plan);
+    const int np = (int)probs.size();
+    if (np < 1 || maps.size() != 2 * probs.size()) return false;
+    std::vector<int2> m[kGsSteps];
+    int maxne = 0;
+    for (int j = 0; j < np; ++j) {
+        const GroupProb &g = probs[j];
+        if (!group_supported(g.ne, g.ny) || g.ldx % 16 || g.ldx < g.ne) return false;
+        maxne = std::max(maxne, g.ne);
+        auto add = [&](int step, long long nb) {
+            for (long long b = 0; b < nb; ++b) m[step].push_back(make_int2(j, (int)b));
+        };
+        const int nf = g.nc * g.r;
+        add(kGsRestrict, ceil_div(g.nx, 256));
+        add(kGsObsApply, (long long)ceil_div(g.ny, 128) * (g.ne + 1));
+        add(kGsObsMean, ceil_div(g.ny, 32));
+        add(kGsPerturb, ceil_div(((long long)g.ne * g.ny + 3) / 4, 128));
+        add(kGsInnov, 1);
+        {
+            const int tx = ceil_div(2 * g.ne + 1, 16), ty = ceil_div(g.ne, 16);
+            for (int z = 0; z < g.splits; ++z)
+                for (int by = 0; by < ty; ++by)
+                    for (int bx = by; bx < tx; ++bx) m[kGsGemm].push_back(make_int2(j, (z * ty + by) * tx + bx));
+        }
+        if (g.splits > 1) add(kGsReduce, ceil_div((long long)g.ne * (2 * g.ne + 1), 256));
+        if (g.ne >= 32 && g.ne <= 256)
+            add(kGsCholCluster, 1);
+        else
+            add(kGsChol, 1);
+        add(kGsSolve, ceil_div(g.ne + 1, kSolveColsPerCta));
+        add(kGsProlong, (long long)ceil_div(nf, 128) * ceil_div(4 * nf, 8));
+    }
+    // launch shapes (the largest problem's shared memory)
+    plan->solve_maxr = maxne <= 128 ? 4 : 8;
+    plan->solve_smem = chol_solve_smem(maxne);
+    plan->chol_cluster_smem = 0;
+    plan->chol_smem = 0;
+    for (const GroupProb &g : probs) {
+        if (g.ne >= 32 && g.ne <= 256)
+            plan->chol_cluster_smem = std::max(plan->chol_cluster_smem, cholesky_cluster_smem(g.ne));
+        else
+            plan->chol_smem = std::max(plan->chol_smem, sizeof(double) * (size_t)g.ne * (g.ne + 1));
+    }
+    if (plan->chol_smem > 210 * 1024) return false;
+    // update: problems grouped by the CTAs per SM their shared memory and TMEM
+    // columns allow, one launch per group of at most kUpdateGroupMax (each
+    // launch asks for its largest problem's shared memory)
+    {
+        auto per_sm = [](size_t smem) { return (int)((size_t)227 * 1024 / smem); };
+        std::vector<int> order(np);
+        for (int j = 0; j < np; ++j) order[j] = j;
+        auto need = [&](int j) {
+            const GroupProb &g = probs[j];
+            return update_tc_launch_smem(update_tc_smem(g.kblocks, g.ntile, g.ne), g.tmem_cols);
+        };
+        for (int j = 0; j < np; ++j)
+            if (need(j) > 200 * 1024) return false;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return per_sm(need(a)) > per_sm(need(b)); });
+        for (size_t k = 0; k < order.size();) {
+            GroupPlan::UpdateLaunch L;
+            const int cls = per_sm(need(order[k]));
+            L.map_begin = (int)m[kGsUpdate].size();
+            while (k < order.size() && per_sm(need(order[k])) == cls && (int)L.probs.size() < kUpdateGroupMax) {
+                const int j = order[k++];
+                const int q = (int)L.probs.size();
+                L.probs.push_back(j);
+                L.smem = std::max(L.smem, need(j));
+                for (int t = 0; t < ceil_div(probs[j].nx, 128); ++t) m[kGsUpdate].push_back(make_int2(q, t));
+            }
+            L.map_end = (int)m[kGsUpdate].size();
+            plan->upd.push_back(L);
+        }
+    }
+    plan->upd_maps = maps;
+    // one allocation for the table and every map
+    size_t total = 0;
+    for (int k = 0; k < kGsSteps; ++k) {
+        plan->map_off[k] = (int)total;
+        plan->nblocks[k] = (int)m[k].size();
+        total += m[k].size();
+    }
+    std::vector<int2> all;
+    all.reserve(total);
+    for (int k = 0; k < kGsSteps; ++k) all.insert(all.end(), m[k].begin(), m[k].end());
+    if (cudaMalloc(&plan->d_probs, np * sizeof(GroupProb)) != cudaSuccess ||
+        cudaMalloc(&plan->d_maps, std::max<size_t>(total, 1) * sizeof(int2)) != cudaSuccess) {
+        cudaGetLastError();
+        group_plan_free(plan);
+        return false;
+    }
+    plan->nprob = np;
+    if (cudaMemcpyAsync(plan->d_probs, probs.data(), np * sizeof(GroupProb), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(plan->d_maps, all.data(), total * sizeof(int2), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        group_plan_free(plan);
+        return false;
+    }
+    return true;
+}
+
+cudaError_t group_analyse(const GroupPlan &plan, cudaStream_t s) {
+    static OncePerDevice attr;
+    cudaError_t ae = attr.run([](int) {
+        cudaError_t e = cudaFuncSetAttribute(kg_cholesky_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kg_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kg_chol_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kg_chol_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+        return e;
+    });
+    if (ae != cudaSuccess) return ae;
+    const GroupProb *P = plan.d_probs;
+    auto M = [&](int k) { return plan.d_maps + plan.map_off[k]; };
+    auto n = [&](int k) { return plan.nblocks[k]; };
+    int launches = 0;
+    auto step = [&](int k) {
+        if (n(k)) ++launches;
+        return n(k) > 0;
+    };
+    if (step(kGsRestrict)) kg_restrict<<<n(kGsRestrict), 256, 0, s>>>(P, M(kGsRestrict));
+    if (step(kGsObsApply)) kg_obs_apply<<<n(kGsObsApply), 128, 0, s>>>(P, M(kGsObsApply));
+    if (step(kGsObsMean)) kg_obs_mean<<<n(kGsObsMean), 256, 0, s>>>(P, M(kGsObsMean));
+    if (step(kGsPerturb)) kg_obs_perturb<<<n(kGsPerturb), 128, 0, s>>>(P, M(kGsPerturb));
+    if (step(kGsInnov)) kg_innov_rms<<<n(kGsInnov), 256, 0, s>>>(P, M(kGsInnov));
+    if (step(kGsGemm)) kg_gemm<<<n(kGsGemm), 256, 0, s>>>(P, M(kGsGemm));
+    if (step(kGsReduce)) kg_gemm_reduce<<<n(kGsReduce), 256, 0, s>>>(P, M(kGsReduce));
+    if (step(kGsCholCluster))
+        kg_cholesky_cluster<<<n(kGsCholCluster) * kCholCluster, 288, plan.chol_cluster_smem, s>>>(P, M(kGsCholCluster));
+    if (step(kGsChol)) kg_cholesky<<<n(kGsChol), 256, plan.chol_smem, s>>>(P, M(kGsChol));
+    if (step(kGsSolve)) {
+        if (plan.solve_maxr == 4)
+            kg_chol_solve<4><<<n(kGsSolve), 32 * kSolveColsPerCta, plan.solve_smem, s>>>(P, M(kGsSolve));
+        else
+            kg_chol_solve<8><<<n(kGsSolve), 32 * kSolveColsPerCta, plan.solve_smem, s>>>(P, M(kGsSolve));
+    }
+    count_launches(launches);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_update_tc_group(plan, s);
+    if (e != cudaSuccess) return e;
+    if (n(kGsProlong)) {
+        count_launches(1);
+        kg_prolong<<<n(kGsProlong), 128, 0, s>>>(P, M(kGsProlong));
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

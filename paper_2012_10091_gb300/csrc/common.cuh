@@ -49,7 +49,7 @@ class OncePerDevice {
 // ---------------------------------------------------------------------------
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (grids are sized from the device query)
 
-inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+__host__ __device__ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // device status word values (a subset of mgenkf_status)
 constexpr int kStatusOk = 0;

@@ -15,6 +15,7 @@
 #include "../../include/mgenkf.h"
 #include "../../include/mgenkf_ops.h"
 #include "analysis.h"
+#include "batch_analysis.h"
 #include "common.cuh"
 #include "forecast.h"
 #include "forecast_ns2d.h"
@@ -354,7 +355,7 @@ static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const 
     if (h->mixed) {
         const char *sel = getenv("MGENKF_UPDATE");
         if (!(sel && strcmp(sel, "simt") == 0))
-            update_tc_prepare(&h->tc, h->X16, h->ldx, (int)h->nx, h->Tt, h->ntpad, h->ne, (const float *)h->members);
+            update_tc_prepare(&h->tc, h->ldx, (int)h->nx, h->Tt, h->ntpad, h->ne, (const float *)h->members);
     }
     H_CUDA(cudaStreamSynchronize(h->stream));
     return MGENKF_OK;
@@ -515,7 +516,8 @@ static void analyse_kernels(mgenkf_ctx *h, int gen_eps) {
     launch_obs_mean(h->yf, h->yo, ne, ny, h->ybar, h->Z, h->status, s);
     launch_obs_perturb(h->yf, h->ybar, h->yo, h->eps, gen_eps, h->cfg.seed, h->cycle_d,
                        h->cfg.obs_sigma, ne, ny, h->Y, h->Z, s);
-    launch_ens_anom<T>(members, nx, ne, h->X64, h->X16, h->status, s);
+    // the tensor-core update forms the BF16 anomalies itself from the members it reads
+    if (!(h->mixed && h->tc.ready)) launch_ens_anom<T>(members, nx, ne, h->X64, h->X16, h->status, s);
     const double s2 = h->cfg.obs_sigma * h->cfg.obs_sigma;
     if (!h->direct) {
         // S = I + Y^T R^-1 Y (ne x ne) and B = Y^T R^-1 [D | d*]; T = S^-1 B
@@ -977,6 +979,11 @@ struct mgenkf_batch {
     cudaGraphExec_t exec = nullptr;
     int graph_nsteps = -1;
     double gamma = 1.4, mu = 1e-3, prandtl = 0.72;
+    // grouped analysis: one launch per analysis step over all problems (when
+    // every problem fits it; otherwise one chain per problem on the branches)
+    bool grouped = false;
+    GroupPlan gplan;
+    std::vector<long long> gplan_wait;  // each handle's update wait limit the plan was built with
     std::string err;
 };
 
@@ -1080,6 +1087,7 @@ static mgenkf_status upload_tables(mgenkf_batch *b, const std::vector<std::vecto
 }
 
 static void batch_free(mgenkf_batch *b) {
+    group_plan_free(&b->gplan);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (NsGroup<float> *d : b->d_groups)
@@ -1250,6 +1258,101 @@ static mgenkf_status batch_analyse(mgenkf_batch *b) {
     return MGENKF_OK;
 }
 
+// whether handle h runs in the grouped analysis: the ensemble-space gain on the
+// tensor-core update, without the re-centring, the learned correction or the
+// final fine iteration, at sizes the grouped kernels take
+static bool groupable(const mgenkf_ctx *h) {
+    return !h->direct && !h->recentre && h->tc.ready && !h->cnn && !h->record_prev && h->alpha == 0.0 &&
+           h->filter_sigma == 0.0 && group_supported(h->ne, h->ny);
+}
+
+// (Re)build the grouped plan when none exists or a handle's update wait limit
+// changed; b->grouped says whether the analyses run grouped.
+static mgenkf_status batch_group_prepare(mgenkf_batch *b) {
+    const char *env = getenv("MGENKF_BATCH_GROUPED");
+    bool want = !(env && strcmp(env, "0") == 0);
+    for (const mgenkf_ctx *h : b->hs) want = want && groupable(h);
+    if (!want) {
+        b->grouped = false;
+        return MGENKF_OK;
+    }
+    bool fresh = b->gplan.nprob == (int)b->hs.size() && b->gplan_wait.size() == b->hs.size();
+    for (size_t j = 0; fresh && j < b->hs.size(); ++j) fresh = b->gplan_wait[j] == b->hs[j]->tc.wait_limit;
+    if (fresh) {
+        b->grouped = true;
+        return MGENKF_OK;
+    }
+    // nothing may still read the old plan
+    B_CUDA(cudaStreamSynchronize(b->s0));
+    for (cudaStream_t s : b->aux) B_CUDA(cudaStreamSynchronize(s));
+    std::vector<GroupProb> probs(b->hs.size());
+    std::vector<CUtensorMap> maps;
+    b->gplan_wait.clear();
+    for (size_t j = 0; j < b->hs.size(); ++j) {
+        const mgenkf_ctx *h = b->hs[j];
+        GroupProb &g = probs[j];
+        memset(&g, 0, sizeof(g));
+        g.fine = (float *)h->fine;
+        g.members = (float *)h->members;
+        g.xstar = (float *)h->xstar;
+        g.dC = (float *)h->dC;
+        g.tap_idx = h->tap_idx;
+        g.tap_w = h->tap_w;
+        g.yo_in = b->obs_stage + b->obs_off[j];
+        g.yo = h->yo;
+        g.yf = h->yf;
+        g.ybar = h->ybar;
+        g.eps = h->eps;
+        g.Y = h->Y;
+        g.Z = h->Z;
+        g.S = h->S;
+        g.Lt = h->Lt;
+        g.Bt = h->Bt;
+        g.part = h->gemm_part;
+        g.innov = b->innov + j;
+        g.Tt = h->Tt;
+        g.status = h->status;
+        g.cycle = h->cycle_d;
+        g.seed = h->cfg.seed;
+        g.sigma = h->cfg.obs_sigma;
+        g.s2 = h->cfg.obs_sigma * h->cfg.obs_sigma;
+        // the same host-side constants as the single-problem launches
+        g.inv_ne = 1.0 / h->ne;
+        g.isq = 1.0 / std::sqrt((double)(h->ne - 1));
+        g.nc = h->nc;
+        g.r = h->r;
+        g.ne = h->ne;
+        g.ny = h->ny;
+        g.taps = h->taps;
+        g.ldx = h->ldx;
+        g.nx = (int)h->nx;
+        g.splits = gemm_nt_splits(h->ne, h->ne, h->ne + 1, h->ny);
+        g.kchunk = ceil_div(ceil_div(h->ny, g.splits), 32) * 32;
+        g.kblocks = h->tc.kblocks;
+        g.ntile = h->tc.ntile;
+        g.tmem_cols = h->tc.tmem_cols;
+        g.wait_limit = h->tc.wait_limit;
+        g.pw = h->pw;
+        maps.push_back(h->tc.map_t);
+        maps.push_back(h->tc.map_m);
+        b->gplan_wait.push_back(h->tc.wait_limit);
+    }
+    b->grouped = group_plan_build(&b->gplan, probs, maps, b->s0);
+    if (!b->grouped) {
+        cudaGetLastError();
+        b->gplan_wait.clear();
+    }
+    return MGENKF_OK;
+}
+
+// the analyses and prolongations of every handle, grouped: after all forecasts
+static mgenkf_status batch_analyse_grouped(mgenkf_batch *b) {
+    for (int k = 0; k < (int)b->sizes.size(); ++k) B_CUDA(cudaStreamWaitEvent(b->s0, b->ev[1 + k], 0));
+    cudaError_t e = group_analyse(b->gplan, b->s0);
+    if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("grouped analysis: ") + cudaGetErrorString(e));
+    return MGENKF_OK;
+}
+
 extern "C" mgenkf_status mgenkf_batch_forecast(mgenkf_batch_t b, int32_t nsteps) {
     if (!b || nsteps < 0) return MGENKF_ERR_INVALID_ARG;
     b->err.clear();
@@ -1266,9 +1369,13 @@ extern "C" mgenkf_status mgenkf_batch_cycle(mgenkf_batch_t b, int32_t nsteps, co
         if (b->graph) cudaGraphDestroy(b->graph);
         b->exec = nullptr;
         b->graph = nullptr;
+        {
+            mgenkf_status st = batch_group_prepare(b);
+            if (st) return st;
+        }
         B_CUDA(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed));
         mgenkf_status st = batch_forecast(b, nsteps, false);
-        if (st == MGENKF_OK) st = batch_analyse(b);
+        if (st == MGENKF_OK) st = b->grouped ? batch_analyse_grouped(b) : batch_analyse(b);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(b->s0, &g);
         if (st) {

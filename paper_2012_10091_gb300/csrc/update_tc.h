@@ -11,7 +11,6 @@ namespace mgk {
 
 // TMA descriptors and launch shape of the update for one handle's buffers.
 struct UpdateTcPlan {
-    CUtensorMap map_x;  // X^T, [nx][ldx] bf16, K-major, box 64 x 128
     CUtensorMap map_t;  // T^T, [ntpad][ldx] bf16, K-major, box 64 x ntpad
     CUtensorMap map_m;  // members, [ne][nx] fp32, box 128 points x ne members
     const float *members;
@@ -22,10 +21,19 @@ struct UpdateTcPlan {
 };
 
 bool update_tc_supported(int ne, int ldx, int ntpad, int nx);
-bool update_tc_prepare(UpdateTcPlan *plan, const __nv_bfloat16 *X16, int ldx, int nx, const __nv_bfloat16 *Tt,
-                       int ntpad, int ne, const float *members);
-// members[c][p] += sum_a X[p][a] T[c][a] (c < ne), dC[p] = sum_a X[p][a] T[ne][a];
-// `members` must be the buffer the plan was prepared for
+bool update_tc_prepare(UpdateTcPlan *plan, int ldx, int nx, const __nv_bfloat16 *Tt, int ntpad, int ne,
+                       const float *members);
+// members[c][p] += sum_a X[p][a] T[c][a] (c < ne), dC[p] = sum_a X[p][a] T[ne][a],
+// with X the BF16 normalised anomalies of the members as they are on entry
+// (formed in the kernel); `members` must be the buffer the plan was prepared for
 cudaError_t launch_update_tc(const UpdateTcPlan &plan, float *members, float *dC, int *status, cudaStream_t s);
+// dynamic shared memory of one update tile (operands and the member tile), and
+// what a launch asks for so that its CTAs never oversubscribe TMEM
+size_t update_tc_smem(int kblocks, int ntpad, int ne);
+size_t update_tc_launch_smem(size_t smem, int tmem_cols);
+
+// the update step of a grouped analysis (every problem of the plan)
+struct GroupPlan;
+cudaError_t launch_update_tc_group(const GroupPlan &plan, cudaStream_t s);
 
 }  // namespace mgk

@@ -38,18 +38,19 @@ def _inputs(ws, cycles):
     return inps, yos
 
 
-def _runs(M, ws, inps):
+def _runs(M, ws, inps, gain_forms=None):
     runs = []
-    for w, inp in zip(ws, inps):
-        g = M.MGEnKF.from_workload(w, precision="mixed")
+    for j, (w, inp) in enumerate(zip(ws, inps)):
+        gf = gain_forms[j] if gain_forms else M.MGENKF_GAIN_ENSEMBLE
+        g = M.MGEnKF.from_workload(w, precision="mixed", gain_form=gf)
         g.set_state(inp["fine0"], inp["members0"])
         runs.append(g)
     return runs
 
 
-def _per_handle(M, ws, inps, yos, nsteps):
+def _per_handle(M, ws, inps, yos, nsteps, gain_forms=None):
     out = []
-    for j, g in enumerate(_runs(M, ws, inps)):
+    for j, g in enumerate(_runs(M, ws, inps, gain_forms)):
         for k, n in enumerate(nsteps):
             g.cycle(n, yos[j][k])
         assert g.sync() == 0
@@ -68,7 +69,12 @@ def _batched(M, b, ws, yos, nsteps, innov=None):
     return [g.get_state() for g in b.runs]
 
 
-def test_batch_equals_per_problem_handles(M):
+@pytest.mark.parametrize("grouped", ["1", "0"])
+def test_batch_equals_per_problem_handles(M, monkeypatch, grouped):
+    """Grouped analysis (one launch per analysis step over all problems) and
+    the per-problem chains on the graph's branches (MGENKF_BATCH_GROUPED=0)
+    both give each problem's own handle results, bit for bit."""
+    monkeypatch.setenv("MGENKF_BATCH_GROUPED", grouped)
     ws = _problems()
     assert len({w.nc for w in ws}) > 1 and len({w.ne for w in ws}) > 1
     nsteps = [10, 10, 7, 10]        # a changed step count recaptures the graph
@@ -217,4 +223,59 @@ def test_batch_at_multi_tile_sizes_matches_oracle(M):
             mg.prolong_correct()
         assert rel_err(got[j][0], mg.fine) < 1e-3
         assert rel_err(got[j][1], mg.members) < 1e-3
+    b.close()
+
+
+def test_grouped_cycle_launches(M, monkeypatch):
+    """A grouped batch cycle launches the forecast steps of each grid size and
+    a fixed number of analysis launches, whatever the problem count; the
+    per-problem chains launch about 13 kernels per problem."""
+    ws = _problems()
+    inps, yos = _inputs(ws, 1)
+    counts = {}
+    for grouped in ("1", "0"):
+        monkeypatch.setenv("MGENKF_BATCH_GROUPED", grouped)
+        b = M.Batch(_runs(M, ws, inps))
+        n0 = M.mgk_kernel_launches()
+        b.cycle(4, np.concatenate([yos[j][0] for j in range(len(ws))]))
+        assert b.sync() == 0
+        counts[grouped] = M.mgk_kernel_launches() - n0
+        b.close()
+    nsizes = len({w.nc for w in ws} | {w.nf for w in ws})
+    # forecast: 4 step launches per grid size (plus a copy-back per size at most)
+    assert counts["1"] <= 5 * nsizes + 14
+    assert counts["0"] >= counts["1"] + 10 * (len(ws) - 1)
+
+
+def test_batch_with_a_direct_form_problem(M):
+    """A problem the grouped kernels do not take (direct gain form) sends the
+    batch to the per-problem chains; the results are still each handle's own."""
+    ws = _problems()
+    forms = [M.MGENKF_GAIN_ENSEMBLE] * len(ws)
+    forms[1] = M.MGENKF_GAIN_DIRECT
+    nsteps = [10, 10]
+    inps, yos = _inputs(ws, len(nsteps))
+    ref = _per_handle(M, ws, inps, yos, nsteps, forms)
+    b = M.Batch(_runs(M, ws, inps, forms))
+    got = _batched(M, b, ws, yos, nsteps)
+    for (f0, m0), (f1, m1) in zip(ref, got):
+        np.testing.assert_array_equal(f1, f0)
+        np.testing.assert_array_equal(m1, m0)
+    b.close()
+
+
+def test_grouped_analysis_at_every_member_count_equals_handles(M):
+    """Member counts 16..128 in one batch: one-CTA and clustered Cholesky,
+    split and unsplit gain products, 1..17 solve CTAs per problem, 32..256
+    TMEM columns in one grouped update; bit for bit each handle's results."""
+    ws = W.ns2d_batch(nprob=6, seed=4, coarse=(16, 24), members=(16, 32, 64, 128), n_obs=(64, 512))
+    assert {w.ne for w in ws} >= {16, 128}
+    nsteps = [6, 6]
+    inps, yos = _inputs(ws, len(nsteps))
+    ref = _per_handle(M, ws, inps, yos, nsteps)
+    b = M.Batch(_runs(M, ws, inps))
+    got = _batched(M, b, ws, yos, nsteps)
+    for (f0, m0), (f1, m1) in zip(ref, got):
+        np.testing.assert_array_equal(f1, f0)
+        np.testing.assert_array_equal(m1, m0)
     b.close()

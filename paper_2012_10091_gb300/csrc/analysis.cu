@@ -72,32 +72,51 @@ void launch_restrict(const T *fine, T *xstar, int dim, int V, int nc, int r, cud
 // ---------------------------------------------------------------------------
 // predicted observations H^C x (Algorithm 3 step 2): sparse 4- or 16-tap rows
 // ---------------------------------------------------------------------------
+// Thread: observation j = bx * blockDim.x + threadIdx.x, rows i = i0 .. i0 +
+// kObsRows - 1 of yf (members, then x^C* as row ne); its taps (<= 16) stay in
+// registers for those rows.
+constexpr int kObsRows = 8;
+
 template <typename T>
 __device__ __forceinline__ void obs_apply_body(const T *__restrict__ members, const T *__restrict__ xstar,
                                                size_t nx, int ne, int ny, int taps,
                                                const int32_t *__restrict__ tap_idx,
                                                const double *__restrict__ tap_w, double *__restrict__ yf, int bx,
-                                               int i) {
+                                               int i0) {
     const int j = bx * blockDim.x + threadIdx.x;
     if (j >= ny) return;
-    const T *x = i < ne ? members + (size_t)i * nx : xstar;
-    double acc = 0.0;
-    for (int t = 0; t < taps; ++t) acc = fma(tap_w[(size_t)j * taps + t], (double)x[tap_idx[(size_t)j * taps + t]], acc);
-    yf[(size_t)i * ny + j] = acc;
+    int32_t idx[16];
+    double w[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+        if (t < taps) {
+            idx[t] = tap_idx[(size_t)j * taps + t];
+            w[t] = tap_w[(size_t)j * taps + t];
+        }
+    const int i1 = min(i0 + kObsRows, ne + 1);
+    for (int i = i0; i < i1; ++i) {
+        const T *x = i < ne ? members + (size_t)i * nx : xstar;
+        double acc = 0.0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+            if (t < taps) acc = fma(w[t], (double)x[idx[t]], acc);
+        yf[(size_t)i * ny + j] = acc;
+    }
 }
 
 template <typename T>
-__global__ void k_obs_apply(const T *__restrict__ members, const T *__restrict__ xstar, size_t nx, int ne, int ny,
-                            int taps, const int32_t *__restrict__ tap_idx, const double *__restrict__ tap_w,
-                            double *__restrict__ yf) {
-    obs_apply_body<T>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf, blockIdx.x, blockIdx.y);
+__global__ void __launch_bounds__(128) k_obs_apply(const T *__restrict__ members, const T *__restrict__ xstar,
+                                                   size_t nx, int ne, int ny, int taps,
+                                                   const int32_t *__restrict__ tap_idx,
+                                                   const double *__restrict__ tap_w, double *__restrict__ yf) {
+    obs_apply_body<T>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf, blockIdx.x, blockIdx.y * kObsRows);
 }
 
 template <typename T>
 void launch_obs_apply(const T *members, const T *xstar, size_t nx, int ne, int ny, int taps,
                       const int32_t *tap_idx, const double *tap_w, double *yf, cudaStream_t s) {
     count_launches(1);
-    dim3 grid(ceil_div(ny, 128), ne + 1);
+    dim3 grid(ceil_div(ny, 128), ceil_div(ne + 1, kObsRows));
     k_obs_apply<T><<<grid, 128, 0, s>>>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf);
 }
 
@@ -1058,38 +1077,56 @@ __device__ __forceinline__ int wrap_tap(int c, int nc) {
 // 2-D launch: x over the points of a fine row, y over the rows of all
 // variables, so the only divisions are by r and the periodic wraps are
 // compares.
-// 2-D: fine points bx * blockDim.x + threadIdx.x of the rows row0, row0 +
-// rstep, ... (row = v nf + fine y)
+// 2-D: fine column fx of the r fine rows of coarse interval Jy of variable v
+// (vj = v nc + Jy).  The four sums along x (coarse rows Jy - 1 .. Jy + 2) are
+// the same for the r rows and are formed once; each row is then its 4-tap sum
+// along y.  The fine values of up to 4 rows are loaded before any of them is written.
+// wt: the weights converted to T ([m][t], in shared memory).
 template <typename T>
-__device__ __forceinline__ void prolong2d_rows(T *__restrict__ fine, const T *__restrict__ dC, int V, int nc, int r,
-                                               const ProlongWeights &w, int bx, int row0, int rstep) {
+__device__ __forceinline__ void prolong2d_interval(T *__restrict__ fine, const T *__restrict__ dC, int nc, int r,
+                                                   const T (*wt)[4], int fx, int vj) {
     const int nf = nc * r;
-    const int fx = bx * blockDim.x + threadIdx.x;
-    if (fx >= nf) return;
+    const int v = vj / nc, Jy = vj - v * nc;
     const int Jx = fx / r, mx = fx - Jx * r;
     int cx[4];
     T wx[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         cx[t] = wrap_tap(Jx - 1 + t, nc);
-        wx[t] = (T)w.w[mx][t];
+        wx[t] = wt[mx][t];
     }
-    const size_t cpl = (size_t)nc * nc, fpl = (size_t)nf * nf;
-    for (int row = row0; row < V * nf; row += rstep) {
-        const int v = row / nf, fy = row - v * nf;
-        const int Jy = fy / r, my = fy - Jy * r;
-        const T *d = dC + (size_t)v * cpl;
-        T acc = T(0);
+    const T *d = dC + (size_t)v * nc * nc;
+    T sx[4];
 #pragma unroll
-        for (int ty = 0; ty < 4; ++ty) {
-            const T *dr = d + (size_t)wrap_tap(Jy - 1 + ty, nc) * nc;
-            T sx = T(0);
+    for (int ty = 0; ty < 4; ++ty) {
+        const T *dr = d + (size_t)wrap_tap(Jy - 1 + ty, nc) * nc;
+        T a = T(0);
 #pragma unroll
-            for (int tx = 0; tx < 4; ++tx) sx = fma_t(wx[tx], dr[cx[tx]], sx);
-            acc = fma_t((T)w.w[my][ty], sx, acc);
-        }
-        fine[(size_t)v * fpl + (size_t)fy * nf + fx] += acc;
+        for (int tx = 0; tx < 4; ++tx) a = fma_t(wx[tx], dr[cx[tx]], a);
+        sx[ty] = a;
     }
+    T *f = fine + (size_t)v * nf * nf + (size_t)Jy * r * nf + fx;
+    for (int m0 = 0; m0 < r; m0 += 4) {
+        T old[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (m0 + k < r) old[k] = f[(size_t)(m0 + k) * nf];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (m0 + k < r) {
+                T acc = T(0);
+#pragma unroll
+                for (int ty = 0; ty < 4; ++ty) acc = fma_t(wt[m0 + k][ty], sx[ty], acc);
+                f[(size_t)(m0 + k) * nf] = old[k] + acc;
+            }
+    }
+}
+
+// the Lagrange weights of offsets 0 .. r - 1 converted to T, into shared memory
+template <typename T>
+__device__ __forceinline__ void prolong_stage_weights(const ProlongWeights &w, int r, T (*wt)[4]) {
+    for (int e = threadIdx.x; e < 4 * r; e += blockDim.x) wt[e >> 2][e & 3] = (T)w.w[e >> 2][e & 3];
+    __syncthreads();
 }
 
 template <typename T>
@@ -1111,7 +1148,11 @@ __global__ void k_prolong_add(T *__restrict__ fine, const T *__restrict__ dC, in
         }
         return;
     }
-    prolong2d_rows<T>(fine, dC, V, nc, r, w, blockIdx.x, blockIdx.y, gridDim.y);
+    __shared__ T wt[kMaxRatio][4];
+    prolong_stage_weights<T>(w, r, wt);
+    const int fx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (fx >= nf) return;
+    for (int vj = blockIdx.y; vj < V * nc; vj += gridDim.y) prolong2d_interval<T>(fine, dC, nc, r, wt, fx, vj);
 }
 
 template <typename T>
@@ -1122,7 +1163,7 @@ void launch_prolong_add(T *fine, const T *dC, int dim, int V, int nc, int r,
     if (dim == 1) {
         k_prolong_add<T><<<grid_for((size_t)V * nf, 256), 256, 0, s>>>(fine, dC, dim, V, nc, r, w, status);
     } else {
-        const dim3 grid(ceil_div(nf, 128), std::min(V * nf, 65535));
+        const dim3 grid(ceil_div(nf, 128), std::min(V * nc, 65535));
         k_prolong_add<T><<<grid, 128, 0, s>>>(fine, dC, dim, V, nc, r, w, status);
     }
 }
@@ -1266,7 +1307,8 @@ __global__ void __launch_bounds__(128) kg_obs_apply(const GroupProb *__restrict_
     const int2 e = map[blockIdx.x];
     const GroupProb &g = P[e.x];
     const int gx = ceil_div(g.ny, 128);
-    obs_apply_body<float>(g.members, g.xstar, g.nx, g.ne, g.ny, g.taps, g.tap_idx, g.tap_w, g.yf, e.y % gx, e.y / gx);
+    obs_apply_body<float>(g.members, g.xstar, g.nx, g.ne, g.ny, g.taps, g.tap_idx, g.tap_w, g.yf, e.y % gx,
+                          (e.y / gx) * kObsRows);
 }
 
 __global__ void __launch_bounds__(256) kg_obs_mean(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
@@ -1327,15 +1369,34 @@ __global__ void __launch_bounds__(32 * kSolveColsPerCta)
                           kSolveColsPerCta);
 }
 
-// prolongation rows ry, ry + R, ... (R = ceil(4 nf / 8)) of fine column block
-// bx; block 0 of each problem advances its analysis counter
-__global__ void __launch_bounds__(128) kg_prolong(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+// prolongation of the coarse intervals vj = kProlongIntervals e.y .. + 7 of
+// one problem, all fine columns; the problem's scalars and weights are read
+// once per block (the table entry is shared by all of the problem's blocks);
+// block 0 of each problem advances its analysis counter
+constexpr int kProlongIntervals = 8;
+
+__global__ void __launch_bounds__(256) kg_prolong(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+    __shared__ float wt[kMaxRatio][4];
+    __shared__ float *s_fine;
+    __shared__ const float *s_dc;
+    __shared__ int s_nc, s_r, s_skip;
     const int2 e = map[blockIdx.x];
-    const GroupProb &g = P[e.x];
-    if (e.y == 0 && threadIdx.x == 0) *g.cycle += 1;
-    if (*g.status) return;
-    const int nf = g.nc * g.r, gx = ceil_div(nf, 128), R = ceil_div(4 * nf, 8);
-    prolong2d_rows<float>(g.fine, g.dC, 4, g.nc, g.r, g.pw, e.y % gx, e.y / gx, R);
+    if (threadIdx.x == 0) {
+        const GroupProb &g = P[e.x];
+        if (e.y == 0) *g.cycle += 1;
+        s_skip = *g.status;
+        s_fine = g.fine;
+        s_dc = g.dC;
+        s_nc = g.nc;
+        s_r = g.r;
+    }
+    __syncthreads();
+    if (s_skip) return;
+    const int nc = s_nc, r = s_r, nf = nc * r;
+    prolong_stage_weights<float>(P[e.x].pw, r, wt);
+    const int vj0 = e.y * kProlongIntervals, vj1 = min(vj0 + kProlongIntervals, 4 * nc);
+    for (int fx = threadIdx.x; fx < nf; fx += blockDim.x)
+        for (int vj = vj0; vj < vj1; ++vj) prolong2d_interval<float>(s_fine, s_dc, nc, r, wt, fx, vj);
 }
 
 bool group_supported(int ne, int ny) {
@@ -1366,7 +1427,7 @@ bool group_plan_build(GroupPlan *plan, const std::vector<GroupProb> &probs, cons
         };
         const int nf = g.nc * g.r;
         add(kGsRestrict, ceil_div(g.nx, 256));
-        add(kGsObsApply, (long long)ceil_div(g.ny, 128) * (g.ne + 1));
+        add(kGsObsApply, (long long)ceil_div(g.ny, 128) * ceil_div(g.ne + 1, kObsRows));
         add(kGsObsMean, ceil_div(g.ny, 32));
         add(kGsPerturb, ceil_div(((long long)g.ne * g.ny + 3) / 4, 128));
         add(kGsInnov, 1);
@@ -1382,7 +1443,7 @@ bool group_plan_build(GroupPlan *plan, const std::vector<GroupProb> &probs, cons
         else
             add(kGsChol, 1);
         add(kGsSolve, ceil_div(g.ne + 1, kSolveColsPerCta));
-        add(kGsProlong, (long long)ceil_div(nf, 128) * ceil_div(4 * nf, 8));
+        add(kGsProlong, ceil_div(4 * g.nc, kProlongIntervals));
     }
     // launch shapes (the largest problem's shared memory)
     plan->solve_maxr = maxne <= 128 ? 4 : 8;
@@ -1497,7 +1558,7 @@ cudaError_t group_analyse(const GroupPlan &plan, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (n(kGsProlong)) {
         count_launches(1);
-        kg_prolong<<<n(kGsProlong), 128, 0, s>>>(P, M(kGsProlong));
+        kg_prolong<<<n(kGsProlong), 256, 0, s>>>(P, M(kGsProlong));
     }
     return cudaGetLastError();
 }

@@ -216,10 +216,30 @@ struct UpdateGroupMaps {
 __global__ void __launch_bounds__(128) k_update_tc_group(const __grid_constant__ UpdateGroupMaps maps,
                                                          const GroupProb *__restrict__ probs,
                                                          const int2 *__restrict__ map) {
+    // the problem's scalars are read once per block (every block of the
+    // problem reads the same table entry)
+    __shared__ float *s_dc;
+    __shared__ int *s_status;
+    __shared__ int s_nx, s_ne, s_kb, s_nt, s_cols;
+    __shared__ long long s_wait;
+    __shared__ double s_inv, s_isq;
     const int2 e = map[blockIdx.x];
-    const GroupProb &g = probs[maps.prob[e.x]];
-    update_tc_tile(&maps.m[2 * e.x], &maps.m[2 * e.x + 1], g.dC, g.nx, g.ne, g.kblocks, g.ntile, g.tmem_cols,
-                   g.wait_limit, g.status, e.y * kTileM, g.inv_ne, g.isq);
+    if (threadIdx.x == 0) {
+        const GroupProb &g = probs[maps.prob[e.x]];
+        s_dc = g.dC;
+        s_status = g.status;
+        s_nx = g.nx;
+        s_ne = g.ne;
+        s_kb = g.kblocks;
+        s_nt = g.ntile;
+        s_cols = g.tmem_cols;
+        s_wait = g.wait_limit;
+        s_inv = g.inv_ne;
+        s_isq = g.isq;
+    }
+    __syncthreads();
+    update_tc_tile(&maps.m[2 * e.x], &maps.m[2 * e.x + 1], s_dc, s_nx, s_ne, s_kb, s_nt, s_cols, s_wait, s_status,
+                   e.y * kTileM, s_inv, s_isq);
 }
 
 // ---------------------------------------------------------------------------

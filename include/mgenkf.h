@@ -177,8 +177,8 @@ mgenkf_status mgenkf_sync(mgenkf_handle h);
 
 /* Limit, in SM clock cycles, of the tensor-core member update's wait for its
  * operands (mixed-precision handles whose update runs on the tensor cores;
- * default about one second at 2 GHz; 0 = give up at the first unsuccessful
- * poll).  The paper has no counterpart: every device wait of this library is
+ * default about one second at 2 GHz; 0 = one non-blocking test of each
+ * operand copy, which gives up unless the copy has already landed).  The paper has no counterpart: every device wait of this library is
  * bounded so that a stalled copy returns MGENKF_ERR_TIMEOUT instead of
  * hanging the GPU, and this sets that bound.  A wait that runs out records
  * MGENKF_ERR_TIMEOUT (reported by mgenkf_sync); the CTA issues no further

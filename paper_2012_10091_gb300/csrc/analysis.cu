@@ -1458,15 +1458,16 @@ bool group_plan_build(GroupPlan *plan, const std::vector<GroupProb> &probs, cons
     }
     if (plan->chol_smem > 210 * 1024) return false;
     // update: problems grouped by the CTAs per SM their shared memory and TMEM
-    // columns allow, one launch per group of at most kUpdateGroupMax (each
-    // launch asks for its largest problem's shared memory)
+    // columns allow, one launch per group of at most kUpdateLaunchMax
     {
         auto per_sm = [](size_t smem) { return (int)((size_t)227 * 1024 / smem); };
         std::vector<int> order(np);
         for (int j = 0; j < np; ++j) order[j] = j;
         auto need = [&](int j) {
             const GroupProb &g = probs[j];
-            return update_tc_launch_smem(update_tc_smem(g.kblocks, g.ntile, g.ne), g.tmem_cols);
+            const size_t two = update_tc_smem(g.kblocks, g.ntile, g.ne, 2);
+            return update_tc_launch_smem(two <= 200 * 1024 ? two : update_tc_smem(g.kblocks, g.ntile, g.ne, 1),
+                                         g.tmem_cols);
         };
         for (int j = 0; j < np; ++j)
             if (need(j) > 200 * 1024) return false;
@@ -1475,11 +1476,10 @@ bool group_plan_build(GroupPlan *plan, const std::vector<GroupProb> &probs, cons
             GroupPlan::UpdateLaunch L;
             const int cls = per_sm(need(order[k]));
             L.map_begin = (int)m[kGsUpdate].size();
-            while (k < order.size() && per_sm(need(order[k])) == cls && (int)L.probs.size() < kUpdateGroupMax) {
+            while (k < order.size() && per_sm(need(order[k])) == cls && (int)L.probs.size() < kUpdateLaunchMax) {
                 const int j = order[k++];
                 const int q = (int)L.probs.size();
                 L.probs.push_back(j);
-                L.smem = std::max(L.smem, need(j));
                 for (int t = 0; t < ceil_div(probs[j].nx, 128); ++t) m[kGsUpdate].push_back(make_int2(q, t));
             }
             L.map_end = (int)m[kGsUpdate].size();
@@ -1487,6 +1487,21 @@ bool group_plan_build(GroupPlan *plan, const std::vector<GroupProb> &probs, cons
         }
     }
     plan->upd_maps = maps;
+    plan->upd_probs.resize(np);
+    for (int j = 0; j < np; ++j) {
+        const GroupProb &g = probs[j];
+        UpdateProb &u = plan->upd_probs[j];
+        u.members = g.members;
+        u.dC = g.dC;
+        u.status = g.status;
+        u.nx = g.nx;
+        u.ne = g.ne;
+        u.kblocks = g.kblocks;
+        u.ntile = g.ntile;
+        u.wait_limit = g.wait_limit;
+        u.inv_ne = g.inv_ne;
+        u.isq = g.isq;
+    }
     // one allocation for the table and every map
     size_t total = 0;
     for (int k = 0; k < kGsSteps; ++k) {

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "analysis.h"
+#include "update_tc.h"
 
 namespace mgk {
 
@@ -58,7 +59,6 @@ enum GroupStep {
 };
 
 constexpr int kSolveColsPerCta = 8;  // right-hand sides per CTA of the grouped solve
-constexpr int kUpdateGroupMax = 112;  // problems per launch of the grouped update (tensor maps as parameters)
 
 // host side of a grouped analysis: the device table, the block maps of every
 // step and the launch shapes
@@ -70,15 +70,15 @@ struct GroupPlan {
     size_t chol_cluster_smem = 0, chol_smem = 0, solve_smem = 0;
     int solve_maxr = 4;
     // update: one launch per class of problems that fit the same number of
-    // CTAs per SM (at most kUpdateGroupMax problems each), over the blocks
+    // CTAs per SM (at most kUpdateLaunchMax problems each), over the tiles
     // [map_begin, map_end) of the update map (entry = (index in probs, tile))
     struct UpdateLaunch {
         std::vector<int> probs;
         int map_begin = 0, map_end = 0;
-        size_t smem = 0;
     };
     std::vector<UpdateLaunch> upd;
     std::vector<CUtensorMap> upd_maps;  // 2 per problem: T, members
+    std::vector<UpdateProb> upd_probs;  // per problem
 };
 
 // Fills `plan` for the problems `probs` (host copies; pointers are device

@@ -27,9 +27,22 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
+// whether phase `parity` has completed, without waiting
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // bounded wait on phase `parity`; returns false if the limit (SM clock
-// cycles) expired
+// cycles) expired.  try_wait may itself suspend for a while, so a limit <= 0
+// is one non-blocking test.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = kWaitLimitCycles) {
+    if (limit <= 0) return mbar_test(bar, parity);
     const long long t0 = clock64();
     while (true) {
         uint32_t done;

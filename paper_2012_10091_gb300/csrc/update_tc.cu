@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -47,44 +48,94 @@ using namespace tc;
 
 }  // namespace
 
-// One 128-point tile (first point m0) of one problem; the tensor maps are
-// kernel parameters (__grid_constant__) of the calling kernel.  inv_ne = 1/Ne,
-// isq = 1/sqrt(Ne - 1) (host values).
-__device__ __forceinline__ void update_tc_tile(const CUtensorMap *map_t, const CUtensorMap *map_m,
-                                               float *__restrict__ dC, int nx, int ne, int kblocks, int ntile,
-                                               int tmem_cols, long long wait_limit, int *status, int m0,
-                                               double inv_ne, double isq) {
+// The update of the tiles of up to kUpdateLaunchMax problems: the tensor maps
+// and scalars of the launch's problems travel as one parameter block (T and
+// members of problem q at m[2 q], m[2 q + 1]); tile k of the launch is tile
+// map[k].y of problem map[k].x (map NULL: tile k of problem 0).
+struct UpdateLaunchArgs {
+    CUtensorMap m[2 * kUpdateLaunchMax];
+    UpdateProb p[kUpdateLaunchMax];
+    int kbmax, ntmax, nemax, cols;  // shared-memory layout and TMEM columns of the launch
+    int nbuf;                       // member buffers (2: the next tile's load overlaps this tile)
+};
+
+// Persistent: CTA b works through the tiles [b n / G, (b + 1) n / G) in
+// order, one 128-point tile at a time, with two member buffers (one where two
+// do not fit shared memory), one anomaly (A) buffer, one T buffer and one TMEM
+// accumulator.  Tile k (buffer k & 1):
+//   a. thread 0 starts the next tile's member load into the other buffer
+//      (free: the previous tile's epilogue has read it; with one buffer the
+//      load starts after this tile's epilogue);
+//   b. wait for the tile's members (and T when the problem changed);
+//   c. the anomalies of the tile into A;
+//   d. thread 0 issues the MMAs and commits them; wait for the accumulator;
+//   e. thread 0 starts the next problem's T load if the problem changes;
+//   f. epilogue: members[c][p] = x[c][p] + D[p][c] from the buffer, stored to
+//      HBM directly; dC[p] = D[p][Ne].
+// Tiles of a problem whose status word is set are skipped.  Any wait that
+// runs out stops the CTA: MGENKF_ERR_TIMEOUT in that problem's status word,
+// the copies in flight awaited (default bound), TMEM freed.
+__global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ UpdateLaunchArgs a,
+                                                   const int2 *__restrict__ map, int nent) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned operand buffers
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    unsigned char *sa = base;                                        // kblocks x [128][64] bf16 (written here)
-    unsigned char *sb = base + (size_t)kblocks * kTileM * 128;       // kblocks x [ntile][64] bf16 (TMA)
-    float *sm = reinterpret_cast<float *>(sb + (size_t)kblocks * ntile * 128);  // [ne][128] members (TMA)
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + (size_t)ne * kTileM);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
-    __shared__ int s_fail, s_bad;
+    unsigned char *sa = base;                                            // kbmax x [128][64] bf16 (written here)
+    unsigned char *sb = base + (size_t)a.kbmax * kTileM * 128;           // kbmax x [ntile][64] bf16 (TMA)
+    float *smb = reinterpret_cast<float *>(sb + (size_t)a.kbmax * a.ntmax * 128);  // nbuf x [ne][128] members (TMA)
+    const size_t bstride = (size_t)a.nemax * kTileM;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smb + a.nbuf * bstride);  // members x2, MMA, T
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
+    __shared__ int s_abort, s_next, s_next2, s_tload;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int e0 = (int)((long long)blockIdx.x * nent / gridDim.x);
+    const int e1 = (int)((long long)(blockIdx.x + 1) * nent / gridDim.x);
+    auto entry = [&](int k) { return map ? map[k] : make_int2(0, k); };
+
+    // thread 0's view of the copies: the problem whose T is (being) loaded, the
+    // status of the last problem looked at; per member barrier (bit b) the
+    // parity of its last load and whether that load is outstanding
+    int tq = -1, sq = -1, sq_ok = 0, lpar = 0, pend = 0, ntl = 0, pend_t = 0;
+    auto next_valid = [&](int k) {
+        for (; k < e1; ++k) {
+            const int q = entry(k).x;
+            if (q != sq) {
+                sq = q;
+                sq_ok = *(volatile int *)a.p[q].status == 0;
+            }
+            if (sq_ok) break;
+        }
+        return k;
+    };
+    int nld[2] = {0, 0};  // loads issued per member barrier (thread 0)
+    auto load_members = [&](int k, int b) {
+        const int2 e = entry(k);
+        mbar_expect_tx(&bars[b], (uint32_t)a.p[e.x].ne * kTileM * 4);
+        tma_load_2d(smb + b * bstride, &a.m[2 * e.x + 1], &bars[b], e.y * kTileM, 0);
+        const int n = b ? ++nld[1] : ++nld[0];
+        lpar = (lpar & ~(1 << b)) | (((n - 1) & 1) << b);
+        pend |= 1 << b;
+    };
+    auto load_t = [&](int q) {
+        const UpdateProb &P = a.p[q];
+        mbar_expect_tx(&bars[3], (uint32_t)P.kblocks * P.ntile * 128);
+        for (int kb = 0; kb < P.kblocks; ++kb)
+            tma_load_2d(sb + (size_t)kb * P.ntile * 128, &a.m[2 * q], &bars[3], kb * kAtomK, 0);
+        tq = q;
+        pend_t = 1;
+        ++ntl;
+    };
+
     if (tid == 0) {
-        s_fail = *status;  // one read: the whole CTA leaves or none of it
-        s_bad = 0;
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        s_abort = 0;
+        for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    if (s_fail) return;  // s_fail is 0 from here on until the operand wait below
-    const uint32_t tx_bytes = (uint32_t)kblocks * ntile * 128 + (uint32_t)ne * kTileM * 4;
-    if (tid == 0) {
-        mbar_expect_tx(&bars[0], tx_bytes);
-        for (int kb = 0; kb < kblocks; ++kb)
-            tma_load_2d(sb + (size_t)kb * ntile * 128, map_t, &bars[0], kb * kAtomK, 0);
-        tma_load_2d(sm, map_m, &bars[0], m0, 0);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(tmem_cols)
+                     "r"(a.cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -92,154 +143,168 @@ __device__ __forceinline__ void update_tc_tile(const CUtensorMap *map_t, const C
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    // the first tile's copies, and thread 0's bounded wait for them straight
+    // after (its limit read before the copies are issued)
+    int cur_q = -1;  // the problem of the tile in hand (its status word takes a timeout)
+    if (tid == 0) {
+        const int k = next_valid(e0);
+        s_next = k;
+        s_tload = 0;
+        if (k < e1) {
+            cur_q = entry(k).x;
+            const long long lim = a.p[cur_q].wait_limit;
+            load_t(entry(k).x);
+            s_tload = 1;
+            load_members(k, 0);
+            if (!(mbar_wait(&bars[0], 0, lim) && mbar_wait(&bars[3], 0, lim))) s_abort = 1;
+        }
+    }
+    __syncthreads();
 
-    // the operand wait uses the plan's limit (thread 0 decides for the CTA); an
-    // expired wait issues no MMA
-    if (tid == 0 && !mbar_wait(&bars[0], 0, wait_limit)) s_fail = 1;
-    __syncthreads();
-    bool ok = s_fail == 0;
-    if (ok) {
-        mbar_wait(&bars[0], 0);  // complete: each thread's own acquire of the copied tiles
-        // ensemble mean of point pl: members i = q, q + 8, ... summed in FP32
-        // with their rounding errors (error-free two-sum), the 8 slice sums
-        // combined in FP64 in slice order
-        const int pl = tid;
-        double sum = 0.0;
-        for (int q = 0; q < 8; ++q) {
-            float sh = 0.f, sl = 0.f;
-            for (int i = q; i < ne; i += 8) {
-                const float a = sm[i * kTileM + pl];
-                const float t = sh + a, bv = t - sh;
-                sl += (sh - (t - bv)) + (a - bv);
-                sh = t;
-            }
-            sum += (double)sh + (double)sl;
-        }
-        // BF16 anomalies, FP32 centring and scaling; K padding is zero.  Row pl
-        // of atom kb: 8 granules of 16 bytes, granule g stored at g ^ (pl mod 8)
-        const float xbf = (float)(sum * inv_ne), isqf = (float)isq;
-        const uint32_t sw = (uint32_t)(pl & 7);
-        for (int kb = 0; kb < kblocks; ++kb) {
-            unsigned char *row = sa + (size_t)kb * kTileM * 128 + (size_t)pl * 128;
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                uint32_t w[4];
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int i0 = kb * kAtomK + g * 8 + 2 * h;
-                    const float v0 = i0 < ne ? (sm[i0 * kTileM + pl] - xbf) * isqf : 0.f;
-                    const float v1 = i0 + 1 < ne ? (sm[(i0 + 1) * kTileM + pl] - xbf) * isqf : 0.f;
-                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);  // v0 at the lower address
-                    w[h] = *reinterpret_cast<const uint32_t *>(&b2);
-                }
-                *reinterpret_cast<uint4 *>(row + (((uint32_t)g ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
-            }
-        }
-        // the anomaly rows are read by the MMA (async proxy)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    if (ok && tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t idesc = idesc_bf16(kTileM, ntile);
-        const int ksteps = kblocks * (kAtomK / 16);
-        for (int j = 0; j < ksteps; ++j) {
-            const int kb = j / (kAtomK / 16), kk = j % (kAtomK / 16);
-            const uint64_t adesc = smem_desc_sw128(smem_u32(sa + (size_t)kb * kTileM * 128 + kk * 32));
-            const uint64_t bdesc = smem_desc_sw128(smem_u32(sb + (size_t)kb * ntile * 128 + kk * 32));
-            mma_bf16(tmem, adesc, bdesc, idesc, j > 0 ? 1u : 0u);
-        }
-        mma_commit(&bars[1]);
-    }
-    // the accumulator wait; the CTA goes on only if every thread saw it
-    if (ok && !mbar_wait(&bars[1], 0)) s_bad = 1;
-    __syncthreads();
-    const bool done = ok && s_bad == 0;
-    if (!done) {
+    const bool two = a.nbuf == 2;
+    int k = s_next, it = 0, tph = 0, ph = 0;  // ph bit b: parity of buffer b's next completion
+    while (k < e1 && !s_abort) {
+        const int b = two ? (it & 1) : 0;
+        const int2 e = entry(k);
+        const UpdateProb &P = a.p[e.x];
+        cur_q = e.x;
+        const bool tload = s_tload != 0;
+        float *sm = smb + b * bstride;
+        // a. the next tile's members into the other buffer
         if (tid == 0) {
-            atomicCAS(status, 0, kStTimeout);
-            if (!ok) mbar_wait(&bars[0], 0);  // let our own copies land (default bound) before the CTA exits
+            const int nk = next_valid(k + 1);
+            s_next2 = nk;
+            if (two && nk < e1) load_members(nk, b ^ 1);
         }
-    } else {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int pl = warp * 32 + lane, p = m0 + pl;
-        const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < ntile; c0 += 16) {
-            uint32_t r[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(row + (uint32_t)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // b. the operands: thread 0 waits with the handle's limit and decides
+        // for the CTA (for the first tile it did so when it issued the copies);
+        // the others then acquire the completed copies at once
+        if (tid == 0 && it > 0) {
+            bool ok = mbar_wait(&bars[b], (ph >> b) & 1, P.wait_limit);
+            if (ok && tload) ok = mbar_wait(&bars[3], tph & 1, P.wait_limit);
+            if (!ok) s_abort = 1;
+        }
+        __syncthreads();
+        if (s_abort) break;
+        mbar_wait(&bars[b], (ph >> b) & 1);
+        if (tload) mbar_wait(&bars[3], tph & 1);
+        if (tid == 0) {
+            pend &= ~(1 << b);
+            if (tload) pend_t = 0;
+        }
+        ph ^= 1 << b;
+        tph += tload ? 1 : 0;
+        const int nk = s_next2;
+        // c. anomalies of point pl: the ensemble mean from 8 member slices
+        // (FP32 error-free sums, combined in FP64 in slice order), then the
+        // BF16 rows (x_i - mean) / sqrt(Ne - 1), K padding zero.  Row pl of
+        // atom kb: 8 granules of 16 bytes, granule g stored at g ^ (pl mod 8)
+        {
+            const int ne = P.ne, pl = tid;
+            double sum = 0.0;
+            for (int q = 0; q < 8; ++q) {
+                float sh = 0.f, sl = 0.f;
+                for (int i = q; i < ne; i += 8) {
+                    const float x = sm[i * kTileM + pl];
+                    const float t = sh + x, bv = t - sh;
+                    sl += (sh - (t - bv)) + (x - bv);
+                    sh = t;
+                }
+                sum += (double)sh + (double)sl;
+            }
+            const float xbf = (float)(sum * P.inv_ne), isqf = (float)P.isq;
+            const uint32_t sw = (uint32_t)(pl & 7);
+            for (int kb = 0; kb < P.kblocks; ++kb) {
+                unsigned char *row = sa + (size_t)kb * kTileM * 128 + (size_t)pl * 128;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int c = c0 + q;
-                const float v = __uint_as_float(r[q]);
-                if (c < ne)
-                    sm[c * kTileM + pl] += v;  // rows past nx are clipped by the TMA store
-                else if (c == ne && p < nx)
-                    dC[p] = v;
+                for (int g = 0; g < 8; ++g) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int i0 = kb * kAtomK + g * 8 + 2 * h;
+                        const float v0 = i0 < ne ? (sm[i0 * kTileM + pl] - xbf) * isqf : 0.f;
+                        const float v1 = i0 + 1 < ne ? (sm[(i0 + 1) * kTileM + pl] - xbf) * isqf : 0.f;
+                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);  // v0 at the lower address
+                        w[h] = *reinterpret_cast<const uint32_t *>(&b2);
+                    }
+                    *reinterpret_cast<uint4 *>(row + (((uint32_t)g ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A is read by the MMA (async proxy)
+        }
+        __syncthreads();
+        // d. D = A T^T
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = idesc_bf16(kTileM, P.ntile);
+            const int ksteps = P.kblocks * (kAtomK / 16);
+            for (int j = 0; j < ksteps; ++j) {
+                const int kb = j / (kAtomK / 16), kk = j % (kAtomK / 16);
+                const uint64_t adesc = smem_desc_sw128(smem_u32(sa + (size_t)kb * kTileM * 128 + kk * 32));
+                const uint64_t bdesc = smem_desc_sw128(smem_u32(sb + (size_t)kb * P.ntile * 128 + kk * 32));
+                mma_bf16(tmem, adesc, bdesc, idesc, j > 0 ? 1u : 0u);
+            }
+            mma_commit(&bars[2]);
+        }
+        if (!mbar_wait(&bars[2], it & 1)) s_abort = 1;  // default bound
+        __syncthreads();
+        if (s_abort) break;
+        // e. T of the next problem (the MMAs reading T are complete)
+        if (tid == 0) {
+            s_tload = 0;
+            if (nk < e1 && entry(nk).x != tq) {
+                load_t(entry(nk).x);
+                s_tload = 1;
             }
         }
-        // the member tile goes back with one TMA store (generic-proxy writes
-        // made visible to the async proxy first)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // f. epilogue: lanes 32 w .. 32 w + 31 of TMEM are warp w's points
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        {
+            const int pl = warp * 32 + lane, p = e.y * kTileM + pl, ne = P.ne, nx = P.nx;
+            const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
+            float *mem = P.members;
+            for (int c0 = 0; c0 < P.ntile; c0 += 16) {
+                uint32_t r[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15])
+                    : "r"(row + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (p < nx) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int c = c0 + q;
+                        const float v = __uint_as_float(r[q]);
+                        if (c < ne)
+                            mem[(size_t)c * nx + p] = sm[c * kTileM + pl] + v;
+                        else if (c == ne)
+                            P.dC[p] = v;
+                    }
+                }
+            }
+        }
+        // g. TMEM, A and this buffer are free for the next tiles
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        if (tid == 0) tma_store_2d(map_m, sm, m0, 0);
+        if (!two && tid == 0 && nk < e1) load_members(nk, 0);
+        k = nk;
+        ++it;
+    }
+    __syncthreads();
+    if (s_abort && tid == 0) {
+        if (cur_q >= 0) atomicCAS(a.p[cur_q].status, 0, kStTimeout);
+        // let our own copies land (default bound) before the CTA exits
+        for (int i = 0; i < 2; ++i)
+            if ((pend >> i) & 1) mbar_wait(&bars[i], (lpar >> i) & 1);
+        if (pend_t) mbar_wait(&bars[3], (ntl - 1) & 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
-}
-
-__global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ CUtensorMap map_t,
-                                                   const __grid_constant__ CUtensorMap map_m,
-                                                   float *__restrict__ dC, int nx, int ne, int kblocks,
-                                                   int ntile, int tmem_cols, long long wait_limit, int *status,
-                                                   double inv_ne, double isq) {
-    update_tc_tile(&map_t, &map_m, dC, nx, ne, kblocks, ntile, tmem_cols, wait_limit, status, blockIdx.x * kTileM,
-                   inv_ne, isq);
-}
-
-// The update of up to kUpdateGroupMax problems in one launch: their tensor
-// maps travel as one parameter block (T and members of the launch's problem q
-// at 2 q, 2 q + 1; prob[q] its index in the table); block b works on tile
-// map[b].y of the launch's problem map[b].x.
-struct UpdateGroupMaps {
-    CUtensorMap m[2 * kUpdateGroupMax];
-    int prob[kUpdateGroupMax];
-};
-
-__global__ void __launch_bounds__(128) k_update_tc_group(const __grid_constant__ UpdateGroupMaps maps,
-                                                         const GroupProb *__restrict__ probs,
-                                                         const int2 *__restrict__ map) {
-    // the problem's scalars are read once per block (every block of the
-    // problem reads the same table entry)
-    __shared__ float *s_dc;
-    __shared__ int *s_status;
-    __shared__ int s_nx, s_ne, s_kb, s_nt, s_cols;
-    __shared__ long long s_wait;
-    __shared__ double s_inv, s_isq;
-    const int2 e = map[blockIdx.x];
-    if (threadIdx.x == 0) {
-        const GroupProb &g = probs[maps.prob[e.x]];
-        s_dc = g.dC;
-        s_status = g.status;
-        s_nx = g.nx;
-        s_ne = g.ne;
-        s_kb = g.kblocks;
-        s_nt = g.ntile;
-        s_cols = g.tmem_cols;
-        s_wait = g.wait_limit;
-        s_inv = g.inv_ne;
-        s_isq = g.isq;
-    }
-    __syncthreads();
-    update_tc_tile(&maps.m[2 * e.x], &maps.m[2 * e.x + 1], s_dc, s_nx, s_ne, s_kb, s_nt, s_cols, s_wait, s_status,
-                   e.y * kTileM, s_inv, s_isq);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.cols) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -274,8 +339,9 @@ static bool encode_kmajor(CUtensorMap *m, const __nv_bfloat16 *ptr, int ld, int 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t update_tc_smem(int kblocks, int ntpad, int ne) {
-    return 1024 + (size_t)kblocks * (kTileM + ntpad) * 128 + (size_t)ne * kTileM * 4 + 64;
+size_t update_tc_smem(int kblocks, int ntpad, int ne, int nbuf) {
+    // alignment slack, A, T, the member tiles, barriers and the TMEM slot
+    return 1024 + (size_t)kblocks * (kTileM + ntpad) * 128 + (size_t)nbuf * ne * kTileM * 4 + 64;
 }
 
 size_t update_tc_launch_smem(size_t smem, int tmem_cols) {
@@ -293,7 +359,7 @@ bool update_tc_supported(int ne, int ldx, int ntpad, int nx) {
     // The anomaly rows hold 64 kblocks >= ne values.
     if (ntpad < 16 || ntpad > 256 || ntpad % 16 || ldx % 16 || ne < 2 || ne > 256 || nx % 4) return false;
     const int kblocks = (ldx + kAtomK - 1) / kAtomK;
-    return update_tc_smem(kblocks, ntpad, ne) <= 200 * 1024 && encode_fn() != nullptr;
+    return update_tc_smem(kblocks, ntpad, ne, 1) <= 200 * 1024 && encode_fn() != nullptr;
 }
 
 static bool encode_members(CUtensorMap *m, const float *ptr, int nx, int ne) {
@@ -317,7 +383,7 @@ bool update_tc_prepare(UpdateTcPlan *plan, int ldx, int nx, const __nv_bfloat16 
     int cols = 32;
     while (cols < ntpad) cols <<= 1;
     plan->tmem_cols = cols;
-    plan->smem = update_tc_launch_smem(update_tc_smem(plan->kblocks, ntpad, ne), cols);
+    plan->smem = update_tc_launch_smem(update_tc_smem(plan->kblocks, ntpad, ne, 1), cols);
     plan->nx = nx;
     plan->ne = ne;
     plan->wait_limit = kWaitLimitCycles;
@@ -328,36 +394,79 @@ bool update_tc_prepare(UpdateTcPlan *plan, int ldx, int nx, const __nv_bfloat16 
     return true;
 }
 
-cudaError_t launch_update_tc(const UpdateTcPlan &plan, float *members, float *dC, int *status, cudaStream_t s) {
+// one launch of the persistent update over `nent` tiles of the problems
+// args.p[0 .. nprob) (maps filled); its layout from their largest sizes
+static cudaError_t update_launch(UpdateLaunchArgs &args, int nprob, const int2 *map, int nent, cudaStream_t s) {
     static OncePerDevice attr;
-    attr.run([](int) { return cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); });
-    if (members != plan.members) return cudaErrorInvalidValue;
+    cudaError_t e =
+        attr.run([](int) { return cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); });
+    if (e != cudaSuccess) return e;
+    if (nent <= 0) return cudaSuccess;
+    int kbmax = 1, ntmax = 16, nemax = 2;
+    for (int q = 0; q < nprob; ++q) {
+        kbmax = std::max(kbmax, args.p[q].kblocks);
+        ntmax = std::max(ntmax, args.p[q].ntile);
+        nemax = std::max(nemax, args.p[q].ne);
+    }
+    int cols = 32;
+    while (cols < ntmax) cols <<= 1;
+    args.kbmax = kbmax;
+    args.ntmax = ntmax;
+    args.nemax = nemax;
+    args.cols = cols;
+    args.nbuf = update_tc_smem(kbmax, ntmax, nemax, 2) <= 200 * 1024 ? 2 : 1;
+    const size_t smem = update_tc_launch_smem(update_tc_smem(kbmax, ntmax, nemax, args.nbuf), cols);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    int dev = 0, sms = kNumSMs;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
+    // besides the kernel's 1 KB of static shared memory
+    const int per_sm = std::max(1, std::min(16, (int)((size_t)228 * 1024 / (smem + 2048))));
+    const int grid = std::min(nent, std::max(1, sms) * per_sm);
     count_launches(1);
-    const int grid = (plan.nx + kTileM - 1) / kTileM;
-    k_update_tc<<<grid, 128, plan.smem, s>>>(plan.map_t, plan.map_m, dC, plan.nx, plan.ne, plan.kblocks, plan.ntile,
-                                             plan.tmem_cols, plan.wait_limit, status, 1.0 / plan.ne,
-                                             1.0 / std::sqrt((double)(plan.ne - 1)));
+    k_update_tc<<<grid, 128, smem, s>>>(args, map, nent);
     return cudaGetLastError();
 }
 
+UpdateProb update_tc_prob(const UpdateTcPlan &plan, float *dC, int *status) {
+    UpdateProb p;
+    p.members = const_cast<float *>(plan.members);
+    p.dC = dC;
+    p.status = status;
+    p.nx = plan.nx;
+    p.ne = plan.ne;
+    p.kblocks = plan.kblocks;
+    p.ntile = plan.ntile;
+    p.wait_limit = plan.wait_limit;
+    p.inv_ne = 1.0 / plan.ne;
+    p.isq = 1.0 / std::sqrt((double)(plan.ne - 1));
+    return p;
+}
+
+cudaError_t launch_update_tc(const UpdateTcPlan &plan, float *members, float *dC, int *status, cudaStream_t s) {
+    if (members != plan.members) return cudaErrorInvalidValue;
+    UpdateLaunchArgs args;
+    memset(&args, 0, sizeof(args));
+    args.m[0] = plan.map_t;
+    args.m[1] = plan.map_m;
+    args.p[0] = update_tc_prob(plan, dC, status);
+    return update_launch(args, 1, nullptr, (plan.nx + kTileM - 1) / kTileM, s);
+}
+
 cudaError_t launch_update_tc_group(const GroupPlan &plan, cudaStream_t s) {
-    static OncePerDevice attr;
-    cudaError_t e = attr.run(
-        [](int) { return cudaFuncSetAttribute(k_update_tc_group, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); });
-    if (e != cudaSuccess) return e;
-    UpdateGroupMaps maps;
+    UpdateLaunchArgs args;
     for (const GroupPlan::UpdateLaunch &L : plan.upd) {
-        const int nb = L.map_end - L.map_begin;
-        if (nb <= 0) continue;
-        memset(&maps, 0, sizeof(maps));
-        for (size_t q = 0; q < L.probs.size(); ++q) {
-            maps.m[2 * q] = plan.upd_maps[2 * (size_t)L.probs[q]];
-            maps.m[2 * q + 1] = plan.upd_maps[2 * (size_t)L.probs[q] + 1];
-            maps.prob[q] = L.probs[q];
+        memset(&args, 0, sizeof(args));
+        const int np = (int)L.probs.size();
+        if (np > kUpdateLaunchMax) return cudaErrorInvalidValue;
+        for (int q = 0; q < np; ++q) {
+            const int j = L.probs[q];
+            args.m[2 * q] = plan.upd_maps[2 * (size_t)j];
+            args.m[2 * q + 1] = plan.upd_maps[2 * (size_t)j + 1];
+            args.p[q] = plan.upd_probs[j];
         }
-        count_launches(1);
-        k_update_tc_group<<<nb, 128, L.smem, s>>>(maps, plan.d_probs, plan.d_maps + plan.map_off[kGsUpdate] + L.map_begin);
-        e = cudaGetLastError();
+        cudaError_t e = update_launch(args, np, plan.d_maps + plan.map_off[kGsUpdate] + L.map_begin,
+                                      L.map_end - L.map_begin, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

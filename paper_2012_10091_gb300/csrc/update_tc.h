@@ -20,6 +20,16 @@ struct UpdateTcPlan {
     bool ready;
 };
 
+// one problem of an update launch (the kernel's view)
+struct UpdateProb {
+    float *members, *dC;
+    int *status;
+    int nx, ne, kblocks, ntile;
+    long long wait_limit;  // operand waits, SM clock cycles
+    double inv_ne, isq;    // 1/Ne, 1/sqrt(Ne - 1) (host values)
+};
+constexpr int kUpdateLaunchMax = 96;  // problems per launch (tensor maps and scalars as parameters)
+
 bool update_tc_supported(int ne, int ldx, int ntpad, int nx);
 bool update_tc_prepare(UpdateTcPlan *plan, int ldx, int nx, const __nv_bfloat16 *Tt, int ntpad, int ne,
                        const float *members);
@@ -27,9 +37,11 @@ bool update_tc_prepare(UpdateTcPlan *plan, int ldx, int nx, const __nv_bfloat16 
 // with X the BF16 normalised anomalies of the members as they are on entry
 // (formed in the kernel); `members` must be the buffer the plan was prepared for
 cudaError_t launch_update_tc(const UpdateTcPlan &plan, float *members, float *dC, int *status, cudaStream_t s);
-// dynamic shared memory of one update tile (operands and the member tile), and
+// the launch view of a handle's update
+UpdateProb update_tc_prob(const UpdateTcPlan &plan, float *dC, int *status);
+// dynamic shared memory of the update (operands and nbuf member tiles), and
 // what a launch asks for so that its CTAs never oversubscribe TMEM
-size_t update_tc_smem(int kblocks, int ntpad, int ne);
+size_t update_tc_smem(int kblocks, int ntpad, int ne, int nbuf);
 size_t update_tc_launch_smem(size_t smem, int tmem_cols);
 
 // the update step of a grouped analysis (every problem of the plan)

@@ -276,21 +276,19 @@ template void launch_recentre<float>(float *, size_t, int, const float *, const 
 template void launch_recentre<double>(double *, size_t, int, const double *, const int *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// ensemble mean (FP64 accuracy) and normalised anomalies X
+// ensemble mean and normalised anomalies X
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void ens_anom_body(const T *__restrict__ m, size_t nx, int ne, double inv_ne, double isq,
                                               double *__restrict__ X64, __nv_bfloat16 *__restrict__ X16, int ldx,
                                               const int *status, size_t blk) {
     // CTA: 32 consecutive points (lane) x the members split over the 8 warps.
-    // Mean: per-warp slice sums combined in FP64 in a fixed order by warp 0;
-    // then the normalised anomalies: FP64 member-major rows, or BF16
-    // point-major rows assembled in shared memory so every row of ldx values
-    // is stored contiguously.  GB300 runs about 2 FP64 FMAs per clock per SM,
-    // so FP32 states are summed per slice in FP32 with an error-free two-sum
-    // (the running sum and its rounding errors, both exact in FP32), and
-    // 1/Ne and 1/sqrt(Ne - 1) come from the host: 3 FP64 operations per
-    // thread instead of one per member plus a division and a square root.
+    // Mean: per-warp slice sums combined in a fixed order by warp 0; then the
+    // normalised anomalies: FP64 member-major rows, or BF16 point-major rows
+    // assembled in shared memory so every row of ldx values is stored
+    // contiguously.  GB300 runs about 2 FP64 FMAs per clock per SM, so FP32
+    // states are summed in double-FP32 arithmetic (no FP64 operation), and
+    // 1/Ne and 1/sqrt(Ne - 1) come from the host.
     extern __shared__ __align__(16) unsigned char sm_raw[];
     double *part = reinterpret_cast<double *>(sm_raw);                        // [8][32]
     double *mean = part + 8 * 32;                                             // [32]
@@ -300,8 +298,11 @@ __device__ __forceinline__ void ens_anom_body(const T *__restrict__ m, size_t nx
     const size_t p0 = blk * 32;
     const size_t p = p0 + lane;
     const bool ok = p < nx;
-    double slice;
     if constexpr (std::is_same<T, float>::value) {
+        // FP32 states: each slice an error-free FP32 sum (running sum and the
+        // sum of its rounding errors), the 8 slices combined in slice order in
+        // the same double-FP32 arithmetic, the mean rounded to FP32 (the
+        // tensor-core update forms its anomalies with these same operations)
         float sh = 0.f, sl = 0.f;
         if (ok)
             for (int i = wp; i < ne; i += 8) {
@@ -310,20 +311,32 @@ __device__ __forceinline__ void ens_anom_body(const T *__restrict__ m, size_t nx
                 sl += (sh - (t - bv)) + (a - bv);  // rounding error of sh + a, exact
                 sh = t;
             }
-        slice = (double)sh + (double)sl;
+        float2 *part2 = reinterpret_cast<float2 *>(part);
+        part2[wp * 32 + lane] = make_float2(sh, sl);
+        __syncthreads();
+        if (wp == 0) {
+            float H = 0.f, L = 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 v = part2[q * 32 + lane];
+                const float t = H + v.x, bv = t - H;
+                L += (H - (t - bv)) + (v.x - bv) + v.y;
+                H = t;
+            }
+            mean[lane] = (double)((H + L) * (float)inv_ne);
+        }
     } else {
         double acc = 0.0;
         if (ok)
             for (int i = wp; i < ne; i += 8) acc += (double)m[(size_t)i * nx + p];
-        slice = acc;
-    }
-    part[wp * 32 + lane] = slice;
-    __syncthreads();
-    if (wp == 0) {
-        double sum = 0.0;
+        part[wp * 32 + lane] = acc;
+        __syncthreads();
+        if (wp == 0) {
+            double sum = 0.0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) sum += part[q * 32 + lane];
-        mean[lane] = sum * inv_ne;
+            for (int q = 0; q < 8; ++q) sum += part[q * 32 + lane];
+            mean[lane] = sum * inv_ne;
+        }
     }
     __syncthreads();
     const double xb = mean[lane];
@@ -333,10 +346,10 @@ __device__ __forceinline__ void ens_anom_body(const T *__restrict__ m, size_t nx
             for (int i = wp; i < ne; i += 8) X64[(size_t)i * nx + p] = ((double)m[(size_t)i * nx + p] - xb) * isq;
         return;
     }
-    // BF16 path: FP64-accurate mean, FP32 centring and scaling.  The FP32
-    // rounding of the mean (2^-24 of the state) is far below the BF16 rounding
-    // of the anomaly (2^-9 of the anomaly) for any spread above 2^-15 of the
-    // state.
+    // BF16 path: a mean accurate to its FP32 rounding, FP32 centring and
+    // scaling.  The FP32 rounding of the mean (2^-24 of the state) is far below
+    // the BF16 rounding of the anomaly (2^-9 of the anomaly) for any spread
+    // above 2^-15 of the state.
     const float isqf = (float)isq, xbf = (float)xb;
     for (int i = wp; i < ldx; i += 8)
         tile[lane * ldt + i] = __float2bfloat16((ok && i < ne) ? ((float)m[(size_t)i * nx + p] - xbf) * isqf : 0.f);

@@ -43,6 +43,7 @@ namespace mgk {
 namespace {
 
 constexpr int kTileM = 128;
+constexpr int kUpdateThreads = 256;  // two threads per point of the tile
 constexpr int kAtomK = 64;                        // bf16 values per 128-byte swizzle row
 using namespace tc;
 
@@ -75,7 +76,7 @@ struct UpdateLaunchArgs {
 // Tiles of a problem whose status word is set are skipped.  Any wait that
 // runs out stops the CTA: MGENKF_ERR_TIMEOUT in that problem's status word,
 // the copies in flight awaited (default bound), TMEM freed.
-__global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ UpdateLaunchArgs a,
+__global__ void __launch_bounds__(kUpdateThreads) k_update_tc(const __grid_constant__ UpdateLaunchArgs a,
                                                    const int2 *__restrict__ map, int nent) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned operand buffers
@@ -88,6 +89,8 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ Updat
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + a.nbuf * bstride);  // members x2, MMA, T
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
     __shared__ int s_abort, s_next, s_next2, s_tload;
+    __shared__ float2 s_part[4][kTileM];  // slice sums 4..7 of the second thread half
+    __shared__ float s_mean[kTileM];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int e0 = (int)((long long)blockIdx.x * nent / gridDim.x);
@@ -195,40 +198,60 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ Updat
         ph ^= 1 << b;
         tph += tload ? 1 : 0;
         const int nk = s_next2;
-        // c. anomalies of point pl: the ensemble mean from 8 member slices
-        // (FP32 error-free sums, combined in FP64 in slice order), then the
-        // BF16 rows (x_i - mean) / sqrt(Ne - 1), K padding zero.  Row pl of
-        // atom kb: 8 granules of 16 bytes, granule g stored at g ^ (pl mod 8)
+        // c. anomalies of point pl = tid mod 128: the ensemble mean from 8
+        // member slices i = q, q + 8, ... (half h = tid / 128 sums slices
+        // 4h .. 4h + 3), each an FP32 error-free sum (running sum and the sum
+        // of its rounding errors), the slices combined in slice order in the
+        // same double-FP32 arithmetic and the mean rounded to FP32; then the
+        // BF16 rows (x_i - mean) / sqrt(Ne - 1), K padding zero, granules split
+        // between the halves.  Row pl of atom kb: 8 granules of 16 bytes,
+        // granule g stored at g ^ (pl mod 8)
         {
-            const int ne = P.ne, pl = tid;
-            double sum = 0.0;
-            for (int q = 0; q < 8; ++q) {
-                float sh = 0.f, sl = 0.f;
-                for (int i = q; i < ne; i += 8) {
+            const int ne = P.ne, pl = tid & (kTileM - 1), half = tid >> 7;
+            float2 sl4[4];
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                float sh = 0.f, se = 0.f;
+                for (int i = 4 * half + qq; i < ne; i += 8) {
                     const float x = sm[i * kTileM + pl];
                     const float t = sh + x, bv = t - sh;
-                    sl += (sh - (t - bv)) + (x - bv);
+                    se += (sh - (t - bv)) + (x - bv);
                     sh = t;
                 }
-                sum += (double)sh + (double)sl;
+                sl4[qq] = make_float2(sh, se);
             }
-            const float xbf = (float)(sum * P.inv_ne), isqf = (float)P.isq;
-            const uint32_t sw = (uint32_t)(pl & 7);
-            for (int kb = 0; kb < P.kblocks; ++kb) {
-                unsigned char *row = sa + (size_t)kb * kTileM * 128 + (size_t)pl * 128;
+            if (half) {
 #pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    uint32_t w[4];
+                for (int qq = 0; qq < 4; ++qq) s_part[qq][pl] = sl4[qq];
+            }
+            __syncthreads();
+            if (!half) {
+                float H = 0.f, L = 0.f;
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int i0 = kb * kAtomK + g * 8 + 2 * h;
-                        const float v0 = i0 < ne ? (sm[i0 * kTileM + pl] - xbf) * isqf : 0.f;
-                        const float v1 = i0 + 1 < ne ? (sm[(i0 + 1) * kTileM + pl] - xbf) * isqf : 0.f;
-                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);  // v0 at the lower address
-                        w[h] = *reinterpret_cast<const uint32_t *>(&b2);
-                    }
-                    *reinterpret_cast<uint4 *>(row + (((uint32_t)g ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+                for (int q = 0; q < 8; ++q) {
+                    const float2 v = q < 4 ? sl4[q] : s_part[q - 4][pl];
+                    const float t = H + v.x, bv = t - H;
+                    L += (H - (t - bv)) + (v.x - bv) + v.y;
+                    H = t;
                 }
+                s_mean[pl] = (H + L) * (float)P.inv_ne;
+            }
+            __syncthreads();
+            const float xbf = s_mean[pl], isqf = (float)P.isq;
+            const uint32_t sw = (uint32_t)(pl & 7);
+            for (int gi = half; gi < P.kblocks * 8; gi += 2) {
+                const int kb = gi >> 3, g = gi & 7;
+                unsigned char *row = sa + (size_t)kb * kTileM * 128 + (size_t)pl * 128;
+                uint32_t w[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int i0 = gi * 8 + 2 * h;
+                    const float v0 = i0 < ne ? (sm[i0 * kTileM + pl] - xbf) * isqf : 0.f;
+                    const float v1 = i0 + 1 < ne ? (sm[(i0 + 1) * kTileM + pl] - xbf) * isqf : 0.f;
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);  // v0 at the lower address
+                    w[h] = *reinterpret_cast<const uint32_t *>(&b2);
+                }
+                *reinterpret_cast<uint4 *>(row + (((uint32_t)g ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A is read by the MMA (async proxy)
         }
@@ -257,13 +280,13 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ Updat
                 s_tload = 1;
             }
         }
-        // f. epilogue: lanes 32 w .. 32 w + 31 of TMEM are warp w's points
+        // f. epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its points)
+        // and the 16-column chunks w / 4, w / 4 + 2, ...
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         {
-            const int pl = warp * 32 + lane, p = e.y * kTileM + pl, ne = P.ne, nx = P.nx;
-            const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
-            float *mem = P.members;
-            for (int c0 = 0; c0 < P.ntile; c0 += 16) {
+            const int lq = warp & 3, pl = lq * 32 + lane, p = e.y * kTileM + pl, ne = P.ne, nx = P.nx;
+            const uint32_t row = tmem + ((uint32_t)(lq * 32) << 16);
+            for (int c0 = (warp >> 2) * 16; c0 < P.ntile; c0 += 32) {
                 uint32_t r[16];
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
@@ -274,12 +297,14 @@ __global__ void __launch_bounds__(128) k_update_tc(const __grid_constant__ Updat
                     : "r"(row + (uint32_t)c0));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (p < nx) {
+                    float *mp = P.members + (size_t)c0 * nx + p;
+                    const float *sp = sm + c0 * kTileM + pl;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const int c = c0 + q;
                         const float v = __uint_as_float(r[q]);
                         if (c < ne)
-                            mem[(size_t)c * nx + p] = sm[c * kTileM + pl] + v;
+                            mp[(size_t)q * nx] = sp[q * kTileM] + v;
                         else if (c == ne)
                             P.dC[p] = v;
                     }
@@ -420,11 +445,13 @@ static cudaError_t update_launch(UpdateLaunchArgs &args, int nprob, const int2 *
     int dev = 0, sms = kNumSMs;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
-    // besides the kernel's 1 KB of static shared memory
-    const int per_sm = std::max(1, std::min(16, (int)((size_t)228 * 1024 / (smem + 2048))));
+    // besides the kernel's static shared memory; 8 warps per CTA
+    cudaFuncAttributes fa;
+    const size_t stat = cudaFuncGetAttributes(&fa, k_update_tc) == cudaSuccess ? fa.sharedSizeBytes : 8192;
+    const int per_sm = std::max(1, std::min(8, (int)((size_t)228 * 1024 / (smem + stat + 1024))));
     const int grid = std::min(nent, std::max(1, sms) * per_sm);
     count_launches(1);
-    k_update_tc<<<grid, 128, smem, s>>>(args, map, nent);
+    k_update_tc<<<grid, kUpdateThreads, smem, s>>>(args, map, nent);
     return cudaGetLastError();
 }
 

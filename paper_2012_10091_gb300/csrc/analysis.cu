@@ -123,11 +123,22 @@ void launch_obs_apply(const T *members, const T *xstar, size_t nx, int ne, int n
 // ---------------------------------------------------------------------------
 // observation means and innovations (Algorithm 1 step 4; Algorithm 4 step 5)
 // ---------------------------------------------------------------------------
-// yo_copy (if not NULL) receives y^o as read
+// x = hi[o] + lo[o] up to 2^-48 |x|: hi = x rounded to FP32, lo = the
+// remainder (exact in FP64) rounded to FP32.  The operands of the
+// double-FP32 gain products (mixed precision).
+__device__ __forceinline__ void split_df(double x, float *__restrict__ hi, float *__restrict__ lo, size_t o) {
+    const float h = __double2float_rn(x);
+    hi[o] = h;
+    lo[o] = __double2float_rn(__dsub_rn(x, (double)h));
+}
+
+// yo_copy (if not NULL) receives y^o as read; Zh, Zl (if not NULL) the
+// double-FP32 split of row ne of Z
 __device__ __forceinline__ void obs_mean_body(const double *__restrict__ yf, const double *__restrict__ yo, int ne,
                                               double inv_ne, int ny, double *__restrict__ ybar,
                                               double *__restrict__ Z, int *status, int blk,
-                                              double *__restrict__ yo_copy) {
+                                              double *__restrict__ yo_copy, float *__restrict__ Zh = nullptr,
+                                              float *__restrict__ Zl = nullptr) {
     // 32 observations per CTA (lane), 8 slices of the members (warp); the slice
     // sums are combined in a fixed order.
     __shared__ double part[8][33];
@@ -146,20 +157,23 @@ __device__ __forceinline__ void obs_mean_body(const double *__restrict__ yf, con
         const double y = yo[j];
         if (!isfinite(y)) atomicCAS(status, 0, kStNonFinite);
         if (yo_copy) yo_copy[j] = y;
-        Z[(size_t)ne * ny + j] = y - yf[(size_t)ne * ny + j];
+        const double d = y - yf[(size_t)ne * ny + j];
+        Z[(size_t)ne * ny + j] = d;
+        if (Zh) split_df(d, Zh, Zl, (size_t)ne * ny + j);
     }
 }
 
 __global__ void __launch_bounds__(256) k_obs_mean(const double *__restrict__ yf, const double *__restrict__ yo,
                                                   int ne, double inv_ne, int ny, double *__restrict__ ybar,
-                                                  double *__restrict__ Z, int *status) {
-    obs_mean_body(yf, yo, ne, inv_ne, ny, ybar, Z, status, blockIdx.x, nullptr);
+                                                  double *__restrict__ Z, int *status, float *__restrict__ Zh,
+                                                  float *__restrict__ Zl) {
+    obs_mean_body(yf, yo, ne, inv_ne, ny, ybar, Z, status, blockIdx.x, nullptr, Zh, Zl);
 }
 
 void launch_obs_mean(const double *yf, const double *yo, int ne, int ny, double *ybar, double *Z,
-                     int *status, cudaStream_t s) {
+                     int *status, cudaStream_t s, float *Zh, float *Zl) {
     count_launches(1);
-    k_obs_mean<<<ceil_div(ny, 32), 256, 0, s>>>(yf, yo, ne, 1.0 / ne, ny, ybar, Z, status);
+    k_obs_mean<<<ceil_div(ny, 32), 256, 0, s>>>(yf, yo, ne, 1.0 / ne, ny, ybar, Z, status, Zh, Zl);
 }
 
 // RMS of the innovation d* = y^o - H^C x^C* (one value; fixed-order FP64 sums)
@@ -194,7 +208,9 @@ __device__ __forceinline__ void obs_perturb_body(const double *__restrict__ yf, 
                                                  const double *__restrict__ yo, double *__restrict__ eps,
                                                  int gen_eps, uint64_t seed, const uint64_t *__restrict__ cycle,
                                                  double sigma, int ne, int ny, double isq, double *__restrict__ Y,
-                                                 double *__restrict__ Z, size_t blk) {
+                                                 double *__restrict__ Z, size_t blk, float *__restrict__ Yh = nullptr,
+                                                 float *__restrict__ Yl = nullptr, float *__restrict__ Zh = nullptr,
+                                                 float *__restrict__ Zl = nullptr) {
     const size_t total = (size_t)ne * ny;
     const size_t b = blk * blockDim.x + threadIdx.x;
     if (4 * b >= total) return;
@@ -220,8 +236,13 @@ __device__ __forceinline__ void obs_perturb_body(const double *__restrict__ yf, 
                 e = eps[o];
             }
             const double f = yf[o];
-            Y[o] = __dmul_rn(__dsub_rn(f, ybar[j]), isq);
-            Z[o] = __dsub_rn(__dadd_rn(yo[j], e), f);
+            const double yv = __dmul_rn(__dsub_rn(f, ybar[j]), isq), zv = __dsub_rn(__dadd_rn(yo[j], e), f);
+            Y[o] = yv;
+            Z[o] = zv;
+            if (Yh) {
+                split_df(yv, Yh, Yl, o);
+                split_df(zv, Zh, Zl, o);
+            }
         }
         if (++j == ny) {
             j = 0;
@@ -234,22 +255,26 @@ template <bool F32>
 __global__ void k_obs_perturb(const double *__restrict__ yf, const double *__restrict__ ybar,
                               const double *__restrict__ yo, double *__restrict__ eps, int gen_eps, uint64_t seed,
                               const uint64_t *__restrict__ cycle, double sigma, int ne, int ny, double isq,
-                              double *__restrict__ Y, double *__restrict__ Z) {
-    obs_perturb_body<F32>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma, ne, ny, isq, Y, Z, blockIdx.x);
+                              double *__restrict__ Y, double *__restrict__ Z, float *__restrict__ Yh,
+                              float *__restrict__ Yl, float *__restrict__ Zh, float *__restrict__ Zl) {
+    obs_perturb_body<F32>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma, ne, ny, isq, Y, Z, blockIdx.x, Yh, Yl, Zh,
+                          Zl);
 }
 
 void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, double *eps,
                         int gen_eps, uint64_t seed, const uint64_t *cycle, double sigma, int ne, int ny,
-                        double *Y, double *Z, cudaStream_t s) {
+                        double *Y, double *Z, cudaStream_t s, const DfOperands &df) {
     count_launches(1);
     const size_t blocks = ((size_t)ne * ny + 3) / 4;
     // isq = 1/sqrt(Ne - 1) from the host (an FP64 division and square root per thread on the device)
     const unsigned grid = (unsigned)ceil_div(blocks, 128);
     const double isq = 1.0 / std::sqrt((double)(ne - 1));
     if (gen_eps == 2)
-        k_obs_perturb<true><<<grid, 128, 0, s>>>(yf, ybar, yo, eps, 1, seed, cycle, sigma, ne, ny, isq, Y, Z);
+        k_obs_perturb<true><<<grid, 128, 0, s>>>(yf, ybar, yo, eps, 1, seed, cycle, sigma, ne, ny, isq, Y, Z, df.Yh,
+                                                 df.Yl, df.Zh, df.Zl);
     else
-        k_obs_perturb<false><<<grid, 128, 0, s>>>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma, ne, ny, isq, Y, Z);
+        k_obs_perturb<false><<<grid, 128, 0, s>>>(yf, ybar, yo, eps, gen_eps, seed, cycle, sigma, ne, ny, isq, Y, Z,
+                                                  df.Yh, df.Yl, df.Zh, df.Zl);
 }
 
 // Fine-to-coarse feedback: the forecast ensemble re-centred on the restricted
@@ -516,6 +541,127 @@ int gemm_nt_splits(int m, int n1, int n2, int K) {
     int splits = 1;
     while (tiles * splits * 2 <= 2 * kNumSMs && K / (splits * 2) >= 128) splits *= 2;
     return splits;
+}
+
+// ---------------------------------------------------------------------------
+// The gain products of the mixed path in double-FP32 arithmetic on the FP32
+// pipes (GB300 runs FP32 FMAs about 64 times faster than FP64 ones): each FP64
+// operand is a pair hi + lo of FP32 values (split_df); a b = ah bh + ah bl +
+// al bh (+ al bl, below 2^-48 |a b|, dropped), ah bh exactly as p + e with
+// e = fma(ah, bh, -p); the products are summed into a running FP32 sum s and
+// the FP32 sum c of its rounding errors (error-free two-sum) and of the small
+// terms.  The result s + c carries a relative error of order 2^-44 of the sum
+// of |a b|, far below the BF16 rounding of T that follows.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float &s, float &c) {
+    const float p = __fmul_rn(ah, bh);
+    const float e = __fmaf_rn(ah, bh, -p);
+    const float x = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+    const float t = __fadd_rn(s, p), bv = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(p, bv)), x));
+    s = t;
+}
+
+constexpr int kDfThreads = 64;  // a 16 x 16 output tile, 2 x 2 outputs per thread
+constexpr int kDfK = 32;        // K chunk staged in shared memory
+
+// Output tile (bx, by) of [S | Y^T R^-1 [D | d*]] as gemm_nt_block (A = B1 = Y,
+// m = n1 = ne, B2 = Z, n2 = ne + 1, symmetric S: tiles with bx < by are not
+// computed), from the double-FP32 operands.
+__device__ __forceinline__ void gemm_df_block(const DfOperands &df, int ne, int K, double divisor, double diag,
+                                              double *__restrict__ out1, double *__restrict__ out2, int bx, int by,
+                                              int bz, int kchunk, double *__restrict__ part) {
+    if (bx < by) return;
+    __shared__ float sAh[16][kDfK + 1], sAl[16][kDfK + 1], sBh[16][kDfK + 1], sBl[16][kDfK + 1];
+    const int m = ne, n1 = ne, n2 = ne + 1;
+    const int a0 = by * 16, c0 = bx * 16;
+    const int kb = part ? bz * kchunk : 0, ke = part ? min(K, kb + kchunk) : K;
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    // staging: row tid / 4 of the A and B tiles, k = (tid mod 4) * 8 .. + 7 of the chunk
+    const int sr = tid >> 2, sk = (tid & 3) * 8;
+    const int ar = a0 + sr, cr = c0 + sr;
+    const float *ah = ar < m ? df.Yh + (size_t)ar * K : nullptr, *al = ar < m ? df.Yl + (size_t)ar * K : nullptr;
+    const float *bh = cr < n1 ? df.Yh + (size_t)cr * K : (cr < n1 + n2 ? df.Zh + (size_t)(cr - n1) * K : nullptr);
+    const float *bl = cr < n1 ? df.Yl + (size_t)cr * K : (cr < n1 + n2 ? df.Zl + (size_t)(cr - n1) * K : nullptr);
+    float va[2][8], vb[2][8];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = k0 + sk + j;
+            const bool ok = k < ke;
+            va[0][j] = (ah && ok) ? ah[k] : 0.f;
+            va[1][j] = (al && ok) ? al[k] : 0.f;
+            vb[0][j] = (bh && ok) ? bh[k] : 0.f;
+            vb[1][j] = (bl && ok) ? bl[k] : 0.f;
+        }
+    };
+    float s[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, c[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    fetch(kb);
+    for (int k0 = kb; k0 < ke; k0 += kDfK) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            sAh[sr][sk + j] = va[0][j];
+            sAl[sr][sk + j] = va[1][j];
+            sBh[sr][sk + j] = vb[0][j];
+            sBl[sr][sk + j] = vb[1][j];
+        }
+        __syncthreads();
+        if (k0 + kDfK < ke) fetch(k0 + kDfK);  // in flight during the chunk's products
+#pragma unroll 4
+        for (int kk = 0; kk < kDfK; ++kk) {
+            float xh[2], xl[2], yh[2], yl[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                xh[i] = sAh[2 * ty + i][kk];
+                xl[i] = sAl[2 * ty + i][kk];
+                yh[i] = sBh[2 * tx + i][kk];
+                yl[i] = sBl[2 * tx + i][kk];
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) df_mac(xh[i], xl[i], yh[j], yl[j], s[i][j], c[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int a = a0 + 2 * ty + i, cc = c0 + 2 * tx + j;
+            const double acc = (double)s[i][j] + (double)c[i][j];
+            if (part) {
+                if (a < m && cc < n1 + n2) part[((size_t)bz * m + a) * (n1 + n2) + cc] = acc;
+                continue;
+            }
+            if (a < m) {
+                if (cc < n1) {
+                    out1[(size_t)a * n1 + cc] = (a == cc ? diag : 0.0) + acc / divisor;
+                    if (bx > by) out1[(size_t)cc * n1 + a] = acc / divisor;
+                } else if (cc < n1 + n2) {
+                    out2[(size_t)(cc - n1) * m + a] = acc / divisor;
+                }
+            }
+        }
+}
+
+__global__ void __launch_bounds__(kDfThreads) k_gemm_df(DfOperands df, int ne, int K, double divisor, double diag,
+                                                        double *__restrict__ out1, double *__restrict__ out2,
+                                                        int kchunk, double *__restrict__ part, const int *status) {
+    if (*status) return;
+    gemm_df_block(df, ne, K, divisor, diag, out1, out2, blockIdx.x, blockIdx.y, blockIdx.z, kchunk, part);
+}
+
+void launch_gemm_df(const DfOperands &df, int ne, int ny, double s2, double *S, double *Bt, const int *status,
+                    cudaStream_t s, double *part) {
+    const int splits = part ? gemm_nt_splits(ne, ne, ne + 1, ny) : 1;
+    const int kchunk = ceil_div(ceil_div(ny, splits), 32) * 32;
+    dim3 grid(ceil_div(2 * ne + 1, 16), ceil_div(ne, 16), splits);
+    count_launches(splits > 1 ? 2 : 1);
+    k_gemm_df<<<grid, kDfThreads, 0, s>>>(df, ne, ny, s2, 1.0, S, Bt, kchunk, splits > 1 ? part : nullptr, status);
+    if (splits > 1)
+        k_gemm_nt_reduce<<<grid_for((size_t)ne * (2 * ne + 1), 256), 256, 0, s>>>(part, splits, ne, ne, ne + 1, true,
+                                                                                s2, 1.0, S, Bt, status);
 }
 
 void launch_gemm_nt_f64(const double *A, int m, const double *B1, int n1, const double *B2, int n2,
@@ -1327,13 +1473,14 @@ __global__ void __launch_bounds__(128) kg_obs_apply(const GroupProb *__restrict_
 __global__ void __launch_bounds__(256) kg_obs_mean(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
     const int2 e = map[blockIdx.x];
     const GroupProb &g = P[e.x];
-    obs_mean_body(g.yf, g.yo_in, g.ne, g.inv_ne, g.ny, g.ybar, g.Z, g.status, e.y, g.yo);
+    obs_mean_body(g.yf, g.yo_in, g.ne, g.inv_ne, g.ny, g.ybar, g.Z, g.status, e.y, g.yo, g.df.Zh, g.df.Zl);
 }
 
 __global__ void __launch_bounds__(128) kg_obs_perturb(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
     const int2 e = map[blockIdx.x];
     const GroupProb &g = P[e.x];
-    obs_perturb_body<true>(g.yf, g.ybar, g.yo, g.eps, 1, g.seed, g.cycle, g.sigma, g.ne, g.ny, g.isq, g.Y, g.Z, e.y);
+    obs_perturb_body<true>(g.yf, g.ybar, g.yo, g.eps, 1, g.seed, g.cycle, g.sigma, g.ne, g.ny, g.isq, g.Y, g.Z, e.y,
+                           g.df.Yh, g.df.Yl, g.df.Zh, g.df.Zl);
 }
 
 __global__ void __launch_bounds__(256) kg_innov_rms(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
@@ -1343,14 +1490,13 @@ __global__ void __launch_bounds__(256) kg_innov_rms(const GroupProb *__restrict_
 
 // block e.y = (z ty + by) tx + bx over the tiles of [S | Y^T R^-1 [D | d*]]
 // and the K chunks z (tiles strictly below the diagonal of S are not listed)
-__global__ void __launch_bounds__(256) kg_gemm(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
+__global__ void __launch_bounds__(kDfThreads) kg_gemm(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
     const int2 e = map[blockIdx.x];
     const GroupProb &g = P[e.x];
     if (*g.status) return;
     const int ne = g.ne, tx = ceil_div(2 * ne + 1, 16), ty = ceil_div(ne, 16);
     const int bx = e.y % tx, by = (e.y / tx) % ty, bz = e.y / (tx * ty);
-    gemm_nt_block(g.Y, ne, g.Y, ne, g.Z, ne + 1, g.ny, g.s2, 1.0, g.S, g.Bt, bx, by, bz, g.kchunk,
-                  g.splits > 1 ? g.part : nullptr);
+    gemm_df_block(g.df, ne, g.ny, g.s2, 1.0, g.S, g.Bt, bx, by, bz, g.kchunk, g.splits > 1 ? g.part : nullptr);
 }
 
 __global__ void __launch_bounds__(256) kg_gemm_reduce(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
@@ -1568,7 +1714,7 @@ cudaError_t group_analyse(const GroupPlan &plan, cudaStream_t s) {
     if (step(kGsObsMean)) kg_obs_mean<<<n(kGsObsMean), 256, 0, s>>>(P, M(kGsObsMean));
     if (step(kGsPerturb)) kg_obs_perturb<<<n(kGsPerturb), 128, 0, s>>>(P, M(kGsPerturb));
     if (step(kGsInnov)) kg_innov_rms<<<n(kGsInnov), 256, 0, s>>>(P, M(kGsInnov));
-    if (step(kGsGemm)) kg_gemm<<<n(kGsGemm), 256, 0, s>>>(P, M(kGsGemm));
+    if (step(kGsGemm)) kg_gemm<<<n(kGsGemm), kDfThreads, 0, s>>>(P, M(kGsGemm));
     if (step(kGsReduce)) kg_gemm_reduce<<<n(kGsReduce), 256, 0, s>>>(P, M(kGsReduce));
     if (step(kGsCholCluster))
         kg_cholesky_cluster<<<n(kGsCholCluster) * kCholCluster, 288, plan.chol_cluster_smem, s>>>(P, M(kGsCholCluster));

@@ -37,9 +37,17 @@ template <typename T>
 void launch_obs_apply(const T *members, const T *xstar, size_t nx, int ne, int ny, int taps,
                       const int32_t *tap_idx, const double *tap_w, double *yf, cudaStream_t s);
 
-// ybar_j, innovation of x^C* (row ne of Z), finiteness check of y^o.
+// FP32 hi/lo copies of Y [ne][ny] and Z [ne+1][ny] (x = hi + lo up to 2^-48
+// |x|), the operands of the double-FP32 gain products of the mixed path;
+// NULL pointers: none
+struct DfOperands {
+    float *Yh = nullptr, *Yl = nullptr, *Zh = nullptr, *Zl = nullptr;
+};
+
+// ybar_j, innovation of x^C* (row ne of Z), finiteness check of y^o; Zh, Zl
+// (if not NULL) receive the split of row ne of Z.
 void launch_obs_mean(const double *yf, const double *yo, int ne, int ny, double *ybar, double *Z,
-                     int *status, cudaStream_t s);
+                     int *status, cudaStream_t s, float *Zh = nullptr, float *Zl = nullptr);
 
 // eps (drawn or given), Y = (yf - ybar)/sqrt(ne-1), Z[i] = yo + eps_i - yf_i.
 // cycle: device pointer to the analysis counter (Philox counter word 0)
@@ -77,7 +85,7 @@ void launch_recentre(T *members, size_t nx, int ne, const T *xstar, const int *s
 // words with the Box-Muller transform in FP32 (mixed precision)
 void launch_obs_perturb(const double *yf, const double *ybar, const double *yo, double *eps,
                         int gen_eps, uint64_t seed, const uint64_t *cycle, double sigma, int ne, int ny,
-                        double *Y, double *Z, cudaStream_t s);
+                        double *Y, double *Z, cudaStream_t s, const DfOperands &df = DfOperands());
 void launch_bump_counter(uint64_t *c, cudaStream_t s);
 
 // normalised state anomalies X (Eq. Ensemble_Anomaly); FP64 [ne][nx] or BF16 [nx][ne].
@@ -93,6 +101,11 @@ void launch_gemm_nt_f64(const double *A, int m, const double *B1, int n1, const 
                         int K, double scale, double diag, double *out1, double *out2,
                         const int *status, cudaStream_t s, double *part = nullptr);
 int gemm_nt_splits(int m, int n1, int n2, int K);
+// S = I + Y^T R^-1 Y (ne x ne) and Bt = Y^T R^-1 [D | d*] (column c of Bt
+// contiguous) as launch_gemm_nt_f64 (same split of K with `part`), from the
+// double-FP32 operands, summed in double-FP32 arithmetic (mixed precision).
+void launch_gemm_df(const DfOperands &df, int ne, int ny, double s2, double *S, double *Bt, const int *status,
+                    cudaStream_t s, double *part);
 
 // C[j][l] = sum_i Y[i][j] Y[i][l] + diag*(j==l), j,l < ny (direct form).
 void launch_gemm_tn_f64(const double *Y, int ne, int ny, double diag, double *C, const int *status,

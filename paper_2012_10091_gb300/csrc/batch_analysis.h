@@ -28,6 +28,7 @@ struct GroupProb {
     double *yf, *ybar, *eps, *Y, *Z;
     double *S, *Lt, *Bt;  // S = I + Y^T R^-1 Y and its factor; T (column c contiguous) in Bt
     double *part;         // split-K partial sums of the gain products
+    DfOperands df;        // double-FP32 copies of Y and Z (the gain products' operands)
     double *innov;        // RMS of d* = y^o - H^C x^C*
     __nv_bfloat16 *Tt;
     int *status;
@@ -48,7 +49,7 @@ enum GroupStep {
     kGsObsMean,      // observation means, d*, y^o check and copy
     kGsPerturb,      // perturbed observations, Y, Z
     kGsInnov,        // RMS of d*
-    kGsGemm,         // S and Y^T R^-1 [D | d*] (tiles or K chunks)
+    kGsGemm,         // S and Y^T R^-1 [D | d*] in double-FP32 arithmetic (tiles or K chunks)
     kGsReduce,       // sum of the K chunks
     kGsCholCluster,  // Cholesky of S, 8-CTA clusters (32 <= Ne <= 256)
     kGsChol,         // Cholesky of S, one CTA (Ne < 32)

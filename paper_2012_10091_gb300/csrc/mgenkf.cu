@@ -59,6 +59,7 @@ struct mgenkf_ctx {
     bool recentre = false;       // re-centre the forecast ensemble on x^C* before each analysis
     double filter_sigma = 0.0;   // NS: sixth-order filter after every model step (0: off)
     double *gemm_part = nullptr; // split-K partial sums of the gain GEMMs
+    DfOperands df;               // mixed precision, ensemble form: double-FP32 copies of Y and Z
     UpdateTcPlan tc;             // tensor-core member update (mixed precision)
     mgk_cnn_t cnn = nullptr;     // learned correction added by prolong_correct (not owned)
     size_t scratch_n = 0;
@@ -138,7 +139,8 @@ static void free_all(mgenkf_ctx *h) {
     void *ptrs[] = {h->fine, h->members, h->xstar, h->dC, h->tap_idx, h->tap_w, h->yf, h->yo,
                     h->ybar, h->eps, h->Y, h->Z, h->X64, h->X16, h->Tt, h->S, h->Lt, h->Bt, h->C,
                     h->Ct, h->W, h->truth_d, h->rmse_part, h->rmse_d, h->scratch, h->status,
-                    h->ns_scratch, h->gemm_part, h->cycle_d, h->fine_prev, h->fine_tmp};
+                    h->ns_scratch, h->gemm_part, h->cycle_d, h->fine_prev, h->fine_tmp,
+                    h->df.Yh, h->df.Yl, h->df.Zh, h->df.Zl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->Tm && h->Tm != h->Bt) cudaFree(h->Tm);
@@ -280,6 +282,12 @@ static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const 
     H_ALLOC(h->Z, (ne + 1) * ny * sizeof(double));
     h->ldx = (int)((ne + 15) / 16 * 16);
     h->ntpad = (int)((ne + 1 + 15) / 16 * 16);
+    if (h->mixed && !h->direct) {
+        H_ALLOC(h->df.Yh, ne * ny * sizeof(float));
+        H_ALLOC(h->df.Yl, ne * ny * sizeof(float));
+        H_ALLOC(h->df.Zh, (ne + 1) * ny * sizeof(float));
+        H_ALLOC(h->df.Zl, (ne + 1) * ny * sizeof(float));
+    }
     if (h->mixed) {
         H_ALLOC(h->X16, nx * h->ldx * sizeof(__nv_bfloat16));
         H_ALLOC(h->Tt, (size_t)h->ntpad * h->ldx * sizeof(__nv_bfloat16));
@@ -513,16 +521,20 @@ static void analyse_kernels(mgenkf_ctx *h, int gen_eps) {
     launch_restrict<T>((const T *)h->fine, xstar, h->dim, h->V, h->nc, h->r, s);
     if (h->recentre) launch_recentre<T>(members, nx, ne, xstar, h->status, s);
     launch_obs_apply<T>(members, xstar, nx, ne, ny, h->taps, h->tap_idx, h->tap_w, h->yf, s);
-    launch_obs_mean(h->yf, h->yo, ne, ny, h->ybar, h->Z, h->status, s);
+    launch_obs_mean(h->yf, h->yo, ne, ny, h->ybar, h->Z, h->status, s, h->df.Zh, h->df.Zl);
     launch_obs_perturb(h->yf, h->ybar, h->yo, h->eps, gen_eps, h->cfg.seed, h->cycle_d,
-                       h->cfg.obs_sigma, ne, ny, h->Y, h->Z, s);
+                       h->cfg.obs_sigma, ne, ny, h->Y, h->Z, s, h->df);
     // the tensor-core update forms the BF16 anomalies itself from the members it reads
     if (!(h->mixed && h->tc.ready)) launch_ens_anom<T>(members, nx, ne, h->X64, h->X16, h->status, s);
     const double s2 = h->cfg.obs_sigma * h->cfg.obs_sigma;
     if (!h->direct) {
         // S = I + Y^T R^-1 Y (ne x ne) and B = Y^T R^-1 [D | d*]; T = S^-1 B
-        launch_gemm_nt_f64(h->Y, ne, h->Y, ne, h->Z, ne + 1, ny, s2, 1.0, h->S, h->Bt, h->status, s,
-                           h->gemm_part);
+        // (mixed precision: the products in double-FP32 arithmetic)
+        if (h->df.Yh)
+            launch_gemm_df(h->df, ne, ny, s2, h->S, h->Bt, h->status, s, h->gemm_part);
+        else
+            launch_gemm_nt_f64(h->Y, ne, h->Y, ne, h->Z, ne + 1, ny, s2, 1.0, h->S, h->Bt, h->status, s,
+                               h->gemm_part);
         launch_cholesky(h->S, h->Lt, ne, h->status, s);
         launch_chol_solve(h->S, h->Lt, ne, h->Bt, h->Bt, ne + 1, h->mixed ? h->Tt : nullptr, h->ldx,
                           h->status, s);
@@ -1262,7 +1274,7 @@ static mgenkf_status batch_analyse(mgenkf_batch *b) {
 // tensor-core update, without the re-centring, the learned correction or the
 // final fine iteration, at sizes the grouped kernels take
 static bool groupable(const mgenkf_ctx *h) {
-    return !h->direct && !h->recentre && h->tc.ready && !h->cnn && !h->record_prev && h->alpha == 0.0 &&
+    return !h->direct && h->df.Yh && !h->recentre && h->tc.ready && !h->cnn && !h->record_prev && h->alpha == 0.0 &&
            h->filter_sigma == 0.0 && group_supported(h->ne, h->ny);
 }
 
@@ -1309,6 +1321,7 @@ static mgenkf_status batch_group_prepare(mgenkf_batch *b) {
         g.Lt = h->Lt;
         g.Bt = h->Bt;
         g.part = h->gemm_part;
+        g.df = h->df;
         g.innov = b->innov + j;
         g.Tt = h->Tt;
         g.status = h->status;

@@ -51,7 +51,7 @@ def _one_analysis(M, w, gain_form, precision, explicit_eps):
     assert st == 0
     fine_ref = O.prolong_add(dC_ref, f0, 1, 1, w.nc, w.ratio)
     return dict(fine=fine, mem=mem, fields=fields, xstar=xstar, e=e, m_ref=m_ref, dC_ref=dC_ref,
-                fine_ref=fine_ref, m0=m0, f0=f0)
+                fine_ref=fine_ref, m0=m0, f0=f0, yo=yo)
 
 
 @pytest.mark.parametrize("gain_form", [0, 1])
@@ -90,6 +90,27 @@ def test_mixed_analysis_matches_oracle(M, nf, ratio, ne, npr):
     dfine = r["fine_ref"] - r["f0"]
     bound_f = tol * np.max(np.abs(dfine)) + 1e-6 * np.max(np.abs(r["fine_ref"]))
     assert np.max(np.abs(r["fine"] - r["fine_ref"])) < bound_f
+
+
+@pytest.mark.parametrize("nf,ratio,ne,npr", [(256, 4, 32, 16), (4096, 4, 37, 130), (16384, 4, 128, 512)])
+def test_mixed_gain_coefficients_match_oracle(M, nf, ratio, ne, npr):
+    """The mixed path forms S = I + Y^T R^-1 Y and Y^T R^-1 [D | d*] in
+    double-FP32 arithmetic (each FP64 operand split into two FP32 values): its
+    gain coefficients T agree with the oracle's gain K = Y^T (Y Y^T + R)^-1
+    (Algorithm 3 step 8, X = I) applied to [D | d*] to 1e-9 of the largest
+    coefficient, where FP32 products would be off by about 1e-6."""
+    w = W.burgers_custom(nf, ratio, ne, npr, obs_kind="random", sigma=0.05, precision="mixed")
+    r = _one_analysis(M, w, 0, "mixed", explicit_eps=True)
+    idx, var = W.observation_layout(w)
+    yf = np.stack([O.obs_coarse(x, 1, 1, w.nc, w.ratio, idx, var) for x in list(r["m0"]) + [r["xstar"]]])
+    Y = (yf[:ne] - yf[:ne].mean(axis=0)) / np.sqrt(ne - 1)          # ne x ny
+    D = r["yo"][None, :] + r["e"] - yf[:ne]                          # ne x ny
+    dstar = r["yo"] - yf[ne]
+    st, K = O.enkf_gain(np.eye(ne), Y.T, w.sigma ** 2 * np.eye(w.ny))
+    assert st == 0
+    T_ref = np.vstack([D @ K.T, (K @ dstar)[None, :]])               # (ne + 1) x ne, row c = column c of T
+    T = r["fields"][M.MGENKF_FIELD_T].reshape(ne + 1, ne)
+    assert np.max(np.abs(T - T_ref)) <= 1e-9 * np.max(np.abs(T_ref))
 
 
 def test_mixed_perturbations_follow_the_oracle_stream(M):

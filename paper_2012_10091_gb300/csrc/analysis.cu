@@ -73,16 +73,17 @@ void launch_restrict(const T *fine, T *xstar, int dim, int V, int nc, int r, cud
 // predicted observations H^C x (Algorithm 3 step 2): sparse 4- or 16-tap rows
 // ---------------------------------------------------------------------------
 // Thread: observation j = bx * blockDim.x + threadIdx.x, rows i = i0 .. i0 +
-// kObsRows - 1 of yf (members, then x^C* as row ne); its taps (<= 16) stay in
-// registers for those rows.
-constexpr int kObsRows = 8;
+// rows - 1 of yf (members, then x^C* as row ne); its taps (<= 16) stay in
+// registers for those rows.  One problem alone takes 2 rows per thread (enough
+// threads to hide the gathers); a grouped launch over many problems 8.
+constexpr int kObsRows = 8, kObsRowsOne = 2;
 
 template <typename T>
 __device__ __forceinline__ void obs_apply_body(const T *__restrict__ members, const T *__restrict__ xstar,
                                                size_t nx, int ne, int ny, int taps,
                                                const int32_t *__restrict__ tap_idx,
                                                const double *__restrict__ tap_w, double *__restrict__ yf, int bx,
-                                               int i0) {
+                                               int i0, int rows) {
     const int j = bx * blockDim.x + threadIdx.x;
     if (j >= ny) return;
     int32_t idx[16];
@@ -93,7 +94,7 @@ __device__ __forceinline__ void obs_apply_body(const T *__restrict__ members, co
             idx[t] = tap_idx[(size_t)j * taps + t];
             w[t] = tap_w[(size_t)j * taps + t];
         }
-    const int i1 = min(i0 + kObsRows, ne + 1);
+    const int i1 = min(i0 + rows, ne + 1);
     for (int i = i0; i < i1; ++i) {
         const T *x = i < ne ? members + (size_t)i * nx : xstar;
         double acc = 0.0;
@@ -109,14 +110,15 @@ __global__ void __launch_bounds__(128) k_obs_apply(const T *__restrict__ members
                                                    size_t nx, int ne, int ny, int taps,
                                                    const int32_t *__restrict__ tap_idx,
                                                    const double *__restrict__ tap_w, double *__restrict__ yf) {
-    obs_apply_body<T>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf, blockIdx.x, blockIdx.y * kObsRows);
+    obs_apply_body<T>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf, blockIdx.x, blockIdx.y * kObsRowsOne,
+                      kObsRowsOne);
 }
 
 template <typename T>
 void launch_obs_apply(const T *members, const T *xstar, size_t nx, int ne, int ny, int taps,
                       const int32_t *tap_idx, const double *tap_w, double *yf, cudaStream_t s) {
     count_launches(1);
-    dim3 grid(ceil_div(ny, 128), ceil_div(ne + 1, kObsRows));
+    dim3 grid(ceil_div(ny, 128), ceil_div(ne + 1, kObsRowsOne));
     k_obs_apply<T><<<grid, 128, 0, s>>>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf);
 }
 
@@ -1467,7 +1469,7 @@ __global__ void __launch_bounds__(128) kg_obs_apply(const GroupProb *__restrict_
     const GroupProb &g = P[e.x];
     const int gx = ceil_div(g.ny, 128);
     obs_apply_body<float>(g.members, g.xstar, g.nx, g.ne, g.ny, g.taps, g.tap_idx, g.tap_w, g.yf, e.y % gx,
-                          (e.y / gx) * kObsRows);
+                          (e.y / gx) * kObsRows, kObsRows);
 }
 
 __global__ void __launch_bounds__(256) kg_obs_mean(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {

@@ -991,11 +991,21 @@ struct mgenkf_batch {
     cudaGraphExec_t exec = nullptr;
     int graph_nsteps = -1;
     double gamma = 1.4, mu = 1e-3, prandtl = 0.72;
-    // grouped analysis: one launch per analysis step over all problems (when
-    // every problem fits it; otherwise one chain per problem on the branches)
+    // grouped analysis: one launch per analysis step over all problems of a
+    // part (when every problem fits it; otherwise one chain per problem on the
+    // branches).  The problems are split into parts balanced by forecast work:
+    // part p + 1's forecast of a grid size starts when part p's has finished,
+    // and part p's analysis runs beside part p + 1's forecast.
     bool grouped = false;
-    GroupPlan gplan;
-    std::vector<long long> gplan_wait;  // each handle's update wait limit the plan was built with
+    int nparts = 0;                     // parts the plans and part tables were built for
+    std::vector<int> part;              // part of each problem
+    std::vector<GroupPlan> gplans;      // per part
+    std::vector<long long> gplan_wait;  // each handle's update wait limit the plans were built with
+    bool ptables_stale = true;          // part tables behind the current forecast choices
+    std::vector<NsGroup<float> *> pd_groups;  // [part x sizes]: device tables of the part's groups per size
+    std::vector<int> pngroups, punits;
+    std::vector<cudaStream_t> pstreams;  // [part x (sizes + 1)]: forecast streams per size, then the analysis stream
+    std::vector<cudaEvent_t> pev;        // [part x (sizes + 1)] + 1: forecast done per size, analysis done; start
     std::string err;
 };
 
@@ -1068,6 +1078,14 @@ static void build_tables(mgenkf_batch *b, std::vector<std::vector<NsGroup<float>
     }
 }
 
+static void free_part_tables(mgenkf_batch *b) {
+    for (NsGroup<float> *d : b->pd_groups)
+        if (d) cudaFree(d);
+    b->pd_groups.clear();
+    b->pngroups.clear();
+    b->punits.clear();
+}
+
 static mgenkf_status upload_tables(mgenkf_batch *b, const std::vector<std::vector<NsGroup<float>>> &tab) {
     // nothing may still read the old tables
     B_CUDA(cudaStreamSynchronize(b->s0));
@@ -1095,11 +1113,51 @@ static mgenkf_status upload_tables(mgenkf_batch *b, const std::vector<std::vecto
     b->exec = nullptr;
     b->graph = nullptr;
     b->graph_nsteps = -1;
+    b->ptables_stale = true;
+    return MGENKF_OK;
+}
+
+// device tables of the groups of each (part, grid size), for the current
+// forecast choices; nothing may read the old ones (the caller synchronised)
+static mgenkf_status upload_part_tables(mgenkf_batch *b) {
+    const int ns = (int)b->sizes.size(), np = b->nparts;
+    std::vector<std::vector<NsGroup<float>>> tab((size_t)np * ns);
+    std::vector<int> units((size_t)np * ns, 0);
+    for (size_t j = 0; j < b->hs.size(); ++j) {
+        NsGroup<float> g[2];
+        handle_groups(b->hs[j], g);
+        for (int k = 0; k < 2; ++k) {
+            const int si = size_index(b, g[k].n), ti = b->part[j] * ns + si;
+            int bands = 0, segs = 0, threads = 0;
+            ns2d_march_layout(g[k].n, b->shape[si], &bands, &segs, &threads);
+            g[k].tx = bands;
+            g[k].ty = segs;
+            g[k].tile_begin = units[ti];
+            units[ti] += bands * segs * g[k].nprob;
+            tab[ti].push_back(g[k]);
+        }
+    }
+    free_part_tables(b);
+    b->pd_groups.assign(tab.size(), nullptr);
+    b->pngroups.assign(tab.size(), 0);
+    b->punits = units;
+    for (size_t t = 0; t < tab.size(); ++t) {
+        b->pngroups[t] = (int)tab[t].size();
+        if (tab[t].empty()) continue;
+        B_CUDA(cudaMalloc(&b->pd_groups[t], tab[t].size() * sizeof(NsGroup<float>)));
+        B_CUDA(cudaMemcpyAsync(b->pd_groups[t], tab[t].data(), tab[t].size() * sizeof(NsGroup<float>),
+                               cudaMemcpyHostToDevice, b->s0));
+    }
+    B_CUDA(cudaStreamSynchronize(b->s0));
+    b->ptables_stale = false;
     return MGENKF_OK;
 }
 
 static void batch_free(mgenkf_batch *b) {
-    group_plan_free(&b->gplan);
+    for (GroupPlan &gp : b->gplans) group_plan_free(&gp);
+    free_part_tables(b);
+    for (cudaStream_t s : b->pstreams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->pev) cudaEventDestroy(e);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (NsGroup<float> *d : b->d_groups)
@@ -1278,8 +1336,64 @@ static bool groupable(const mgenkf_ctx *h) {
            h->filter_sigma == 0.0 && group_supported(h->ne, h->ny);
 }
 
-// (Re)build the grouped plan when none exists or a handle's update wait limit
-// changed; b->grouped says whether the analyses run grouped.
+// parts of the grouped cycle: MGENKF_BATCH_PARTS, default kDefaultBatchParts,
+// at most one per problem
+constexpr int kDefaultBatchParts = 2;
+constexpr int kMaxBatchParts = 8;
+
+static GroupProb group_prob(const mgenkf_batch *b, size_t j) {
+    const mgenkf_ctx *h = b->hs[j];
+    GroupProb g;
+    memset(&g, 0, sizeof(g));
+    g.fine = (float *)h->fine;
+    g.members = (float *)h->members;
+    g.xstar = (float *)h->xstar;
+    g.dC = (float *)h->dC;
+    g.tap_idx = h->tap_idx;
+    g.tap_w = h->tap_w;
+    g.yo_in = b->obs_stage + b->obs_off[j];
+    g.yo = h->yo;
+    g.yf = h->yf;
+    g.ybar = h->ybar;
+    g.eps = h->eps;
+    g.Y = h->Y;
+    g.Z = h->Z;
+    g.S = h->S;
+    g.Lt = h->Lt;
+    g.Bt = h->Bt;
+    g.part = h->gemm_part;
+    g.df = h->df;
+    g.innov = b->innov + j;
+    g.Tt = h->Tt;
+    g.status = h->status;
+    g.cycle = h->cycle_d;
+    g.seed = h->cfg.seed;
+    g.sigma = h->cfg.obs_sigma;
+    g.s2 = h->cfg.obs_sigma * h->cfg.obs_sigma;
+    // the same host-side constants as the single-problem launches
+    g.inv_ne = 1.0 / h->ne;
+    g.isq = 1.0 / std::sqrt((double)(h->ne - 1));
+    g.nc = h->nc;
+    g.r = h->r;
+    g.ne = h->ne;
+    g.ny = h->ny;
+    g.taps = h->taps;
+    g.ldx = h->ldx;
+    g.nx = (int)h->nx;
+    g.splits = gemm_nt_splits(h->ne, h->ne, h->ne + 1, h->ny);
+    g.kchunk = ceil_div(ceil_div(h->ny, g.splits), 32) * 32;
+    g.kblocks = h->tc.kblocks;
+    g.ntile = h->tc.ntile;
+    g.tmem_cols = h->tc.tmem_cols;
+    g.wait_limit = h->tc.wait_limit;
+    g.pw = h->pw;
+    return g;
+}
+
+// (Re)build the parts, their grouped plans and part tables when none exist,
+// the part count changed or a handle's update wait limit changed, and the
+// part tables when the forecast choices changed; b->grouped says whether the
+// analyses run grouped.
 static mgenkf_status batch_group_prepare(mgenkf_batch *b) {
     const char *env = getenv("MGENKF_BATCH_GROUPED");
     bool want = !(env && strcmp(env, "0") == 0);
@@ -1288,81 +1402,112 @@ static mgenkf_status batch_group_prepare(mgenkf_batch *b) {
         b->grouped = false;
         return MGENKF_OK;
     }
-    bool fresh = b->gplan.nprob == (int)b->hs.size() && b->gplan_wait.size() == b->hs.size();
+    int nparts = kDefaultBatchParts;
+    if (const char *e = getenv("MGENKF_BATCH_PARTS")) nparts = atoi(e);
+    nparts = std::max(1, std::min({nparts, kMaxBatchParts, (int)b->hs.size()}));
+    bool fresh = b->nparts == nparts && (int)b->gplans.size() == nparts && b->gplan_wait.size() == b->hs.size();
     for (size_t j = 0; fresh && j < b->hs.size(); ++j) fresh = b->gplan_wait[j] == b->hs[j]->tc.wait_limit;
-    if (fresh) {
-        b->grouped = true;
-        return MGENKF_OK;
-    }
-    // nothing may still read the old plan
+    if (fresh && b->grouped && !b->ptables_stale) return MGENKF_OK;
+    // nothing may still read the old plans and tables
     B_CUDA(cudaStreamSynchronize(b->s0));
     for (cudaStream_t s : b->aux) B_CUDA(cudaStreamSynchronize(s));
-    std::vector<GroupProb> probs(b->hs.size());
-    std::vector<CUtensorMap> maps;
-    b->gplan_wait.clear();
-    for (size_t j = 0; j < b->hs.size(); ++j) {
-        const mgenkf_ctx *h = b->hs[j];
-        GroupProb &g = probs[j];
-        memset(&g, 0, sizeof(g));
-        g.fine = (float *)h->fine;
-        g.members = (float *)h->members;
-        g.xstar = (float *)h->xstar;
-        g.dC = (float *)h->dC;
-        g.tap_idx = h->tap_idx;
-        g.tap_w = h->tap_w;
-        g.yo_in = b->obs_stage + b->obs_off[j];
-        g.yo = h->yo;
-        g.yf = h->yf;
-        g.ybar = h->ybar;
-        g.eps = h->eps;
-        g.Y = h->Y;
-        g.Z = h->Z;
-        g.S = h->S;
-        g.Lt = h->Lt;
-        g.Bt = h->Bt;
-        g.part = h->gemm_part;
-        g.df = h->df;
-        g.innov = b->innov + j;
-        g.Tt = h->Tt;
-        g.status = h->status;
-        g.cycle = h->cycle_d;
-        g.seed = h->cfg.seed;
-        g.sigma = h->cfg.obs_sigma;
-        g.s2 = h->cfg.obs_sigma * h->cfg.obs_sigma;
-        // the same host-side constants as the single-problem launches
-        g.inv_ne = 1.0 / h->ne;
-        g.isq = 1.0 / std::sqrt((double)(h->ne - 1));
-        g.nc = h->nc;
-        g.r = h->r;
-        g.ne = h->ne;
-        g.ny = h->ny;
-        g.taps = h->taps;
-        g.ldx = h->ldx;
-        g.nx = (int)h->nx;
-        g.splits = gemm_nt_splits(h->ne, h->ne, h->ne + 1, h->ny);
-        g.kchunk = ceil_div(ceil_div(h->ny, g.splits), 32) * 32;
-        g.kblocks = h->tc.kblocks;
-        g.ntile = h->tc.ntile;
-        g.tmem_cols = h->tc.tmem_cols;
-        g.wait_limit = h->tc.wait_limit;
-        g.pw = h->pw;
-        maps.push_back(h->tc.map_t);
-        maps.push_back(h->tc.map_m);
-        b->gplan_wait.push_back(h->tc.wait_limit);
-    }
-    b->grouped = group_plan_build(&b->gplan, probs, maps, b->s0);
-    if (!b->grouped) {
-        cudaGetLastError();
+    for (cudaStream_t s : b->pstreams) B_CUDA(cudaStreamSynchronize(s));
+    if (!fresh) {
+        for (GroupPlan &gp : b->gplans) group_plan_free(&gp);
+        b->gplans.assign(nparts, GroupPlan());
         b->gplan_wait.clear();
+        b->nparts = nparts;
+        // parts balanced by forecast work (points of the members and the
+        // fine run per step), largest problems first onto the lightest part
+        const size_t n = b->hs.size();
+        std::vector<double> work(n);
+        std::vector<int> order(n);
+        for (size_t j = 0; j < n; ++j) {
+            const mgenkf_ctx *h = b->hs[j];
+            work[j] = (double)h->ne * h->nc * h->nc + (double)h->nf * h->nf;
+            order[j] = (int)j;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+        std::vector<double> load(nparts, 0.0);
+        b->part.assign(n, 0);
+        for (int j : order) {
+            const int p = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            b->part[j] = p;
+            load[p] += work[j];
+        }
+        b->grouped = true;
+        for (int p = 0; p < nparts && b->grouped; ++p) {
+            std::vector<GroupProb> probs;
+            std::vector<CUtensorMap> maps;
+            for (size_t j = 0; j < n; ++j) {
+                if (b->part[j] != p) continue;
+                probs.push_back(group_prob(b, j));
+                maps.push_back(b->hs[j]->tc.map_t);
+                maps.push_back(b->hs[j]->tc.map_m);
+            }
+            b->grouped = !probs.empty() && group_plan_build(&b->gplans[p], probs, maps, b->s0);
+        }
+        if (!b->grouped) {
+            cudaGetLastError();
+            for (GroupPlan &gp : b->gplans) group_plan_free(&gp);
+            b->gplans.clear();
+            b->nparts = 0;
+            return MGENKF_OK;
+        }
+        for (const mgenkf_ctx *h : b->hs) b->gplan_wait.push_back(h->tc.wait_limit);
+        // streams and events of the parts
+        const size_t need_s = (size_t)nparts * (b->sizes.size() + 1);
+        while (b->pstreams.size() < need_s) {
+            cudaStream_t st;
+            B_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            b->pstreams.push_back(st);
+        }
+        while (b->pev.size() < need_s + 1) {
+            cudaEvent_t ev;
+            B_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            b->pev.push_back(ev);
+        }
+        b->ptables_stale = true;
+    }
+    if (b->ptables_stale) {
+        mgenkf_status st = upload_part_tables(b);
+        if (st) return st;
     }
     return MGENKF_OK;
 }
 
-// the analyses and prolongations of every handle, grouped: after all forecasts
-static mgenkf_status batch_analyse_grouped(mgenkf_batch *b) {
-    for (int k = 0; k < (int)b->sizes.size(); ++k) B_CUDA(cudaStreamWaitEvent(b->s0, b->ev[1 + k], 0));
-    cudaError_t e = group_analyse(b->gplan, b->s0);
-    if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("grouped analysis: ") + cudaGetErrorString(e));
+// One grouped cycle: for each grid size the parts' forecasts one after the
+// other on that size's stream of each part; part p's analysis waits for its own
+// forecasts of every size and runs beside part p + 1's.
+static mgenkf_status batch_cycle_grouped(mgenkf_batch *b, int nsteps) {
+    const int ns = (int)b->sizes.size(), np = b->nparts;
+    auto fstream = [&](int p, int k) { return b->pstreams[(size_t)p * (ns + 1) + k]; };
+    auto fdone = [&](int p, int k) { return b->pev[(size_t)p * (ns + 1) + k]; };
+    cudaEvent_t start = b->pev[(size_t)np * (ns + 1)];
+    B_CUDA(cudaEventRecord(start, b->s0));
+    for (int p = 0; p < np; ++p)
+        for (int k = 0; k < ns; ++k) {
+            cudaStream_t s = fstream(p, k);
+            B_CUDA(cudaStreamWaitEvent(s, p == 0 ? start : fdone(p - 1, k), 0));
+            const size_t t = (size_t)p * ns + k;
+            if (b->punits[t]) {
+                cudaError_t e = ns2d_forecast_table(b->pd_groups[t], b->pngroups[t], b->punits[t], b->sizes[k],
+                                                    nsteps, b->gamma, b->mu, b->prandtl, s);
+                if (e != cudaSuccess)
+                    B_FAIL(MGENKF_ERR_CUDA, std::string("batched forecast: ") + cudaGetErrorString(e));
+            }
+            B_CUDA(cudaEventRecord(fdone(p, k), s));
+        }
+    for (int p = 0; p < np; ++p) {
+        cudaStream_t a = b->pstreams[(size_t)p * (ns + 1) + ns];
+        for (int k = 0; k < ns; ++k) B_CUDA(cudaStreamWaitEvent(a, fdone(p, k), 0));
+        cudaError_t e = group_analyse(b->gplans[p], a);
+        if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("grouped analysis: ") + cudaGetErrorString(e));
+        cudaEvent_t adone = b->pev[(size_t)p * (ns + 1) + ns];
+        B_CUDA(cudaEventRecord(adone, a));
+        B_CUDA(cudaStreamWaitEvent(b->s0, adone, 0));
+    }
+    for (int k = 0; k < ns; ++k) B_CUDA(cudaStreamWaitEvent(b->s0, fdone(np - 1, k), 0));
     return MGENKF_OK;
 }
 
@@ -1387,8 +1532,13 @@ extern "C" mgenkf_status mgenkf_batch_cycle(mgenkf_batch_t b, int32_t nsteps, co
             if (st) return st;
         }
         B_CUDA(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed));
-        mgenkf_status st = batch_forecast(b, nsteps, false);
-        if (st == MGENKF_OK) st = b->grouped ? batch_analyse_grouped(b) : batch_analyse(b);
+        mgenkf_status st;
+        if (b->grouped) {
+            st = batch_cycle_grouped(b, nsteps);
+        } else {
+            st = batch_forecast(b, nsteps, false);
+            if (st == MGENKF_OK) st = batch_analyse(b);
+        }
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(b->s0, &g);
         if (st) {

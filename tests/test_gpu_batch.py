@@ -69,12 +69,15 @@ def _batched(M, b, ws, yos, nsteps, innov=None):
     return [g.get_state() for g in b.runs]
 
 
-@pytest.mark.parametrize("grouped", ["1", "0"])
-def test_batch_equals_per_problem_handles(M, monkeypatch, grouped):
-    """Grouped analysis (one launch per analysis step over all problems) and
-    the per-problem chains on the graph's branches (MGENKF_BATCH_GROUPED=0)
-    both give each problem's own handle results, bit for bit."""
+@pytest.mark.parametrize("grouped,parts", [("1", "1"), ("1", "2"), ("1", "4"), ("0", "1")])
+def test_batch_equals_per_problem_handles(M, monkeypatch, grouped, parts):
+    """Grouped analysis (one launch per analysis step over the problems of a
+    part; with several parts, part p's analysis runs beside part p + 1's
+    forecast) and the per-problem chains on the graph's branches
+    (MGENKF_BATCH_GROUPED=0) all give each problem's own handle results, bit
+    for bit."""
     monkeypatch.setenv("MGENKF_BATCH_GROUPED", grouped)
+    monkeypatch.setenv("MGENKF_BATCH_PARTS", parts)
     ws = _problems()
     assert len({w.nc for w in ws}) > 1 and len({w.ne for w in ws}) > 1
     nsteps = [10, 10, 7, 10]        # a changed step count recaptures the graph
@@ -227,9 +230,10 @@ def test_batch_at_multi_tile_sizes_matches_oracle(M):
 
 
 def test_grouped_cycle_launches(M, monkeypatch):
-    """A grouped batch cycle launches the forecast steps of each grid size and
-    a fixed number of analysis launches, whatever the problem count; the
-    per-problem chains launch about 13 kernels per problem."""
+    """A grouped batch cycle (one part) launches the forecast steps of each
+    grid size and a fixed number of analysis launches, whatever the problem
+    count; the per-problem chains launch about 13 kernels per problem."""
+    monkeypatch.setenv("MGENKF_BATCH_PARTS", "1")
     ws = _problems()
     inps, yos = _inputs(ws, 1)
     counts = {}

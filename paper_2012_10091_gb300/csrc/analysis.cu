@@ -78,15 +78,51 @@ void launch_restrict(const T *fine, T *xstar, int dim, int V, int nc, int r, cud
 // threads to hide the gathers); a grouped launch over many problems 8.
 constexpr int kObsRows = 8, kObsRowsOne = 2;
 
+// With FP32 states and the weights split into FP32 pairs (wh, wl: w = wh + wl
+// up to 2^-48 |w|, mixed precision) the taps are summed in double-FP32
+// arithmetic on the FP32 pipes: wh x exactly as p + e (e by FMA), wl x
+// rounded, the products summed into a running FP32 sum and the FP32 sum of its
+// rounding errors (error-free two-sum); otherwise in FP64.
 template <typename T>
 __device__ __forceinline__ void obs_apply_body(const T *__restrict__ members, const T *__restrict__ xstar,
                                                size_t nx, int ne, int ny, int taps,
                                                const int32_t *__restrict__ tap_idx,
                                                const double *__restrict__ tap_w, double *__restrict__ yf, int bx,
-                                               int i0, int rows) {
+                                               int i0, int rows, const float *__restrict__ wh = nullptr,
+                                               const float *__restrict__ wl = nullptr) {
     const int j = bx * blockDim.x + threadIdx.x;
     if (j >= ny) return;
     int32_t idx[16];
+    const int i1 = min(i0 + rows, ne + 1);
+    if constexpr (std::is_same<T, float>::value) {
+        if (wh) {
+            float w1[16], w2[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                if (t < taps) {
+                    idx[t] = tap_idx[(size_t)j * taps + t];
+                    w1[t] = wh[(size_t)j * taps + t];
+                    w2[t] = wl[(size_t)j * taps + t];
+                }
+            for (int i = i0; i < i1; ++i) {
+                const float *x = i < ne ? members + (size_t)i * nx : xstar;
+                float s = 0.f, c = 0.f;
+#pragma unroll
+                for (int t = 0; t < 16; ++t)
+                    if (t < taps) {
+                        const float xv = x[idx[t]];
+                        const float p = __fmul_rn(w1[t], xv), e = __fmaf_rn(w1[t], xv, -p);
+                        const float q = __fmul_rn(w2[t], xv);
+                        const float u = __fadd_rn(s, p), bv = __fsub_rn(u, s);
+                        c = __fadd_rn(c, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(u, bv)), __fsub_rn(p, bv)),
+                                                   __fadd_rn(e, q)));
+                        s = u;
+                    }
+                yf[(size_t)i * ny + j] = (double)s + (double)c;
+            }
+            return;
+        }
+    }
     double w[16];
 #pragma unroll
     for (int t = 0; t < 16; ++t)
@@ -94,7 +130,6 @@ __device__ __forceinline__ void obs_apply_body(const T *__restrict__ members, co
             idx[t] = tap_idx[(size_t)j * taps + t];
             w[t] = tap_w[(size_t)j * taps + t];
         }
-    const int i1 = min(i0 + rows, ne + 1);
     for (int i = i0; i < i1; ++i) {
         const T *x = i < ne ? members + (size_t)i * nx : xstar;
         double acc = 0.0;
@@ -109,17 +144,19 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_obs_apply(const T *__restrict__ members, const T *__restrict__ xstar,
                                                    size_t nx, int ne, int ny, int taps,
                                                    const int32_t *__restrict__ tap_idx,
-                                                   const double *__restrict__ tap_w, double *__restrict__ yf) {
+                                                   const double *__restrict__ tap_w, double *__restrict__ yf,
+                                                   const float *__restrict__ wh, const float *__restrict__ wl) {
     obs_apply_body<T>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf, blockIdx.x, blockIdx.y * kObsRowsOne,
-                      kObsRowsOne);
+                      kObsRowsOne, wh, wl);
 }
 
 template <typename T>
 void launch_obs_apply(const T *members, const T *xstar, size_t nx, int ne, int ny, int taps,
-                      const int32_t *tap_idx, const double *tap_w, double *yf, cudaStream_t s) {
+                      const int32_t *tap_idx, const double *tap_w, double *yf, cudaStream_t s, const float *wh,
+                      const float *wl) {
     count_launches(1);
     dim3 grid(ceil_div(ny, 128), ceil_div(ne + 1, kObsRowsOne));
-    k_obs_apply<T><<<grid, 128, 0, s>>>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf);
+    k_obs_apply<T><<<grid, 128, 0, s>>>(members, xstar, nx, ne, ny, taps, tap_idx, tap_w, yf, wh, wl);
 }
 
 // ---------------------------------------------------------------------------
@@ -1469,7 +1506,7 @@ __global__ void __launch_bounds__(128) kg_obs_apply(const GroupProb *__restrict_
     const GroupProb &g = P[e.x];
     const int gx = ceil_div(g.ny, 128);
     obs_apply_body<float>(g.members, g.xstar, g.nx, g.ne, g.ny, g.taps, g.tap_idx, g.tap_w, g.yf, e.y % gx,
-                          (e.y / gx) * kObsRows, kObsRows);
+                          (e.y / gx) * kObsRows, kObsRows, g.tap_wh, g.tap_wl);
 }
 
 __global__ void __launch_bounds__(256) kg_obs_mean(const GroupProb *__restrict__ P, const int2 *__restrict__ map) {
@@ -1745,7 +1782,8 @@ cudaError_t group_analyse(const GroupPlan &plan, cudaStream_t s) {
 #define MGK_INST(T)                                                                              \
     template void launch_restrict<T>(const T *, T *, int, int, int, int, cudaStream_t);          \
     template void launch_obs_apply<T>(const T *, const T *, size_t, int, int, int, const int32_t *, \
-                                      const double *, double *, cudaStream_t);                   \
+                                      const double *, double *, cudaStream_t, const float *,     \
+                                      const float *);                                            \
     template void launch_ens_anom<T>(const T *, size_t, int, double *, __nv_bfloat16 *,          \
                                      const int *, cudaStream_t);                                 \
     template void launch_update_f64<T>(T *, T *, const double *, const double *, size_t, int,    \

@@ -32,10 +32,13 @@ constexpr int kStNonFinite = 5;
 template <typename T>
 void launch_restrict(const T *fine, T *xstar, int dim, int V, int nc, int r, cudaStream_t s);
 
-// yf[i][j] = sum_t w[j][t] x_i[idx[j][t]] for members i < ne and x^C* (row ne).
+// yf[i][j] = sum_t w[j][t] x_i[idx[j][t]] for members i < ne and x^C* (row ne);
+// FP32 states with wh, wl (the weights split into FP32 pairs) are summed in
+// double-FP32 arithmetic, otherwise in FP64.
 template <typename T>
 void launch_obs_apply(const T *members, const T *xstar, size_t nx, int ne, int ny, int taps,
-                      const int32_t *tap_idx, const double *tap_w, double *yf, cudaStream_t s);
+                      const int32_t *tap_idx, const double *tap_w, double *yf, cudaStream_t s,
+                      const float *wh = nullptr, const float *wl = nullptr);
 
 // FP32 hi/lo copies of Y [ne][ny] and Z [ne+1][ny] (x = hi + lo up to 2^-48
 // |x|), the operands of the double-FP32 gain products of the mixed path;

@@ -23,6 +23,7 @@ struct GroupProb {
     float *fine, *members, *xstar, *dC;
     const int32_t *tap_idx;  // H^C taps [ny][taps]
     const double *tap_w;
+    const float *tap_wh, *tap_wl;  // the weights split into FP32 pairs (double-FP32 sums)
     const double *yo_in;  // this problem's observations (read by the innovation step)
     double *yo;           // copy of them in the problem's own buffer
     double *yf, *ybar, *eps, *Y, *Z;

@@ -41,6 +41,7 @@ struct mgenkf_ctx {
     void *fine = nullptr, *members = nullptr, *xstar = nullptr, *dC = nullptr;
     int32_t *tap_idx = nullptr;
     double *tap_w = nullptr;
+    float *tap_wh = nullptr, *tap_wl = nullptr;  // mixed precision: the weights split into FP32 pairs
     ProlongWeights pw;
     double *yf = nullptr, *yo = nullptr, *ybar = nullptr, *eps = nullptr, *Y = nullptr, *Z = nullptr;
     double *X64 = nullptr;
@@ -136,7 +137,7 @@ static mgenkf_status dalloc(mgenkf_ctx *h, P **p, size_t bytes) {
     } while (0)
 
 static void free_all(mgenkf_ctx *h) {
-    void *ptrs[] = {h->fine, h->members, h->xstar, h->dC, h->tap_idx, h->tap_w, h->yf, h->yo,
+    void *ptrs[] = {h->fine, h->members, h->xstar, h->dC, h->tap_idx, h->tap_w, h->tap_wh, h->tap_wl, h->yf, h->yo,
                     h->ybar, h->eps, h->Y, h->Z, h->X64, h->X16, h->Tt, h->S, h->Lt, h->Bt, h->C,
                     h->Ct, h->W, h->truth_d, h->rmse_part, h->rmse_d, h->scratch, h->status,
                     h->ns_scratch, h->gemm_part, h->cycle_d, h->fine_prev, h->fine_tmp,
@@ -355,6 +356,20 @@ static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const 
     }
     H_CUDA(cudaMemcpyAsync(h->tap_idx, tidx.data(), tidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
     H_CUDA(cudaMemcpyAsync(h->tap_w, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (h->mixed) {
+        // w = hi + lo: hi the weight rounded to FP32, lo the remainder (exact in
+        // FP64) rounded to FP32
+        std::vector<float> whi(tw.size()), wlo(tw.size());
+        for (size_t q = 0; q < tw.size(); ++q) {
+            whi[q] = (float)tw[q];
+            wlo[q] = (float)(tw[q] - (double)whi[q]);
+        }
+        H_ALLOC(h->tap_wh, tw.size() * sizeof(float));
+        H_ALLOC(h->tap_wl, tw.size() * sizeof(float));
+        H_CUDA(cudaMemcpyAsync(h->tap_wh, whi.data(), whi.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        H_CUDA(cudaMemcpyAsync(h->tap_wl, wlo.data(), wlo.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        H_CUDA(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
+    }
     for (int m = 0; m < h->r; ++m) cubic_weights((double)m / h->r, h->pw.w[m]);
     // mixed precision: the member update runs on the tensor cores when the
     // shapes allow (N = Ne + 1 <= 256); MGENKF_UPDATE=simt selects the
@@ -520,7 +535,7 @@ static void analyse_kernels(mgenkf_ctx *h, int gen_eps) {
     T *members = (T *)h->members, *xstar = (T *)h->xstar, *dC = (T *)h->dC;
     launch_restrict<T>((const T *)h->fine, xstar, h->dim, h->V, h->nc, h->r, s);
     if (h->recentre) launch_recentre<T>(members, nx, ne, xstar, h->status, s);
-    launch_obs_apply<T>(members, xstar, nx, ne, ny, h->taps, h->tap_idx, h->tap_w, h->yf, s);
+    launch_obs_apply<T>(members, xstar, nx, ne, ny, h->taps, h->tap_idx, h->tap_w, h->yf, s, h->tap_wh, h->tap_wl);
     launch_obs_mean(h->yf, h->yo, ne, ny, h->ybar, h->Z, h->status, s, h->df.Zh, h->df.Zl);
     launch_obs_perturb(h->yf, h->ybar, h->yo, h->eps, gen_eps, h->cfg.seed, h->cycle_d,
                        h->cfg.obs_sigma, ne, ny, h->Y, h->Z, s, h->df);
@@ -1351,6 +1366,8 @@ static GroupProb group_prob(const mgenkf_batch *b, size_t j) {
     g.dC = (float *)h->dC;
     g.tap_idx = h->tap_idx;
     g.tap_w = h->tap_w;
+    g.tap_wh = h->tap_wh;
+    g.tap_wl = h->tap_wl;
     g.yo_in = b->obs_stage + b->obs_off[j];
     g.yo = h->yo;
     g.yf = h->yf;

@@ -208,18 +208,22 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update_tc(const __grid_const
         // granule g stored at g ^ (pl mod 8)
         {
             const int ne = P.ne, pl = tid & (kTileM - 1), half = tid >> 7;
+            // the half's four slices as four independent chains in one loop
+            float sh[4] = {0.f, 0.f, 0.f, 0.f}, se[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int i0 = 4 * half; i0 < ne; i0 += 8) {
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    if (i0 + qq < ne) {
+                        const float x = sm[(i0 + qq) * kTileM + pl];
+                        const float t = sh[qq] + x, bv = t - sh[qq];
+                        se[qq] += (sh[qq] - (t - bv)) + (x - bv);
+                        sh[qq] = t;
+                    }
+                }
+            }
             float2 sl4[4];
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-                float sh = 0.f, se = 0.f;
-                for (int i = 4 * half + qq; i < ne; i += 8) {
-                    const float x = sm[i * kTileM + pl];
-                    const float t = sh + x, bv = t - sh;
-                    se += (sh - (t - bv)) + (x - bv);
-                    sh = t;
-                }
-                sl4[qq] = make_float2(sh, se);
-            }
+            for (int qq = 0; qq < 4; ++qq) sl4[qq] = make_float2(sh[qq], se[qq]);
             if (half) {
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) s_part[qq][pl] = sl4[qq];

@@ -283,3 +283,33 @@ def test_grouped_analysis_at_every_member_count_equals_handles(M):
         np.testing.assert_array_equal(f1, f0)
         np.testing.assert_array_equal(m1, m0)
     b.close()
+
+
+def _shear(nf, ne, n_probes, seed):
+    import dataclasses
+    w = W.ns2d_shear(nf=nf, ratio=4, ne=ne, n_probes=n_probes, cycles=4, precision="mixed", seed=seed)
+    return dataclasses.replace(w, name=f"edge_{nf}_{ne}_{seed}")
+
+
+@pytest.mark.parametrize("case", ["one problem", "extremes", "fallback"])
+def test_batch_edge_cases_equal_handles(M, case):
+    """A batch of one problem; Ne = 2 and Ne = 160, the largest the grouped
+    kernels take (its tensor-core update has room for one member buffer only,
+    so each tile's load waits for the previous tile's epilogue), beside a
+    ragged Ne = 17; and a batch with Ne = 161, which runs one chain per
+    problem: each problem's results are its own handle's, bit for bit."""
+    if case == "one problem":
+        ws = [_shear(64, 8, 32, 1)]
+    elif case == "extremes":
+        ws = [_shear(64, 2, 24, 2), _shear(64, 160, 200, 3), _shear(96, 17, 40, 4)]
+    else:
+        ws = [_shear(64, 161, 60, 5), _shear(64, 16, 30, 6)]
+    nsteps = [5, 5]
+    inps, yos = _inputs(ws, len(nsteps))
+    ref = _per_handle(M, ws, inps, yos, nsteps)
+    b = M.Batch(_runs(M, ws, inps))
+    got = _batched(M, b, ws, yos, nsteps)
+    for (f0, m0), (f1, m1) in zip(ref, got):
+        np.testing.assert_array_equal(f1, f0)
+        np.testing.assert_array_equal(m1, m0)
+    b.close()

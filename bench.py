@@ -1027,6 +1027,7 @@ def run_gpu_batched(args, dist):
                        "problems_rank0": len(ws), "steps_per_cycle": nsteps, "precision": "mixed",
                        "gain_form": "ensemble-space", "segment_rows": {str(k): M.SEGMENT_ROWS[v] for k, v in
                                                                 sorted(tiles.items())},
+                       "narrow_bands": [k for k, v in sorted(tiles.items()) if M.NARROW_BANDS[v]],
                        "tile_table": tuned, "autotune_s": t_tune,
                        "l2": f"not flushed: working set {sum(4 * 4 * (3 * problem_work(w)) for w in ws) / 1e9:.2f} GB "
                              f"(states + stage buffers) > L2 (129 MB)"},

@@ -307,11 +307,16 @@ mgenkf_status mgenkf_batch_forecast(mgenkf_batch_t b, int32_t nsteps);
 /* wait for the batch stream; returns the first device status of any problem */
 mgenkf_status mgenkf_batch_sync(mgenkf_batch_t b);
 /* Autotuner: for every grid size time `reps` repetitions of one model step
- * (written to scratch: the states are not touched) with each segment choice
- * of the forecast (rows per segment of the column march: 0 = 32, 1 = 16,
- * 2 = 64) and keep the fastest.  Synchronous; invalidates the captured graph. */
+ * (written to scratch: the states are not touched) with each choice of the
+ * forecast and keep the fastest.  A choice c in [0, 6) sets the rows per
+ * segment of the column march (c mod 3: 0 = 32, 1 = 16, 2 = 64) and its band
+ * width (c / 3: 0 = the whole width up to 512 points per side, 1 = bands of at
+ * most 122 columns with recomputed 3-column halos, about 64 threads per CTA).
+ * The arithmetic does not depend on the choice.  Synchronous; invalidates the
+ * captured graph. */
 mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps);
-/* read (up to max entries) / set the segment choice per grid size (`shapes`) */
+/* read (up to max entries) / set the forecast choice per grid size (`shapes`,
+ * each in [0, 6)) */
 mgenkf_status mgenkf_batch_tiles(mgenkf_batch_t b, int32_t *sizes, int32_t *shapes, int32_t max, int32_t *count);
 mgenkf_status mgenkf_batch_set_tiles(mgenkf_batch_t b, const int32_t *sizes, const int32_t *shapes, int32_t count);
 const char *mgenkf_batch_last_error(mgenkf_batch_t b);

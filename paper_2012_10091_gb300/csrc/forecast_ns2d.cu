@@ -601,6 +601,7 @@ __host__ __device__ __forceinline__ size_t march_smem_bytes(int threads) {
 }
 constexpr int kMarchMaxThreads = 256;
 constexpr int kMarchBandMax = 2 * kMarchMaxThreads - 6;  // output columns of a band (even)
+constexpr int kMarchNarrowBand = 122;  // output columns of a narrow band: 64 threads per CTA
 
 // Thread t's slot in a ring row (row pitch T + 2), and the slot that holds its
 // pair swapped for the thread at the other end of the fold (-1: none).
@@ -690,7 +691,10 @@ struct MarchUnit {
 };
 
 // bands and row segments of one n x n grid (host and device agree)
-__host__ __device__ __forceinline__ int march_bands(int n) {
+// bands of at most kMarchBandMax columns (the whole width up to 512), or
+// with `narrow` of at most kMarchNarrowBand (the whole width up to 128)
+__host__ __device__ __forceinline__ int march_bands(int n, bool narrow = false) {
+    if (narrow) return n <= 128 ? 1 : (n + kMarchNarrowBand - 1) / kMarchNarrowBand;
     return n <= 2 * kMarchMaxThreads ? 1 : (n + kMarchBandMax - 1) / kMarchBandMax;
 }
 __host__ __device__ __forceinline__ int march_band_width(int n, int bands) {
@@ -698,8 +702,8 @@ __host__ __device__ __forceinline__ int march_band_width(int n, int bands) {
     const int w = (n + bands - 1) / bands;
     return w + (w & 1);
 }
-__host__ __device__ __forceinline__ int march_threads(int n) {
-    const int b = march_bands(n);
+__host__ __device__ __forceinline__ int march_threads(int n, bool narrow = false) {
+    const int b = march_bands(n, narrow);
     return b == 1 ? n / 2 : (march_band_width(n, b) + 6) / 2;
 }
 
@@ -1013,14 +1017,19 @@ static void march_sequence(const Units &src, int ngroups, int units, int threads
     }
 }
 
-// rows per segment of the march for a segment choice (the batch's tuned "shape")
-int ns2d_seg_rows(int shape) { return shape == 1 ? 16 : (shape == 2 ? 64 : 32); }
+// rows per segment of the march for a choice (the batch's tuned "shape":
+// shape mod 3 the segment rows, shape / 3 = 1 narrow bands)
+int ns2d_seg_rows(int shape) {
+    const int r = shape % 3;
+    return r == 1 ? 16 : (r == 2 ? 64 : 32);
+}
 
 void ns2d_march_layout(int n, int shape, int *bands, int *segs, int *threads) {
     const int S = std::min(n, ns2d_seg_rows(shape));
-    *bands = march_bands(n);
+    const bool narrow = shape / 3 == 1;
+    *bands = march_bands(n, narrow);
     *segs = (n + S - 1) / S;
-    *threads = march_threads(n);
+    *threads = march_threads(n, narrow);
 }
 
 // per-handle FP64 launch: two groups (members, fine run) passed by value, 32 x 8 tiles
@@ -1130,11 +1139,11 @@ cudaError_t ns2d_forecast(T *whole, int n_whole, int n_whole_probs, T *split, in
 }
 
 static cudaError_t table_steps(const NsGroup<float> *d_groups, int ngroups, int units, int n, int nsteps,
-                               bool probe, double gamma, double mu, double prandtl, cudaStream_t s) {
+                               bool probe, double gamma, double mu, double prandtl, int shape, cudaStream_t s) {
     if (units == 0 || nsteps == 0) return cudaSuccess;
     const float gm1 = (float)(gamma - 1.0), m = (float)mu, kap = (float)(mu * gamma / ((gamma - 1.0) * prandtl));
     const TableUnits src{d_groups, ngroups};
-    const int threads = march_threads(n);
+    const int threads = march_threads(n, shape / 3 == 1);
     if (probe) {  // one step into the scratch buffers: the states stay as they are
         march_launch(src, units, threads, 0, gm1, m, kap, s);
         count_launches(1);
@@ -1145,13 +1154,13 @@ static cudaError_t table_steps(const NsGroup<float> *d_groups, int ngroups, int 
 }
 
 cudaError_t ns2d_forecast_table(const NsGroup<float> *d_groups, int ngroups, int units, int n, int nsteps,
-                                double gamma, double mu, double prandtl, cudaStream_t s) {
-    return table_steps(d_groups, ngroups, units, n, nsteps, false, gamma, mu, prandtl, s);
+                                double gamma, double mu, double prandtl, int shape, cudaStream_t s) {
+    return table_steps(d_groups, ngroups, units, n, nsteps, false, gamma, mu, prandtl, shape, s);
 }
 
 cudaError_t ns2d_probe_step(const NsGroup<float> *d_groups, int ngroups, int units, int n, double gamma,
-                            double mu, double prandtl, cudaStream_t s) {
-    return table_steps(d_groups, ngroups, units, n, 1, true, gamma, mu, prandtl, s);
+                            double mu, double prandtl, int shape, cudaStream_t s) {
+    return table_steps(d_groups, ngroups, units, n, 1, true, gamma, mu, prandtl, shape, s);
 }
 
 #define MGK_NS_INST(T)                                                                            \

@@ -15,9 +15,11 @@ struct NsGroup {
     T inv_h, inv_2h, dt;
 };
 
-// Segment choices of the FP32 step (the batch's tuned "tile shape" per grid
-// size): rows per segment of the march 0 = 32, 1 = 16, 2 = 64.
-constexpr int kNsTileShapes = 3;
+// Choices of the FP32 step (the batch's tuned "tile shape" per grid size):
+// rows per segment of the march (shape mod 3: 0 = 32, 1 = 16, 2 = 64) and the
+// band width (shape / 3: 0 = the whole width up to 512 columns, 1 = bands of
+// at most 122 columns, 64 threads per CTA).
+constexpr int kNsTileShapes = 6;
 int ns2d_seg_rows(int shape);
 // bands, row segments and threads per CTA of the FP32 step on an n x n grid
 void ns2d_march_layout(int n, int shape, int *bands, int *segs, int *threads);
@@ -26,7 +28,7 @@ void ns2d_march_layout(int n, int shape, int *bands, int *segs, int *threads);
 // all groups of grid size n, units = bands x segments x grids in total), FP32
 // states.
 cudaError_t ns2d_forecast_table(const NsGroup<float> *d_groups, int ngroups, int units, int n, int nsteps,
-                                double gamma, double mu, double prandtl, cudaStream_t s);
+                                double gamma, double mu, double prandtl, int shape, cudaStream_t s);
 
 // NULL if grids of n_whole (one member per CTA group) and n_split points per
 // side can be advanced, else the reason.
@@ -55,6 +57,6 @@ cudaError_t ns2d_forecast(T *whole, int n_whole, int n_whole_probs, T *split, in
 
 // one step from u0 into s1 (it leaves the states untouched): timing probe of the autotuner
 cudaError_t ns2d_probe_step(const NsGroup<float> *d_groups, int ngroups, int units, int n, double gamma,
-                            double mu, double prandtl, cudaStream_t s);
+                            double mu, double prandtl, int shape, cudaStream_t s);
 
 }  // namespace mgk

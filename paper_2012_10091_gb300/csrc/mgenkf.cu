@@ -1302,7 +1302,7 @@ static mgenkf_status batch_forecast(mgenkf_batch *b, int nsteps, bool join) {
         B_CUDA(cudaStreamWaitEvent(s, b->ev[0], 0));
         if (b->units[k]) {
             cudaError_t e = ns2d_forecast_table(b->d_groups[k], b->ngroups[k], b->units[k], b->sizes[k], nsteps,
-                                                b->gamma, b->mu, b->prandtl, s);
+                                                b->gamma, b->mu, b->prandtl, b->shape[k], s);
             if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("batched forecast: ") + cudaGetErrorString(e));
         }
         B_CUDA(cudaEventRecord(b->ev[1 + k], s));
@@ -1509,7 +1509,7 @@ static mgenkf_status batch_cycle_grouped(mgenkf_batch *b, int nsteps) {
             const size_t t = (size_t)p * ns + k;
             if (b->punits[t]) {
                 cudaError_t e = ns2d_forecast_table(b->pd_groups[t], b->pngroups[t], b->punits[t], b->sizes[k],
-                                                    nsteps, b->gamma, b->mu, b->prandtl, s);
+                                                    nsteps, b->gamma, b->mu, b->prandtl, b->shape[k], s);
                 if (e != cudaSuccess)
                     B_FAIL(MGENKF_ERR_CUDA, std::string("batched forecast: ") + cudaGetErrorString(e));
             }
@@ -1611,7 +1611,7 @@ extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
             float ms = 0.f;
             for (int r = 0; r <= reps; ++r) {  // first repetition warms up
                 B_CUDA(cudaEventRecord(t0, b->s0));
-                cudaError_t e = ns2d_probe_step(d, ng, units, b->sizes[si], b->gamma, b->mu, b->prandtl, b->s0);
+                cudaError_t e = ns2d_probe_step(d, ng, units, b->sizes[si], b->gamma, b->mu, b->prandtl, sh, b->s0);
                 if (e != cudaSuccess) B_FAIL(MGENKF_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
                 B_CUDA(cudaEventRecord(t1, b->s0));
                 B_CUDA(cudaEventSynchronize(t1));

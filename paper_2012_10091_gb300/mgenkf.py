@@ -466,8 +466,10 @@ class MGEnKF:
 # ---------------------------------------------------------------------------
 # batches of independent NS-2D problems (mgenkf_batch_* in include/mgenkf.h)
 # ---------------------------------------------------------------------------
-# segment choices of the batched forecast: rows per segment of the column march
-SEGMENT_ROWS = {0: 32, 1: 16, 2: 64}
+# choices of the batched forecast: rows per segment of the column march and
+# whether its bands are narrow (at most 122 columns)
+SEGMENT_ROWS = {c: (32, 16, 64)[c % 3] for c in range(6)}
+NARROW_BANDS = {c: c // 3 == 1 for c in range(6)}
 
 
 def _bcheck(st, where, b):
@@ -519,7 +521,7 @@ class Batch:
         return self.tiles()
 
     def tiles(self) -> dict:
-        """{grid size: segment choice} (SEGMENT_ROWS gives the rows per segment)."""
+        """{grid size: forecast choice} (SEGMENT_ROWS and NARROW_BANDS decode it)."""
         cnt = ctypes.c_int32()
         _bcheck(lib.mgenkf_batch_tiles(self.b, None, None, 0, ctypes.byref(cnt)), "mgenkf_batch_tiles", self.b)
         n = cnt.value
@@ -534,11 +536,12 @@ class Batch:
         _bcheck(lib.mgenkf_batch_set_tiles(self.b, sizes, shapes, n), "mgenkf_batch_set_tiles", self.b)
 
     def save_tiles(self, path):
-        """Persist the tuned table (JSON, grid size -> segment choice) for later runs."""
+        """Persist the tuned table (JSON, grid size -> forecast choice) for later runs."""
         import json
         with open(path, "w") as f:
             json.dump({"tiles": {str(k): v for k, v in self.tiles().items()},
-                       "segment_rows": {str(k): v for k, v in SEGMENT_ROWS.items()}}, f, indent=1)
+                       "segment_rows": {str(k): v for k, v in SEGMENT_ROWS.items()},
+                       "narrow_bands": {str(k): v for k, v in NARROW_BANDS.items()}}, f, indent=1)
 
     def load_tiles(self, path):
         import json

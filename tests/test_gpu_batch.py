@@ -92,7 +92,7 @@ def test_batch_equals_per_problem_handles(M, monkeypatch, grouped, parts):
     b.close()
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2])
+@pytest.mark.parametrize("shape", list(range(6)))
 def test_every_tile_shape_matches(M, shape):
     ws = _problems()
     nsteps = [10, 10]
@@ -103,7 +103,8 @@ def test_every_tile_shape_matches(M, shape):
     assert set(b.tiles().values()) == {shape}
     got = _batched(M, b, ws, yos, nsteps)
     for (f0, m0), (f1, m1) in zip(ref, got):
-        # the per-point arithmetic does not depend on the tile
+        # the per-point arithmetic does not depend on the segment length or
+        # on the band width
         np.testing.assert_array_equal(f1, f0)
         np.testing.assert_array_equal(m1, m0)
     b.close()
@@ -118,7 +119,7 @@ def test_autotune_and_persisted_tiles(M, tmp_path):
     assert set(tiles.values()) <= set(M.SEGMENT_ROWS)
     path = tmp_path / "tiles.json"
     b.save_tiles(path)
-    b.set_tiles({k: (v + 1) % 3 for k, v in tiles.items()})
+    b.set_tiles({k: (v + 1) % 6 for k, v in tiles.items()})
     b.load_tiles(path)
     assert b.tiles() == tiles
     # autotuning ran stages on scratch only: the states are still the initial ones

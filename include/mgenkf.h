@@ -312,8 +312,10 @@ mgenkf_status mgenkf_batch_sync(mgenkf_batch_t b);
  * segment of the column march (c mod 3: 0 = 32, 1 = 16, 2 = 64) and its band
  * width (c / 3: 0 = the whole width up to 512 points per side, 1 = bands of at
  * most 122 columns with recomputed 3-column halos, about 64 threads per CTA).
- * The arithmetic does not depend on the choice.  Synchronous; invalidates the
- * captured graph. */
+ * Then, size by size from the slowest, every choice is timed again with all
+ * grid sizes stepping at once on their own streams, as the forecast runs them,
+ * and the fastest joint choice is kept.  The arithmetic does not depend on the
+ * choice.  Synchronous; invalidates the captured graph. */
 mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps);
 /* read (up to max entries) / set the forecast choice per grid size (`shapes`,
  * each in [0, 6)) */

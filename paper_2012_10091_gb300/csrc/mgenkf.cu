@@ -1589,6 +1589,64 @@ extern "C" mgenkf_status mgenkf_batch_sync(mgenkf_batch_t b) {
 
 // Time one step into the scratch buffers (the states are not touched) of
 // every grid size with every segment choice and keep the fastest per size.
+constexpr int kJointSteps = 4;  // model steps per stream of one joint probe
+
+// `reps` timings (after one warm-up) of `steps` model steps of every grid size
+// at once, each size on its own stream as the forecast runs them, with the
+// current choices; the steps write to scratch, the states stay as they are.
+// Total milliseconds in *ms.
+static mgenkf_status probe_joint(mgenkf_batch *b, int steps, int reps, float *ms) {
+    std::vector<std::vector<NsGroup<float>>> tab;
+    build_tables(b, tab, 0, 0);
+    const int ns = (int)b->sizes.size();
+    std::vector<NsGroup<float> *> d(ns, nullptr);
+    std::vector<int> units(ns, 0);
+    mgenkf_status st = MGENKF_OK;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    auto cuda = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && st == MGENKF_OK) {
+            b->err = std::string("autotune: ") + what + ": " + cudaGetErrorString(e);
+            st = MGENKF_ERR_CUDA;
+        }
+        return st == MGENKF_OK;
+    };
+    for (int k = 0; k < ns && st == MGENKF_OK; ++k) {
+        if (tab[k].empty()) continue;
+        const NsGroup<float> &last = tab[k].back();
+        units[k] = last.tile_begin + last.tx * last.ty * last.nprob;
+        if (cuda(cudaMalloc(&d[k], tab[k].size() * sizeof(NsGroup<float>)), "cudaMalloc"))
+            cuda(cudaMemcpyAsync(d[k], tab[k].data(), tab[k].size() * sizeof(NsGroup<float>),
+                                 cudaMemcpyHostToDevice, b->s0),
+                 "cudaMemcpyAsync");
+    }
+    cuda(cudaEventCreate(&t0), "cudaEventCreate") && cuda(cudaEventCreate(&t1), "cudaEventCreate");
+    *ms = 0.f;
+    for (int r = 0; r <= reps && st == MGENKF_OK; ++r) {  // first repetition warms up
+        cuda(cudaEventRecord(t0, b->s0), "cudaEventRecord");
+        cuda(cudaEventRecord(b->ev[0], b->s0), "cudaEventRecord");
+        for (int k = 0; k < ns && st == MGENKF_OK; ++k) {
+            cudaStream_t s = b->aux[b->nbranch + k];
+            cuda(cudaStreamWaitEvent(s, b->ev[0], 0), "cudaStreamWaitEvent");
+            for (int i = 0; i < steps && units[k] && st == MGENKF_OK; ++i)
+                cuda(ns2d_probe_step(d[k], (int)tab[k].size(), units[k], b->sizes[k], b->gamma, b->mu, b->prandtl,
+                                     b->shape[k], s),
+                     "probe step");
+            cuda(cudaEventRecord(b->ev[1 + k], s), "cudaEventRecord");
+            cuda(cudaStreamWaitEvent(b->s0, b->ev[1 + k], 0), "cudaStreamWaitEvent");
+        }
+        cuda(cudaEventRecord(t1, b->s0), "cudaEventRecord");
+        cuda(cudaEventSynchronize(t1), "cudaEventSynchronize");
+        float t = 0.f;
+        if (cuda(cudaEventElapsedTime(&t, t0, t1), "cudaEventElapsedTime") && r) *ms += t;
+    }
+    cudaStreamSynchronize(b->s0);
+    for (NsGroup<float> *p : d)
+        if (p) cudaFree(p);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    return st;
+}
+
 extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
     if (!b || reps < 1) return MGENKF_ERR_INVALID_ARG;
     b->err.clear();
@@ -1596,6 +1654,7 @@ extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
     B_CUDA(cudaEventCreate(&t0));
     B_CUDA(cudaEventCreate(&t1));
     NsGroup<float> *d = nullptr;
+    std::vector<float> alone(b->sizes.size(), 0.f);
     for (size_t si = 0; si < b->sizes.size(); ++si) {
         float best = 1e30f;
         int best_shape = 0;
@@ -1627,9 +1686,35 @@ extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
             }
         }
         b->shape[si] = best_shape;
+        alone[si] = best;
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
+    // Alone, a size's last partial wave of CTAs counts in full; in the cycle the
+    // sizes step at once and fill each other's tails.  So, size by size (the
+    // slowest first), every choice is timed again with all sizes stepping
+    // together on their own streams, and the fastest joint choice is kept.
+    const int ns = (int)b->sizes.size();
+    if (ns > 1) {
+        std::vector<int> order(ns);
+        for (int k = 0; k < ns; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return alone[x] > alone[y]; });
+        for (int si : order) {
+            float best = 1e30f;
+            int best_shape = b->shape[si];
+            for (int sh = 0; sh < kNsTileShapes; ++sh) {
+                b->shape[si] = sh;
+                float ms = 0.f;
+                mgenkf_status st = probe_joint(b, kJointSteps, reps, &ms);
+                if (st) return st;
+                if (ms < best) {
+                    best = ms;
+                    best_shape = sh;
+                }
+            }
+            b->shape[si] = best_shape;
+        }
+    }
     std::vector<std::vector<NsGroup<float>>> tab;
     build_tables(b, tab, 0, 0);
     return upload_tables(b, tab);

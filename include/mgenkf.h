@@ -308,17 +308,18 @@ mgenkf_status mgenkf_batch_forecast(mgenkf_batch_t b, int32_t nsteps);
 mgenkf_status mgenkf_batch_sync(mgenkf_batch_t b);
 /* Autotuner: for every grid size time `reps` repetitions of one model step
  * (written to scratch: the states are not touched) with each choice of the
- * forecast and keep the fastest.  A choice c in [0, 6) sets the rows per
- * segment of the column march (c mod 3: 0 = 32, 1 = 16, 2 = 64) and its band
- * width (c / 3: 0 = the whole width up to 512 points per side, 1 = bands of at
- * most 122 columns with recomputed 3-column halos, about 64 threads per CTA).
+ * forecast and keep the fastest.  A choice c in [0, 10) sets the rows per
+ * segment of the column march (c mod 5: 0 = 32, 1 = 16, 2 = 64, 3 = 128,
+ * 4 = 256) and its band width (c / 5: 0 = the whole width up to 512 points
+ * per side, 1 = bands of at most 122 columns with recomputed 3-column halos,
+ * about 64 threads per CTA).
  * Then, size by size from the slowest, every choice is timed again with all
  * grid sizes stepping at once on their own streams, as the forecast runs them,
  * and the fastest joint choice is kept.  The arithmetic does not depend on the
  * choice.  Synchronous; invalidates the captured graph. */
 mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps);
 /* read (up to max entries) / set the forecast choice per grid size (`shapes`,
- * each in [0, 6)) */
+ * each in [0, 10)) */
 mgenkf_status mgenkf_batch_tiles(mgenkf_batch_t b, int32_t *sizes, int32_t *shapes, int32_t max, int32_t *count);
 mgenkf_status mgenkf_batch_set_tiles(mgenkf_batch_t b, const int32_t *sizes, const int32_t *shapes, int32_t count);
 const char *mgenkf_batch_last_error(mgenkf_batch_t b);

@@ -1018,15 +1018,17 @@ static void march_sequence(const Units &src, int ngroups, int units, int threads
 }
 
 // rows per segment of the march for a choice (the batch's tuned "shape":
-// shape mod 3 the segment rows, shape / 3 = 1 narrow bands)
+// shape mod kNsSegChoices the segment rows, shape / kNsSegChoices = 1 narrow
+// bands)
 int ns2d_seg_rows(int shape) {
-    const int r = shape % 3;
-    return r == 1 ? 16 : (r == 2 ? 64 : 32);
+    constexpr int rows[kNsSegChoices] = {32, 16, 64, 128, 256};
+    return rows[shape % kNsSegChoices];
 }
+bool ns2d_narrow(int shape) { return shape / kNsSegChoices == 1; }
 
 void ns2d_march_layout(int n, int shape, int *bands, int *segs, int *threads) {
     const int S = std::min(n, ns2d_seg_rows(shape));
-    const bool narrow = shape / 3 == 1;
+    const bool narrow = ns2d_narrow(shape);
     *bands = march_bands(n, narrow);
     *segs = (n + S - 1) / S;
     *threads = march_threads(n, narrow);
@@ -1143,7 +1145,7 @@ static cudaError_t table_steps(const NsGroup<float> *d_groups, int ngroups, int 
     if (units == 0 || nsteps == 0) return cudaSuccess;
     const float gm1 = (float)(gamma - 1.0), m = (float)mu, kap = (float)(mu * gamma / ((gamma - 1.0) * prandtl));
     const TableUnits src{d_groups, ngroups};
-    const int threads = march_threads(n, shape / 3 == 1);
+    const int threads = march_threads(n, ns2d_narrow(shape));
     if (probe) {  // one step into the scratch buffers: the states stay as they are
         march_launch(src, units, threads, 0, gm1, m, kap, s);
         count_launches(1);

@@ -16,11 +16,13 @@ struct NsGroup {
 };
 
 // Choices of the FP32 step (the batch's tuned "tile shape" per grid size):
-// rows per segment of the march (shape mod 3: 0 = 32, 1 = 16, 2 = 64) and the
-// band width (shape / 3: 0 = the whole width up to 512 columns, 1 = bands of
-// at most 122 columns, 64 threads per CTA).
-constexpr int kNsTileShapes = 6;
+// rows per segment of the march (shape mod 5: 0 = 32, 1 = 16, 2 = 64,
+// 3 = 128, 4 = 256) and the band width (shape / 5: 0 = the whole width up to
+// 512 columns, 1 = bands of at most 122 columns, 64 threads per CTA).
+constexpr int kNsSegChoices = 5;
+constexpr int kNsTileShapes = 2 * kNsSegChoices;
 int ns2d_seg_rows(int shape);
+bool ns2d_narrow(int shape);
 // bands, row segments and threads per CTA of the FP32 step on an n x n grid
 void ns2d_march_layout(int n, int shape, int *bands, int *segs, int *threads);
 

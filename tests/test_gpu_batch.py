@@ -92,7 +92,7 @@ def test_batch_equals_per_problem_handles(M, monkeypatch, grouped, parts):
     b.close()
 
 
-@pytest.mark.parametrize("shape", list(range(6)))
+@pytest.mark.parametrize("shape", list(range(10)))
 def test_every_tile_shape_matches(M, shape):
     ws = _problems()
     nsteps = [10, 10]
@@ -119,7 +119,7 @@ def test_autotune_and_persisted_tiles(M, tmp_path):
     assert set(tiles.values()) <= set(M.SEGMENT_ROWS)
     path = tmp_path / "tiles.json"
     b.save_tiles(path)
-    b.set_tiles({k: (v + 1) % 6 for k, v in tiles.items()})
+    b.set_tiles({k: (v + 1) % len(M.SEGMENT_ROWS) for k, v in tiles.items()})
     b.load_tiles(path)
     assert b.tiles() == tiles
     # autotuning ran stages on scratch only: the states are still the initial ones

@@ -61,11 +61,14 @@ WORKLOADS = {
     # primitives of its input, plus 8 + 20 + 20 for the three stage updates:
     # 3 x 125 + 48 = 423.  Algorithmic bytes: the state read and
     # written once per step, 2 x 4 variables x 4 B = 32 per point-step.
-    "ns2d": dict(flops=423, bytes=32, kernel="ns2d_rk3_step<32,16,2,PairTiles>", launches_per_step=1,
-                 traffic=None, truth="fp64"),
+    # The handle's forecast is the column march (autotuned layout), the members
+    # and the fine run on two streams: one launch each per model step, side by
+    # side; the roofline takes the whole forecast as one unit.
+    "ns2d": dict(flops=423, bytes=32, kernel="ns2d_rk3_march<TableUnits> members + fine run",
+                 launches_per_step=None, traffic=None, truth="fp64"),
     # NS-2D 1024^2 / 256^2 with the learned correction of the prolongation
-    "ns2d_cnn": dict(flops=423, bytes=32, kernel="ns2d_rk3_step<32,16,2,PairTiles>", launches_per_step=1,
-                     traffic=None, truth="fp64"),
+    "ns2d_cnn": dict(flops=423, bytes=32, kernel="ns2d_rk3_march<TableUnits> members + fine run",
+                     launches_per_step=None, traffic=None, truth="fp64"),
     # Dual EnKF parameter estimation on the Burgers inlet model (latency-bound: small grids)
     "dual": dict(kernel="k_burgers_inlet"),
     # 96 independent NS-2D problems: one march launch per model step and grid
@@ -347,6 +350,13 @@ def truth_and_obs(M, w, inp, ncycles, torch, truth_prec):
     return truths, yos
 
 
+def _layout(M, choice):
+    """Column-march layout of a handle's forecast (members, fine run) for the
+    config: rows per segment and narrow bands per grid."""
+    return {grid: {"segment_rows": M.SEGMENT_ROWS[c], "narrow_bands": M.NARROW_BANDS[c]}
+            for grid, c in zip(("members", "fine"), choice)}
+
+
 def run_gpu(args, dist, w, inp):
     import torch
 
@@ -367,6 +377,7 @@ def run_gpu(args, dist, w, inp):
 
     g = M.MGEnKF.from_workload(w, stream=sp)
     g.set_state(inp["fine0"], inp["members0"])
+    fc_choice = g.forecast_autotune(reps=3)  # NS-2D: the march layout per grid; Burgers: nothing to tune
     if args.regularise is not None:
         g.set_regularisation(args.regularise)
     rmse_dev = torch.zeros((ncyc, w.V), dtype=torch.float64, device="cuda")
@@ -530,6 +541,8 @@ def run_gpu(args, dist, w, inp):
     if not args.no_e2e:
         ge = M.MGEnKF.from_workload(w, stream=sp)
         ge.set_state(inp["fine0"], inp["members0"])
+        if fc_choice[0] >= 0:
+            ge.set_forecast_choice(*fc_choice)
         if args.regularise is not None:
             ge.set_regularisation(args.regularise)
         y_h = torch.empty((ncyc, w.ny), dtype=torch.float64, pin_memory=True)
@@ -584,7 +597,8 @@ def run_gpu(args, dist, w, inp):
                        "steps_per_cycle": w.steps_per_cycle, "precision": "mixed",
                        "gain_form": "ensemble-space", "replicas": dist.world,
                        "final_fine_iteration": args.regularise if args.regularise is not None else "off",
-                       "l2": "flushed between timed cycles (256 MB write)"},
+                       "l2": "flushed between timed cycles (256 MB write)",
+                       **({"forecast_layout": _layout(M, fc_choice)} if fc_choice[0] >= 0 else {})},
             "member_steps_per_s": value * w.ne * w.steps_per_cycle,
             "forecast_ms_per_cycle": fc_mean * 1e3,
             "analysis_ms_per_cycle": (t_total / args.steps - fc_mean) * 1e3,
@@ -1111,7 +1125,10 @@ def run_gpu_cnn(args, dist, w, inp):
         g = M.MGEnKF.from_workload(w, stream=sp)
         g.set_state(inp["fine0"], inp["members0"])
         if mode == "cnn":
+            fc_choice = g.forecast_autotune(reps=3)
             g.set_prolong_cnn(cnn)
+        else:
+            g.set_forecast_choice(*fc_choice)
         rm = torch.zeros((ncyc, w.V), dtype=torch.float64, device="cuda")
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
                torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -1155,6 +1172,7 @@ def run_gpu_cnn(args, dist, w, inp):
                        "steps_per_cycle": w.steps_per_cycle, "precision": "mixed",
                        "prolongation": "Pi_F + learned residual (BF16 CNN, 30080 parameters)",
                        "training_pairs": args.cnn_pairs, "epochs": args.cnn_epochs,
+                       "forecast_layout": _layout(M, fc_choice),
                        "l2": "inputs larger than L2 (fine state 16 MB, members 67 MB per cycle step)"},
             "plain_prolongation": {"cycles_per_s": res["plain"]["cps"],
                                    "prolong_ms": res["plain"]["prolong_ms"],

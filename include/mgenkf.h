@@ -105,6 +105,25 @@ mgenkf_status mgenkf_set_state(mgenkf_handle h, const double *fine, const double
  * (Algorithm 4 step 2, Algorithm 3 step 2).  nsteps >= 0. */
 mgenkf_status mgenkf_forecast(mgenkf_handle h, int32_t nsteps);
 
+/* Layout of the FP32 NS-2D forecast of a mixed-precision handle (Section 6
+ * model, SSP-RK3 step of Algorithm 4 step 2 and Algorithm 3 step 2): per grid
+ * (members, fine run) a choice c in [0, 10) of the column march, as described
+ * at mgenkf_batch_autotune (rows per segment and band width; the two grids
+ * then run on two streams), or -1 for both grids: the 2-D tile kernel, both
+ * grids in one launch per model step.  The per-point arithmetic, and so every
+ * result, is the same for all choices.  The default is set at create from the
+ * grid sizes: narrow bands above 256 points per side and the longest segments
+ * that still give each grid two units per SM.
+ * mgenkf_forecast_autotune times `reps` repetitions (after one warm-up) of
+ * model steps written to the stage buffers (the states are not touched) for
+ * every choice, each grid alone, then both at once as the forecast runs them,
+ * and keeps the fastest; synchronous.  It does nothing for other handles.
+ * mgenkf_set_forecast_choice returns MGENKF_ERR_INVALID_ARG for other handles,
+ * for a choice out of range, or for -1 on one grid only. */
+mgenkf_status mgenkf_forecast_autotune(mgenkf_handle h, int32_t reps);
+mgenkf_status mgenkf_get_forecast_choice(mgenkf_handle h, int32_t *members, int32_t *fine);
+mgenkf_status mgenkf_set_forecast_choice(mgenkf_handle h, int32_t members, int32_t fine);
+
 /* Analysis at the current time (Algorithm 4 steps 4-5 first line, Algorithm 3
  * steps 2-3 and 7-8): restriction, predicted observations, anomalies, gain
  * solve, member update and coarse correction dC = x^C' - x^C*.

@@ -1026,6 +1026,17 @@ int ns2d_seg_rows(int shape) {
 }
 bool ns2d_narrow(int shape) { return shape / kNsSegChoices == 1; }
 
+int ns2d_default_choice(int n, int grids, int sms) {
+    const int base = n > 256 ? kNsSegChoices : 0;
+    constexpr int longest_first[kNsSegChoices] = {4, 3, 2, 0, 1};  // 256, 128, 64, 32, 16 rows
+    for (int r : longest_first) {
+        int bands = 0, segs = 0, threads = 0;
+        ns2d_march_layout(n, base + r, &bands, &segs, &threads);
+        if ((long long)bands * segs * grids >= 2LL * sms) return base + r;
+    }
+    return base + 1;
+}
+
 void ns2d_march_layout(int n, int shape, int *bands, int *segs, int *threads) {
     const int S = std::min(n, ns2d_seg_rows(shape));
     const bool narrow = ns2d_narrow(shape);

@@ -23,6 +23,10 @@ constexpr int kNsSegChoices = 5;
 constexpr int kNsTileShapes = 2 * kNsSegChoices;
 int ns2d_seg_rows(int shape);
 bool ns2d_narrow(int shape);
+// default choice for `grids` n x n grids stepped on their own: narrow bands
+// above 256 points per side, the longest segments that still give two units
+// per SM (`sms` SMs), else 16 rows
+int ns2d_default_choice(int n, int grids, int sms);
 // bands, row segments and threads per CTA of the FP32 step on an n x n grid
 void ns2d_march_layout(int n, int shape, int *bands, int *segs, int *threads);
 

@@ -69,6 +69,15 @@ struct mgenkf_ctx {
     // mgenkf_cycle with a host truth: its copy runs on cstream beside the forecast
     cudaStream_t cstream = nullptr;
     cudaEvent_t ev_prev = nullptr, ev_truth = nullptr;
+    // mixed NS-2D forecast: a column-march choice per grid (members, fine run;
+    // ns2d_march_layout), or -1 for both (the 2-D tile kernel), the device
+    // table of the two groups for it, the fine run's stream and the events
+    // that fork it from and join it to the handle's stream
+    int fc_choice[2] = {-1, -1};
+    int fc_units[2] = {0, 0};
+    NsGroup<float> *d_fc = nullptr;
+    cudaStream_t fstream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -141,13 +150,16 @@ static void free_all(mgenkf_ctx *h) {
                     h->ybar, h->eps, h->Y, h->Z, h->X64, h->X16, h->Tt, h->S, h->Lt, h->Bt, h->C,
                     h->Ct, h->W, h->truth_d, h->rmse_part, h->rmse_d, h->scratch, h->status,
                     h->ns_scratch, h->gemm_part, h->cycle_d, h->fine_prev, h->fine_tmp,
-                    h->df.Yh, h->df.Yl, h->df.Zh, h->df.Zl};
+                    h->df.Yh, h->df.Yl, h->df.Zh, h->df.Zl, h->d_fc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->Tm && h->Tm != h->Bt) cudaFree(h->Tm);
     if (h->cstream) cudaStreamDestroy(h->cstream);
     if (h->ev_prev) cudaEventDestroy(h->ev_prev);
     if (h->ev_truth) cudaEventDestroy(h->ev_truth);
+    if (h->fstream) cudaStreamDestroy(h->fstream);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
 }
 
 // copy n doubles from a host or device pointer into device buffer dst (FP64)
@@ -244,6 +256,8 @@ static mgenkf_status validate(mgenkf_ctx *h, const mgenkf_config *c, const int32
     }
     return MGENKF_OK;
 }
+
+static mgenkf_status upload_fc_table(mgenkf_ctx *h);
 
 static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const int32_t *obs_index,
                                  const int32_t *obs_var) {
@@ -380,6 +394,18 @@ static mgenkf_status create_impl(mgenkf_ctx *h, const mgenkf_config *cfg, const 
         if (!(sel && strcmp(sel, "simt") == 0))
             update_tc_prepare(&h->tc, h->ldx, (int)h->nx, h->Tt, h->ntpad, h->ne, (const float *)h->members);
     }
+    if (h->mixed && cfg->model == MGENKF_NS2D) {
+        H_ALLOC(h->d_fc, 2 * sizeof(NsGroup<float>));
+        H_CUDA(cudaStreamCreateWithFlags(&h->fstream, cudaStreamNonBlocking));
+        H_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        H_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        int sms = 0;
+        H_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+        h->fc_choice[0] = ns2d_default_choice(h->nc, h->ne, sms);
+        h->fc_choice[1] = ns2d_default_choice(h->nf, 1, sms);
+        mgenkf_status st = upload_fc_table(h);
+        if (st) return st;
+    }
     H_CUDA(cudaStreamSynchronize(h->stream));
     return MGENKF_OK;
 }
@@ -458,6 +484,47 @@ extern "C" mgenkf_status mgenkf_get_state(mgenkf_handle h, double *fine, double 
     return MGENKF_OK;
 }
 
+// the two groups (members, fine run) of one handle, scratch laid out as in
+// ns2d_forecast_scratch
+static void handle_groups(const mgenkf_ctx *h, NsGroup<float> g[2]) {
+    const size_t sz0 = (size_t)4 * h->nc * h->nc * h->ne, sz1 = (size_t)4 * h->nf * h->nf;
+    float *sc = (float *)h->ns_scratch;
+    const int ns[2] = {h->nc, h->nf}, np[2] = {h->ne, 1};
+    float *u0[2] = {(float *)h->members, (float *)h->fine};
+    float *s1[2] = {sc, sc + 2 * sz0}, *s2[2] = {sc + sz0, sc + 2 * sz0 + sz1};
+    for (int k = 0; k < 2; ++k) {
+        g[k] = {};
+        g[k].u0 = u0[k];
+        g[k].s1 = s1[k];
+        g[k].s2 = s2[k];
+        g[k].n = ns[k];
+        g[k].nprob = np[k];
+        const double hh = h->cfg.length / ns[k];
+        g[k].inv_h = (float)(1.0 / hh);
+        g[k].inv_2h = (float)(1.0 / (2.0 * hh));
+        g[k].dt = (float)h->cfg.dt;
+    }
+}
+
+// the handle's forecast table for its current choices (synchronous)
+static mgenkf_status upload_fc_table(mgenkf_ctx *h) {
+    NsGroup<float> g[2];
+    handle_groups(h, g);
+    for (int k = 0; k < 2; ++k) {
+        h->fc_units[k] = 0;
+        if (h->fc_choice[k] < 0) continue;
+        int bands = 0, segs = 0, threads = 0;
+        ns2d_march_layout(g[k].n, h->fc_choice[k], &bands, &segs, &threads);
+        g[k].tx = bands;
+        g[k].ty = segs;
+        g[k].tile_begin = 0;
+        h->fc_units[k] = bands * segs * g[k].nprob;
+    }
+    H_CUDA(cudaMemcpyAsync(h->d_fc, g, sizeof(g), cudaMemcpyHostToDevice, h->stream));
+    H_CUDA(cudaStreamSynchronize(h->stream));
+    return MGENKF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // the cycle
 // ---------------------------------------------------------------------------
@@ -474,6 +541,24 @@ static mgenkf_status forecast_impl(mgenkf_ctx *h, int nsteps) {
     st = advance_impl(h, 1);
     if (st == MGENKF_OK) h->have_prev = true;
     return st;
+}
+
+// nsteps FP32 NS-2D steps with the column march: the members on the handle's
+// stream, the fine run beside them on its own stream (forked and joined by
+// events, so the call is ordered on the handle's stream as a whole)
+static cudaError_t march_forecast(mgenkf_ctx *h, int nsteps) {
+    const mgenkf_config &c = h->cfg;
+    cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->fstream, h->ev_fork, 0);
+    if (e == cudaSuccess)
+        e = ns2d_forecast_table(h->d_fc + 1, 1, h->fc_units[1], h->nf, nsteps, c.gamma, c.nu, c.prandtl,
+                                h->fc_choice[1], h->fstream);
+    if (e == cudaSuccess)
+        e = ns2d_forecast_table(h->d_fc, 1, h->fc_units[0], h->nc, nsteps, c.gamma, c.nu, c.prandtl,
+                                h->fc_choice[0], h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->fstream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    return e;
 }
 
 static mgenkf_status advance_impl(mgenkf_ctx *h, int nsteps) {
@@ -494,9 +579,12 @@ static mgenkf_status advance_impl(mgenkf_ctx *h, int nsteps) {
         e = cudaSuccess;
         for (int done = 0; done < nsteps && e == cudaSuccess; done += chunk) {
             if (h->mixed) {
-                e = ns2d_forecast_scratch<float>((float *)h->members, h->nc, h->ne, (float *)h->fine, h->nf, 1,
-                                                 c.length, c.dt, c.nu, c.gamma, c.prandtl, chunk,
-                                                 (float *)h->ns_scratch, h->stream);
+                if (h->fc_choice[0] >= 0)
+                    e = march_forecast(h, chunk);
+                else
+                    e = ns2d_forecast_scratch<float>((float *)h->members, h->nc, h->ne, (float *)h->fine, h->nf,
+                                                     1, c.length, c.dt, c.nu, c.gamma, c.prandtl, chunk,
+                                                     (float *)h->ns_scratch, h->stream);
                 if (e == cudaSuccess && h->filter_sigma > 0.0)
                     e = launch_ns2d_filter6<float>((float *)h->members, (float *)h->ns_scratch, h->nc, h->ne,
                                                    h->filter_sigma, h->stream);
@@ -525,6 +613,132 @@ extern "C" mgenkf_status mgenkf_forecast(mgenkf_handle h, int32_t nsteps) {
     if (!h) return MGENKF_ERR_INVALID_ARG;
     h->err.clear();
     return forecast_impl(h, nsteps);
+}
+
+static bool has_fc_choice(const mgenkf_ctx *h) { return h->mixed && h->cfg.model == MGENKF_NS2D; }
+
+extern "C" mgenkf_status mgenkf_get_forecast_choice(mgenkf_handle h, int32_t *members, int32_t *fine) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    if (members) *members = h->fc_choice[0];
+    if (fine) *fine = h->fc_choice[1];
+    return MGENKF_OK;
+}
+
+extern "C" mgenkf_status mgenkf_set_forecast_choice(mgenkf_handle h, int32_t members, int32_t fine) {
+    if (!h) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    if (!has_fc_choice(h)) H_FAIL(MGENKF_ERR_INVALID_ARG, "forecast choices exist for mixed-precision NS-2D handles");
+    const bool tile = members == -1 && fine == -1;
+    const bool march = members >= 0 && members < kNsTileShapes && fine >= 0 && fine < kNsTileShapes;
+    if (!tile && !march) H_FAIL(MGENKF_ERR_INVALID_ARG, "forecast choice out of range (each in [0, 10), or both -1)");
+    H_CUDA(cudaStreamSynchronize(h->stream));  // launches in flight read the old table
+    h->fc_choice[0] = members;
+    h->fc_choice[1] = fine;
+    return upload_fc_table(h);
+}
+
+// `reps` timings (after one warm-up) of kJointSteps model steps, written to
+// the stage buffers, of the handle's grids with the current choices: the
+// members (which & 1) on the handle's stream, the fine run (which & 2) on its
+// own; total milliseconds in *ms
+static constexpr int kHandleProbeSteps = 4;
+static mgenkf_status probe_handle(mgenkf_ctx *h, int which, int reps, cudaEvent_t t0, cudaEvent_t t1, float *ms) {
+    const mgenkf_config &c = h->cfg;
+    mgenkf_status st = upload_fc_table(h);
+    if (st) return st;
+    *ms = 0.f;
+    for (int r = 0; r <= reps; ++r) {
+        H_CUDA(cudaEventRecord(t0, h->stream));
+        H_CUDA(cudaEventRecord(h->ev_fork, h->stream));
+        H_CUDA(cudaStreamWaitEvent(h->fstream, h->ev_fork, 0));
+        for (int i = 0; i < kHandleProbeSteps; ++i) {
+            if (which & 2)
+                H_CUDA(ns2d_probe_step(h->d_fc + 1, 1, h->fc_units[1], h->nf, c.gamma, c.nu, c.prandtl,
+                                       h->fc_choice[1], h->fstream));
+            if (which & 1)
+                H_CUDA(ns2d_probe_step(h->d_fc, 1, h->fc_units[0], h->nc, c.gamma, c.nu, c.prandtl,
+                                       h->fc_choice[0], h->stream));
+        }
+        H_CUDA(cudaEventRecord(h->ev_join, h->fstream));
+        H_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+        H_CUDA(cudaEventRecord(t1, h->stream));
+        H_CUDA(cudaEventSynchronize(t1));
+        float t = 0.f;
+        H_CUDA(cudaEventElapsedTime(&t, t0, t1));
+        if (r) *ms += t;
+    }
+    return MGENKF_OK;
+}
+
+static mgenkf_status forecast_autotune_impl(mgenkf_ctx *h, int reps, cudaEvent_t t0, cudaEvent_t t1) {
+    const int start[2] = {h->fc_choice[0] >= 0 ? h->fc_choice[0] : 0, h->fc_choice[1] >= 0 ? h->fc_choice[1] : 0};
+    float alone[2] = {0.f, 0.f};
+    int best[2] = {start[0], start[1]};
+    // each grid alone
+    for (int k = 0; k < 2; ++k) {
+        float tbest = 1e30f;
+        for (int sh = 0; sh < kNsTileShapes; ++sh) {
+            h->fc_choice[0] = k == 0 ? sh : start[0];
+            h->fc_choice[1] = k == 1 ? sh : start[1];
+            float ms = 0.f;
+            mgenkf_status st = probe_handle(h, 1 << k, reps, t0, t1, &ms);
+            if (st) return st;
+            if (ms < tbest) {
+                tbest = ms;
+                best[k] = sh;
+            }
+        }
+        alone[k] = tbest;
+    }
+    // both at once, the slower grid first
+    const int order[2] = {alone[0] >= alone[1] ? 0 : 1, alone[0] >= alone[1] ? 1 : 0};
+    for (int k : order) {
+        float tbest = 1e30f;
+        int pick = best[k];
+        for (int sh = 0; sh < kNsTileShapes; ++sh) {
+            h->fc_choice[k] = sh;
+            h->fc_choice[1 - k] = best[1 - k];
+            float ms = 0.f;
+            mgenkf_status st = probe_handle(h, 3, reps, t0, t1, &ms);
+            if (st) return st;
+            if (ms < tbest) {
+                tbest = ms;
+                pick = sh;
+            }
+        }
+        best[k] = pick;
+    }
+    h->fc_choice[0] = best[0];
+    h->fc_choice[1] = best[1];
+    return upload_fc_table(h);
+}
+
+extern "C" mgenkf_status mgenkf_forecast_autotune(mgenkf_handle h, int32_t reps) {
+    if (!h || reps < 1) return MGENKF_ERR_INVALID_ARG;
+    h->err.clear();
+    if (!has_fc_choice(h)) return MGENKF_OK;
+    H_CUDA(cudaStreamSynchronize(h->stream));
+    const int keep[2] = {h->fc_choice[0], h->fc_choice[1]};
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    H_CUDA(cudaEventCreate(&t0));
+    mgenkf_status st = MGENKF_OK;
+    if (cudaEventCreate(&t1) != cudaSuccess) {
+        h->err = "cudaEventCreate failed";
+        st = MGENKF_ERR_CUDA;
+    }
+    if (st == MGENKF_OK) st = forecast_autotune_impl(h, reps, t0, t1);
+    if (st != MGENKF_OK) {  // keep the choices the handle had
+        cudaStreamSynchronize(h->stream);
+        cudaStreamSynchronize(h->fstream);
+        h->fc_choice[0] = keep[0];
+        h->fc_choice[1] = keep[1];
+        const std::string why = h->err;
+        upload_fc_table(h);
+        h->err = why;
+    }
+    cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    return st;
 }
 
 template <typename T>
@@ -1044,27 +1258,6 @@ static int size_index(const mgenkf_batch *b, int n) {
     return -1;
 }
 
-// the two groups (members, fine run) of one handle, scratch laid out as in
-// ns2d_forecast_scratch
-static void handle_groups(const mgenkf_ctx *h, NsGroup<float> g[2]) {
-    const size_t sz0 = (size_t)4 * h->nc * h->nc * h->ne, sz1 = (size_t)4 * h->nf * h->nf;
-    float *sc = (float *)h->ns_scratch;
-    const int ns[2] = {h->nc, h->nf}, np[2] = {h->ne, 1};
-    float *u0[2] = {(float *)h->members, (float *)h->fine};
-    float *s1[2] = {sc, sc + 2 * sz0}, *s2[2] = {sc + sz0, sc + 2 * sz0 + sz1};
-    for (int k = 0; k < 2; ++k) {
-        g[k] = {};
-        g[k].u0 = u0[k];
-        g[k].s1 = s1[k];
-        g[k].s2 = s2[k];
-        g[k].n = ns[k];
-        g[k].nprob = np[k];
-        const double hh = h->cfg.length / ns[k];
-        g[k].inv_h = (float)(1.0 / hh);
-        g[k].inv_2h = (float)(1.0 / (2.0 * hh));
-        g[k].dt = (float)h->cfg.dt;
-    }
-}
 
 // host tables of groups per grid size (only the size `only_size`, with the
 // segment choice `only_shape`, if given)

@@ -63,6 +63,9 @@ def _load():
         "mgenkf_create": [ctypes.POINTER(mgenkf_config), P, P, P, ctypes.POINTER(P)],
         "mgenkf_set_state": [P, P, P],
         "mgenkf_forecast": [P, i32],
+        "mgenkf_forecast_autotune": [P, i32],
+        "mgenkf_get_forecast_choice": [P, P, P],
+        "mgenkf_set_forecast_choice": [P, i32, i32],
         "mgenkf_analyse": [P, P, P],
         "mgenkf_prolong_correct": [P],
         "mgenkf_cycle": [P, i32, P, P, P],
@@ -381,6 +384,22 @@ class MGEnKF:
 
     def forecast(self, nsteps):
         mgenkf_forecast(self.h, nsteps)
+
+    def forecast_choice(self) -> tuple:
+        """(members, fine run) layout of the FP32 NS-2D forecast: column-march
+        choices (SEGMENT_ROWS and NARROW_BANDS decode them), or (-1, -1) for
+        the 2-D tile kernel."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.mgenkf_get_forecast_choice(self.h, ctypes.byref(a), ctypes.byref(b)),
+               "mgenkf_get_forecast_choice", self.h)
+        return a.value, b.value
+
+    def set_forecast_choice(self, members: int, fine: int):
+        _check(lib.mgenkf_set_forecast_choice(self.h, members, fine), "mgenkf_set_forecast_choice", self.h)
+
+    def forecast_autotune(self, reps=3) -> tuple:
+        _check(lib.mgenkf_forecast_autotune(self.h, reps), "mgenkf_forecast_autotune", self.h)
+        return self.forecast_choice()
 
     def analyse(self, y_obs, eps=None):
         mgenkf_analyse(self.h, y_obs, eps)

@@ -51,6 +51,9 @@ def _runs(M, ws, inps, gain_forms=None):
 def _per_handle(M, ws, inps, yos, nsteps, gain_forms=None):
     out = []
     for j, g in enumerate(_runs(M, ws, inps, gain_forms)):
+        # the handles step with the 2-D tile kernel, the batch with the column
+        # march: two kernels that must agree bit for bit
+        g.set_forecast_choice(-1, -1)
         for k, n in enumerate(nsteps):
             g.cycle(n, yos[j][k])
         assert g.sync() == 0

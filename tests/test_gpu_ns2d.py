@@ -103,14 +103,20 @@ def test_ns2d_fp32_multi_tile_matches_oracle(M, n, nprob):
         assert np.max(np.abs(got3[:, k] - ref3[:, k])) <= 1e-5 * np.max(np.abs(ref3[:, k])), k
 
 
-@pytest.mark.parametrize("steps", [10, 3])
-def test_ns2d_handle_forecast_at_full_size_matches_oracle(M, steps):
+@pytest.mark.parametrize("steps,kernel", [(10, "march"), (3, "march"), (10, "tile"), (3, "tile")])
+def test_ns2d_handle_forecast_at_full_size_matches_oracle(M, steps, kernel):
     # A handle of the 512^2 / 128^2, 64-member workload advances its members
-    # and fine run with the tile kernel: 64 x 16 + 256 = 1280 tiles of 32 x 32
-    # points over 2 x 152 resident CTAs (4.2 tiles per CTA).
+    # and fine run with the column march (its default choice: the members and
+    # the fine run on two streams; an odd step count ends with a copy back) or
+    # with the tile kernel: 64 x 16 + 256 = 1280 tiles of 32 x 32 points over
+    # 2 x 152 resident CTAs (4.2 tiles per CTA).
     w = W.ns2d_shear(nf=512, ratio=4, ne=64, n_probes=1024, cycles=1, precision="mixed")
     inp = W.make_inputs(w)
     g = M.MGEnKF.from_workload(w, precision="mixed")
+    if kernel == "tile":
+        g.set_forecast_choice(-1, -1)
+    else:
+        assert min(g.forecast_choice()) >= 0
     g.set_state(inp["fine0"], inp["members0"])
     g.forecast(steps)
     assert g.sync() == 0
@@ -130,6 +136,66 @@ def test_ns2d_handle_forecast_at_full_size_matches_oracle(M, steps):
         for k in range(4):
             scale = mom if k in (1, 2) else np.max(np.abs(ref[..., k, :, :]))
             assert np.max(np.abs(got[..., k, :, :] - ref[..., k, :, :])) <= 2e-5 * scale, k
+
+
+def _choice_handle(M):
+    # fine 544^2 (two whole-width bands, five narrow ones), coarse 136^2 (one
+    # whole-width band, two narrow ones): ragged bands and segments everywhere
+    w = W.ns2d_shear(nf=544, ratio=4, ne=6, n_probes=64, cycles=1, precision="mixed")
+    inp = W.make_inputs(w)
+    return w, inp, M.MGEnKF.from_workload(w, precision="mixed")
+
+
+def _advance(g, inp, steps):
+    g.set_state(inp["fine0"], inp["members0"])
+    g.forecast(steps)
+    assert g.sync() == 0
+    return g.get_state()
+
+
+@pytest.mark.parametrize("steps", [2, 3])
+def test_ns2d_handle_forecast_choices_are_bit_exact(M, steps):
+    """Every layout of a handle's FP32 forecast (the tile kernel, each column
+    march choice per grid) runs the same per-point arithmetic: bit-equal
+    states after an even and an odd number of steps."""
+    w, inp, g = _choice_handle(M)
+    default = g.forecast_choice()
+    assert all(c in M.SEGMENT_ROWS for c in default)
+    ref_f, ref_m = _advance(g, inp, steps)
+    g.set_forecast_choice(-1, -1)
+    assert g.forecast_choice() == (-1, -1)
+    tf, tm = _advance(g, inp, steps)
+    np.testing.assert_array_equal(tf, ref_f)
+    np.testing.assert_array_equal(tm, ref_m)
+    n = len(M.SEGMENT_ROWS)
+    for c in range(n):
+        g.set_forecast_choice(c, (c + 3) % n)
+        f, m = _advance(g, inp, steps)
+        np.testing.assert_array_equal(f, ref_f)
+        np.testing.assert_array_equal(m, ref_m)
+    g.close()
+
+
+def test_ns2d_forecast_autotune_and_choice_checks(M):
+    w, inp, g = _choice_handle(M)
+    ref_f, ref_m = _advance(g, inp, 3)
+    got = g.forecast_autotune(reps=1)
+    assert all(c in M.SEGMENT_ROWS for c in got) and g.forecast_choice() == got
+    f, m = _advance(g, inp, 3)
+    np.testing.assert_array_equal(f, ref_f)
+    np.testing.assert_array_equal(m, ref_m)
+    for bad in ((-1, 0), (0, -1), (len(M.SEGMENT_ROWS), 0), (0, -2)):
+        with pytest.raises(M.MGEnKFError):
+            g.set_forecast_choice(*bad)
+    assert g.forecast_choice() == got
+    g.close()
+    # FP64 handles have one forecast kernel: nothing to choose
+    w64 = W.ns2d_shear(nf=64, ratio=4, ne=4, n_probes=8, cycles=1, precision="fp64")
+    g64 = M.MGEnKF.from_workload(w64)
+    assert g64.forecast_autotune(reps=1) == (-1, -1)
+    with pytest.raises(M.MGEnKFError):
+        g64.set_forecast_choice(0, 0)
+    g64.close()
 
 
 def test_ns2d_rejects_bad_sizes(M):

@@ -106,6 +106,9 @@ def parse():
     ap.add_argument("--tiles", default=None,
                     help="batched: JSON tile table to load (autotuned and written there if missing)")
     ap.add_argument("--problems", type=int, default=96, help="batched: number of problems")
+    ap.add_argument("--forecast-choice", default="auto",
+                    help="ns2d, ns2d_cnn: layout of the handle's forecast, 'auto' (autotuned) or two "
+                         "choices 'members,fine' (see mgenkf_set_forecast_choice; -1,-1 the tile kernel)")
     ap.add_argument("--filter", type=float, default=None,
                     help="ns2d: add an ablation of the centred sixth-order filter of the NS model "
                          "(this strength after every model step): cycles/s and RMSE against no filter")
@@ -350,9 +353,20 @@ def truth_and_obs(M, w, inp, ncycles, torch, truth_prec):
     return truths, yos
 
 
+def _forecast_choice(g, args):
+    """Autotune the handle's forecast layout, or set the one given."""
+    if args.forecast_choice == "auto":
+        return g.forecast_autotune(reps=3)
+    m, f = (int(x) for x in args.forecast_choice.split(","))
+    g.set_forecast_choice(m, f)
+    return g.forecast_choice()
+
+
 def _layout(M, choice):
     """Column-march layout of a handle's forecast (members, fine run) for the
     config: rows per segment and narrow bands per grid."""
+    if choice[0] < 0:
+        return "2-D tile kernel, both grids in one launch per step"
     return {grid: {"segment_rows": M.SEGMENT_ROWS[c], "narrow_bands": M.NARROW_BANDS[c]}
             for grid, c in zip(("members", "fine"), choice)}
 
@@ -377,7 +391,7 @@ def run_gpu(args, dist, w, inp):
 
     g = M.MGEnKF.from_workload(w, stream=sp)
     g.set_state(inp["fine0"], inp["members0"])
-    fc_choice = g.forecast_autotune(reps=3)  # NS-2D: the march layout per grid; Burgers: nothing to tune
+    fc_choice = _forecast_choice(g, args)  # NS-2D: the march layout per grid; Burgers: nothing to choose
     if args.regularise is not None:
         g.set_regularisation(args.regularise)
     rmse_dev = torch.zeros((ncyc, w.V), dtype=torch.float64, device="cuda")
@@ -598,7 +612,7 @@ def run_gpu(args, dist, w, inp):
                        "gain_form": "ensemble-space", "replicas": dist.world,
                        "final_fine_iteration": args.regularise if args.regularise is not None else "off",
                        "l2": "flushed between timed cycles (256 MB write)",
-                       **({"forecast_layout": _layout(M, fc_choice)} if fc_choice[0] >= 0 else {})},
+                       **({"forecast_layout": _layout(M, fc_choice)} if args.workload == "ns2d" else {})},
             "member_steps_per_s": value * w.ne * w.steps_per_cycle,
             "forecast_ms_per_cycle": fc_mean * 1e3,
             "analysis_ms_per_cycle": (t_total / args.steps - fc_mean) * 1e3,
@@ -1125,7 +1139,7 @@ def run_gpu_cnn(args, dist, w, inp):
         g = M.MGEnKF.from_workload(w, stream=sp)
         g.set_state(inp["fine0"], inp["members0"])
         if mode == "cnn":
-            fc_choice = g.forecast_autotune(reps=3)
+            fc_choice = _forecast_choice(g, args)
             g.set_prolong_cnn(cnn)
         else:
             g.set_forecast_choice(*fc_choice)

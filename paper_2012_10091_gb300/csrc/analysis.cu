@@ -1623,7 +1623,6 @@ bool group_plan_build(GroupPlan *plan, const std::vector<GroupProb> &probs, cons
         auto add = [&](int step, long long nb) {
             for (long long b = 0; b < nb; ++b) m[step].push_back(make_int2(j, (int)b));
         };
-        const int nf = g.nc * g.r;
         add(kGsRestrict, ceil_div(g.nx, 256));
         add(kGsObsApply, (long long)ceil_div(g.ny, 128) * ceil_div(g.ne + 1, kObsRows));
         add(kGsObsMean, ceil_div(g.ny, 32));

@@ -351,8 +351,8 @@ __device__ __forceinline__ void ens_anom_body(const T *__restrict__ m, size_t nx
     // normalised anomalies: FP64 member-major rows, or BF16 point-major rows
     // assembled in shared memory so every row of ldx values is stored
     // contiguously.  GB300 runs about 2 FP64 FMAs per clock per SM, so FP32
-    // states are summed in double-FP32 arithmetic (no FP64 operation), and
-    // 1/Ne and 1/sqrt(Ne - 1) come from the host.
+    // states are averaged without FP64 operations (below), and 1/Ne and
+    // 1/sqrt(Ne - 1) come from the host.
     extern __shared__ __align__(16) unsigned char sm_raw[];
     double *part = reinterpret_cast<double *>(sm_raw);                        // [8][32]
     double *mean = part + 8 * 32;                                             // [32]
@@ -362,32 +362,32 @@ __device__ __forceinline__ void ens_anom_body(const T *__restrict__ m, size_t nx
     const size_t p0 = blk * 32;
     const size_t p = p0 + lane;
     const bool ok = p < nx;
+    // FP32 states: slice sums in floats [0, 256) of `part`, x_ref and the mean
+    // offset per lane in floats [256, 320)
+    float *rfm = reinterpret_cast<float *>(part) + 256;
     if constexpr (std::is_same<T, float>::value) {
-        // FP32 states: each slice an error-free FP32 sum (running sum and the
-        // sum of its rounding errors), the 8 slices combined in slice order in
-        // the same double-FP32 arithmetic, the mean rounded to FP32 (the
-        // tensor-core update forms its anomalies with these same operations)
-        float sh = 0.f, sl = 0.f;
+        // FP32 states: the mean as x_ref + dm, x_ref = member 0's value at the
+        // point and dm the mean of the differences x_i - x_ref.  Members at a
+        // point lie within a small spread of each other, so the differences
+        // are exact (Sterbenz) and their FP32 sum carries an error of order
+        // 2^-24 of the spread, not of the state.  Slice q (members q, q + 8,
+        // ...) is summed in member order, the 8 slices in slice order (the
+        // tensor-core update forms its anomalies with these same operations).
+        const float xr = ok ? (float)m[p] : 0.f;
+        float ps = 0.f;
         if (ok)
-            for (int i = wp; i < ne; i += 8) {
-                const float a = m[(size_t)i * nx + p];
-                const float t = sh + a, bv = t - sh;
-                sl += (sh - (t - bv)) + (a - bv);  // rounding error of sh + a, exact
-                sh = t;
-            }
-        float2 *part2 = reinterpret_cast<float2 *>(part);
-        part2[wp * 32 + lane] = make_float2(sh, sl);
+            for (int i = wp; i < ne; i += 8) ps = __fadd_rn(ps, __fsub_rn((float)m[(size_t)i * nx + p], xr));
+        float *partf = reinterpret_cast<float *>(part);
+        partf[wp * 32 + lane] = ps;
         __syncthreads();
         if (wp == 0) {
-            float H = 0.f, L = 0.f;
+            float D = 0.f;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float2 v = part2[q * 32 + lane];
-                const float t = H + v.x, bv = t - H;
-                L += (H - (t - bv)) + (v.x - bv) + v.y;
-                H = t;
-            }
-            mean[lane] = (double)((H + L) * (float)inv_ne);
+            for (int q = 0; q < 8; ++q) D = __fadd_rn(D, partf[q * 32 + lane]);
+            const float dm = __fmul_rn(D, (float)inv_ne);
+            rfm[lane] = xr;
+            rfm[32 + lane] = dm;
+            mean[lane] = (double)xr + (double)dm;
         }
     } else {
         double acc = 0.0;
@@ -410,13 +410,13 @@ __device__ __forceinline__ void ens_anom_body(const T *__restrict__ m, size_t nx
             for (int i = wp; i < ne; i += 8) X64[(size_t)i * nx + p] = ((double)m[(size_t)i * nx + p] - xb) * isq;
         return;
     }
-    // BF16 path: a mean accurate to its FP32 rounding, FP32 centring and
-    // scaling.  The FP32 rounding of the mean (2^-24 of the state) is far below
-    // the BF16 rounding of the anomaly (2^-9 of the anomaly) for any spread
-    // above 2^-15 of the state.
-    const float isqf = (float)isq, xbf = (float)xb;
+    // BF16 path (FP32 states): FP32 centring on the exact differences,
+    // ((x_i - x_ref) - dm) / sqrt(Ne - 1), then BF16 rounding (2^-9 of the
+    // anomaly, far above the FP32 errors of the centring)
+    const float isqf = (float)isq, xr = rfm[lane], dm = rfm[32 + lane];
     for (int i = wp; i < ldx; i += 8)
-        tile[lane * ldt + i] = __float2bfloat16((ok && i < ne) ? ((float)m[(size_t)i * nx + p] - xbf) * isqf : 0.f);
+        tile[lane * ldt + i] = __float2bfloat16(
+            (ok && i < ne) ? __fmul_rn(__fsub_rn(__fsub_rn((float)m[(size_t)i * nx + p], xr), dm), isqf) : 0.f);
     __syncthreads();
     // store: row r of the tile (point p0 + r) is ldx bf16 = ldx/8 16-byte chunks
     const int chunks = ldx / 8;

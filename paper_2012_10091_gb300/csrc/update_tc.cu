@@ -10,9 +10,10 @@
 //     values per swizzle atom) and of the members' 128-point tile ([Ne][128]
 //     FP32) and waits on an mbarrier;
 //   * warp 0 allocates TMEM for the 128 x N FP32 accumulator;
-//   * each thread forms its point's ensemble mean from the member tile (FP32
-//     error-free sums over 8 member slices, combined in FP64) and its row of
-//     BF16 anomalies (x_i - mean) / sqrt(Ne - 1), written in the 128-byte
+//   * each thread forms its point's ensemble mean from the member tile (x_ref
+//     = member 0's value plus the mean of the exact differences x_i - x_ref,
+//     summed in FP32 over 8 member slices) and its row of BF16 anomalies
+//     ((x_i - x_ref) - dm) / sqrt(Ne - 1), written in the 128-byte
 //     swizzled K-major layout the MMA reads (the layout TMA would write), so
 //     the members are read from HBM once for both the anomalies and the update;
 //   * one thread issues K/16 tcgen05.mma (kind::f16, cta_group::1) and commits
@@ -89,8 +90,8 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update_tc(const __grid_const
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + a.nbuf * bstride);  // members x2, MMA, T
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
     __shared__ int s_abort, s_next, s_next2, s_tload;
-    __shared__ float2 s_part[4][kTileM];  // slice sums 4..7 of the second thread half
-    __shared__ float s_mean[kTileM];
+    __shared__ float s_part[4][kTileM];  // slice sums 4..7 of the second thread half
+    __shared__ float2 s_ref[kTileM];     // per point: x_ref, mean offset dm
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int e0 = (int)((long long)blockIdx.x * nent / gridDim.x);
@@ -198,50 +199,39 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update_tc(const __grid_const
         ph ^= 1 << b;
         tph += tload ? 1 : 0;
         const int nk = s_next2;
-        // c. anomalies of point pl = tid mod 128: the ensemble mean from 8
-        // member slices i = q, q + 8, ... (half h = tid / 128 sums slices
-        // 4h .. 4h + 3), each an FP32 error-free sum (running sum and the sum
-        // of its rounding errors), the slices combined in slice order in the
-        // same double-FP32 arithmetic and the mean rounded to FP32; then the
-        // BF16 rows (x_i - mean) / sqrt(Ne - 1), K padding zero, granules split
-        // between the halves.  Row pl of atom kb: 8 granules of 16 bytes,
-        // granule g stored at g ^ (pl mod 8)
+        // c. anomalies of point pl = tid mod 128: the mean as x_ref + dm,
+        // x_ref = member 0's value and dm the mean of the differences
+        // x_i - x_ref (exact for members within a factor 2 of each other), the
+        // differences summed in FP32 per member slice i = q, q + 8, ... in
+        // member order (half h = tid / 128 sums slices 4h .. 4h + 3 as four
+        // independent chains), the slices in slice order; then the BF16 rows
+        // ((x_i - x_ref) - dm) / sqrt(Ne - 1), K padding zero, granules split
+        // between the halves.  The same operations as the CUDA-core anomaly
+        // kernel, so both updates see identical operands.  Row pl of atom kb:
+        // 8 granules of 16 bytes, granule g stored at g ^ (pl mod 8)
         {
             const int ne = P.ne, pl = tid & (kTileM - 1), half = tid >> 7;
-            // the half's four slices as four independent chains in one loop
-            float sh[4] = {0.f, 0.f, 0.f, 0.f}, se[4] = {0.f, 0.f, 0.f, 0.f};
+            const float xr = sm[pl];
+            float ps[4] = {0.f, 0.f, 0.f, 0.f};
             for (int i0 = 4 * half; i0 < ne; i0 += 8) {
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    if (i0 + qq < ne) {
-                        const float x = sm[(i0 + qq) * kTileM + pl];
-                        const float t = sh[qq] + x, bv = t - sh[qq];
-                        se[qq] += (sh[qq] - (t - bv)) + (x - bv);
-                        sh[qq] = t;
-                    }
-                }
+                for (int qq = 0; qq < 4; ++qq)
+                    if (i0 + qq < ne) ps[qq] = __fadd_rn(ps[qq], __fsub_rn(sm[(i0 + qq) * kTileM + pl], xr));
             }
-            float2 sl4[4];
-#pragma unroll
-            for (int qq = 0; qq < 4; ++qq) sl4[qq] = make_float2(sh[qq], se[qq]);
             if (half) {
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) s_part[qq][pl] = sl4[qq];
+                for (int qq = 0; qq < 4; ++qq) s_part[qq][pl] = ps[qq];
             }
             __syncthreads();
             if (!half) {
-                float H = 0.f, L = 0.f;
+                float D = 0.f;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float2 v = q < 4 ? sl4[q] : s_part[q - 4][pl];
-                    const float t = H + v.x, bv = t - H;
-                    L += (H - (t - bv)) + (v.x - bv) + v.y;
-                    H = t;
-                }
-                s_mean[pl] = (H + L) * (float)P.inv_ne;
+                for (int q = 0; q < 8; ++q) D = __fadd_rn(D, q < 4 ? ps[q] : s_part[q - 4][pl]);
+                s_ref[pl] = make_float2(xr, __fmul_rn(D, (float)P.inv_ne));
             }
             __syncthreads();
-            const float xbf = s_mean[pl], isqf = (float)P.isq;
+            const float2 rf = s_ref[pl];
+            const float isqf = (float)P.isq;
             const uint32_t sw = (uint32_t)(pl & 7);
             for (int gi = half; gi < P.kblocks * 8; gi += 2) {
                 const int kb = gi >> 3, g = gi & 7;
@@ -250,8 +240,11 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update_tc(const __grid_const
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     const int i0 = gi * 8 + 2 * h;
-                    const float v0 = i0 < ne ? (sm[i0 * kTileM + pl] - xbf) * isqf : 0.f;
-                    const float v1 = i0 + 1 < ne ? (sm[(i0 + 1) * kTileM + pl] - xbf) * isqf : 0.f;
+                    const float v0 =
+                        i0 < ne ? __fmul_rn(__fsub_rn(__fsub_rn(sm[i0 * kTileM + pl], rf.x), rf.y), isqf) : 0.f;
+                    const float v1 = i0 + 1 < ne
+                                         ? __fmul_rn(__fsub_rn(__fsub_rn(sm[(i0 + 1) * kTileM + pl], rf.x), rf.y), isqf)
+                                         : 0.f;
                     const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);  // v0 at the lower address
                     w[h] = *reinterpret_cast<const uint32_t *>(&b2);
                 }

@@ -74,11 +74,11 @@ WORKLOADS = {
     # 96 independent NS-2D problems: one march launch per model step and grid
     # size.  traffic_per_point_step: dram__bytes_read.sum + dram__bytes_write.sum
     # per point-step of the march launches of one cycle, measured by ncu on the
-    # 8-problem batch (16.71 B read, 4.55 B written: ncu counts the lines L2
+    # 8-problem batch (16.71 B read, 4.45 B written: ncu counts the lines L2
     # evicts during a launch; two-part cycle, autotuned choices), scaled to this
     # batch by its point-steps; None once the kernel changes.
     "batched": dict(flops=423, bytes=32, kernel="ns2d_rk3_march<TableUnits>", launches_per_step=None,
-                    traffic_per_point_step=21.26, truth="fp32"),
+                    traffic_per_point_step=21.15, truth="fp32"),
 }
 CNN_FLOPS_PER_PIXEL = 2 * 9 * (8 * 32 + 32 * 32 + 32 * 64)  # three 3x3 convolutions per coarse pixel
 

@@ -47,8 +47,9 @@ size_t ns2d_scratch_elems(int n_whole, int n_whole_probs, int n_split, int n_spl
 // Advance n_whole_probs grids of n_whole^2 x 4 and n_split_probs grids of
 // n_split^2 x 4 conserved variables by nsteps SSP-RK3 steps, with caller
 // scratch of ns2d_scratch_elems() elements.  FP32: with both groups (a
-// handle's members and fine run) one launch of the tile kernel per step, with
-// one group the column march.
+// handle's members and fine run, when its layout choice is -1) one launch of
+// the tile kernel per step, with one group the column march.  (A handle's
+// default steps each grid with ns2d_forecast_table on its own stream.)
 template <typename T>
 cudaError_t ns2d_forecast_scratch(T *whole, int n_whole, int n_whole_probs, T *split, int n_split,
                                   int n_split_probs, double length, double dt, double mu,

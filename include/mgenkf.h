@@ -107,7 +107,7 @@ mgenkf_status mgenkf_forecast(mgenkf_handle h, int32_t nsteps);
 
 /* Layout of the FP32 NS-2D forecast of a mixed-precision handle (Section 6
  * model, SSP-RK3 step of Algorithm 4 step 2 and Algorithm 3 step 2): per grid
- * (members, fine run) a choice c in [0, 10) of the column march, as described
+ * (members, fine run) a choice c in [0, 16) of the column march, as described
  * at mgenkf_batch_autotune (rows per segment and band width; the two grids
  * then run on two streams), or -1 for both grids: the 2-D tile kernel, both
  * grids in one launch per model step.  The per-point arithmetic, and so every
@@ -327,18 +327,18 @@ mgenkf_status mgenkf_batch_forecast(mgenkf_batch_t b, int32_t nsteps);
 mgenkf_status mgenkf_batch_sync(mgenkf_batch_t b);
 /* Autotuner: for every grid size time `reps` repetitions of one model step
  * (written to scratch: the states are not touched) with each choice of the
- * forecast and keep the fastest.  A choice c in [0, 10) sets the rows per
- * segment of the column march (c mod 5: 0 = 32, 1 = 16, 2 = 64, 3 = 128,
- * 4 = 256) and its band width (c / 5: 0 = the whole width up to 512 points
- * per side, 1 = bands of at most 122 columns with recomputed 3-column halos,
- * about 64 threads per CTA).
+ * forecast and keep the fastest.  A choice c in [0, 16) sets the rows per
+ * segment of the column march (c mod 8: 0 = 32, 1 = 16, 2 = 64, 3 = 128,
+ * 4 = 256, 5 = 24, 6 = 48, 7 = 20) and its band width (c / 8: 0 = the whole
+ * width up to 512 points per side, 1 = bands of at most 122 columns with
+ * recomputed 3-column halos, about 64 threads per CTA).
  * Then, size by size from the slowest, every choice is timed again with all
  * grid sizes stepping at once on their own streams, as the forecast runs them,
  * and the fastest joint choice is kept.  The arithmetic does not depend on the
  * choice.  Synchronous; invalidates the captured graph. */
 mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps);
 /* read (up to max entries) / set the forecast choice per grid size (`shapes`,
- * each in [0, 10)) */
+ * each in [0, 16)) */
 mgenkf_status mgenkf_batch_tiles(mgenkf_batch_t b, int32_t *sizes, int32_t *shapes, int32_t max, int32_t *count);
 mgenkf_status mgenkf_batch_set_tiles(mgenkf_batch_t b, const int32_t *sizes, const int32_t *shapes, int32_t count);
 const char *mgenkf_batch_last_error(mgenkf_batch_t b);

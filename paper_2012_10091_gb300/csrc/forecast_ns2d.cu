@@ -1021,14 +1021,14 @@ static void march_sequence(const Units &src, int ngroups, int units, int threads
 // shape mod kNsSegChoices the segment rows, shape / kNsSegChoices = 1 narrow
 // bands)
 int ns2d_seg_rows(int shape) {
-    constexpr int rows[kNsSegChoices] = {32, 16, 64, 128, 256};
+    constexpr int rows[kNsSegChoices] = {32, 16, 64, 128, 256, 24, 48, 20};
     return rows[shape % kNsSegChoices];
 }
 bool ns2d_narrow(int shape) { return shape / kNsSegChoices == 1; }
 
 int ns2d_default_choice(int n, int grids, int sms) {
     const int base = n > 256 ? kNsSegChoices : 0;
-    constexpr int longest_first[kNsSegChoices] = {4, 3, 2, 0, 1};  // 256, 128, 64, 32, 16 rows
+    constexpr int longest_first[kNsSegChoices] = {4, 3, 2, 6, 0, 5, 7, 1};  // 256, 128, 64, 48, 32, 24, 20, 16 rows
     for (int r : longest_first) {
         int bands = 0, segs = 0, threads = 0;
         ns2d_march_layout(n, base + r, &bands, &segs, &threads);

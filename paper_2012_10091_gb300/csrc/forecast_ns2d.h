@@ -16,10 +16,12 @@ struct NsGroup {
 };
 
 // Choices of the FP32 step (the batch's tuned "tile shape" per grid size):
-// rows per segment of the march (shape mod 5: 0 = 32, 1 = 16, 2 = 64,
-// 3 = 128, 4 = 256) and the band width (shape / 5: 0 = the whole width up to
-// 512 columns, 1 = bands of at most 122 columns, 64 threads per CTA).
-constexpr int kNsSegChoices = 5;
+// rows per segment of the march (shape mod 8: 0 = 32, 1 = 16, 2 = 64,
+// 3 = 128, 4 = 256, 5 = 24, 6 = 48, 7 = 20; a grid of n rows is cut into
+// ceil(n / rows) segments of equal length but the last) and the band width
+// (shape / 8: 0 = the whole width up to 512 columns, 1 = bands of at most 122
+// columns, 64 threads per CTA).
+constexpr int kNsSegChoices = 8;
 constexpr int kNsTileShapes = 2 * kNsSegChoices;
 int ns2d_seg_rows(int shape);
 bool ns2d_narrow(int shape);

@@ -630,7 +630,7 @@ extern "C" mgenkf_status mgenkf_set_forecast_choice(mgenkf_handle h, int32_t mem
     if (!has_fc_choice(h)) H_FAIL(MGENKF_ERR_INVALID_ARG, "forecast choices exist for mixed-precision NS-2D handles");
     const bool tile = members == -1 && fine == -1;
     const bool march = members >= 0 && members < kNsTileShapes && fine >= 0 && fine < kNsTileShapes;
-    if (!tile && !march) H_FAIL(MGENKF_ERR_INVALID_ARG, "forecast choice out of range (each in [0, 10), or both -1)");
+    if (!tile && !march) H_FAIL(MGENKF_ERR_INVALID_ARG, "forecast choice out of range (each in [0, 16), or both -1)");
     H_CUDA(cudaStreamSynchronize(h->stream));  // launches in flight read the old table
     h->fc_choice[0] = members;
     h->fc_choice[1] = fine;

@@ -487,8 +487,8 @@ class MGEnKF:
 # ---------------------------------------------------------------------------
 # choices of the batched forecast: rows per segment of the column march and
 # whether its bands are narrow (at most 122 columns)
-SEGMENT_ROWS = {c: (32, 16, 64, 128, 256)[c % 5] for c in range(10)}
-NARROW_BANDS = {c: c // 5 == 1 for c in range(10)}
+SEGMENT_ROWS = {c: (32, 16, 64, 128, 256, 24, 48, 20)[c % 8] for c in range(16)}
+NARROW_BANDS = {c: c // 8 == 1 for c in range(16)}
 
 
 def _bcheck(st, where, b):

@@ -95,7 +95,7 @@ def test_batch_equals_per_problem_handles(M, monkeypatch, grouped, parts):
     b.close()
 
 
-@pytest.mark.parametrize("shape", list(range(10)))
+@pytest.mark.parametrize("shape", list(range(16)))
 def test_every_tile_shape_matches(M, shape):
     ws = _problems()
     nsteps = [10, 10]

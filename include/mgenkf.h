@@ -115,9 +115,9 @@ mgenkf_status mgenkf_forecast(mgenkf_handle h, int32_t nsteps);
  * grid sizes: narrow bands above 256 points per side and the longest segments
  * that still give each grid two units per SM.
  * mgenkf_forecast_autotune times `reps` repetitions (after one warm-up) of
- * model steps written to the stage buffers (the states are not touched) for
- * every choice, each grid alone, then both at once as the forecast runs them,
- * and keeps the fastest; synchronous.  It does nothing for other handles.
+ * ten model steps written to the stage buffers (the states are not touched)
+ * for every choice, each grid alone, then both at once as the forecast runs
+ * them, and keeps the choice whose fastest repetition is fastest; synchronous.  It does nothing for other handles.
  * mgenkf_set_forecast_choice returns MGENKF_ERR_INVALID_ARG for other handles,
  * for a choice out of range, or for -1 on one grid only. */
 mgenkf_status mgenkf_forecast_autotune(mgenkf_handle h, int32_t reps);

@@ -637,11 +637,13 @@ extern "C" mgenkf_status mgenkf_set_forecast_choice(mgenkf_handle h, int32_t mem
     return upload_fc_table(h);
 }
 
-// `reps` timings (after one warm-up) of kJointSteps model steps, written to
-// the stage buffers, of the handle's grids with the current choices: the
-// members (which & 1) on the handle's stream, the fine run (which & 2) on its
-// own; total milliseconds in *ms
-static constexpr int kHandleProbeSteps = 4;
+// `reps` timings (after one warm-up) of kHandleProbeSteps model steps (one
+// observation interval of the workloads), written to the stage buffers, of the
+// handle's grids with the current choices: the members (which & 1) on the
+// handle's stream, the fine run (which & 2) on its own; the fastest
+// repetition's milliseconds in *ms (a few tens of microseconds per step, so
+// the minimum, not the sum, keeps a stray slow repetition from deciding)
+static constexpr int kHandleProbeSteps = 10;
 static mgenkf_status probe_handle(mgenkf_ctx *h, int which, int reps, cudaEvent_t t0, cudaEvent_t t1, float *ms) {
     const mgenkf_config &c = h->cfg;
     mgenkf_status st = upload_fc_table(h);
@@ -665,7 +667,7 @@ static mgenkf_status probe_handle(mgenkf_ctx *h, int which, int reps, cudaEvent_
         H_CUDA(cudaEventSynchronize(t1));
         float t = 0.f;
         H_CUDA(cudaEventElapsedTime(&t, t0, t1));
-        if (r) *ms += t;
+        if (r) *ms = r == 1 ? t : std::min(*ms, t);
     }
     return MGENKF_OK;
 }
@@ -1787,7 +1789,7 @@ constexpr int kJointSteps = 4;  // model steps per stream of one joint probe
 // `reps` timings (after one warm-up) of `steps` model steps of every grid size
 // at once, each size on its own stream as the forecast runs them, with the
 // current choices; the steps write to scratch, the states stay as they are.
-// Total milliseconds in *ms.
+// The fastest repetition's milliseconds in *ms.
 static mgenkf_status probe_joint(mgenkf_batch *b, int steps, int reps, float *ms) {
     std::vector<std::vector<NsGroup<float>>> tab;
     build_tables(b, tab, 0, 0);
@@ -1830,7 +1832,7 @@ static mgenkf_status probe_joint(mgenkf_batch *b, int steps, int reps, float *ms
         cuda(cudaEventRecord(t1, b->s0), "cudaEventRecord");
         cuda(cudaEventSynchronize(t1), "cudaEventSynchronize");
         float t = 0.f;
-        if (cuda(cudaEventElapsedTime(&t, t0, t1), "cudaEventElapsedTime") && r) *ms += t;
+        if (cuda(cudaEventElapsedTime(&t, t0, t1), "cudaEventElapsedTime") && r) *ms = r == 1 ? t : std::min(*ms, t);
     }
     cudaStreamSynchronize(b->s0);
     for (NsGroup<float> *p : d)
@@ -1869,7 +1871,7 @@ extern "C" mgenkf_status mgenkf_batch_autotune(mgenkf_batch_t b, int32_t reps) {
                 B_CUDA(cudaEventSynchronize(t1));
                 float t = 0.f;
                 B_CUDA(cudaEventElapsedTime(&t, t0, t1));
-                if (r) ms += t;
+                if (r) ms = r == 1 ? t : std::min(ms, t);
             }
             cudaFree(d);
             d = nullptr;

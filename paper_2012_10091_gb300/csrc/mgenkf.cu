@@ -1629,8 +1629,8 @@ static mgenkf_status batch_group_prepare(mgenkf_batch *b) {
         b->gplans.assign(nparts, GroupPlan());
         b->gplan_wait.clear();
         b->nparts = nparts;
-        // parts balanced by forecast work (points of the members and the
-        // fine run per step), largest problems first onto the lightest part
+        // parts with equal shares of the forecast work (points of the members
+        // and the fine run per step)
         const size_t n = b->hs.size();
         std::vector<double> work(n);
         std::vector<int> order(n);
@@ -1639,13 +1639,35 @@ static mgenkf_status batch_group_prepare(mgenkf_batch *b) {
             work[j] = (double)h->ne * h->nc * h->nc + (double)h->nf * h->nf;
             order[j] = (int)j;
         }
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
-        std::vector<double> load(nparts, 0.0);
         b->part.assign(n, 0);
-        for (int j : order) {
-            const int p = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-            b->part[j] = p;
-            load[p] += work[j];
+        // MGENKF_BATCH_SPLIT=work: the largest problems first onto the lightest
+        // part, whatever their Ne (used to measure the default against it)
+        const char *split = getenv("MGENKF_BATCH_SPLIT");
+        if (!(split && strcmp(split, "work") == 0)) {
+            // by ensemble size: the largest Ne first, each part filled to its
+            // share of the forecast work, so the last part (whose analysis
+            // follows the last forecast, exposed) holds the problems of the
+            // shortest analysis chains (the Cholesky and solve latencies grow
+            // with Ne) and the longer ones run beside the last forecast
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+                return b->hs[x]->ne != b->hs[y]->ne ? b->hs[x]->ne > b->hs[y]->ne : work[x] > work[y];
+            });
+            double total = 0.0, acc = 0.0;
+            for (double v : work) total += v;
+            int p = 0;
+            for (int j : order) {
+                b->part[j] = p;
+                acc += work[j];
+                while (p + 1 < nparts && acc >= total * (p + 1) / nparts) ++p;
+            }
+        } else {
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+            std::vector<double> load(nparts, 0.0);
+            for (int j : order) {
+                const int p = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                b->part[j] = p;
+                load[p] += work[j];
+            }
         }
         b->grouped = true;
         for (int p = 0; p < nparts && b->grouped; ++p) {

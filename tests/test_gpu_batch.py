@@ -72,15 +72,17 @@ def _batched(M, b, ws, yos, nsteps, innov=None):
     return [g.get_state() for g in b.runs]
 
 
-@pytest.mark.parametrize("grouped,parts", [("1", "1"), ("1", "2"), ("1", "4"), ("0", "1")])
-def test_batch_equals_per_problem_handles(M, monkeypatch, grouped, parts):
+@pytest.mark.parametrize("grouped,parts,split", [("1", "1", "ne"), ("1", "2", "ne"), ("1", "4", "ne"),
+                                                  ("1", "2", "work"), ("0", "1", "ne")])
+def test_batch_equals_per_problem_handles(M, monkeypatch, grouped, parts, split):
     """Grouped analysis (one launch per analysis step over the problems of a
     part; with several parts, part p's analysis runs beside part p + 1's
-    forecast) and the per-problem chains on the graph's branches
-    (MGENKF_BATCH_GROUPED=0) all give each problem's own handle results, bit
-    for bit."""
+    forecast; parts ordered by Ne or balanced by work alone) and the
+    per-problem chains on the graph's branches (MGENKF_BATCH_GROUPED=0) all
+    give each problem's own handle results, bit for bit."""
     monkeypatch.setenv("MGENKF_BATCH_GROUPED", grouped)
     monkeypatch.setenv("MGENKF_BATCH_PARTS", parts)
+    monkeypatch.setenv("MGENKF_BATCH_SPLIT", split)
     ws = _problems()
     assert len({w.nc for w in ws}) > 1 and len({w.ne for w in ws}) > 1
     nsteps = [10, 10, 7, 10]        # a changed step count recaptures the graph

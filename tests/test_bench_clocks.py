@@ -50,3 +50,51 @@ def test_throttle_reasons_are_collected_and_bad_lines_skipped():
 def test_missing_nvidia_smi_is_reported():
     c = bench.ClockSampler(0)
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+# --- forecast layout of a handle (bench --forecast-choice) -----------------
+class _FakeHandle:
+    """Stands in for MGEnKF: records the choice set or autotuned."""
+
+    def __init__(self, tuned=(7, 9)):
+        self.choice, self.tuned, self.calls = (-1, -1), tuned, []
+
+    def forecast_autotune(self, reps=3):
+        self.calls.append(("autotune", reps))
+        self.choice = self.tuned
+        return self.choice
+
+    def set_forecast_choice(self, m, f):
+        self.calls.append(("set", m, f))
+        self.choice = (m, f)
+
+    def forecast_choice(self):
+        return self.choice
+
+
+class _Args:
+    def __init__(self, forecast_choice):
+        self.forecast_choice = forecast_choice
+
+
+def test_forecast_choice_auto_tunes_and_explicit_sets():
+    g = _FakeHandle()
+    assert bench._forecast_choice(g, _Args("auto")) == (7, 9)
+    assert g.calls == [("autotune", 3)]
+    g = _FakeHandle()
+    assert bench._forecast_choice(g, _Args("1,9")) == (1, 9)
+    assert g.calls == [("set", 1, 9)]
+    g = _FakeHandle()
+    assert bench._forecast_choice(g, _Args("-1,-1")) == (-1, -1)
+
+
+def test_layout_decodes_choices_like_the_binding():
+    from paper_2012_10091_gb300 import build as B
+    B.build()  # the binding loads the library at import (no GPU needed)
+    from paper_2012_10091_gb300 import mgenkf as M
+    lay = bench._layout(M, (7, 9))
+    # choice c: rows (32, 16, 64, 128, 256, 24, 48, 20)[c % 8], narrow bands for c >= 8
+    assert lay == {"members": {"segment_rows": 20, "narrow_bands": False},
+                   "fine": {"segment_rows": 16, "narrow_bands": True}}
+    assert bench._layout(M, (-1, -1)).startswith("2-D tile kernel")
+    assert len(M.SEGMENT_ROWS) == len(M.NARROW_BANDS) == 16

@@ -354,7 +354,10 @@ def truth_and_obs(M, w, inp, ncycles, torch, truth_prec):
 
 
 def _forecast_choice(g, args):
-    """Autotune the handle's forecast layout, or set the one given."""
+    """Autotune the handle's forecast layout, or set the one given (NS-2D
+    workloads; the Burgers forecast has no layout to choose)."""
+    if getattr(args, "workload", "ns2d") not in ("ns2d", "ns2d_cnn"):
+        return g.forecast_choice()
     if args.forecast_choice == "auto":
         return g.forecast_autotune(reps=3)
     m, f = (int(x) for x in args.forecast_choice.split(","))

@@ -73,8 +73,8 @@ class _FakeHandle:
 
 
 class _Args:
-    def __init__(self, forecast_choice):
-        self.forecast_choice = forecast_choice
+    def __init__(self, forecast_choice, workload="ns2d"):
+        self.forecast_choice, self.workload = forecast_choice, workload
 
 
 def test_forecast_choice_auto_tunes_and_explicit_sets():
@@ -86,6 +86,9 @@ def test_forecast_choice_auto_tunes_and_explicit_sets():
     assert g.calls == [("set", 1, 9)]
     g = _FakeHandle()
     assert bench._forecast_choice(g, _Args("-1,-1")) == (-1, -1)
+    g = _FakeHandle()  # Burgers: no layout, the choice flag is ignored
+    assert bench._forecast_choice(g, _Args("1,9", workload="burgers_large")) == (-1, -1)
+    assert g.calls == []
 
 
 def test_layout_decodes_choices_like_the_binding():
